@@ -1,0 +1,199 @@
+"""Preconditioner of the oracle.
+
+Block-diagonal preconditioner (Eq. (stoch-prec) steady, Eq. (precon for time)):
+  block 1: M_gamma^{-1}   ~ Chebyshev semi-iteration on M, columns scaled by 1/H^gamma
+  block 2: (beta M)^{-1}  ~ Chebyshev on M, scaled by 1/beta
+  block 3: S^{-1} = Z^{-1} M_gamma Z^{-1} with Z = A + sqrt((1+gamma)/beta) M_cal (Eq. (mathcalZ));
+           time: S~^{-1} = tau Z~^{-1} (D (x) M_gamma) Z~^{-1} with Z~ block diagonal in time
+           (Eqs. (Z hat approx), (S_tilde), (S hat)); time blocks 1, 2 carry the extra 1/(tau D_t).
+  Solves with Z / Z~ use the hierarchical Gauss-Seidel sweep of Alg. 1 (one application,
+  i.e. the Richardson iteration of Sec. 5 with N = 1 and zero initial guess), truncated to
+  the first r terms of the expansion (Sec. 2, Eq. (matvec-block) and the index set I_tau).
+
+Readings (the paper leaves these open):
+* Chebyshev: the textbook Golub-Varga semi-iteration with omega_1 = 1,
+  omega_2 = 2/(2-rho^2), omega_{k+1} = 1/(1 - rho^2 omega_k / 4), x^(0) = 0, and the
+  paper's D = (lmin+lmax)/2 diag(M), rho = (lmax-lmin)/(lmax+lmin), lmin = 1/4, lmax = 9/4.
+* hGS: correction form V_(d) += B (R_(d) - (Z_r V)_(d)) over the palindromic level order
+  0, 1, ..., p, ..., 1, 0; identical to Alg. 1 when B = A~_1^{-1} and symmetric for any
+  symmetric B.
+* Mean solves B: one V(nu_pre, nu_post) cycle with damped Jacobi (omega), bilinear
+  prolongation P, restriction P^T and Galerkin coarse operators P^T A P, down to the
+  2x2-element grid (one interior node) which is solved exactly; or, in 'exact' mode,
+  a sparse LU solve (used for pins only).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import basis
+
+
+# ---------------------------------------------------------------- Chebyshev --
+CHEB_LMIN, CHEB_LMAX = 0.25, 2.25
+
+
+def chebyshev(Mass, B, steps):
+    """N-step Chebyshev semi-iteration for Mass X = B (B: n or n x c)."""
+    gam = 0.5 * (CHEB_LMIN + CHEB_LMAX)
+    rho = (CHEB_LMAX - CHEB_LMIN) / (CHEB_LMAX + CHEB_LMIN)
+    dinv = 1.0 / (gam * Mass.diagonal())
+    if B.ndim == 2:
+        dinv = dinv[:, None]
+    x_old = np.zeros_like(B)
+    x = np.zeros_like(B)
+    omega = 1.0
+    for k in range(steps):
+        if k == 0:
+            omega = 1.0
+        elif k == 1:
+            omega = 2.0 / (2.0 - rho * rho)
+        else:
+            omega = 1.0 / (1.0 - rho * rho * omega / 4.0)
+        r = B - Mass @ x
+        x_new = omega * (dinv * r + x - x_old) + x_old
+        x_old, x = x, x_new
+    return x
+
+
+# ----------------------------------------------------------------- V-cycle --
+def prolongation(nx: int):
+    """Bilinear interpolation from the (nx/2)-element grid to the nx-element grid,
+    interior nodes only (x1 fastest): P = P1 (x) P1."""
+    mf, mc = nx - 1, nx // 2 - 1
+    P1 = sp.lil_matrix((mf, mc))
+    for I in range(1, nx // 2):
+        fi = 2 * I - 1                 # 0-based fine interior index of fine node 2I
+        P1[fi, I - 1] = 1.0
+        P1[fi - 1, I - 1] = 0.5
+        if fi + 1 < mf:
+            P1[fi + 1, I - 1] = 0.5
+    P1 = P1.tocsr()
+    return sp.kron(P1, P1, format="csr")
+
+
+class VCycle:
+    """Geometric multigrid V-cycle for an SPD Q1 operator on a power-of-two grid."""
+
+    def __init__(self, A, nx, nu_pre=2, nu_post=2, omega=0.8):
+        assert nx >= 2 and (nx & (nx - 1)) == 0, "grid must be a power of two"
+        self.levels = []      # (A, dinv, P to this level from the next coarser)
+        self.nu_pre, self.nu_post, self.omega = nu_pre, nu_post, omega
+        A = sp.csr_matrix(A)
+        while True:
+            if nx == 2:
+                self.levels.append((A, None, None))
+                break
+            P = prolongation(nx)
+            self.levels.append((A, 1.0 / A.diagonal(), P))
+            A = sp.csr_matrix(P.T @ A @ P)
+            nx //= 2
+        self.coarse = A.toarray()
+
+    def apply(self, B, level=0):
+        """One V-cycle with zero initial guess for A X = B (B: n or n x c)."""
+        A, dinv, P = self.levels[level]
+        if P is None:
+            return np.linalg.solve(self.coarse, B)
+        d = dinv[:, None] if B.ndim == 2 else dinv
+        X = np.zeros_like(B)
+        for _ in range(self.nu_pre):
+            X = X + self.omega * d * (B - A @ X)
+        R = B - A @ X
+        X = X + P @ self.apply(P.T @ R, level + 1)
+        for _ in range(self.nu_post):
+            X = X + self.omega * d * (B - A @ X)
+        return X
+
+
+class ExactSolve:
+    def __init__(self, A):
+        self.lu = spla.splu(sp.csc_matrix(A))
+
+    def apply(self, B):
+        return self.lu.solve(B)
+
+
+# --------------------------------------------------------------------- hGS --
+def visit_order(p: int):
+    """Level order of one symmetric hierarchical sweep: 0, 1, ..., p, ..., 1, 0."""
+    return list(range(p + 1)) + list(range(p - 1, -1, -1))
+
+
+class HGS:
+    """One application of the hierarchical Gauss-Seidel sweep (Alg. 1) to
+    Z_r = A~_0 (x) I + sum_{k=1}^{r-1} G_k (x) coef_k K_k, matricized."""
+
+    def __init__(self, data, A0, coef, r, mean_solver):
+        self.d = data
+        self.A0 = A0                   # mean operator A~_1 (steady) / A^_1 (time)
+        self.coef = coef               # scalar multiplying K_k, k >= 1 (1 steady, tau time)
+        self.r = r
+        self.B = mean_solver
+        self.off = basis.level_offsets(data.M, data.p)
+
+    def zr_apply(self, V):
+        Y = self.A0 @ V
+        for k in range(1, self.r):
+            Y += self.coef * (self.d.K[k] @ V @ self.d.G[k])
+        return Y
+
+    def apply(self, R):
+        V = np.zeros_like(R)
+        for lev in visit_order(self.d.p):
+            a, b = self.off[lev], self.off[lev + 1]
+            rhs = R[:, a:b] - self.zr_apply(V)[:, a:b]
+            V[:, a:b] += self.B.apply(rhs)
+        return V
+
+
+# ------------------------------------------------------- block preconditioner --
+class BlockPreconditioner:
+    def __init__(self, data, mode="vcycle"):
+        self.d = data
+        pr = data.pr
+        s = math.sqrt((1.0 + data.gamma) / data.beta)
+        Mm = data.Mass
+        if data.nt == 0:
+            A0 = data.K[0] + s * Mm                       # A~_1 = A_1 + sqrt((1+g)/b) M
+            coef = 1.0
+        else:
+            tau = data.tau
+            A0 = (1.0 + tau * s) * Mm + tau * data.K[0]   # A^_1 of Eq. (A_hat)
+            coef = tau
+        self.A0 = A0
+        if mode == "exact":
+            solver = ExactSolve(A0)
+        else:
+            solver = VCycle(A0, data.nx, pr.nu_pre, pr.nu_post, pr.omega)
+        self.hgs = HGS(data, A0, coef, pr.trunc, solver)
+        self.steps = pr.cheb_steps
+
+    def apply(self, r):
+        d = self.d
+        F = d.slabs * d.P * d.n
+        nP = d.P * d.n
+        z = np.zeros_like(r)
+        Mm = d.Mass
+        Dw = d.d_weights()
+        for t in range(d.slabs):
+            sl = slice(t * nP, (t + 1) * nP)
+            R1 = d.mat(r[:F][sl])
+            R2 = d.mat(r[F:2 * F][sl])
+            R3 = d.mat(r[2 * F:][sl])
+            sc = 1.0 if d.nt == 0 else d.tau * Dw[t]
+            Z1 = chebyshev(Mm, R1, self.steps) / (sc * d.hgam[None, :])
+            Z2 = chebyshev(Mm, R2, self.steps) / (sc * d.beta)
+            W = self.hgs.apply(R3)
+            if d.nt == 0:
+                Z3 = self.hgs.apply(Mm @ W * d.hgam[None, :])
+            else:
+                Z3 = d.tau * self.hgs.apply(Dw[t] * (Mm @ W) * d.hgam[None, :])
+            z[:F][sl] = d.vec(Z1)
+            z[F:2 * F][sl] = d.vec(Z2)
+            z[2 * F:][sl] = d.vec(Z3)
+        return z
