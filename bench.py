@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark of the SG-KKT solve on the 128x128 Q1 workload (M=6, p=3, P=84,
+beta in {1e-2, 1e-4, 1e-6}): solves/s at a 1e-8 float64 relative residual.
+
+One step = the three solves of the workload (a batch), in the library's
+mixed precision (float32 operator/preconditioner/inner MINRES inside float64
+iterative refinement; --precision fp64 for the plain float64 path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Multi-GPU: replicas only (each rank solves its
+own batch, no collective on the data path), value = all solves / max time.
+`--impl reference` times the float64 CPU oracle on bounded samples of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SG-KKT solves/s at 1e-8 rel. residual, p50/p99 latency; SG matvec HBM GB/s"
+UNIT = "solves/s"
+WORKLOAD = "steady_128x128_M6_p3_P84_beta{1e-2,1e-4,1e-6}"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip fp64/e2e/profile/matvec legs")
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured", d
+    return 6800.0, "fallback", {}
+
+
+# float64 ALU peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2070 MHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# float32 non-tensor peak: 152 SMs x 128 FMA/clk x 2 flop x 2070 MHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------- oracle arm --
+def oracle_sample(beta, iters):
+    """Time oracle set-up + `iters` MINRES iterations of one solve; returns (seconds, full-solve estimate)."""
+    import sg_inputs as si
+    from oracle.krylov import minres
+    from oracle.operators import SGData
+    from oracle.precond import BlockPreconditioner
+    t0 = time.perf_counter()
+    pr = si.steady_128(beta)
+    d = SGData(pr)
+    Pc = BlockPreconditioner(d)
+    b = d.rhs()
+    t1 = time.perf_counter()
+    minres(d.kkt_apply, Pc.apply, b, tol=pr.tol, max_iter=iters)
+    t2 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / iters
+
+
+def oracle_iterations():
+    path = os.path.join(ROOT, "tests", "golden", "full_size_oracle.json")
+    out = {}
+    if os.path.exists(path):
+        g = json.load(open(path))
+        for b in (1e-2, 1e-4, 1e-6):
+            key = "steady_128_beta%g" % b
+            if key in g:
+                out[b] = g[key]["iterations"]
+    return out
+
+
+def cpu_baseline_value(iters_sample=3, betas=(1e-4,), gpu_iters=None):
+    its = oracle_iterations()
+    total_s, parts = 0.0, []
+    for b in betas:
+        t_setup, t_it = oracle_sample(b, iters_sample)
+        n_it = its.get(b) or (gpu_iters or {}).get(b) or 40
+        parts.append((b, t_setup, t_it, n_it))
+        total_s += t_setup + t_it * n_it
+    per_solve = total_s / len(betas)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    sample = "; ".join(f"beta={b:g}: set-up {ts:.1f}s + {iters_sample} MINRES iterations at {ti:.2f}s, "
+                       f"scaled to the oracle's {n} iterations" for b, ts, ti, n in parts)
+    return 1.0 / per_solve, cores, sample
+
+
+def run_reference(args):
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return
+    betas = (1e-2, 1e-4, 1e-6)
+    vals = []
+    for s in range(args.warmup + args.steps):
+        b = betas[s % 3]
+        v, cores, sample = cpu_baseline_value(iters_sample=2, betas=(b,))
+        if s >= args.warmup:
+            vals.append(1.0 / v)
+    sec_per_solve = sum(vals) / len(vals)
+    value = 1.0 / sec_per_solve
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 3e3 * sec_per_solve,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "solves_per_step": 3},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "each step: set-up + 2 MINRES iterations of one beta, scaled to the "
+                                   "oracle's full iteration count"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm --
+def run_ours(args):
+    import torch
+    import sg_inputs as si
+    world, rank, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2512_23804_gb300 import SGProblem, abi, build
+    build.build()
+    lib = abi.load()
+    hbm_peak, peak_kind, _ = load_peaks()
+
+    betas = si.STEADY_128_BETAS
+    problems = [si.steady_128(b) for b in betas]
+    sps = [SGProblem.from_problem(pr, precision=args.precision).upload() for pr in problems]
+    for sp in sps:
+        sp.workspace()
+    xs = [torch.empty(sp.kkt_size, dtype=torch.float64, device="cuda") for sp in sps]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(record=None):
+        infos = []
+        for sp, x in zip(sps, xs):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, info = sp.solve(out=x)
+            e1.record(stream)
+            infos.append((info, e0, e1))
+        return infos
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = lib.sgoc_kernel_launches()
+    step_ms, solve_ms, iters, outer, resid = [], [], [], [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)                       # L2 flush (256 MiB write), outside the events
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        infos = step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(s0.elapsed_time(s1))
+        for info, e0, e1 in infos:
+            solve_ms.append(e0.elapsed_time(e1))
+            iters.append(info["iterations"])
+            outer.append(info["outer_iterations"])
+            resid.append(info["rel_true_residual"])
+    torch.cuda.synchronize()
+    launches = lib.sgoc_kernel_launches() - l0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    solves = 3 * args.steps * world
+    value = solves / (total_ms / 1e3)
+    assert max(resid) <= 1e-8, resid
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32/f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "solves_per_step": 3, "n": sps[0].n, "P": sps[0].P,
+                   "kkt_unknowns": sps[0].kkt_size,
+                   "precision": ("float32 operator/preconditioner/inner MINRES, float64 refinement"
+                                 if args.precision == "mixed" else "float64"),
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": float(sorted(solve_ms)[len(solve_ms) // 2]),
+                       "p99": float(sorted(solve_ms)[min(len(solve_ms) - 1, math.ceil(0.99 * len(solve_ms)) - 1)])},
+        "iterations": {"per_solve": iters[:3], "outer": outer[:3], "max_rel_residual": max(resid)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+
+    if not args.no_extras and rank == 0:
+        # plain float64 path (same solves), for the mixed-vs-fp64 comparison
+        if args.precision == "mixed":
+            sp64 = [SGProblem.from_problem(pr, precision="fp64").upload() for pr in problems]
+            t64, it64 = [], []
+            for sp, x in zip(sp64, xs):
+                sp.solve(out=x)                    # warm
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _, info = sp.solve(out=x)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t64.append(e0.elapsed_time(e1))
+                it64.append(info["iterations"])
+                sp.release_workspace()
+            line["fp64_path"] = {"solves_per_s": 3 / (sum(t64) / 1e3), "ms_per_solve": t64, "iterations": it64}
+            del sp64
+
+        # end to end through the public API: host arrays in, host solution out
+        pin = [torch.empty(sp.kkt_size, dtype=torch.float64, pin_memory=True) for sp in sps]
+        h2d = d2h = 0
+        e2e_ms = []
+        for rep in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for pr, hx in zip(problems, pin):
+                sp = SGProblem.from_problem(pr, precision=args.precision).upload()
+                x, _ = sp.solve()
+                hx.copy_(x, non_blocking=True)
+                if rep == 0:
+                    h2d += sp.persistent_bytes
+                    d2h += sp.kkt_size * 8
+            torch.cuda.synchronize()
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        line["e2e"] = {"value": 3 / (min(e2e_ms) / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h,
+                       "includes": "problem set-up from host arrays, upload, workspace, solve, D2H of x"}
+
+        # instrumented pass: per-kernel-class device time with CUDA events on the launching stream
+        abi.profile_enable(True)
+        flush.fill_(1.0)
+        step()
+        torch.cuda.synchronize()
+        rep = abi.profile_report()
+        abi.profile_enable(False)
+        tot = sum(v["ms"] for v in rep.values())
+        kinds = {k: dict(v, share=v["ms"] / tot) for k, v in rep.items()}
+        dom = max(kinds, key=lambda k: kinds[k]["ms"])
+        dv = kinds[dom]
+        esize_fp64 = args.precision == "fp64"
+        if esize_fp64 and dom in ("sg_operator", "mg_vcycle_fused", "mg_smooth"):
+            ach = dv["flops"] / (dv["ms"] / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "kernel": dom,
+                    "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 x 2070 MHz"}
+        else:
+            ach = dv["bytes"] / (dv["ms"] / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                    "traffic": None, "kernel": dom, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+        roof["launches"] = dv["launches"]
+        roof["avg_launch_us"] = 1e3 * dv["ms"] / dv["launches"]
+        line["roofline"] = roof
+        line["kernel_breakdown"] = {k: {"share": round(v["share"], 4), "launches": v["launches"],
+                                        "ms": round(v["ms"], 3),
+                                        "GB/s": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
+                                    for k, v in sorted(kinds.items(), key=lambda kv: -kv[1]["ms"])}
+
+        # SG matvec bandwidth: 128x128 workload (L2-resident operands) and a 512x512, M=8, p=3
+        # operand set (P=165) larger than L2; float32 and float64; L2 flushed between launches
+        mv = {}
+        for tag, pr in (("128x128_P84", problems[1]), ("512x512_P165", si.steady_512())):
+            sp = SGProblem.from_problem(pr).upload()
+            for dt, name in ((torch.float32, "f32"), (torch.float64, "f64")):
+                X = torch.randn(sp.n * sp.P, dtype=dt, device="cuda")
+                Y = torch.empty_like(X)
+                sp.apply_operator(X, out=Y)
+                ts = []
+                for _ in range(5):
+                    flush.fill_(1.0)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    sp.apply_operator(X, out=Y)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                w = X.element_size()
+                byts = w * (2 * sp.n * sp.P) + w * (pr.M + 1) * pr.nx * pr.nx
+                t = statistics.median(ts) / 1e3
+                mv[f"{tag}_{name}"] = {"GB/s": byts / t / 1e9, "frac_hbm": byts / t / 1e9 / hbm_peak,
+                                       "us": t * 1e6}
+            del sp
+        line["sg_matvec"] = mv
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = cpu_baseline_value(iters_sample=3, betas=(1e-4,))
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * sgoc.h - C ABI of the GB300 stochastic Galerkin optimal-control solver.
+ *
+ * The library solves the stochastic Galerkin (SG) KKT saddle-point system of
+ * distributed optimal control of  -div(k(x,xi) grad y) = u  (steady) or
+ * y_t - div(k grad y) = u  (all-at-once backward Euler) on the unit square,
+ * with homogeneous Dirichlet data, Q1 elements on a uniform nx x nx grid, an
+ * affine coefficient k(x,xi) = kappa_0(x) + sum_{k=1..M} kappa_k(x) xi_k with
+ * xi_k ~ U[-1,1] independent, and an orthonormal Legendre chaos of total degree p.
+ * Reference: Li, Onwunta, Sousedik, "Stochastic Galerkin Method and Hierarchical
+ * Preconditioning for PDE-constrained Optimization" (Sec. 2, Eq. (stoch-system);
+ * Sec. 3, Eq. (KKT:stoch-time-dependent)).  The Krylov method is preconditioned
+ * MINRES with the block-diagonal preconditioner of Eq. (stoch-prec) / Eq.
+ * (precon for time), whose Schur block uses the hierarchical Gauss-Seidel sweep
+ * of Alg. 1 with geometric-multigrid mean solves.
+ *
+ * Conventions (all entry points):
+ * - Every call returns sgoc_status; no exception or abort crosses the ABI.
+ *   sgoc_last_error() gives a human-readable message for the last failure of
+ *   the calling thread.
+ * - Memory: the library never allocates device memory.  The caller owns every
+ *   device buffer (persistent problem data, workspace, vectors) and every
+ *   stream; `stream` arguments are cudaStream_t values passed as void*.
+ *   Host arrays passed to sgoc_problem_create are copied; the caller may free
+ *   them afterwards.
+ * - Layout of an SG vector: the paper's vec order (Sec. 2, Eq. (m)): interior
+ *   node index fastest (nodes numbered lexicographically, x1 fastest,
+ *   n = (nx-1)^2), then the chaos index alpha (graded order, see
+ *   sgoc_pc_indices), then the time level.  A KKT vector is [y; u; lambda],
+ *   each block of length slabs*P*n with slabs = max(nt, 1).  KKT vectors at the
+ *   ABI are float64 in both precisions.
+ * - Asynchrony: device work is enqueued on `stream`; calls that return results
+ *   to the host (sgoc_solve) synchronize the stream before returning.
+ * - Thread safety: one sgoc_problem may be used by one host thread at a time.
+ */
+#ifndef SGOC_H
+#define SGOC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SGOC_OK = 0,
+  SGOC_ERR_INVALID_ARG = 1,           /* bad size, pointer or parameter */
+  SGOC_ERR_UNSUPPORTED = 2,           /* valid problem outside the structured-grid scope */
+  SGOC_ERR_WORKSPACE_TOO_SMALL = 3,   /* caller buffer smaller than the queried size */
+  SGOC_ERR_CUDA = 4,                  /* a CUDA runtime call failed (see sgoc_last_error) */
+  SGOC_ERR_NO_CONVERGENCE = 5,        /* max_iter / max_outer reached */
+  SGOC_ERR_BREAKDOWN = 6,             /* Lanczos breakdown before convergence */
+  SGOC_ERR_NOT_SPD = 7,               /* <v, P^{-1} v> <= 0: preconditioner not positive */
+  SGOC_ERR_NAN = 8,                   /* NaN or Inf in the recurrences or the inputs */
+  SGOC_ERR_NOT_UPLOADED = 9           /* device data missing: call sgoc_problem_upload */
+} sgoc_status;
+
+typedef enum {
+  SGOC_FP64 = 0,        /* operator, preconditioner and Krylov vectors in float64 */
+  SGOC_MIXED_FP32 = 1   /* float32 operator/preconditioner/inner MINRES vectors with
+                           float64 inner products and scalars, inside float64
+                           iterative refinement on the true residual */
+} sgoc_precision;
+
+/* Problem statement (Sec. 2 and Sec. 3).  All pointers are host pointers. */
+typedef struct {
+  int32_t nx;            /* elements per side of the unit square: a power of two, 2..4096 */
+  int32_t M;             /* number of random variables / KL terms, 0..16 */
+  int32_t p;             /* total degree of the chaos, 0..10; P = C(M+p, p) columns */
+  const double* kappa;   /* (M+1)*nx*nx element values kappa_k(e), index (k*nx + ey)*nx + ex
+                            (ex along x1); kappa_0 is the mean field and must be a positive
+                            constant (the mean-operator multigrid relies on it) */
+  double beta;           /* control cost beta > 0 */
+  double gamma;          /* variance penalty gamma >= 0 (Eq. (problem-stoch)) */
+  int32_t nt;            /* 0: steady problem; >= 1: number of backward-Euler steps */
+  double T;              /* final time (nt >= 1), tau = T / nt */
+  const double* yhat;    /* max(nt,1)*n target values at interior nodes; in time mode
+                            slab t holds yhat(., t_{t+1}), t_k = k tau */
+  const double* y0;      /* n initial-state values (time mode) or NULL for y(0) = 0 */
+} sgoc_problem_desc;
+
+/* Solver options; sgoc_default_options fills the defaults given here. */
+typedef struct {
+  double tol;            /* relative residual target ||b - K x||_2 / ||b||_2 (1e-8) */
+  int32_t max_iter;      /* MINRES iteration cap (FP64) / inner cap (mixed) (1000) */
+  int32_t r;             /* truncation: hGS couplings use kappa_1..kappa_{r-1}; 1..M+1;
+                            0 selects M+1 (Sec. 2, index set I_tau; Sec. 5, r = m+1) */
+  int32_t cheb_steps;    /* Chebyshev steps for the mass blocks (5) */
+  int32_t nu_pre;        /* V-cycle pre-smoothing sweeps (2) */
+  int32_t nu_post;       /* V-cycle post-smoothing sweeps (2) */
+  double omega;          /* damped-Jacobi weight (0.8) */
+  int32_t precision;     /* sgoc_precision (SGOC_FP64) */
+  double inner_tol;      /* mixed: inner MINRES relative tolerance (1e-4) */
+  int32_t max_outer;     /* mixed: refinement steps cap (20) */
+} sgoc_options;
+
+typedef struct {
+  sgoc_status status;
+  int32_t iterations;          /* MINRES iterations (total inner iterations in mixed mode) */
+  int32_t outer_iterations;    /* refinement steps (mixed), 1 for FP64 */
+  double rel_true_residual;    /* ||b - K x||_2 / ||b||_2 in float64 at exit */
+  double rel_estimate;         /* last MINRES estimate |eta| / ||b||_{P^-1} */
+  double ms_total;             /* wall time of the call, milliseconds */
+} sgoc_result;
+
+typedef struct sgoc_problem sgoc_problem;
+
+/* Fill `opt` with the defaults documented in sgoc_options. */
+void sgoc_default_options(sgoc_options* opt);
+
+/* Host set-up of a problem (Sec. 2-3 problem statement): validates `desc`, builds
+ * the multi-index set, the triple-product tables and the multigrid hierarchy,
+ * and copies the host inputs.  opt may be NULL (defaults).  Errors:
+ * INVALID_ARG for bad sizes/pointers, UNSUPPORTED for a non-constant kappa_0 or
+ * a grid that is not a power of two. */
+sgoc_status sgoc_problem_create(const sgoc_problem_desc* desc, const sgoc_options* opt,
+                                sgoc_problem** out);
+void sgoc_problem_destroy(sgoc_problem* pb);
+
+/* n = (nx-1)^2 interior nodes, P chaos columns, slabs = max(nt,1),
+ * kkt = 3*slabs*P*n entries of a KKT vector.  Any pointer may be NULL. */
+sgoc_status sgoc_problem_sizes(const sgoc_problem* pb, int64_t* n, int64_t* P,
+                               int64_t* slabs, int64_t* kkt);
+
+/* Device bytes the caller must provide: `persistent` for sgoc_problem_upload and
+ * `workspace` for sgoc_solve / sgoc_apply_precond at the problem's precision. */
+sgoc_status sgoc_problem_device_bytes(const sgoc_problem* pb, size_t* persistent,
+                                      size_t* workspace);
+
+/* Copy the coefficient and table data into the caller's device buffer
+ * d_persistent (>= persistent bytes, 256-byte aligned).  The buffer must stay
+ * alive and unmodified while the problem is used. */
+sgoc_status sgoc_problem_upload(sgoc_problem* pb, void* d_persistent, size_t bytes,
+                                void* stream);
+
+/* Right-hand side b of Eq. (stoch-system) / Eq. (KKT:stoch-time-dependent):
+ * [M_cal yhat e_1; 0; 0] steady, [tau (D (x) M_cal) yhat; 0; -d] in time mode
+ * with d = [M y0 e_1, 0, ...].  d_b: kkt float64 entries. */
+sgoc_status sgoc_rhs(sgoc_problem* pb, double* d_b, void* stream);
+
+/* Solve K x = b by preconditioned MINRES (FP64) or FP32 MINRES inside FP64
+ * iterative refinement (mixed).  d_x0 (nullable) is an initial guess; d_x
+ * (kkt float64) receives the solution.  d_ws: workspace of >= the queried
+ * size, 256-byte aligned.  Synchronizes `stream`; fills *res (nullable). */
+sgoc_status sgoc_solve(sgoc_problem* pb, void* d_ws, size_t ws_bytes, const double* d_x0,
+                       double* d_x, void* stream, sgoc_result* res);
+
+/* ---- building blocks (used by tests and benchmarks) ---- */
+
+/* Y = sum_{k=0}^{M} K_k X G_k (Sec. 2, Eq. (Zv) with A_l in place of A~_l),
+ * applied to `nslabs` consecutive n x P panels.  precision 0: X, Y float64;
+ * 1: float32.  X and Y must not overlap. */
+sgoc_status sgoc_apply_operator(sgoc_problem* pb, int32_t precision, const void* d_X,
+                                void* d_Y, int32_t nslabs, void* stream);
+
+/* w = K v, the KKT matrix of Eq. (stoch-system) or Eq. (KKT:stoch-time-dependent).
+ * precision 0: float64 vectors; 1: float32 vectors.  No workspace. */
+sgoc_status sgoc_apply_kkt(sgoc_problem* pb, int32_t precision, const void* d_v, void* d_w,
+                           void* stream);
+
+/* z = P^{-1} r, the block preconditioner (Eq. (stoch-prec) / Eq. (precon for time))
+ * in the given precision (vectors of that type). */
+sgoc_status sgoc_apply_precond(sgoc_problem* pb, int32_t precision, const void* d_r,
+                               void* d_z, void* d_ws, size_t ws_bytes, void* stream);
+
+/* V = Z_hGS^{-1} R: one hierarchical Gauss-Seidel sweep (Alg. 1) over the
+ * slabs of R (nslabs panels n x P), with the mean operator of the problem's mode. */
+sgoc_status sgoc_apply_hgs(sgoc_problem* pb, int32_t precision, const void* d_R, void* d_V,
+                           int32_t nslabs, void* d_ws, size_t ws_bytes, void* stream);
+
+/* X = B(R) for ncols columns of length n: one V-cycle for the mean operator
+ * (A~_1 of Eq. (mathcalZ) steady, A^_1 of Eq. (A_hat) in time mode). */
+sgoc_status sgoc_apply_vcycle(sgoc_problem* pb, int32_t precision, const void* d_R, void* d_X,
+                              int32_t ncols, void* d_ws, size_t ws_bytes, void* stream);
+
+/* X = Chebyshev semi-iteration (cheb_steps steps) for M X = R on ncols <= 2*slabs*P
+ * columns of length n (Sec. 2: the mass blocks of Eq. (stoch-prec); textbook
+ * Golub-Varga weights with D = (5/4) diag(M), eigenvalue bounds [1/4, 9/4]).
+ * Uses the preconditioner workspace (sgoc_problem_device_bytes sizes cover it). */
+sgoc_status sgoc_apply_chebyshev(sgoc_problem* pb, int32_t precision, const void* d_R,
+                                 void* d_X, int32_t ncols, void* d_ws, size_t ws_bytes,
+                                 void* stream);
+
+/* The multi-index set, P x M int32 (host), graded by total degree and
+ * lexicographically descending within a degree. */
+sgoc_status sgoc_pc_indices(const sgoc_problem* pb, int32_t* host_out);
+
+/* Non-zeros of G_k = E[xi_k Psi_a Psi_b], k = 1..M (G_0 = I is implicit):
+ * host arrays of capacity *nnz on input; *nnz returns the count.  Pass NULL
+ * arrays to query the count. */
+sgoc_status sgoc_triple_products(const sgoc_problem* pb, int32_t* k, int32_t* a, int32_t* b,
+                                 double* c, int64_t* nnz);
+
+/* Diagnostic: number of kernels this library has launched in the process so far
+ * (all problems and streams).  No counterpart in the paper. */
+int64_t sgoc_kernel_launches(void);
+
+/* Diagnostic kernel timing.  sgoc_profile_enable(1) clears the record and makes
+ * every later launch record CUDA events around itself on its stream together
+ * with its algorithmic bytes and flops; sgoc_profile_enable(0) stops recording.
+ * sgoc_profile_query(kind, ...) waits for the recorded events of one kernel
+ * class (kind in [0, SGOC_KERNEL_KINDS)) and returns the launch count, summed
+ * device milliseconds, bytes and flops.  No counterpart in the paper. */
+#define SGOC_KERNEL_KINDS 11
+sgoc_status sgoc_profile_enable(int32_t on);
+sgoc_status sgoc_profile_query(int32_t kind, int64_t* launches, double* ms, double* bytes,
+                               double* flops);
+const char* sgoc_kernel_kind_name(int32_t kind);
+
+const char* sgoc_status_string(sgoc_status s);
+const char* sgoc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGOC_H */

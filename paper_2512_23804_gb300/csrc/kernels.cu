@@ -1,0 +1,971 @@
+// Device kernels of the SG optimal-control solver (sm_103a).
+//
+// Grid conventions: interior nodes (ix, iy), 0 <= ix, iy < n1 = nx - 1, node index
+// iy*n1 + ix; element (ex, ey), 0 <= ex, ey < nx.  Interior node (ix, iy) is the
+// north-east corner of element (ix, iy), the north-west corner of (ix+1, iy), the
+// south-west corner of (ix+1, iy+1) and the south-east corner of (ix, iy+1).
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "kernels.h"
+
+namespace sgoc {
+
+static std::atomic<int64_t> g_launches{0};
+static inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t kernel_launches() { return g_launches.load(std::memory_order_relaxed); }
+
+// ---- optional per-kernel-class profiler (events pooled and reused) ----
+namespace {
+struct ProfRec { int kind; cudaEvent_t a, b; double bytes, flops; };
+struct Profiler {
+  std::mutex mu;
+  bool on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  cudaEvent_t get() {
+    if (used < pool.size()) return pool[used++];
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    pool.push_back(e);
+    ++used;
+    return e;
+  }
+};
+Profiler& prof() { static Profiler p; return p; }
+const char* kKindNames[KK_COUNT] = {"sg_operator", "mass", "chebyshev", "mg_smooth", "mg_residual",
+                                    "mg_restrict", "mg_prolong", "mg_vcycle_fused", "dot", "minres_scalar",
+                                    "vector_update"};
+}  // namespace
+
+const char* kernel_kind_name(int kind) { return (kind >= 0 && kind < KK_COUNT) ? kKindNames[kind] : "?"; }
+
+void profile_enable(bool on) {
+  Profiler& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  p.on = on;
+  p.recs.clear();
+  p.used = 0;
+}
+
+ProfScope::ProfScope(int k, cudaStream_t s, double bytes, double flops) : kind(k), st(s), slot(-1) {
+  Profiler& p = prof();
+  if (!p.on) return;
+  std::lock_guard<std::mutex> g(p.mu);
+  ProfRec r{k, p.get(), p.get(), bytes, flops};
+  if (!r.a || !r.b) return;
+  cudaEventRecord(r.a, s);
+  slot = int(p.recs.size());
+  p.recs.push_back(r);
+}
+
+ProfScope::~ProfScope() {
+  if (slot < 0) return;
+  Profiler& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  cudaEventRecord(p.recs[slot].b, st);
+}
+
+bool profile_query(int kind, int64_t* launches, double* ms, double* bytes, double* flops) {
+  Profiler& p = prof();
+  std::lock_guard<std::mutex> g(p.mu);
+  int64_t nl = 0;
+  double t = 0, by = 0, fl = 0;
+  for (auto& r : p.recs) {
+    if (r.kind != kind) continue;
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return false;
+    float e = 0;
+    if (cudaEventElapsedTime(&e, r.a, r.b) != cudaSuccess) return false;
+    ++nl; t += e; by += r.bytes; fl += r.flops;
+  }
+  *launches = nl; *ms = t; *bytes = by; *flops = fl;
+  return true;
+}
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4; };
+
+template <typename T>
+__device__ __forceinline__ T ldz(const T* __restrict__ X, int ix, int iy, int n1) {
+  return (ix >= 0 && ix < n1 && iy >= 0 && iy < n1) ? X[iy * n1 + ix] : T(0);
+}
+
+// Sum over the 4 elements of a node of kappa_k(e)/6 * T_e, where
+// T_e = 4 X_C - X_a - X_b - 2 X_c (a, b the edge neighbours and c the opposite
+// corner of the node inside element e).  Element order: SW, SE, NE, NW.
+template <typename T>
+__device__ __forceinline__ T dot4(const typename Vec4<T>::type& a, const typename Vec4<T>::type& b) {
+  T r = a.x * b.x;
+  r = fma(a.y, b.y, r);
+  r = fma(a.z, b.z, r);
+  r = fma(a.w, b.w, r);
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// SG operator tile kernel (Sec. 2, Eq. (Zv)): one CTA = TX consecutive nodes
+// of one grid row and one slab, all requested chaos columns.
+//   phase 0: kappa_k(e)/6 of the 4 elements of each node -> shared
+//   phase 1: for every input column alpha, the 4 element terms T_e(alpha) -> shared
+//            (and the mass stencil value of the output columns)
+//   phase 2: out(beta) = sum_e kappa_0(e) T_e(beta) + sum_{(alpha,k,c)} c sum_e kappa_k(e) T_e(alpha)
+// ---------------------------------------------------------------------------
+constexpr int kSGThreads = 256;
+constexpr int kSGChunk = 8;
+
+template <typename T, int TX>
+__global__ void __launch_bounds__(kSGThreads) sg_kernel(SGArgs<T> a) {
+  using V4 = typename Vec4<T>::type;
+  extern __shared__ __align__(32) unsigned char sg_smem_raw[];
+  unsigned char* smem_raw = sg_smem_raw;
+  const int nin = a.in1 - a.in0;
+  const int nout = a.out1 - a.out0;
+  V4* Ts = reinterpret_cast<V4*>(smem_raw);                   // [nin][TX]
+  V4* Ks = Ts + size_t(nin) * TX;                            // [M+1][TX]
+  T* Ms = reinterpret_cast<T*>(Ks + size_t(a.M + 1) * TX);   // [nout][TX]
+  T* Xs = Ms + size_t(nout) * TX;                            // [kSGChunk][3][TX+2]
+
+  const int ix0 = blockIdx.x * TX;
+  const int iy = blockIdx.y;
+  const int t = blockIdx.z;
+  const int tid = threadIdx.x;
+  const int n1 = a.n1;
+  const T* X = a.X + int64_t(t) * a.xs;
+
+  // phase 0: element coefficients
+  for (int q = tid; q < (a.M + 1) * TX; q += kSGThreads) {
+    const int k = q / TX, lx = q % TX;
+    const int ix = min(ix0 + lx, n1 - 1);
+    const T* kk = a.kap + int64_t(k) * a.nx * a.nx;
+    V4 v;
+    v.x = kk[int64_t(iy) * a.nx + ix];            // SW element (ix, iy)
+    v.y = kk[int64_t(iy) * a.nx + ix + 1];        // SE element (ix+1, iy)
+    v.z = kk[int64_t(iy + 1) * a.nx + ix + 1];    // NE element (ix+1, iy+1)
+    v.w = kk[int64_t(iy + 1) * a.nx + ix];        // NW element (ix, iy+1)
+    Ks[k * TX + lx] = v;
+  }
+
+  // phase 1: element terms of all input columns
+  constexpr int W = TX + 2;
+  for (int c0 = a.in0; c0 < a.in1; c0 += kSGChunk) {
+    const int nc = min(kSGChunk, a.in1 - c0);
+    for (int q = tid; q < nc * 3 * W; q += kSGThreads) {
+      const int c = q / (3 * W), rem = q % (3 * W), dy = rem / W, lx = rem % W;
+      const int gx = ix0 + lx - 1, gy = iy + dy - 1;
+      Xs[q] = ldz(X + int64_t(c0 + c) * a.n, gx, gy, n1);
+    }
+    __syncthreads();
+    for (int q = tid; q < nc * TX; q += kSGThreads) {
+      const int c = q / TX, lx = q % TX;
+      const T* s = Xs + c * 3 * W + lx;   // s[dy*W + dx], dx,dy in 0..2 (1 = centre)
+      const T SW = s[0], S = s[1], SE = s[2];
+      const T Wv = s[W], C = s[W + 1], E = s[W + 2];
+      const T NW = s[2 * W], N = s[2 * W + 1], NE = s[2 * W + 2];
+      const T c4 = T(4) * C;
+      const T aS = c4 - S, aN = c4 - N;
+      V4 v;
+      v.x = fma(T(-2), SW, aS - Wv);
+      v.y = fma(T(-2), SE, aS - E);
+      v.z = fma(T(-2), NE, aN - E);
+      v.w = fma(T(-2), NW, aN - Wv);
+      const int col = c0 + c;
+      Ts[size_t(col - a.in0) * TX + lx] = v;
+      if (col >= a.out0 && col < a.out1) {
+        const T edges = (N + S) + (E + Wv);
+        const T corners = (NE + NW) + (SE + SW);
+        Ms[size_t(col - a.out0) * TX + lx] = a.mass * fma(T(16), C, fma(T(4), edges, corners));
+      }
+    }
+    __syncthreads();
+  }
+
+  // phase 2: contraction with the triple products
+  for (int q = tid; q < nout * TX; q += kSGThreads) {
+    const int lx = q % TX, beta = a.out0 + q / TX;
+    const int ix = ix0 + lx;
+    if (ix >= n1) continue;
+    const V4 tb = Ts[size_t(beta - a.in0) * TX + lx];
+    const T diag = dot4<T>(Ks[lx], tb);
+    T off = T(0);
+    const int e1 = a.nbr_ptr[beta + 1];
+    for (int e = a.nbr_ptr[beta]; e < e1; ++e) {
+      const int k = a.nbr_k[e];
+      if (k >= a.kmax) break;                        // table is sorted by k
+      const int al = a.nbr_alpha[e];
+      off = fma(a.nbr_c[e], dot4<T>(Ks[k * TX + lx], Ts[size_t(al - a.in0) * TX + lx]), off);
+    }
+    T out = a.c0 * diag + a.c1 * off;
+    if (a.cm != T(0)) out = fma(a.cm, Ms[size_t(beta - a.out0) * TX + lx], out);
+    const int64_t node = int64_t(iy) * n1 + ix;
+    if (a.R) out = fma(a.cr, a.R[int64_t(t) * a.rs + int64_t(beta - a.rcol0) * a.n + node], out);
+    T* yp = a.Y + int64_t(t) * a.ys + int64_t(beta - a.ycol0) * a.n + node;
+    if (a.cy != T(0)) out = fma(a.cy, *yp, out);
+    *yp = out;
+  }
+}
+
+template <typename T, int TX>
+static size_t sg_smem(const SGArgs<T>& a) {
+  using V4 = typename Vec4<T>::type;
+  return sizeof(V4) * (size_t(a.in1 - a.in0) * TX + size_t(a.M + 1) * TX) +
+         sizeof(T) * (size_t(a.out1 - a.out0) * TX + size_t(kSGChunk) * 3 * (TX + 2));
+}
+
+template <typename T, int TX>
+static cudaError_t launch_sg_tx(const SGArgs<T>& a, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(sg_kernel<T, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.n1 + TX - 1) / TX, a.n1, a.nslabs);
+  const double w = sizeof(T), cells = double(a.n) * a.nslabs;
+  const int nout = a.out1 - a.out0, nin = a.in1 - a.in0;
+  const double bytes = w * cells * (nin + nout * (1.0 + (a.R ? 1 : 0) + (a.cy != T(0) ? 1 : 0))) +
+                       w * (a.M + 1.0) * a.nx * a.nx;
+  const double flops = cells * (15.0 * nin + 9.0 * nout + 9.0 * (a.c1 != T(0) ? a.deg_sum : 0));
+  ProfScope ps(KK_SG, st, bytes, flops);
+  sg_kernel<T, TX><<<grid, kSGThreads, smem, st>>>(a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+constexpr size_t kMaxSmem = 227 * 1024;
+
+template <typename T>
+cudaError_t launch_sg(const SGArgs<T>& a, cudaStream_t st) {
+  if (a.out1 <= a.out0 || a.nslabs <= 0) return cudaSuccess;
+  if (a.out0 < a.in0 || a.out1 > a.in1) return cudaErrorInvalidValue;
+  size_t s32 = sg_smem<T, 32>(a), s16 = sg_smem<T, 16>(a), s8 = sg_smem<T, 8>(a);
+  if (s32 <= kMaxSmem && a.n1 >= 24) return launch_sg_tx<T, 32>(a, s32, st);
+  if (s16 <= kMaxSmem && a.n1 >= 12) return launch_sg_tx<T, 16>(a, s16, st);
+  if (s8 <= kMaxSmem) return launch_sg_tx<T, 8>(a, s8, st);
+  return cudaErrorInvalidConfiguration;
+}
+
+// ---------------------------------------------------------------------------
+// Mass-matrix combinations (Eq. (def-Mcal): M_cal = I (x) M, M_gamma = H^gamma (x) M)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T mass_apply(const T* __restrict__ V, int ix, int iy, int n1, T mass) {
+  const T C = V[iy * n1 + ix];
+  const T N = ldz(V, ix, iy + 1, n1), S = ldz(V, ix, iy - 1, n1);
+  const T E = ldz(V, ix + 1, iy, n1), Wv = ldz(V, ix - 1, iy, n1);
+  const T NE = ldz(V, ix + 1, iy + 1, n1), NW = ldz(V, ix - 1, iy + 1, n1);
+  const T SE = ldz(V, ix + 1, iy - 1, n1), SW = ldz(V, ix - 1, iy - 1, n1);
+  const T edges = (N + S) + (E + Wv);
+  const T corners = (NE + NW) + (SE + SW);
+  return mass * fma(T(16), C, fma(T(4), edges, corners));
+}
+
+template <typename T>
+__global__ void mass_kernel(MassArgs<T> a) {
+  const int64_t total = int64_t(a.nslabs) * a.ncols * a.n;
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total; q += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t node = q % a.n;
+    const int64_t cq = q / a.n;
+    const int c = int(cq % a.ncols);
+    const int t = int(cq / a.ncols);
+    const int ix = int(node % a.n1), iy = int(node / a.n1);
+    const int col = a.col0 + c;
+    const T hg = col == 0 ? T(1) : T(1) + a.gamma;
+    const T dt = (a.nt > 1 && (t == 0 || t == a.nt - 1)) ? T(0.5) : T(1);
+    T* op = a.out + int64_t(t) * a.os + int64_t(c) * a.n + node;
+    T acc = a.cy != T(0) ? a.cy * *op : T(0);
+    for (int j = 0; j < a.nv; ++j) {
+      const int ts = t + a.shift[j];
+      if (ts < 0 || ts >= a.nslabs) continue;
+      T w = a.a[j];
+      if (a.wflags[j] & 1) w *= hg;
+      if (a.wflags[j] & 2) w *= dt;
+      const T* V = a.V[j] + int64_t(ts) * a.vs[j] + int64_t(c) * a.n;
+      acc = fma(w, mass_apply(V, ix, iy, a.n1, a.mass), acc);
+    }
+    if (a.R) acc = fma(a.ar, a.R[int64_t(t) * a.rs + int64_t(c) * a.n + node], acc);
+    *op = acc;
+  }
+}
+
+static int grid_for(int64_t total, int threads) {
+  int64_t b = (total + threads - 1) / threads;
+  const int64_t cap = 152 * 32;
+  return int(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+template <typename T>
+cudaError_t launch_mass(const MassArgs<T>& a, cudaStream_t st) {
+  const int64_t total = int64_t(a.nslabs) * a.ncols * a.n;
+  if (total == 0) return cudaSuccess;
+  const double w = sizeof(T);
+  ProfScope ps(KK_MASS, st, w * total * (a.nv + 1 + (a.cy != T(0) ? 1 : 0) + (a.R ? 1 : 0)),
+               double(total) * (20.0 * a.nv + 2.0));
+  mass_kernel<T><<<grid_for(total, 256), 256, 0, st>>>(a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Chebyshev semi-iteration for the mass blocks (Sec. 2, Sec. 5: Chebyshev-5)
+// x_{k+1} = omega_{k+1} (D^{-1}(b - M x_k) + x_k - x_{k-1}) + x_{k-1},
+// omega_1 = 1, omega_2 = 2/(2 - rho^2), omega_{k+1} = 1/(1 - rho^2 omega_k / 4).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void cheb_kernel(const T* __restrict__ B, const T* __restrict__ xk, T* xkm1, T* out, int64_t ncols,
+                            int n1, int64_t n, T mass, T dinv, T omega, int mode, int scale_mode, int P,
+                            int slabs, int nt, T tau, T beta, T gamma) {
+  const int64_t total = ncols * n;
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total; q += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t col = q / n, node = q % n;
+    const T b = B[q];
+    T x;
+    if (mode == 0) {
+      x = dinv * b;                                 // x_1 = D^{-1} b (x_0 = 0)
+    } else {
+      const int ix = int(node % n1), iy = int(node / n1);
+      const T* Xc = xk + col * n;
+      const T r = b - mass_apply(Xc, ix, iy, n1, mass);
+      const T xprev = mode == 1 ? T(0) : xkm1[q];
+      x = fma(omega, fma(dinv, r, Xc[node] - xprev), xprev);
+    }
+    if (out) {
+      T sc = T(1);
+      if (scale_mode == 1) {
+        const int64_t blk = col / (int64_t(slabs) * P);
+        const int64_t cc = col % (int64_t(slabs) * P);
+        const int t = int(cc / P), al = int(cc % P);
+        T s = nt > 0 ? tau * ((nt > 1 && (t == 0 || t == nt - 1)) ? T(0.5) : T(1)) : T(1);
+        s *= blk == 0 ? (al == 0 ? T(1) : T(1) + gamma) : beta;
+        sc = T(1) / s;
+      }
+      out[q] = sc * x;
+    } else {
+      xkm1[q] = x;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_cheb(const ChebArgs<T>& a, cudaStream_t st) {
+  const int64_t total = a.ncols * a.n;
+  if (total == 0) return cudaSuccess;
+  const double lmin = 0.25, lmax = 2.25;
+  const double gam = 0.5 * (lmin + lmax), rho = (lmax - lmin) / (lmax + lmin);
+  const T dinv = T(1.0 / (gam * 16.0 * double(a.mass)));
+  const int g = grid_for(total, 256);
+  double omega = 1.0;
+  // x_{k+1} is written over x_{k-1}: x_1 -> A, x_2 -> B, x_3 -> A, ...
+  for (int k = 0; k < a.steps; ++k) {
+    if (k == 1) omega = 2.0 / (2.0 - rho * rho);
+    else if (k >= 2) omega = 1.0 / (1.0 - rho * rho * omega / 4.0);
+    T* dst = (k % 2 == 0) ? a.tmpA : a.tmpB;      // buffer receiving x_{k+1}
+    const T* xk = (k % 2 == 0) ? a.tmpB : a.tmpA; // x_k
+    T* out = (k == a.steps - 1) ? a.X : nullptr;
+    const int mode = k == 0 ? 0 : (k == 1 ? 1 : 2);
+    ProfScope ps(KK_CHEB, st, double(sizeof(T)) * total * (2 + mode), double(total) * (mode == 0 ? 1.0 : 24.0));
+    cheb_kernel<T><<<g, 256, 0, st>>>(a.B, xk, dst, out, a.ncols, a.n1, a.n, a.mass, dinv, T(omega), mode,
+                                       a.scale_mode, a.P, a.slabs, a.nt, a.tau, a.beta, a.gamma);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Geometric multigrid for the mean operator: constant 9-point stencils.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T stencil_apply(const T* __restrict__ X, int ix, int iy, int n1, T d, T e, T c) {
+  const T C = X[iy * n1 + ix];
+  const T edges = (ldz(X, ix, iy + 1, n1) + ldz(X, ix, iy - 1, n1)) + (ldz(X, ix + 1, iy, n1) + ldz(X, ix - 1, iy, n1));
+  const T corners = (ldz(X, ix + 1, iy + 1, n1) + ldz(X, ix - 1, iy + 1, n1)) +
+                    (ldz(X, ix + 1, iy - 1, n1) + ldz(X, ix - 1, iy - 1, n1));
+  return fma(d, C, fma(e, edges, c * corners));
+}
+
+template <typename T>
+__global__ void smooth_kernel(const T* __restrict__ b, const T* __restrict__ xin, T* xout, int64_t B, int n1, T d,
+                              T e, T c, T omega, T* acc, int64_t acc_ss, int acc_L, int acc_col0) {
+  const int64_t n = int64_t(n1) * n1;
+  const int64_t total = B * n;
+  const T wd = omega / d;
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total; q += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t col = q / n, node = q % n;
+    T x;
+    if (xin) {
+      const int ix = int(node % n1), iy = int(node / n1);
+      const T* X = xin + col * n;
+      x = fma(wd, b[q] - stencil_apply(X, ix, iy, n1, d, e, c), X[node]);
+    } else {
+      x = wd * b[q];
+    }
+    if (acc) {
+      const int64_t t = col / acc_L, cc = col % acc_L;
+      acc[t * acc_ss + (acc_col0 + cc) * n + node] += x;
+    } else {
+      xout[q] = x;
+    }
+  }
+}
+
+template <typename T>
+__global__ void residual_kernel(const T* __restrict__ b, const T* __restrict__ x, T* r, int64_t B, int n1, T d, T e, T c) {
+  const int64_t n = int64_t(n1) * n1;
+  const int64_t total = B * n;
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total; q += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t col = q / n, node = q % n;
+    const int ix = int(node % n1), iy = int(node / n1);
+    r[q] = b[q] - stencil_apply(x + col * n, ix, iy, n1, d, e, c);
+  }
+}
+
+// full weighting = transpose of bilinear prolongation: coarse interior (I,J) sits on
+// fine interior (2I+1, 2J+1); weights 1, 1/2, 1/4.
+template <typename T>
+__global__ void restrict_kernel(const T* __restrict__ r, T* bc, int64_t B, int n1f) {
+  const int n1c = (n1f - 1) / 2;
+  const int64_t nf = int64_t(n1f) * n1f, nc = int64_t(n1c) * n1c;
+  const int64_t total = B * nc;
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total; q += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t col = q / nc, node = q % nc;
+    const int I = int(node % n1c), J = int(node / n1c);
+    const T* R = r + col * nf;
+    const int fx = 2 * I + 1, fy = 2 * J + 1;
+    const T cen = R[fy * n1f + fx];
+    const T edg = (R[(fy + 1) * n1f + fx] + R[(fy - 1) * n1f + fx]) + (R[fy * n1f + fx + 1] + R[fy * n1f + fx - 1]);
+    const T cor = (R[(fy + 1) * n1f + fx + 1] + R[(fy + 1) * n1f + fx - 1]) +
+                  (R[(fy - 1) * n1f + fx + 1] + R[(fy - 1) * n1f + fx - 1]);
+    bc[q] = cen + T(0.5) * edg + T(0.25) * cor;
+  }
+}
+
+// bilinear interpolation: fine interior i (grid node i+1); even grid node -> coarse node,
+// odd -> mean of the two neighbouring coarse nodes (boundary values are zero).
+template <typename T>
+__device__ __forceinline__ T ldc(const T* X, int I, int J, int n1c) {
+  return (I >= 0 && I < n1c && J >= 0 && J < n1c) ? X[J * n1c + I] : T(0);
+}
+
+template <typename T>
+__global__ void prolong_kernel(const T* __restrict__ xc, T* xf, int64_t B, int n1f) {
+  const int n1c = (n1f - 1) / 2;
+  const int64_t nf = int64_t(n1f) * n1f, nc = int64_t(n1c) * n1c;
+  const int64_t total = B * nf;
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total; q += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t col = q / nf, node = q % nf;
+    const int i = int(node % n1f), j = int(node / n1f);
+    const T* X = xc + col * nc;
+    const int gi = i + 1, gj = j + 1;     // fine grid node
+    T v;
+    if ((gi & 1) == 0 && (gj & 1) == 0) {
+      v = X[(gj / 2 - 1) * n1c + gi / 2 - 1];
+    } else if ((gi & 1) == 0) {
+      v = T(0.5) * (ldc(X, gi / 2 - 1, (gj - 1) / 2 - 1, n1c) + ldc(X, gi / 2 - 1, (gj + 1) / 2 - 1, n1c));
+    } else if ((gj & 1) == 0) {
+      v = T(0.5) * (ldc(X, (gi - 1) / 2 - 1, gj / 2 - 1, n1c) + ldc(X, (gi + 1) / 2 - 1, gj / 2 - 1, n1c));
+    } else {
+      v = T(0.25) * ((ldc(X, (gi - 1) / 2 - 1, (gj - 1) / 2 - 1, n1c) + ldc(X, (gi + 1) / 2 - 1, (gj - 1) / 2 - 1, n1c)) +
+                     (ldc(X, (gi - 1) / 2 - 1, (gj + 1) / 2 - 1, n1c) + ldc(X, (gi + 1) / 2 - 1, (gj + 1) / 2 - 1, n1c)));
+    }
+    xf[q] += v;
+  }
+}
+
+template <typename T>
+__global__ void scale_kernel(const T* __restrict__ b, T* x, int64_t cnt, T a) {
+  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < cnt; q += int64_t(gridDim.x) * blockDim.x)
+    x[q] = a * b[q];
+}
+
+template <typename T>
+cudaError_t launch_smooth(const T* b, const T* xin, T* xout, int64_t B, int n1, Stencil s, T omega, T* acc,
+                          int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st) {
+  const int64_t total = B * int64_t(n1) * n1;
+  if (total == 0) return cudaSuccess;
+  ProfScope ps(KK_SMOOTH, st, double(sizeof(T)) * total * (xin ? 3 : 2) + (acc ? double(sizeof(T)) * total : 0.0),
+               double(total) * (xin ? 21.0 : 1.0));
+  smooth_kernel<T><<<grid_for(total, 256), 256, 0, st>>>(b, xin, xout, B, n1, T(s.diag), T(s.edge), T(s.corner),
+                                                          omega, acc, acc_ss, acc_L, acc_col0);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_residual(const T* b, const T* x, T* r, int64_t B, int n1, Stencil s, cudaStream_t st) {
+  const int64_t total = B * int64_t(n1) * n1;
+  if (total == 0) return cudaSuccess;
+  ProfScope ps(KK_RESIDUAL, st, double(sizeof(T)) * total * 3, double(total) * 18.0);
+  residual_kernel<T><<<grid_for(total, 256), 256, 0, st>>>(b, x, r, B, n1, T(s.diag), T(s.edge), T(s.corner));
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_restrict(const T* r, T* bc, int64_t B, int n1f, cudaStream_t st) {
+  const int n1c = (n1f - 1) / 2;
+  const int64_t total = B * int64_t(n1c) * n1c;
+  if (total == 0) return cudaSuccess;
+  ProfScope ps(KK_RESTRICT, st, double(sizeof(T)) * total * 5, double(total) * 12.0);
+  restrict_kernel<T><<<grid_for(total, 256), 256, 0, st>>>(r, bc, B, n1f);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prolong_add(const T* xc, T* xf, int64_t B, int n1f, cudaStream_t st) {
+  const int64_t total = B * int64_t(n1f) * n1f;
+  if (total == 0) return cudaSuccess;
+  ProfScope ps(KK_PROLONG, st, double(sizeof(T)) * total * 2.25, double(total) * 3.0);
+  prolong_kernel<T><<<grid_for(total, 256), 256, 0, st>>>(xc, xf, B, n1f);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_scale(const T* b, T* x, int64_t cnt, T a, cudaStream_t st) {
+  if (cnt == 0) return cudaSuccess;
+  ProfScope ps(KK_VECTOR, st, 2.0 * sizeof(T) * cnt, 0.0);
+  scale_kernel<T><<<grid_for(cnt, 256), 256, 0, st>>>(b, x, cnt, a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Fused coarse V-cycle: one CTA per column, all levels in shared memory.
+// Level l arrays x_l, b_l; the residual is formed on the fly in the restriction.
+// Jacobi sweeps update in place through registers (read all, barrier, write all).
+// ---------------------------------------------------------------------------
+constexpr int kFusedThreads = 512;
+constexpr int kFusedPts = 8;                 // points per thread per sweep (registers)
+
+int fused_vcycle_max_n1(int esize) {
+  // largest n1 = 2^j - 1 whose level arrays (x, b on every level) fit in shared memory
+  // and whose sweeps fit kFusedThreads * kFusedPts points per pass
+  int best = 1;
+  for (int n1 = 1; n1 <= 4095; n1 = 2 * n1 + 1) {
+    size_t tot = 0;
+    for (int m = n1; m >= 1; m = (m - 1) / 2) tot += size_t(m) * m * 2 * esize;
+    if (tot <= 200 * 1024 && int64_t(n1) * n1 <= int64_t(kFusedThreads) * kFusedPts) best = n1;
+  }
+  return best;
+}
+
+template <typename T>
+__device__ void fused_smooth(T* x, const T* b, int n1, T d, T e, T c, T omega, bool from_zero) {
+  const int n = n1 * n1;
+  T nv[kFusedPts];
+  const T wd = omega / d;
+#pragma unroll
+  for (int j = 0; j < kFusedPts; ++j) {
+    const int q = threadIdx.x + j * kFusedThreads;
+    if (q < n) {
+      if (from_zero) {
+        nv[j] = wd * b[q];
+      } else {
+        const int ix = q % n1, iy = q / n1;
+        nv[j] = fma(wd, b[q] - stencil_apply(x, ix, iy, n1, d, e, c), x[q]);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kFusedPts; ++j) {
+    const int q = threadIdx.x + j * kFusedThreads;
+    if (q < n) x[q] = nv[j];
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFusedThreads) vcycle_fused_kernel(const T* __restrict__ bg, T* xg, FusedLevels L, T omega,
+                                                                     int nu, T* acc, int64_t acc_ss, int acc_L,
+                                                                     int acc_col0) {
+  extern __shared__ __align__(32) unsigned char vc_smem_raw[];
+  T* base = reinterpret_cast<T*>(vc_smem_raw);
+  T* xs[13];
+  T* bs[13];
+  {
+    size_t o = 0;
+    for (int l = 0; l < L.nlev; ++l) {
+      const int n = L.n1[l] * L.n1[l];
+      xs[l] = base + o; o += n;
+      bs[l] = base + o; o += n;
+    }
+  }
+  const int64_t col = blockIdx.x;
+  const int n0 = L.n1[0] * L.n1[0];
+  for (int q = threadIdx.x; q < n0; q += kFusedThreads) bs[0][q] = bg[col * n0 + q];
+  __syncthreads();
+  // descend
+  for (int l = 0; l < L.nlev - 1; ++l) {
+    const int n1 = L.n1[l];
+    const T d = T(L.diag[l]), e = T(L.edge[l]), c = T(L.corner[l]);
+    for (int s = 0; s < nu; ++s) fused_smooth(xs[l], bs[l], n1, d, e, c, omega, s == 0);
+    if (nu == 0) {
+      for (int q = threadIdx.x; q < n1 * n1; q += kFusedThreads) xs[l][q] = T(0);
+      __syncthreads();
+    }
+    // restriction of the residual b - A x
+    const int n1c = L.n1[l + 1];
+    for (int q = threadIdx.x; q < n1c * n1c; q += kFusedThreads) {
+      const int I = q % n1c, J = q / n1c;
+      const int fx = 2 * I + 1, fy = 2 * J + 1;
+      T acc_r = T(0);
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int ix = fx + dx, iy = fy + dy;
+          const T w = (dx == 0 ? T(1) : T(0.5)) * (dy == 0 ? T(1) : T(0.5));
+          const T rr = bs[l][iy * n1 + ix] - stencil_apply(xs[l], ix, iy, n1, d, e, c);
+          acc_r = fma(w, rr, acc_r);
+        }
+      bs[l + 1][q] = acc_r;
+    }
+    __syncthreads();
+  }
+  // coarsest: a single node
+  {
+    const int l = L.nlev - 1;
+    const int n = L.n1[l] * L.n1[l];
+    for (int q = threadIdx.x; q < n; q += kFusedThreads) xs[l][q] = bs[l][q] / T(L.diag[l]);
+    __syncthreads();
+  }
+  // ascend
+  for (int l = L.nlev - 2; l >= 0; --l) {
+    const int n1 = L.n1[l], n1c = L.n1[l + 1];
+    const T* X = xs[l + 1];
+    for (int q = threadIdx.x; q < n1 * n1; q += kFusedThreads) {
+      const int gi = q % n1 + 1, gj = q / n1 + 1;
+      T v;
+      if ((gi & 1) == 0 && (gj & 1) == 0) {
+        v = X[(gj / 2 - 1) * n1c + gi / 2 - 1];
+      } else if ((gi & 1) == 0) {
+        v = T(0.5) * (ldc(X, gi / 2 - 1, (gj - 1) / 2 - 1, n1c) + ldc(X, gi / 2 - 1, (gj + 1) / 2 - 1, n1c));
+      } else if ((gj & 1) == 0) {
+        v = T(0.5) * (ldc(X, (gi - 1) / 2 - 1, gj / 2 - 1, n1c) + ldc(X, (gi + 1) / 2 - 1, gj / 2 - 1, n1c));
+      } else {
+        v = T(0.25) * ((ldc(X, (gi - 1) / 2 - 1, (gj - 1) / 2 - 1, n1c) + ldc(X, (gi + 1) / 2 - 1, (gj - 1) / 2 - 1, n1c)) +
+                       (ldc(X, (gi - 1) / 2 - 1, (gj + 1) / 2 - 1, n1c) + ldc(X, (gi + 1) / 2 - 1, (gj + 1) / 2 - 1, n1c)));
+      }
+      xs[l][q] += v;
+    }
+    __syncthreads();
+    const T d = T(L.diag[l]), e = T(L.edge[l]), c = T(L.corner[l]);
+    for (int s = 0; s < nu; ++s) fused_smooth(xs[l], bs[l], n1, d, e, c, omega, false);
+  }
+  for (int q = threadIdx.x; q < n0; q += kFusedThreads) {
+    if (acc) {
+      const int64_t t = col / acc_L, cc = col % acc_L;
+      acc[t * acc_ss + (acc_col0 + cc) * int64_t(n0) + q] += xs[0][q];
+    } else {
+      xg[col * n0 + q] = xs[0][q];
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_vcycle_fused(const T* b, T* x, int64_t B, const FusedLevels& L, T omega, int nu, T* acc,
+                                int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  size_t smem = 0;
+  for (int l = 0; l < L.nlev; ++l) smem += size_t(L.n1[l]) * L.n1[l] * 2 * sizeof(T);
+  if (int64_t(L.n1[0]) * L.n1[0] > int64_t(kFusedThreads) * kFusedPts || smem > kMaxSmem)
+    return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(vcycle_fused_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const double n0 = double(L.n1[0]) * L.n1[0];
+  ProfScope ps(KK_VCYCLE_FUSED, st, double(sizeof(T)) * B * n0 * (acc ? 3 : 2),
+               double(B) * n0 * (4.0 / 3.0) * (21.0 * 2 * nu + 18.0 * 9 / 4 + 10.0));
+  vcycle_fused_kernel<T><<<dim3(unsigned(B)), kFusedThreads, smem, st>>>(b, x, L, omega, nu, acc, acc_ss, acc_L, acc_col0);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic float64 reductions and MINRES recurrences
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int NT>
+__device__ double block_sum(double v) {
+  __shared__ double red[NT / 32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    r = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  return r;   // valid in thread 0
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) dot_kernel(const T* __restrict__ a, const T* __restrict__ b, int64_t n, double* partial) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * int64_t(256) + threadIdx.x; i < n; i += int64_t(kDotBlocks) * 256)
+    s = fma(double(a[i]), double(b[i]), s);
+  s = block_sum<256>(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+template <typename T>
+cudaError_t launch_dot_partial(const T* a, const T* b, int64_t n, double* partial, cudaStream_t st) {
+  ProfScope ps(KK_DOT, st, double(sizeof(T)) * n * 2, double(n) * 2);
+  dot_kernel<T><<<kDotBlocks, 256, 0, st>>>(a, b, n, partial);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__device__ double reduce_partials(const double* partial) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += 256) s += partial[i];
+  return block_sum<256>(s);
+}
+
+__global__ void sum_partials_kernel(const double* partial, double* out) {
+  const double s = reduce_partials(partial);
+  if (threadIdx.x == 0) *out = s;
+}
+
+cudaError_t launch_sum_partials(const double* partial, double* out, cudaStream_t st) {
+  ProfScope ps(KK_SCALAR, st, 8.0 * kDotBlocks, 2.0 * kDotBlocks);
+  sum_partials_kernel<<<1, 256, 0, st>>>(partial, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void minres_init_kernel(MinresState* s, const double* partial, double target) {
+  const double vz = reduce_partials(partial);
+  if (threadIdx.x != 0) return;
+  s->dot = vz;
+  s->flag = 0;
+  s->iter = 0;
+  if (!(vz > 0.0)) { s->flag = (vz == vz) ? 3 : 4; s->beta = 1.0; s->beta1 = 1.0; s->est = 1.0; return; }
+  s->beta = sqrt(vz);
+  s->beta1 = s->beta;
+  s->beta_prev = 1.0;
+  s->eta = s->beta;
+  s->c_m1 = s->c_m2 = 1.0;
+  s->s_m1 = s->s_m2 = 0.0;
+  s->est = 1.0;
+  s->target = target;
+}
+
+__global__ void minres_alpha_kernel(MinresState* s, const double* partial) {
+  const double zkz = reduce_partials(partial);
+  if (threadIdx.x != 0) return;
+  const double b = s->beta;
+  s->dot = zkz;
+  s->alpha = zkz / (b * b);                 // q^T K q with q = z / beta
+  s->coef_q = 1.0 / b;
+  s->coef_v = s->alpha / b;
+  s->coef_vp = s->iter == 0 ? 0.0 : b / s->beta_prev;
+  if (!(s->alpha == s->alpha)) s->flag = 4;
+}
+
+__global__ void minres_rotate_kernel(MinresState* s, const double* partial) {
+  const double vz = reduce_partials(partial);
+  if (threadIdx.x != 0) return;
+  s->dot = vz;
+  if (!(vz == vz)) { s->flag = 4; return; }
+  if (vz < 0.0) { s->flag = 3; return; }
+  const double bn = sqrt(vz);
+  const double b = s->beta, al = s->alpha;
+  const double eps = s->s_m2 * b;
+  const double dprime = s->c_m2 * b;
+  const double delta = s->c_m1 * dprime + s->s_m1 * al;
+  const double gbar = -s->s_m1 * dprime + s->c_m1 * al;
+  const double rho = hypot(gbar, bn);
+  if (rho == 0.0) { s->flag = 2; s->w_q = s->w_m1 = s->w_m2 = s->x_w = 0.0; return; }
+  const double c = gbar / rho, sn = bn / rho;
+  s->eps = eps; s->delta = delta; s->rho = rho; s->c = c; s->s = sn;
+  s->w_q = 1.0 / (b * rho);
+  s->w_m1 = delta / rho;
+  s->w_m2 = eps / rho;
+  s->x_w = c * s->eta;
+  s->eta = -sn * s->eta;
+  s->est = fabs(s->eta) / s->beta1;
+  s->c_m2 = s->c_m1; s->s_m2 = s->s_m1;
+  s->c_m1 = c; s->s_m1 = sn;
+  s->beta_prev = b;
+  s->beta = bn;
+  s->iter += 1;
+  if (!(s->est == s->est)) s->flag = 4;
+  else if (s->est <= s->target) s->flag = 1;
+  else if (bn == 0.0) s->flag = 2;
+}
+
+cudaError_t launch_minres_init(MinresState* s, const double* partial, double target, cudaStream_t st) {
+  ProfScope ps(KK_SCALAR, st, 8.0 * kDotBlocks, 2.0 * kDotBlocks);
+  minres_init_kernel<<<1, 256, 0, st>>>(s, partial, target);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_minres_alpha(MinresState* s, const double* partial, cudaStream_t st) {
+  ProfScope ps(KK_SCALAR, st, 8.0 * kDotBlocks, 2.0 * kDotBlocks);
+  minres_alpha_kernel<<<1, 256, 0, st>>>(s, partial);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_minres_rotate(MinresState* s, const double* partial, cudaStream_t st) {
+  ProfScope ps(KK_SCALAR, st, 8.0 * kDotBlocks, 2.0 * kDotBlocks);
+  minres_rotate_kernel<<<1, 256, 0, st>>>(s, partial);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void minres_v_kernel(const T* __restrict__ Kz, const T* __restrict__ v, T* vprev, int64_t n,
+                                const MinresState* s) {
+  const T cq = T(s->coef_q), cv = T(s->coef_v), cvp = T(s->coef_vp);
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    T r = cq * Kz[i] - cv * v[i];
+    if (cvp != T(0)) r -= cvp * vprev[i];
+    vprev[i] = r;
+  }
+}
+
+template <typename T, typename TX>
+__global__ void minres_wx_kernel(const T* __restrict__ z, const T* __restrict__ wm1, T* wm2, TX* x, int64_t n,
+                                 const MinresState* s) {
+  const T wq = T(s->w_q), w1 = T(s->w_m1), w2 = T(s->w_m2);
+  const TX xw = TX(s->x_w);
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const T w = wq * z[i] - w1 * wm1[i] - w2 * wm2[i];
+    wm2[i] = w;
+    x[i] += xw * TX(w);
+  }
+}
+
+template <typename T>
+cudaError_t launch_minres_v(const T* Kz, const T* v, T* vprev, int64_t n, const MinresState* s, cudaStream_t st) {
+  ProfScope ps(KK_VECTOR, st, double(sizeof(T)) * n * 4, double(n) * 5);
+  minres_v_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(Kz, v, vprev, n, s);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T, typename TX>
+cudaError_t launch_minres_wx(const T* z, const T* wm1, T* wm2, TX* x, int64_t n, const MinresState* s,
+                             cudaStream_t st) {
+  ProfScope ps(KK_VECTOR, st, double(sizeof(T)) * n * 4 + double(sizeof(TX)) * n * 2, double(n) * 8);
+  minres_wx_kernel<T, TX><<<grid_for(n, 256), 256, 0, st>>>(z, wm1, wm2, x, n, s);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename TA, typename TB>
+__global__ void convert_kernel(const TA* a, TB* b, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    b[i] = TB(a[i]);
+}
+template <typename TA, typename TB>
+cudaError_t launch_convert(const TA* a, TB* b, int64_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  ProfScope ps(KK_VECTOR, st, double(sizeof(TA) + sizeof(TB)) * n, 0.0);
+  convert_kernel<TA, TB><<<grid_for(n, 256), 256, 0, st>>>(a, b, n);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void sub_kernel(const double* a, const double* b, double* y, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    y[i] = a[i] - b[i];
+}
+cudaError_t launch_sub(const double* a, const double* b, double* y, int64_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  ProfScope ps(KK_VECTOR, st, 24.0 * n, 0.0);
+  sub_kernel<<<grid_for(n, 256), 256, 0, st>>>(a, b, y, n);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void add_to_kernel(const T* d, double* x, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    x[i] += double(d[i]);
+}
+template <typename T>
+cudaError_t launch_add_to(const T* d, double* x, int64_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  ProfScope ps(KK_VECTOR, st, (sizeof(T) + 16.0) * n, 0.0);
+  add_to_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(d, x, n);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void add_scaled_kernel(const float* d, double* x, int64_t n, double a) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    x[i] = fma(a, double(d[i]), x[i]);
+}
+cudaError_t launch_add_scaled(const float* d, double* x, int64_t n, double a, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  ProfScope ps(KK_VECTOR, st, 20.0 * n, 0.0);
+  add_scaled_kernel<<<grid_for(n, 256), 256, 0, st>>>(d, x, n, a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void scale_to32_kernel(const double* x, float* y, int64_t n, double a) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    y[i] = float(a * x[i]);
+}
+cudaError_t launch_scale_to32(const double* x, float* y, int64_t n, double a, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  ProfScope ps(KK_VECTOR, st, 12.0 * n, 0.0);
+  scale_to32_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, y, n, a);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void fill_kernel(T* x, int64_t n, T v) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) x[i] = v;
+}
+template <typename T>
+cudaError_t launch_fill(T* x, int64_t n, T v, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  ProfScope ps(KK_VECTOR, st, double(sizeof(T)) * n, 0.0);
+  fill_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(x, n, v);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// explicit instantiations
+#define SGOC_INST(T)                                                                                               \
+  template cudaError_t launch_sg<T>(const SGArgs<T>&, cudaStream_t);                                               \
+  template cudaError_t launch_mass<T>(const MassArgs<T>&, cudaStream_t);                                           \
+  template cudaError_t launch_cheb<T>(const ChebArgs<T>&, cudaStream_t);                                           \
+  template cudaError_t launch_smooth<T>(const T*, const T*, T*, int64_t, int, Stencil, T, T*, int64_t, int, int,   \
+                                        cudaStream_t);                                                             \
+  template cudaError_t launch_residual<T>(const T*, const T*, T*, int64_t, int, Stencil, cudaStream_t);            \
+  template cudaError_t launch_restrict<T>(const T*, T*, int64_t, int, cudaStream_t);                               \
+  template cudaError_t launch_prolong_add<T>(const T*, T*, int64_t, int, cudaStream_t);                            \
+  template cudaError_t launch_scale<T>(const T*, T*, int64_t, T, cudaStream_t);                                    \
+  template cudaError_t launch_vcycle_fused<T>(const T*, T*, int64_t, const FusedLevels&, T, int, T*, int64_t, int, \
+                                              int, cudaStream_t);                                                  \
+  template cudaError_t launch_dot_partial<T>(const T*, const T*, int64_t, double*, cudaStream_t);                  \
+  template cudaError_t launch_minres_v<T>(const T*, const T*, T*, int64_t, const MinresState*, cudaStream_t);      \
+  template cudaError_t launch_add_to<T>(const T*, double*, int64_t, cudaStream_t);                                 \
+  template cudaError_t launch_fill<T>(T*, int64_t, T, cudaStream_t);
+
+SGOC_INST(float)
+SGOC_INST(double)
+template cudaError_t launch_minres_wx<double, double>(const double*, const double*, double*, double*, int64_t,
+                                                      const MinresState*, cudaStream_t);
+template cudaError_t launch_minres_wx<float, float>(const float*, const float*, float*, float*, int64_t,
+                                                    const MinresState*, cudaStream_t);
+template cudaError_t launch_convert<double, float>(const double*, float*, int64_t, cudaStream_t);
+template cudaError_t launch_convert<float, double>(const float*, double*, int64_t, cudaStream_t);
+
+}  // namespace sgoc

@@ -1,0 +1,144 @@
+// Launchers of the device kernels (templated on the vector type T = float or double).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sgoc {
+
+// Number of kernels this library has launched in the process (all streams).
+int64_t kernel_launches();
+
+// Optional per-kernel-class timing: when enabled, every launch is bracketed by
+// CUDA events on its stream and its algorithmic bytes/flops are recorded.
+enum KernelKind {
+  KK_SG = 0, KK_MASS, KK_CHEB, KK_SMOOTH, KK_RESIDUAL, KK_RESTRICT, KK_PROLONG, KK_VCYCLE_FUSED,
+  KK_DOT, KK_SCALAR, KK_VECTOR, KK_COUNT
+};
+const char* kernel_kind_name(int kind);
+void profile_enable(bool on);
+bool profile_query(int kind, int64_t* launches, double* ms, double* bytes, double* flops);
+struct ProfScope {
+  ProfScope(int kind, cudaStream_t st, double bytes, double flops);
+  ~ProfScope();
+  int kind; cudaStream_t st; int slot;
+};
+
+// out[t][beta] = cr*R + c0*(K_0 X)[beta] + c1*sum_{k=1}^{kmax-1} (K_k X G_k)[beta]
+//              + cm*(M X)[beta] + cy*out_old,   beta in [out0, out1), t < nslabs.
+// X is read in columns [in0, in1) (must contain every neighbour of the output
+// columns and the output columns themselves).  Column beta of slab t of an
+// operand Z lives at Z + t*zs + (beta - zcol0)*n.
+template <typename T>
+struct SGArgs {
+  const T* X; int64_t xs;
+  T* Y; int64_t ys; int ycol0;
+  const T* R; int64_t rs; int rcol0;
+  int n1; int64_t n; int nx; int M;
+  int out0, out1, in0, in1, kmax, nslabs;
+  T c0, c1, cm, cr, cy;
+  T mass;                       // h^2/36
+  const T* kap;                 // kappa_k(e)/6, (M+1) x nx x nx
+  const int* nbr_ptr; const int* nbr_alpha; const int* nbr_k; const T* nbr_c;
+  double deg_sum;               // number of (beta, neighbour) pairs used (work accounting only)
+};
+template <typename T>
+cudaError_t launch_sg(const SGArgs<T>& a, cudaStream_t st);
+
+// out[t][c] = cy*out_old + sum_j a_j w_j(c,t) (M V_j[t + shift_j])[c] + ar*R[t][c]
+// for columns c in [0, ncols) of each slab (column c is global column col0 + c).
+// Weight flags: bit 0 multiplies by H^gamma(col) = (col == 0 ? 1 : 1 + gamma),
+// bit 1 by D_t (1/2 at the first and last of nt >= 2 steps, else 1).
+template <typename T>
+struct MassArgs {
+  T* out; int64_t os;
+  int ncols, col0, nslabs, n1; int64_t n;
+  T mass, cy, ar, gamma;
+  int nt;
+  int nv;
+  const T* V[3]; int64_t vs[3]; int shift[3]; T a[3]; int wflags[3];
+  const T* R; int64_t rs;
+};
+template <typename T>
+cudaError_t launch_mass(const MassArgs<T>& a, cudaStream_t st);
+
+// Chebyshev semi-iteration for M X = B on ncols columns of n entries
+// (textbook Golub-Varga weights, D = 5/4 diag(M), rho = 4/5).
+// scale_mode 0: X scaled by 1; 1: block-preconditioner scaling of the
+// (1,1)/(2,2) blocks (1/(sc_t H^gamma) for the first slabs*P columns, 1/(sc_t beta) after).
+template <typename T>
+struct ChebArgs {
+  const T* B; T* X; T* tmpA; T* tmpB;
+  int64_t ncols; int n1; int64_t n; int steps; T mass;
+  int scale_mode; int P; int slabs; int nt; T tau; T beta; T gamma;
+};
+template <typename T>
+cudaError_t launch_cheb(const ChebArgs<T>& a, cudaStream_t st);
+
+// Multigrid level kernels on batches of columns stored contiguously [b][node].
+struct Stencil { double diag, edge, corner; };
+template <typename T>
+cudaError_t launch_smooth(const T* b, const T* xin, T* xout, int64_t B, int n1, Stencil s, T omega,
+                          T* acc, int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st);
+template <typename T>
+cudaError_t launch_residual(const T* b, const T* x, T* r, int64_t B, int n1, Stencil s, cudaStream_t st);
+template <typename T>
+cudaError_t launch_restrict(const T* r, T* bc, int64_t B, int n1f, cudaStream_t st);
+template <typename T>
+cudaError_t launch_prolong_add(const T* xc, T* xf, int64_t B, int n1f, cudaStream_t st);
+template <typename T>
+cudaError_t launch_scale(const T* b, T* x, int64_t cnt, T a, cudaStream_t st);
+
+// Fused V-cycle of the coarse part of the hierarchy, one CTA per column:
+// levels lv[0] (finest handled, n1 = lv_n1[0]) down to a single node.
+struct FusedLevels { int nlev; int n1[13]; double diag[13], edge[13], corner[13]; };
+template <typename T>
+cudaError_t launch_vcycle_fused(const T* b, T* x, int64_t B, const FusedLevels& L, T omega, int nu,
+                                T* acc, int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st);
+int fused_vcycle_max_n1(int esize);
+
+// Krylov kernels.  Reductions are deterministic: fixed grid, fixed order.
+constexpr int kDotBlocks = 608;
+template <typename T>
+cudaError_t launch_dot_partial(const T* a, const T* b, int64_t n, double* partial, cudaStream_t st);
+cudaError_t launch_sum_partials(const double* partial, double* out, cudaStream_t st);
+
+// MINRES scalar state (float64, device resident)
+struct MinresState {
+  double beta, beta_prev, beta1, eta;
+  double c_m1, s_m1, c_m2, s_m2;
+  double alpha, eps, delta, rho, c, s;
+  double est, target;
+  double coef_v, coef_vp, coef_q;      // coefficients of the v-recurrence
+  double w_q, w_m1, w_m2, x_w;         // coefficients of the w/x updates
+  double dot;                          // last reduced dot
+  int flag;                            // 0 running, 1 est<=target, 2 breakdown(beta=0), 3 not SPD, 4 NaN
+  int iter;
+};
+cudaError_t launch_minres_init(MinresState* s, const double* partial, double target, cudaStream_t st);
+cudaError_t launch_minres_alpha(MinresState* s, const double* partial, cudaStream_t st);
+cudaError_t launch_minres_rotate(MinresState* s, const double* partial, cudaStream_t st);
+// v_new (in place over v_prev) = Kz*coef_q - v*coef_v - v_prev*coef_vp
+template <typename T>
+cudaError_t launch_minres_v(const T* Kz, const T* v, T* vprev, int64_t n, const MinresState* s, cudaStream_t st);
+// w_new (over w_m2) = z*w_q - w_m1*w_m1c - w_m2*w_m2c ; x += x_w * w_new
+template <typename T, typename TX>
+cudaError_t launch_minres_wx(const T* z, const T* wm1, T* wm2, TX* x, int64_t n, const MinresState* s,
+                             cudaStream_t st);
+
+// elementwise helpers
+template <typename TA, typename TB>
+cudaError_t launch_convert(const TA* a, TB* b, int64_t n, cudaStream_t st);
+// y = a - b (float64); y may alias a
+cudaError_t launch_sub(const double* a, const double* b, double* y, int64_t n, cudaStream_t st);
+// x += (double) d
+template <typename T>
+cudaError_t launch_add_to(const T* d, double* x, int64_t n, cudaStream_t st);
+// x += a * (double) d
+cudaError_t launch_add_scaled(const float* d, double* x, int64_t n, double a, cudaStream_t st);
+// y = a * x (scaling into float32 with a float64 scale)
+cudaError_t launch_scale_to32(const double* x, float* y, int64_t n, double a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fill(T* x, int64_t n, T v, cudaStream_t st);
+
+}  // namespace sgoc

@@ -1,0 +1,310 @@
+// Host set-up of an SG optimal-control problem: validation, chaos basis,
+// triple-product tables, multigrid hierarchy of the mean operator, and the
+// upload of the coefficient data into the caller's persistent device buffer.
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "sgoc_internal.h"
+
+namespace sgoc {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+// Graded multi-index set, lexicographically descending inside each degree
+// (degree 1 is e_1, ..., e_M): the level structure swept by Alg. 1.
+static void gen_degree(int M, int pos, int remaining, std::vector<int32_t>& cur,
+                       std::vector<int32_t>& out) {
+  if (pos == M - 1) {
+    cur[pos] = remaining;
+    out.insert(out.end(), cur.begin(), cur.end());
+    return;
+  }
+  for (int v = remaining; v >= 0; --v) {
+    cur[pos] = v;
+    gen_degree(M, pos + 1, remaining - v, cur, out);
+  }
+}
+
+static double binom(int a, int b) {
+  if (b < 0 || b > a) return 0.0;
+  double r = 1.0;
+  for (int i = 1; i <= b; ++i) r = r * (a - b + i) / i;
+  return r;
+}
+
+// E[xi psi_n psi_{n+1}] for orthonormal Legendre polynomials psi_n = sqrt(2n+1) P_n,
+// xi ~ U[-1,1], from the three-term recurrence xi P_n = ((n+1) P_{n+1} + n P_{n-1})/(2n+1).
+static double legendre_coupling(int n) {
+  return (n + 1) / std::sqrt((2.0 * n + 1.0) * (2.0 * n + 3.0));
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace sgoc
+
+using namespace sgoc;
+
+extern "C" {
+
+const char* sgoc_last_error(void) { return g_last_error.c_str(); }
+
+const char* sgoc_status_string(sgoc_status s) {
+  switch (s) {
+    case SGOC_OK: return "ok";
+    case SGOC_ERR_INVALID_ARG: return "invalid argument";
+    case SGOC_ERR_UNSUPPORTED: return "unsupported problem";
+    case SGOC_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case SGOC_ERR_CUDA: return "CUDA error";
+    case SGOC_ERR_NO_CONVERGENCE: return "no convergence";
+    case SGOC_ERR_BREAKDOWN: return "Lanczos breakdown";
+    case SGOC_ERR_NOT_SPD: return "preconditioner not positive definite";
+    case SGOC_ERR_NAN: return "NaN or Inf";
+    case SGOC_ERR_NOT_UPLOADED: return "problem data not uploaded";
+  }
+  return "unknown status";
+}
+
+void sgoc_default_options(sgoc_options* o) {
+  if (!o) return;
+  o->tol = 1e-8;
+  o->max_iter = 1000;
+  o->r = 0;
+  o->cheb_steps = 5;
+  o->nu_pre = 2;
+  o->nu_post = 2;
+  o->omega = 0.8;
+  o->precision = SGOC_FP64;
+  o->inner_tol = 1e-4;
+  o->max_outer = 20;
+}
+
+sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* opt,
+                                sgoc_problem** out) {
+  if (!d || !out) { set_error("null desc/out"); return SGOC_ERR_INVALID_ARG; }
+  *out = nullptr;
+  const int nx = d->nx;
+  if (nx < 2 || nx > 4096 || (nx & (nx - 1)) != 0) {
+    set_error("nx must be a power of two in [2, 4096]");
+    return (nx >= 2 && nx <= 4096) ? SGOC_ERR_UNSUPPORTED : SGOC_ERR_INVALID_ARG;
+  }
+  if (d->M < 0 || d->M > 16 || d->p < 0 || d->p > 10) { set_error("M in [0,16], p in [0,10]"); return SGOC_ERR_INVALID_ARG; }
+  if (!(d->beta > 0.0) || !(d->gamma >= 0.0) || !std::isfinite(d->beta) || !std::isfinite(d->gamma)) {
+    set_error("beta > 0 and gamma >= 0 required"); return SGOC_ERR_INVALID_ARG;
+  }
+  if (d->nt < 0 || d->nt > 100000 || (d->nt > 0 && !(d->T > 0.0))) { set_error("nt >= 0, T > 0"); return SGOC_ERR_INVALID_ARG; }
+  if (!d->kappa || !d->yhat) { set_error("kappa and yhat are required"); return SGOC_ERR_INVALID_ARG; }
+  const double Pd = binom(d->M + d->p, d->p);
+  if (Pd > 20000) { set_error("chaos basis too large (P > 20000)"); return SGOC_ERR_UNSUPPORTED; }
+  sgoc_options o;
+  sgoc_default_options(&o);
+  if (opt) o = *opt;
+  if (o.r == 0) o.r = d->M + 1;
+  if (o.r < 1 || o.r > d->M + 1) { set_error("truncation r must be in [1, M+1]"); return SGOC_ERR_INVALID_ARG; }
+  if (!(o.tol > 0) || o.max_iter < 1 || o.cheb_steps < 1 || o.cheb_steps > 64 || o.nu_pre < 0 || o.nu_post < 0 ||
+      o.nu_pre > 16 || o.nu_post > 16 || o.nu_pre != o.nu_post || !(o.omega > 0 && o.omega < 2) ||
+      (o.precision != SGOC_FP64 && o.precision != SGOC_MIXED_FP32) || !(o.inner_tol > 0 && o.inner_tol < 1) ||
+      o.max_outer < 1) {
+    set_error("invalid options (nu_pre must equal nu_post for a symmetric V-cycle)");
+    return SGOC_ERR_INVALID_ARG;
+  }
+
+  auto* pb = new sgoc_problem();
+  pb->nx = nx; pb->M = d->M; pb->p = d->p; pb->nt = d->nt;
+  pb->beta = d->beta; pb->gamma = d->gamma; pb->T = d->T;
+  pb->tau = d->nt > 0 ? d->T / d->nt : 1.0;
+  pb->n1 = nx - 1;
+  pb->n = int64_t(pb->n1) * pb->n1;
+  pb->P = int(Pd + 0.5);
+  pb->slabs = d->nt > 0 ? d->nt : 1;
+  pb->F = int64_t(pb->slabs) * pb->P * pb->n;
+  pb->N = 3 * pb->F;
+  pb->opt = o;
+  pb->r = o.r;
+  pb->s = std::sqrt((1.0 + d->gamma) / d->beta);
+
+  const int64_t nel = int64_t(nx) * nx;
+  pb->kappa.assign(d->kappa, d->kappa + (d->M + 1) * nel);
+  for (double v : pb->kappa)
+    if (!std::isfinite(v)) { delete pb; set_error("non-finite kappa"); return SGOC_ERR_NAN; }
+  pb->kappa0 = pb->kappa[0];
+  for (int64_t e = 0; e < nel; ++e)
+    if (pb->kappa[e] != pb->kappa0) {
+      delete pb;
+      set_error("kappa_0 (the mean field) must be spatially constant");
+      return SGOC_ERR_UNSUPPORTED;
+    }
+  if (!(pb->kappa0 > 0)) { delete pb; set_error("kappa_0 must be positive"); return SGOC_ERR_INVALID_ARG; }
+  pb->yhat.assign(d->yhat, d->yhat + int64_t(pb->slabs) * pb->n);
+  for (double v : pb->yhat)
+    if (!std::isfinite(v)) { delete pb; set_error("non-finite yhat"); return SGOC_ERR_NAN; }
+  if (d->nt > 0 && d->y0) {
+    pb->y0.assign(d->y0, d->y0 + pb->n);
+    for (double v : pb->y0)
+      if (!std::isfinite(v)) { delete pb; set_error("non-finite y0"); return SGOC_ERR_NAN; }
+  }
+
+  // chaos multi-indices, graded
+  const int M = d->M, p = d->p;
+  if (M > 0) {
+    std::vector<int32_t> cur(M, 0);
+    for (int deg = 0; deg <= p; ++deg) gen_degree(M, 0, deg, cur, pb->idx);
+  }
+  pb->off.resize(p + 2);
+  pb->off[0] = 0;
+  for (int deg = 0; deg <= p; ++deg) pb->off[deg + 1] = int(binom(M + deg, deg) + 0.5);
+  if (M > 0 && int64_t(pb->idx.size()) != int64_t(pb->P) * M) {
+    delete pb; set_error("internal: multi-index count"); return SGOC_ERR_INVALID_ARG;
+  }
+  // neighbour table of G_k: beta couples to beta + e_k and beta - e_k
+  std::map<std::vector<int32_t>, int> pos;
+  for (int a = 0; a < pb->P && M > 0; ++a)
+    pos[std::vector<int32_t>(pb->idx.begin() + int64_t(a) * M, pb->idx.begin() + int64_t(a + 1) * M)] = a;
+  pb->nbr_ptr.assign(pb->P + 1, 0);
+  for (int b = 0; b < pb->P; ++b) {
+    for (int k = 0; k < M; ++k) {
+      std::vector<int32_t> v(pb->idx.begin() + int64_t(b) * M, pb->idx.begin() + int64_t(b + 1) * M);
+      const int bk = v[k];
+      if (bk >= 1) {
+        v[k] = bk - 1;
+        auto it = pos.find(v);
+        if (it != pos.end()) {
+          pb->nbr_alpha.push_back(it->second); pb->nbr_k.push_back(k + 1);
+          pb->nbr_c.push_back(legendre_coupling(bk - 1));
+        }
+      }
+      v[k] = bk + 1;
+      auto it = pos.find(v);
+      if (it != pos.end()) {
+        pb->nbr_alpha.push_back(it->second); pb->nbr_k.push_back(k + 1);
+        pb->nbr_c.push_back(legendre_coupling(bk));
+      }
+    }
+    pb->nbr_ptr[b + 1] = int(pb->nbr_alpha.size());
+  }
+
+  // multigrid hierarchy of the mean operator:
+  // steady  A~_1 = kappa0 K + s M            (Eq. (mathcalZ))
+  // time    A^_1 = (1 + tau s) M + tau kappa0 K  (Eq. (A_hat))
+  // Q1 on a uniform grid: K stencil (1/3)[-1 -1 -1; -1 8 -1; -1 -1 -1], M = h^2/36 [1 4 1; 4 16 4; 1 4 1];
+  // Galerkin coarse operators of nested Q1 spaces are the coarse-grid Q1 matrices.
+  const double ck = d->nt > 0 ? pb->tau * pb->kappa0 : pb->kappa0;
+  const double cm = d->nt > 0 ? 1.0 + pb->tau * pb->s : pb->s;
+  for (int g = nx; g >= 2; g /= 2) {
+    Level L;
+    L.nx = g; L.n1 = g - 1; L.n = int64_t(L.n1) * L.n1;
+    const double h = 1.0 / g, m = h * h / 36.0;
+    L.diag = ck * (8.0 / 3.0) + cm * 16.0 * m;
+    L.edge = -ck / 3.0 + cm * 4.0 * m;
+    L.corner = -ck / 3.0 + cm * m;
+    pb->levels.push_back(L);
+  }
+  pb->mass_h2_36 = 1.0 / (36.0 * nx * double(nx));
+  pb->dweights.assign(pb->slabs, 1.0);
+  if (d->nt > 1) { pb->dweights[0] = 0.5; pb->dweights[d->nt - 1] = 0.5; }
+
+  // persistent layout
+  const size_t nk = size_t(M + 1) * nel;
+  const size_t nnz = pb->nbr_alpha.size();
+  size_t off = 0;
+  off = align256(off + nk * 8); off = align256(off + nk * 4);
+  off = align256(off + (pb->P + 1) * 4); off = align256(off + nnz * 4); off = align256(off + nnz * 4);
+  off = align256(off + nnz * 8); off = align256(off + nnz * 4);
+  off = align256(off + size_t(pb->slabs) * pb->n * 8); off = align256(off + size_t(pb->n) * 8);
+  pb->persistent_bytes = off;
+  *out = pb;
+  return SGOC_OK;
+}
+
+void sgoc_problem_destroy(sgoc_problem* pb) { delete pb; }
+
+sgoc_status sgoc_problem_sizes(const sgoc_problem* pb, int64_t* n, int64_t* P, int64_t* slabs,
+                               int64_t* kkt) {
+  if (!pb) { set_error("null problem"); return SGOC_ERR_INVALID_ARG; }
+  if (n) *n = pb->n;
+  if (P) *P = pb->P;
+  if (slabs) *slabs = pb->slabs;
+  if (kkt) *kkt = pb->N;
+  return SGOC_OK;
+}
+
+sgoc_status sgoc_problem_device_bytes(const sgoc_problem* pb, size_t* persistent, size_t* workspace) {
+  if (!pb) { set_error("null problem"); return SGOC_ERR_INVALID_ARG; }
+  if (persistent) *persistent = pb->persistent_bytes;
+  if (workspace) *workspace = workspace_bytes(pb, pb->opt.precision);
+  return SGOC_OK;
+}
+
+sgoc_status sgoc_problem_upload(sgoc_problem* pb, void* d_persistent, size_t bytes, void* stream) {
+  if (!pb || !d_persistent) { set_error("null problem/buffer"); return SGOC_ERR_INVALID_ARG; }
+  if (bytes < pb->persistent_bytes) { set_error("persistent buffer too small"); return SGOC_ERR_WORKSPACE_TOO_SMALL; }
+  if (reinterpret_cast<uintptr_t>(d_persistent) % 256) { set_error("persistent buffer must be 256-byte aligned"); return SGOC_ERR_INVALID_ARG; }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int M = pb->M;
+  const size_t nel = size_t(pb->nx) * pb->nx, nk = size_t(M + 1) * nel;
+  const size_t nnz = pb->nbr_alpha.size();
+  char* base = static_cast<char*>(d_persistent);
+  size_t off = 0;
+  auto carve = [&](size_t b) { char* p = base + off; off = align256(off + b); return p; };
+  pb->dev.kap64 = reinterpret_cast<double*>(carve(nk * 8));
+  pb->dev.kap32 = reinterpret_cast<float*>(carve(nk * 4));
+  pb->dev.nbr_ptr = reinterpret_cast<int*>(carve((pb->P + 1) * 4));
+  pb->dev.nbr_alpha = reinterpret_cast<int*>(carve(nnz * 4));
+  pb->dev.nbr_k = reinterpret_cast<int*>(carve(nnz * 4));
+  pb->dev.nbr_c64 = reinterpret_cast<double*>(carve(nnz * 8));
+  pb->dev.nbr_c32 = reinterpret_cast<float*>(carve(nnz * 4));
+  pb->dev.yhat = reinterpret_cast<double*>(carve(size_t(pb->slabs) * pb->n * 8));
+  pb->dev.y0 = reinterpret_cast<double*>(carve(size_t(pb->n) * 8));
+
+  std::vector<double> k64(nk);
+  std::vector<float> k32(nk);
+  for (size_t i = 0; i < nk; ++i) { k64[i] = pb->kappa[i] / 6.0; k32[i] = float(k64[i]); }
+  std::vector<float> c32(pb->nbr_c.begin(), pb->nbr_c.end());
+  SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.kap64, k64.data(), nk * 8, cudaMemcpyHostToDevice, st));
+  SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.kap32, k32.data(), nk * 4, cudaMemcpyHostToDevice, st));
+  SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.nbr_ptr, pb->nbr_ptr.data(), (pb->P + 1) * 4, cudaMemcpyHostToDevice, st));
+  if (nnz) {
+    SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.nbr_alpha, pb->nbr_alpha.data(), nnz * 4, cudaMemcpyHostToDevice, st));
+    SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.nbr_k, pb->nbr_k.data(), nnz * 4, cudaMemcpyHostToDevice, st));
+    SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.nbr_c64, pb->nbr_c.data(), nnz * 8, cudaMemcpyHostToDevice, st));
+    SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.nbr_c32, c32.data(), nnz * 4, cudaMemcpyHostToDevice, st));
+  }
+  SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.yhat, pb->yhat.data(), size_t(pb->slabs) * pb->n * 8,
+                                cudaMemcpyHostToDevice, st));
+  if (!pb->y0.empty())
+    SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.y0, pb->y0.data(), size_t(pb->n) * 8, cudaMemcpyHostToDevice, st));
+  else
+    SGOC_CUDA_TRY(cudaMemsetAsync(pb->dev.y0, 0, size_t(pb->n) * 8, st));
+  // the host vectors above go out of scope: finish the copies first
+  SGOC_CUDA_TRY(cudaStreamSynchronize(st));
+  pb->uploaded = true;
+  return SGOC_OK;
+}
+
+sgoc_status sgoc_pc_indices(const sgoc_problem* pb, int32_t* host_out) {
+  if (!pb || (!host_out && pb->M > 0)) { set_error("null argument"); return SGOC_ERR_INVALID_ARG; }
+  if (pb->M > 0) std::memcpy(host_out, pb->idx.data(), pb->idx.size() * sizeof(int32_t));
+  return SGOC_OK;
+}
+
+sgoc_status sgoc_triple_products(const sgoc_problem* pb, int32_t* k, int32_t* a, int32_t* b,
+                                 double* c, int64_t* nnz) {
+  if (!pb || !nnz) { set_error("null argument"); return SGOC_ERR_INVALID_ARG; }
+  const int64_t cnt = int64_t(pb->nbr_alpha.size());
+  if (!k && !a && !b && !c) { *nnz = cnt; return SGOC_OK; }
+  if (!k || !a || !b || !c) { set_error("all output arrays are required"); return SGOC_ERR_INVALID_ARG; }
+  if (*nnz < cnt) { *nnz = cnt; set_error("capacity too small"); return SGOC_ERR_INVALID_ARG; }
+  int64_t q = 0;
+  for (int beta = 0; beta < pb->P; ++beta)
+    for (int e = pb->nbr_ptr[beta]; e < pb->nbr_ptr[beta + 1]; ++e, ++q) {
+      k[q] = pb->nbr_k[e]; a[q] = pb->nbr_alpha[e]; b[q] = beta; c[q] = pb->nbr_c[e];
+    }
+  *nnz = cnt;
+  return SGOC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,87 @@
+// Internal definitions of the SG optimal-control solver library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sgoc.h"
+
+namespace sgoc {
+
+// Thread-local message for sgoc_last_error().
+void set_error(const std::string& msg);
+
+#define SGOC_CUDA_TRY(expr)                                                       \
+  do {                                                                            \
+    cudaError_t e_ = (expr);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      ::sgoc::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));      \
+      return SGOC_ERR_CUDA;                                                       \
+    }                                                                             \
+  } while (0)
+
+#define SGOC_TRY(expr)                      \
+  do {                                      \
+    sgoc_status s_ = (expr);                \
+    if (s_ != SGOC_OK) return s_;           \
+  } while (0)
+
+// One level of the geometric hierarchy for the mean operator: a constant
+// 9-point stencil (centre, edge, corner) on an nx-element grid.
+struct Level {
+  int nx;        // elements per side
+  int n1;        // interior nodes per side = nx - 1
+  int64_t n;     // n1 * n1
+  double diag, edge, corner;
+};
+
+// Device pointers into the caller's persistent buffer.
+struct DevData {
+  double* kap64 = nullptr;     // (M+1) x nx x nx, kappa_k(e) / 6
+  float* kap32 = nullptr;
+  int* nbr_ptr = nullptr;      // CSR over output columns beta: P + 1
+  int* nbr_alpha = nullptr;    // neighbour column alpha = beta +- e_k
+  int* nbr_k = nullptr;        // KL index k (1..M)
+  double* nbr_c64 = nullptr;   // E[xi_k Psi_alpha Psi_beta]
+  float* nbr_c32 = nullptr;
+  double* yhat = nullptr;      // slabs x n target values
+  double* y0 = nullptr;        // n initial state (zeros when absent)
+};
+
+}  // namespace sgoc
+
+struct sgoc_problem {
+  // problem statement
+  int nx = 0, M = 0, p = 0, nt = 0;
+  double beta = 0, gamma = 0, T = 1, tau = 1, kappa0 = 1, s = 0;  // s = sqrt((1+gamma)/beta)
+  int n1 = 0, P = 0, slabs = 1;
+  int64_t n = 0, F = 0, N = 0;       // F = slabs * P * n, N = 3F
+  std::vector<double> kappa, yhat, y0;
+  sgoc_options opt{};
+  int r = 1;                         // truncation
+  // chaos basis
+  std::vector<int32_t> idx;          // P x M
+  std::vector<int> off;              // p + 2 level offsets
+  std::vector<int> nbr_ptr, nbr_alpha, nbr_k;
+  std::vector<double> nbr_c;
+  // multigrid hierarchy of the mean operator (level 0 = finest)
+  std::vector<sgoc::Level> levels;
+  double mass_h2_36 = 0;             // h^2 / 36 on the finest grid
+  std::vector<double> dweights;      // time weights D_t (1 when steady)
+  // device
+  sgoc::DevData dev;
+  bool uploaded = false;
+  size_t persistent_bytes = 0;
+};
+
+namespace sgoc {
+
+// Workspace needs for one precision (bytes), see solver.cu.
+size_t workspace_bytes(const sgoc_problem* pb, int precision);
+size_t precond_workspace_bytes(const sgoc_problem* pb, int esize);
+int level_columns_max(const sgoc_problem* pb);
+
+}  // namespace sgoc

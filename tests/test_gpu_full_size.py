@@ -1,0 +1,79 @@
+"""Full-size workloads in the launch configuration the benchmark times, against
+oracle results stored by tests/golden/make_golden.py (oracle only).
+
+Checks: float64 iteration count within +-1 of the oracle's, true residual <=
+1e-8, block norms within 1e-7 relative, sampled solution entries within
+1e-7 * ||x_oracle||_2 (implied by a 1e-7 relative 2-norm error); the mixed
+solve reaches the same 1e-8 float64 residual, and its distance to the float64
+GPU solution is bounded by 1e-6 relative.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import sg_inputs as si
+from oracle.operators import SGData
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "full_size_oracle.json")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_ready():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests selected but no CUDA device is visible")
+    from paper_2512_23804_gb300 import build
+    build.build()
+
+
+def golden():
+    if not os.path.exists(GOLD):
+        pytest.fail("tests/golden/full_size_oracle.json missing: run tests/golden/make_golden.py")
+    return json.load(open(GOLD))
+
+
+def workloads():
+    out = [("steady_128_beta%g" % b, (lambda b=b: si.steady_128(b))) for b in si.STEADY_128_BETAS]
+    out.append(("time_64", si.time_64))
+    return out
+
+
+@pytest.mark.parametrize("key,mk", workloads(), ids=[k for k, _ in workloads()])
+def test_full_size_fp64_and_mixed(key, mk):
+    from paper_2512_23804_gb300 import SGProblem
+    g = golden()
+    if key not in g:
+        pytest.fail(f"{key} missing from the golden file")
+    ref = g[key]
+    pr = mk()
+    sp = SGProblem.from_problem(pr)
+    x, info = sp.solve()
+    assert info["status_name"] == "SGOC_OK"
+    assert abs(info["iterations"] - ref["iterations"]) <= 1, (info["iterations"], ref["iterations"])
+    assert info["rel_true_residual"] <= 1e-8
+    xh = x.cpu().numpy()
+    F = pr.kkt_size // 3
+    for b in range(3):
+        nb = np.linalg.norm(xh[b * F:(b + 1) * F])
+        assert abs(nb - ref["block_norms"][b]) <= 1e-7 * ref["block_norms"][b]
+    xnorm = np.linalg.norm(ref["block_norms"])
+    idx = np.array(ref["sample_idx"])
+    assert np.max(np.abs(xh[idx] - np.array(ref["sample_val"]))) <= 1e-7 * xnorm
+    sp.release_workspace()
+
+    spm = SGProblem.from_problem(pr, precision="mixed")
+    xm, im = spm.solve()
+    assert im["status_name"] == "SGOC_OK"
+    assert im["rel_true_residual"] <= 1e-8
+    err = float(torch.linalg.norm(xm - x) / torch.linalg.norm(x))
+    assert err <= 1e-6, err
+    # independent residual check of the mixed solution with the oracle's operator
+    if pr.nt == 0:
+        d = SGData(pr)
+        xmh = xm.cpu().numpy()
+        r = np.linalg.norm(d.kkt_apply(xmh) - d.rhs()) / np.linalg.norm(d.rhs())
+        assert r <= 1.01e-8, r
