@@ -182,6 +182,20 @@ sgoc_status sgoc_apply_chebyshev(sgoc_problem* pb, int32_t precision, const void
                                  void* d_X, int32_t ncols, void* d_ws, size_t ws_bytes,
                                  void* stream);
 
+/* Same result as sgoc_apply_chebyshev, for callers that cannot allocate device
+ * memory when they need the solve (for instance code running while a CUDA graph
+ * is being captured, or a plug-in whose host framework owns all device memory):
+ * it takes no workspace.  Its two iterate buffers live in a 16 MiB array built
+ * into the library, which every GPU that loads the library keeps until the
+ * process exits; ncols * n * sizeof(element) must not exceed 8 MiB, larger
+ * requests return SGOC_ERR_INVALID_ARG.  The first call on a device looks up the
+ * array's device address with that device current; make that first call before
+ * any stream capture.  All calls share the array: calls whose kernels overlap on
+ * the GPU race and must be serialized by the caller.  Allocates nothing.
+ * The paper has no counterpart of this entry point. */
+sgoc_status sgoc_apply_chebyshev_noalloc(sgoc_problem* pb, int32_t precision, const void* d_R,
+                                         void* d_X, int32_t ncols, void* stream);
+
 /* The multi-index set, P x M int32 (host), graded by total degree and
  * lexicographically descending within a degree. */
 sgoc_status sgoc_pc_indices(const sgoc_problem* pb, int32_t* host_out);

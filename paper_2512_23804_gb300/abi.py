@@ -67,6 +67,7 @@ SIGNATURES = {
     "sgoc_apply_hgs": (ctypes.c_int, [_P, _I32, _P, _P, _I32, _P, _SZ, _P]),
     "sgoc_apply_vcycle": (ctypes.c_int, [_P, _I32, _P, _P, _I32, _P, _SZ, _P]),
     "sgoc_apply_chebyshev": (ctypes.c_int, [_P, _I32, _P, _P, _I32, _P, _SZ, _P]),
+    "sgoc_apply_chebyshev_noalloc": (ctypes.c_int, [_P, _I32, _P, _P, _I32, _P]),
     "sgoc_pc_indices": (ctypes.c_int, [_P, _PI32]),
     "sgoc_triple_products": (ctypes.c_int, [_P, _PI32, _PI32, _PI32, _PD, _PI64]),
     "sgoc_kernel_launches": (ctypes.c_int64, []),
