@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip fp64/e2e/profile/matvec legs")
+    ap.add_argument("--sequential", action="store_true", help="solve the batch one problem at a time")
     return ap.parse_args()
 
 
@@ -194,7 +195,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    from paper_2512_23804_gb300 import SGProblem, abi, build
+    from paper_2512_23804_gb300 import SGProblem, abi, build, solve_batch
     build.build()
     lib = abi.load()
     hbm_peak, peak_kind, _ = load_peaks()
@@ -208,15 +209,19 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step(record=None):
+    streams = [torch.cuda.Stream() for _ in sps]
+
+    def step_sequential():
         infos = []
         for sp, x in zip(sps, xs):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
             _, info = sp.solve(out=x)
-            e1.record(stream)
-            infos.append((info, e0, e1))
+            infos.append(info)
+        return infos
+
+    def step():
+        if args.sequential:
+            return step_sequential()
+        _, infos = solve_batch(sps, outs=xs, streams=streams)
         return infos
 
     for _ in range(args.warmup):
@@ -239,8 +244,8 @@ def run_ours(args):
         s1.record(stream)
         torch.cuda.synchronize()
         step_ms.append(s0.elapsed_time(s1))
-        for info, e0, e1 in infos:
-            solve_ms.append(e0.elapsed_time(e1))
+        for info in infos:
+            solve_ms.append(info["ms_total"])
             iters.append(info["iterations"])
             outer.append(info["outer_iterations"])
             resid.append(info["rel_true_residual"])
@@ -268,7 +273,8 @@ def run_ours(args):
                    "kkt_unknowns": sps[0].kkt_size,
                    "precision": ("float32 operator/preconditioner/inner MINRES, float64 refinement"
                                  if args.precision == "mixed" else "float64"),
-                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}",
+                   "batching": "sequential" if args.sequential else "3 concurrent solves (sgoc_solve_batch, 3 streams)"},
         "latency_ms": {"p50": float(sorted(solve_ms)[len(solve_ms) // 2]),
                        "p99": float(sorted(solve_ms)[min(len(solve_ms) - 1, math.ceil(0.99 * len(solve_ms)) - 1)])},
         "iterations": {"per_solve": iters[:3], "outer": outer[:3], "max_rel_residual": max(resid)},
@@ -277,6 +283,15 @@ def run_ours(args):
     }
 
     if not args.no_extras and rank == 0:
+        # the same three solves one after the other (no overlap), same precision
+        flush.fill_(1.0)
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        step_sequential()
+        q1.record(stream)
+        torch.cuda.synchronize()
+        line["sequential_solves_per_s"] = 3 / (q0.elapsed_time(q1) / 1e3)
         # plain float64 path (same solves), for the mixed-vs-fp64 comparison
         if args.precision == "mixed":
             sp64 = [SGProblem.from_problem(pr, precision="fp64").upload() for pr in problems]
@@ -319,7 +334,7 @@ def run_ours(args):
         # instrumented pass: per-kernel-class device time with CUDA events on the launching stream
         abi.profile_enable(True)
         flush.fill_(1.0)
-        step()
+        step_sequential()
         torch.cuda.synchronize()
         rep = abi.profile_report()
         abi.profile_enable(False)

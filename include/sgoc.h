@@ -146,6 +146,47 @@ sgoc_status sgoc_rhs(sgoc_problem* pb, double* d_b, void* stream);
 sgoc_status sgoc_solve(sgoc_problem* pb, void* d_ws, size_t ws_bytes, const double* d_x0,
                        double* d_x, void* stream, sgoc_result* res);
 
+/* Solve `count` distinct problems concurrently: problem i uses workspace d_ws[i]
+ * (ws_bytes[i]), initial guess d_x0[i] (d_x0 or its entries may be NULL),
+ * output d_x[i] and stream streams[i] (distinct streams let the solves overlap
+ * on the GPU).  The calling thread advances every unfinished solve by one unit of
+ * work per sweep (one MINRES iteration, a residual check or a refinement step),
+ * so all solves stay in flight together.  Results are identical to sgoc_solve of
+ * each problem alone.  res (nullable) receives count results; the return value is
+ * the first non-OK status (or OK).  Synchronizes every stream before returning. */
+sgoc_status sgoc_solve_batch(int32_t count, sgoc_problem* const* pbs, void* const* d_ws,
+                             const size_t* ws_bytes, const double* const* d_x0,
+                             double* const* d_x, void* const* streams, sgoc_result* res);
+
+/* ---- serving: continuous batching of solves over a caller-owned device pool ----
+ *
+ * A server owns no device memory of its own: requests are sub-allocated (first
+ * fit, 256-byte aligned) from d_pool, each needing its problem's persistent +
+ * workspace bytes.  sgoc_server_submit queues a request (the problem created
+ * with sgoc_problem_create, not necessarily uploaded; d_x receives the
+ * solution); sgoc_server_step admits queued requests in FIFO order while a slot
+ * and memory are free (uploading the problem into its pool block), advances
+ * every active solve whose previous unit of work has finished by one unit (one
+ * MINRES iteration, a residual check or a refinement step), retires finished
+ * solves (freeing their memory and slot) and admits again.  Each active solve
+ * runs on its own stream, so solves that arrived at different times overlap on
+ * the GPU.  sgoc_server_poll returns finished requests with their results;
+ * ms_total is then the latency from submission to completion.  A problem
+ * belongs to the server from submission until it is polled; its device data is
+ * released with its pool block (upload it again before using it elsewhere).
+ * Results are identical to sgoc_solve of the same problem alone. */
+typedef struct sgoc_server sgoc_server;
+sgoc_status sgoc_server_create(void* d_pool, size_t pool_bytes, int32_t max_active,
+                               sgoc_server** out);
+void sgoc_server_destroy(sgoc_server* sv);
+/* SGOC_ERR_WORKSPACE_TOO_SMALL when the request cannot fit even an empty pool. */
+sgoc_status sgoc_server_submit(sgoc_server* sv, sgoc_problem* pb, double* d_x, uint64_t request_id);
+sgoc_status sgoc_server_step(sgoc_server* sv, int32_t* n_active, int32_t* n_queued);
+sgoc_status sgoc_server_poll(sgoc_server* sv, uint64_t* ids, sgoc_result* res, int32_t cap,
+                             int32_t* n_done);
+sgoc_status sgoc_server_stats(const sgoc_server* sv, int64_t* admitted, int64_t* completed,
+                              int64_t* rejected, size_t* pool_high_water);
+
 /* ---- building blocks (used by tests and benchmarks) ---- */
 
 /* Y = sum_{k=0}^{M} K_k X G_k (Sec. 2, Eq. (Zv) with A_l in place of A~_l),

@@ -7,6 +7,6 @@ include/sgoc.h; `abi` binds it with ctypes and `SGProblem` manages device
 memory and streams through PyTorch.
 """
 from . import abi
-from .problem import SGProblem
+from .problem import SGProblem, SGServer, solve_batch
 
-__all__ = ["abi", "SGProblem"]
+__all__ = ["abi", "SGProblem", "SGServer", "solve_batch"]

@@ -61,6 +61,14 @@ SIGNATURES = {
     "sgoc_problem_upload": (ctypes.c_int, [_P, _P, _SZ, _P]),
     "sgoc_rhs": (ctypes.c_int, [_P, _P, _P]),
     "sgoc_solve": (ctypes.c_int, [_P, _P, _SZ, _P, _P, _P, ctypes.POINTER(Result)]),
+    "sgoc_solve_batch": (ctypes.c_int, [_I32, ctypes.POINTER(_P), ctypes.POINTER(_P), _PSZ, ctypes.POINTER(_P),
+                                        ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(Result)]),
+    "sgoc_server_create": (ctypes.c_int, [_P, _SZ, _I32, ctypes.POINTER(_P)]),
+    "sgoc_server_destroy": (None, [_P]),
+    "sgoc_server_submit": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint64]),
+    "sgoc_server_step": (ctypes.c_int, [_P, _PI32, _PI32]),
+    "sgoc_server_poll": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Result), _I32, _PI32]),
+    "sgoc_server_stats": (ctypes.c_int, [_P, _PI64, _PI64, _PI64, _PSZ]),
     "sgoc_apply_operator": (ctypes.c_int, [_P, _I32, _P, _P, _I32, _P]),
     "sgoc_apply_kkt": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
     "sgoc_apply_precond": (ctypes.c_int, [_P, _I32, _P, _P, _P, _SZ, _P]),

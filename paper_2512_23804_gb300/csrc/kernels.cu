@@ -18,6 +18,7 @@ namespace sgoc {
 static std::atomic<int64_t> g_launches{0};
 static inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 int64_t kernel_launches() { return g_launches.load(std::memory_order_relaxed); }
+void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // ---- optional per-kernel-class profiler (events pooled and reused) ----
 namespace {
@@ -44,6 +45,8 @@ const char* kKindNames[KK_COUNT] = {"sg_operator", "mass", "chebyshev", "mg_smoo
 }  // namespace
 
 const char* kernel_kind_name(int kind) { return (kind >= 0 && kind < KK_COUNT) ? kKindNames[kind] : "?"; }
+
+bool profile_enabled() { return prof().on; }
 
 void profile_enable(bool on) {
   Profiler& p = prof();
@@ -117,19 +120,36 @@ __device__ __forceinline__ T dot4(const typename Vec4<T>::type& a, const typenam
 //   phase 2: out(beta) = sum_e kappa_0(e) T_e(beta) + sum_{(alpha,k,c)} c sum_e kappa_k(e) T_e(alpha)
 // ---------------------------------------------------------------------------
 constexpr int kSGThreads = 256;
-constexpr int kSGChunk = 8;
+constexpr int kSGChunk = 16;     // input columns per asynchronous staging chunk
+
+// asynchronous global->shared copy of one element; invalid elements are zero-filled
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gsrc, bool valid) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  const int sz = valid ? int(sizeof(T)) : 0;
+  if (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gsrc), "r"(sz));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gsrc), "r"(sz));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 template <typename T, int TX>
 __global__ void __launch_bounds__(kSGThreads) sg_kernel(SGArgs<T> a) {
   using V4 = typename Vec4<T>::type;
   extern __shared__ __align__(32) unsigned char sg_smem_raw[];
-  unsigned char* smem_raw = sg_smem_raw;
+  constexpr int W = TX + 2;
   const int nin = a.in1 - a.in0;
   const int nout = a.out1 - a.out0;
-  V4* Ts = reinterpret_cast<V4*>(smem_raw);                   // [nin][TX]
+  V4* Ts = reinterpret_cast<V4*>(sg_smem_raw);               // [nin][TX]
   V4* Ks = Ts + size_t(nin) * TX;                            // [M+1][TX]
   T* Ms = reinterpret_cast<T*>(Ks + size_t(a.M + 1) * TX);   // [nout][TX]
-  T* Xs = Ms + size_t(nout) * TX;                            // [kSGChunk][3][TX+2]
+  T* Xs = Ms + (a.cm != T(0) ? size_t(nout) * TX : 0);       // [2][kSGChunk][3][W]
+  T* Cs = Xs + size_t(2) * kSGChunk * 3 * W;                 // neighbour coefficients [nnz_out]
+  int* Es = reinterpret_cast<int*>(Cs + a.nnz_out);          // packed (alpha - in0) | k << 20
+  int* Ps = Es + a.nnz_out;                                  // [nout + 1] local CSR
 
   const int ix0 = blockIdx.x * TX;
   const int iy = blockIdx.y;
@@ -137,8 +157,24 @@ __global__ void __launch_bounds__(kSGThreads) sg_kernel(SGArgs<T> a) {
   const int tid = threadIdx.x;
   const int n1 = a.n1;
   const T* X = a.X + int64_t(t) * a.xs;
+  const int nchunks = (nin + kSGChunk - 1) / kSGChunk;
 
-  // phase 0: element coefficients
+  auto issue = [&](int ch) {
+    const int c0 = a.in0 + ch * kSGChunk;
+    const int nc = min(kSGChunk, a.in1 - c0);
+    T* dst = Xs + size_t(ch & 1) * kSGChunk * 3 * W;
+    for (int q = tid; q < nc * 3 * W; q += kSGThreads) {
+      const int c = q / (3 * W), rem = q % (3 * W), dy = rem / W, lx = rem % W;
+      const int gx = ix0 + lx - 1, gy = iy + dy - 1;
+      const bool ok = gx >= 0 && gx < n1 && gy >= 0 && gy < n1;
+      const T* col = X + int64_t(c0 + c) * a.n;
+      cp_async_elem(dst + q, ok ? col + (int64_t(gy) * n1 + gx) : col, ok);
+    }
+    cp_async_commit();
+  };
+  issue(0);
+
+  // phase 0: element coefficients and the local neighbour table (overlaps the first copies)
   for (int q = tid; q < (a.M + 1) * TX; q += kSGThreads) {
     const int k = q / TX, lx = q % TX;
     const int ix = min(ix0 + lx, n1 - 1);
@@ -150,20 +186,23 @@ __global__ void __launch_bounds__(kSGThreads) sg_kernel(SGArgs<T> a) {
     v.w = kk[int64_t(iy + 1) * a.nx + ix];        // NW element (ix, iy+1)
     Ks[k * TX + lx] = v;
   }
+  const int ebase = a.nbr_ptr[a.out0];
+  for (int q = tid; q <= nout; q += kSGThreads) Ps[q] = a.nbr_ptr[a.out0 + q] - ebase;
+  for (int q = tid; q < a.nnz_out; q += kSGThreads) {
+    Cs[q] = a.nbr_c[ebase + q];
+    Es[q] = (a.nbr_alpha[ebase + q] - a.in0) | (a.nbr_k[ebase + q] << 20);
+  }
 
-  // phase 1: element terms of all input columns
-  constexpr int W = TX + 2;
-  for (int c0 = a.in0; c0 < a.in1; c0 += kSGChunk) {
-    const int nc = min(kSGChunk, a.in1 - c0);
-    for (int q = tid; q < nc * 3 * W; q += kSGThreads) {
-      const int c = q / (3 * W), rem = q % (3 * W), dy = rem / W, lx = rem % W;
-      const int gx = ix0 + lx - 1, gy = iy + dy - 1;
-      Xs[q] = ldz(X + int64_t(c0 + c) * a.n, gx, gy, n1);
-    }
+  // phase 1: element terms T_e of every input column (double-buffered chunks)
+  for (int ch = 0; ch < nchunks; ++ch) {
+    if (ch + 1 < nchunks) { issue(ch + 1); cp_async_wait<1>(); } else { cp_async_wait<0>(); }
     __syncthreads();
+    const int c0 = a.in0 + ch * kSGChunk;
+    const int nc = min(kSGChunk, a.in1 - c0);
+    const T* src = Xs + size_t(ch & 1) * kSGChunk * 3 * W;
     for (int q = tid; q < nc * TX; q += kSGThreads) {
       const int c = q / TX, lx = q % TX;
-      const T* s = Xs + c * 3 * W + lx;   // s[dy*W + dx], dx,dy in 0..2 (1 = centre)
+      const T* s = src + c * 3 * W + lx;   // s[dy*W + dx], dx,dy in 0..2 (1 = centre)
       const T SW = s[0], S = s[1], SE = s[2];
       const T Wv = s[W], C = s[W + 1], E = s[W + 2];
       const T NW = s[2 * W], N = s[2 * W + 1], NE = s[2 * W + 2];
@@ -176,7 +215,7 @@ __global__ void __launch_bounds__(kSGThreads) sg_kernel(SGArgs<T> a) {
       v.w = fma(T(-2), NW, aN - Wv);
       const int col = c0 + c;
       Ts[size_t(col - a.in0) * TX + lx] = v;
-      if (col >= a.out0 && col < a.out1) {
+      if (a.cm != T(0) && col >= a.out0 && col < a.out1) {
         const T edges = (N + S) + (E + Wv);
         const T corners = (NE + NW) + (SE + SW);
         Ms[size_t(col - a.out0) * TX + lx] = a.mass * fma(T(16), C, fma(T(4), edges, corners));
@@ -185,23 +224,26 @@ __global__ void __launch_bounds__(kSGThreads) sg_kernel(SGArgs<T> a) {
     __syncthreads();
   }
 
-  // phase 2: contraction with the triple products
+  // phase 2: contraction with the triple products (warp-uniform output column when TX = 32)
+  const int kmax = a.kmax;
   for (int q = tid; q < nout * TX; q += kSGThreads) {
-    const int lx = q % TX, beta = a.out0 + q / TX;
+    const int lx = q % TX, bl = q / TX;
     const int ix = ix0 + lx;
-    if (ix >= n1) continue;
+    const int beta = a.out0 + bl;
     const V4 tb = Ts[size_t(beta - a.in0) * TX + lx];
-    const T diag = dot4<T>(Ks[lx], tb);
+    T diag = dot4<T>(Ks[lx], tb);
     T off = T(0);
-    const int e1 = a.nbr_ptr[beta + 1];
-    for (int e = a.nbr_ptr[beta]; e < e1; ++e) {
-      const int k = a.nbr_k[e];
-      if (k >= a.kmax) break;                        // table is sorted by k
-      const int al = a.nbr_alpha[e];
-      off = fma(a.nbr_c[e], dot4<T>(Ks[k * TX + lx], Ts[size_t(al - a.in0) * TX + lx]), off);
+    const int e1 = Ps[bl + 1];
+    for (int e = Ps[bl]; e < e1; ++e) {
+      const int pk = Es[e];
+      const int k = pk >> 20;
+      if (k >= kmax) break;                          // table is sorted by k
+      const int al = pk & 0xFFFFF;
+      off = fma(Cs[e], dot4<T>(Ks[k * TX + lx], Ts[size_t(al) * TX + lx]), off);
     }
+    if (ix >= n1) continue;
     T out = a.c0 * diag + a.c1 * off;
-    if (a.cm != T(0)) out = fma(a.cm, Ms[size_t(beta - a.out0) * TX + lx], out);
+    if (a.cm != T(0)) out = fma(a.cm, Ms[size_t(bl) * TX + lx], out);
     const int64_t node = int64_t(iy) * n1 + ix;
     if (a.R) out = fma(a.cr, a.R[int64_t(t) * a.rs + int64_t(beta - a.rcol0) * a.n + node], out);
     T* yp = a.Y + int64_t(t) * a.ys + int64_t(beta - a.ycol0) * a.n + node;
@@ -214,7 +256,9 @@ template <typename T, int TX>
 static size_t sg_smem(const SGArgs<T>& a) {
   using V4 = typename Vec4<T>::type;
   return sizeof(V4) * (size_t(a.in1 - a.in0) * TX + size_t(a.M + 1) * TX) +
-         sizeof(T) * (size_t(a.out1 - a.out0) * TX + size_t(kSGChunk) * 3 * (TX + 2));
+         sizeof(T) * ((a.cm != T(0) ? size_t(a.out1 - a.out0) * TX : 0) + size_t(2) * kSGChunk * 3 * (TX + 2) +
+                      a.nnz_out) +
+         sizeof(int) * (size_t(a.nnz_out) + (a.out1 - a.out0) + 1);
 }
 
 template <typename T, int TX>
@@ -534,111 +578,160 @@ cudaError_t launch_scale(const T* b, T* x, int64_t cnt, T a, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// Fused coarse V-cycle: one CTA per column, all levels in shared memory.
-// Level l arrays x_l, b_l; the residual is formed on the fly in the restriction.
-// Jacobi sweeps update in place through registers (read all, barrier, write all).
+// Full-hierarchy V-cycle, one CTA per column (1024 threads, levels in shared
+// memory).  The finest right-hand side b_0 is read from global memory (it is the
+// output of the preceding kernel and sits in L2); x_l, r_l (all levels) and b_l
+// (coarse levels) live in shared memory.  Jacobi sweeps are register-blocked:
+// each thread owns a vertical strip of up to kStripRows points of one grid
+// column and slides a 3x3 window down it (3 shared loads per point).
 // ---------------------------------------------------------------------------
-constexpr int kFusedThreads = 512;
-constexpr int kFusedPts = 8;                 // points per thread per sweep (registers)
+constexpr int kVFThreads = 1024;
+constexpr int kStripRows = 16;
 
-int fused_vcycle_max_n1(int esize) {
-  // largest n1 = 2^j - 1 whose level arrays (x, b on every level) fit in shared memory
-  // and whose sweeps fit kFusedThreads * kFusedPts points per pass
-  int best = 1;
-  for (int n1 = 1; n1 <= 4095; n1 = 2 * n1 + 1) {
-    size_t tot = 0;
-    for (int m = n1; m >= 1; m = (m - 1) / 2) tot += size_t(m) * m * 2 * esize;
-    if (tot <= 200 * 1024 && int64_t(n1) * n1 <= int64_t(kFusedThreads) * kFusedPts) best = n1;
-  }
-  return best;
+template <typename T>
+struct StripGeom {
+  int x, y0, y1;   // column and row range [y0, y1) of this thread; x < 0: idle
+};
+
+template <typename T>
+__device__ __forceinline__ StripGeom<T> strip_of(int n1) {
+  StripGeom<T> g;
+  const int nchunks = (n1 + kStripRows - 1) / kStripRows;
+  const int rows = (n1 + nchunks - 1) / nchunks;
+  const int t = threadIdx.x;
+  const int chunk = t / n1;
+  g.x = (chunk < nchunks) ? t % n1 : -1;
+  g.y0 = chunk * rows;
+  g.y1 = min(n1, g.y0 + rows);
+  return g;
 }
 
 template <typename T>
-__device__ void fused_smooth(T* x, const T* b, int n1, T d, T e, T c, T omega, bool from_zero) {
-  const int n = n1 * n1;
-  T nv[kFusedPts];
+__device__ __forceinline__ T ldrow(const T* X, int x, int y, int n1) {
+  return (y >= 0 && y < n1 && x >= 0 && x < n1) ? X[y * n1 + x] : T(0);
+}
+
+// One damped-Jacobi sweep x <- x + omega/d (b - A x) in place (from_zero: x <- omega/d b).
+// b may be in global or shared memory.  Contains the barriers.
+template <typename T>
+__device__ void strip_sweep(T* x, const T* b, int n1, T d, T e, T c, T omega, bool from_zero) {
+  const StripGeom<T> g = strip_of<T>(n1);
+  T nv[kStripRows];
   const T wd = omega / d;
+  if (g.x >= 0) {
+    if (from_zero) {
 #pragma unroll
-  for (int j = 0; j < kFusedPts; ++j) {
-    const int q = threadIdx.x + j * kFusedThreads;
-    if (q < n) {
-      if (from_zero) {
-        nv[j] = wd * b[q];
-      } else {
-        const int ix = q % n1, iy = q / n1;
-        nv[j] = fma(wd, b[q] - stencil_apply(x, ix, iy, n1, d, e, c), x[q]);
+      for (int j = 0; j < kStripRows; ++j) {
+        const int y = g.y0 + j;
+        if (y < g.y1) nv[j] = wd * b[y * n1 + g.x];
+      }
+    } else {
+      const int xm = g.x - 1, xp = g.x + 1;
+      T wm0 = ldrow(x, xm, g.y0 - 1, n1), wc0 = ldrow(x, g.x, g.y0 - 1, n1), wp0 = ldrow(x, xp, g.y0 - 1, n1);
+      T wm1 = ldrow(x, xm, g.y0, n1), wc1 = ldrow(x, g.x, g.y0, n1), wp1 = ldrow(x, xp, g.y0, n1);
+#pragma unroll
+      for (int j = 0; j < kStripRows; ++j) {
+        const int y = g.y0 + j;
+        if (y < g.y1) {
+          const T wm2 = ldrow(x, xm, y + 1, n1), wc2 = ldrow(x, g.x, y + 1, n1), wp2 = ldrow(x, xp, y + 1, n1);
+          const T edges = (wc0 + wc2) + (wm1 + wp1);
+          const T corners = (wm0 + wp0) + (wm2 + wp2);
+          const T ax = fma(d, wc1, fma(e, edges, c * corners));
+          nv[j] = fma(wd, b[y * n1 + g.x] - ax, wc1);
+          wm0 = wm1; wc0 = wc1; wp0 = wp1;
+          wm1 = wm2; wc1 = wc2; wp1 = wp2;
+        }
       }
     }
   }
   __syncthreads();
+  if (g.x >= 0) {
 #pragma unroll
-  for (int j = 0; j < kFusedPts; ++j) {
-    const int q = threadIdx.x + j * kFusedThreads;
-    if (q < n) x[q] = nv[j];
+    for (int j = 0; j < kStripRows; ++j) {
+      const int y = g.y0 + j;
+      if (y < g.y1) x[y * n1 + g.x] = nv[j];
+    }
   }
   __syncthreads();
 }
 
+// r <- b - A x (register-blocked, no barrier inside; caller syncs)
 template <typename T>
-__global__ void __launch_bounds__(kFusedThreads) vcycle_fused_kernel(const T* __restrict__ bg, T* xg, FusedLevels L, T omega,
-                                                                     int nu, T* acc, int64_t acc_ss, int acc_L,
-                                                                     int acc_col0) {
-  extern __shared__ __align__(32) unsigned char vc_smem_raw[];
-  T* base = reinterpret_cast<T*>(vc_smem_raw);
+__device__ void strip_residual(const T* x, const T* b, T* r, int n1, T d, T e, T c) {
+  const StripGeom<T> g = strip_of<T>(n1);
+  if (g.x < 0) return;
+  const int xm = g.x - 1, xp = g.x + 1;
+  T wm0 = ldrow(x, xm, g.y0 - 1, n1), wc0 = ldrow(x, g.x, g.y0 - 1, n1), wp0 = ldrow(x, xp, g.y0 - 1, n1);
+  T wm1 = ldrow(x, xm, g.y0, n1), wc1 = ldrow(x, g.x, g.y0, n1), wp1 = ldrow(x, xp, g.y0, n1);
+  for (int y = g.y0; y < g.y1; ++y) {
+    const T wm2 = ldrow(x, xm, y + 1, n1), wc2 = ldrow(x, g.x, y + 1, n1), wp2 = ldrow(x, xp, y + 1, n1);
+    const T edges = (wc0 + wc2) + (wm1 + wp1);
+    const T corners = (wm0 + wp0) + (wm2 + wp2);
+    r[y * n1 + g.x] = b[y * n1 + g.x] - fma(d, wc1, fma(e, edges, c * corners));
+    wm0 = wm1; wc0 = wc1; wp0 = wp1;
+    wm1 = wm2; wc1 = wc2; wp1 = wp2;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kVFThreads, 1) vcycle_full_kernel(const T* __restrict__ bg, T* xg, FusedLevels L,
+                                                                    T omega, int nu, T* acc, int64_t acc_ss,
+                                                                    int acc_L, int acc_col0) {
+  extern __shared__ __align__(32) unsigned char vf_smem_raw[];
+  T* base = reinterpret_cast<T*>(vf_smem_raw);
+  // layout: for each level l: x_l, r_l, and b_l for l >= 1
   T* xs[13];
+  T* rs[13];
   T* bs[13];
   {
     size_t o = 0;
+#pragma unroll 1
     for (int l = 0; l < L.nlev; ++l) {
       const int n = L.n1[l] * L.n1[l];
       xs[l] = base + o; o += n;
-      bs[l] = base + o; o += n;
+      rs[l] = base + o; o += n;
+      if (l > 0) { bs[l] = base + o; o += n; } else { bs[l] = nullptr; }
     }
   }
   const int64_t col = blockIdx.x;
   const int n0 = L.n1[0] * L.n1[0];
-  for (int q = threadIdx.x; q < n0; q += kFusedThreads) bs[0][q] = bg[col * n0 + q];
-  __syncthreads();
-  // descend
+  const T* b0 = bg + col * n0;
+  bs[0] = const_cast<T*>(b0);
+#pragma unroll 1
   for (int l = 0; l < L.nlev - 1; ++l) {
-    const int n1 = L.n1[l];
+    const int n1 = L.n1[l], n1c = L.n1[l + 1];
     const T d = T(L.diag[l]), e = T(L.edge[l]), c = T(L.corner[l]);
-    for (int s = 0; s < nu; ++s) fused_smooth(xs[l], bs[l], n1, d, e, c, omega, s == 0);
+#pragma unroll 1
+    for (int s = 0; s < nu; ++s) strip_sweep(xs[l], bs[l], n1, d, e, c, omega, s == 0);
     if (nu == 0) {
-      for (int q = threadIdx.x; q < n1 * n1; q += kFusedThreads) xs[l][q] = T(0);
+      for (int q = threadIdx.x; q < n1 * n1; q += kVFThreads) xs[l][q] = T(0);
       __syncthreads();
     }
-    // restriction of the residual b - A x
-    const int n1c = L.n1[l + 1];
-    for (int q = threadIdx.x; q < n1c * n1c; q += kFusedThreads) {
+    strip_residual(xs[l], bs[l], rs[l], n1, d, e, c);
+    __syncthreads();
+    const T* R = rs[l];
+    for (int q = threadIdx.x; q < n1c * n1c; q += kVFThreads) {
       const int I = q % n1c, J = q / n1c;
       const int fx = 2 * I + 1, fy = 2 * J + 1;
-      T acc_r = T(0);
-#pragma unroll
-      for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int ix = fx + dx, iy = fy + dy;
-          const T w = (dx == 0 ? T(1) : T(0.5)) * (dy == 0 ? T(1) : T(0.5));
-          const T rr = bs[l][iy * n1 + ix] - stencil_apply(xs[l], ix, iy, n1, d, e, c);
-          acc_r = fma(w, rr, acc_r);
-        }
-      bs[l + 1][q] = acc_r;
+      const T cen = R[fy * n1 + fx];
+      const T edg = (R[(fy + 1) * n1 + fx] + R[(fy - 1) * n1 + fx]) + (R[fy * n1 + fx + 1] + R[fy * n1 + fx - 1]);
+      const T cor = (R[(fy + 1) * n1 + fx + 1] + R[(fy + 1) * n1 + fx - 1]) +
+                    (R[(fy - 1) * n1 + fx + 1] + R[(fy - 1) * n1 + fx - 1]);
+      bs[l + 1][q] = cen + T(0.5) * edg + T(0.25) * cor;
     }
     __syncthreads();
   }
-  // coarsest: a single node
   {
     const int l = L.nlev - 1;
     const int n = L.n1[l] * L.n1[l];
-    for (int q = threadIdx.x; q < n; q += kFusedThreads) xs[l][q] = bs[l][q] / T(L.diag[l]);
+    for (int q = threadIdx.x; q < n; q += kVFThreads) xs[l][q] = bs[l][q] / T(L.diag[l]);
     __syncthreads();
   }
-  // ascend
+#pragma unroll 1
   for (int l = L.nlev - 2; l >= 0; --l) {
     const int n1 = L.n1[l], n1c = L.n1[l + 1];
     const T* X = xs[l + 1];
-    for (int q = threadIdx.x; q < n1 * n1; q += kFusedThreads) {
+    for (int q = threadIdx.x; q < n1 * n1; q += kVFThreads) {
       const int gi = q % n1 + 1, gj = q / n1 + 1;
       T v;
       if ((gi & 1) == 0 && (gj & 1) == 0) {
@@ -655,9 +748,10 @@ __global__ void __launch_bounds__(kFusedThreads) vcycle_fused_kernel(const T* __
     }
     __syncthreads();
     const T d = T(L.diag[l]), e = T(L.edge[l]), c = T(L.corner[l]);
-    for (int s = 0; s < nu; ++s) fused_smooth(xs[l], bs[l], n1, d, e, c, omega, false);
+#pragma unroll 1
+    for (int s = 0; s < nu; ++s) strip_sweep(xs[l], bs[l], n1, d, e, c, omega, false);
   }
-  for (int q = threadIdx.x; q < n0; q += kFusedThreads) {
+  for (int q = threadIdx.x; q < n0; q += kVFThreads) {
     if (acc) {
       const int64_t t = col / acc_L, cc = col % acc_L;
       acc[t * acc_ss + (acc_col0 + cc) * int64_t(n0) + q] += xs[0][q];
@@ -667,20 +761,30 @@ __global__ void __launch_bounds__(kFusedThreads) vcycle_fused_kernel(const T* __
   }
 }
 
+size_t vcycle_full_smem(const FusedLevels& L, int esize) {
+  size_t s = 0;
+  for (int l = 0; l < L.nlev; ++l) s += size_t(L.n1[l]) * L.n1[l] * (l > 0 ? 3 : 2) * esize;
+  return s;
+}
+
+bool vcycle_full_fits(const FusedLevels& L, int esize) {
+  const int n1 = L.n1[0];
+  const int nchunks = (n1 + kStripRows - 1) / kStripRows;
+  return int64_t(nchunks) * n1 <= kVFThreads && vcycle_full_smem(L, esize) <= kMaxSmem;
+}
+
 template <typename T>
-cudaError_t launch_vcycle_fused(const T* b, T* x, int64_t B, const FusedLevels& L, T omega, int nu, T* acc,
-                                int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st) {
+cudaError_t launch_vcycle_full(const T* b, T* x, int64_t B, const FusedLevels& L, T omega, int nu, T* acc,
+                               int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st) {
   if (B == 0) return cudaSuccess;
-  size_t smem = 0;
-  for (int l = 0; l < L.nlev; ++l) smem += size_t(L.n1[l]) * L.n1[l] * 2 * sizeof(T);
-  if (int64_t(L.n1[0]) * L.n1[0] > int64_t(kFusedThreads) * kFusedPts || smem > kMaxSmem)
-    return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(vcycle_fused_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (!vcycle_full_fits(L, sizeof(T))) return cudaErrorInvalidConfiguration;
+  const size_t smem = vcycle_full_smem(L, sizeof(T));
+  cudaError_t e = cudaFuncSetAttribute(vcycle_full_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   const double n0 = double(L.n1[0]) * L.n1[0];
   ProfScope ps(KK_VCYCLE_FUSED, st, double(sizeof(T)) * B * n0 * (acc ? 3 : 2),
-               double(B) * n0 * (4.0 / 3.0) * (21.0 * 2 * nu + 18.0 * 9 / 4 + 10.0));
-  vcycle_fused_kernel<T><<<dim3(unsigned(B)), kFusedThreads, smem, st>>>(b, x, L, omega, nu, acc, acc_ss, acc_L, acc_col0);
+               double(B) * n0 * (4.0 / 3.0) * (21.0 * 2 * nu + 18.0 + 10.0));
+  vcycle_full_kernel<T><<<dim3(unsigned(B)), kVFThreads, smem, st>>>(b, x, L, omega, nu, acc, acc_ss, acc_L, acc_col0);
   note_launch();
   return cudaGetLastError();
 }
@@ -952,8 +1056,8 @@ cudaError_t launch_fill(T* x, int64_t n, T v, cudaStream_t st) {
   template cudaError_t launch_restrict<T>(const T*, T*, int64_t, int, cudaStream_t);                               \
   template cudaError_t launch_prolong_add<T>(const T*, T*, int64_t, int, cudaStream_t);                            \
   template cudaError_t launch_scale<T>(const T*, T*, int64_t, T, cudaStream_t);                                    \
-  template cudaError_t launch_vcycle_fused<T>(const T*, T*, int64_t, const FusedLevels&, T, int, T*, int64_t, int, \
-                                              int, cudaStream_t);                                                  \
+  template cudaError_t launch_vcycle_full<T>(const T*, T*, int64_t, const FusedLevels&, T, int, T*, int64_t, int,  \
+                                             int, cudaStream_t);                                                   \
   template cudaError_t launch_dot_partial<T>(const T*, const T*, int64_t, double*, cudaStream_t);                  \
   template cudaError_t launch_minres_v<T>(const T*, const T*, T*, int64_t, const MinresState*, cudaStream_t);      \
   template cudaError_t launch_add_to<T>(const T*, double*, int64_t, cudaStream_t);                                 \

@@ -8,6 +8,8 @@ namespace sgoc {
 
 // Number of kernels this library has launched in the process (all streams).
 int64_t kernel_launches();
+void add_launches(int64_t n);
+bool profile_enabled();
 
 // Optional per-kernel-class timing: when enabled, every launch is bracketed by
 // CUDA events on its stream and its algorithmic bytes/flops are recorded.
@@ -41,6 +43,7 @@ struct SGArgs {
   const T* kap;                 // kappa_k(e)/6, (M+1) x nx x nx
   const int* nbr_ptr; const int* nbr_alpha; const int* nbr_k; const T* nbr_c;
   double deg_sum;               // number of (beta, neighbour) pairs used (work accounting only)
+  int nnz_out;                  // neighbour-table entries of the output columns (all k)
 };
 template <typename T>
 cudaError_t launch_sg(const SGArgs<T>& a, cudaStream_t st);
@@ -89,13 +92,15 @@ cudaError_t launch_prolong_add(const T* xc, T* xf, int64_t B, int n1f, cudaStrea
 template <typename T>
 cudaError_t launch_scale(const T* b, T* x, int64_t cnt, T a, cudaStream_t st);
 
-// Fused V-cycle of the coarse part of the hierarchy, one CTA per column:
-// levels lv[0] (finest handled, n1 = lv_n1[0]) down to a single node.
+// Levels handled by the one-CTA-per-column V-cycle: L.n1[0] (finest handled)
+// down to a single node, with their 9-point stencils.
 struct FusedLevels { int nlev; int n1[13]; double diag[13], edge[13], corner[13]; };
+// Full-hierarchy V-cycle (top level read from global memory, register-blocked
+// sweeps, 1024 threads): usable when vcycle_full_fits(L, sizeof(T)).
+bool vcycle_full_fits(const FusedLevels& L, int esize);
 template <typename T>
-cudaError_t launch_vcycle_fused(const T* b, T* x, int64_t B, const FusedLevels& L, T omega, int nu,
-                                T* acc, int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st);
-int fused_vcycle_max_n1(int esize);
+cudaError_t launch_vcycle_full(const T* b, T* x, int64_t B, const FusedLevels& L, T omega, int nu,
+                               T* acc, int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st);
 
 // Krylov kernels.  Reductions are deterministic: fixed grid, fixed order.
 constexpr int kDotBlocks = 608;

@@ -220,7 +220,11 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
   return SGOC_OK;
 }
 
-void sgoc_problem_destroy(sgoc_problem* pb) { delete pb; }
+void sgoc_problem_destroy(sgoc_problem* pb) {
+  if (!pb) return;
+  release_runtime(pb);
+  delete pb;
+}
 
 sgoc_status sgoc_problem_sizes(const sgoc_problem* pb, int64_t* n, int64_t* P, int64_t* slabs,
                                int64_t* kkt) {
@@ -244,6 +248,7 @@ sgoc_status sgoc_problem_upload(sgoc_problem* pb, void* d_persistent, size_t byt
   if (bytes < pb->persistent_bytes) { set_error("persistent buffer too small"); return SGOC_ERR_WORKSPACE_TOO_SMALL; }
   if (reinterpret_cast<uintptr_t>(d_persistent) % 256) { set_error("persistent buffer must be 256-byte aligned"); return SGOC_ERR_INVALID_ARG; }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  invalidate_graphs(pb);
   const int M = pb->M;
   const size_t nel = size_t(pb->nx) * pb->nx, nk = size_t(M + 1) * nel;
   const size_t nnz = pb->nbr_alpha.size();

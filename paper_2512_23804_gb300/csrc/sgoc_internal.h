@@ -75,6 +75,7 @@ struct sgoc_problem {
   sgoc::DevData dev;
   bool uploaded = false;
   size_t persistent_bytes = 0;
+  void* runtime = nullptr;           // host-side solve resources (solver.cu)
 };
 
 namespace sgoc {
@@ -83,5 +84,8 @@ namespace sgoc {
 size_t workspace_bytes(const sgoc_problem* pb, int precision);
 size_t precond_workspace_bytes(const sgoc_problem* pb, int esize);
 int level_columns_max(const sgoc_problem* pb);
+void release_runtime(sgoc_problem* pb);
+// Captured graphs refer to device addresses of the problem data: drop them on re-upload.
+void invalidate_graphs(sgoc_problem* pb);
 
 }  // namespace sgoc

@@ -5,6 +5,9 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <deque>
+#include <iterator>
+#include <map>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -42,13 +45,12 @@ struct Carver {
   bool ok() const { return dry || off <= cap; }
 };
 
-// Largest finest level handled by the fused one-CTA-per-column V-cycle.
-static int fused_n1_limit(int esize) {
-  const int lim = fused_vcycle_max_n1(esize);
-  // float64 runs at a small fraction of the float32 rate on this GPU: keep
-  // one-SM-per-column work small there and use grid-wide level kernels above.
-  return esize == 8 ? (lim < 15 ? lim : 15) : lim;
-}
+// Largest finest level handled by the one-CTA-per-column V-cycle kernel.
+// float32: the whole hierarchy up to 127 x 127 interior nodes fits one CTA's
+// shared memory.  float64 runs at 1/64 of the float32 rate on this GPU, so a
+// single SM per column would be too slow there: grid-wide level kernels above
+// 15 x 15 spread the fine levels over all SMs.
+static int fused_n1_limit(int esize) { return esize == 8 ? 15 : 127; }
 
 int level_columns_max(const sgoc_problem* pb) {
   int m = 1;
@@ -112,8 +114,9 @@ static sgoc_status vcycle(const sgoc_problem* pb, PrecWS<T>& w, const T* b, T* x
     FL.n1[l - lf] = pb->levels[l].n1;
     FL.diag[l - lf] = pb->levels[l].diag; FL.edge[l - lf] = pb->levels[l].edge; FL.corner[l - lf] = pb->levels[l].corner;
   }
+  if (!vcycle_full_fits(FL, sizeof(T))) { set_error("internal: V-cycle level does not fit"); return SGOC_ERR_UNSUPPORTED; }
   if (lf == 0) {
-    SGOC_LAUNCH(launch_vcycle_fused<T>(b, xout, B, FL, om, nu, acc, acc_ss, acc_L, acc_col0, st));
+    SGOC_LAUNCH(launch_vcycle_full<T>(b, xout, B, FL, om, nu, acc, acc_ss, acc_L, acc_col0, st));
     return SGOC_OK;
   }
   // level-wise descent down to lf
@@ -138,7 +141,7 @@ static sgoc_status vcycle(const sgoc_problem* pb, PrecWS<T>& w, const T* b, T* x
     bl[l + 1] = w.lb[l + 1];
     xcur[l] = cur; spare[l] = sp;
   }
-  SGOC_LAUNCH(launch_vcycle_fused<T>(bl[lf], w.lx[lf], B, FL, om, nu, (T*)nullptr, 0, 1, 0, st));
+  SGOC_LAUNCH(launch_vcycle_full<T>(bl[lf], w.lx[lf], B, FL, om, nu, (T*)nullptr, 0, 1, 0, st));
   T* xc = w.lx[lf];
   for (int l = lf - 1; l >= 0; --l) {
     const Level& L = pb->levels[l];
@@ -205,6 +208,7 @@ static sgoc_status hgs(const sgoc_problem* pb, PrecWS<T>& w, const T* R, T* V, i
     g.kap = kap_of<T>(pb);
     g.nbr_ptr = pb->dev.nbr_ptr; g.nbr_alpha = pb->dev.nbr_alpha; g.nbr_k = pb->dev.nbr_k; g.nbr_c = nbrc_of<T>(pb);
     g.deg_sum = deg_sum(pb, a0, a1, pb->r);
+    g.nnz_out = pb->nbr_ptr[a1] - pb->nbr_ptr[a0];
     SGOC_LAUNCH(launch_sg<T>(g, st));
     SGOC_TRY(vcycle<T>(pb, w, w.RH, nullptr, int64_t(slabs) * L, V, ps, L, a0, st));
   }
@@ -226,6 +230,7 @@ static SGArgs<T> sg_full(const sgoc_problem* pb, const T* X, T* Y, T coef) {
   g.kap = kap_of<T>(pb);
   g.nbr_ptr = pb->dev.nbr_ptr; g.nbr_alpha = pb->dev.nbr_alpha; g.nbr_k = pb->dev.nbr_k; g.nbr_c = nbrc_of<T>(pb);
   g.deg_sum = double(pb->nbr_alpha.size());
+  g.nnz_out = int(pb->nbr_alpha.size());
   return g;
 }
 
@@ -303,12 +308,21 @@ static sgoc_status precond_apply(const sgoc_problem* pb, PrecWS<T>& w, const T* 
 
 // ------------------------------------------------------------------ MINRES --
 struct KrylovWS64 {
-  double *b, *r, *t;                      // float64 rhs, residual, product
+  double *b, *r, *t, *x;                  // float64 rhs, residual, product, iterate
   double* partial; double* scal; MinresState* state;
 };
 
 template <typename T>
 struct MinresVecs { T *vp, *v, *z, *zn, *Kz, *wm1, *wm2; };
+
+// Buffer roles of the next iteration: v_{j+1} was written into vp, z_{j+1} into
+// zn and w_j into wm2, so the roles swap with period two.
+template <typename T>
+static MinresVecs<T> swapped(const MinresVecs<T>& m) {
+  MinresVecs<T> s = m;
+  s.vp = m.v; s.v = m.vp; s.z = m.zn; s.zn = m.z; s.wm1 = m.wm2; s.wm2 = m.wm1;
+  return s;
+}
 
 template <typename T>
 static void carve_minres(const sgoc_problem* pb, Carver& c, MinresVecs<T>& m) {
@@ -334,6 +348,7 @@ static size_t carve_layout(const sgoc_problem* pb, int precision, void* base, si
   L.k64.b = c.take<double>(N);
   L.k64.r = c.take<double>(N);
   L.k64.t = c.take<double>(N);
+  L.k64.x = c.take<double>(N);
   L.k64.partial = c.take<double>(kDotBlocks);
   L.k64.scal = c.take<double>(16);
   L.k64.state = c.take<MinresState>(1);
@@ -357,85 +372,151 @@ size_t workspace_bytes(const sgoc_problem* pb, int precision) {
 template <typename T> static PrecWS<T>& prec_of(Layout& L);
 template <> PrecWS<double>& prec_of<double>(Layout& L) { return L.p64; }
 template <> PrecWS<float>& prec_of<float>(Layout& L) { return L.p32; }
+template <typename T> static MinresVecs<T>& vecs_of(Layout& L);
+template <> MinresVecs<double>& vecs_of<double>(Layout& L) { return L.m64; }
+template <> MinresVecs<float>& vecs_of<float>(Layout& L) { return L.m32; }
 
-static sgoc_status read_state(const MinresState* d, MinresState* h, cudaStream_t st) {
-  SGOC_CUDA_TRY(cudaMemcpyAsync(h, d, sizeof(MinresState), cudaMemcpyDeviceToHost, st));
+// Host-side resources of a problem's solves: pinned mirrors of the device
+// scalars, a private capture stream and the captured MINRES iteration graphs.
+struct Runtime {
+  MinresState* hstate = nullptr;
+  double* hscal = nullptr;
+  cudaStream_t cap = nullptr;
+  const void* ws = nullptr;
+  int prec = -1;
+  cudaGraphExec_t it[2] = {nullptr, nullptr};
+  int64_t nk[2] = {0, 0};
+  cudaEvent_t ev = nullptr;            // completion of the pending unit of a solve
+  void drop_graphs() {
+    for (auto& g : it) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    ws = nullptr; prec = -1;
+  }
+  ~Runtime() {
+    drop_graphs();
+    if (cap) cudaStreamDestroy(cap);
+    if (ev) cudaEventDestroy(ev);
+    if (hstate) cudaFreeHost(hstate);
+    if (hscal) cudaFreeHost(hscal);
+  }
+};
+
+void invalidate_graphs(sgoc_problem* pb) {
+  if (pb->runtime) static_cast<Runtime*>(pb->runtime)->drop_graphs();
+}
+
+void release_runtime(sgoc_problem* pb) {
+  delete static_cast<Runtime*>(pb->runtime);
+  pb->runtime = nullptr;
+}
+
+static sgoc_status runtime_of(sgoc_problem* pb, Runtime** out) {
+  if (!pb->runtime) {
+    auto* rt = new Runtime();
+    pb->runtime = rt;
+    SGOC_CUDA_TRY(cudaMallocHost(&rt->hstate, sizeof(MinresState)));
+    SGOC_CUDA_TRY(cudaMallocHost(&rt->hscal, 16 * sizeof(double)));
+    SGOC_CUDA_TRY(cudaStreamCreateWithFlags(&rt->cap, cudaStreamNonBlocking));
+    SGOC_CUDA_TRY(cudaEventCreateWithFlags(&rt->ev, cudaEventDisableTiming));
+  }
+  *out = static_cast<Runtime*>(pb->runtime);
+  return SGOC_OK;
+}
+
+static sgoc_status sync_state(Runtime& rt, const Layout& L, cudaStream_t st) {
+  SGOC_CUDA_TRY(cudaMemcpyAsync(rt.hstate, L.k64.state, sizeof(MinresState), cudaMemcpyDeviceToHost, st));
   SGOC_CUDA_TRY(cudaStreamSynchronize(st));
   return SGOC_OK;
 }
 
-static sgoc_status norm2(const double* a, int64_t n, double* partial, double* scal_dev, double* out,
-                         cudaStream_t st) {
-  SGOC_LAUNCH(launch_dot_partial<double>(a, a, n, partial, st));
-  SGOC_LAUNCH(launch_sum_partials(partial, scal_dev, st));
-  double h = 0;
-  SGOC_CUDA_TRY(cudaMemcpyAsync(&h, scal_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+static sgoc_status norm2(Runtime& rt, const double* a, int64_t n, const Layout& L, double* out, cudaStream_t st) {
+  SGOC_LAUNCH(launch_dot_partial<double>(a, a, n, L.k64.partial, st));
+  SGOC_LAUNCH(launch_sum_partials(L.k64.partial, L.k64.scal, st));
+  SGOC_CUDA_TRY(cudaMemcpyAsync(rt.hscal, L.k64.scal, sizeof(double), cudaMemcpyDeviceToHost, st));
   SGOC_CUDA_TRY(cudaStreamSynchronize(st));
-  *out = std::sqrt(h);
+  *out = std::sqrt(rt.hscal[0]);
   return SGOC_OK;
 }
 
-// Preconditioned MINRES on K d = rhs (vectors of type T, float64 scalars); the
-// iterate accumulates into x.  Stopping: estimate <= target; when `check` is set
-// the true float64 residual ||b64 - K x||/||b64|| decides (rule of the oracle).
+// MINRES start: v_1 = rhs, z_1 = P^{-1} v_1, beta_1 = sqrt(v_1 . z_1), w = 0.
 template <typename T>
-static sgoc_status minres(const sgoc_problem* pb, Layout& L, MinresVecs<T>& m, const T* rhs, T* x,
-                          double tol, int max_iter, bool check_true, double bnorm, cudaStream_t st,
-                          int* iters, double* est_out, double* rel_out) {
+static sgoc_status minres_start(const sgoc_problem* pb, Layout& L, const MinresVecs<T>& m, const T* rhs,
+                                double target, cudaStream_t st) {
   const int64_t N = pb->N;
-  PrecWS<T>& pw = prec_of<T>(L);
-  MinresState hs{};
-  double target = tol;
-  *iters = 0;
-  // v_1 = rhs, z_1 = P^{-1} v_1
   SGOC_LAUNCH(launch_scale<T>(rhs, m.v, N, T(1), st));
-  SGOC_TRY(precond_apply<T>(pb, pw, m.v, m.z, st));
+  SGOC_TRY(precond_apply<T>(pb, prec_of<T>(L), m.v, m.z, st));
   SGOC_LAUNCH(launch_dot_partial<T>(m.v, m.z, N, L.k64.partial, st));
   SGOC_LAUNCH(launch_minres_init(L.k64.state, L.k64.partial, target, st));
   SGOC_LAUNCH(launch_fill<T>(m.wm1, N, T(0), st));
   SGOC_LAUNCH(launch_fill<T>(m.wm2, N, T(0), st));
-  SGOC_TRY(read_state(L.k64.state, &hs, st));
-  if (hs.flag == 3) { set_error("<v, P^-1 v> <= 0 at start"); return SGOC_ERR_NOT_SPD; }
-  if (hs.flag == 4) { set_error("NaN at start"); return SGOC_ERR_NAN; }
-  double rel = 1.0;
-  for (int j = 1; j <= max_iter; ++j) {
-    SGOC_TRY(kkt_apply<T>(pb, m.z, m.Kz, st));
-    SGOC_LAUNCH(launch_dot_partial<T>(m.z, m.Kz, N, L.k64.partial, st));
-    SGOC_LAUNCH(launch_minres_alpha(L.k64.state, L.k64.partial, st));
-    SGOC_LAUNCH(launch_minres_v<T>(m.Kz, m.v, m.vp, N, L.k64.state, st));   // vp <- v_{j+1}
-    SGOC_TRY(precond_apply<T>(pb, pw, m.vp, m.zn, st));
-    SGOC_LAUNCH(launch_dot_partial<T>(m.vp, m.zn, N, L.k64.partial, st));
-    SGOC_LAUNCH(launch_minres_rotate(L.k64.state, L.k64.partial, st));
-    SGOC_LAUNCH(launch_minres_wx<T, T>(m.z, m.wm1, m.wm2, x, N, L.k64.state, st));  // wm2 <- w_j
-    std::swap(m.vp, m.v);     // v <- v_{j+1}, vp <- v_j
-    std::swap(m.z, m.zn);
-    std::swap(m.wm1, m.wm2);  // wm1 <- w_j, wm2 <- w_{j-1}
-    SGOC_TRY(read_state(L.k64.state, &hs, st));
-    *iters = j;
-    *est_out = hs.est;
-    if (hs.flag == 4) { set_error("NaN in MINRES recurrences"); return SGOC_ERR_NAN; }
-    if (hs.flag == 3) { set_error("preconditioner not positive definite"); return SGOC_ERR_NOT_SPD; }
-    if (hs.flag == 1 || hs.flag == 2) {
-      if (!check_true) return SGOC_OK;
-      // true float64 residual of the outer system (only used with float64 iterates)
-      double rn = 0;
-      if constexpr (std::is_same<T, double>::value) {
-        SGOC_TRY(kkt_apply<double>(pb, x, L.k64.t, st));
-        SGOC_LAUNCH(launch_sub(L.k64.b, L.k64.t, L.k64.r, N, st));
-        SGOC_TRY(norm2(L.k64.r, N, L.k64.partial, L.k64.scal, &rn, st));
-      }
-      rel = rn / bnorm;
-      *rel_out = rel;
-      if (rel <= pb->opt.tol || hs.flag == 2) return SGOC_OK;
-      target *= pb->opt.tol / rel;
-      const int zero = 0;
-      SGOC_CUDA_TRY(cudaMemcpyAsync(&L.k64.state->target, &target, sizeof(double), cudaMemcpyHostToDevice, st));
-      SGOC_CUDA_TRY(cudaMemcpyAsync(&L.k64.state->flag, &zero, sizeof(int), cudaMemcpyHostToDevice, st));
-      SGOC_CUDA_TRY(cudaStreamSynchronize(st));
+  return SGOC_OK;
+}
+
+// One MINRES iteration with fixed buffer roles (see swapped()).
+template <typename T, typename TX>
+static sgoc_status minres_step(const sgoc_problem* pb, Layout& L, const MinresVecs<T>& m, TX* x, cudaStream_t st) {
+  const int64_t N = pb->N;
+  SGOC_TRY(kkt_apply<T>(pb, m.z, m.Kz, st));
+  SGOC_LAUNCH(launch_dot_partial<T>(m.z, m.Kz, N, L.k64.partial, st));
+  SGOC_LAUNCH(launch_minres_alpha(L.k64.state, L.k64.partial, st));
+  SGOC_LAUNCH(launch_minres_v<T>(m.Kz, m.v, m.vp, N, L.k64.state, st));
+  SGOC_TRY(precond_apply<T>(pb, prec_of<T>(L), m.vp, m.zn, st));
+  SGOC_LAUNCH(launch_dot_partial<T>(m.vp, m.zn, N, L.k64.partial, st));
+  SGOC_LAUNCH(launch_minres_rotate(L.k64.state, L.k64.partial, st));
+  SGOC_LAUNCH(launch_minres_wx<T, TX>(m.z, m.wm1, m.wm2, x, N, L.k64.state, st));
+  return SGOC_OK;
+}
+
+// Capture both parities of the iteration (plus the copy of the scalar state to
+// the pinned host mirror) into executable graphs, once per workspace.
+template <typename T, typename TX>
+static sgoc_status ensure_graphs(sgoc_problem* pb, Runtime& rt, Layout& L, const void* ws, TX* x) {
+  const int prec = std::is_same<T, double>::value ? 0 : 1;
+  if (rt.ws == ws && rt.prec == prec && rt.it[0] && rt.it[1]) return SGOC_OK;
+  rt.drop_graphs();
+  MinresVecs<T> m = vecs_of<T>(L);
+  for (int par = 0; par < 2; ++par) {
+    const MinresVecs<T> mp = par == 0 ? m : swapped(m);
+    const int64_t k0 = kernel_launches();
+    SGOC_CUDA_TRY(cudaStreamBeginCapture(rt.cap, cudaStreamCaptureModeRelaxed));
+    sgoc_status s = minres_step<T, TX>(pb, L, mp, x, rt.cap);
+    cudaError_t ce = cudaMemcpyAsync(rt.hstate, L.k64.state, sizeof(MinresState), cudaMemcpyDeviceToHost, rt.cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(rt.cap, &g);
+    const int64_t nk = kernel_launches() - k0;
+    add_launches(-nk);                      // counted when the graph runs
+    if (s != SGOC_OK) { if (g) cudaGraphDestroy(g); return s; }
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_status(ce != cudaSuccess ? ce : ee, "iteration graph capture");
     }
+    cudaError_t ie = cudaGraphInstantiate(&rt.it[par], g, 0);
+    cudaGraphDestroy(g);
+    SGOC_TRY(cuda_status(ie, "cudaGraphInstantiate"));
+    rt.nk[par] = nk;
   }
-  set_error("MINRES iteration limit reached");
-  return SGOC_ERR_NO_CONVERGENCE;
+  rt.ws = ws;
+  rt.prec = prec;
+  return SGOC_OK;
+}
+
+// Run one iteration of parity `par` on `st` and bring the scalar state to the host.
+template <typename T, typename TX>
+static sgoc_status run_step(sgoc_problem* pb, Runtime& rt, Layout& L, bool graphs, int par, TX* x, cudaStream_t st) {
+  if (graphs) {
+    SGOC_CUDA_TRY(cudaGraphLaunch(rt.it[par], st));
+    add_launches(rt.nk[par]);
+    SGOC_CUDA_TRY(cudaStreamSynchronize(st));
+    return SGOC_OK;
+  }
+  const MinresVecs<T>& m = vecs_of<T>(L);
+  SGOC_TRY((minres_step<T, TX>(pb, L, par == 0 ? m : swapped(m), x, st)));
+  return sync_state(rt, L, st);
+}
+
+static sgoc_status state_error(const MinresState& hs) {
+  if (hs.flag == 4) { set_error("NaN in MINRES recurrences"); return SGOC_ERR_NAN; }
+  if (hs.flag == 3) { set_error("preconditioner not positive definite"); return SGOC_ERR_NOT_SPD; }
+  return SGOC_OK;
 }
 
 static sgoc_status rhs_apply(const sgoc_problem* pb, double* b, cudaStream_t st) {
@@ -468,70 +549,412 @@ static sgoc_status check_ws(void* ws, size_t bytes, size_t need) {
   return SGOC_OK;
 }
 
-static sgoc_status solve_impl(sgoc_problem* pb, void* d_ws, size_t ws_bytes, const double* d_x0, double* d_x,
-                              cudaStream_t st, sgoc_result* res) {
-  Layout L;
-  const int prec = pb->opt.precision;
-  carve_layout(pb, prec, d_ws, ws_bytes, L);
-  const int64_t N = pb->N;
-  SGOC_TRY(rhs_apply(pb, L.k64.b, st));
-  double bnorm = 0;
-  SGOC_TRY(norm2(L.k64.b, N, L.k64.partial, L.k64.scal, &bnorm, st));
-  if (res) { res->iterations = 0; res->outer_iterations = 0; res->rel_true_residual = 0; res->rel_estimate = 0; }
-  if (d_x0) SGOC_CUDA_TRY(cudaMemcpyAsync(d_x, d_x0, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  else SGOC_LAUNCH(launch_fill<double>(d_x, N, 0.0, st));
-  if (bnorm == 0.0) { SGOC_LAUNCH(launch_fill<double>(d_x, N, 0.0, st)); SGOC_CUDA_TRY(cudaStreamSynchronize(st)); return SGOC_OK; }
-  if (!std::isfinite(bnorm)) { set_error("non-finite right-hand side"); return SGOC_ERR_NAN; }
+// true float64 residual r = b - K x and its relative norm
+static sgoc_status true_residual(sgoc_problem* pb, Runtime& rt, const Layout& L, double bnorm, double* rel,
+                                 double* rn, cudaStream_t st) {
+  SGOC_TRY(kkt_apply<double>(pb, L.k64.x, L.k64.t, st));
+  SGOC_LAUNCH(launch_sub(L.k64.b, L.k64.t, L.k64.r, pb->N, st));
+  SGOC_TRY(norm2(rt, L.k64.r, pb->N, L, rn, st));
+  *rel = *rn / bnorm;
+  return SGOC_OK;
+}
 
-  if (prec == SGOC_FP64) {
-    // r0 = b - K x0; the stopping rule is relative to b, so with an initial guess
-    // the estimate target is rescaled by ||b|| / ||r0|| (2-norms) and the true
-    // residual decides at exit
-    const double* rhs = L.k64.b;
-    double target = pb->opt.tol;
-    if (d_x0) {
-      SGOC_TRY(kkt_apply<double>(pb, d_x, L.k64.t, st));
-      SGOC_LAUNCH(launch_sub(L.k64.b, L.k64.t, L.k64.r, N, st));
-      double rn0 = 0;
-      SGOC_TRY(norm2(L.k64.r, N, L.k64.partial, L.k64.scal, &rn0, st));
-      if (res) { res->iterations = 0; res->outer_iterations = 0; res->rel_true_residual = rn0 / bnorm; }
-      if (rn0 / bnorm <= pb->opt.tol) return SGOC_OK;
-      target = std::min(0.5, pb->opt.tol * bnorm / rn0);
-      rhs = L.k64.r;
+// A solve in progress, as a resumable state machine.  begin() enqueues the first
+// unit of device work; every unit ends by copying the scalars the host needs
+// (norms or the MINRES state) to pinned host memory and recording `ev`.  After
+// `ev` has completed, step() reads those scalars, takes the decision of the
+// stopping rule and enqueues the next unit.  One host thread can thus keep many
+// solves in flight on their own streams (sgoc_solve_batch, the server).
+struct SolveTask {
+  enum Phase { BNORM, R0, START64, ITER64, CHECK64, OUTER, START32, ITER32, DONE };
+  sgoc_problem* pb = nullptr;
+  Runtime* rt = nullptr;
+  Layout L;
+  cudaStream_t st = nullptr;
+  void* ws = nullptr;
+  const double* x0 = nullptr;
+  double* x_out = nullptr;
+  bool graphs = true;
+  Phase phase = DONE;
+  double bnorm = 0, target = 0, rn = 0;
+  int j = 0, jin = 0, par = 0, outer = 0, total = 0, last_flag = 0;
+  sgoc_status status = SGOC_OK;
+  sgoc_result result{};
+  std::chrono::steady_clock::time_point t0;
+
+  sgoc_status record() { SGOC_CUDA_TRY(cudaEventRecord(rt->ev, st)); return SGOC_OK; }
+
+  sgoc_status launch_norm(const double* a) {
+    SGOC_LAUNCH(launch_dot_partial<double>(a, a, pb->N, L.k64.partial, st));
+    SGOC_LAUNCH(launch_sum_partials(L.k64.partial, L.k64.scal, st));
+    SGOC_CUDA_TRY(cudaMemcpyAsync(rt->hscal, L.k64.scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+    return record();
+  }
+  sgoc_status launch_true_residual() {
+    SGOC_TRY(kkt_apply<double>(pb, L.k64.x, L.k64.t, st));
+    SGOC_LAUNCH(launch_sub(L.k64.b, L.k64.t, L.k64.r, pb->N, st));
+    return launch_norm(L.k64.r);
+  }
+  template <typename T, typename TX>
+  sgoc_status launch_start(const T* rhs, double tgt) {
+    SGOC_TRY(minres_start<T>(pb, L, vecs_of<T>(L), rhs, tgt, st));
+    SGOC_CUDA_TRY(cudaMemcpyAsync(rt->hstate, L.k64.state, sizeof(MinresState), cudaMemcpyDeviceToHost, st));
+    par = 0;
+    return record();
+  }
+  template <typename T, typename TX>
+  sgoc_status launch_iter(TX* x) {
+    if (graphs) {
+      SGOC_CUDA_TRY(cudaGraphLaunch(rt->it[par], st));
+      add_launches(rt->nk[par]);
+    } else {
+      const MinresVecs<T>& m = vecs_of<T>(L);
+      SGOC_TRY((minres_step<T, TX>(pb, L, par == 0 ? m : swapped(m), x, st)));
+      SGOC_CUDA_TRY(cudaMemcpyAsync(rt->hstate, L.k64.state, sizeof(MinresState), cudaMemcpyDeviceToHost, st));
     }
-    int it = 0; double est = 1, rel = 1;
-    sgoc_status s = minres<double>(pb, L, L.m64, rhs, d_x, target, pb->opt.max_iter, true, bnorm, st, &it,
-                                   &est, &rel);
-    if (res) { res->iterations = it; res->outer_iterations = 1; res->rel_estimate = est; res->rel_true_residual = rel; }
+    par ^= 1;
+    return record();
+  }
+  sgoc_status finish(sgoc_status s) {
+    status = s;
+    phase = DONE;
+    cudaError_t e = cudaMemcpyAsync(x_out, L.k64.x, pb->N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (status == SGOC_OK && e != cudaSuccess) status = cuda_status(e, "copy solution");
+    result.status = status;
+    return status;
+  }
+  sgoc_status fail(sgoc_status s) {
+    status = s;
+    phase = DONE;
+    result.status = s;
     return s;
   }
-  // mixed: float32 inner MINRES inside float64 iterative refinement
-  int total = 0;
-  double rel = 1, est = 1;
-  for (int k = 0; k < pb->opt.max_outer; ++k) {
-    SGOC_TRY(kkt_apply<double>(pb, d_x, L.k64.t, st));
-    SGOC_LAUNCH(launch_sub(L.k64.b, L.k64.t, L.k64.r, N, st));
-    double rn = 0;
-    SGOC_TRY(norm2(L.k64.r, N, L.k64.partial, L.k64.scal, &rn, st));
-    rel = rn / bnorm;
-    if (res) { res->outer_iterations = k; res->rel_true_residual = rel; res->iterations = total; }
-    if (!std::isfinite(rel)) { set_error("non-finite residual in refinement"); return SGOC_ERR_NAN; }
-    if (rel <= pb->opt.tol) return SGOC_OK;
-    // unit-norm residual in float32, inner solve K c = r / ||r||, then x += ||r|| c
-    SGOC_LAUNCH(launch_scale_to32(L.k64.r, L.rhs32, N, 1.0 / rn, st));
-    SGOC_LAUNCH(launch_fill<float>(L.c32, N, 0.0f, st));
-    int it = 0;
-    double unused = 0;
-    sgoc_status s = minres<float>(pb, L, L.m32, L.rhs32, L.c32, pb->opt.inner_tol, pb->opt.max_iter, false, 1.0,
-                                  st, &it, &est, &unused);
-    total += it;
-    if (s != SGOC_OK && s != SGOC_ERR_NO_CONVERGENCE) return s;
-    SGOC_LAUNCH(launch_add_scaled(L.c32, d_x, N, rn, st));
-    if (res) { res->iterations = total; res->rel_estimate = est; res->outer_iterations = k + 1; }
+
+  sgoc_status begin(sgoc_problem* p, void* d_ws, size_t ws_bytes, const double* d_x0, double* d_x, cudaStream_t s) {
+    t0 = std::chrono::steady_clock::now();
+    pb = p; ws = d_ws; x0 = d_x0; x_out = d_x; st = s;
+    result = sgoc_result{};
+    carve_layout(pb, pb->opt.precision, d_ws, ws_bytes, L);
+    SGOC_TRY(runtime_of(pb, &rt));
+    graphs = !profile_enabled();
+    if (graphs) {
+      if (pb->opt.precision == SGOC_FP64) SGOC_TRY((ensure_graphs<double, double>(pb, *rt, L, ws, L.k64.x)));
+      else SGOC_TRY((ensure_graphs<float, float>(pb, *rt, L, ws, L.c32)));
+    }
+    SGOC_TRY(rhs_apply(pb, L.k64.b, st));
+    phase = BNORM;
+    return launch_norm(L.k64.b);
   }
-  set_error("iterative refinement step limit reached");
-  return SGOC_ERR_NO_CONVERGENCE;
+
+  // Consume the completed unit and enqueue the next one.
+  sgoc_status step() {
+    const double tol = pb->opt.tol;
+    const int64_t N = pb->N;
+    switch (phase) {
+      case BNORM: {
+        bnorm = std::sqrt(rt->hscal[0]);
+        if (bnorm == 0.0) { SGOC_LAUNCH(launch_fill<double>(L.k64.x, N, 0.0, st)); return finish(SGOC_OK); }
+        if (!std::isfinite(bnorm)) { set_error("non-finite right-hand side"); return fail(SGOC_ERR_NAN); }
+        if (x0) SGOC_CUDA_TRY(cudaMemcpyAsync(L.k64.x, x0, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        else SGOC_LAUNCH(launch_fill<double>(L.k64.x, N, 0.0, st));
+        if (pb->opt.precision != SGOC_FP64) { phase = OUTER; return launch_true_residual(); }
+        if (x0) { phase = R0; return launch_true_residual(); }
+        target = tol;
+        phase = START64;
+        return launch_start<double, double>(L.k64.b, target);
+      }
+      case R0: {
+        // the stopping rule is relative to b: with an initial guess the estimate target
+        // is rescaled by ||b|| / ||r0|| (2-norms) and the true residual decides at exit
+        const double rn0 = std::sqrt(rt->hscal[0]);
+        result.rel_true_residual = rn0 / bnorm;
+        if (rn0 / bnorm <= tol) return finish(SGOC_OK);
+        target = std::min(0.5, tol * bnorm / rn0);
+        phase = START64;
+        return launch_start<double, double>(L.k64.r, target);
+      }
+      case START64:
+      case START32: {
+        sgoc_status e = state_error(*rt->hstate);
+        if (e != SGOC_OK) return fail(e);
+        jin = 0;
+        phase = phase == START64 ? ITER64 : ITER32;
+        if (phase == ITER64) return launch_iter<double, double>(L.k64.x);
+        return launch_iter<float, float>(L.c32);
+      }
+      case ITER64: {
+        const MinresState hs = *rt->hstate;
+        ++j;
+        result.iterations = j; result.outer_iterations = 1; result.rel_estimate = hs.est;
+        sgoc_status e = state_error(hs);
+        if (e != SGOC_OK) return fail(e);
+        if (hs.flag == 1 || hs.flag == 2) { last_flag = hs.flag; phase = CHECK64; return launch_true_residual(); }
+        if (j >= pb->opt.max_iter) { set_error("MINRES iteration limit reached"); return finish(SGOC_ERR_NO_CONVERGENCE); }
+        return launch_iter<double, double>(L.k64.x);
+      }
+      case CHECK64: {
+        const double rel = std::sqrt(rt->hscal[0]) / bnorm;
+        result.rel_true_residual = rel;
+        if (rel <= tol || last_flag == 2) return finish(SGOC_OK);
+        if (j >= pb->opt.max_iter) { set_error("MINRES iteration limit reached"); return finish(SGOC_ERR_NO_CONVERGENCE); }
+        target *= tol / rel;
+        rt->hstate->target = target;
+        rt->hstate->flag = 0;
+        SGOC_CUDA_TRY(cudaMemcpyAsync(&L.k64.state->target, &rt->hstate->target, sizeof(double),
+                                      cudaMemcpyHostToDevice, st));
+        SGOC_CUDA_TRY(cudaMemcpyAsync(&L.k64.state->flag, &rt->hstate->flag, sizeof(int), cudaMemcpyHostToDevice, st));
+        phase = ITER64;
+        return launch_iter<double, double>(L.k64.x);
+      }
+      case OUTER: {
+        rn = std::sqrt(rt->hscal[0]);
+        const double rel = rn / bnorm;
+        result.rel_true_residual = rel; result.outer_iterations = outer; result.iterations = total;
+        if (!std::isfinite(rel)) { set_error("non-finite residual in refinement"); return fail(SGOC_ERR_NAN); }
+        if (rel <= tol) return finish(SGOC_OK);
+        if (outer >= pb->opt.max_outer) { set_error("iterative refinement step limit reached"); return finish(SGOC_ERR_NO_CONVERGENCE); }
+        // unit-norm residual in float32, inner solve K c = r / ||r||, then x += ||r|| c
+        SGOC_LAUNCH(launch_scale_to32(L.k64.r, L.rhs32, N, 1.0 / rn, st));
+        SGOC_LAUNCH(launch_fill<float>(L.c32, N, 0.0f, st));
+        phase = START32;
+        return launch_start<float, float>(L.rhs32, pb->opt.inner_tol);
+      }
+      case ITER32: {
+        const MinresState hs = *rt->hstate;
+        ++jin; ++total;
+        result.rel_estimate = hs.est; result.iterations = total;
+        sgoc_status e = state_error(hs);
+        if (e != SGOC_OK) return fail(e);
+        if (hs.flag == 1 || hs.flag == 2 || jin >= pb->opt.max_iter) {
+          SGOC_LAUNCH(launch_add_scaled(L.c32, L.k64.x, N, rn, st));
+          ++outer;
+          phase = OUTER;
+          return launch_true_residual();
+        }
+        return launch_iter<float, float>(L.c32);
+      }
+      case DONE:
+        return status;
+    }
+    return status;
+  }
+
+  // wait for the pending unit (host blocks) and advance
+  sgoc_status wait_and_step() {
+    cudaError_t e = cudaEventSynchronize(rt->ev);
+    if (e != cudaSuccess) return fail(cuda_status(e, "cudaEventSynchronize"));
+    sgoc_status s = step();
+    if (s != SGOC_OK && phase != DONE) return fail(s);
+    return s;
+  }
+};
+
+// ----------------------------------------------------------------- server --
+// First-fit sub-allocator over the caller's device pool (offsets, 256-B aligned).
+class PoolAllocator {
+ public:
+  explicit PoolAllocator(size_t bytes) { free_[0] = bytes; }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = align256(bytes);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes;
+        const size_t start = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[start] = rest;
+        used_ += bytes;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = align256(bytes);
+    used_ -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) { it->second += nx->second; free_.erase(nx); }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) { pv->second += it->second; free_.erase(it); }
+    }
+  }
+  size_t used() const { return used_; }
+
+ private:
+  std::map<size_t, size_t> free_;
+  size_t used_ = 0;
+};
+
+struct ServerRequest {
+  sgoc_problem* pb;
+  double* d_x;
+  uint64_t id;
+  std::chrono::steady_clock::time_point t_submit;
+};
+
+struct ServerSlot {
+  bool busy = false;
+  cudaStream_t st = nullptr;
+  SolveTask task;
+  ServerRequest req{};
+  size_t off = 0, bytes = 0, pers = 0;
+  std::chrono::steady_clock::time_point t_admit;
+};
+
+}  // namespace sgoc
+
+struct sgoc_server {
+  char* pool = nullptr;
+  size_t pool_bytes = 0;
+  sgoc::PoolAllocator alloc{0};
+  std::vector<sgoc::ServerSlot> slots;
+  std::deque<sgoc::ServerRequest> queue;
+  std::vector<std::pair<uint64_t, sgoc_result>> done;
+  int64_t admitted = 0, completed = 0, rejected = 0;
+  size_t high_water = 0;
+};
+
+namespace sgoc {
+
+static sgoc_status server_admit(sgoc_server* sv) {
+  while (!sv->queue.empty()) {
+    ServerSlot* slot = nullptr;
+    for (auto& s : sv->slots) if (!s.busy) { slot = &s; break; }
+    if (!slot) return SGOC_OK;
+    ServerRequest& rq = sv->queue.front();
+    const size_t pers = align256(rq.pb->persistent_bytes);
+    const size_t need = pers + workspace_bytes(rq.pb, rq.pb->opt.precision);
+    size_t off = 0;
+    if (!sv->alloc.alloc(need, &off)) return SGOC_OK;     // FIFO: wait for memory
+    slot->busy = true;
+    slot->req = rq;
+    slot->off = off; slot->bytes = need; slot->pers = pers;
+    slot->t_admit = std::chrono::steady_clock::now();
+    sv->queue.pop_front();
+    sv->admitted++;
+    sv->high_water = std::max(sv->high_water, sv->alloc.used());
+    char* base = sv->pool + off;
+    sgoc_status s = sgoc_problem_upload(slot->req.pb, base, pers, slot->st);
+    if (s == SGOC_OK) s = slot->task.begin(slot->req.pb, base + pers, need - pers, nullptr, slot->req.d_x, slot->st);
+    if (s != SGOC_OK) slot->task.fail(s);
+  }
+  return SGOC_OK;
 }
+
+static void server_retire(sgoc_server* sv, ServerSlot& slot) {
+  cudaStreamSynchronize(slot.st);
+  sgoc_result r = slot.task.result;
+  r.status = slot.task.status;
+  r.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - slot.req.t_submit).count();
+  sv->done.emplace_back(slot.req.id, r);
+  sv->alloc.release(slot.off, slot.bytes);
+  slot.req.pb->uploaded = false;           // its device data lived in the pool
+  slot.busy = false;
+  sv->completed++;
+}
+
+}  // namespace sgoc
+
+extern "C" {
+
+sgoc_status sgoc_server_create(void* d_pool, size_t pool_bytes, int32_t max_active, sgoc_server** out) {
+  using namespace sgoc;
+  if (!out || !d_pool || pool_bytes < 256 || max_active < 1 || max_active > 1024 ||
+      reinterpret_cast<uintptr_t>(d_pool) % 256) {
+    set_error("server: pool must be non-null, >= 256 bytes and 256-byte aligned; 1 <= max_active <= 1024");
+    return SGOC_ERR_INVALID_ARG;
+  }
+  auto* sv = new sgoc_server();
+  sv->pool = static_cast<char*>(d_pool);
+  sv->pool_bytes = pool_bytes;
+  sv->alloc = PoolAllocator(pool_bytes);
+  sv->slots.resize(max_active);
+  for (auto& s : sv->slots) {
+    cudaError_t e = cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { sgoc_server_destroy(sv); return cuda_status(e, "server stream"); }
+  }
+  *out = sv;
+  return SGOC_OK;
+}
+
+void sgoc_server_destroy(sgoc_server* sv) {
+  if (!sv) return;
+  for (auto& s : sv->slots) {
+    if (s.st) { cudaStreamSynchronize(s.st); cudaStreamDestroy(s.st); }
+    if (s.busy) s.req.pb->uploaded = false;
+  }
+  delete sv;
+}
+
+sgoc_status sgoc_server_submit(sgoc_server* sv, sgoc_problem* pb, double* d_x, uint64_t request_id) {
+  using namespace sgoc;
+  if (!sv || !pb || !d_x) { set_error("server submit: null argument"); return SGOC_ERR_INVALID_ARG; }
+  const size_t need = align256(pb->persistent_bytes) + workspace_bytes(pb, pb->opt.precision);
+  if (need > sv->pool_bytes) {
+    sv->rejected++;
+    set_error("server submit: request needs " + std::to_string(need) + " bytes, more than the whole pool");
+    return SGOC_ERR_WORKSPACE_TOO_SMALL;
+  }
+  sv->queue.push_back(ServerRequest{pb, d_x, request_id, std::chrono::steady_clock::now()});
+  return SGOC_OK;
+}
+
+sgoc_status sgoc_server_step(sgoc_server* sv, int32_t* n_active, int32_t* n_queued) {
+  using namespace sgoc;
+  if (!sv) { set_error("null server"); return SGOC_ERR_INVALID_ARG; }
+  SGOC_TRY(server_admit(sv));
+  // advance every active solve whose pending unit has completed; if none has,
+  // block on the oldest one so that the sweep always makes progress
+  bool progressed = false;
+  ServerSlot* oldest = nullptr;
+  for (auto& s : sv->slots) {
+    if (!s.busy) continue;
+    if (s.task.phase == SolveTask::DONE) { server_retire(sv, s); progressed = true; continue; }
+    if (!oldest || s.t_admit < oldest->t_admit) oldest = &s;
+    if (cudaEventQuery(s.task.rt->ev) == cudaSuccess) {
+      s.task.wait_and_step();
+      progressed = true;
+      if (s.task.phase == SolveTask::DONE) server_retire(sv, s);
+    }
+  }
+  if (!progressed && oldest) {
+    oldest->task.wait_and_step();
+    if (oldest->task.phase == SolveTask::DONE) server_retire(sv, *oldest);
+  }
+  SGOC_TRY(server_admit(sv));
+  int act = 0;
+  for (auto& s : sv->slots) act += s.busy ? 1 : 0;
+  if (n_active) *n_active = act;
+  if (n_queued) *n_queued = int32_t(sv->queue.size());
+  return SGOC_OK;
+}
+
+sgoc_status sgoc_server_poll(sgoc_server* sv, uint64_t* ids, sgoc_result* res, int32_t cap, int32_t* n_done) {
+  using namespace sgoc;
+  if (!sv || !n_done || cap < 0 || (cap > 0 && (!ids || !res))) { set_error("server poll: bad arguments"); return SGOC_ERR_INVALID_ARG; }
+  const int n = std::min<int>(cap, int(sv->done.size()));
+  for (int i = 0; i < n; ++i) { ids[i] = sv->done[i].first; res[i] = sv->done[i].second; }
+  sv->done.erase(sv->done.begin(), sv->done.begin() + n);
+  *n_done = n;
+  return SGOC_OK;
+}
+
+sgoc_status sgoc_server_stats(const sgoc_server* sv, int64_t* admitted, int64_t* completed, int64_t* rejected,
+                              size_t* pool_high_water) {
+  using namespace sgoc;
+  if (!sv) { set_error("null server"); return SGOC_ERR_INVALID_ARG; }
+  if (admitted) *admitted = sv->admitted;
+  if (completed) *completed = sv->completed;
+  if (rejected) *rejected = sv->rejected;
+  if (pool_high_water) *pool_high_water = sv->high_water;
+  return SGOC_OK;
+}
+
+}  // extern "C"
+
+namespace sgoc {
 
 template <typename T>
 static sgoc_status prec_hook(sgoc_problem* pb, void* ws, size_t bytes, PrecWS<T>& w) {
@@ -577,19 +1000,67 @@ sgoc_status sgoc_rhs(sgoc_problem* pb, double* d_b, void* stream) {
 
 sgoc_status sgoc_solve(sgoc_problem* pb, void* d_ws, size_t ws_bytes, const double* d_x0, double* d_x,
                        void* stream, sgoc_result* res) {
-  auto t0 = std::chrono::steady_clock::now();
   SGOC_TRY(check_ready(pb));
   if (!d_x) { set_error("null solution buffer"); return SGOC_ERR_INVALID_ARG; }
   SGOC_TRY(check_ws(d_ws, ws_bytes, workspace_bytes(pb, pb->opt.precision)));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  sgoc_status s = solve_impl(pb, d_ws, ws_bytes, d_x0, d_x, st, res);
+  SolveTask task;
+  sgoc_status s = task.begin(pb, d_ws, ws_bytes, d_x0, d_x, st);
+  if (s != SGOC_OK) task.fail(s);
+  while (task.phase != SolveTask::DONE) task.wait_and_step();
+  s = task.status;
   cudaError_t e = cudaStreamSynchronize(st);
   if (s == SGOC_OK && e != cudaSuccess) s = cuda_status(e, "cudaStreamSynchronize");
   if (res) {
+    *res = task.result;
     res->status = s;
-    res->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    res->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - task.t0).count();
   }
   return s;
+}
+
+sgoc_status sgoc_solve_batch(int32_t count, sgoc_problem* const* pbs, void* const* d_ws, const size_t* ws_bytes,
+                             const double* const* d_x0, double* const* d_x, void* const* streams,
+                             sgoc_result* res) {
+  if (count < 0 || (count > 0 && (!pbs || !d_ws || !ws_bytes || !d_x || !streams))) {
+    set_error("bad batch arguments");
+    return SGOC_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < count; ++i) {
+    SGOC_TRY(check_ready(pbs[i]));
+    if (!d_x[i]) { set_error("null solution buffer"); return SGOC_ERR_INVALID_ARG; }
+    SGOC_TRY(check_ws(d_ws[i], ws_bytes[i], workspace_bytes(pbs[i], pbs[i]->opt.precision)));
+    for (int k = 0; k < i; ++k)
+      if (pbs[k] == pbs[i]) { set_error("a problem may appear only once in a batch"); return SGOC_ERR_INVALID_ARG; }
+  }
+  std::vector<SolveTask> tasks(count);
+  for (int i = 0; i < count; ++i) {
+    sgoc_status s = tasks[i].begin(pbs[i], d_ws[i], ws_bytes[i], d_x0 ? d_x0[i] : nullptr, d_x[i],
+                                   static_cast<cudaStream_t>(streams[i]));
+    if (s != SGOC_OK) tasks[i].fail(s);
+  }
+  // round robin: while one solve's unit runs, the others' units are already queued
+  for (bool busy = true; busy;) {
+    busy = false;
+    for (auto& t : tasks) {
+      if (t.phase == SolveTask::DONE) continue;
+      t.wait_and_step();
+      busy = busy || t.phase != SolveTask::DONE;
+    }
+  }
+  sgoc_status first = SGOC_OK;
+  for (int i = 0; i < count; ++i) {
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(streams[i]));
+    sgoc_status s = tasks[i].status;
+    if (s == SGOC_OK && e != cudaSuccess) s = cuda_status(e, "cudaStreamSynchronize");
+    if (res) {
+      res[i] = tasks[i].result;
+      res[i].status = s;
+      res[i].ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tasks[i].t0).count();
+    }
+    if (first == SGOC_OK) first = s;
+  }
+  return first;
 }
 
 sgoc_status sgoc_apply_operator(sgoc_problem* pb, int32_t precision, const void* d_X, void* d_Y, int32_t nslabs,

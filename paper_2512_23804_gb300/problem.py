@@ -204,3 +204,103 @@ class SGProblem:
                                            c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(nnz)),
                   "sgoc_triple_products")
         return k, a, b, c
+
+
+def solve_batch(problems, x0s=None, outs=None, streams=None):
+    """Solve several SGProblem instances concurrently (sgoc_solve_batch): each on its
+    own CUDA stream, all advanced together by the calling thread.  Returns
+    ([x_i], [info_i])."""
+    import torch
+    lib = abi.load()
+    n = len(problems)
+    for sp in problems:
+        sp.upload()
+    if streams is None:
+        streams = [torch.cuda.Stream() for _ in range(n)]
+    # the caller's current stream must not race with the solve streams
+    cur = torch.cuda.current_stream()
+    for s in streams:
+        s.wait_stream(cur)
+    xs = outs if outs is not None else [torch.empty(sp.kkt_size, dtype=torch.float64, device="cuda")
+                                        for sp in problems]
+    wss = [sp.workspace() for sp in problems]
+    P = ctypes.c_void_p
+    arr = lambda vals: (P * n)(*vals)
+    res = (abi.Result * n)()
+    st = lib.sgoc_solve_batch(
+        n, arr([sp._handle.value for sp in problems]), arr([w.data_ptr() for w in wss]),
+        (ctypes.c_size_t * n)(*[w.numel() for w in wss]),
+        arr([(x0.data_ptr() if x0 is not None else None) for x0 in x0s]) if x0s is not None else None,
+        arr([x.data_ptr() for x in xs]), arr([s.cuda_stream for s in streams]), res)
+    for s in streams:
+        cur.wait_stream(s)
+    infos = []
+    for r in res:
+        d = r.as_dict()
+        d["status_name"] = abi.STATUS_NAMES.get(r.status, r.status)
+        infos.append(d)
+    if st != abi.SGOC_OK:
+        raise abi.SgocError(st, f"sgoc_solve_batch {infos}")
+    return xs, infos
+
+
+class SGServer:
+    """Continuous-batching solve server (sgoc_server_*) over a device pool taken
+    from PyTorch.  submit() queues a problem; step() runs one sweep; poll()
+    returns finished (request_id, solution tensor, info)."""
+
+    def __init__(self, pool_bytes, max_active=8):
+        import torch
+        lib = abi.load()
+        self._pool = torch.empty(pool_bytes, dtype=torch.uint8, device="cuda")
+        h = ctypes.c_void_p()
+        abi.check(lib.sgoc_server_create(_dptr(self._pool), pool_bytes, max_active, ctypes.byref(h)),
+                  "sgoc_server_create")
+        self._h = h
+        self._pending = {}
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None:
+            try:
+                abi.load().sgoc_server_destroy(self._h)
+            except Exception:
+                pass
+            self._h = None
+
+    def submit(self, sp, request_id):
+        import torch
+        x = torch.empty(sp.kkt_size, dtype=torch.float64, device="cuda")
+        torch.cuda.current_stream().synchronize()
+        abi.check(abi.load().sgoc_server_submit(self._h, sp._handle, _dptr(x), ctypes.c_uint64(request_id)),
+                  "sgoc_server_submit")
+        sp._persistent = None                 # the server uploads into its pool
+        self._pending[request_id] = (sp, x)
+
+    def step(self):
+        na, nq = ctypes.c_int32(), ctypes.c_int32()
+        abi.check(abi.load().sgoc_server_step(self._h, ctypes.byref(na), ctypes.byref(nq)), "sgoc_server_step")
+        return na.value, nq.value
+
+    def poll(self, cap=64):
+        ids = (ctypes.c_uint64 * cap)()
+        res = (abi.Result * cap)()
+        n = ctypes.c_int32()
+        abi.check(abi.load().sgoc_server_poll(self._h, ids, res, cap, ctypes.byref(n)), "sgoc_server_poll")
+        out = []
+        for i in range(n.value):
+            sp, x = self._pending.pop(ids[i])
+            d = res[i].as_dict()
+            d["status_name"] = abi.STATUS_NAMES.get(res[i].status, res[i].status)
+            out.append((ids[i], x, d))
+        return out
+
+    def stats(self):
+        a, c, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        hw = ctypes.c_size_t()
+        abi.check(abi.load().sgoc_server_stats(self._h, ctypes.byref(a), ctypes.byref(c), ctypes.byref(r),
+                                               ctypes.byref(hw)), "sgoc_server_stats")
+        return dict(admitted=a.value, completed=c.value, rejected=r.value, pool_high_water=hw.value)
+
+    @property
+    def pending(self):
+        return len(self._pending)
