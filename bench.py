@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip fp64/e2e/profile/matvec legs")
     ap.add_argument("--sequential", action="store_true", help="solve the batch one problem at a time")
+    ap.add_argument("--kernel-case", choices=["vcycle128", "sg128", "sg512", "hgs128"], default=None,
+                    help="run one kernel class a few times on a small case (for ncu captures) and exit")
     return ap.parse_args()
 
 
@@ -396,8 +398,39 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_kernel_case(args):
+    """A few launches of one kernel class on a small case, for hardware-counter captures."""
+    import torch
+    import sg_inputs as si
+    from paper_2512_23804_gb300 import SGProblem, build
+    build.build()
+    case = args.kernel_case
+    pr = si.steady_512() if case == "sg512" else si.steady_128(1e-4)
+    sp = SGProblem.from_problem(pr, precision="mixed").upload()
+    if case in ("sg128", "sg512"):
+        X = torch.randn(sp.n * sp.P, dtype=torch.float32, device="cuda")
+        Y = torch.empty_like(X)
+        for _ in range(3):
+            sp.apply_operator(X, out=Y)
+    elif case == "vcycle128":
+        ncols = 56                                  # the largest chaos level of M=6, p=3
+        R = torch.randn(ncols * sp.n, dtype=torch.float32, device="cuda")
+        X = torch.empty_like(R)
+        for _ in range(3):
+            sp.apply_vcycle(R, ncols, out=X)
+    else:
+        R = torch.randn(sp.n * sp.P, dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            sp.apply_hgs(R)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": case, "ok": True}))
+
+
 def main():
     args = parse()
+    if args.kernel_case:
+        run_kernel_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

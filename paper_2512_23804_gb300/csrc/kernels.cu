@@ -6,6 +6,7 @@
 // south-west corner of (ix+1, iy+1) and the south-east corner of (ix, iy+1).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <mutex>
@@ -120,7 +121,6 @@ __device__ __forceinline__ T dot4(const typename Vec4<T>::type& a, const typenam
 //   phase 2: out(beta) = sum_e kappa_0(e) T_e(beta) + sum_{(alpha,k,c)} c sum_e kappa_k(e) T_e(alpha)
 // ---------------------------------------------------------------------------
 constexpr int kSGThreads = 256;
-constexpr int kSGChunk = 16;     // input columns per asynchronous staging chunk
 
 // asynchronous global->shared copy of one element; invalid elements are zero-filled
 template <typename T>
@@ -136,76 +136,103 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+// SG operator kernel: one CTA walks rows [r0, r1) of one TX-wide x-tile of one
+// slab.  A ring of four X row panels (input columns [in0, in1), TX+2 nodes with
+// halo) lives in shared memory; row iy+2 is prefetched with cp.async while row
+// iy is computed, so every X element is read once per CTA.
+//   phase 1: kappa_k(e)/6 of the row's elements; T_e(alpha) for every node and
+//            input column (and the mass stencil of the output columns)
+//   phase 2: out(beta) = sum_e kappa_0(e) T_e(beta) + sum_{(alpha,k,c)} c sum_e kappa_k(e) T_e(alpha)
+// neighbour-table entry staged in shared memory (16 bytes for both types)
+template <typename T> struct NbrEntry;
+template <> struct __align__(16) NbrEntry<float> { int ts, ks; float c; int pad; };
+template <> struct __align__(16) NbrEntry<double> { int ts, ks; double c; };
+
 template <typename T, int TX>
-__global__ void __launch_bounds__(kSGThreads) sg_kernel(SGArgs<T> a) {
+__global__ void __launch_bounds__(kSGThreads) sg_kernel(SGArgs<T> a, int rows_per_cta) {
   using V4 = typename Vec4<T>::type;
   extern __shared__ __align__(32) unsigned char sg_smem_raw[];
   constexpr int W = TX + 2;
   const int nin = a.in1 - a.in0;
   const int nout = a.out1 - a.out0;
+  const bool use_m = a.cm != T(0);
   V4* Ts = reinterpret_cast<V4*>(sg_smem_raw);               // [nin][TX]
   V4* Ks = Ts + size_t(nin) * TX;                            // [M+1][TX]
-  T* Ms = reinterpret_cast<T*>(Ks + size_t(a.M + 1) * TX);   // [nout][TX]
-  T* Xs = Ms + (a.cm != T(0) ? size_t(nout) * TX : 0);       // [2][kSGChunk][3][W]
-  T* Cs = Xs + size_t(2) * kSGChunk * 3 * W;                 // neighbour coefficients [nnz_out]
-  int* Es = reinterpret_cast<int*>(Cs + a.nnz_out);          // packed (alpha - in0) | k << 20
-  int* Ps = Es + a.nnz_out;                                  // [nout + 1] local CSR
+  T* Ms = reinterpret_cast<T*>(Ks + size_t(a.M + 1) * TX);   // [nout][TX] (when cm != 0)
+  T* Xr = Ms + (use_m ? size_t(nout) * TX : 0);              // ring [4][nin][W]
+  NbrEntry<T>* Es = reinterpret_cast<NbrEntry<T>*>(Xr + size_t(4) * nin * W);  // [nnz_out]
+  int* Ps = reinterpret_cast<int*>(Es + a.nnz_out);          // [nout] first entry of each output column
+  int* Pe = Ps + nout;                                       // [nout] end of its entries with k < kmax
 
   const int ix0 = blockIdx.x * TX;
-  const int iy = blockIdx.y;
+  const int r0 = blockIdx.y * rows_per_cta;
+  const int r1 = min(a.n1, r0 + rows_per_cta);
   const int t = blockIdx.z;
   const int tid = threadIdx.x;
   const int n1 = a.n1;
   const T* X = a.X + int64_t(t) * a.xs;
-  const int nchunks = (nin + kSGChunk - 1) / kSGChunk;
+  const size_t ring_stride = size_t(nin) * W;
+  if (r0 >= r1) return;
 
-  auto issue = [&](int ch) {
-    const int c0 = a.in0 + ch * kSGChunk;
-    const int nc = min(kSGChunk, a.in1 - c0);
-    T* dst = Xs + size_t(ch & 1) * kSGChunk * 3 * W;
-    for (int q = tid; q < nc * 3 * W; q += kSGThreads) {
-      const int c = q / (3 * W), rem = q % (3 * W), dy = rem / W, lx = rem % W;
-      const int gx = ix0 + lx - 1, gy = iy + dy - 1;
-      const bool ok = gx >= 0 && gx < n1 && gy >= 0 && gy < n1;
-      const T* col = X + int64_t(c0 + c) * a.n;
+  // row gy (-1 and n1 give zeros) into ring slot (gy + 1) & 3
+  auto issue_row = [&](int gy) {
+    T* dst = Xr + size_t((gy + 1) & 3) * ring_stride;
+    const bool rok = gy >= 0 && gy < n1;
+    for (int q = tid; q < nin * W; q += kSGThreads) {
+      const int c = q / W, lx = q - c * W;
+      const int gx = ix0 + lx - 1;
+      const bool ok = rok && gx >= 0 && gx < n1;
+      const T* col = X + int64_t(a.in0 + c) * a.n;
       cp_async_elem(dst + q, ok ? col + (int64_t(gy) * n1 + gx) : col, ok);
     }
-    cp_async_commit();
   };
-  issue(0);
+  issue_row(r0 - 1);
+  issue_row(r0);
+  issue_row(r0 + 1);
+  cp_async_commit();
 
-  // phase 0: element coefficients and the local neighbour table (overlaps the first copies)
-  for (int q = tid; q < (a.M + 1) * TX; q += kSGThreads) {
-    const int k = q / TX, lx = q % TX;
-    const int ix = min(ix0 + lx, n1 - 1);
-    const T* kk = a.kap + int64_t(k) * a.nx * a.nx;
-    V4 v;
-    v.x = kk[int64_t(iy) * a.nx + ix];            // SW element (ix, iy)
-    v.y = kk[int64_t(iy) * a.nx + ix + 1];        // SE element (ix+1, iy)
-    v.z = kk[int64_t(iy + 1) * a.nx + ix + 1];    // NE element (ix+1, iy+1)
-    v.w = kk[int64_t(iy + 1) * a.nx + ix];        // NW element (ix, iy+1)
-    Ks[k * TX + lx] = v;
-  }
+  // neighbour table of the output columns with shared-memory offsets pre-multiplied;
+  // per column only the entries with k < kmax (a prefix: the table is sorted by k)
   const int ebase = a.nbr_ptr[a.out0];
-  for (int q = tid; q <= nout; q += kSGThreads) Ps[q] = a.nbr_ptr[a.out0 + q] - ebase;
   for (int q = tid; q < a.nnz_out; q += kSGThreads) {
-    Cs[q] = a.nbr_c[ebase + q];
-    Es[q] = (a.nbr_alpha[ebase + q] - a.in0) | (a.nbr_k[ebase + q] << 20);
+    NbrEntry<T> en;
+    en.ts = (a.nbr_alpha[ebase + q] - a.in0) * TX;
+    en.ks = a.nbr_k[ebase + q] * TX;
+    en.c = a.nbr_c[ebase + q];
+    Es[q] = en;
+  }
+  for (int q = tid; q < nout; q += kSGThreads) {
+    const int e0 = a.nbr_ptr[a.out0 + q], e1 = a.nbr_ptr[a.out0 + q + 1];
+    int e = e0;
+    while (e < e1 && a.nbr_k[e] < a.kmax) ++e;
+    Ps[q] = e0 - ebase;
+    Pe[q] = e - ebase;
   }
 
-  // phase 1: element terms T_e of every input column (double-buffered chunks)
-  for (int ch = 0; ch < nchunks; ++ch) {
-    if (ch + 1 < nchunks) { issue(ch + 1); cp_async_wait<1>(); } else { cp_async_wait<0>(); }
+  for (int iy = r0; iy < r1; ++iy) {
+    // prefetch the row the next output row needs, then wait for this row's three
+    if (iy + 1 < r1) { issue_row(iy + 2); cp_async_commit(); cp_async_wait<1>(); } else { cp_async_wait<0>(); }
+    for (int q = tid; q < (a.M + 1) * TX; q += kSGThreads) {
+      const int kk = q / TX, lx = q - kk * TX;
+      const int ix = min(ix0 + lx, n1 - 1);
+      const T* kp = a.kap + int64_t(kk) * a.nx * a.nx;
+      V4 v;
+      v.x = kp[int64_t(iy) * a.nx + ix];            // SW element (ix, iy)
+      v.y = kp[int64_t(iy) * a.nx + ix + 1];        // SE element (ix+1, iy)
+      v.z = kp[int64_t(iy + 1) * a.nx + ix + 1];    // NE element (ix+1, iy+1)
+      v.w = kp[int64_t(iy + 1) * a.nx + ix];        // NW element (ix, iy+1)
+      Ks[kk * TX + lx] = v;
+    }
     __syncthreads();
-    const int c0 = a.in0 + ch * kSGChunk;
-    const int nc = min(kSGChunk, a.in1 - c0);
-    const T* src = Xs + size_t(ch & 1) * kSGChunk * 3 * W;
-    for (int q = tid; q < nc * TX; q += kSGThreads) {
-      const int c = q / TX, lx = q % TX;
-      const T* s = src + c * 3 * W + lx;   // s[dy*W + dx], dx,dy in 0..2 (1 = centre)
-      const T SW = s[0], S = s[1], SE = s[2];
-      const T Wv = s[W], C = s[W + 1], E = s[W + 2];
-      const T NW = s[2 * W], N = s[2 * W + 1], NE = s[2 * W + 2];
+    const T* rS = Xr + size_t(iy & 3) * ring_stride;         // row iy-1
+    const T* rC = Xr + size_t((iy + 1) & 3) * ring_stride;   // row iy
+    const T* rN = Xr + size_t((iy + 2) & 3) * ring_stride;   // row iy+1
+    for (int q = tid; q < nin * TX; q += kSGThreads) {
+      const int c = q / TX, lx = q - c * TX;
+      const size_t o = size_t(c) * W + lx;
+      const T SW = rS[o], S = rS[o + 1], SE = rS[o + 2];
+      const T Wv = rC[o], C = rC[o + 1], E = rC[o + 2];
+      const T NW = rN[o], N = rN[o + 1], NE = rN[o + 2];
       const T c4 = T(4) * C;
       const T aS = c4 - S, aN = c4 - N;
       V4 v;
@@ -213,66 +240,69 @@ __global__ void __launch_bounds__(kSGThreads) sg_kernel(SGArgs<T> a) {
       v.y = fma(T(-2), SE, aS - E);
       v.z = fma(T(-2), NE, aN - E);
       v.w = fma(T(-2), NW, aN - Wv);
-      const int col = c0 + c;
-      Ts[size_t(col - a.in0) * TX + lx] = v;
-      if (a.cm != T(0) && col >= a.out0 && col < a.out1) {
+      Ts[size_t(c) * TX + lx] = v;
+      const int col = a.in0 + c;
+      if (use_m && col >= a.out0 && col < a.out1) {
         const T edges = (N + S) + (E + Wv);
         const T corners = (NE + NW) + (SE + SW);
         Ms[size_t(col - a.out0) * TX + lx] = a.mass * fma(T(16), C, fma(T(4), edges, corners));
       }
     }
     __syncthreads();
-  }
-
-  // phase 2: contraction with the triple products (warp-uniform output column when TX = 32)
-  const int kmax = a.kmax;
-  for (int q = tid; q < nout * TX; q += kSGThreads) {
-    const int lx = q % TX, bl = q / TX;
-    const int ix = ix0 + lx;
-    const int beta = a.out0 + bl;
-    const V4 tb = Ts[size_t(beta - a.in0) * TX + lx];
-    T diag = dot4<T>(Ks[lx], tb);
-    T off = T(0);
-    const int e1 = Ps[bl + 1];
-    for (int e = Ps[bl]; e < e1; ++e) {
-      const int pk = Es[e];
-      const int k = pk >> 20;
-      if (k >= kmax) break;                          // table is sorted by k
-      const int al = pk & 0xFFFFF;
-      off = fma(Cs[e], dot4<T>(Ks[k * TX + lx], Ts[size_t(al) * TX + lx]), off);
+    for (int q = tid; q < nout * TX; q += kSGThreads) {
+      const int lx = q % TX, bl = q / TX;
+      const int ix = ix0 + lx;
+      const int beta = a.out0 + bl;
+      const V4 tb = Ts[size_t(beta - a.in0) * TX + lx];
+      T diag = dot4<T>(Ks[lx], tb);
+      T off = T(0);
+      const int e1 = Pe[bl];
+      for (int e = Ps[bl]; e < e1; ++e) {
+        const NbrEntry<T> en = Es[e];
+        off = fma(en.c, dot4<T>(Ks[en.ks + lx], Ts[en.ts + lx]), off);
+      }
+      if (ix >= n1) continue;
+      T out = a.c0 * diag + a.c1 * off;
+      if (use_m) out = fma(a.cm, Ms[size_t(bl) * TX + lx], out);
+      const int64_t node = int64_t(iy) * n1 + ix;
+      if (a.R) out = fma(a.cr, a.R[int64_t(t) * a.rs + int64_t(beta - a.rcol0) * a.n + node], out);
+      T* yp = a.Y + int64_t(t) * a.ys + int64_t(beta - a.ycol0) * a.n + node;
+      if (a.cy != T(0)) out = fma(a.cy, *yp, out);
+      *yp = out;
     }
-    if (ix >= n1) continue;
-    T out = a.c0 * diag + a.c1 * off;
-    if (a.cm != T(0)) out = fma(a.cm, Ms[size_t(bl) * TX + lx], out);
-    const int64_t node = int64_t(iy) * n1 + ix;
-    if (a.R) out = fma(a.cr, a.R[int64_t(t) * a.rs + int64_t(beta - a.rcol0) * a.n + node], out);
-    T* yp = a.Y + int64_t(t) * a.ys + int64_t(beta - a.ycol0) * a.n + node;
-    if (a.cy != T(0)) out = fma(a.cy, *yp, out);
-    *yp = out;
+    __syncthreads();                                    // Ts, Ks and the oldest ring slot are reused
   }
 }
 
 template <typename T, int TX>
 static size_t sg_smem(const SGArgs<T>& a) {
   using V4 = typename Vec4<T>::type;
-  return sizeof(V4) * (size_t(a.in1 - a.in0) * TX + size_t(a.M + 1) * TX) +
-         sizeof(T) * ((a.cm != T(0) ? size_t(a.out1 - a.out0) * TX : 0) + size_t(2) * kSGChunk * 3 * (TX + 2) +
-                      a.nnz_out) +
-         sizeof(int) * (size_t(a.nnz_out) + (a.out1 - a.out0) + 1);
+  const size_t nin = a.in1 - a.in0, nout = a.out1 - a.out0;
+  size_t b = sizeof(V4) * (nin * TX + size_t(a.M + 1) * TX) +
+             sizeof(T) * ((a.cm != T(0) ? nout * TX : 0) + 4 * nin * (TX + 2));
+  b = (b + 15) & ~size_t(15);
+  return b + 16 * size_t(a.nnz_out) + sizeof(int) * 2 * nout;
 }
 
 template <typename T, int TX>
 static cudaError_t launch_sg_tx(const SGArgs<T>& a, size_t smem, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(sg_kernel<T, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  dim3 grid((a.n1 + TX - 1) / TX, a.n1, a.nslabs);
+  const int xt = (a.n1 + TX - 1) / TX;
+  const int per_sm = std::max(1, int((228 * 1024) / (smem + 1024)));
+  // about two CTAs per resident slot of the GPU
+  const int64_t want = int64_t(152) * per_sm * 2;
+  const int64_t tiles = int64_t(xt) * a.nslabs;
+  int rows = int(std::max<int64_t>(1, (tiles * a.n1 + want - 1) / want));
+  rows = std::min(rows, a.n1);
+  dim3 grid(xt, (a.n1 + rows - 1) / rows, a.nslabs);
   const double w = sizeof(T), cells = double(a.n) * a.nslabs;
   const int nout = a.out1 - a.out0, nin = a.in1 - a.in0;
   const double bytes = w * cells * (nin + nout * (1.0 + (a.R ? 1 : 0) + (a.cy != T(0) ? 1 : 0))) +
                        w * (a.M + 1.0) * a.nx * a.nx;
   const double flops = cells * (15.0 * nin + 9.0 * nout + 9.0 * (a.c1 != T(0) ? a.deg_sum : 0));
   ProfScope ps(KK_SG, st, bytes, flops);
-  sg_kernel<T, TX><<<grid, kSGThreads, smem, st>>>(a);
+  sg_kernel<T, TX><<<grid, kSGThreads, smem, st>>>(a, rows);
   note_launch();
   return cudaGetLastError();
 }
@@ -578,98 +608,126 @@ cudaError_t launch_scale(const T* b, T* x, int64_t cnt, T a, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// Full-hierarchy V-cycle, one CTA per column (1024 threads, levels in shared
-// memory).  The finest right-hand side b_0 is read from global memory (it is the
-// output of the preceding kernel and sits in L2); x_l, r_l (all levels) and b_l
-// (coarse levels) live in shared memory.  Jacobi sweeps are register-blocked:
-// each thread owns a vertical strip of up to kStripRows points of one grid
-// column and slides a 3x3 window down it (3 shared loads per point).
+// Full-hierarchy V-cycle, one CTA (1024 threads) per column, all levels in
+// shared memory.  Every level array carries a one-node zero border (stride
+// n1 + 2) so that stencil loads need no bounds checks.  Level 0 holds two
+// iterate buffers (ping-pong; the idle one takes the residual), levels >= 1
+// hold two iterate buffers and the right-hand side.  The level-0 right-hand
+// side stays in registers: each thread owns a vertical strip of up to
+// kStripRows nodes of one grid column and slides a 3x3 window down it.
+// Coarse levels are processed point-parallel on a 32 x 32 thread grid.
 // ---------------------------------------------------------------------------
 constexpr int kVFThreads = 1024;
 constexpr int kStripRows = 16;
 
-template <typename T>
-struct StripGeom {
-  int x, y0, y1;   // column and row range [y0, y1) of this thread; x < 0: idle
+__device__ __forceinline__ int vf_padded(int n1) { return (n1 + 2) * (n1 + 2); }
+
+// shared-memory offset (elements) of level l
+__device__ __forceinline__ size_t vf_level_off(const FusedLevels& L, int l) {
+  size_t o = 0;
+  for (int q = 0; q < l; ++q) o += size_t(vf_padded(L.n1[q])) * (q > 0 ? 3 : 2);
+  return o;
+}
+
+struct Strip {
+  int x, y0, y1;   // column and interior rows [y0, y1) of this thread; x < 0: idle
 };
 
-template <typename T>
-__device__ __forceinline__ StripGeom<T> strip_of(int n1) {
-  StripGeom<T> g;
+__device__ __forceinline__ Strip strip_of(int n1) {
+  Strip g;
   const int nchunks = (n1 + kStripRows - 1) / kStripRows;
   const int rows = (n1 + nchunks - 1) / nchunks;
   const int t = threadIdx.x;
   const int chunk = t / n1;
-  g.x = (chunk < nchunks) ? t % n1 : -1;
+  g.x = (chunk < nchunks) ? t - chunk * n1 : -1;
   g.y0 = chunk * rows;
   g.y1 = min(n1, g.y0 + rows);
   return g;
 }
 
-template <typename T>
-__device__ __forceinline__ T ldrow(const T* X, int x, int y, int n1) {
-  return (y >= 0 && y < n1 && x >= 0 && x < n1) ? X[y * n1 + x] : T(0);
-}
-
-// One damped-Jacobi sweep x <- x + omega/d (b - A x) in place (from_zero: x <- omega/d b).
-// b may be in global or shared memory.  Contains the barriers.
-template <typename T>
-__device__ void strip_sweep(T* x, const T* b, int n1, T d, T e, T c, T omega, bool from_zero) {
-  const StripGeom<T> g = strip_of<T>(n1);
-  T nv[kStripRows];
-  const T wd = omega / d;
-  if (g.x >= 0) {
-    if (from_zero) {
-#pragma unroll
-      for (int j = 0; j < kStripRows; ++j) {
-        const int y = g.y0 + j;
-        if (y < g.y1) nv[j] = wd * b[y * n1 + g.x];
-      }
-    } else {
-      const int xm = g.x - 1, xp = g.x + 1;
-      T wm0 = ldrow(x, xm, g.y0 - 1, n1), wc0 = ldrow(x, g.x, g.y0 - 1, n1), wp0 = ldrow(x, xp, g.y0 - 1, n1);
-      T wm1 = ldrow(x, xm, g.y0, n1), wc1 = ldrow(x, g.x, g.y0, n1), wp1 = ldrow(x, xp, g.y0, n1);
-#pragma unroll
-      for (int j = 0; j < kStripRows; ++j) {
-        const int y = g.y0 + j;
-        if (y < g.y1) {
-          const T wm2 = ldrow(x, xm, y + 1, n1), wc2 = ldrow(x, g.x, y + 1, n1), wp2 = ldrow(x, xp, y + 1, n1);
-          const T edges = (wc0 + wc2) + (wm1 + wp1);
-          const T corners = (wm0 + wp0) + (wm2 + wp2);
-          const T ax = fma(d, wc1, fma(e, edges, c * corners));
-          nv[j] = fma(wd, b[y * n1 + g.x] - ax, wc1);
-          wm0 = wm1; wc0 = wc1; wp0 = wp1;
-          wm1 = wm2; wc1 = wc2; wp1 = wp2;
-        }
-      }
-    }
-  }
-  __syncthreads();
-  if (g.x >= 0) {
+// Level-0 pass over this thread's strip: Jacobi (xd = xs + omega/d (b - A xs)),
+// from zero (xd = omega/d b) or residual (xd = b - A xs).  No barrier inside.
+template <typename T, int MODE>   // 0 jacobi, 1 from zero, 2 residual
+__device__ __forceinline__ void strip_pass(const T* __restrict__ xs, T* __restrict__ xd, const T (&bv)[kStripRows],
+                                           const Strip& g, int n1, T d, T e, T c, T wd) {
+  if (g.x < 0) return;
+  const int s = n1 + 2;
+  if (MODE == 1) {
 #pragma unroll
     for (int j = 0; j < kStripRows; ++j) {
       const int y = g.y0 + j;
-      if (y < g.y1) x[y * n1 + g.x] = nv[j];
+      if (y < g.y1) xd[(y + 1) * s + g.x + 1] = wd * bv[j];
+    }
+    return;
+  }
+  const T* p = xs + g.y0 * s + g.x;      // padded (row y0, col x) = interior (y0-1, x-1)
+  T wm0 = p[0], wc0 = p[1], wp0 = p[2];
+  p += s;
+  T wm1 = p[0], wc1 = p[1], wp1 = p[2];
+  T* q = xd + (g.y0 + 1) * s + g.x + 1;
+#pragma unroll
+  for (int j = 0; j < kStripRows; ++j) {
+    if (g.y0 + j < g.y1) {
+      p += s;
+      const T wm2 = p[0], wc2 = p[1], wp2 = p[2];
+      const T edges = (wc0 + wc2) + (wm1 + wp1);
+      const T corners = (wm0 + wp0) + (wm2 + wp2);
+      const T r = bv[j] - fma(d, wc1, fma(e, edges, c * corners));
+      *q = MODE == 2 ? r : fma(wd, r, wc1);
+      q += s;
+      wm0 = wm1; wc0 = wc1; wp0 = wp1;
+      wm1 = wm2; wc1 = wc2; wp1 = wp2;
     }
   }
-  __syncthreads();
 }
 
-// r <- b - A x (register-blocked, no barrier inside; caller syncs)
+// Coarse-level pass (point parallel): Jacobi / from zero / residual against b in shared memory.
+template <typename T, int MODE>
+__device__ __forceinline__ void point_pass(const T* __restrict__ xs, T* __restrict__ xd, const T* __restrict__ b,
+                                          int n1, T d, T e, T c, T wd) {
+  const int s = n1 + 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int y = ty; y < n1; y += 32)
+    for (int x = tx; x < n1; x += 32) {
+      const int o = (y + 1) * s + x + 1;
+      if (MODE == 1) { xd[o] = wd * b[o]; continue; }
+      const T edges = (xs[o - s] + xs[o + s]) + (xs[o - 1] + xs[o + 1]);
+      const T corners = (xs[o - s - 1] + xs[o - s + 1]) + (xs[o + s - 1] + xs[o + s + 1]);
+      const T r = b[o] - fma(d, xs[o], fma(e, edges, c * corners));
+      xd[o] = MODE == 2 ? r : fma(wd, r, xs[o]);
+    }
+}
+
+// full weighting: coarse interior (I, J) = fine interior (2I+1, 2J+1) = fine padded (2I+2, 2J+2)
 template <typename T>
-__device__ void strip_residual(const T* x, const T* b, T* r, int n1, T d, T e, T c) {
-  const StripGeom<T> g = strip_of<T>(n1);
-  if (g.x < 0) return;
-  const int xm = g.x - 1, xp = g.x + 1;
-  T wm0 = ldrow(x, xm, g.y0 - 1, n1), wc0 = ldrow(x, g.x, g.y0 - 1, n1), wp0 = ldrow(x, xp, g.y0 - 1, n1);
-  T wm1 = ldrow(x, xm, g.y0, n1), wc1 = ldrow(x, g.x, g.y0, n1), wp1 = ldrow(x, xp, g.y0, n1);
-  for (int y = g.y0; y < g.y1; ++y) {
-    const T wm2 = ldrow(x, xm, y + 1, n1), wc2 = ldrow(x, g.x, y + 1, n1), wp2 = ldrow(x, xp, y + 1, n1);
-    const T edges = (wc0 + wc2) + (wm1 + wp1);
-    const T corners = (wm0 + wp0) + (wm2 + wp2);
-    r[y * n1 + g.x] = b[y * n1 + g.x] - fma(d, wc1, fma(e, edges, c * corners));
-    wm0 = wm1; wc0 = wc1; wp0 = wp1;
-    wm1 = wm2; wc1 = wc2; wp1 = wp2;
+__device__ __forceinline__ void restrict_pass(const T* __restrict__ R, T* __restrict__ bc, int n1, int n1c) {
+  const int s = n1 + 2, sc = n1c + 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int J = ty; J < n1c; J += 32)
+    for (int I = tx; I < n1c; I += 32) {
+      const T* r = R + (2 * J + 2) * s + 2 * I + 2;
+      const T cen = r[0];
+      const T edg = (r[s] + r[-s]) + (r[1] + r[-1]);
+      const T cor = (r[s + 1] + r[s - 1]) + (r[-s + 1] + r[-s - 1]);
+      bc[(J + 1) * sc + I + 1] = cen + T(0.5) * edg + T(0.25) * cor;
+    }
+}
+
+// bilinear interpolation added to the fine iterate; fine grid node g = i + 1 takes
+// coarse padded nodes g >> 1 and (g + 1) >> 1 (equal when g is even); borders are zero
+template <typename T>
+__device__ __forceinline__ void prolong_pass(const T* __restrict__ Xc, T* __restrict__ xf, int n1, int n1c) {
+  const int s = n1 + 2, sc = n1c + 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int j = ty; j < n1; j += 32) {
+    const int gj = j + 1;
+    const T* r0 = Xc + (gj >> 1) * sc;
+    const T* r1 = Xc + ((gj + 1) >> 1) * sc;
+    for (int i = tx; i < n1; i += 32) {
+      const int gi = i + 1;
+      const int c0 = gi >> 1, c1 = (gi + 1) >> 1;
+      xf[(j + 1) * s + i + 1] += T(0.25) * ((r0[c0] + r0[c1]) + (r1[c0] + r1[c1]));
+    }
   }
 }
 
@@ -679,91 +737,129 @@ __global__ void __launch_bounds__(kVFThreads, 1) vcycle_full_kernel(const T* __r
                                                                     int acc_L, int acc_col0) {
   extern __shared__ __align__(32) unsigned char vf_smem_raw[];
   T* base = reinterpret_cast<T*>(vf_smem_raw);
-  // layout: for each level l: x_l, r_l, and b_l for l >= 1
-  T* xs[13];
-  T* rs[13];
-  T* bs[13];
-  {
-    size_t o = 0;
-#pragma unroll 1
-    for (int l = 0; l < L.nlev; ++l) {
-      const int n = L.n1[l] * L.n1[l];
-      xs[l] = base + o; o += n;
-      rs[l] = base + o; o += n;
-      if (l > 0) { bs[l] = base + o; o += n; } else { bs[l] = nullptr; }
+  const int64_t col = blockIdx.x;
+  const int n10 = L.n1[0];
+  const int n0 = n10 * n10;
+  // zero borders of every array (interiors are always written before they are read)
+  for (int l = 0; l < L.nlev; ++l) {
+    const int n1 = L.n1[l], s = n1 + 2;
+    T* a = base + vf_level_off(L, l);
+    const int narr = l > 0 ? 3 : 2;
+    for (int q = threadIdx.x; q < narr * 4 * (n1 + 1); q += kVFThreads) {
+      const int arr = q / (4 * (n1 + 1)), k = q - arr * 4 * (n1 + 1);
+      T* A = a + size_t(arr) * s * s;
+      const int side = k / (n1 + 1), pos = k - side * (n1 + 1);
+      int o;
+      if (side == 0) o = pos;                               // top row, columns 0..n1
+      else if (side == 1) o = (n1 + 1) * s + pos + 1;       // bottom row, columns 1..n1+1
+      else if (side == 2) o = (pos + 1) * s;                // left column, rows 1..n1+1
+      else o = pos * s + n1 + 1;                            // right column, rows 0..n1
+      A[o] = T(0);
     }
   }
-  const int64_t col = blockIdx.x;
-  const int n0 = L.n1[0] * L.n1[0];
-  const T* b0 = bg + col * n0;
-  bs[0] = const_cast<T*>(b0);
+  const Strip g = strip_of(n10);
+  T bv[kStripRows];
+  {
+    const T* b0 = bg + col * n0;
+#pragma unroll
+    for (int j = 0; j < kStripRows; ++j) {
+      const int y = g.y0 + j;
+      bv[j] = (g.x >= 0 && y < g.y1) ? b0[y * n10 + g.x] : T(0);
+    }
+  }
+  __syncthreads();
+  int cur_l[13];
 #pragma unroll 1
   for (int l = 0; l < L.nlev - 1; ++l) {
     const int n1 = L.n1[l], n1c = L.n1[l + 1];
+    const int np = vf_padded(n1);
+    T* xa = base + vf_level_off(L, l);
+    T* xb = xa + np;
+    const T* bl = xb + np;                                   // levels >= 1
     const T d = T(L.diag[l]), e = T(L.edge[l]), c = T(L.corner[l]);
-#pragma unroll 1
-    for (int s = 0; s < nu; ++s) strip_sweep(xs[l], bs[l], n1, d, e, c, omega, s == 0);
+    const T wd = omega / d;
+    int cur = 0;
     if (nu == 0) {
-      for (int q = threadIdx.x; q < n1 * n1; q += kVFThreads) xs[l][q] = T(0);
+      for (int q = threadIdx.x; q < np; q += kVFThreads) xa[q] = T(0);
       __syncthreads();
     }
-    strip_residual(xs[l], bs[l], rs[l], n1, d, e, c);
-    __syncthreads();
-    const T* R = rs[l];
-    for (int q = threadIdx.x; q < n1c * n1c; q += kVFThreads) {
-      const int I = q % n1c, J = q / n1c;
-      const int fx = 2 * I + 1, fy = 2 * J + 1;
-      const T cen = R[fy * n1 + fx];
-      const T edg = (R[(fy + 1) * n1 + fx] + R[(fy - 1) * n1 + fx]) + (R[fy * n1 + fx + 1] + R[fy * n1 + fx - 1]);
-      const T cor = (R[(fy + 1) * n1 + fx + 1] + R[(fy + 1) * n1 + fx - 1]) +
-                    (R[(fy - 1) * n1 + fx + 1] + R[(fy - 1) * n1 + fx - 1]);
-      bs[l + 1][q] = cen + T(0.5) * edg + T(0.25) * cor;
+#pragma unroll 1
+    for (int sw = 0; sw < nu; ++sw) {
+      const T* src = cur == 0 ? xa : xb;
+      T* dst = sw == 0 ? xa : (cur == 0 ? xb : xa);
+      if (l == 0) {
+        if (sw == 0) strip_pass<T, 1>(src, dst, bv, g, n1, d, e, c, wd);
+        else strip_pass<T, 0>(src, dst, bv, g, n1, d, e, c, wd);
+      } else {
+        if (sw == 0) point_pass<T, 1>(src, dst, bl, n1, d, e, c, wd);
+        else point_pass<T, 0>(src, dst, bl, n1, d, e, c, wd);
+      }
+      cur = dst == xa ? 0 : 1;
+      __syncthreads();
     }
+    const T* xcur = cur == 0 ? xa : xb;
+    T* rbuf = cur == 0 ? xb : xa;
+    if (l == 0) strip_pass<T, 2>(xcur, rbuf, bv, g, n1, d, e, c, wd);
+    else point_pass<T, 2>(xcur, rbuf, bl, n1, d, e, c, wd);
+    __syncthreads();
+    T* bc = base + vf_level_off(L, l + 1) + 2 * size_t(vf_padded(n1c));
+    restrict_pass<T>(rbuf, bc, n1, n1c);
+    cur_l[l] = cur;
     __syncthreads();
   }
   {
+    // coarsest level: a single node (n1 = 1) solved exactly, or (one level only) n1 = 1 at the top
     const int l = L.nlev - 1;
-    const int n = L.n1[l] * L.n1[l];
-    for (int q = threadIdx.x; q < n; q += kVFThreads) xs[l][q] = bs[l][q] / T(L.diag[l]);
+    T* xa = base + vf_level_off(L, l);
+    if (threadIdx.x == 0) {
+      const T bq = l == 0 ? bv[0] : xa[2 * vf_padded(L.n1[l]) + 4];   // interior (0,0) sits at padded 4
+      xa[4] = bq / T(L.diag[l]);
+    }
+    cur_l[l] = 0;
     __syncthreads();
   }
 #pragma unroll 1
   for (int l = L.nlev - 2; l >= 0; --l) {
     const int n1 = L.n1[l], n1c = L.n1[l + 1];
-    const T* X = xs[l + 1];
-    for (int q = threadIdx.x; q < n1 * n1; q += kVFThreads) {
-      const int gi = q % n1 + 1, gj = q / n1 + 1;
-      T v;
-      if ((gi & 1) == 0 && (gj & 1) == 0) {
-        v = X[(gj / 2 - 1) * n1c + gi / 2 - 1];
-      } else if ((gi & 1) == 0) {
-        v = T(0.5) * (ldc(X, gi / 2 - 1, (gj - 1) / 2 - 1, n1c) + ldc(X, gi / 2 - 1, (gj + 1) / 2 - 1, n1c));
-      } else if ((gj & 1) == 0) {
-        v = T(0.5) * (ldc(X, (gi - 1) / 2 - 1, gj / 2 - 1, n1c) + ldc(X, (gi + 1) / 2 - 1, gj / 2 - 1, n1c));
-      } else {
-        v = T(0.25) * ((ldc(X, (gi - 1) / 2 - 1, (gj - 1) / 2 - 1, n1c) + ldc(X, (gi + 1) / 2 - 1, (gj - 1) / 2 - 1, n1c)) +
-                       (ldc(X, (gi - 1) / 2 - 1, (gj + 1) / 2 - 1, n1c) + ldc(X, (gi + 1) / 2 - 1, (gj + 1) / 2 - 1, n1c)));
-      }
-      xs[l][q] += v;
-    }
+    const int np = vf_padded(n1);
+    T* xa = base + vf_level_off(L, l);
+    T* xb = xa + np;
+    const T* bl = xb + np;
+    const T* xca = base + vf_level_off(L, l + 1);
+    const T* xc = cur_l[l + 1] == 0 ? xca : xca + vf_padded(n1c);
+    int cur = cur_l[l];
+    prolong_pass<T>(xc, cur == 0 ? xa : xb, n1, n1c);
     __syncthreads();
     const T d = T(L.diag[l]), e = T(L.edge[l]), c = T(L.corner[l]);
+    const T wd = omega / d;
 #pragma unroll 1
-    for (int s = 0; s < nu; ++s) strip_sweep(xs[l], bs[l], n1, d, e, c, omega, false);
-  }
-  for (int q = threadIdx.x; q < n0; q += kVFThreads) {
-    if (acc) {
-      const int64_t t = col / acc_L, cc = col % acc_L;
-      acc[t * acc_ss + (acc_col0 + cc) * int64_t(n0) + q] += xs[0][q];
-    } else {
-      xg[col * n0 + q] = xs[0][q];
+    for (int sw = 0; sw < nu; ++sw) {
+      const T* src = cur == 0 ? xa : xb;
+      T* dst = cur == 0 ? xb : xa;
+      if (l == 0) strip_pass<T, 0>(src, dst, bv, g, n1, d, e, c, wd);
+      else point_pass<T, 0>(src, dst, bl, n1, d, e, c, wd);
+      cur ^= 1;
+      __syncthreads();
     }
+    cur_l[l] = cur;
+  }
+  const T* x0 = base + (cur_l[0] == 0 ? 0 : size_t(vf_padded(n10)));
+  const int s0 = n10 + 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  if (acc) {
+    T* A = acc + (col / acc_L) * acc_ss + (acc_col0 + col % acc_L) * int64_t(n0);
+    for (int y = ty; y < n10; y += 32)
+      for (int x = tx; x < n10; x += 32) A[y * n10 + x] += x0[(y + 1) * s0 + x + 1];
+  } else {
+    T* X = xg + col * n0;
+    for (int y = ty; y < n10; y += 32)
+      for (int x = tx; x < n10; x += 32) X[y * n10 + x] = x0[(y + 1) * s0 + x + 1];
   }
 }
 
 size_t vcycle_full_smem(const FusedLevels& L, int esize) {
   size_t s = 0;
-  for (int l = 0; l < L.nlev; ++l) s += size_t(L.n1[l]) * L.n1[l] * (l > 0 ? 3 : 2) * esize;
+  for (int l = 0; l < L.nlev; ++l) s += size_t(L.n1[l] + 2) * (L.n1[l] + 2) * (l > 0 ? 3 : 2) * esize;
   return s;
 }
 

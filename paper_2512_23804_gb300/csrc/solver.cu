@@ -634,6 +634,9 @@ struct SolveTask {
     t0 = std::chrono::steady_clock::now();
     pb = p; ws = d_ws; x0 = d_x0; x_out = d_x; st = s;
     result = sgoc_result{};
+    status = SGOC_OK;
+    bnorm = target = rn = 0;
+    j = jin = par = outer = total = last_flag = 0;
     carve_layout(pb, pb->opt.precision, d_ws, ws_bytes, L);
     SGOC_TRY(runtime_of(pb, &rt));
     graphs = !profile_enabled();
