@@ -43,6 +43,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip fp64/e2e/profile/matvec legs")
     ap.add_argument("--sequential", action="store_true", help="solve the batch one problem at a time")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving stream: the first --requests seeded requests through the server")
+    ap.add_argument("--requests", type=int, default=40)
+    ap.add_argument("--max-unknowns", type=float, default=6e7,
+                    help="serving: skip requests with more KKT unknowns (device memory and run time)")
     ap.add_argument("--kernel-case", choices=["vcycle128", "sg128", "sg512", "hgs128"], default=None,
                     help="run one kernel class a few times on a small case (for ncu captures) and exit")
     return ap.parse_args()
@@ -389,6 +394,31 @@ def run_ours(args):
             del sp
         line["sg_matvec"] = mv
 
+    if not args.no_extras and rank == 0:
+        # the other workload shapes: one timed solve each (after a warm-up solve), mixed and float64
+        ow = {}
+        for name, mk in (("steady_16x16_M2_p2", si.steady_16), ("time_64x64_M4_p3_nt32", si.time_64),
+                         ("steady_512x512_M8_p3", si.steady_512)):
+            pr = mk()
+            rec = {"kkt_unknowns": pr.kkt_size}
+            for prec in ("mixed", "fp64"):
+                sp = SGProblem.from_problem(pr, precision=prec).upload()
+                x, _ = sp.solve()
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                x, info = sp.solve(out=x)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                rec[prec] = {"ms": ms, "solves_per_s": 1e3 / ms, "iterations": info["iterations"],
+                             "outer": info["outer_iterations"], "rel_residual": info["rel_true_residual"]}
+                del sp, x
+                torch.cuda.empty_cache()
+            ow[name] = rec
+        line["other_workloads"] = ow
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample = cpu_baseline_value(iters_sample=3, betas=(1e-4,))
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
@@ -426,10 +456,87 @@ def run_kernel_case(args):
     print(json.dumps({"kernel_case": case, "ok": True}))
 
 
+def run_serve(args):
+    """Serving stream: requests arrive as a Poisson process (rate calibrated at 80% of
+    the saturated throughput), are admitted by memory footprint, and are solved to a
+    1e-8 float64 residual in mixed precision; reported beside sequential float64
+    solves of the same requests on the same GPU."""
+    import numpy as np
+    import torch
+    import sg_inputs as si
+    from paper_2512_23804_gb300 import SGProblem, SGServer, build
+    build.build()
+    reqs, skipped = [], 0
+    i = 0
+    while len(reqs) < args.requests:
+        pr = si.serving_request(i)
+        i += 1
+        if pr.kkt_size > args.max_unknowns:
+            skipped += 1
+            continue
+        reqs.append(pr)
+    pool_bytes = int(min(torch.cuda.mem_get_info()[0] * 0.6, 120e9))
+
+    def run_stream(arrivals, label):
+        sv = SGServer(pool_bytes=pool_bytes, max_active=16)
+        sps = [SGProblem.from_problem(pr, precision="mixed") for pr in reqs]
+        done, lat = {}, {}
+        t0 = time.perf_counter()
+        nxt = 0
+        while len(done) < len(reqs):
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and arrivals[nxt] <= now:
+                sv.submit(sps[nxt], nxt)
+                nxt += 1
+            if sv.pending == 0:
+                time.sleep(max(0.0, min(arrivals[nxt] - now, 0.01)))
+                continue
+            sv.step()
+            for rid, x, info in sv.poll():
+                assert info["status_name"] == "SGOC_OK" and info["rel_true_residual"] <= 1e-8, info
+                done[rid] = info
+                lat[rid] = info["ms_total"]
+        wall = time.perf_counter() - t0
+        stats = sv.stats()
+        l = sorted(lat.values())
+        return {"solves_per_s": len(reqs) / wall, "wall_s": wall,
+                "p50_ms": l[len(l) // 2], "p99_ms": l[min(len(l) - 1, int(math.ceil(0.99 * len(l))) - 1)],
+                "pool_high_water_GB": stats["pool_high_water"] / 1e9, "admitted": stats["admitted"]}
+
+    # saturation: everything arrives at t = 0 -> capacity mu
+    sat = run_stream([0.0] * len(reqs), "saturated")
+    mu = sat["solves_per_s"]
+    rng = np.random.default_rng([5, 2**31])            # the arrival stream of master seed 5
+    gaps = rng.exponential(1.0 / (0.8 * mu), size=len(reqs))
+    arrivals = list(np.cumsum(gaps) - gaps[0])
+    open_loop = run_stream(arrivals, "poisson")
+    # sequential plain float64 solves of the same requests
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq_lat = []
+    for pr in reqs:
+        sp = SGProblem.from_problem(pr, precision="fp64")
+        t1 = time.perf_counter()
+        x, info = sp.solve()
+        seq_lat.append((time.perf_counter() - t1) * 1e3)
+        del sp, x
+    seq_wall = time.perf_counter() - t0
+    sl = sorted(seq_lat)
+    line = {"mode": "serve", "requests": len(reqs), "skipped_over_cap": skipped,
+            "max_unknowns": args.max_unknowns, "saturated": sat, "poisson_at_0.8mu": open_loop,
+            "sequential_fp64": {"solves_per_s": len(reqs) / seq_wall,
+                                "p50_ms": sl[len(sl) // 2], "p99_ms": sl[-1]},
+            "speedup_vs_sequential_fp64": sat["solves_per_s"] / (len(reqs) / seq_wall)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.kernel_case:
         run_kernel_case(args)
+        return
+    if args.serve:
+        run_serve(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -4,6 +4,7 @@
 // iy*n1 + ix; element (ex, ey), 0 <= ex, ey < nx.  Interior node (ix, iy) is the
 // north-east corner of element (ix, iy), the north-west corner of (ix+1, iy), the
 // south-west corner of (ix+1, iy+1) and the south-east corner of (ix, iy+1).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -120,7 +121,7 @@ __device__ __forceinline__ T dot4(const typename Vec4<T>::type& a, const typenam
 //            (and the mass stencil value of the output columns)
 //   phase 2: out(beta) = sum_e kappa_0(e) T_e(beta) + sum_{(alpha,k,c)} c sum_e kappa_k(e) T_e(alpha)
 // ---------------------------------------------------------------------------
-constexpr int kSGThreads = 256;
+constexpr int kSGThreads = 512;
 
 // asynchronous global->shared copy of one element; invalid elements are zero-filled
 template <typename T>
@@ -137,9 +138,10 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
 // SG operator kernel: one CTA walks rows [r0, r1) of one TX-wide x-tile of one
-// slab.  A ring of four X row panels (input columns [in0, in1), TX+2 nodes with
-// halo) lives in shared memory; row iy+2 is prefetched with cp.async while row
-// iy is computed, so every X element is read once per CTA.
+// slab.  A ring of three X row panels (input columns [in0, in1), TX+2 nodes with
+// halo) lives in shared memory; once the element terms of row iy are formed,
+// row iy+2 is fetched with cp.async into the slot of row iy-1 while the
+// contraction of row iy runs, so every X element is read once per CTA.
 //   phase 1: kappa_k(e)/6 of the row's elements; T_e(alpha) for every node and
 //            input column (and the mass stencil of the output columns)
 //   phase 2: out(beta) = sum_e kappa_0(e) T_e(beta) + sum_{(alpha,k,c)} c sum_e kappa_k(e) T_e(alpha)
@@ -149,7 +151,7 @@ template <> struct __align__(16) NbrEntry<float> { int ts, ks; float c; int pad;
 template <> struct __align__(16) NbrEntry<double> { int ts, ks; double c; };
 
 template <typename T, int TX>
-__global__ void __launch_bounds__(kSGThreads) sg_kernel(SGArgs<T> a, int rows_per_cta) {
+__global__ void __launch_bounds__(kSGThreads, 2) sg_kernel(SGArgs<T> a, int rows_per_cta) {
   using V4 = typename Vec4<T>::type;
   extern __shared__ __align__(32) unsigned char sg_smem_raw[];
   constexpr int W = TX + 2;
@@ -159,8 +161,11 @@ __global__ void __launch_bounds__(kSGThreads) sg_kernel(SGArgs<T> a, int rows_pe
   V4* Ts = reinterpret_cast<V4*>(sg_smem_raw);               // [nin][TX]
   V4* Ks = Ts + size_t(nin) * TX;                            // [M+1][TX]
   T* Ms = reinterpret_cast<T*>(Ks + size_t(a.M + 1) * TX);   // [nout][TX] (when cm != 0)
-  T* Xr = Ms + (use_m ? size_t(nout) * TX : 0);              // ring [4][nin][W]
-  NbrEntry<T>* Es = reinterpret_cast<NbrEntry<T>*>(Xr + size_t(4) * nin * W);  // [nnz_out]
+  T* Xr = Ms + (use_m ? size_t(nout) * TX : 0);              // ring [3][nin][W]
+  // the 16-byte table entries start at the next 16-byte boundary after the ring
+  const size_t es_off = (size_t(reinterpret_cast<unsigned char*>(Xr + size_t(3) * nin * W) - sg_smem_raw) + 15) &
+                        ~size_t(15);
+  NbrEntry<T>* Es = reinterpret_cast<NbrEntry<T>*>(sg_smem_raw + es_off);       // [nnz_out]
   int* Ps = reinterpret_cast<int*>(Es + a.nnz_out);          // [nout] first entry of each output column
   int* Pe = Ps + nout;                                       // [nout] end of its entries with k < kmax
 
@@ -174,9 +179,9 @@ __global__ void __launch_bounds__(kSGThreads) sg_kernel(SGArgs<T> a, int rows_pe
   const size_t ring_stride = size_t(nin) * W;
   if (r0 >= r1) return;
 
-  // row gy (-1 and n1 give zeros) into ring slot (gy + 1) & 3
+  // row gy (-1 and n1 give zeros) into ring slot (gy + 1) % 3
   auto issue_row = [&](int gy) {
-    T* dst = Xr + size_t((gy + 1) & 3) * ring_stride;
+    T* dst = Xr + size_t((gy + 1) % 3) * ring_stride;
     const bool rok = gy >= 0 && gy < n1;
     for (int q = tid; q < nin * W; q += kSGThreads) {
       const int c = q / W, lx = q - c * W;
@@ -202,16 +207,13 @@ __global__ void __launch_bounds__(kSGThreads) sg_kernel(SGArgs<T> a, int rows_pe
     Es[q] = en;
   }
   for (int q = tid; q < nout; q += kSGThreads) {
-    const int e0 = a.nbr_ptr[a.out0 + q], e1 = a.nbr_ptr[a.out0 + q + 1];
-    int e = e0;
-    while (e < e1 && a.nbr_k[e] < a.kmax) ++e;
-    Ps[q] = e0 - ebase;
-    Pe[q] = e - ebase;
+    Ps[q] = a.nbr_ptr[a.out0 + q] - ebase;
+    Pe[q] = a.nbr_end[a.out0 + q] - ebase;        // entries with k < kmax (host-computed)
   }
 
   for (int iy = r0; iy < r1; ++iy) {
-    // prefetch the row the next output row needs, then wait for this row's three
-    if (iy + 1 < r1) { issue_row(iy + 2); cp_async_commit(); cp_async_wait<1>(); } else { cp_async_wait<0>(); }
+    cp_async_wait<0>();
+    __syncthreads();                                   // rows iy-1..iy+1 landed; previous contraction done
     for (int q = tid; q < (a.M + 1) * TX; q += kSGThreads) {
       const int kk = q / TX, lx = q - kk * TX;
       const int ix = min(ix0 + lx, n1 - 1);
@@ -223,10 +225,9 @@ __global__ void __launch_bounds__(kSGThreads) sg_kernel(SGArgs<T> a, int rows_pe
       v.w = kp[int64_t(iy + 1) * a.nx + ix];        // NW element (ix, iy+1)
       Ks[kk * TX + lx] = v;
     }
-    __syncthreads();
-    const T* rS = Xr + size_t(iy & 3) * ring_stride;         // row iy-1
-    const T* rC = Xr + size_t((iy + 1) & 3) * ring_stride;   // row iy
-    const T* rN = Xr + size_t((iy + 2) & 3) * ring_stride;   // row iy+1
+    const T* rS = Xr + size_t(iy % 3) * ring_stride;         // row iy-1
+    const T* rC = Xr + size_t((iy + 1) % 3) * ring_stride;   // row iy
+    const T* rN = Xr + size_t((iy + 2) % 3) * ring_stride;   // row iy+1
     for (int q = tid; q < nin * TX; q += kSGThreads) {
       const int c = q / TX, lx = q - c * TX;
       const size_t o = size_t(c) * W + lx;
@@ -248,7 +249,8 @@ __global__ void __launch_bounds__(kSGThreads) sg_kernel(SGArgs<T> a, int rows_pe
         Ms[size_t(col - a.out0) * TX + lx] = a.mass * fma(T(16), C, fma(T(4), edges, corners));
       }
     }
-    __syncthreads();
+    __syncthreads();                                   // element terms ready; row iy-1 no longer needed
+    if (iy + 1 < r1) { issue_row(iy + 2); cp_async_commit(); }
     for (int q = tid; q < nout * TX; q += kSGThreads) {
       const int lx = q % TX, bl = q / TX;
       const int ix = ix0 + lx;
@@ -270,8 +272,8 @@ __global__ void __launch_bounds__(kSGThreads) sg_kernel(SGArgs<T> a, int rows_pe
       if (a.cy != T(0)) out = fma(a.cy, *yp, out);
       *yp = out;
     }
-    __syncthreads();                                    // Ts, Ks and the oldest ring slot are reused
   }
+  cp_async_wait<0>();
 }
 
 template <typename T, int TX>
@@ -279,7 +281,7 @@ static size_t sg_smem(const SGArgs<T>& a) {
   using V4 = typename Vec4<T>::type;
   const size_t nin = a.in1 - a.in0, nout = a.out1 - a.out0;
   size_t b = sizeof(V4) * (nin * TX + size_t(a.M + 1) * TX) +
-             sizeof(T) * ((a.cm != T(0) ? nout * TX : 0) + 4 * nin * (TX + 2));
+             sizeof(T) * ((a.cm != T(0) ? nout * TX : 0) + 3 * nin * (TX + 2));
   b = (b + 15) & ~size_t(15);
   return b + 16 * size_t(a.nnz_out) + sizeof(int) * 2 * nout;
 }
@@ -289,9 +291,9 @@ static cudaError_t launch_sg_tx(const SGArgs<T>& a, size_t smem, cudaStream_t st
   cudaError_t e = cudaFuncSetAttribute(sg_kernel<T, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   const int xt = (a.n1 + TX - 1) / TX;
-  const int per_sm = std::max(1, int((228 * 1024) / (smem + 1024)));
-  // about two CTAs per resident slot of the GPU
-  const int64_t want = int64_t(152) * per_sm * 2;
+  const int per_sm = std::max(1, std::min(2, int((228 * 1024) / (smem + 1024))));
+  // about one CTA per resident slot of the GPU: rows per CTA amortise the set-up
+  const int64_t want = int64_t(152) * per_sm;
   const int64_t tiles = int64_t(xt) * a.nslabs;
   int rows = int(std::max<int64_t>(1, (tiles * a.n1 + want - 1) / want));
   rows = std::min(rows, a.n1);
@@ -622,12 +624,6 @@ constexpr int kStripRows = 16;
 
 __device__ __forceinline__ int vf_padded(int n1) { return (n1 + 2) * (n1 + 2); }
 
-// shared-memory offset (elements) of level l
-__device__ __forceinline__ size_t vf_level_off(const FusedLevels& L, int l) {
-  size_t o = 0;
-  for (int q = 0; q < l; ++q) o += size_t(vf_padded(L.n1[q])) * (q > 0 ? 3 : 2);
-  return o;
-}
 
 struct Strip {
   int x, y0, y1;   // column and interior rows [y0, y1) of this thread; x < 0: idle
@@ -681,13 +677,25 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ xs, T* __restri
   }
 }
 
-// Coarse-level pass (point parallel): Jacobi / from zero / residual against b in shared memory.
+// threads taking part in the passes of a level with n1 interior nodes per side
+__device__ __forceinline__ int vf_group(int n1) { return n1 >= 63 ? kVFThreads : (n1 >= 15 ? 256 : 32); }
+
+__device__ __forceinline__ void vf_sync(int nt) {
+  if (nt == kVFThreads) __syncthreads();
+  else if (nt > 32) asm volatile("bar.sync 1, %0;\n" ::"r"(nt) : "memory");
+  else __syncwarp();
+}
+
+template <typename T>
+struct VFLevel { int off, n1, grp; T d, e, c, wd; };
+
+// Coarse-level pass on a group of nt threads (point parallel, 32 x (nt/32) grid).
 template <typename T, int MODE>
-__device__ __forceinline__ void point_pass(const T* __restrict__ xs, T* __restrict__ xd, const T* __restrict__ b,
-                                          int n1, T d, T e, T c, T wd) {
+__device__ __forceinline__ void group_pass(const T* __restrict__ xs, T* __restrict__ xd, const T* __restrict__ b,
+                                          int n1, int nt, T d, T e, T c, T wd) {
   const int s = n1 + 2;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int y = ty; y < n1; y += 32)
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, sy = nt >> 5;
+  for (int y = ty; y < n1; y += sy)
     for (int x = tx; x < n1; x += 32) {
       const int o = (y + 1) * s + x + 1;
       if (MODE == 1) { xd[o] = wd * b[o]; continue; }
@@ -698,12 +706,11 @@ __device__ __forceinline__ void point_pass(const T* __restrict__ xs, T* __restri
     }
 }
 
-// full weighting: coarse interior (I, J) = fine interior (2I+1, 2J+1) = fine padded (2I+2, 2J+2)
 template <typename T>
-__device__ __forceinline__ void restrict_pass(const T* __restrict__ R, T* __restrict__ bc, int n1, int n1c) {
+__device__ __forceinline__ void group_restrict(const T* __restrict__ R, T* __restrict__ bc, int n1, int n1c, int nt) {
   const int s = n1 + 2, sc = n1c + 2;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int J = ty; J < n1c; J += 32)
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, sy = nt >> 5;
+  for (int J = ty; J < n1c; J += sy)
     for (int I = tx; I < n1c; I += 32) {
       const T* r = R + (2 * J + 2) * s + 2 * I + 2;
       const T cen = r[0];
@@ -713,13 +720,11 @@ __device__ __forceinline__ void restrict_pass(const T* __restrict__ R, T* __rest
     }
 }
 
-// bilinear interpolation added to the fine iterate; fine grid node g = i + 1 takes
-// coarse padded nodes g >> 1 and (g + 1) >> 1 (equal when g is even); borders are zero
 template <typename T>
-__device__ __forceinline__ void prolong_pass(const T* __restrict__ Xc, T* __restrict__ xf, int n1, int n1c) {
+__device__ __forceinline__ void group_prolong(const T* __restrict__ Xc, T* __restrict__ xf, int n1, int n1c, int nt) {
   const int s = n1 + 2, sc = n1c + 2;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int j = ty; j < n1; j += 32) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, sy = nt >> 5;
+  for (int j = ty; j < n1; j += sy) {
     const int gj = j + 1;
     const T* r0 = Xc + (gj >> 1) * sc;
     const T* r1 = Xc + ((gj + 1) >> 1) * sc;
@@ -736,24 +741,34 @@ __global__ void __launch_bounds__(kVFThreads, 1) vcycle_full_kernel(const T* __r
                                                                     T omega, int nu, T* acc, int64_t acc_ss,
                                                                     int acc_L, int acc_col0) {
   extern __shared__ __align__(32) unsigned char vf_smem_raw[];
+  __shared__ VFLevel<T> lv[13];
+  __shared__ int curs[13];
   T* base = reinterpret_cast<T*>(vf_smem_raw);
   const int64_t col = blockIdx.x;
-  const int n10 = L.n1[0];
+  const int nlev = L.nlev;
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int l = 0; l < nlev; ++l) {
+      const int n1 = L.n1[l];
+      lv[l].off = o; lv[l].n1 = n1; lv[l].grp = vf_group(n1);
+      lv[l].d = T(L.diag[l]); lv[l].e = T(L.edge[l]); lv[l].c = T(L.corner[l]);
+      lv[l].wd = omega / T(L.diag[l]);
+      o += (n1 + 2) * (n1 + 2) * (l > 0 ? 3 : 2);
+    }
+  }
+  __syncthreads();
+  const int n10 = lv[0].n1;
   const int n0 = n10 * n10;
   // zero borders of every array (interiors are always written before they are read)
-  for (int l = 0; l < L.nlev; ++l) {
-    const int n1 = L.n1[l], s = n1 + 2;
-    T* a = base + vf_level_off(L, l);
+  for (int l = 0; l < nlev; ++l) {
+    const int n1 = lv[l].n1, s = n1 + 2, per = 4 * (n1 + 1);
+    T* a = base + lv[l].off;
     const int narr = l > 0 ? 3 : 2;
-    for (int q = threadIdx.x; q < narr * 4 * (n1 + 1); q += kVFThreads) {
-      const int arr = q / (4 * (n1 + 1)), k = q - arr * 4 * (n1 + 1);
-      T* A = a + size_t(arr) * s * s;
+    for (int q = threadIdx.x; q < narr * per; q += kVFThreads) {
+      const int arr = q / per, k = q - arr * per;
+      T* A = a + arr * s * s;
       const int side = k / (n1 + 1), pos = k - side * (n1 + 1);
-      int o;
-      if (side == 0) o = pos;                               // top row, columns 0..n1
-      else if (side == 1) o = (n1 + 1) * s + pos + 1;       // bottom row, columns 1..n1+1
-      else if (side == 2) o = (pos + 1) * s;                // left column, rows 1..n1+1
-      else o = pos * s + n1 + 1;                            // right column, rows 0..n1
+      const int o = side == 0 ? pos : side == 1 ? (n1 + 1) * s + pos + 1 : side == 2 ? (pos + 1) * s : pos * s + n1 + 1;
       A[o] = T(0);
     }
   }
@@ -768,82 +783,84 @@ __global__ void __launch_bounds__(kVFThreads, 1) vcycle_full_kernel(const T* __r
     }
   }
   __syncthreads();
-  int cur_l[13];
+  // descent
 #pragma unroll 1
-  for (int l = 0; l < L.nlev - 1; ++l) {
-    const int n1 = L.n1[l], n1c = L.n1[l + 1];
-    const int np = vf_padded(n1);
-    T* xa = base + vf_level_off(L, l);
+  for (int l = 0; l < nlev - 1; ++l) {
+    const VFLevel<T> P = lv[l];
+    const int nt = P.grp;
+    if (threadIdx.x >= nt) break;                         // this thread waits at the ascent
+    const int n1 = P.n1, n1c = lv[l + 1].n1;
+    const int np = (n1 + 2) * (n1 + 2);
+    T* xa = base + P.off;
     T* xb = xa + np;
-    const T* bl = xb + np;                                   // levels >= 1
-    const T d = T(L.diag[l]), e = T(L.edge[l]), c = T(L.corner[l]);
-    const T wd = omega / d;
+    const T* bl = xb + np;
     int cur = 0;
     if (nu == 0) {
-      for (int q = threadIdx.x; q < np; q += kVFThreads) xa[q] = T(0);
-      __syncthreads();
+      for (int q = threadIdx.x; q < np; q += nt) xa[q] = T(0);
+      vf_sync(nt);
     }
 #pragma unroll 1
     for (int sw = 0; sw < nu; ++sw) {
       const T* src = cur == 0 ? xa : xb;
       T* dst = sw == 0 ? xa : (cur == 0 ? xb : xa);
       if (l == 0) {
-        if (sw == 0) strip_pass<T, 1>(src, dst, bv, g, n1, d, e, c, wd);
-        else strip_pass<T, 0>(src, dst, bv, g, n1, d, e, c, wd);
+        if (sw == 0) strip_pass<T, 1>(src, dst, bv, g, n1, P.d, P.e, P.c, P.wd);
+        else strip_pass<T, 0>(src, dst, bv, g, n1, P.d, P.e, P.c, P.wd);
       } else {
-        if (sw == 0) point_pass<T, 1>(src, dst, bl, n1, d, e, c, wd);
-        else point_pass<T, 0>(src, dst, bl, n1, d, e, c, wd);
+        if (sw == 0) group_pass<T, 1>(src, dst, bl, n1, nt, P.d, P.e, P.c, P.wd);
+        else group_pass<T, 0>(src, dst, bl, n1, nt, P.d, P.e, P.c, P.wd);
       }
       cur = dst == xa ? 0 : 1;
-      __syncthreads();
+      vf_sync(nt);
     }
     const T* xcur = cur == 0 ? xa : xb;
     T* rbuf = cur == 0 ? xb : xa;
-    if (l == 0) strip_pass<T, 2>(xcur, rbuf, bv, g, n1, d, e, c, wd);
-    else point_pass<T, 2>(xcur, rbuf, bl, n1, d, e, c, wd);
-    __syncthreads();
-    T* bc = base + vf_level_off(L, l + 1) + 2 * size_t(vf_padded(n1c));
-    restrict_pass<T>(rbuf, bc, n1, n1c);
-    cur_l[l] = cur;
-    __syncthreads();
+    if (l == 0) strip_pass<T, 2>(xcur, rbuf, bv, g, n1, P.d, P.e, P.c, P.wd);
+    else group_pass<T, 2>(xcur, rbuf, bl, n1, nt, P.d, P.e, P.c, P.wd);
+    vf_sync(nt);
+    T* bc = base + lv[l + 1].off + 2 * (n1c + 2) * (n1c + 2);
+    group_restrict<T>(rbuf, bc, n1, n1c, nt);
+    if (threadIdx.x == 0) curs[l] = cur;
+    vf_sync(nt);
   }
-  {
-    // coarsest level: a single node (n1 = 1) solved exactly, or (one level only) n1 = 1 at the top
-    const int l = L.nlev - 1;
-    T* xa = base + vf_level_off(L, l);
-    if (threadIdx.x == 0) {
-      const T bq = l == 0 ? bv[0] : xa[2 * vf_padded(L.n1[l]) + 4];   // interior (0,0) sits at padded 4
-      xa[4] = bq / T(L.diag[l]);
-    }
-    cur_l[l] = 0;
-    __syncthreads();
+  // coarsest level: one node, solved exactly (thread 0 of the smallest group)
+  if (threadIdx.x == 0) {
+    const int l = nlev - 1;
+    T* xa = base + lv[l].off;
+    const T bq = l == 0 ? bv[0] : xa[2 * 9 + 4];          // padded 3 x 3: interior at 4
+    xa[4] = bq / lv[l].d;
+    curs[l] = 0;
   }
+  // ascent: a level's group waits for the coarser level's (smaller) group
 #pragma unroll 1
-  for (int l = L.nlev - 2; l >= 0; --l) {
-    const int n1 = L.n1[l], n1c = L.n1[l + 1];
-    const int np = vf_padded(n1);
-    T* xa = base + vf_level_off(L, l);
+  for (int l = nlev - 2; l >= 0; --l) {
+    const VFLevel<T> P = lv[l];
+    const int nt = P.grp;
+    if (threadIdx.x >= nt) continue;
+    vf_sync(nt);
+    const int n1 = P.n1, n1c = lv[l + 1].n1;
+    const int np = (n1 + 2) * (n1 + 2);
+    T* xa = base + P.off;
     T* xb = xa + np;
     const T* bl = xb + np;
-    const T* xca = base + vf_level_off(L, l + 1);
-    const T* xc = cur_l[l + 1] == 0 ? xca : xca + vf_padded(n1c);
-    int cur = cur_l[l];
-    prolong_pass<T>(xc, cur == 0 ? xa : xb, n1, n1c);
-    __syncthreads();
-    const T d = T(L.diag[l]), e = T(L.edge[l]), c = T(L.corner[l]);
-    const T wd = omega / d;
+    const T* xca = base + lv[l + 1].off;
+    const T* xc = curs[l + 1] == 0 ? xca : xca + (n1c + 2) * (n1c + 2);
+    int cur = curs[l];
+    group_prolong<T>(xc, cur == 0 ? xa : xb, n1, n1c, nt);
+    vf_sync(nt);
 #pragma unroll 1
     for (int sw = 0; sw < nu; ++sw) {
       const T* src = cur == 0 ? xa : xb;
       T* dst = cur == 0 ? xb : xa;
-      if (l == 0) strip_pass<T, 0>(src, dst, bv, g, n1, d, e, c, wd);
-      else point_pass<T, 0>(src, dst, bl, n1, d, e, c, wd);
+      if (l == 0) strip_pass<T, 0>(src, dst, bv, g, n1, P.d, P.e, P.c, P.wd);
+      else group_pass<T, 0>(src, dst, bl, n1, nt, P.d, P.e, P.c, P.wd);
       cur ^= 1;
-      __syncthreads();
+      vf_sync(nt);
     }
-    cur_l[l] = cur;
+    if (threadIdx.x == 0) curs[l] = cur;
   }
-  const T* x0 = base + (cur_l[0] == 0 ? 0 : size_t(vf_padded(n10)));
+  __syncthreads();
+  const T* x0 = base + (curs[0] == 0 ? 0 : (n10 + 2) * (n10 + 2));
   const int s0 = n10 + 2;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   if (acc) {
@@ -882,6 +899,339 @@ cudaError_t launch_vcycle_full(const T* b, T* x, int64_t B, const FusedLevels& L
                double(B) * n0 * (4.0 / 3.0) * (21.0 * 2 * nu + 18.0 + 10.0));
   vcycle_full_kernel<T><<<dim3(unsigned(B)), kVFThreads, smem, st>>>(b, x, L, omega, nu, acc, acc_ss, acc_L, acc_col0);
   note_launch();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Cluster V-cycle: one thread-block cluster of C CTAs per column.  The fine
+// levels ("distributed", band height B_l = (n1_l + 1) / C >= kMinBand rows)
+// are split into horizontal bands, one per CTA; each band array carries one
+// halo row above and below, filled from the neighbouring CTAs' shared memory
+// (DSMEM) after a cluster barrier whenever a pass reads neighbours.  The first
+// level below the distributed ones is gathered into every CTA, and the
+// remaining small levels are solved redundantly (identically) in each CTA.
+// Local band row i of rank r holds global row r*B + i - 1; the last rank's
+// row B is the Dirichlet boundary and stays zero.
+// ---------------------------------------------------------------------------
+constexpr int kVCThreads = 512;
+constexpr int kMinBand = 8;
+constexpr int kCStrip = 16;
+
+template <typename T>
+struct VCLevel { int off, n1, band, rows, s; T d, e, c, wd; };
+
+template <typename T, int MODE>   // 0 jacobi, 1 from zero, 2 residual; b in smem (band layout)
+__device__ __forceinline__ void band_pass(const T* __restrict__ xs, T* __restrict__ xd, const T* __restrict__ b,
+                                         int rows, int n1, int s, T d, T e, T c, T wd) {
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int i = 1 + ty; i <= rows; i += kVCThreads / 32)
+    for (int x = tx; x < n1; x += 32) {
+      const int o = i * s + x + 1;
+      if (MODE == 1) { xd[o] = wd * b[o]; continue; }
+      const T edges = (xs[o - s] + xs[o + s]) + (xs[o - 1] + xs[o + 1]);
+      const T corners = (xs[o - s - 1] + xs[o - s + 1]) + (xs[o + s - 1] + xs[o + s + 1]);
+      const T r = b[o] - fma(d, xs[o], fma(e, edges, c * corners));
+      xd[o] = MODE == 2 ? r : fma(wd, r, xs[o]);
+    }
+}
+
+// level-0 strip pass with the right-hand side in registers (strip of `cr` rows)
+template <typename T, int MODE>
+__device__ __forceinline__ void cstrip_pass(const T* __restrict__ xs, T* __restrict__ xd, const T (&bv)[kCStrip],
+                                           int x, int i0, int cr, int s, T d, T e, T c, T wd) {
+  if (x < 0) return;
+  if (MODE == 1) {
+#pragma unroll
+    for (int j = 0; j < kCStrip; ++j)
+      if (j < cr) xd[(i0 + j) * s + x + 1] = wd * bv[j];
+    return;
+  }
+  const T* p = xs + (i0 - 1) * s + x;
+  T wm0 = p[0], wc0 = p[1], wp0 = p[2];
+  p += s;
+  T wm1 = p[0], wc1 = p[1], wp1 = p[2];
+  T* q = xd + i0 * s + x + 1;
+#pragma unroll
+  for (int j = 0; j < kCStrip; ++j) {
+    if (j < cr) {
+      p += s;
+      const T wm2 = p[0], wc2 = p[1], wp2 = p[2];
+      const T edges = (wc0 + wc2) + (wm1 + wp1);
+      const T corners = (wm0 + wp0) + (wm2 + wp2);
+      const T r = bv[j] - fma(d, wc1, fma(e, edges, c * corners));
+      *q = MODE == 2 ? r : fma(wd, r, wc1);
+      q += s;
+      wm0 = wm1; wc0 = wc1; wp0 = wp1;
+      wm1 = wm2; wc1 = wc2; wp1 = wp2;
+    }
+  }
+}
+
+// fill the halo rows of band array X from the neighbouring CTAs (caller: cluster.sync() before)
+template <typename T>
+__device__ __forceinline__ void band_exchange(T* X, int band, int s, int rank, int C) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  if (rank > 0) {
+    const T* up = cl.map_shared_rank(X, rank - 1);
+    for (int q = threadIdx.x; q < s; q += kVCThreads) X[q] = up[band * s + q];
+  }
+  if (rank < C - 1) {
+    const T* dn = cl.map_shared_rank(X, rank + 1);
+    for (int q = threadIdx.x; q < s; q += kVCThreads) X[(band + 1) * s + q] = dn[s + q];
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kVCThreads) vcycle_cluster_kernel(const T* __restrict__ bg, T* xg,
+                                                                    ClusterLevels L, T omega, int nu, T* acc,
+                                                                    int64_t acc_ss, int acc_L, int acc_col0) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(32) unsigned char vc_smem_raw[];
+  __shared__ VCLevel<T> lv[13];
+  __shared__ int curs[13];
+  T* base = reinterpret_cast<T*>(vc_smem_raw);
+  const int C = int(cl.num_blocks());
+  const int rank = int(cl.block_rank());
+  const int64_t col = blockIdx.x / C;
+  const int nlev = L.nlev, nd = L.nd;
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int l = 0; l < nlev; ++l) {
+      const int n1 = L.n1[l], s = n1 + 2;
+      lv[l].n1 = n1; lv[l].s = s; lv[l].off = o;
+      if (l < nd) {
+        const int band = (n1 + 1) / C;
+        lv[l].band = band;
+        lv[l].rows = min(band, n1 - rank * band);          // valid rows of this rank
+        o += (band + 2) * s * (l > 0 ? 3 : 2);
+      } else {
+        lv[l].band = n1; lv[l].rows = n1;
+        o += s * s * 3;
+      }
+      lv[l].d = T(L.diag[l]); lv[l].e = T(L.edge[l]); lv[l].c = T(L.corner[l]);
+      lv[l].wd = omega / T(L.diag[l]);
+    }
+    curs[0] = o;                                           // total elements (used just below)
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < curs[0]; q += kVCThreads) base[q] = T(0);
+  // level-0 strip geometry and right-hand side (registers)
+  const VCLevel<T> L0 = lv[0];
+  const int n10 = L0.n1;
+  const int nch = max(1, min(kVCThreads / n10, (L0.rows + kCStrip - 1) / 1));
+  const int cr = (L0.rows + nch - 1) / nch;               // rows per strip (<= kCStrip by construction)
+  int sx = -1, si0 = 1, scr = 0;
+  {
+    const int t = threadIdx.x, ch = t / n10;
+    if (ch < nch) {
+      sx = t - ch * n10;
+      si0 = 1 + ch * cr;
+      scr = max(0, min(cr, L0.rows - ch * cr));
+      if (scr == 0) sx = -1;
+    }
+  }
+  T bv[kCStrip];
+  {
+    const T* b0 = bg + col * int64_t(n10) * n10;
+#pragma unroll
+    for (int j = 0; j < kCStrip; ++j) {
+      const int gy = rank * L0.band + si0 - 1 + j;
+      bv[j] = (sx >= 0 && j < scr) ? b0[int64_t(gy) * n10 + sx] : T(0);
+    }
+  }
+  cl.sync();                                                // zeroed everywhere before any exchange
+  // ----- descent -----
+#pragma unroll 1
+  for (int l = 0; l < nlev - 1; ++l) {
+    const VCLevel<T> P = lv[l];
+    const VCLevel<T> Q = lv[l + 1];
+    const bool dist = l < nd;
+    const int s = P.s;
+    const int hgt = dist ? P.band + 2 : P.n1 + 2;
+    T* xa = base + P.off;
+    T* xb = xa + hgt * s;
+    const T* bl = xb + hgt * s;
+    int cur = 0;
+#pragma unroll 1
+    for (int sw = 0; sw < nu; ++sw) {
+      T* src = cur == 0 ? xa : xb;
+      T* dst = sw == 0 ? xa : (cur == 0 ? xb : xa);
+      if (sw > 0) {
+        if (dist) { cl.sync(); band_exchange(src, P.band, s, rank, C); }
+        else __syncthreads();
+      }
+      if (l == 0) {
+        if (sw == 0) cstrip_pass<T, 1>(src, dst, bv, sx, si0, scr, s, P.d, P.e, P.c, P.wd);
+        else cstrip_pass<T, 0>(src, dst, bv, sx, si0, scr, s, P.d, P.e, P.c, P.wd);
+      } else {
+        if (sw == 0) band_pass<T, 1>(src, dst, bl, P.rows, P.n1, s, P.d, P.e, P.c, P.wd);
+        else band_pass<T, 0>(src, dst, bl, P.rows, P.n1, s, P.d, P.e, P.c, P.wd);
+      }
+      cur = dst == xa ? 0 : 1;
+    }
+    T* xcur = cur == 0 ? xa : xb;
+    T* rbuf = cur == 0 ? xb : xa;
+    if (dist) { cl.sync(); band_exchange(xcur, P.band, s, rank, C); }
+    else __syncthreads();
+    if (l == 0) cstrip_pass<T, 2>(xcur, rbuf, bv, sx, si0, scr, s, P.d, P.e, P.c, P.wd);
+    else band_pass<T, 2>(xcur, rbuf, bl, P.rows, P.n1, s, P.d, P.e, P.c, P.wd);
+    // restriction into the coarse right-hand side
+    const int sc = Q.s;
+    const bool cdist = (l + 1) < nd;
+    T* bc = base + Q.off + 2 * (cdist ? Q.band + 2 : Q.n1 + 2) * sc;
+    if (dist) { cl.sync(); band_exchange(rbuf, P.band, s, rank, C); }
+    else __syncthreads();
+    {
+      const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+      // coarse rows handled here: local band rows (distributed coarse) or this rank's
+      // global rows (first gathered level) or all rows (redundant)
+      const int cb = dist ? P.band / 2 : 0;                    // coarse band height of this rank
+      const int nrows = dist ? min(cb, Q.n1 - rank * cb) : Q.n1;
+      for (int ic = ty; ic < nrows; ic += kVCThreads / 32) {
+        // fine local row of the coarse row's centre: dist -> 2*ic + 2 (band layout), else 2*ic + 2 (padded)
+        const T* r = rbuf + (2 * ic + 2) * s;
+        T* out = cdist ? bc + (ic + 1) * sc : bc + (dist ? rank * cb + ic + 1 : ic + 1) * sc;
+        for (int I = tx; I < Q.n1; I += 32) {
+          const T* rr = r + 2 * I + 2;
+          const T cen = rr[0];
+          const T edg = (rr[s] + rr[-s]) + (rr[1] + rr[-1]);
+          const T cor = (rr[s + 1] + rr[s - 1]) + (rr[-s + 1] + rr[-s - 1]);
+          out[I + 1] = cen + T(0.5) * edg + T(0.25) * cor;
+        }
+      }
+    }
+    if (dist && !cdist) {
+      // gather the first redundant level's right-hand side from every rank
+      cl.sync();
+      const int cb = P.band / 2;
+      for (int rk = 0; rk < C; ++rk) {
+        if (rk == rank) continue;
+        const T* peer = cl.map_shared_rank(bc, rk);
+        const int r0 = rk * cb, nr = min(cb, Q.n1 - r0);
+        for (int q = threadIdx.x; q < nr * sc; q += kVCThreads) bc[(r0 + 1) * sc + q] = peer[(r0 + 1) * sc + q];
+      }
+    }
+    if (threadIdx.x == 0) curs[l] = cur;
+    __syncthreads();
+  }
+  // coarsest: one node (redundant in every CTA)
+  if (threadIdx.x == 0) {
+    const int l = nlev - 1;
+    T* xa = base + lv[l].off;
+    xa[4] = xa[2 * 9 + 4] / lv[l].d;
+    curs[l] = 0;
+  }
+  __syncthreads();
+  // ----- ascent -----
+#pragma unroll 1
+  for (int l = nlev - 2; l >= 0; --l) {
+    const VCLevel<T> P = lv[l];
+    const VCLevel<T> Q = lv[l + 1];
+    const bool dist = l < nd, cdist = (l + 1) < nd;
+    const int s = P.s, sc = Q.s;
+    const int hgt = dist ? P.band + 2 : P.n1 + 2;
+    const int hgtc = cdist ? Q.band + 2 : Q.n1 + 2;
+    T* xa = base + P.off;
+    T* xb = xa + hgt * s;
+    const T* bl = xb + hgt * s;
+    T* xca = base + Q.off;
+    T* xc = curs[l + 1] == 0 ? xca : xca + hgtc * sc;
+    if (cdist) { cl.sync(); band_exchange(xc, Q.band, sc, rank, C); }
+    else __syncthreads();
+    int cur = curs[l];
+    {
+      T* xf = cur == 0 ? xa : xb;
+      const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+      const int rows = dist ? P.rows : P.n1;
+      for (int i = 1 + ty; i <= rows; i += kVCThreads / 32) {
+        // coarse local rows of fine local row i: distributed fine over distributed coarse ->
+        // (i >> 1, (i + 1) >> 1); distributed fine over the full coarse grid -> global rows
+        int c0, c1;
+        if (!dist || cdist) { c0 = i >> 1; c1 = (i + 1) >> 1; }
+        else { const int gi = rank * P.band + i; c0 = gi >> 1; c1 = (gi + 1) >> 1; }
+        const T* r0 = xc + c0 * sc;
+        const T* r1 = xc + c1 * sc;
+        for (int x = tx; x < P.n1; x += 32) {
+          const int gx = x + 1;
+          const int a0 = gx >> 1, a1 = (gx + 1) >> 1;
+          xf[i * s + x + 1] += T(0.25) * ((r0[a0] + r0[a1]) + (r1[a0] + r1[a1]));
+        }
+      }
+    }
+#pragma unroll 1
+    for (int sw = 0; sw < nu; ++sw) {
+      T* src = cur == 0 ? xa : xb;
+      T* dst = cur == 0 ? xb : xa;
+      if (dist) { cl.sync(); band_exchange(src, P.band, s, rank, C); }
+      else __syncthreads();
+      if (l == 0) cstrip_pass<T, 0>(src, dst, bv, sx, si0, scr, s, P.d, P.e, P.c, P.wd);
+      else band_pass<T, 0>(src, dst, bl, P.rows, P.n1, s, P.d, P.e, P.c, P.wd);
+      cur ^= 1;
+    }
+    if (threadIdx.x == 0) curs[l] = cur;
+    __syncthreads();
+  }
+  // this rank's band of the level-0 result
+  {
+    const T* x0 = base + (curs[0] == 0 ? 0 : (L0.band + 2) * L0.s);
+    const int s0 = L0.s;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t n0 = int64_t(n10) * n10;
+    T* dstg = acc ? acc + (col / acc_L) * acc_ss + (acc_col0 + col % acc_L) * n0 : xg + col * n0;
+    for (int i = ty; i < L0.rows; i += kVCThreads / 32) {
+      const int64_t gy = int64_t(rank) * L0.band + i;
+      for (int x = tx; x < n10; x += 32) {
+        const T v = x0[(i + 1) * s0 + x + 1];
+        if (acc) dstg[gy * n10 + x] += v; else dstg[gy * n10 + x] = v;
+      }
+    }
+  }
+  cl.sync();                                               // peers may still read our shared memory
+}
+
+size_t vcycle_cluster_smem(const ClusterLevels& L, int C, int esize) {
+  size_t o = 0;
+  for (int l = 0; l < L.nlev; ++l) {
+    const size_t s = L.n1[l] + 2;
+    if (l < L.nd) o += (size_t((L.n1[l] + 1) / C) + 2) * s * (l > 0 ? 3 : 2);
+    else o += s * s * 3;
+  }
+  return o * esize;
+}
+
+template <typename T>
+cudaError_t launch_vcycle_cluster(const T* b, T* x, int64_t B, const ClusterLevels& L, int C, T omega, int nu, T* acc,
+                                  int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  const size_t smem = vcycle_cluster_smem(L, C, sizeof(T));
+  if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(vcycle_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  if (C > 8) {
+    e = cudaFuncSetAttribute(vcycle_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(B * C));
+  cfg.blockDim = dim3(kVCThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const double n0 = double(L.n1[0]) * L.n1[0];
+  ProfScope ps(KK_VCYCLE_FUSED, st, double(sizeof(T)) * B * n0 * (acc ? 3 : 2),
+               double(B) * n0 * (4.0 / 3.0) * (21.0 * 2 * nu + 18.0 + 10.0));
+  e = cudaLaunchKernelEx(&cfg, vcycle_cluster_kernel<T>, b, x, L, omega, nu, acc, acc_ss, acc_L, acc_col0);
+  note_launch();
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -1154,6 +1504,8 @@ cudaError_t launch_fill(T* x, int64_t n, T v, cudaStream_t st) {
   template cudaError_t launch_scale<T>(const T*, T*, int64_t, T, cudaStream_t);                                    \
   template cudaError_t launch_vcycle_full<T>(const T*, T*, int64_t, const FusedLevels&, T, int, T*, int64_t, int,  \
                                              int, cudaStream_t);                                                   \
+  template cudaError_t launch_vcycle_cluster<T>(const T*, T*, int64_t, const ClusterLevels&, int, T, int, T*,      \
+                                                int64_t, int, int, cudaStream_t);                                  \
   template cudaError_t launch_dot_partial<T>(const T*, const T*, int64_t, double*, cudaStream_t);                  \
   template cudaError_t launch_minres_v<T>(const T*, const T*, T*, int64_t, const MinresState*, cudaStream_t);      \
   template cudaError_t launch_add_to<T>(const T*, double*, int64_t, cudaStream_t);                                 \

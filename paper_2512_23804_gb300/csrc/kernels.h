@@ -42,6 +42,7 @@ struct SGArgs {
   T mass;                       // h^2/36
   const T* kap;                 // kappa_k(e)/6, (M+1) x nx x nx
   const int* nbr_ptr; const int* nbr_alpha; const int* nbr_k; const T* nbr_c;
+  const int* nbr_end;           // per output column: end of its entries with k < kmax
   double deg_sum;               // number of (beta, neighbour) pairs used (work accounting only)
   int nnz_out;                  // neighbour-table entries of the output columns (all k)
 };
@@ -95,6 +96,15 @@ cudaError_t launch_scale(const T* b, T* x, int64_t cnt, T a, cudaStream_t st);
 // Levels handled by the one-CTA-per-column V-cycle: L.n1[0] (finest handled)
 // down to a single node, with their 9-point stencils.
 struct FusedLevels { int nlev; int n1[13]; double diag[13], edge[13], corner[13]; };
+// Cluster V-cycle: one thread-block cluster of C CTAs per column; the first nd
+// levels are split into C horizontal bands (halo rows through distributed shared
+// memory), the remaining small levels are solved redundantly in every CTA.
+struct ClusterLevels { int nlev; int nd; int n1[13]; double diag[13], edge[13], corner[13]; };
+size_t vcycle_cluster_smem(const ClusterLevels& L, int C, int esize);
+template <typename T>
+cudaError_t launch_vcycle_cluster(const T* b, T* x, int64_t B, const ClusterLevels& L, int C, T omega, int nu,
+                                  T* acc, int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st);
+
 // Full-hierarchy V-cycle (top level read from global memory, register-blocked
 // sweeps, 1024 threads): usable when vcycle_full_fits(L, sizeof(T)).
 bool vcycle_full_fits(const FusedLevels& L, int esize);

@@ -79,7 +79,7 @@ void sgoc_default_options(sgoc_options* o) {
   o->nu_post = 2;
   o->omega = 0.8;
   o->precision = SGOC_FP64;
-  o->inner_tol = 1e-4;
+  o->inner_tol = 1e-3;
   o->max_outer = 20;
 }
 
@@ -186,6 +186,13 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
     }
     pb->nbr_ptr[b + 1] = int(pb->nbr_alpha.size());
   }
+  // end of each column's entries with k < r (the table is sorted by k inside a column)
+  pb->nbr_end_r.resize(pb->P);
+  for (int b = 0; b < pb->P; ++b) {
+    int e = pb->nbr_ptr[b];
+    while (e < pb->nbr_ptr[b + 1] && pb->nbr_k[e] < pb->r) ++e;
+    pb->nbr_end_r[b] = e;
+  }
 
   // multigrid hierarchy of the mean operator:
   // steady  A~_1 = kappa0 K + s M            (Eq. (mathcalZ))
@@ -213,6 +220,7 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
   size_t off = 0;
   off = align256(off + nk * 8); off = align256(off + nk * 4);
   off = align256(off + (pb->P + 1) * 4); off = align256(off + nnz * 4); off = align256(off + nnz * 4);
+  off = align256(off + pb->P * 4);
   off = align256(off + nnz * 8); off = align256(off + nnz * 4);
   off = align256(off + size_t(pb->slabs) * pb->n * 8); off = align256(off + size_t(pb->n) * 8);
   pb->persistent_bytes = off;
@@ -258,6 +266,8 @@ sgoc_status sgoc_problem_upload(sgoc_problem* pb, void* d_persistent, size_t byt
   pb->dev.kap64 = reinterpret_cast<double*>(carve(nk * 8));
   pb->dev.kap32 = reinterpret_cast<float*>(carve(nk * 4));
   pb->dev.nbr_ptr = reinterpret_cast<int*>(carve((pb->P + 1) * 4));
+  pb->dev.nbr_end_all = pb->dev.nbr_ptr + 1;                     // all entries: the next column's start
+  pb->dev.nbr_end_r = reinterpret_cast<int*>(carve(pb->P * 4));
   pb->dev.nbr_alpha = reinterpret_cast<int*>(carve(nnz * 4));
   pb->dev.nbr_k = reinterpret_cast<int*>(carve(nnz * 4));
   pb->dev.nbr_c64 = reinterpret_cast<double*>(carve(nnz * 8));
@@ -272,6 +282,7 @@ sgoc_status sgoc_problem_upload(sgoc_problem* pb, void* d_persistent, size_t byt
   SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.kap64, k64.data(), nk * 8, cudaMemcpyHostToDevice, st));
   SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.kap32, k32.data(), nk * 4, cudaMemcpyHostToDevice, st));
   SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.nbr_ptr, pb->nbr_ptr.data(), (pb->P + 1) * 4, cudaMemcpyHostToDevice, st));
+  SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.nbr_end_r, pb->nbr_end_r.data(), pb->P * 4, cudaMemcpyHostToDevice, st));
   if (nnz) {
     SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.nbr_alpha, pb->nbr_alpha.data(), nnz * 4, cudaMemcpyHostToDevice, st));
     SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.nbr_k, pb->nbr_k.data(), nnz * 4, cudaMemcpyHostToDevice, st));

@@ -43,6 +43,8 @@ struct DevData {
   double* kap64 = nullptr;     // (M+1) x nx x nx, kappa_k(e) / 6
   float* kap32 = nullptr;
   int* nbr_ptr = nullptr;      // CSR over output columns beta: P + 1
+  int* nbr_end_r = nullptr;    // per column: end of the entries with k < r (truncation)
+  int* nbr_end_all = nullptr;  // per column: end of all entries
   int* nbr_alpha = nullptr;    // neighbour column alpha = beta +- e_k
   int* nbr_k = nullptr;        // KL index k (1..M)
   double* nbr_c64 = nullptr;   // E[xi_k Psi_alpha Psi_beta]
@@ -65,7 +67,7 @@ struct sgoc_problem {
   // chaos basis
   std::vector<int32_t> idx;          // P x M
   std::vector<int> off;              // p + 2 level offsets
-  std::vector<int> nbr_ptr, nbr_alpha, nbr_k;
+  std::vector<int> nbr_ptr, nbr_alpha, nbr_k, nbr_end_r;
   std::vector<double> nbr_c;
   // multigrid hierarchy of the mean operator (level 0 = finest)
   std::vector<sgoc::Level> levels;

@@ -45,12 +45,38 @@ struct Carver {
   bool ok() const { return dry || off <= cap; }
 };
 
-// Largest finest level handled by the one-CTA-per-column V-cycle kernel.
-// float32: the whole hierarchy up to 127 x 127 interior nodes fits one CTA's
-// shared memory.  float64 runs at 1/64 of the float32 rate on this GPU, so a
-// single SM per column would be too slow there: grid-wide level kernels above
-// 15 x 15 spread the fine levels over all SMs.
-static int fused_n1_limit(int esize) { return esize == 8 ? 15 : 127; }
+// Where the fused V-cycle starts and which kernel runs it.  Levels above lf use
+// grid-wide level kernels.  float32: up to 127 x 127 interior nodes the whole
+// hierarchy fits one CTA's shared memory; a 4-CTA cluster per column shortens
+// each cycle but costs more SM time, so it is used only when the batch of
+// columns leaves SMs idle (B * C <= 152); 255 x 255 always takes an 8-CTA
+// cluster (no single CTA holds it).  float64 runs at 1/64 of the float32 rate on
+// this GPU: one CTA only up to 15 x 15, clusters of 2-8 CTAs for 31..127 so that
+// each column's cycle is spread over several SMs.
+struct VPlan { int lf = 0; bool cluster = false; int C = 1; int nd = 0; };
+
+static VPlan plan_vcycle(const sgoc_problem* pb, int esize, int64_t ncols) {
+  VPlan v;
+  const int nl = int(pb->levels.size());
+  for (int l = 0; l < nl; ++l) {
+    const int n1 = pb->levels[l].n1;
+    const int single_max = esize == 4 ? 127 : 15;
+    const int cluster_max = esize == 4 ? 255 : 127;
+    const int band0 = esize == 4 ? 32 : 16;
+    const bool cluster_ok = n1 >= 31 && n1 <= cluster_max;
+    const int C = (n1 + 1) / band0;
+    const bool prefer_cluster = cluster_ok && (n1 > single_max || int64_t(C) * ncols <= 152);
+    if (n1 <= single_max && !prefer_cluster) { v.lf = l; v.cluster = false; return v; }
+    if (cluster_ok) {
+      v.lf = l; v.cluster = true; v.C = C;
+      v.nd = 0;
+      for (int q = l; q < nl && (pb->levels[q].n1 + 1) / v.C >= 8; ++q) ++v.nd;
+      return v;
+    }
+  }
+  v.lf = nl - 1;
+  return v;
+}
 
 int level_columns_max(const sgoc_problem* pb) {
   int m = 1;
@@ -78,13 +104,13 @@ static void carve_prec(const sgoc_problem* pb, Carver& c, PrecWS<T>& w) {
   w.RH = c.template take<T>(B * pb->n);
   const int nl = int(pb->levels.size());
   w.lx.assign(nl, nullptr); w.lt.assign(nl, nullptr); w.lb.assign(nl, nullptr);
-  const int lim = fused_n1_limit(sizeof(T));
-  for (int l = 0; l < nl; ++l) {
+  // the level-wise buffers above the fused start do not depend on the column count
+  const int lf = plan_vcycle(pb, sizeof(T), 1 << 30).lf;
+  for (int l = 0; l <= lf; ++l) {
     const size_t nlv = size_t(pb->levels[l].n);
     w.lx[l] = c.template take<T>(B * nlv);
-    if (pb->levels[l].n1 > lim) w.lt[l] = c.template take<T>(B * nlv);
+    if (l < lf) w.lt[l] = c.template take<T>(B * nlv);
     if (l > 0) w.lb[l] = c.template take<T>(B * nlv);
-    if (pb->levels[l].n1 <= lim) break;
   }
 }
 
@@ -103,20 +129,27 @@ template <typename T>
 static sgoc_status vcycle(const sgoc_problem* pb, PrecWS<T>& w, const T* b, T* xout, int64_t B, T* acc,
                           int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st) {
   const int nl = int(pb->levels.size());
-  const int lim = fused_n1_limit(sizeof(T));
   const T om = T(pb->opt.omega);
   const int nu = pb->opt.nu_pre;
-  int lf = 0;
-  while (lf < nl - 1 && pb->levels[lf].n1 > lim) ++lf;
+  const VPlan vp = plan_vcycle(pb, sizeof(T), B);
+  const int lf = vp.lf;
   FusedLevels FL;
-  FL.nlev = nl - lf;
+  ClusterLevels CL;
+  FL.nlev = CL.nlev = nl - lf;
+  CL.nd = vp.nd;
   for (int l = lf; l < nl; ++l) {
-    FL.n1[l - lf] = pb->levels[l].n1;
-    FL.diag[l - lf] = pb->levels[l].diag; FL.edge[l - lf] = pb->levels[l].edge; FL.corner[l - lf] = pb->levels[l].corner;
+    FL.n1[l - lf] = CL.n1[l - lf] = pb->levels[l].n1;
+    FL.diag[l - lf] = CL.diag[l - lf] = pb->levels[l].diag;
+    FL.edge[l - lf] = CL.edge[l - lf] = pb->levels[l].edge;
+    FL.corner[l - lf] = CL.corner[l - lf] = pb->levels[l].corner;
   }
-  if (!vcycle_full_fits(FL, sizeof(T))) { set_error("internal: V-cycle level does not fit"); return SGOC_ERR_UNSUPPORTED; }
+  if (!vp.cluster && !vcycle_full_fits(FL, sizeof(T))) { set_error("internal: V-cycle level does not fit"); return SGOC_ERR_UNSUPPORTED; }
+  auto fused = [&](const T* bb, T* xx, T* ac, int64_t ss, int aL, int ac0) -> cudaError_t {
+    if (vp.cluster) return launch_vcycle_cluster<T>(bb, xx, B, CL, vp.C, om, nu, ac, ss, aL, ac0, st);
+    return launch_vcycle_full<T>(bb, xx, B, FL, om, nu, ac, ss, aL, ac0, st);
+  };
   if (lf == 0) {
-    SGOC_LAUNCH(launch_vcycle_full<T>(b, xout, B, FL, om, nu, acc, acc_ss, acc_L, acc_col0, st));
+    SGOC_LAUNCH(fused(b, xout, acc, acc_ss, acc_L, acc_col0));
     return SGOC_OK;
   }
   // level-wise descent down to lf
@@ -141,7 +174,7 @@ static sgoc_status vcycle(const sgoc_problem* pb, PrecWS<T>& w, const T* b, T* x
     bl[l + 1] = w.lb[l + 1];
     xcur[l] = cur; spare[l] = sp;
   }
-  SGOC_LAUNCH(launch_vcycle_full<T>(bl[lf], w.lx[lf], B, FL, om, nu, (T*)nullptr, 0, 1, 0, st));
+  SGOC_LAUNCH(fused(bl[lf], w.lx[lf], (T*)nullptr, 0, 1, 0));
   T* xc = w.lx[lf];
   for (int l = lf - 1; l >= 0; --l) {
     const Level& L = pb->levels[l];
@@ -207,6 +240,7 @@ static sgoc_status hgs(const sgoc_problem* pb, PrecWS<T>& w, const T* R, T* V, i
     g.mass = T(pb->mass_h2_36);
     g.kap = kap_of<T>(pb);
     g.nbr_ptr = pb->dev.nbr_ptr; g.nbr_alpha = pb->dev.nbr_alpha; g.nbr_k = pb->dev.nbr_k; g.nbr_c = nbrc_of<T>(pb);
+    g.nbr_end = pb->r == pb->M + 1 ? pb->dev.nbr_end_all : pb->dev.nbr_end_r;
     g.deg_sum = deg_sum(pb, a0, a1, pb->r);
     g.nnz_out = pb->nbr_ptr[a1] - pb->nbr_ptr[a0];
     SGOC_LAUNCH(launch_sg<T>(g, st));
@@ -229,6 +263,7 @@ static SGArgs<T> sg_full(const sgoc_problem* pb, const T* X, T* Y, T coef) {
   g.mass = T(pb->mass_h2_36);
   g.kap = kap_of<T>(pb);
   g.nbr_ptr = pb->dev.nbr_ptr; g.nbr_alpha = pb->dev.nbr_alpha; g.nbr_k = pb->dev.nbr_k; g.nbr_c = nbrc_of<T>(pb);
+  g.nbr_end = pb->dev.nbr_end_all;
   g.deg_sum = double(pb->nbr_alpha.size());
   g.nnz_out = int(pb->nbr_alpha.size());
   return g;

@@ -30,7 +30,7 @@ class SGProblem:
     """
 
     def __init__(self, nx, M, p, kappa, beta, yhat, gamma=0.0, nt=0, T=1.0, y0=None, *, tol=1e-8,
-                 max_iter=1000, r=0, cheb_steps=5, nu=2, omega=0.8, precision="fp64", inner_tol=1e-4,
+                 max_iter=1000, r=0, cheb_steps=5, nu=2, omega=0.8, precision="fp64", inner_tol=1e-3,
                  max_outer=20):
         self._handle = None
         lib = abi.load()

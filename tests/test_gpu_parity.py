@@ -236,3 +236,32 @@ def test_solve_is_deterministic():
     xb, ib = sp.solve()
     assert ia["iterations"] == ib["iterations"]
     assert torch.equal(xa, xb)
+
+
+@pytest.mark.parametrize("nx,ncols", [(64, 3), (128, 3), (128, 56), (256, 3)])
+def test_vcycle_fp32_cluster_and_single(nx, ncols):
+    """float32 V-cycle against the float64 oracle cycle (float32 rounding over ~50
+    stencil passes): one CTA per column (64x64; 128x128 with many columns) and
+    thread-block clusters (128x128 with few columns; 256x256)."""
+    pr = si.random_small(40 + nx, nx=nx, M=2, p=2, beta=1e-3)
+    if ncols > 6:
+        pr = si.random_small(40 + nx, nx=nx, M=6, p=3, beta=1e-3)
+    d = SGData(pr)
+    sp = SGProblem.from_problem(pr, precision="mixed")
+    Pc = BlockPreconditioner(d)
+    B = si.random_panel(41, d.n, ncols)
+    X = host(sp.apply_vcycle(dev(B, torch.float32), ncols))
+    V = VCycle(Pc.A0, pr.nx, pr.nu_pre, pr.nu_post, pr.omega)
+    ref = V.apply(B.astype(np.float32).astype(np.float64).reshape(ncols, d.n).T).T.reshape(-1)
+    assert rel(X, ref) <= 2e-5
+
+
+def test_hgs_fp32_128():
+    pr = si.random_small(50, nx=128, M=3, p=2, beta=1e-4)
+    d = SGData(pr)
+    sp = SGProblem.from_problem(pr, precision="mixed")
+    Pc = BlockPreconditioner(d)
+    R = si.random_panel(51, d.n, d.P)
+    V = host(sp.apply_hgs(dev(R, torch.float32)))
+    ref = d.vec(Pc.hgs.apply(d.mat(R.astype(np.float32).astype(np.float64))))
+    assert rel(V, ref) <= 2e-5
