@@ -641,128 +641,226 @@ __device__ __forceinline__ Strip strip_of(int n1) {
   return g;
 }
 
-// Level-0 pass over this thread's strip: Jacobi (xd = xs + omega/d (b - A xs)),
-// from zero (xd = omega/d b) or residual (xd = b - A xs).  No barrier inside.
-template <typename T, int MODE>   // 0 jacobi, 1 from zero, 2 residual
-__device__ __forceinline__ void strip_pass(const T* __restrict__ xs, T* __restrict__ xd, const T (&bv)[kStripRows],
-                                           const Strip& g, int n1, T d, T e, T c, T wd) {
-  if (g.x < 0) return;
-  const int s = n1 + 2;
-  if (MODE == 1) {
+template <typename T>
+struct VFLevel { int off, n1, grp; T d, e, c, wd; };
+
+// ---------------------------------------------------------------------------
+// One-CTA-per-column V-cycle with the grid size as a template parameter: every
+// level's size, stride and shared-memory offset is a compile-time constant, and
+// the levels are visited by compile-time recursion.  Level l of a hierarchy with
+// N1 interior nodes per side has n1(l) = (N1 + 1) / 2^l - 1 nodes per side;
+// arrays carry a zero border (stride n1 + 2).  Level 0 holds two iterate buffers
+// (the idle one takes the residual) and keeps its right-hand side in registers
+// (16-row strips); coarse levels hold two iterates and the right-hand side, run
+// point-parallel on nested thread groups (1024 / 256 / 32 threads), and fold the
+// two pre-smoothing sweeps from a zero start into one pass:
+// x2 = (omega/d) (2 b - (omega/d) A b).
+// ---------------------------------------------------------------------------
+template <int N1>
+struct VT {
+  static constexpr int n1(int l) { return ((N1 + 1) >> l) - 1; }
+  static constexpr int s(int l) { return n1(l) + 2; }
+  static constexpr int np(int l) { return s(l) * s(l); }
+  static constexpr int off(int l) { return l == 0 ? 0 : off(l - 1) + np(l - 1) * (l - 1 > 0 ? 3 : 2); }
+  static constexpr int nlev() { return N1 == 1 ? 1 : 1 + VT<(N1 - 1) / 2>::nlev(); }
+  static constexpr int total() { return off(nlev()); }
+  static constexpr int grp(int l) { return n1(l) >= 63 ? kVFThreads : (n1(l) >= 15 ? 256 : 32); }
+};
+template <>
+struct VT<0> {
+  static constexpr int nlev() { return 0; }
+};
+
+template <int NT>
+__device__ __forceinline__ void vt_sync() {
+  if (NT == kVFThreads) __syncthreads();
+  else if (NT > 32) asm volatile("bar.sync 1, %0;\n" ::"r"(NT) : "memory");
+  else __syncwarp();
+}
+
+// coarse-level pass: 0 jacobi, 1 double sweep from zero, 2 residual
+template <typename T, int N, int NT, int MODE>
+__device__ __forceinline__ void vt_pass(const T* __restrict__ xs, T* __restrict__ xd, const T* __restrict__ b,
+                                       T d, T e, T c, T wd) {
+  constexpr int S = N + 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
 #pragma unroll
-    for (int j = 0; j < kStripRows; ++j) {
-      const int y = g.y0 + j;
-      if (y < g.y1) xd[(y + 1) * s + g.x + 1] = wd * bv[j];
+  for (int y0 = 0; y0 < N; y0 += NT / 32) {
+    const int y = y0 + ty;
+    if (y < N) {
+#pragma unroll
+      for (int x0 = 0; x0 < N; x0 += 32) {
+        const int x = x0 + tx;
+        if (x < N) {
+          const int o = (y + 1) * S + x + 1;
+          const T* v = MODE == 1 ? b : xs;
+          const T edges = (v[o - S] + v[o + S]) + (v[o - 1] + v[o + 1]);
+          const T corners = (v[o - S - 1] + v[o - S + 1]) + (v[o + S - 1] + v[o + S + 1]);
+          const T av = fma(d, v[o], fma(e, edges, c * corners));
+          if (MODE == 1) xd[o] = wd * fma(T(2), b[o], -wd * av);
+          else if (MODE == 2) xd[o] = b[o] - av;
+          else xd[o] = fma(wd, b[o] - av, xs[o]);
+        }
+      }
     }
+  }
+}
+
+template <typename T, int N, int NT>
+__device__ __forceinline__ void vt_restrict(const T* __restrict__ R, T* __restrict__ bc) {
+  constexpr int S = N + 2, NC = (N - 1) / 2, SC = NC + 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+  for (int J0 = 0; J0 < NC; J0 += NT / 32) {
+    const int J = J0 + ty;
+    if (J < NC) {
+#pragma unroll
+      for (int I0 = 0; I0 < NC; I0 += 32) {
+        const int I = I0 + tx;
+        if (I < NC) {
+          const T* r = R + (2 * J + 2) * S + 2 * I + 2;
+          const T cen = r[0];
+          const T edg = (r[S] + r[-S]) + (r[1] + r[-1]);
+          const T cor = (r[S + 1] + r[S - 1]) + (r[-S + 1] + r[-S - 1]);
+          bc[(J + 1) * SC + I + 1] = cen + T(0.5) * edg + T(0.25) * cor;
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int N, int NT>
+__device__ __forceinline__ void vt_prolong(const T* __restrict__ Xc, T* __restrict__ xf) {
+  constexpr int S = N + 2, NC = (N - 1) / 2, SC = NC + 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+  for (int j0 = 0; j0 < N; j0 += NT / 32) {
+    const int j = j0 + ty;
+    if (j < N) {
+      const int gj = j + 1;
+      const T* r0 = Xc + (gj >> 1) * SC;
+      const T* r1 = Xc + ((gj + 1) >> 1) * SC;
+#pragma unroll
+      for (int i0 = 0; i0 < N; i0 += 32) {
+        const int i = i0 + tx;
+        if (i < N) {
+          const int gi = i + 1;
+          const int c0 = gi >> 1, c1 = (gi + 1) >> 1;
+          xf[(j + 1) * S + i + 1] += T(0.25) * ((r0[c0] + r0[c1]) + (r1[c0] + r1[c1]));
+        }
+      }
+    }
+  }
+}
+
+// level-0 strip pass over compile-time stride S: 0 jacobi, 1 from zero, 2 residual
+template <typename T, int S, int MODE>
+__device__ __forceinline__ void vt_strip(const T* __restrict__ xs, T* __restrict__ xd, const T (&bv)[kStripRows],
+                                        const Strip& g, T d, T e, T c, T wd) {
+  if (g.x < 0) return;
+  const int cr = g.y1 - g.y0;
+  if (MODE == 1) {
+    T* q = xd + (g.y0 + 1) * S + g.x + 1;
+#pragma unroll
+    for (int j = 0; j < kStripRows; ++j)
+      if (j < cr) q[j * S] = wd * bv[j];
     return;
   }
-  const T* p = xs + g.y0 * s + g.x;      // padded (row y0, col x) = interior (y0-1, x-1)
+  const T* p = xs + g.y0 * S + g.x;
   T wm0 = p[0], wc0 = p[1], wp0 = p[2];
-  p += s;
-  T wm1 = p[0], wc1 = p[1], wp1 = p[2];
-  T* q = xd + (g.y0 + 1) * s + g.x + 1;
+  T wm1 = p[S], wc1 = p[S + 1], wp1 = p[S + 2];
+  T* q = xd + (g.y0 + 1) * S + g.x + 1;
 #pragma unroll
   for (int j = 0; j < kStripRows; ++j) {
-    if (g.y0 + j < g.y1) {
-      p += s;
-      const T wm2 = p[0], wc2 = p[1], wp2 = p[2];
+    if (j < cr) {
+      const T wm2 = p[(j + 2) * S], wc2 = p[(j + 2) * S + 1], wp2 = p[(j + 2) * S + 2];
       const T edges = (wc0 + wc2) + (wm1 + wp1);
       const T corners = (wm0 + wp0) + (wm2 + wp2);
       const T r = bv[j] - fma(d, wc1, fma(e, edges, c * corners));
-      *q = MODE == 2 ? r : fma(wd, r, wc1);
-      q += s;
+      q[j * S] = MODE == 2 ? r : fma(wd, r, wc1);
       wm0 = wm1; wc0 = wc1; wp0 = wp1;
       wm1 = wm2; wc1 = wc2; wp1 = wp2;
     }
   }
 }
 
-// threads taking part in the passes of a level with n1 interior nodes per side
-__device__ __forceinline__ int vf_group(int n1) { return n1 >= 63 ? kVFThreads : (n1 >= 15 ? 256 : 32); }
-
-__device__ __forceinline__ void vf_sync(int nt) {
-  if (nt == kVFThreads) __syncthreads();
-  else if (nt > 32) asm volatile("bar.sync 1, %0;\n" ::"r"(nt) : "memory");
-  else __syncwarp();
-}
-
-template <typename T>
-struct VFLevel { int off, n1, grp; T d, e, c, wd; };
-
-// Coarse-level pass on a group of nt threads (point parallel, 32 x (nt/32) grid).
-template <typename T, int MODE>
-__device__ __forceinline__ void group_pass(const T* __restrict__ xs, T* __restrict__ xd, const T* __restrict__ b,
-                                          int n1, int nt, T d, T e, T c, T wd) {
-  const int s = n1 + 2;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, sy = nt >> 5;
-  for (int y = ty; y < n1; y += sy)
-    for (int x = tx; x < n1; x += 32) {
-      const int o = (y + 1) * s + x + 1;
-      if (MODE == 1) { xd[o] = wd * b[o]; continue; }
-      const T edges = (xs[o - s] + xs[o + s]) + (xs[o - 1] + xs[o + 1]);
-      const T corners = (xs[o - s - 1] + xs[o - s + 1]) + (xs[o + s - 1] + xs[o + s + 1]);
-      const T r = b[o] - fma(d, xs[o], fma(e, edges, c * corners));
-      xd[o] = MODE == 2 ? r : fma(wd, r, xs[o]);
+// One level of the cycle (coarse levels L >= 1): pre-smoothing, residual, restriction,
+// the coarser levels, prolongation, post-smoothing.  Returns the buffer holding x.
+template <typename T, int N1, int L>
+__device__ int vt_coarse(T* base, const VFLevel<T>* lv, int nu) {
+  using G = VT<N1>;
+  constexpr int N = G::n1(L);
+  constexpr int NT = G::grp(L);
+  T* xa = base + G::off(L);
+  T* xb = xa + G::np(L);
+  T* bl = xb + G::np(L);
+  const T d = lv[L].d, e = lv[L].e, c = lv[L].c, wd = lv[L].wd;
+  if constexpr (N == 1) {
+    if (threadIdx.x == 0) xa[4] = bl[4] / d;
+    vt_sync<NT>();
+    return 0;
+  } else {
+    int cur = 0;
+    if (nu == 2) {
+      vt_pass<T, N, NT, 1>(xa, xa, bl, d, e, c, wd);
+      vt_sync<NT>();
+    } else {
+      for (int q = threadIdx.x; q < G::np(L); q += NT) xa[q] = T(0);
+      vt_sync<NT>();
+      for (int sw = 0; sw < nu; ++sw) {
+        if (cur == 0) vt_pass<T, N, NT, 0>(xa, xb, bl, d, e, c, wd); else vt_pass<T, N, NT, 0>(xb, xa, bl, d, e, c, wd);
+        cur ^= 1;
+        vt_sync<NT>();
+      }
     }
-}
-
-template <typename T>
-__device__ __forceinline__ void group_restrict(const T* __restrict__ R, T* __restrict__ bc, int n1, int n1c, int nt) {
-  const int s = n1 + 2, sc = n1c + 2;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, sy = nt >> 5;
-  for (int J = ty; J < n1c; J += sy)
-    for (int I = tx; I < n1c; I += 32) {
-      const T* r = R + (2 * J + 2) * s + 2 * I + 2;
-      const T cen = r[0];
-      const T edg = (r[s] + r[-s]) + (r[1] + r[-1]);
-      const T cor = (r[s + 1] + r[s - 1]) + (r[-s + 1] + r[-s - 1]);
-      bc[(J + 1) * sc + I + 1] = cen + T(0.5) * edg + T(0.25) * cor;
+    T* xcur = cur == 0 ? xa : xb;
+    T* rbuf = cur == 0 ? xb : xa;
+    vt_pass<T, N, NT, 2>(xcur, rbuf, bl, d, e, c, wd);
+    vt_sync<NT>();
+    T* bc = base + G::off(L + 1) + 2 * G::np(L + 1);
+    vt_restrict<T, N, NT>(rbuf, bc);
+    vt_sync<NT>();
+    int ccur = 0;
+    if (threadIdx.x < G::grp(L + 1)) ccur = vt_coarse<T, N1, L + 1>(base, lv, nu);
+    vt_sync<NT>();
+    // the coarse result's buffer index is the same in every thread of the coarse group; share it
+    __shared__ int cbuf;
+    if (threadIdx.x == 0) cbuf = ccur;
+    vt_sync<NT>();
+    const T* xc = base + G::off(L + 1) + (cbuf == 0 ? 0 : G::np(L + 1));
+    vt_prolong<T, N, NT>(xc, xcur);
+    vt_sync<NT>();
+    for (int sw = 0; sw < nu; ++sw) {
+      if (cur == 0) vt_pass<T, N, NT, 0>(xa, xb, bl, d, e, c, wd); else vt_pass<T, N, NT, 0>(xb, xa, bl, d, e, c, wd);
+      cur ^= 1;
+      vt_sync<NT>();
     }
-}
-
-template <typename T>
-__device__ __forceinline__ void group_prolong(const T* __restrict__ Xc, T* __restrict__ xf, int n1, int n1c, int nt) {
-  const int s = n1 + 2, sc = n1c + 2;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, sy = nt >> 5;
-  for (int j = ty; j < n1; j += sy) {
-    const int gj = j + 1;
-    const T* r0 = Xc + (gj >> 1) * sc;
-    const T* r1 = Xc + ((gj + 1) >> 1) * sc;
-    for (int i = tx; i < n1; i += 32) {
-      const int gi = i + 1;
-      const int c0 = gi >> 1, c1 = (gi + 1) >> 1;
-      xf[(j + 1) * s + i + 1] += T(0.25) * ((r0[c0] + r0[c1]) + (r1[c0] + r1[c1]));
-    }
+    return cur;
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kVFThreads, 1) vcycle_full_kernel(const T* __restrict__ bg, T* xg, FusedLevels L,
-                                                                    T omega, int nu, T* acc, int64_t acc_ss,
-                                                                    int acc_L, int acc_col0) {
-  extern __shared__ __align__(32) unsigned char vf_smem_raw[];
+template <typename T, int N1>
+__global__ void __launch_bounds__(kVFThreads, 1) vcycle_t_kernel(const T* __restrict__ bg, T* xg, FusedLevels L,
+                                                                 T omega, int nu, T* acc, int64_t acc_ss, int acc_L,
+                                                                 int acc_col0) {
+  using G = VT<N1>;
+  constexpr int NL = G::nlev();
+  constexpr int S0 = N1 + 2;
+  extern __shared__ __align__(32) unsigned char vt_smem_raw[];
   __shared__ VFLevel<T> lv[13];
-  __shared__ int curs[13];
-  T* base = reinterpret_cast<T*>(vf_smem_raw);
+  T* base = reinterpret_cast<T*>(vt_smem_raw);
   const int64_t col = blockIdx.x;
-  const int nlev = L.nlev;
-  if (threadIdx.x == 0) {
-    int o = 0;
-    for (int l = 0; l < nlev; ++l) {
-      const int n1 = L.n1[l];
-      lv[l].off = o; lv[l].n1 = n1; lv[l].grp = vf_group(n1);
-      lv[l].d = T(L.diag[l]); lv[l].e = T(L.edge[l]); lv[l].c = T(L.corner[l]);
-      lv[l].wd = omega / T(L.diag[l]);
-      o += (n1 + 2) * (n1 + 2) * (l > 0 ? 3 : 2);
-    }
+  constexpr int n0 = N1 * N1;
+  if (threadIdx.x < NL) {
+    const int l = threadIdx.x;
+    lv[l].d = T(L.diag[l]); lv[l].e = T(L.edge[l]); lv[l].c = T(L.corner[l]);
+    lv[l].wd = omega / T(L.diag[l]);
   }
-  __syncthreads();
-  const int n10 = lv[0].n1;
-  const int n0 = n10 * n10;
   // zero borders of every array (interiors are always written before they are read)
-  for (int l = 0; l < nlev; ++l) {
-    const int n1 = lv[l].n1, s = n1 + 2, per = 4 * (n1 + 1);
-    T* a = base + lv[l].off;
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    const int n1 = G::n1(l), s = n1 + 2, per = 4 * (n1 + 1);
+    T* a = base + G::off(l);
     const int narr = l > 0 ? 3 : 2;
     for (int q = threadIdx.x; q < narr * per; q += kVFThreads) {
       const int arr = q / per, k = q - arr * per;
@@ -772,106 +870,84 @@ __global__ void __launch_bounds__(kVFThreads, 1) vcycle_full_kernel(const T* __r
       A[o] = T(0);
     }
   }
-  const Strip g = strip_of(n10);
+  const Strip g = strip_of(N1);
   T bv[kStripRows];
   {
     const T* b0 = bg + col * n0;
 #pragma unroll
     for (int j = 0; j < kStripRows; ++j) {
       const int y = g.y0 + j;
-      bv[j] = (g.x >= 0 && y < g.y1) ? b0[y * n10 + g.x] : T(0);
+      bv[j] = (g.x >= 0 && y < g.y1) ? b0[y * N1 + g.x] : T(0);
     }
   }
   __syncthreads();
-  // descent
-#pragma unroll 1
-  for (int l = 0; l < nlev - 1; ++l) {
-    const VFLevel<T> P = lv[l];
-    const int nt = P.grp;
-    if (threadIdx.x >= nt) break;                         // this thread waits at the ascent
-    const int n1 = P.n1, n1c = lv[l + 1].n1;
-    const int np = (n1 + 2) * (n1 + 2);
-    T* xa = base + P.off;
-    T* xb = xa + np;
-    const T* bl = xb + np;
-    int cur = 0;
-    if (nu == 0) {
-      for (int q = threadIdx.x; q < np; q += nt) xa[q] = T(0);
-      vf_sync(nt);
-    }
-#pragma unroll 1
-    for (int sw = 0; sw < nu; ++sw) {
-      const T* src = cur == 0 ? xa : xb;
-      T* dst = sw == 0 ? xa : (cur == 0 ? xb : xa);
-      if (l == 0) {
-        if (sw == 0) strip_pass<T, 1>(src, dst, bv, g, n1, P.d, P.e, P.c, P.wd);
-        else strip_pass<T, 0>(src, dst, bv, g, n1, P.d, P.e, P.c, P.wd);
-      } else {
-        if (sw == 0) group_pass<T, 1>(src, dst, bl, n1, nt, P.d, P.e, P.c, P.wd);
-        else group_pass<T, 0>(src, dst, bl, n1, nt, P.d, P.e, P.c, P.wd);
+  T* xa = base;
+  T* xb = base + G::np(0);
+  int cur = 0;
+  if constexpr (N1 == 1) {
+    if (threadIdx.x == 0) xa[4] = bv[0] / lv[0].d;
+    __syncthreads();
+  } else {
+    constexpr int NT0 = G::grp(0);
+    const T d = lv[0].d, e = lv[0].e, c = lv[0].c, wd = lv[0].wd;
+    if (threadIdx.x < NT0) {
+      if (nu == 0) {
+        for (int q = threadIdx.x; q < G::np(0); q += NT0) xa[q] = T(0);
+        vt_sync<NT0>();
       }
-      cur = dst == xa ? 0 : 1;
-      vf_sync(nt);
+      for (int sw = 0; sw < nu; ++sw) {
+        if (sw == 0) vt_strip<T, S0, 1>(xb, xa, bv, g, d, e, c, wd);
+        else if (cur == 0) vt_strip<T, S0, 0>(xa, xb, bv, g, d, e, c, wd);
+        else vt_strip<T, S0, 0>(xb, xa, bv, g, d, e, c, wd);
+        cur = sw == 0 ? 0 : cur ^ 1;
+        vt_sync<NT0>();
+      }
+      T* xcur = cur == 0 ? xa : xb;
+      T* rbuf = cur == 0 ? xb : xa;
+      vt_strip<T, S0, 2>(xcur, rbuf, bv, g, d, e, c, wd);
+      vt_sync<NT0>();
+      vt_restrict<T, N1, NT0>(rbuf, base + G::off(1) + 2 * G::np(1));
+      vt_sync<NT0>();
+      int ccur = 0;
+      if (threadIdx.x < G::grp(1)) ccur = vt_coarse<T, N1, 1>(base, lv, nu);
+      vt_sync<NT0>();
+      __shared__ int cbuf0;
+      if (threadIdx.x == 0) cbuf0 = ccur;
+      vt_sync<NT0>();
+      vt_prolong<T, N1, NT0>(base + G::off(1) + (cbuf0 == 0 ? 0 : G::np(1)), xcur);
+      vt_sync<NT0>();
+      for (int sw = 0; sw < nu; ++sw) {
+        if (cur == 0) vt_strip<T, S0, 0>(xa, xb, bv, g, d, e, c, wd); else vt_strip<T, S0, 0>(xb, xa, bv, g, d, e, c, wd);
+        cur ^= 1;
+        vt_sync<NT0>();
+      }
     }
-    const T* xcur = cur == 0 ? xa : xb;
-    T* rbuf = cur == 0 ? xb : xa;
-    if (l == 0) strip_pass<T, 2>(xcur, rbuf, bv, g, n1, P.d, P.e, P.c, P.wd);
-    else group_pass<T, 2>(xcur, rbuf, bl, n1, nt, P.d, P.e, P.c, P.wd);
-    vf_sync(nt);
-    T* bc = base + lv[l + 1].off + 2 * (n1c + 2) * (n1c + 2);
-    group_restrict<T>(rbuf, bc, n1, n1c, nt);
-    if (threadIdx.x == 0) curs[l] = cur;
-    vf_sync(nt);
+    __syncthreads();
   }
-  // coarsest level: one node, solved exactly (thread 0 of the smallest group)
-  if (threadIdx.x == 0) {
-    const int l = nlev - 1;
-    T* xa = base + lv[l].off;
-    const T bq = l == 0 ? bv[0] : xa[2 * 9 + 4];          // padded 3 x 3: interior at 4
-    xa[4] = bq / lv[l].d;
-    curs[l] = 0;
-  }
-  // ascent: a level's group waits for the coarser level's (smaller) group
-#pragma unroll 1
-  for (int l = nlev - 2; l >= 0; --l) {
-    const VFLevel<T> P = lv[l];
-    const int nt = P.grp;
-    if (threadIdx.x >= nt) continue;
-    vf_sync(nt);
-    const int n1 = P.n1, n1c = lv[l + 1].n1;
-    const int np = (n1 + 2) * (n1 + 2);
-    T* xa = base + P.off;
-    T* xb = xa + np;
-    const T* bl = xb + np;
-    const T* xca = base + lv[l + 1].off;
-    const T* xc = curs[l + 1] == 0 ? xca : xca + (n1c + 2) * (n1c + 2);
-    int cur = curs[l];
-    group_prolong<T>(xc, cur == 0 ? xa : xb, n1, n1c, nt);
-    vf_sync(nt);
-#pragma unroll 1
-    for (int sw = 0; sw < nu; ++sw) {
-      const T* src = cur == 0 ? xa : xb;
-      T* dst = cur == 0 ? xb : xa;
-      if (l == 0) strip_pass<T, 0>(src, dst, bv, g, n1, P.d, P.e, P.c, P.wd);
-      else group_pass<T, 0>(src, dst, bl, n1, nt, P.d, P.e, P.c, P.wd);
-      cur ^= 1;
-      vf_sync(nt);
-    }
-    if (threadIdx.x == 0) curs[l] = cur;
-  }
+  __shared__ int cfin;
+  if (threadIdx.x == 0) cfin = cur;
   __syncthreads();
-  const T* x0 = base + (curs[0] == 0 ? 0 : (n10 + 2) * (n10 + 2));
-  const int s0 = n10 + 2;
+  const T* x0 = base + (cfin == 0 ? 0 : G::np(0));
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   if (acc) {
     T* A = acc + (col / acc_L) * acc_ss + (acc_col0 + col % acc_L) * int64_t(n0);
-    for (int y = ty; y < n10; y += 32)
-      for (int x = tx; x < n10; x += 32) A[y * n10 + x] += x0[(y + 1) * s0 + x + 1];
+    for (int y = ty; y < N1; y += 32)
+      for (int x = tx; x < N1; x += 32) A[y * N1 + x] += x0[(y + 1) * S0 + x + 1];
   } else {
     T* X = xg + col * n0;
-    for (int y = ty; y < n10; y += 32)
-      for (int x = tx; x < n10; x += 32) X[y * n10 + x] = x0[(y + 1) * s0 + x + 1];
+    for (int y = ty; y < N1; y += 32)
+      for (int x = tx; x < N1; x += 32) X[y * N1 + x] = x0[(y + 1) * S0 + x + 1];
   }
+}
+
+template <typename T, int N1>
+static cudaError_t launch_vt(const T* b, T* x, int64_t B, const FusedLevels& L, T omega, int nu, T* acc,
+                             int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st) {
+  const size_t smem = size_t(VT<N1>::total()) * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(vcycle_t_kernel<T, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  vcycle_t_kernel<T, N1><<<dim3(unsigned(B)), kVFThreads, smem, st>>>(b, x, L, omega, nu, acc, acc_ss, acc_L, acc_col0);
+  return cudaGetLastError();
 }
 
 size_t vcycle_full_smem(const FusedLevels& L, int esize) {
@@ -891,15 +967,22 @@ cudaError_t launch_vcycle_full(const T* b, T* x, int64_t B, const FusedLevels& L
                                int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st) {
   if (B == 0) return cudaSuccess;
   if (!vcycle_full_fits(L, sizeof(T))) return cudaErrorInvalidConfiguration;
-  const size_t smem = vcycle_full_smem(L, sizeof(T));
-  cudaError_t e = cudaFuncSetAttribute(vcycle_full_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
   const double n0 = double(L.n1[0]) * L.n1[0];
   ProfScope ps(KK_VCYCLE_FUSED, st, double(sizeof(T)) * B * n0 * (acc ? 3 : 2),
                double(B) * n0 * (4.0 / 3.0) * (21.0 * 2 * nu + 18.0 + 10.0));
-  vcycle_full_kernel<T><<<dim3(unsigned(B)), kVFThreads, smem, st>>>(b, x, L, omega, nu, acc, acc_ss, acc_L, acc_col0);
+  cudaError_t e;
+  switch (L.n1[0]) {
+    case 1: e = launch_vt<T, 1>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st); break;
+    case 3: e = launch_vt<T, 3>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st); break;
+    case 7: e = launch_vt<T, 7>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st); break;
+    case 15: e = launch_vt<T, 15>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st); break;
+    case 31: e = launch_vt<T, 31>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st); break;
+    case 63: e = launch_vt<T, 63>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st); break;
+    case 127: e = launch_vt<T, 127>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st); break;
+    default: return cudaErrorInvalidConfiguration;
+  }
   note_launch();
-  return cudaGetLastError();
+  return e;
 }
 
 // ---------------------------------------------------------------------------
