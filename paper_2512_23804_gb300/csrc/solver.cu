@@ -47,15 +47,14 @@ struct Carver {
 
 // Where the fused V-cycle starts and which kernel runs it.  Levels above lf use
 // grid-wide level kernels.  float32: up to 127 x 127 interior nodes the whole
-// hierarchy fits one CTA's shared memory; a 4-CTA cluster per column shortens
-// each cycle but costs more SM time, so it is used only when the batch of
-// columns leaves SMs idle (B * C <= 152); 255 x 255 always takes an 8-CTA
-// cluster (no single CTA holds it).  float64 runs at 1/64 of the float32 rate on
-// this GPU: one CTA only up to 15 x 15, clusters of 2-8 CTAs for 31..127 so that
-// each column's cycle is spread over several SMs.
+// hierarchy fits one CTA's shared memory (34 us per 127 x 127 cycle, faster than
+// a 4-CTA cluster per column, 43 us); 255 x 255 takes an 8-CTA cluster (no single
+// CTA holds it).  float64 runs at 1/64 of the float32 rate on this GPU: one CTA
+// only up to 15 x 15, clusters of 2-8 CTAs for 31..127 so that each column's
+// cycle is spread over several SMs.
 struct VPlan { int lf = 0; bool cluster = false; int C = 1; int nd = 0; };
 
-static VPlan plan_vcycle(const sgoc_problem* pb, int esize, int64_t ncols) {
+static VPlan plan_vcycle(const sgoc_problem* pb, int esize) {
   VPlan v;
   const int nl = int(pb->levels.size());
   for (int l = 0; l < nl; ++l) {
@@ -65,7 +64,7 @@ static VPlan plan_vcycle(const sgoc_problem* pb, int esize, int64_t ncols) {
     const int band0 = esize == 4 ? 32 : 16;
     const bool cluster_ok = n1 >= 31 && n1 <= cluster_max;
     const int C = (n1 + 1) / band0;
-    const bool prefer_cluster = cluster_ok && (n1 > single_max || int64_t(C) * ncols <= 152);
+    const bool prefer_cluster = cluster_ok && (n1 > single_max || esize == 8);
     if (n1 <= single_max && !prefer_cluster) { v.lf = l; v.cluster = false; return v; }
     if (cluster_ok) {
       v.lf = l; v.cluster = true; v.C = C;
@@ -104,8 +103,7 @@ static void carve_prec(const sgoc_problem* pb, Carver& c, PrecWS<T>& w) {
   w.RH = c.template take<T>(B * pb->n);
   const int nl = int(pb->levels.size());
   w.lx.assign(nl, nullptr); w.lt.assign(nl, nullptr); w.lb.assign(nl, nullptr);
-  // the level-wise buffers above the fused start do not depend on the column count
-  const int lf = plan_vcycle(pb, sizeof(T), 1 << 30).lf;
+  const int lf = plan_vcycle(pb, sizeof(T)).lf;
   for (int l = 0; l <= lf; ++l) {
     const size_t nlv = size_t(pb->levels[l].n);
     w.lx[l] = c.template take<T>(B * nlv);
@@ -131,7 +129,7 @@ static sgoc_status vcycle(const sgoc_problem* pb, PrecWS<T>& w, const T* b, T* x
   const int nl = int(pb->levels.size());
   const T om = T(pb->opt.omega);
   const int nu = pb->opt.nu_pre;
-  const VPlan vp = plan_vcycle(pb, sizeof(T), B);
+  const VPlan vp = plan_vcycle(pb, sizeof(T));
   const int lf = vp.lf;
   FusedLevels FL;
   ClusterLevels CL;
@@ -249,6 +247,19 @@ static sgoc_status hgs(const sgoc_problem* pb, PrecWS<T>& w, const T* R, T* V, i
   return SGOC_OK;
 }
 
+// Independent pieces of one KKT product or preconditioner application run on two
+// auxiliary streams (parallel branches when captured into a graph).
+struct Fork {
+  cudaStream_t s1 = nullptr, s2 = nullptr;
+  cudaEvent_t e[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+static sgoc_status fork_to(cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
+  SGOC_CUDA_TRY(cudaEventRecord(ev, from));
+  SGOC_CUDA_TRY(cudaStreamWaitEvent(to, ev, 0));
+  return SGOC_OK;
+}
+
 // -------------------------------------------------------------- KKT apply --
 template <typename T>
 static SGArgs<T> sg_full(const sgoc_problem* pb, const T* X, T* Y, T coef) {
@@ -286,20 +297,32 @@ static void mass_add(MassArgs<T>& m, const T* V, int shift, double a, int wflags
 }
 
 template <typename T>
-static sgoc_status kkt_apply(const sgoc_problem* pb, const T* v, T* w, cudaStream_t st) {
+static sgoc_status kkt_apply(const sgoc_problem* pb, const T* v, T* w, cudaStream_t st,
+                             const Fork* f = nullptr) {
   const int64_t F = pb->F, ps = int64_t(pb->P) * pb->n;
   const T* y = v; const T* u = v + F; const T* lam = v + 2 * F;
   T* w1 = w; T* w2 = w + F; T* w3 = w + 2 * F;
   if (pb->nt == 0) {
     // w1 = M Y H^gamma - A Lambda ; w2 = beta M U + M Lambda ; w3 = -A Y + M U   (Eq. (stoch-system))
+    // the three block rows are independent: rows 2 and 3 on the auxiliary streams
+    cudaStream_t s2 = st, s3 = st;
+    if (f) {
+      SGOC_TRY(fork_to(st, f->s1, f->e[0]));
+      SGOC_TRY(fork_to(st, f->s2, f->e[0]));
+      s2 = f->s1; s3 = f->s2;
+    }
     MassArgs<T> m1 = mass_base<T>(pb, w1); mass_add(m1, y, 0, 1.0, 1, ps);
     SGOC_LAUNCH(launch_mass<T>(m1, st));
     SGOC_LAUNCH(launch_sg<T>(sg_full<T>(pb, lam, w1, T(-1)), st));
     MassArgs<T> m2 = mass_base<T>(pb, w2); mass_add(m2, u, 0, pb->beta, 0, ps); mass_add(m2, lam, 0, 1.0, 0, ps);
-    SGOC_LAUNCH(launch_mass<T>(m2, st));
+    SGOC_LAUNCH(launch_mass<T>(m2, s2));
     MassArgs<T> m3 = mass_base<T>(pb, w3); mass_add(m3, u, 0, 1.0, 0, ps);
-    SGOC_LAUNCH(launch_mass<T>(m3, st));
-    SGOC_LAUNCH(launch_sg<T>(sg_full<T>(pb, y, w3, T(-1)), st));
+    SGOC_LAUNCH(launch_mass<T>(m3, s3));
+    SGOC_LAUNCH(launch_sg<T>(sg_full<T>(pb, y, w3, T(-1)), s3));
+    if (f) {
+      SGOC_TRY(fork_to(f->s1, st, f->e[1]));
+      SGOC_TRY(fork_to(f->s2, st, f->e[2]));
+    }
     return SGOC_OK;
   }
   // time (Eq. (KKT:stoch-time-dependent)), A_t = I (x) (M_cal + tau A) - C (x) M_cal:
@@ -307,23 +330,34 @@ static sgoc_status kkt_apply(const sgoc_problem* pb, const T* v, T* w, cudaStrea
   // w2_t = beta tau D_t M U_t + tau M L_t
   // w3_t = -(M Y_t + tau A Y_t - M Y_{t-1}) + tau M U_t
   const double tau = pb->tau;
+  cudaStream_t s2 = st, s3 = st;
+  if (f) {
+    SGOC_TRY(fork_to(st, f->s1, f->e[0]));
+    SGOC_TRY(fork_to(st, f->s2, f->e[0]));
+    s2 = f->s1; s3 = f->s2;
+  }
   MassArgs<T> m1 = mass_base<T>(pb, w1);
   mass_add(m1, y, 0, tau, 3, ps); mass_add(m1, lam, 0, -1.0, 0, ps); mass_add(m1, lam, 1, 1.0, 0, ps);
   SGOC_LAUNCH(launch_mass<T>(m1, st));
   SGOC_LAUNCH(launch_sg<T>(sg_full<T>(pb, lam, w1, T(-tau)), st));
   MassArgs<T> m2 = mass_base<T>(pb, w2);
   mass_add(m2, u, 0, pb->beta * tau, 2, ps); mass_add(m2, lam, 0, tau, 0, ps);
-  SGOC_LAUNCH(launch_mass<T>(m2, st));
+  SGOC_LAUNCH(launch_mass<T>(m2, s2));
   MassArgs<T> m3 = mass_base<T>(pb, w3);
   mass_add(m3, y, 0, -1.0, 0, ps); mass_add(m3, y, -1, 1.0, 0, ps); mass_add(m3, u, 0, tau, 0, ps);
-  SGOC_LAUNCH(launch_mass<T>(m3, st));
-  SGOC_LAUNCH(launch_sg<T>(sg_full<T>(pb, y, w3, T(-tau)), st));
+  SGOC_LAUNCH(launch_mass<T>(m3, s3));
+  SGOC_LAUNCH(launch_sg<T>(sg_full<T>(pb, y, w3, T(-tau)), s3));
+  if (f) {
+    SGOC_TRY(fork_to(f->s1, st, f->e[1]));
+    SGOC_TRY(fork_to(f->s2, st, f->e[2]));
+  }
   return SGOC_OK;
 }
 
 // ------------------------------------------------------ block preconditioner --
 template <typename T>
-static sgoc_status precond_apply(const sgoc_problem* pb, PrecWS<T>& w, const T* r, T* z, cudaStream_t st) {
+static sgoc_status precond_apply(const sgoc_problem* pb, PrecWS<T>& w, const T* r, T* z, cudaStream_t st,
+                                 const Fork* f = nullptr) {
   const int64_t F = pb->F, ps = int64_t(pb->P) * pb->n;
   // blocks 1, 2: Chebyshev on M, scaled by 1/(sc_t H^gamma) and 1/(sc_t beta)
   ChebArgs<T> c{};
@@ -331,13 +365,17 @@ static sgoc_status precond_apply(const sgoc_problem* pb, PrecWS<T>& w, const T* 
   c.ncols = 2 * int64_t(pb->slabs) * pb->P; c.n1 = pb->n1; c.n = pb->n; c.steps = pb->opt.cheb_steps;
   c.mass = T(pb->mass_h2_36); c.scale_mode = 1; c.P = pb->P; c.slabs = pb->slabs; c.nt = pb->nt;
   c.tau = T(pb->tau); c.beta = T(pb->beta); c.gamma = T(pb->gamma);
-  SGOC_LAUNCH(launch_cheb<T>(c, st));
+  // blocks 1, 2 (Chebyshev) are independent of block 3: run them on an auxiliary stream
+  cudaStream_t sc = st;
+  if (f) { SGOC_TRY(fork_to(st, f->s1, f->e[3])); sc = f->s1; }
+  SGOC_LAUNCH(launch_cheb<T>(c, sc));
   // block 3: S^{-1} = Z^{-1} M_gamma Z^{-1} (steady), tau Z~^{-1} (D (x) M_gamma) Z~^{-1} (time)
   SGOC_TRY(hgs<T>(pb, w, r + 2 * F, w.W1, pb->slabs, st));
   MassArgs<T> m = mass_base<T>(pb, w.W2);
   mass_add(m, w.W1, 0, pb->nt > 0 ? pb->tau : 1.0, pb->nt > 0 ? 3 : 1, ps);
   SGOC_LAUNCH(launch_mass<T>(m, st));
   SGOC_TRY(hgs<T>(pb, w, w.W2, z + 2 * F, pb->slabs, st));
+  if (f) SGOC_TRY(fork_to(f->s1, st, f->e[4]));
   return SGOC_OK;
 }
 
@@ -422,6 +460,7 @@ struct Runtime {
   cudaGraphExec_t it[2] = {nullptr, nullptr};
   int64_t nk[2] = {0, 0};
   cudaEvent_t ev = nullptr;            // completion of the pending unit of a solve
+  Fork fork;                           // auxiliary streams of the parallel branches
   void drop_graphs() {
     for (auto& g : it) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
     ws = nullptr; prec = -1;
@@ -430,10 +469,17 @@ struct Runtime {
     drop_graphs();
     if (cap) cudaStreamDestroy(cap);
     if (ev) cudaEventDestroy(ev);
+    if (fork.s1) cudaStreamDestroy(fork.s1);
+    if (fork.s2) cudaStreamDestroy(fork.s2);
+    for (auto& e : fork.e) if (e) cudaEventDestroy(e);
     if (hstate) cudaFreeHost(hstate);
     if (hscal) cudaFreeHost(hscal);
   }
 };
+
+// Parallel branches are left out while per-kernel timing is on: overlapping
+// kernels would inflate each other's event-bracketed durations.
+static const Fork* fork_of(Runtime* rt) { return profile_enabled() ? nullptr : &rt->fork; }
 
 void invalidate_graphs(sgoc_problem* pb) {
   if (pb->runtime) static_cast<Runtime*>(pb->runtime)->drop_graphs();
@@ -452,6 +498,9 @@ static sgoc_status runtime_of(sgoc_problem* pb, Runtime** out) {
     SGOC_CUDA_TRY(cudaMallocHost(&rt->hscal, 16 * sizeof(double)));
     SGOC_CUDA_TRY(cudaStreamCreateWithFlags(&rt->cap, cudaStreamNonBlocking));
     SGOC_CUDA_TRY(cudaEventCreateWithFlags(&rt->ev, cudaEventDisableTiming));
+    SGOC_CUDA_TRY(cudaStreamCreateWithFlags(&rt->fork.s1, cudaStreamNonBlocking));
+    SGOC_CUDA_TRY(cudaStreamCreateWithFlags(&rt->fork.s2, cudaStreamNonBlocking));
+    for (auto& e : rt->fork.e) SGOC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
   *out = static_cast<Runtime*>(pb->runtime);
   return SGOC_OK;
@@ -475,10 +524,10 @@ static sgoc_status norm2(Runtime& rt, const double* a, int64_t n, const Layout& 
 // MINRES start: v_1 = rhs, z_1 = P^{-1} v_1, beta_1 = sqrt(v_1 . z_1), w = 0.
 template <typename T>
 static sgoc_status minres_start(const sgoc_problem* pb, Layout& L, const MinresVecs<T>& m, const T* rhs,
-                                double target, cudaStream_t st) {
+                                double target, cudaStream_t st, const Fork* f) {
   const int64_t N = pb->N;
   SGOC_LAUNCH(launch_scale<T>(rhs, m.v, N, T(1), st));
-  SGOC_TRY(precond_apply<T>(pb, prec_of<T>(L), m.v, m.z, st));
+  SGOC_TRY(precond_apply<T>(pb, prec_of<T>(L), m.v, m.z, st, f));
   SGOC_LAUNCH(launch_dot_partial<T>(m.v, m.z, N, L.k64.partial, st));
   SGOC_LAUNCH(launch_minres_init(L.k64.state, L.k64.partial, target, st));
   SGOC_LAUNCH(launch_fill<T>(m.wm1, N, T(0), st));
@@ -488,13 +537,14 @@ static sgoc_status minres_start(const sgoc_problem* pb, Layout& L, const MinresV
 
 // One MINRES iteration with fixed buffer roles (see swapped()).
 template <typename T, typename TX>
-static sgoc_status minres_step(const sgoc_problem* pb, Layout& L, const MinresVecs<T>& m, TX* x, cudaStream_t st) {
+static sgoc_status minres_step(const sgoc_problem* pb, Layout& L, const MinresVecs<T>& m, TX* x, cudaStream_t st,
+                               const Fork* f) {
   const int64_t N = pb->N;
-  SGOC_TRY(kkt_apply<T>(pb, m.z, m.Kz, st));
+  SGOC_TRY(kkt_apply<T>(pb, m.z, m.Kz, st, f));
   SGOC_LAUNCH(launch_dot_partial<T>(m.z, m.Kz, N, L.k64.partial, st));
   SGOC_LAUNCH(launch_minres_alpha(L.k64.state, L.k64.partial, st));
   SGOC_LAUNCH(launch_minres_v<T>(m.Kz, m.v, m.vp, N, L.k64.state, st));
-  SGOC_TRY(precond_apply<T>(pb, prec_of<T>(L), m.vp, m.zn, st));
+  SGOC_TRY(precond_apply<T>(pb, prec_of<T>(L), m.vp, m.zn, st, f));
   SGOC_LAUNCH(launch_dot_partial<T>(m.vp, m.zn, N, L.k64.partial, st));
   SGOC_LAUNCH(launch_minres_rotate(L.k64.state, L.k64.partial, st));
   SGOC_LAUNCH(launch_minres_wx<T, TX>(m.z, m.wm1, m.wm2, x, N, L.k64.state, st));
@@ -513,7 +563,7 @@ static sgoc_status ensure_graphs(sgoc_problem* pb, Runtime& rt, Layout& L, const
     const MinresVecs<T> mp = par == 0 ? m : swapped(m);
     const int64_t k0 = kernel_launches();
     SGOC_CUDA_TRY(cudaStreamBeginCapture(rt.cap, cudaStreamCaptureModeRelaxed));
-    sgoc_status s = minres_step<T, TX>(pb, L, mp, x, rt.cap);
+    sgoc_status s = minres_step<T, TX>(pb, L, mp, x, rt.cap, &rt.fork);
     cudaError_t ce = cudaMemcpyAsync(rt.hstate, L.k64.state, sizeof(MinresState), cudaMemcpyDeviceToHost, rt.cap);
     cudaGraph_t g = nullptr;
     cudaError_t ee = cudaStreamEndCapture(rt.cap, &g);
@@ -626,13 +676,13 @@ struct SolveTask {
     return record();
   }
   sgoc_status launch_true_residual() {
-    SGOC_TRY(kkt_apply<double>(pb, L.k64.x, L.k64.t, st));
+    SGOC_TRY(kkt_apply<double>(pb, L.k64.x, L.k64.t, st, fork_of(rt)));
     SGOC_LAUNCH(launch_sub(L.k64.b, L.k64.t, L.k64.r, pb->N, st));
     return launch_norm(L.k64.r);
   }
   template <typename T, typename TX>
   sgoc_status launch_start(const T* rhs, double tgt) {
-    SGOC_TRY(minres_start<T>(pb, L, vecs_of<T>(L), rhs, tgt, st));
+    SGOC_TRY(minres_start<T>(pb, L, vecs_of<T>(L), rhs, tgt, st, fork_of(rt)));
     SGOC_CUDA_TRY(cudaMemcpyAsync(rt->hstate, L.k64.state, sizeof(MinresState), cudaMemcpyDeviceToHost, st));
     par = 0;
     return record();
@@ -644,7 +694,7 @@ struct SolveTask {
       add_launches(rt->nk[par]);
     } else {
       const MinresVecs<T>& m = vecs_of<T>(L);
-      SGOC_TRY((minres_step<T, TX>(pb, L, par == 0 ? m : swapped(m), x, st)));
+      SGOC_TRY((minres_step<T, TX>(pb, L, par == 0 ? m : swapped(m), x, st, fork_of(rt))));
       SGOC_CUDA_TRY(cudaMemcpyAsync(rt->hstate, L.k64.state, sizeof(MinresState), cudaMemcpyDeviceToHost, st));
     }
     par ^= 1;
