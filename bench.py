@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--requests", type=int, default=40)
     ap.add_argument("--max-unknowns", type=float, default=6e7,
                     help="serving: skip requests with more KKT unknowns (device memory and run time)")
-    ap.add_argument("--kernel-case", choices=["vcycle128", "sg128", "sg512", "hgs128"], default=None,
+    ap.add_argument("--kernel-case", choices=["vcycle128", "sg128", "sg512", "hgs128", "solve128"], default=None,
                     help="run one kernel class a few times on a small case (for ncu captures) and exit")
     return ap.parse_args()
 
@@ -437,7 +437,16 @@ def run_kernel_case(args):
     case = args.kernel_case
     pr = si.steady_512() if case == "sg512" else si.steady_128(1e-4)
     sp = SGProblem.from_problem(pr, precision="mixed").upload()
-    if case in ("sg128", "sg512"):
+    if case == "solve128":
+        # a few MINRES iterations of the 128x128 workload (loose tolerance), launched eagerly
+        # (per-kernel timing on) so that a profiler sees ordinary launches, not graph nodes
+        from paper_2512_23804_gb300 import abi
+        abi.profile_enable(True)
+        sq = SGProblem.from_problem(pr, precision="mixed", tol=1e-2).upload()
+        for _ in range(2):
+            sq.solve()
+        abi.profile_enable(False)
+    elif case in ("sg128", "sg512"):
         X = torch.randn(sp.n * sp.P, dtype=torch.float32, device="cuda")
         Y = torch.empty_like(X)
         for _ in range(3):

@@ -5,6 +5,7 @@
 // north-east corner of element (ix, iy), the north-west corner of (ix+1, iy), the
 // south-west corner of (ix+1, iy+1) and the south-east corner of (ix, iy+1).
 #include <cooperative_groups.h>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -92,6 +93,66 @@ bool profile_query(int kind, int64_t* launches, double* ms, double* bytes, doubl
   return true;
 }
 
+constexpr size_t kMaxSmem = 227 * 1024;   // dynamic shared memory per CTA on sm_103
+
+// Raise a kernel's dynamic shared-memory limit to everything its static shared
+// memory leaves.  The limit is a property of the function, not of one launch:
+// kept at the maximum, a later and smaller launch never lowers it below what a
+// captured (or replayed) launch needs.
+template <typename F>
+static cudaError_t allow_max_smem(F* f) {
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, f);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMaxSmem - fa.sharedSizeBytes));
+}
+
+// Programmatic dependent launch: every kernel does its work on constant data
+// (tables, shared-memory set-up) first, then waits for the grid it depends on
+// (griddepcontrol.wait returns once that grid has completed and its memory is
+// visible; at once when there is none).  As every kernel waits before it
+// touches memory that other kernels write, the stream order of all reads and
+// writes is kept, transitively along the chain.  A kernel lets its dependants
+// launch (their CTAs then occupy SM resources while they wait) near its end:
+// short kernels right after the wait, long ones before their last phase.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() { pdl_wait(); pdl_trigger(); }
+
+// Streams whose next launch must take a full dependency: the overlap is only
+// for a kernel that directly follows another kernel of this library in the same
+// stream.  After a cross-stream event wait, a copy or a graph launch the next
+// kernel is launched without the attribute (its wait would not cover the work
+// on the other stream, which was seen to race).
+static std::mutex g_fence_mu;
+static std::vector<cudaStream_t> g_fenced;
+
+void pdl_fence(cudaStream_t st) {
+  std::lock_guard<std::mutex> g(g_fence_mu);
+  for (cudaStream_t s : g_fenced)
+    if (s == st) return;
+  g_fenced.push_back(st);
+}
+
+static bool take_fence(cudaStream_t st) {
+  std::lock_guard<std::mutex> g(g_fence_mu);
+  for (size_t i = 0; i < g_fenced.size(); ++i)
+    if (g_fenced[i] == st) { g_fenced[i] = g_fenced.back(); g_fenced.pop_back(); return true; }
+  return false;
+}
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid; cfg.blockDim = block; cfg.dynamicSmemBytes = smem; cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at; cfg.numAttrs = take_fence(st) ? 0 : 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<double> { using type = double4; };
@@ -177,7 +238,24 @@ __global__ void __launch_bounds__(kSGThreads, 2) sg_kernel(SGArgs<T> a, int rows
   const int n1 = a.n1;
   const T* X = a.X + int64_t(t) * a.xs;
   const size_t ring_stride = size_t(nin) * W;
-  if (r0 >= r1) return;
+
+  // neighbour table of the output columns with shared-memory offsets pre-multiplied;
+  // per column only the entries with k < kmax (a prefix: the table is sorted by k)
+  const int ebase = a.nbr_ptr[a.out0];
+  for (int q = tid; q < a.nnz_out; q += kSGThreads) {
+    NbrEntry<T> en;
+    en.ts = (a.nbr_alpha[ebase + q] - a.in0) * TX;
+    en.ks = a.nbr_k[ebase + q] * TX;
+    en.c = a.nbr_c[ebase + q];
+    Es[q] = en;
+  }
+  for (int q = tid; q < nout; q += kSGThreads) {
+    Ps[q] = a.nbr_ptr[a.out0 + q] - ebase;
+    Pe[q] = a.nbr_end[a.out0 + q] - ebase;        // entries with k < kmax (host-computed)
+  }
+
+  pdl_wait();                                        // X (and Y, R) are written by earlier kernels
+  if (r0 >= r1) { pdl_trigger(); return; }
 
   // row gy (-1 and n1 give zeros) into ring slot (gy + 1) % 3
   auto issue_row = [&](int gy) {
@@ -196,22 +274,8 @@ __global__ void __launch_bounds__(kSGThreads, 2) sg_kernel(SGArgs<T> a, int rows
   issue_row(r0 + 1);
   cp_async_commit();
 
-  // neighbour table of the output columns with shared-memory offsets pre-multiplied;
-  // per column only the entries with k < kmax (a prefix: the table is sorted by k)
-  const int ebase = a.nbr_ptr[a.out0];
-  for (int q = tid; q < a.nnz_out; q += kSGThreads) {
-    NbrEntry<T> en;
-    en.ts = (a.nbr_alpha[ebase + q] - a.in0) * TX;
-    en.ks = a.nbr_k[ebase + q] * TX;
-    en.c = a.nbr_c[ebase + q];
-    Es[q] = en;
-  }
-  for (int q = tid; q < nout; q += kSGThreads) {
-    Ps[q] = a.nbr_ptr[a.out0 + q] - ebase;
-    Pe[q] = a.nbr_end[a.out0 + q] - ebase;        // entries with k < kmax (host-computed)
-  }
-
   for (int iy = r0; iy < r1; ++iy) {
+    if (iy == r1 - 1) pdl_trigger();
     cp_async_wait<0>();
     __syncthreads();                                   // rows iy-1..iy+1 landed; previous contraction done
     for (int q = tid; q < (a.M + 1) * TX; q += kSGThreads) {
@@ -288,7 +352,7 @@ static size_t sg_smem(const SGArgs<T>& a) {
 
 template <typename T, int TX>
 static cudaError_t launch_sg_tx(const SGArgs<T>& a, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(sg_kernel<T, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaError_t e = allow_max_smem(sg_kernel<T, TX>);
   if (e != cudaSuccess) return e;
   const int xt = (a.n1 + TX - 1) / TX;
   const int per_sm = std::max(1, std::min(2, int((228 * 1024) / (smem + 1024))));
@@ -304,12 +368,14 @@ static cudaError_t launch_sg_tx(const SGArgs<T>& a, size_t smem, cudaStream_t st
                        w * (a.M + 1.0) * a.nx * a.nx;
   const double flops = cells * (15.0 * nin + 9.0 * nout + 9.0 * (a.c1 != T(0) ? a.deg_sum : 0));
   ProfScope ps(KK_SG, st, bytes, flops);
-  sg_kernel<T, TX><<<grid, kSGThreads, smem, st>>>(a, rows);
+  {
+    const cudaError_t le_ = launch_pdl(sg_kernel<T, TX>, dim3(grid), dim3(kSGThreads), size_t(smem), st,
+                                      a, rows);
+    if (le_ != cudaSuccess) return le_;
+  }
   note_launch();
   return cudaGetLastError();
 }
-
-constexpr size_t kMaxSmem = 227 * 1024;
 
 template <typename T>
 cudaError_t launch_sg(const SGArgs<T>& a, cudaStream_t st) {
@@ -337,31 +403,71 @@ __device__ __forceinline__ T mass_apply(const T* __restrict__ V, int ix, int iy,
   return mass * fma(T(16), C, fma(T(4), edges, corners));
 }
 
+// One thread owns node column ix of a strip of kMassRows rows of one chaos column
+// and slab; it walks the strip keeping the centre value c(y) and the horizontal
+// pair h(y) = V(x-1,y) + V(x+1,y) of three consecutive rows, so every output
+// (h^2/36)(16 c(y) + 4 (c(y-1) + c(y+1) + h(y)) + h(y-1) + h(y+1)) costs three
+// coalesced loads.  blockIdx.y runs over (strip, column, slab) work items.
+constexpr int kMassRows = 8;
+
 template <typename T>
-__global__ void mass_kernel(MassArgs<T> a) {
-  const int64_t total = int64_t(a.nslabs) * a.ncols * a.n;
-  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total; q += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t node = q % a.n;
-    const int64_t cq = q / a.n;
+__device__ __forceinline__ void mass_row(const T* __restrict__ V, int ix, int y, int n1, T& c, T& h) {
+  if (y < 0 || y >= n1) { c = T(0); h = T(0); return; }
+  const T* row = V + int64_t(y) * n1;
+  c = row[ix];
+  h = (ix > 0 ? row[ix - 1] : T(0)) + (ix + 1 < n1 ? row[ix + 1] : T(0));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) mass_kernel(MassArgs<T> a, int strips, int64_t nwork) {
+  pdl_enter();
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ix >= a.n1) return;
+  const int n1 = a.n1;
+  for (int64_t w = blockIdx.y; w < nwork; w += gridDim.y) {
+    const int strip = int(w % strips);
+    const int64_t cq = w / strips;
     const int c = int(cq % a.ncols);
     const int t = int(cq / a.ncols);
-    const int ix = int(node % a.n1), iy = int(node / a.n1);
+    const int y0 = strip * kMassRows;
+    const int ny = min(kMassRows, n1 - y0);
     const int col = a.col0 + c;
     const T hg = col == 0 ? T(1) : T(1) + a.gamma;
     const T dt = (a.nt > 1 && (t == 0 || t == a.nt - 1)) ? T(0.5) : T(1);
-    T* op = a.out + int64_t(t) * a.os + int64_t(c) * a.n + node;
-    T acc = a.cy != T(0) ? a.cy * *op : T(0);
+    T* op = a.out + int64_t(t) * a.os + int64_t(c) * a.n + int64_t(y0) * n1 + ix;
+    T acc[kMassRows];
+#pragma unroll
+    for (int r = 0; r < kMassRows; ++r) acc[r] = (r < ny && a.cy != T(0)) ? a.cy * op[int64_t(r) * n1] : T(0);
     for (int j = 0; j < a.nv; ++j) {
       const int ts = t + a.shift[j];
       if (ts < 0 || ts >= a.nslabs) continue;
-      T w = a.a[j];
-      if (a.wflags[j] & 1) w *= hg;
-      if (a.wflags[j] & 2) w *= dt;
+      T wj = a.a[j];
+      if (a.wflags[j] & 1) wj *= hg;
+      if (a.wflags[j] & 2) wj *= dt;
+      wj *= a.mass;
       const T* V = a.V[j] + int64_t(ts) * a.vs[j] + int64_t(c) * a.n;
-      acc = fma(w, mass_apply(V, ix, iy, a.n1, a.mass), acc);
+      T cm, hm, c0, h0, cp, hp;
+      mass_row(V, ix, y0 - 1, n1, cm, hm);
+      mass_row(V, ix, y0, n1, c0, h0);
+#pragma unroll
+      for (int r = 0; r < kMassRows; ++r) {
+        if (r >= ny) break;
+        mass_row(V, ix, y0 + r + 1, n1, cp, hp);
+        const T edges = (cm + cp) + h0;
+        const T corners = hm + hp;
+        acc[r] = fma(wj, fma(T(16), c0, fma(T(4), edges, corners)), acc[r]);
+        cm = c0; hm = h0; c0 = cp; h0 = hp;
+      }
     }
-    if (a.R) acc = fma(a.ar, a.R[int64_t(t) * a.rs + int64_t(c) * a.n + node], acc);
-    *op = acc;
+    if (a.R) {
+      const T* Rp = a.R + int64_t(t) * a.rs + int64_t(c) * a.n + int64_t(y0) * n1 + ix;
+#pragma unroll
+      for (int r = 0; r < kMassRows; ++r)
+        if (r < ny) acc[r] = fma(a.ar, Rp[int64_t(r) * n1], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < kMassRows; ++r)
+      if (r < ny) op[int64_t(r) * n1] = acc[r];
   }
 }
 
@@ -378,7 +484,15 @@ cudaError_t launch_mass(const MassArgs<T>& a, cudaStream_t st) {
   const double w = sizeof(T);
   ProfScope ps(KK_MASS, st, w * total * (a.nv + 1 + (a.cy != T(0) ? 1 : 0) + (a.R ? 1 : 0)),
                double(total) * (20.0 * a.nv + 2.0));
-  mass_kernel<T><<<grid_for(total, 256), 256, 0, st>>>(a);
+  const int tx = a.n1 >= 128 ? 128 : ((a.n1 + 31) / 32) * 32;
+  const int strips = (a.n1 + kMassRows - 1) / kMassRows;
+  const int64_t nwork = int64_t(strips) * a.ncols * a.nslabs;
+  const dim3 grid(unsigned((a.n1 + tx - 1) / tx), unsigned(nwork < 65535 ? nwork : 65535));
+  {
+    const cudaError_t le_ = launch_pdl(mass_kernel<T>, dim3(grid), dim3(tx), size_t(0), st,
+                                      a, strips, nwork);
+    if (le_ != cudaSuccess) return le_;
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -389,37 +503,128 @@ cudaError_t launch_mass(const MassArgs<T>& a, cudaStream_t st) {
 // omega_1 = 1, omega_2 = 2/(2 - rho^2), omega_{k+1} = 1/(1 - rho^2 omega_k / 4).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void cheb_kernel(const T* __restrict__ B, const T* __restrict__ xk, T* xkm1, T* out, int64_t ncols,
-                            int n1, int64_t n, T mass, T dinv, T omega, int mode, int scale_mode, int P,
-                            int slabs, int nt, T tau, T beta, T gamma) {
-  const int64_t total = ncols * n;
-  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total; q += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t col = q / n, node = q % n;
-    const T b = B[q];
+__device__ __forceinline__ T cheb_scale(const ChebArgs<T>& a, int64_t col) {
+  if (a.scale_mode != 1) return T(1);
+  const int64_t sp = int64_t(a.slabs) * a.P;
+  const int64_t blk = col / sp, cc = col % sp;
+  const int t = int(cc / a.P), al = int(cc % a.P);
+  T s = a.nt > 0 ? a.tau * ((a.nt > 1 && (t == 0 || t == a.nt - 1)) ? T(0.5) : T(1)) : T(1);
+  s *= blk == 0 ? (al == 0 ? T(1) : T(1) + a.gamma) : a.beta;
+  return T(1) / s;
+}
+
+// omega_{k+1} of the Golub-Varga recurrence (omega_1 = 1), in float64 on host and device alike
+__host__ __device__ __forceinline__ double cheb_omega(int k, double rho, double prev) {
+  if (k == 0) return 1.0;
+  if (k == 1) return 2.0 / (2.0 - rho * rho);
+  return 1.0 / (1.0 - rho * rho * prev / 4.0);
+}
+
+// float32, all steps for one column in one CTA: x_k lives in shared memory with a
+// zero border (pitch n1 + 2); thread (tx, ty) owns nodes (tx, ty + j blockDim.y),
+// j < NPT, and keeps their x_{k-1} and x_{k+1} in registers.  Same arithmetic
+// as the per-step kernel below.
+struct ChebWeights { float om[64]; };   // omega_{k+1}, k < steps <= 64, from the host
+
+template <int NPT>
+__global__ void __launch_bounds__(1024, 1) cheb_fused_kernel(ChebArgs<float> a, float dinv, ChebWeights w) {
+  pdl_wait();
+  extern __shared__ __align__(16) unsigned char cheb_smem[];
+  float* S = reinterpret_cast<float*>(cheb_smem);
+  const int n1 = a.n1, pitch = n1 + 2;
+  const int n = n1 * n1;
+  const int tx = threadIdx.x, ty = threadIdx.y, by = blockDim.y;
+  const int tid = ty * blockDim.x + tx, nt = blockDim.x * blockDim.y;
+  const bool own = tx < n1;
+  const float mass = a.mass;
+  for (int64_t col = blockIdx.x; col < a.ncols; col += gridDim.x) {
+    const float* __restrict__ B = a.B + col * n;
+    float* __restrict__ O = a.X + col * n;
+    const float sc = cheb_scale(a, col);
+    for (int q = tid; q < pitch * pitch; q += nt) S[q] = 0.f;
+    float xp[NPT], xn[NPT];
+    // x_1 = D^{-1} b (x_0 = 0)
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+      const int iy = ty + j * by;
+      xp[j] = 0.f;
+      xn[j] = (own && iy < n1) ? dinv * B[iy * n1 + tx] : 0.f;
+    }
+    __syncthreads();
+    if (a.steps == 1) {
+      pdl_trigger();
+#pragma unroll
+      for (int j = 0; j < NPT; ++j) {
+        const int iy = ty + j * by;
+        if (own && iy < n1) O[iy * n1 + tx] = sc * xn[j];
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < NPT; ++j) {
+        const int iy = ty + j * by;
+        if (own && iy < n1) S[(iy + 1) * pitch + tx + 1] = xn[j];
+      }
+    }
+    for (int k = 1; k < a.steps; ++k) {
+      __syncthreads();
+      if (k == a.steps - 1) pdl_trigger();
+      const float om = w.om[k];
+#pragma unroll
+      for (int j = 0; j < NPT; ++j) {
+        const int iy = ty + j * by;
+        if (own && iy < n1) {
+          const float* c = S + (iy + 1) * pitch + tx + 1;
+          const float C = c[0];
+          const float edges = (c[pitch] + c[-pitch]) + (c[1] + c[-1]);
+          const float corners = (c[pitch + 1] + c[pitch - 1]) + (c[1 - pitch] + c[-1 - pitch]);
+          const float r = B[iy * n1 + tx] - mass * fmaf(16.f, C, fmaf(4.f, edges, corners));
+          xn[j] = fmaf(om, fmaf(dinv, r, C - xp[j]), xp[j]);
+          xp[j] = C;
+        }
+      }
+      if (k == a.steps - 1) {
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+          const int iy = ty + j * by;
+          if (own && iy < n1) O[iy * n1 + tx] = sc * xn[j];
+        }
+      } else {
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+          const int iy = ty + j * by;
+          if (own && iy < n1) S[(iy + 1) * pitch + tx + 1] = xn[j];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// One step for columns that do not fit in shared memory: blockIdx.y runs over
+// columns, x over the nodes of a column.
+template <typename T>
+__global__ void cheb_kernel(ChebArgs<T> a, const T* __restrict__ xk, T* xkm1, T* out, T dinv, T omega, int mode) {
+  pdl_enter();
+  const int n1 = a.n1;
+  const int n = n1 * n1;
+  const int node = blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= n) return;
+  const int iy = node / n1, ix = node - iy * n1;
+  for (int64_t col = blockIdx.y; col < a.ncols; col += gridDim.y) {
+    const int64_t q = col * n + node;
+    const T b = a.B[q];
     T x;
     if (mode == 0) {
       x = dinv * b;                                 // x_1 = D^{-1} b (x_0 = 0)
     } else {
-      const int ix = int(node % n1), iy = int(node / n1);
       const T* Xc = xk + col * n;
-      const T r = b - mass_apply(Xc, ix, iy, n1, mass);
+      const T r = b - mass_apply(Xc, ix, iy, n1, a.mass);
       const T xprev = mode == 1 ? T(0) : xkm1[q];
       x = fma(omega, fma(dinv, r, Xc[node] - xprev), xprev);
     }
-    if (out) {
-      T sc = T(1);
-      if (scale_mode == 1) {
-        const int64_t blk = col / (int64_t(slabs) * P);
-        const int64_t cc = col % (int64_t(slabs) * P);
-        const int t = int(cc / P), al = int(cc % P);
-        T s = nt > 0 ? tau * ((nt > 1 && (t == 0 || t == nt - 1)) ? T(0.5) : T(1)) : T(1);
-        s *= blk == 0 ? (al == 0 ? T(1) : T(1) + gamma) : beta;
-        sc = T(1) / s;
-      }
-      out[q] = sc * x;
-    } else {
-      xkm1[q] = x;
-    }
+    if (out) out[q] = cheb_scale(a, col) * x;
+    else xkm1[q] = x;
   }
 }
 
@@ -430,19 +635,50 @@ cudaError_t launch_cheb(const ChebArgs<T>& a, cudaStream_t st) {
   const double lmin = 0.25, lmax = 2.25;
   const double gam = 0.5 * (lmin + lmax), rho = (lmax - lmin) / (lmax + lmin);
   const T dinv = T(1.0 / (gam * 16.0 * double(a.mass)));
-  const int g = grid_for(total, 256);
+  if constexpr (std::is_same<T, float>::value) if (a.n1 <= 127) {
+    // float32 columns of up to 127 x 127 nodes: one fused launch
+    const int tx = ((a.n1 + 31) / 32) * 32;
+    const int by = 1024 / tx;
+    const int npt = (a.n1 + by - 1) / by;                 // <= 16
+    const size_t fsm = size_t(a.n1 + 2) * (a.n1 + 2) * sizeof(float);
+    const ChebArgs<float>& af = a;
+    auto go = [&](auto kern) -> cudaError_t {
+      cudaError_t e = allow_max_smem(kern);
+      if (e != cudaSuccess) return e;
+      const int64_t g = a.ncols < 65535 ? a.ncols : 65535;
+      // algorithmic: b read and x written once, the iterates stay on chip
+      ProfScope ps(KK_CHEB, st, double(sizeof(T)) * total * 2.0, double(total) * (1.0 + 24.0 * (a.steps - 1)));
+      ChebWeights wts{};
+      double om = 1.0;
+      for (int k = 0; k < a.steps && k < 64; ++k) { om = cheb_omega(k, rho, om); wts.om[k] = float(om); }
+      {
+        const cudaError_t le_ = launch_pdl(kern, dim3(unsigned(g)), (dim3(tx, by)), size_t(fsm), st,
+                                          af, float(dinv), wts);
+        if (le_ != cudaSuccess) return le_;
+      }
+      note_launch();
+      return cudaGetLastError();
+    };
+    if (npt <= 1) return go(cheb_fused_kernel<1>);
+    if (npt <= 4) return go(cheb_fused_kernel<4>);
+    return go(cheb_fused_kernel<16>);
+  }
+  const int n = a.n1 * a.n1;
+  const dim3 grid(unsigned((n + 255) / 256), unsigned(a.ncols < 65535 ? a.ncols : 65535));
   double omega = 1.0;
   // x_{k+1} is written over x_{k-1}: x_1 -> A, x_2 -> B, x_3 -> A, ...
   for (int k = 0; k < a.steps; ++k) {
-    if (k == 1) omega = 2.0 / (2.0 - rho * rho);
-    else if (k >= 2) omega = 1.0 / (1.0 - rho * rho * omega / 4.0);
+    omega = cheb_omega(k, rho, omega);
     T* dst = (k % 2 == 0) ? a.tmpA : a.tmpB;      // buffer receiving x_{k+1}
     const T* xk = (k % 2 == 0) ? a.tmpB : a.tmpA; // x_k
     T* out = (k == a.steps - 1) ? a.X : nullptr;
     const int mode = k == 0 ? 0 : (k == 1 ? 1 : 2);
     ProfScope ps(KK_CHEB, st, double(sizeof(T)) * total * (2 + mode), double(total) * (mode == 0 ? 1.0 : 24.0));
-    cheb_kernel<T><<<g, 256, 0, st>>>(a.B, xk, dst, out, a.ncols, a.n1, a.n, a.mass, dinv, T(omega), mode,
-                                       a.scale_mode, a.P, a.slabs, a.nt, a.tau, a.beta, a.gamma);
+    {
+      const cudaError_t le_ = launch_pdl(cheb_kernel<T>, dim3(grid), dim3(256), size_t(0), st,
+                                        a, xk, dst, out, dinv, T(omega), mode);
+      if (le_ != cudaSuccess) return le_;
+    }
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -465,6 +701,7 @@ __device__ __forceinline__ T stencil_apply(const T* __restrict__ X, int ix, int 
 template <typename T>
 __global__ void smooth_kernel(const T* __restrict__ b, const T* __restrict__ xin, T* xout, int64_t B, int n1, T d,
                               T e, T c, T omega, T* acc, int64_t acc_ss, int acc_L, int acc_col0) {
+  pdl_enter();
   const int64_t n = int64_t(n1) * n1;
   const int64_t total = B * n;
   const T wd = omega / d;
@@ -489,6 +726,7 @@ __global__ void smooth_kernel(const T* __restrict__ b, const T* __restrict__ xin
 
 template <typename T>
 __global__ void residual_kernel(const T* __restrict__ b, const T* __restrict__ x, T* r, int64_t B, int n1, T d, T e, T c) {
+  pdl_enter();
   const int64_t n = int64_t(n1) * n1;
   const int64_t total = B * n;
   for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total; q += int64_t(gridDim.x) * blockDim.x) {
@@ -502,6 +740,7 @@ __global__ void residual_kernel(const T* __restrict__ b, const T* __restrict__ x
 // fine interior (2I+1, 2J+1); weights 1, 1/2, 1/4.
 template <typename T>
 __global__ void restrict_kernel(const T* __restrict__ r, T* bc, int64_t B, int n1f) {
+  pdl_enter();
   const int n1c = (n1f - 1) / 2;
   const int64_t nf = int64_t(n1f) * n1f, nc = int64_t(n1c) * n1c;
   const int64_t total = B * nc;
@@ -527,6 +766,7 @@ __device__ __forceinline__ T ldc(const T* X, int I, int J, int n1c) {
 
 template <typename T>
 __global__ void prolong_kernel(const T* __restrict__ xc, T* xf, int64_t B, int n1f) {
+  pdl_enter();
   const int n1c = (n1f - 1) / 2;
   const int64_t nf = int64_t(n1f) * n1f, nc = int64_t(n1c) * n1c;
   const int64_t total = B * nf;
@@ -552,6 +792,7 @@ __global__ void prolong_kernel(const T* __restrict__ xc, T* xf, int64_t B, int n
 
 template <typename T>
 __global__ void scale_kernel(const T* __restrict__ b, T* x, int64_t cnt, T a) {
+  pdl_enter();
   for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < cnt; q += int64_t(gridDim.x) * blockDim.x)
     x[q] = a * b[q];
 }
@@ -563,8 +804,11 @@ cudaError_t launch_smooth(const T* b, const T* xin, T* xout, int64_t B, int n1, 
   if (total == 0) return cudaSuccess;
   ProfScope ps(KK_SMOOTH, st, double(sizeof(T)) * total * (xin ? 3 : 2) + (acc ? double(sizeof(T)) * total : 0.0),
                double(total) * (xin ? 21.0 : 1.0));
-  smooth_kernel<T><<<grid_for(total, 256), 256, 0, st>>>(b, xin, xout, B, n1, T(s.diag), T(s.edge), T(s.corner),
-                                                          omega, acc, acc_ss, acc_L, acc_col0);
+  {
+    const cudaError_t le_ = launch_pdl(smooth_kernel<T>, dim3(grid_for(total, 256)), dim3(256), size_t(0), st,
+                                      b, xin, xout, B, n1, T(s.diag), T(s.edge), T(s.corner), omega, acc, acc_ss, acc_L, acc_col0);
+    if (le_ != cudaSuccess) return le_;
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -574,7 +818,11 @@ cudaError_t launch_residual(const T* b, const T* x, T* r, int64_t B, int n1, Ste
   const int64_t total = B * int64_t(n1) * n1;
   if (total == 0) return cudaSuccess;
   ProfScope ps(KK_RESIDUAL, st, double(sizeof(T)) * total * 3, double(total) * 18.0);
-  residual_kernel<T><<<grid_for(total, 256), 256, 0, st>>>(b, x, r, B, n1, T(s.diag), T(s.edge), T(s.corner));
+  {
+    const cudaError_t le_ = launch_pdl(residual_kernel<T>, dim3(grid_for(total, 256)), dim3(256), size_t(0), st,
+                                      b, x, r, B, n1, T(s.diag), T(s.edge), T(s.corner));
+    if (le_ != cudaSuccess) return le_;
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -585,7 +833,11 @@ cudaError_t launch_restrict(const T* r, T* bc, int64_t B, int n1f, cudaStream_t 
   const int64_t total = B * int64_t(n1c) * n1c;
   if (total == 0) return cudaSuccess;
   ProfScope ps(KK_RESTRICT, st, double(sizeof(T)) * total * 5, double(total) * 12.0);
-  restrict_kernel<T><<<grid_for(total, 256), 256, 0, st>>>(r, bc, B, n1f);
+  {
+    const cudaError_t le_ = launch_pdl(restrict_kernel<T>, dim3(grid_for(total, 256)), dim3(256), size_t(0), st,
+                                      r, bc, B, n1f);
+    if (le_ != cudaSuccess) return le_;
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -595,7 +847,11 @@ cudaError_t launch_prolong_add(const T* xc, T* xf, int64_t B, int n1f, cudaStrea
   const int64_t total = B * int64_t(n1f) * n1f;
   if (total == 0) return cudaSuccess;
   ProfScope ps(KK_PROLONG, st, double(sizeof(T)) * total * 2.25, double(total) * 3.0);
-  prolong_kernel<T><<<grid_for(total, 256), 256, 0, st>>>(xc, xf, B, n1f);
+  {
+    const cudaError_t le_ = launch_pdl(prolong_kernel<T>, dim3(grid_for(total, 256)), dim3(256), size_t(0), st,
+                                      xc, xf, B, n1f);
+    if (le_ != cudaSuccess) return le_;
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -604,7 +860,11 @@ template <typename T>
 cudaError_t launch_scale(const T* b, T* x, int64_t cnt, T a, cudaStream_t st) {
   if (cnt == 0) return cudaSuccess;
   ProfScope ps(KK_VECTOR, st, 2.0 * sizeof(T) * cnt, 0.0);
-  scale_kernel<T><<<grid_for(cnt, 256), 256, 0, st>>>(b, x, cnt, a);
+  {
+    const cudaError_t le_ = launch_pdl(scale_kernel<T>, dim3(grid_for(cnt, 256)), dim3(256), size_t(0), st,
+                                      b, x, cnt, a);
+    if (le_ != cudaSuccess) return le_;
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -870,6 +1130,7 @@ __global__ void __launch_bounds__(kVFThreads, 1) vcycle_t_kernel(const T* __rest
       A[o] = T(0);
     }
   }
+  pdl_wait();                                        // b and the output are shared with earlier kernels
   const Strip g = strip_of(N1);
   T bv[kStripRows];
   {
@@ -916,14 +1177,18 @@ __global__ void __launch_bounds__(kVFThreads, 1) vcycle_t_kernel(const T* __rest
       vt_sync<NT0>();
       vt_prolong<T, N1, NT0>(base + G::off(1) + (cbuf0 == 0 ? 0 : G::np(1)), xcur);
       vt_sync<NT0>();
+      pdl_trigger();                                   // only the post-smoothing and the write remain
       for (int sw = 0; sw < nu; ++sw) {
         if (cur == 0) vt_strip<T, S0, 0>(xa, xb, bv, g, d, e, c, wd); else vt_strip<T, S0, 0>(xb, xa, bv, g, d, e, c, wd);
         cur ^= 1;
         vt_sync<NT0>();
       }
+    } else {
+      pdl_trigger();
     }
     __syncthreads();
   }
+  if constexpr (N1 == 1) pdl_trigger();
   __shared__ int cfin;
   if (threadIdx.x == 0) cfin = cur;
   __syncthreads();
@@ -944,9 +1209,13 @@ template <typename T, int N1>
 static cudaError_t launch_vt(const T* b, T* x, int64_t B, const FusedLevels& L, T omega, int nu, T* acc,
                              int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st) {
   const size_t smem = size_t(VT<N1>::total()) * sizeof(T);
-  cudaError_t e = cudaFuncSetAttribute(vcycle_t_kernel<T, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaError_t e = allow_max_smem(vcycle_t_kernel<T, N1>);
   if (e != cudaSuccess) return e;
-  vcycle_t_kernel<T, N1><<<dim3(unsigned(B)), kVFThreads, smem, st>>>(b, x, L, omega, nu, acc, acc_ss, acc_L, acc_col0);
+  {
+    const cudaError_t le_ = launch_pdl(vcycle_t_kernel<T, N1>, (dim3(unsigned(B))), dim3(kVFThreads), size_t(smem), st,
+                                      b, x, L, omega, nu, acc, acc_ss, acc_L, acc_col0);
+    if (le_ != cudaSuccess) return le_;
+  }
   return cudaGetLastError();
 }
 
@@ -1116,6 +1385,7 @@ __global__ void __launch_bounds__(kVCThreads) vcycle_cluster_kernel(const T* __r
       if (scr == 0) sx = -1;
     }
   }
+  pdl_wait();
   T bv[kCStrip];
   {
     const T* b0 = bg + col * int64_t(n10) * n10;
@@ -1257,6 +1527,7 @@ __global__ void __launch_bounds__(kVCThreads) vcycle_cluster_kernel(const T* __r
     if (threadIdx.x == 0) curs[l] = cur;
     __syncthreads();
   }
+  pdl_trigger();
   // this rank's band of the level-0 result
   {
     const T* x0 = base + (curs[0] == 0 ? 0 : (L0.band + 2) * L0.s);
@@ -1291,7 +1562,7 @@ cudaError_t launch_vcycle_cluster(const T* b, T* x, int64_t B, const ClusterLeve
   if (B == 0) return cudaSuccess;
   const size_t smem = vcycle_cluster_smem(L, C, sizeof(T));
   if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(vcycle_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaError_t e = allow_max_smem(vcycle_cluster_kernel<T>);
   if (e != cudaSuccess) return e;
   if (C > 8) {
     e = cudaFuncSetAttribute(vcycle_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -1309,10 +1580,14 @@ cudaError_t launch_vcycle_cluster(const T* b, T* x, int64_t B, const ClusterLeve
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  // cluster launches take full stream dependencies on both sides: with programmatic
+  // overlap around this kernel, hGS results were wrong unless it triggered at once
+  take_fence(st);
   const double n0 = double(L.n1[0]) * L.n1[0];
   ProfScope ps(KK_VCYCLE_FUSED, st, double(sizeof(T)) * B * n0 * (acc ? 3 : 2),
                double(B) * n0 * (4.0 / 3.0) * (21.0 * 2 * nu + 18.0 + 10.0));
   e = cudaLaunchKernelEx(&cfg, vcycle_cluster_kernel<T>, b, x, L, omega, nu, acc, acc_ss, acc_L, acc_col0);
+  pdl_fence(st);
   note_launch();
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -1344,6 +1619,7 @@ __device__ double block_sum(double v) {
 
 template <typename T>
 __global__ void __launch_bounds__(256) dot_kernel(const T* __restrict__ a, const T* __restrict__ b, int64_t n, double* partial) {
+  pdl_enter();
   double s = 0.0;
   for (int64_t i = blockIdx.x * int64_t(256) + threadIdx.x; i < n; i += int64_t(kDotBlocks) * 256)
     s = fma(double(a[i]), double(b[i]), s);
@@ -1351,10 +1627,45 @@ __global__ void __launch_bounds__(256) dot_kernel(const T* __restrict__ a, const
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// float32 operands: the four products of a float4 pair are summed in float32
+// and that partial sum is accumulated in float64 (one conversion and one
+// float64 add per four entries; float64 arithmetic runs at 1/64 of the float32
+// rate on this part).  The order is fixed by the grid, so results are reproducible.
+__global__ void __launch_bounds__(256) dot4_kernel(const float4* __restrict__ a, const float4* __restrict__ b,
+                                                   int64_t n4, const float* __restrict__ at,
+                                                   const float* __restrict__ bt, int tail, double* partial) {
+  pdl_enter();
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * int64_t(256) + threadIdx.x; i < n4; i += int64_t(kDotBlocks) * 256) {
+    const float4 x = a[i], y = b[i];
+    const float p = fmaf(x.w, y.w, fmaf(x.z, y.z, fmaf(x.y, y.y, x.x * y.x)));
+    s += double(p);
+  }
+  if (blockIdx.x == 0 && threadIdx.x < tail) s = fma(double(at[threadIdx.x]), double(bt[threadIdx.x]), s);
+  s = block_sum<256>(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
 template <typename T>
 cudaError_t launch_dot_partial(const T* a, const T* b, int64_t n, double* partial, cudaStream_t st) {
   ProfScope ps(KK_DOT, st, double(sizeof(T)) * n * 2, double(n) * 2);
-  dot_kernel<T><<<kDotBlocks, 256, 0, st>>>(a, b, n, partial);
+  const bool aligned = (reinterpret_cast<uintptr_t>(a) % 16 == 0) && (reinterpret_cast<uintptr_t>(b) % 16 == 0);
+  if (sizeof(T) == 4 && aligned) {
+    const float* af = reinterpret_cast<const float*>(a);
+    const float* bf = reinterpret_cast<const float*>(b);
+    const int64_t n4 = n / 4;
+    {
+      const cudaError_t le_ = launch_pdl(dot4_kernel, dim3(kDotBlocks), dim3(256), size_t(0), st,
+                                        reinterpret_cast<const float4*>(af), reinterpret_cast<const float4*>(bf), n4, af + 4 * n4, bf + 4 * n4, int(n - 4 * n4), partial);
+      if (le_ != cudaSuccess) return le_;
+    }
+  } else {
+    {
+      const cudaError_t le_ = launch_pdl(dot_kernel<T>, dim3(kDotBlocks), dim3(256), size_t(0), st,
+                                        a, b, n, partial);
+      if (le_ != cudaSuccess) return le_;
+    }
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -1366,18 +1677,24 @@ __device__ double reduce_partials(const double* partial) {
 }
 
 __global__ void sum_partials_kernel(const double* partial, double* out) {
+  pdl_enter();
   const double s = reduce_partials(partial);
   if (threadIdx.x == 0) *out = s;
 }
 
 cudaError_t launch_sum_partials(const double* partial, double* out, cudaStream_t st) {
   ProfScope ps(KK_SCALAR, st, 8.0 * kDotBlocks, 2.0 * kDotBlocks);
-  sum_partials_kernel<<<1, 256, 0, st>>>(partial, out);
+  {
+    const cudaError_t le_ = launch_pdl(sum_partials_kernel, dim3(1), dim3(256), size_t(0), st,
+                                      partial, out);
+    if (le_ != cudaSuccess) return le_;
+  }
   note_launch();
   return cudaGetLastError();
 }
 
 __global__ void minres_init_kernel(MinresState* s, const double* partial, double target) {
+  pdl_enter();
   const double vz = reduce_partials(partial);
   if (threadIdx.x != 0) return;
   s->dot = vz;
@@ -1395,6 +1712,7 @@ __global__ void minres_init_kernel(MinresState* s, const double* partial, double
 }
 
 __global__ void minres_alpha_kernel(MinresState* s, const double* partial) {
+  pdl_enter();
   const double zkz = reduce_partials(partial);
   if (threadIdx.x != 0) return;
   const double b = s->beta;
@@ -1407,6 +1725,7 @@ __global__ void minres_alpha_kernel(MinresState* s, const double* partial) {
 }
 
 __global__ void minres_rotate_kernel(MinresState* s, const double* partial) {
+  pdl_enter();
   const double vz = reduce_partials(partial);
   if (threadIdx.x != 0) return;
   s->dot = vz;
@@ -1440,19 +1759,31 @@ __global__ void minres_rotate_kernel(MinresState* s, const double* partial) {
 
 cudaError_t launch_minres_init(MinresState* s, const double* partial, double target, cudaStream_t st) {
   ProfScope ps(KK_SCALAR, st, 8.0 * kDotBlocks, 2.0 * kDotBlocks);
-  minres_init_kernel<<<1, 256, 0, st>>>(s, partial, target);
+  {
+    const cudaError_t le_ = launch_pdl(minres_init_kernel, dim3(1), dim3(256), size_t(0), st,
+                                      s, partial, target);
+    if (le_ != cudaSuccess) return le_;
+  }
   note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_minres_alpha(MinresState* s, const double* partial, cudaStream_t st) {
   ProfScope ps(KK_SCALAR, st, 8.0 * kDotBlocks, 2.0 * kDotBlocks);
-  minres_alpha_kernel<<<1, 256, 0, st>>>(s, partial);
+  {
+    const cudaError_t le_ = launch_pdl(minres_alpha_kernel, dim3(1), dim3(256), size_t(0), st,
+                                      s, partial);
+    if (le_ != cudaSuccess) return le_;
+  }
   note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_minres_rotate(MinresState* s, const double* partial, cudaStream_t st) {
   ProfScope ps(KK_SCALAR, st, 8.0 * kDotBlocks, 2.0 * kDotBlocks);
-  minres_rotate_kernel<<<1, 256, 0, st>>>(s, partial);
+  {
+    const cudaError_t le_ = launch_pdl(minres_rotate_kernel, dim3(1), dim3(256), size_t(0), st,
+                                      s, partial);
+    if (le_ != cudaSuccess) return le_;
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -1460,6 +1791,7 @@ cudaError_t launch_minres_rotate(MinresState* s, const double* partial, cudaStre
 template <typename T>
 __global__ void minres_v_kernel(const T* __restrict__ Kz, const T* __restrict__ v, T* vprev, int64_t n,
                                 const MinresState* s) {
+  pdl_enter();
   const T cq = T(s->coef_q), cv = T(s->coef_v), cvp = T(s->coef_vp);
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     T r = cq * Kz[i] - cv * v[i];
@@ -1471,6 +1803,7 @@ __global__ void minres_v_kernel(const T* __restrict__ Kz, const T* __restrict__ 
 template <typename T, typename TX>
 __global__ void minres_wx_kernel(const T* __restrict__ z, const T* __restrict__ wm1, T* wm2, TX* x, int64_t n,
                                  const MinresState* s) {
+  pdl_enter();
   const T wq = T(s->w_q), w1 = T(s->w_m1), w2 = T(s->w_m2);
   const TX xw = TX(s->x_w);
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
@@ -1480,10 +1813,74 @@ __global__ void minres_wx_kernel(const T* __restrict__ z, const T* __restrict__ 
   }
 }
 
+// float32 forms of the two updates on float4 packets; the n % 4 tail entries
+// are done by the first threads of block 0
+__global__ void minres_v4_kernel(const float4* __restrict__ Kz, const float4* __restrict__ v, float4* vprev,
+                                 int64_t n4, const float* Kzt, const float* vt, float* vpt, int tail,
+                                 const MinresState* s) {
+  pdl_enter();
+  const float cq = float(s->coef_q), cv = float(s->coef_v), cvp = float(s->coef_vp);
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n4; i += int64_t(gridDim.x) * blockDim.x) {
+    const float4 k = Kz[i], a = v[i];
+    float4 r = make_float4(cq * k.x - cv * a.x, cq * k.y - cv * a.y, cq * k.z - cv * a.z, cq * k.w - cv * a.w);
+    if (cvp != 0.f) {
+      const float4 p = vprev[i];
+      r.x -= cvp * p.x; r.y -= cvp * p.y; r.z -= cvp * p.z; r.w -= cvp * p.w;
+    }
+    vprev[i] = r;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < tail) {
+    const int i = threadIdx.x;
+    float r = cq * Kzt[i] - cv * vt[i];
+    if (cvp != 0.f) r -= cvp * vpt[i];
+    vpt[i] = r;
+  }
+}
+
+__global__ void minres_wx4_kernel(const float4* __restrict__ z, const float4* __restrict__ wm1, float4* wm2,
+                                  float4* x, int64_t n4, const float* zt, const float* w1t, float* w2t, float* xt,
+                                  int tail, const MinresState* s) {
+  pdl_enter();
+  const float wq = float(s->w_q), w1 = float(s->w_m1), w2 = float(s->w_m2), xw = float(s->x_w);
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n4; i += int64_t(gridDim.x) * blockDim.x) {
+    const float4 a = z[i], b = wm1[i], c = wm2[i];
+    float4 xv = x[i];
+    const float4 w = make_float4(wq * a.x - w1 * b.x - w2 * c.x, wq * a.y - w1 * b.y - w2 * c.y,
+                                 wq * a.z - w1 * b.z - w2 * c.z, wq * a.w - w1 * b.w - w2 * c.w);
+    wm2[i] = w;
+    xv.x += xw * w.x; xv.y += xw * w.y; xv.z += xw * w.z; xv.w += xw * w.w;
+    x[i] = xv;
+  }
+  if (blockIdx.x == 0 && threadIdx.x < tail) {
+    const int i = threadIdx.x;
+    const float w = wq * zt[i] - w1 * w1t[i] - w2 * w2t[i];
+    w2t[i] = w;
+    xt[i] += xw * w;
+  }
+}
+
+static bool al16(const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
+
 template <typename T>
 cudaError_t launch_minres_v(const T* Kz, const T* v, T* vprev, int64_t n, const MinresState* s, cudaStream_t st) {
   ProfScope ps(KK_VECTOR, st, double(sizeof(T)) * n * 4, double(n) * 5);
-  minres_v_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(Kz, v, vprev, n, s);
+  if (sizeof(T) == 4 && al16(Kz) && al16(v) && al16(vprev)) {
+    const float* k = reinterpret_cast<const float*>(Kz);
+    const float* a = reinterpret_cast<const float*>(v);
+    float* p = reinterpret_cast<float*>(vprev);
+    const int64_t n4 = n / 4;
+    {
+      const cudaError_t le_ = launch_pdl(minres_v4_kernel, dim3(grid_for(n4, 256)), dim3(256), size_t(0), st,
+                                         reinterpret_cast<const float4*>(k), reinterpret_cast<const float4*>(a), reinterpret_cast<float4*>(p), n4, k + 4 * n4, a + 4 * n4, p + 4 * n4, int(n - 4 * n4), s);
+      if (le_ != cudaSuccess) return le_;
+    }
+  } else {
+    {
+      const cudaError_t le_ = launch_pdl(minres_v_kernel<T>, dim3(grid_for(n, 256)), dim3(256), size_t(0), st,
+                                        Kz, v, vprev, n, s);
+      if (le_ != cudaSuccess) return le_;
+    }
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -1492,13 +1889,31 @@ template <typename T, typename TX>
 cudaError_t launch_minres_wx(const T* z, const T* wm1, T* wm2, TX* x, int64_t n, const MinresState* s,
                              cudaStream_t st) {
   ProfScope ps(KK_VECTOR, st, double(sizeof(T)) * n * 4 + double(sizeof(TX)) * n * 2, double(n) * 8);
-  minres_wx_kernel<T, TX><<<grid_for(n, 256), 256, 0, st>>>(z, wm1, wm2, x, n, s);
+  if (sizeof(T) == 4 && sizeof(TX) == 4 && al16(z) && al16(wm1) && al16(wm2) && al16(x)) {
+    const float* a = reinterpret_cast<const float*>(z);
+    const float* b = reinterpret_cast<const float*>(wm1);
+    float* c = reinterpret_cast<float*>(wm2);
+    float* xf = reinterpret_cast<float*>(x);
+    const int64_t n4 = n / 4;
+    {
+      const cudaError_t le_ = launch_pdl(minres_wx4_kernel, dim3(grid_for(n4, 256)), dim3(256), size_t(0), st,
+                                         reinterpret_cast<const float4*>(a), reinterpret_cast<const float4*>(b), reinterpret_cast<float4*>(c), reinterpret_cast<float4*>(xf), n4, a + 4 * n4, b + 4 * n4, c + 4 * n4, xf + 4 * n4, int(n - 4 * n4), s);
+      if (le_ != cudaSuccess) return le_;
+    }
+  } else {
+    {
+      const cudaError_t le_ = launch_pdl(minres_wx_kernel<T, TX>, dim3(grid_for(n, 256)), dim3(256), size_t(0), st,
+                                        z, wm1, wm2, x, n, s);
+      if (le_ != cudaSuccess) return le_;
+    }
+  }
   note_launch();
   return cudaGetLastError();
 }
 
 template <typename TA, typename TB>
 __global__ void convert_kernel(const TA* a, TB* b, int64_t n) {
+  pdl_enter();
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     b[i] = TB(a[i]);
 }
@@ -1506,25 +1921,35 @@ template <typename TA, typename TB>
 cudaError_t launch_convert(const TA* a, TB* b, int64_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   ProfScope ps(KK_VECTOR, st, double(sizeof(TA) + sizeof(TB)) * n, 0.0);
-  convert_kernel<TA, TB><<<grid_for(n, 256), 256, 0, st>>>(a, b, n);
+  {
+    const cudaError_t le_ = launch_pdl(convert_kernel<TA, TB>, dim3(grid_for(n, 256)), dim3(256), size_t(0), st,
+                                      a, b, n);
+    if (le_ != cudaSuccess) return le_;
+  }
   note_launch();
   return cudaGetLastError();
 }
 
 __global__ void sub_kernel(const double* a, const double* b, double* y, int64_t n) {
+  pdl_enter();
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     y[i] = a[i] - b[i];
 }
 cudaError_t launch_sub(const double* a, const double* b, double* y, int64_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   ProfScope ps(KK_VECTOR, st, 24.0 * n, 0.0);
-  sub_kernel<<<grid_for(n, 256), 256, 0, st>>>(a, b, y, n);
+  {
+    const cudaError_t le_ = launch_pdl(sub_kernel, dim3(grid_for(n, 256)), dim3(256), size_t(0), st,
+                                      a, b, y, n);
+    if (le_ != cudaSuccess) return le_;
+  }
   note_launch();
   return cudaGetLastError();
 }
 
 template <typename T>
 __global__ void add_to_kernel(const T* d, double* x, int64_t n) {
+  pdl_enter();
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     x[i] += double(d[i]);
 }
@@ -1532,44 +1957,63 @@ template <typename T>
 cudaError_t launch_add_to(const T* d, double* x, int64_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   ProfScope ps(KK_VECTOR, st, (sizeof(T) + 16.0) * n, 0.0);
-  add_to_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(d, x, n);
+  {
+    const cudaError_t le_ = launch_pdl(add_to_kernel<T>, dim3(grid_for(n, 256)), dim3(256), size_t(0), st,
+                                      d, x, n);
+    if (le_ != cudaSuccess) return le_;
+  }
   note_launch();
   return cudaGetLastError();
 }
 
 __global__ void add_scaled_kernel(const float* d, double* x, int64_t n, double a) {
+  pdl_enter();
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     x[i] = fma(a, double(d[i]), x[i]);
 }
 cudaError_t launch_add_scaled(const float* d, double* x, int64_t n, double a, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   ProfScope ps(KK_VECTOR, st, 20.0 * n, 0.0);
-  add_scaled_kernel<<<grid_for(n, 256), 256, 0, st>>>(d, x, n, a);
+  {
+    const cudaError_t le_ = launch_pdl(add_scaled_kernel, dim3(grid_for(n, 256)), dim3(256), size_t(0), st,
+                                      d, x, n, a);
+    if (le_ != cudaSuccess) return le_;
+  }
   note_launch();
   return cudaGetLastError();
 }
 
 __global__ void scale_to32_kernel(const double* x, float* y, int64_t n, double a) {
+  pdl_enter();
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
     y[i] = float(a * x[i]);
 }
 cudaError_t launch_scale_to32(const double* x, float* y, int64_t n, double a, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   ProfScope ps(KK_VECTOR, st, 12.0 * n, 0.0);
-  scale_to32_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, y, n, a);
+  {
+    const cudaError_t le_ = launch_pdl(scale_to32_kernel, dim3(grid_for(n, 256)), dim3(256), size_t(0), st,
+                                      x, y, n, a);
+    if (le_ != cudaSuccess) return le_;
+  }
   note_launch();
   return cudaGetLastError();
 }
 
 template <typename T>
 __global__ void fill_kernel(T* x, int64_t n, T v) {
+  pdl_enter();
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) x[i] = v;
 }
 template <typename T>
 cudaError_t launch_fill(T* x, int64_t n, T v, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   ProfScope ps(KK_VECTOR, st, double(sizeof(T)) * n, 0.0);
-  fill_kernel<T><<<grid_for(n, 256), 256, 0, st>>>(x, n, v);
+  {
+    const cudaError_t le_ = launch_pdl(fill_kernel<T>, dim3(grid_for(n, 256)), dim3(256), size_t(0), st,
+                                      x, n, v);
+    if (le_ != cudaSuccess) return le_;
+  }
   note_launch();
   return cudaGetLastError();
 }

@@ -8,6 +8,10 @@ namespace sgoc {
 
 // Number of kernels this library has launched in the process (all streams).
 int64_t kernel_launches();
+// The next kernel this library launches on `st` takes a full stream dependency
+// (no programmatic overlap): call after a cross-stream event wait, a copy or a
+// graph launch on `st`.
+void pdl_fence(cudaStream_t st);
 void add_launches(int64_t n);
 bool profile_enabled();
 

@@ -87,6 +87,7 @@ extern "C" sgoc_status sgoc_apply_chebyshev_noalloc(sgoc_problem* pb, int32_t pr
   if (!pb->uploaded) { set_error("call sgoc_problem_upload first"); return SGOC_ERR_NOT_UPLOADED; }
   if (!d_R || !d_X || ncols < 1) { set_error("bad arguments"); return SGOC_ERR_INVALID_ARG; }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  pdl_fence(st);                                   // the caller's prior work on st
   if (precision == 0) return cheb_noalloc<double>(pb, d_R, d_X, ncols, st);
   if (precision == 1) return cheb_noalloc<float>(pb, d_R, d_X, ncols, st);
   set_error("precision must be 0 or 1");

@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "kernels.h"
 #include "sgoc_internal.h"
 
 namespace sgoc {
@@ -297,6 +298,7 @@ sgoc_status sgoc_problem_upload(sgoc_problem* pb, void* d_persistent, size_t byt
     SGOC_CUDA_TRY(cudaMemsetAsync(pb->dev.y0, 0, size_t(pb->n) * 8, st));
   // the host vectors above go out of scope: finish the copies first
   SGOC_CUDA_TRY(cudaStreamSynchronize(st));
+  pdl_fence(st);
   pb->uploaded = true;
   return SGOC_OK;
 }

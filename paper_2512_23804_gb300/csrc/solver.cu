@@ -257,6 +257,7 @@ struct Fork {
 static sgoc_status fork_to(cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
   SGOC_CUDA_TRY(cudaEventRecord(ev, from));
   SGOC_CUDA_TRY(cudaStreamWaitEvent(to, ev, 0));
+  pdl_fence(to);
   return SGOC_OK;
 }
 
@@ -508,6 +509,7 @@ static sgoc_status runtime_of(sgoc_problem* pb, Runtime** out) {
 
 static sgoc_status sync_state(Runtime& rt, const Layout& L, cudaStream_t st) {
   SGOC_CUDA_TRY(cudaMemcpyAsync(rt.hstate, L.k64.state, sizeof(MinresState), cudaMemcpyDeviceToHost, st));
+  pdl_fence(st);
   SGOC_CUDA_TRY(cudaStreamSynchronize(st));
   return SGOC_OK;
 }
@@ -516,6 +518,7 @@ static sgoc_status norm2(Runtime& rt, const double* a, int64_t n, const Layout& 
   SGOC_LAUNCH(launch_dot_partial<double>(a, a, n, L.k64.partial, st));
   SGOC_LAUNCH(launch_sum_partials(L.k64.partial, L.k64.scal, st));
   SGOC_CUDA_TRY(cudaMemcpyAsync(rt.hscal, L.k64.scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+  pdl_fence(st);
   SGOC_CUDA_TRY(cudaStreamSynchronize(st));
   *out = std::sqrt(rt.hscal[0]);
   return SGOC_OK;
@@ -589,6 +592,7 @@ template <typename T, typename TX>
 static sgoc_status run_step(sgoc_problem* pb, Runtime& rt, Layout& L, bool graphs, int par, TX* x, cudaStream_t st) {
   if (graphs) {
     SGOC_CUDA_TRY(cudaGraphLaunch(rt.it[par], st));
+    pdl_fence(st);
     add_launches(rt.nk[par]);
     SGOC_CUDA_TRY(cudaStreamSynchronize(st));
     return SGOC_OK;
@@ -673,6 +677,7 @@ struct SolveTask {
     SGOC_LAUNCH(launch_dot_partial<double>(a, a, pb->N, L.k64.partial, st));
     SGOC_LAUNCH(launch_sum_partials(L.k64.partial, L.k64.scal, st));
     SGOC_CUDA_TRY(cudaMemcpyAsync(rt->hscal, L.k64.scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+    pdl_fence(st);
     return record();
   }
   sgoc_status launch_true_residual() {
@@ -684,6 +689,7 @@ struct SolveTask {
   sgoc_status launch_start(const T* rhs, double tgt) {
     SGOC_TRY(minres_start<T>(pb, L, vecs_of<T>(L), rhs, tgt, st, fork_of(rt)));
     SGOC_CUDA_TRY(cudaMemcpyAsync(rt->hstate, L.k64.state, sizeof(MinresState), cudaMemcpyDeviceToHost, st));
+    pdl_fence(st);
     par = 0;
     return record();
   }
@@ -691,11 +697,13 @@ struct SolveTask {
   sgoc_status launch_iter(TX* x) {
     if (graphs) {
       SGOC_CUDA_TRY(cudaGraphLaunch(rt->it[par], st));
+      pdl_fence(st);
       add_launches(rt->nk[par]);
     } else {
       const MinresVecs<T>& m = vecs_of<T>(L);
       SGOC_TRY((minres_step<T, TX>(pb, L, par == 0 ? m : swapped(m), x, st, fork_of(rt))));
       SGOC_CUDA_TRY(cudaMemcpyAsync(rt->hstate, L.k64.state, sizeof(MinresState), cudaMemcpyDeviceToHost, st));
+      pdl_fence(st);
     }
     par ^= 1;
     return record();
@@ -704,6 +712,7 @@ struct SolveTask {
     status = s;
     phase = DONE;
     cudaError_t e = cudaMemcpyAsync(x_out, L.k64.x, pb->N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    pdl_fence(st);
     if (status == SGOC_OK && e != cudaSuccess) status = cuda_status(e, "copy solution");
     result.status = status;
     return status;
@@ -718,6 +727,7 @@ struct SolveTask {
   sgoc_status begin(sgoc_problem* p, void* d_ws, size_t ws_bytes, const double* d_x0, double* d_x, cudaStream_t s) {
     t0 = std::chrono::steady_clock::now();
     pb = p; ws = d_ws; x0 = d_x0; x_out = d_x; st = s;
+    pdl_fence(st);                                 // the caller's prior work on st
     result = sgoc_result{};
     status = SGOC_OK;
     bnorm = target = rn = 0;
@@ -743,8 +753,12 @@ struct SolveTask {
         bnorm = std::sqrt(rt->hscal[0]);
         if (bnorm == 0.0) { SGOC_LAUNCH(launch_fill<double>(L.k64.x, N, 0.0, st)); return finish(SGOC_OK); }
         if (!std::isfinite(bnorm)) { set_error("non-finite right-hand side"); return fail(SGOC_ERR_NAN); }
-        if (x0) SGOC_CUDA_TRY(cudaMemcpyAsync(L.k64.x, x0, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        else SGOC_LAUNCH(launch_fill<double>(L.k64.x, N, 0.0, st));
+        if (x0) {
+          SGOC_CUDA_TRY(cudaMemcpyAsync(L.k64.x, x0, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+          pdl_fence(st);
+        } else {
+          SGOC_LAUNCH(launch_fill<double>(L.k64.x, N, 0.0, st));
+        }
         if (pb->opt.precision != SGOC_FP64) { phase = OUTER; return launch_true_residual(); }
         if (x0) { phase = R0; return launch_true_residual(); }
         target = tol;
@@ -791,6 +805,7 @@ struct SolveTask {
         SGOC_CUDA_TRY(cudaMemcpyAsync(&L.k64.state->target, &rt->hstate->target, sizeof(double),
                                       cudaMemcpyHostToDevice, st));
         SGOC_CUDA_TRY(cudaMemcpyAsync(&L.k64.state->flag, &rt->hstate->flag, sizeof(int), cudaMemcpyHostToDevice, st));
+        pdl_fence(st);
         phase = ITER64;
         return launch_iter<double, double>(L.k64.x);
       }
@@ -1083,7 +1098,9 @@ const char* sgoc_kernel_kind_name(int32_t kind) { return kernel_kind_name(kind);
 sgoc_status sgoc_rhs(sgoc_problem* pb, double* d_b, void* stream) {
   SGOC_TRY(check_ready(pb));
   if (!d_b) { set_error("null output"); return SGOC_ERR_INVALID_ARG; }
-  return rhs_apply(pb, d_b, static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  pdl_fence(st);                                   // the caller's prior work on st
+  return rhs_apply(pb, d_b, st);
 }
 
 sgoc_status sgoc_solve(sgoc_problem* pb, void* d_ws, size_t ws_bytes, const double* d_x0, double* d_x,
@@ -1092,6 +1109,7 @@ sgoc_status sgoc_solve(sgoc_problem* pb, void* d_ws, size_t ws_bytes, const doub
   if (!d_x) { set_error("null solution buffer"); return SGOC_ERR_INVALID_ARG; }
   SGOC_TRY(check_ws(d_ws, ws_bytes, workspace_bytes(pb, pb->opt.precision)));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  pdl_fence(st);                                   // the caller's prior work on st
   SolveTask task;
   sgoc_status s = task.begin(pb, d_ws, ws_bytes, d_x0, d_x, st);
   if (s != SGOC_OK) task.fail(s);
@@ -1156,6 +1174,7 @@ sgoc_status sgoc_apply_operator(sgoc_problem* pb, int32_t precision, const void*
   SGOC_TRY(check_ready(pb));
   if (!d_X || !d_Y || nslabs < 1) { set_error("bad arguments"); return SGOC_ERR_INVALID_ARG; }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  pdl_fence(st);                                   // the caller's prior work on st
   if (precision == 0) {
     SGArgs<double> g = sg_full<double>(pb, static_cast<const double*>(d_X), static_cast<double*>(d_Y), 1.0);
     g.cy = 0.0; g.nslabs = nslabs;
@@ -1174,6 +1193,7 @@ sgoc_status sgoc_apply_kkt(sgoc_problem* pb, int32_t precision, const void* d_v,
   SGOC_TRY(check_ready(pb));
   if (!d_v || !d_w) { set_error("bad arguments"); return SGOC_ERR_INVALID_ARG; }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  pdl_fence(st);                                   // the caller's prior work on st
   if (precision == 0) return kkt_apply<double>(pb, static_cast<const double*>(d_v), static_cast<double*>(d_w), st);
   if (precision == 1) return kkt_apply<float>(pb, static_cast<const float*>(d_v), static_cast<float*>(d_w), st);
   set_error("precision must be 0 or 1");
@@ -1185,6 +1205,7 @@ sgoc_status sgoc_apply_precond(sgoc_problem* pb, int32_t precision, const void* 
   SGOC_TRY(check_ready(pb));
   if (!d_r || !d_z) { set_error("bad arguments"); return SGOC_ERR_INVALID_ARG; }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  pdl_fence(st);                                   // the caller's prior work on st
   if (precision == 0) {
     PrecWS<double> w; SGOC_TRY(prec_hook(pb, d_ws, ws_bytes, w));
     return precond_apply<double>(pb, w, static_cast<const double*>(d_r), static_cast<double*>(d_z), st);
@@ -1202,6 +1223,7 @@ sgoc_status sgoc_apply_hgs(sgoc_problem* pb, int32_t precision, const void* d_R,
   SGOC_TRY(check_ready(pb));
   if (!d_R || !d_V || nslabs < 1 || nslabs > pb->slabs) { set_error("bad arguments"); return SGOC_ERR_INVALID_ARG; }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  pdl_fence(st);                                   // the caller's prior work on st
   if (precision == 0) {
     PrecWS<double> w; SGOC_TRY(prec_hook(pb, d_ws, ws_bytes, w));
     return hgs<double>(pb, w, static_cast<const double*>(d_R), static_cast<double*>(d_V), nslabs, st);
@@ -1222,6 +1244,7 @@ sgoc_status sgoc_apply_vcycle(sgoc_problem* pb, int32_t precision, const void* d
     return SGOC_ERR_INVALID_ARG;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  pdl_fence(st);                                   // the caller's prior work on st
   if (precision == 0) {
     PrecWS<double> w; SGOC_TRY(prec_hook(pb, d_ws, ws_bytes, w));
     return vcycle<double>(pb, w, static_cast<const double*>(d_R), static_cast<double*>(d_X), ncols, nullptr, 0, 1, 0, st);
@@ -1242,6 +1265,7 @@ sgoc_status sgoc_apply_chebyshev(sgoc_problem* pb, int32_t precision, const void
     return SGOC_ERR_INVALID_ARG;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  pdl_fence(st);                                   // the caller's prior work on st
   if (precision == 0) {
     PrecWS<double> w; SGOC_TRY(prec_hook(pb, d_ws, ws_bytes, w));
     ChebArgs<double> c{};

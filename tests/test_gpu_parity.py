@@ -133,6 +133,21 @@ def test_chebyshev_fp64(case):
     assert rel(X, ref) <= 1e-12
 
 
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-6)])
+def test_chebyshev_large_grid(dtype, tol):
+    """255 x 255 interior nodes: the per-step kernels (one column does not fit in shared memory)."""
+    pr = si.random_small(31, nx=256, M=1, p=1)
+    d = SGData(pr)
+    sp = SGProblem.from_problem(pr)
+    ncols = 2 * d.P
+    B = si.random_panel(32, d.n, ncols)
+    if dtype == torch.float32:
+        B = B.astype(np.float32).astype(np.float64)
+    X = host(sp.apply_chebyshev(dev(B, dtype), ncols))
+    ref = chebyshev(d.Mass, B.reshape(ncols, d.n).T, pr.cheb_steps).T.reshape(-1)
+    assert rel(X, ref) <= tol
+
+
 @pytest.mark.parametrize("case", CASES + TIME_CASES[:2])
 def test_vcycle_fp64(case):
     pr, d, sp = make(case)
