@@ -63,6 +63,8 @@ def load_peaks():
 
 # float64 ALU peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2070 MHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# ncu: vcycle_t_kernel<float, 127>, 56 columns: 3,719,936 B read + 256 B written
+VCYCLE_DRAM_BYTES_PER_COLUMN = (3719936 + 256) / 56
 # float32 non-tensor peak: 152 SMs x 128 FMA/clk x 2 flop x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -361,6 +363,14 @@ def run_ours(args):
                     "traffic": None, "kernel": dom, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
         roof["launches"] = dv["launches"]
         roof["avg_launch_us"] = 1e3 * dv["ms"] / dv["launches"]
+        pr_main = problems[0]
+        if dom == "mg_vcycle_fused" and not esize_fp64 and pr_main.nx == 128:
+            # DRAM bytes per column from the ncu capture of this kernel on 56 columns of the
+            # 128x128 workload (profiles/vcycle_128x128_f32.md), times the average columns per
+            # launch here (each hGS launch reads b and reads + writes the output: 3 x 4 B per node)
+            cols = dv["bytes"] / dv["launches"] / (3 * 4 * pr_main.n)
+            roof["traffic"] = VCYCLE_DRAM_BYTES_PER_COLUMN * cols
+            roof["traffic_note"] = f"ncu DRAM bytes per column x {cols:.1f} columns per launch"
         line["roofline"] = roof
         line["kernel_breakdown"] = {k: {"share": round(v["share"], 4), "launches": v["launches"],
                                         "ms": round(v["ms"], 3),
