@@ -520,12 +520,14 @@ __host__ __device__ __forceinline__ double cheb_omega(int k, double rho, double 
   return 1.0 / (1.0 - rho * rho * prev / 4.0);
 }
 
-// float32, all steps for one column in one CTA: x_k lives in shared memory with a
-// zero border (pitch n1 + 2); thread (tx, ty) owns nodes (tx, ty + j blockDim.y),
-// j < NPT, and keeps their x_{k-1} and x_{k+1} in registers.  Same arithmetic
-// as the per-step kernel below.
 struct ChebWeights { float om[64]; };   // omega_{k+1}, k < steps <= 64, from the host
 
+// float32, all steps for one column in one CTA: x_k lives in shared memory with a
+// zero border (pitch n1 + 2).  Thread (tx, ty) owns the vertical strip of NPT
+// consecutive rows ty*NPT .. of column tx and keeps x_{k-1} and x_{k+1} of its
+// nodes in registers; it walks the strip with a three-row window (x-1, x, x+1
+// of rows y-1, y, y+1), so each stencil costs three shared-memory loads.  Same
+// arithmetic (and summation order) as the per-step kernel below.
 template <int NPT>
 __global__ void __launch_bounds__(1024, 1) cheb_fused_kernel(ChebArgs<float> a, float dinv, ChebWeights w) {
   pdl_wait();
@@ -533,71 +535,75 @@ __global__ void __launch_bounds__(1024, 1) cheb_fused_kernel(ChebArgs<float> a, 
   float* S = reinterpret_cast<float*>(cheb_smem);
   const int n1 = a.n1, pitch = n1 + 2;
   const int n = n1 * n1;
-  const int tx = threadIdx.x, ty = threadIdx.y, by = blockDim.y;
+  const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * blockDim.x + tx, nt = blockDim.x * blockDim.y;
-  const bool own = tx < n1;
+  const int y0 = ty * NPT;
+  const int ny = tx < n1 ? max(0, min(NPT, n1 - y0)) : 0;     // rows of this thread
   const float mass = a.mass;
+  // the zero border: rows 0 and n1+1, columns 0 and n1+1 (interiors are written before they are read)
+  for (int q = tid; q < 4 * (n1 + 1); q += nt) {
+    const int side = q / (n1 + 1), pos = q - side * (n1 + 1);
+    const int o = side == 0 ? pos : side == 1 ? (n1 + 1) * pitch + pos + 1 : side == 2 ? (pos + 1) * pitch : pos * pitch + n1 + 1;
+    S[o] = 0.f;
+  }
   for (int64_t col = blockIdx.x; col < a.ncols; col += gridDim.x) {
-    const float* __restrict__ B = a.B + col * n;
-    float* __restrict__ O = a.X + col * n;
+    const float* __restrict__ B = a.B + col * n + int64_t(y0) * n1 + tx;
+    float* __restrict__ O = a.X + col * n + int64_t(y0) * n1 + tx;
     const float sc = cheb_scale(a, col);
-    for (int q = tid; q < pitch * pitch; q += nt) S[q] = 0.f;
     float xp[NPT], xn[NPT];
     // x_1 = D^{-1} b (x_0 = 0)
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
-      const int iy = ty + j * by;
       xp[j] = 0.f;
-      xn[j] = (own && iy < n1) ? dinv * B[iy * n1 + tx] : 0.f;
+      xn[j] = j < ny ? dinv * B[j * n1] : 0.f;
     }
-    __syncthreads();
     if (a.steps == 1) {
       pdl_trigger();
 #pragma unroll
-      for (int j = 0; j < NPT; ++j) {
-        const int iy = ty + j * by;
-        if (own && iy < n1) O[iy * n1 + tx] = sc * xn[j];
-      }
+      for (int j = 0; j < NPT; ++j)
+        if (j < ny) O[j * n1] = sc * xn[j];
     } else {
+      __syncthreads();                                   // the previous column's last reads are done
 #pragma unroll
-      for (int j = 0; j < NPT; ++j) {
-        const int iy = ty + j * by;
-        if (own && iy < n1) S[(iy + 1) * pitch + tx + 1] = xn[j];
-      }
+      for (int j = 0; j < NPT; ++j)
+        if (j < ny) S[(y0 + j + 1) * pitch + tx + 1] = xn[j];
     }
     for (int k = 1; k < a.steps; ++k) {
       __syncthreads();
-      if (k == a.steps - 1) pdl_trigger();
+      const bool last = k == a.steps - 1;
+      if (last) pdl_trigger();
       const float om = w.om[k];
-#pragma unroll
-      for (int j = 0; j < NPT; ++j) {
-        const int iy = ty + j * by;
-        if (own && iy < n1) {
-          const float* c = S + (iy + 1) * pitch + tx + 1;
-          const float C = c[0];
-          const float edges = (c[pitch] + c[-pitch]) + (c[1] + c[-1]);
-          const float corners = (c[pitch + 1] + c[pitch - 1]) + (c[1 - pitch] + c[-1 - pitch]);
-          const float r = B[iy * n1 + tx] - mass * fmaf(16.f, C, fmaf(4.f, edges, corners));
-          xn[j] = fmaf(om, fmaf(dinv, r, C - xp[j]), xp[j]);
-          xp[j] = C;
-        }
-      }
-      if (k == a.steps - 1) {
+      if (ny > 0) {
+        const float* p = S + y0 * pitch + tx;            // row y0 - 1 (padded row y0), column x - 1
+        float l0 = p[0], c0 = p[1], r0 = p[2];
+        p += pitch;
+        float l1 = p[0], c1 = p[1], r1 = p[2];
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
-          const int iy = ty + j * by;
-          if (own && iy < n1) O[iy * n1 + tx] = sc * xn[j];
+          if (j < ny) {
+            p += pitch;
+            const float l2 = p[0], c2 = p[1], r2 = p[2];
+            const float edges = (c2 + c0) + (r1 + l1);
+            const float corners = (r2 + l2) + (r0 + l0);
+            const float r = B[j * n1] - mass * fmaf(16.f, c1, fmaf(4.f, edges, corners));
+            xn[j] = fmaf(om, fmaf(dinv, r, c1 - xp[j]), xp[j]);
+            xp[j] = c1;
+            l0 = l1; c0 = c1; r0 = r1;
+            l1 = l2; c1 = c2; r1 = r2;
+          }
         }
+      }
+      if (last) {
+#pragma unroll
+        for (int j = 0; j < NPT; ++j)
+          if (j < ny) O[j * n1] = sc * xn[j];
       } else {
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < NPT; ++j) {
-          const int iy = ty + j * by;
-          if (own && iy < n1) S[(iy + 1) * pitch + tx + 1] = xn[j];
-        }
+        for (int j = 0; j < NPT; ++j)
+          if (j < ny) S[(y0 + j + 1) * pitch + tx + 1] = xn[j];
       }
     }
-    __syncthreads();
   }
 }
 

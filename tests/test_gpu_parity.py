@@ -133,6 +133,19 @@ def test_chebyshev_fp64(case):
     assert rel(X, ref) <= 1e-12
 
 
+@pytest.mark.parametrize("nx,M,p", [(128, 2, 2), (64, 3, 2), (16, 2, 2), (4, 1, 1)])
+def test_chebyshev_fp32_fused(nx, M, p):
+    """float32 columns of up to 127 x 127 nodes: all steps in one CTA per column."""
+    pr = si.random_small(33 + nx, nx=nx, M=M, p=p)
+    d = SGData(pr)
+    sp = SGProblem.from_problem(pr)
+    ncols = 2 * d.P
+    B = si.random_panel(34, d.n, ncols).astype(np.float32).astype(np.float64)
+    X = host(sp.apply_chebyshev(dev(B, torch.float32), ncols))
+    ref = chebyshev(d.Mass, B.reshape(ncols, d.n).T, pr.cheb_steps).T.reshape(-1)
+    assert rel(X, ref) <= 2e-6
+
+
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-6)])
 def test_chebyshev_large_grid(dtype, tol):
     """255 x 255 interior nodes: the per-step kernels (one column does not fit in shared memory)."""
