@@ -377,10 +377,249 @@ static cudaError_t launch_sg_tx(const SGArgs<T>& a, size_t smem, cudaStream_t st
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// SG apply, quad form: one thread computes four adjacent nodes of one output
+// column, so each neighbour-table entry (alpha, k, c) costs eight 4-wide
+// shared-memory loads (kappa_k and T_e(alpha) of the four nodes, one plane per
+// element) and 20 FMAs for four outputs.  Element terms and kappa are stored
+// node-planar ([column][element][node]); the per-node arithmetic and its order
+// are those of sg_kernel above.  The output columns are visited in order of
+// their entry count (counting sort in the prologue), so the four columns a warp
+// works on have about the same trip count.
+// ---------------------------------------------------------------------------
+constexpr int kSG4Threads = 256;
+constexpr int kSG4Bins = 40;          // entry counts per column are <= 2M <= 32
+
+template <typename T, int TX>
+static size_t sg4_smem(const SGArgs<T>& a) {
+  const size_t nin = a.in1 - a.in0, nout = a.out1 - a.out0;
+  size_t b = sizeof(T) * (nin * 4 * TX + size_t(a.M + 1) * 4 * TX + (a.cm != T(0) ? nout * TX : 0) +
+                          3 * nin * (TX + 2));
+  b = (b + 15) & ~size_t(15);
+  return b + 16 * size_t(a.nnz_out) + sizeof(int) * (3 * nout + 2 * kSG4Bins);
+}
+
+template <typename T, int TX>
+__global__ void __launch_bounds__(kSG4Threads, 2) sg4_kernel(SGArgs<T> a, int rows_per_cta) {
+  using V4 = typename Vec4<T>::type;
+  constexpr int NQ = TX / 4;          // quads per row of the tile
+  constexpr int W = TX + 2;
+  constexpr int NT = kSG4Threads;
+  extern __shared__ __align__(32) unsigned char sg_smem_raw[];
+  const int nin = a.in1 - a.in0;
+  const int nout = a.out1 - a.out0;
+  const bool use_m = a.cm != T(0);
+  T* Ts = reinterpret_cast<T*>(sg_smem_raw);                 // [nin][4][TX]
+  T* Ks = Ts + size_t(nin) * 4 * TX;                         // [M+1][4][TX]
+  T* Ms = Ks + size_t(a.M + 1) * 4 * TX;                     // [nout][TX] (when cm != 0)
+  T* Xr = Ms + (use_m ? size_t(nout) * TX : 0);              // ring [3][nin][W]
+  const size_t es_off = (size_t(reinterpret_cast<unsigned char*>(Xr + size_t(3) * nin * W) - sg_smem_raw) + 15) &
+                        ~size_t(15);
+  NbrEntry<T>* Es = reinterpret_cast<NbrEntry<T>*>(sg_smem_raw + es_off);       // [nnz_out]
+  int* Ps = reinterpret_cast<int*>(Es + a.nnz_out);          // [nout]
+  int* Pe = Ps + nout;                                       // [nout]
+  int* Ord = Pe + nout;                                      // [nout] output columns by entry count
+  int* Hist = Ord + nout;                                    // [2][kSG4Bins]
+  const V4* Ts4 = reinterpret_cast<const V4*>(Ts);
+  const V4* Ks4 = reinterpret_cast<const V4*>(Ks);
+
+  const int ix0 = blockIdx.x * TX;
+  const int r0 = blockIdx.y * rows_per_cta;
+  const int r1 = min(a.n1, r0 + rows_per_cta);
+  const int t = blockIdx.z;
+  const int tid = threadIdx.x;
+  const int n1 = a.n1;
+  const T* X = a.X + int64_t(t) * a.xs;
+  const size_t ring_stride = size_t(nin) * W;
+
+  // neighbour table of the output columns (offsets in 4-node units) and the visiting order
+  const int ebase = a.nbr_ptr[a.out0];
+  for (int q = tid; q < a.nnz_out; q += NT) {
+    NbrEntry<T> en;
+    en.ts = (a.nbr_alpha[ebase + q] - a.in0) * TX;
+    en.ks = a.nbr_k[ebase + q] * TX;
+    en.c = a.nbr_c[ebase + q];
+    Es[q] = en;
+  }
+  for (int q = tid; q < kSG4Bins; q += NT) Hist[q] = 0;
+  __syncthreads();
+  for (int q = tid; q < nout; q += NT) {
+    const int p0 = a.nbr_ptr[a.out0 + q] - ebase, p1 = a.nbr_end[a.out0 + q] - ebase;
+    Ps[q] = p0;
+    Pe[q] = p1;
+    atomicAdd(&Hist[min(p1 - p0, kSG4Bins - 1)], 1);
+  }
+  __syncthreads();
+  if (tid == 0) {                                    // start of each count class, longest first
+    int acc = 0;
+    for (int b = kSG4Bins - 1; b >= 0; --b) { const int h = Hist[b]; Hist[b] = acc; acc += h; }
+  }
+  __syncthreads();
+  for (int q = tid; q < nout; q += NT) Ord[atomicAdd(&Hist[min(Pe[q] - Ps[q], kSG4Bins - 1)], 1)] = q;
+
+  pdl_wait();                                        // X (and Y, R) are written by earlier kernels
+  if (r0 >= r1) { pdl_trigger(); return; }
+
+  auto issue_row = [&](int gy) {
+    T* dst = Xr + size_t((gy + 1) % 3) * ring_stride;
+    const bool rok = gy >= 0 && gy < n1;
+    for (int q = tid; q < nin * W; q += NT) {
+      const int c = q / W, lx = q - c * W;
+      const int gx = ix0 + lx - 1;
+      const bool ok = rok && gx >= 0 && gx < n1;
+      const T* col = X + int64_t(a.in0 + c) * a.n;
+      cp_async_elem(dst + q, ok ? col + (int64_t(gy) * n1 + gx) : col, ok);
+    }
+  };
+  issue_row(r0 - 1);
+  issue_row(r0);
+  issue_row(r0 + 1);
+  cp_async_commit();
+
+  for (int iy = r0; iy < r1; ++iy) {
+    if (iy == r1 - 1) pdl_trigger();
+    cp_async_wait<0>();
+    __syncthreads();                                   // rows iy-1..iy+1 landed; previous contraction done
+    // kappa_k/6 of the four elements of every node of the row: SW, SE, NE, NW planes
+    for (int q = tid; q < (a.M + 1) * 4 * TX; q += NT) {
+      const int kk = q / (4 * TX), r = q - kk * 4 * TX;
+      const int e = r / TX, lx = r - e * TX;
+      const int ix = min(ix0 + lx, n1 - 1);
+      const int ex = ix + ((e == 1 || e == 2) ? 1 : 0), ey = iy + (e >= 2 ? 1 : 0);
+      Ks[q] = a.kap[int64_t(kk) * a.nx * a.nx + int64_t(ey) * a.nx + ex];
+    }
+    const T* rS = Xr + size_t(iy % 3) * ring_stride;         // row iy-1
+    const T* rC = Xr + size_t((iy + 1) % 3) * ring_stride;   // row iy
+    const T* rN = Xr + size_t((iy + 2) % 3) * ring_stride;   // row iy+1
+    // element terms T_e(alpha) of four nodes per item
+    for (int q = tid; q < nin * NQ; q += NT) {
+      const int c = q / NQ, qd = q - c * NQ;
+      const size_t o = size_t(c) * W + 4 * qd;
+      T s[6], m[6], nn[6];
+#pragma unroll
+      for (int j = 0; j < 6; ++j) { s[j] = rS[o + j]; m[j] = rC[o + j]; nn[j] = rN[o + j]; }
+      T tv[4][4];                                     // [element][node]
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const T SW = s[u], S = s[u + 1], SE = s[u + 2];
+        const T Wv = m[u], C = m[u + 1], E = m[u + 2];
+        const T NW = nn[u], N = nn[u + 1], NE = nn[u + 2];
+        const T c4 = T(4) * C;
+        const T aS = c4 - S, aN = c4 - N;
+        tv[0][u] = fma(T(-2), SW, aS - Wv);
+        tv[1][u] = fma(T(-2), SE, aS - E);
+        tv[2][u] = fma(T(-2), NE, aN - E);
+        tv[3][u] = fma(T(-2), NW, aN - Wv);
+      }
+      V4* dst = reinterpret_cast<V4*>(Ts) + size_t(c) * 4 * NQ + qd;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        V4 v; v.x = tv[e][0]; v.y = tv[e][1]; v.z = tv[e][2]; v.w = tv[e][3];
+        dst[e * NQ] = v;
+      }
+      const int col = a.in0 + c;
+      if (use_m && col >= a.out0 && col < a.out1) {
+        V4 mv;
+        T* mp = &mv.x;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const T edges = (nn[u + 1] + s[u + 1]) + (m[u + 2] + m[u]);
+          const T corners = (nn[u + 2] + nn[u]) + (s[u + 2] + s[u]);
+          mp[u] = a.mass * fma(T(16), m[u + 1], fma(T(4), edges, corners));
+        }
+        reinterpret_cast<V4*>(Ms)[size_t(col - a.out0) * NQ + qd] = mv;
+      }
+    }
+    __syncthreads();                                   // element terms ready; row iy-1 no longer needed
+    if (iy + 1 < r1) { issue_row(iy + 2); cp_async_commit(); }
+    for (int q = tid; q < nout * NQ; q += NT) {
+      const int sl = q / NQ, qd = q - sl * NQ;
+      const int bl = Ord[sl];
+      const int beta = a.out0 + bl;
+      T diag[4], off[4];
+      {
+        const V4* kb = Ks4 + qd;
+        const V4* tb = Ts4 + size_t(beta - a.in0) * TX + qd;
+        const V4 k0 = kb[0], k1 = kb[NQ], k2 = kb[2 * NQ], k3 = kb[3 * NQ];
+        const V4 t0 = tb[0], t1 = tb[NQ], t2 = tb[2 * NQ], t3 = tb[3 * NQ];
+        diag[0] = fma(k3.x, t3.x, fma(k2.x, t2.x, fma(k1.x, t1.x, k0.x * t0.x)));
+        diag[1] = fma(k3.y, t3.y, fma(k2.y, t2.y, fma(k1.y, t1.y, k0.y * t0.y)));
+        diag[2] = fma(k3.z, t3.z, fma(k2.z, t2.z, fma(k1.z, t1.z, k0.z * t0.z)));
+        diag[3] = fma(k3.w, t3.w, fma(k2.w, t2.w, fma(k1.w, t1.w, k0.w * t0.w)));
+      }
+      off[0] = off[1] = off[2] = off[3] = T(0);
+      const int e1 = Pe[bl];
+      for (int e = Ps[bl]; e < e1; ++e) {
+        const NbrEntry<T> en = Es[e];
+        const V4* kb = Ks4 + en.ks + qd;
+        const V4* tb = Ts4 + en.ts + qd;
+        const V4 k0 = kb[0], k1 = kb[NQ], k2 = kb[2 * NQ], k3 = kb[3 * NQ];
+        const V4 t0 = tb[0], t1 = tb[NQ], t2 = tb[2 * NQ], t3 = tb[3 * NQ];
+        off[0] = fma(en.c, fma(k3.x, t3.x, fma(k2.x, t2.x, fma(k1.x, t1.x, k0.x * t0.x))), off[0]);
+        off[1] = fma(en.c, fma(k3.y, t3.y, fma(k2.y, t2.y, fma(k1.y, t1.y, k0.y * t0.y))), off[1]);
+        off[2] = fma(en.c, fma(k3.z, t3.z, fma(k2.z, t2.z, fma(k1.z, t1.z, k0.z * t0.z))), off[2]);
+        off[3] = fma(en.c, fma(k3.w, t3.w, fma(k2.w, t2.w, fma(k1.w, t1.w, k0.w * t0.w))), off[3]);
+      }
+      const T* mrow = use_m ? Ms + size_t(bl) * TX + 4 * qd : nullptr;
+      const int64_t rowbase = int64_t(iy) * n1;
+      T* ycol = a.Y + int64_t(t) * a.ys + int64_t(beta - a.ycol0) * a.n;
+      const T* rcol = a.R ? a.R + int64_t(t) * a.rs + int64_t(beta - a.rcol0) * a.n : nullptr;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int ix = ix0 + 4 * qd + u;
+        if (ix >= n1) break;
+        T out = a.c0 * diag[u] + a.c1 * off[u];
+        if (use_m) out = fma(a.cm, mrow[u], out);
+        const int64_t node = rowbase + ix;
+        if (rcol) out = fma(a.cr, rcol[node], out);
+        T* yp = ycol + node;
+        if (a.cy != T(0)) out = fma(a.cy, *yp, out);
+        *yp = out;
+      }
+    }
+  }
+  cp_async_wait<0>();
+}
+
+template <typename T, int TX>
+static cudaError_t launch_sg4_tx(const SGArgs<T>& a, size_t smem, cudaStream_t st) {
+  cudaError_t e = allow_max_smem(sg4_kernel<T, TX>);
+  if (e != cudaSuccess) return e;
+  const int xt = (a.n1 + TX - 1) / TX;
+  // resident CTAs per SM: shared memory, and registers (launch bounds: two of 256 threads)
+  const int per_sm = std::max(1, std::min(2, int((228 * 1024) / (smem + 1024))));
+  const int64_t want = int64_t(152) * per_sm;
+  const int64_t tiles = int64_t(xt) * a.nslabs;
+  int rows = int(std::max<int64_t>(1, (tiles * a.n1 + want - 1) / want));
+  rows = std::min(rows, a.n1);
+  dim3 grid(xt, (a.n1 + rows - 1) / rows, a.nslabs);
+  const double w = sizeof(T), cells = double(a.n) * a.nslabs;
+  const int nout = a.out1 - a.out0, nin = a.in1 - a.in0;
+  const double bytes = w * cells * (nin + nout * (1.0 + (a.R ? 1 : 0) + (a.cy != T(0) ? 1 : 0))) +
+                       w * (a.M + 1.0) * a.nx * a.nx;
+  const double flops = cells * (15.0 * nin + 9.0 * nout + 9.0 * (a.c1 != T(0) ? a.deg_sum : 0));
+  ProfScope ps(KK_SG, st, bytes, flops);
+  {
+    const cudaError_t le_ = launch_pdl(sg4_kernel<T, TX>, dim3(grid), dim3(kSG4Threads), size_t(smem), st,
+                                      a, rows);
+    if (le_ != cudaSuccess) return le_;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_sg(const SGArgs<T>& a, cudaStream_t st) {
   if (a.out1 <= a.out0 || a.nslabs <= 0) return cudaSuccess;
   if (a.out0 < a.in0 || a.out1 > a.in1) return cudaErrorInvalidValue;
+  if (a.n1 >= 15 && a.M + 1 <= 17) {
+    // quad kernel: the 16-node tile when it keeps more CTAs resident than the 32-node one
+    const size_t q32 = sg4_smem<T, 32>(a), q16 = sg4_smem<T, 16>(a);
+    auto resident = [](size_t b) { return int((228 * 1024) / (b + 1024)); };
+    if (q32 <= kMaxSmem && a.n1 >= 24 && resident(q32) >= std::min(2, resident(q16)))
+      return launch_sg4_tx<T, 32>(a, q32, st);
+    if (q16 <= kMaxSmem) return launch_sg4_tx<T, 16>(a, q16, st);
+  }
   size_t s32 = sg_smem<T, 32>(a), s16 = sg_smem<T, 16>(a), s8 = sg_smem<T, 8>(a);
   if (s32 <= kMaxSmem && a.n1 >= 24) return launch_sg_tx<T, 32>(a, s32, st);
   if (s16 <= kMaxSmem && a.n1 >= 12) return launch_sg_tx<T, 16>(a, s16, st);
