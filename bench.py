@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip fp64/e2e/profile/matvec legs")
     ap.add_argument("--sequential", action="store_true", help="solve the batch one problem at a time")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the built-in SG kernel choice")
     ap.add_argument("--serve", action="store_true",
                     help="serving stream: the first --requests seeded requests through the server")
     ap.add_argument("--requests", type=int, default=40)
@@ -63,6 +64,7 @@ def load_peaks():
 
 # float64 ALU peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2070 MHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+SG_KERNEL_NAMES = {0: "one-phase", 1: "quad-32", 2: "quad-16", 3: "two-phase", -1: "none"}
 # ncu: vcycle_t_kernel<float, 127>, 56 columns: 3,719,936 B read + 256 B written
 VCYCLE_DRAM_BYTES_PER_COLUMN = (3719936 + 256) / 56
 # float32 non-tensor peak: 152 SMs x 128 FMA/clk x 2 flop x 2070 MHz
@@ -214,6 +216,8 @@ def run_ours(args):
     sps = [SGProblem.from_problem(pr, precision=args.precision).upload() for pr in problems]
     for sp in sps:
         sp.workspace()
+    # SG kernel per launch shape (process-wide; the three problems share their shapes); untimed
+    sg_kernels = None if args.no_autotune else sps[0].autotune()
     xs = [torch.empty(sp.kkt_size, dtype=torch.float64, device="cuda") for sp in sps]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -283,7 +287,10 @@ def run_ours(args):
                    "precision": ("float32 operator/preconditioner/inner MINRES, float64 refinement"
                                  if args.precision == "mixed" else "float64"),
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}",
-                   "batching": "sequential" if args.sequential else "3 concurrent solves (sgoc_solve_batch, 3 streams)"},
+                   "batching": "sequential" if args.sequential else "3 concurrent solves (sgoc_solve_batch, 3 streams)",
+                   "sg_kernels": "built-in choice" if sg_kernels is None else
+                   dict(zip(["kkt", "operator"] + [f"hgs_level{d}" for d in range(len(sg_kernels) - 2)],
+                            [SG_KERNEL_NAMES[v] for v in sg_kernels]))},
         "latency_ms": {"p50": float(sorted(solve_ms)[len(solve_ms) // 2]),
                        "p99": float(sorted(solve_ms)[min(len(solve_ms) - 1, math.ceil(0.99 * len(solve_ms)) - 1)])},
         "iterations": {"per_solve": iters[:3], "outer": outer[:3], "max_rel_residual": max(resid)},
@@ -385,22 +392,30 @@ def run_ours(args):
             for dt, name in ((torch.float32, "f32"), (torch.float64, "f64")):
                 X = torch.randn(sp.n * sp.P, dtype=dt, device="cuda")
                 Y = torch.empty_like(X)
-                sp.apply_operator(X, out=Y)
-                ts = []
-                for _ in range(5):
-                    flush.fill_(1.0)
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    sp.apply_operator(X, out=Y)
-                    e1.record(stream)
-                    torch.cuda.synchronize()
-                    ts.append(e0.elapsed_time(e1))
                 w = X.element_size()
                 byts = w * (2 * sp.n * sp.P) + w * (pr.M + 1) * pr.nx * pr.nx
-                t = statistics.median(ts) / 1e3
+                per = {}
+                for v in range(4):
+                    try:
+                        sp.apply_operator_variant(X, v, out=Y)
+                    except abi.SgocError:
+                        continue
+                    ts = []
+                    for _ in range(5):
+                        flush.fill_(1.0)
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        sp.apply_operator_variant(X, v, out=Y)
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        ts.append(e0.elapsed_time(e1))
+                    per[SG_KERNEL_NAMES[v]] = statistics.median(ts) / 1e3
+                best = min(per, key=per.get)
+                t = per[best]
                 mv[f"{tag}_{name}"] = {"GB/s": byts / t / 1e9, "frac_hbm": byts / t / 1e9 / hbm_peak,
-                                       "us": t * 1e6}
+                                       "us": t * 1e6, "kernel": best,
+                                       "us_per_kernel": {k: round(v * 1e6, 1) for k, v in per.items()}}
             del sp
         line["sg_matvec"] = mv
 
@@ -413,6 +428,8 @@ def run_ours(args):
             rec = {"kkt_unknowns": pr.kkt_size}
             for prec in ("mixed", "fp64"):
                 sp = SGProblem.from_problem(pr, precision=prec).upload()
+                if not args.no_autotune:
+                    sp.autotune()
                 x, _ = sp.solve()
                 flush.fill_(1.0)
                 e0 = torch.cuda.Event(enable_timing=True)

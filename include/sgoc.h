@@ -187,6 +187,26 @@ sgoc_status sgoc_server_poll(sgoc_server* sv, uint64_t* ids, sgoc_result* res, i
 sgoc_status sgoc_server_stats(const sgoc_server* sv, int64_t* admitted, int64_t* completed,
                               int64_t* rejected, size_t* pool_high_water);
 
+/* ---- tuning ----
+ *
+ * Kernel choice for the SG operator products of a solve.  The library has
+ * several kernels for Y = sum_k K_k X G_k (Sec. 2, Eq. (gPC-A) in Kronecker
+ * form) that form the same products and sums in the same order, so they give
+ * bitwise identical results and differ only in speed.  sgoc_autotune times each
+ * applicable kernel on every SG launch shape a solve of `pb` uses (the KKT
+ * product, the operator alone, the right-hand side of each hGS level visit of
+ * Alg. 1; in mixed precision also the float64 true-residual product) on the
+ * caller's workspace (d_ws, ws_bytes as for sgoc_solve; its contents are
+ * overwritten) and stream, and records the fastest in a process-wide table keyed
+ * by launch shape, which every later launch of that shape (any problem with the
+ * same grid, chaos levels, truncation, slabs and precision) uses.  Without
+ * tuning a built-in rule chooses.  chosen (nullable, nchosen entries) receives
+ * the kernel index per shape in the order above (0 one-phase, 1 and 2 four
+ * nodes per thread on 32- and 16-node tiles, 3 two-phase float32).  Synchronizes
+ * the stream.  The paper has no counterpart: it concerns this GPU code only. */
+sgoc_status sgoc_autotune(sgoc_problem* pb, void* d_ws, size_t ws_bytes, int32_t* chosen,
+                          int32_t nchosen, void* stream);
+
 /* ---- building blocks (used by tests and benchmarks) ---- */
 
 /* Y = sum_{k=0}^{M} K_k X G_k (Sec. 2, Eq. (Zv) with A_l in place of A~_l),
@@ -194,6 +214,11 @@ sgoc_status sgoc_server_stats(const sgoc_server* sv, int64_t* admitted, int64_t*
  * 1: float32.  X and Y must not overlap. */
 sgoc_status sgoc_apply_operator(sgoc_problem* pb, int32_t precision, const void* d_X,
                                 void* d_Y, int32_t nslabs, void* stream);
+/* The same product with one given kernel variant (0..3 as listed for
+ * sgoc_autotune); SGOC_ERR_UNSUPPORTED when that kernel does not apply to this
+ * shape or precision.  For tests of the variants against each other. */
+sgoc_status sgoc_apply_operator_variant(sgoc_problem* pb, int32_t precision, int32_t variant,
+                                        const void* d_X, void* d_Y, int32_t nslabs, void* stream);
 
 /* w = K v, the KKT matrix of Eq. (stoch-system) or Eq. (KKT:stoch-time-dependent).
  * precision 0: float64 vectors; 1: float32 vectors.  No workspace. */

@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsgoc.so")
 
 SGOC_OK = 0
+SGOC_ERR_UNSUPPORTED = 2
 STATUS_NAMES = {
     0: "SGOC_OK", 1: "SGOC_ERR_INVALID_ARG", 2: "SGOC_ERR_UNSUPPORTED", 3: "SGOC_ERR_WORKSPACE_TOO_SMALL",
     4: "SGOC_ERR_CUDA", 5: "SGOC_ERR_NO_CONVERGENCE", 6: "SGOC_ERR_BREAKDOWN", 7: "SGOC_ERR_NOT_SPD",
@@ -69,7 +70,9 @@ SIGNATURES = {
     "sgoc_server_step": (ctypes.c_int, [_P, _PI32, _PI32]),
     "sgoc_server_poll": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Result), _I32, _PI32]),
     "sgoc_server_stats": (ctypes.c_int, [_P, _PI64, _PI64, _PI64, _PSZ]),
+    "sgoc_autotune": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _I32, _P]),
     "sgoc_apply_operator": (ctypes.c_int, [_P, _I32, _P, _P, _I32, _P]),
+    "sgoc_apply_operator_variant": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _I32, _P]),
     "sgoc_apply_kkt": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
     "sgoc_apply_precond": (ctypes.c_int, [_P, _I32, _P, _P, _P, _SZ, _P]),
     "sgoc_apply_hgs": (ctypes.c_int, [_P, _I32, _P, _P, _I32, _P, _SZ, _P]),

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <atomic>
 #include <cstdint>
 #include <mutex>
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(kSGThreads, 2) sg_kernel(SGArgs<T> a, int rows
         off = fma(en.c, dot4<T>(Ks[en.ks + lx], Ts[en.ts + lx]), off);
       }
       if (ix >= n1) continue;
-      T out = a.c0 * diag + a.c1 * off;
+      T out = fma(a.c0, diag, a.c1 * off);
       if (use_m) out = fma(a.cm, Ms[size_t(bl) * TX + lx], out);
       const int64_t node = int64_t(iy) * n1 + ix;
       if (a.R) out = fma(a.cr, a.R[int64_t(t) * a.rs + int64_t(beta - a.rcol0) * a.n + node], out);
@@ -568,7 +569,7 @@ __global__ void __launch_bounds__(kSG4Threads, 2) sg4_kernel(SGArgs<T> a, int ro
       for (int u = 0; u < 4; ++u) {
         const int ix = ix0 + 4 * qd + u;
         if (ix >= n1) break;
-        T out = a.c0 * diag[u] + a.c1 * off[u];
+        T out = fma(a.c0, diag[u], a.c1 * off[u]);
         if (use_m) out = fma(a.cm, mrow[u], out);
         const int64_t node = rowbase + ix;
         if (rcol) out = fma(a.cr, rcol[node], out);
@@ -608,23 +609,309 @@ static cudaError_t launch_sg4_tx(const SGArgs<T>& a, size_t smem, cudaStream_t s
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// SG apply, two-phase form (float32): per row of a 32-node tile,
+//   phase 1: a warp takes one input column alpha (lane = node), forms the element
+//            terms T_e(alpha) from the staged rows and, with kappa_k of its node in
+//            registers, writes U_k(alpha) = sum_e kappa_k(e) T_e(alpha) for exactly
+//            the k the shape's outputs use (slot table, bit k of the column's mask);
+//   phase 2: a warp takes one output column beta and gathers
+//            out = c0 U_0(beta) + c1 sum_entries c U_k(alpha) from the slot list.
+// Every shared-memory access is lane-consecutive (no bank conflicts) and moves
+// 4 bytes per node and product, against 32 for the quad form.  Products and
+// sums are formed in the same order as in sg_kernel.
+// ---------------------------------------------------------------------------
+constexpr int kSGUThreads = 512;
+
+__host__ __device__ __forceinline__ size_t align8(size_t b) { return (b + 7) & ~size_t(7); }
+
+static size_t sgu_smem(const SGArgs<float>& a) {
+  const size_t nin = a.in1 - a.in0, nout = a.out1 - a.out0;
+  size_t b = 4 * (3 * nin * 34 + size_t(a.u_nslots) * 32 + (a.cm != 0.f ? nout * 32 : 0) + size_t(a.M + 1) * 4 * 32);
+  b = align8(b) + 8 * nin + 4 * nout + 4 * (nout + 1);
+  return align8(b) + 8 * size_t(a.u_nent);
+}
+
+template <int KM>
+__global__ void __launch_bounds__(kSGUThreads, 1) sgu_kernel(SGArgs<float> a, int rows_per_cta) {
+  constexpr int TX = 32, W = TX + 2, NW = kSGUThreads / 32;
+  extern __shared__ __align__(16) unsigned char sgu_smem_raw[];
+  const int nin = a.in1 - a.in0;
+  const int nout = a.out1 - a.out0;
+  const bool use_m = a.cm != 0.f;
+  float* Xr = reinterpret_cast<float*>(sgu_smem_raw);                 // ring [3][nin][W]
+  float* U = Xr + size_t(3) * nin * W;                                 // [nslots][TX]
+  float* Ms = U + size_t(a.u_nslots) * TX;                             // [nout][TX] when cm != 0
+  float* Ks = Ms + (use_m ? size_t(nout) * TX : 0);                    // [M+1][4][TX]
+  unsigned char* tail = reinterpret_cast<unsigned char*>(Ks + size_t(a.M + 1) * 4 * TX);
+  int2* MB = reinterpret_cast<int2*>(sgu_smem_raw + align8(size_t(tail - sgu_smem_raw)));   // [nin]
+  int* Dg = reinterpret_cast<int*>(MB + nin);                          // [nout]
+  int* Ep = Dg + nout;                                                 // [nout + 1]
+  int2* Et = reinterpret_cast<int2*>(sgu_smem_raw + align8(size_t(reinterpret_cast<unsigned char*>(Ep + nout + 1) -
+                                                                  sgu_smem_raw)));                  // [nent]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ix0 = blockIdx.x * TX;
+  const int r0 = blockIdx.y * rows_per_cta;
+  const int r1 = min(a.n1, r0 + rows_per_cta);
+  const int t = blockIdx.z;
+  const int n1 = a.n1;
+  const float* X = a.X + int64_t(t) * a.xs;
+  const size_t ring_stride = size_t(nin) * W;
+
+  // slot table of the shape (constant data)
+  const int2* mbg = reinterpret_cast<const int2*>(a.u_mb);
+  for (int q = tid; q < nin; q += kSGUThreads) MB[q] = mbg[q];
+  for (int q = tid; q < nout; q += kSGUThreads) Dg[q] = a.u_diag[q];
+  for (int q = tid; q <= nout; q += kSGUThreads) Ep[q] = a.u_eptr[q];
+  for (int q = tid; q < a.u_nent; q += kSGUThreads) Et[q] = a.u_e32[q];
+
+  pdl_wait();                                        // X (and Y, R) are written by earlier kernels
+  if (r0 >= r1) { pdl_trigger(); return; }
+
+  // ring row gy: one warp per input column, lanes along x (34 values: lanes 0..31, then 0..1)
+  auto issue_row = [&](int gy) {
+    float* dst = Xr + size_t((gy + 1) % 3) * ring_stride;
+    const bool rok = gy >= 0 && gy < n1;
+    const int gx0 = ix0 + lane - 1, gx1 = ix0 + lane + 31;
+    const bool ok0 = rok && gx0 >= 0 && gx0 < n1, ok1 = rok && lane < 2 && gx1 < n1;
+    const float* src = X + int64_t(a.in0 + warp) * a.n + int64_t(rok ? gy : 0) * n1;
+    float* d = dst + size_t(warp) * W + lane;
+    for (int c = warp; c < nin; c += NW) {
+      cp_async_elem(d, ok0 ? src + gx0 : src, ok0);
+      if (lane < 2) cp_async_elem(d + 32, ok1 ? src + gx1 : src, ok1);
+      src += int64_t(NW) * a.n;
+      d += size_t(NW) * W;
+    }
+  };
+  issue_row(r0 - 1);
+  issue_row(r0);
+  issue_row(r0 + 1);
+  cp_async_commit();
+
+  const int nxk = a.nx;
+  const int nkap = (a.M + 1) * 4 * TX;
+  for (int iy = r0; iy < r1; ++iy) {
+    if (iy == r1 - 1) pdl_trigger();
+    cp_async_wait<0>();
+    __syncthreads();                                   // rows iy-1..iy+1 landed; previous gathers done
+    // kappa_k/6 of the four elements of every node of the row: SW, SE, NE, NW planes
+    for (int q = tid; q < nkap; q += kSGUThreads) {
+      const int kk = q >> 7, r = q & 127;              // 4 * TX = 128 values per k
+      const int e = r >> 5, lx = r & 31;
+      const int ix = min(ix0 + lx, n1 - 1);
+      const int ex = ix + ((e == 1 || e == 2) ? 1 : 0), ey = iy + (e >= 2 ? 1 : 0);
+      Ks[q] = a.kap[(int64_t(kk) * nxk + ey) * nxk + ex];
+    }
+    __syncthreads();
+    float kr[KM][4];
+#pragma unroll
+    for (int k = 0; k < KM; ++k)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) kr[k][e] = k <= a.M ? Ks[(k * 4 + e) * TX + lane] : 0.f;
+    const float* rS = Xr + size_t(iy % 3) * ring_stride;         // row iy-1
+    const float* rC = Xr + size_t((iy + 1) % 3) * ring_stride;   // row iy
+    const float* rN = Xr + size_t((iy + 2) % 3) * ring_stride;   // row iy+1
+    for (int c = warp; c < nin; c += NW) {
+      const size_t o = size_t(c) * W + lane;
+      const float SW = rS[o], S = rS[o + 1], SE = rS[o + 2];
+      const float Wv = rC[o], C = rC[o + 1], E = rC[o + 2];
+      const float NW_ = rN[o], N = rN[o + 1], NE = rN[o + 2];
+      const float c4 = 4.f * C;
+      const float aS = c4 - S, aN = c4 - N;
+      const float T0 = fmaf(-2.f, SW, aS - Wv);
+      const float T1 = fmaf(-2.f, SE, aS - E);
+      const float T2 = fmaf(-2.f, NE, aN - E);
+      const float T3 = fmaf(-2.f, NW_, aN - Wv);
+      const int2 mb = MB[c];
+      const unsigned mask = unsigned(mb.x);
+      float* up = U + size_t(mb.y) * TX + lane;
+#pragma unroll
+      for (int k = 0; k < KM; ++k) {
+        if (mask & (1u << k)) {
+          float d = kr[k][0] * T0;
+          d = fmaf(kr[k][1], T1, d);
+          d = fmaf(kr[k][2], T2, d);
+          d = fmaf(kr[k][3], T3, d);
+          *up = d;
+          up += TX;
+        }
+      }
+      const int col = a.in0 + c;
+      if (use_m && col >= a.out0 && col < a.out1) {
+        const float edges = (N + S) + (E + Wv);
+        const float corners = (NE + NW_) + (SE + SW);
+        Ms[size_t(col - a.out0) * TX + lane] = a.mass * fmaf(16.f, C, fmaf(4.f, edges, corners));
+      }
+    }
+    __syncthreads();                                   // products ready; row iy-1 no longer needed
+    if (iy + 1 < r1) { issue_row(iy + 2); cp_async_commit(); }
+    const int ix = ix0 + lane;
+    for (int bl = warp; bl < nout; bl += NW) {
+      const int beta = a.out0 + bl;
+      const float* ul = U + lane;
+      const float diag = ul[Dg[bl] * TX];
+      float off = 0.f;
+      const int e1 = Ep[bl + 1];
+      for (int e = Ep[bl]; e < e1; ++e) {
+        const int2 en = Et[e];                         // (slot * 32, bits of c)
+        off = fmaf(__int_as_float(en.y), ul[en.x], off);
+      }
+      if (ix >= n1) continue;
+      float out = fmaf(a.c0, diag, a.c1 * off);
+      if (use_m) out = fmaf(a.cm, Ms[size_t(bl) * TX + lane], out);
+      const int64_t node = int64_t(iy) * n1 + ix;
+      if (a.R) out = fmaf(a.cr, a.R[int64_t(t) * a.rs + int64_t(beta - a.rcol0) * a.n + node], out);
+      float* yp = a.Y + int64_t(t) * a.ys + int64_t(beta - a.ycol0) * a.n + node;
+      if (a.cy != 0.f) out = fmaf(a.cy, *yp, out);
+      *yp = out;
+    }
+  }
+  cp_async_wait<0>();
+}
+
+template <int KM>
+static cudaError_t launch_sgu_km(const SGArgs<float>& a, size_t smem, cudaStream_t st) {
+  cudaError_t e = allow_max_smem(sgu_kernel<KM>);
+  if (e != cudaSuccess) return e;
+  constexpr int TX = 32;
+  const int xt = (a.n1 + TX - 1) / TX;
+  int per_sm = 1;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sgu_kernel<KM>, kSGUThreads, smem);
+  if (e != cudaSuccess) return e;
+  per_sm = std::max(1, per_sm);
+  const int64_t want = int64_t(152) * per_sm;
+  const int64_t tiles = int64_t(xt) * a.nslabs;
+  int rows = int(std::max<int64_t>(1, (tiles * a.n1 + want - 1) / want));
+  rows = std::min(rows, a.n1);
+  dim3 grid(xt, (a.n1 + rows - 1) / rows, a.nslabs);
+  const double w = 4.0, cells = double(a.n) * a.nslabs;
+  const int nout = a.out1 - a.out0, nin = a.in1 - a.in0;
+  const double bytes = w * cells * (nin + nout * (1.0 + (a.R ? 1 : 0) + (a.cy != 0.f ? 1 : 0))) +
+                       w * (a.M + 1.0) * a.nx * a.nx;
+  const double flops = cells * (15.0 * nin + 9.0 * nout + 9.0 * (a.c1 != 0.f ? a.deg_sum : 0));
+  ProfScope ps(KK_SG, st, bytes, flops);
+  {
+    const cudaError_t le_ = launch_pdl(sgu_kernel<KM>, dim3(grid), dim3(kSGUThreads), size_t(smem), st, a, rows);
+    if (le_ != cudaSuccess) return le_;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+// the two-phase kernel when the shape has a slot table that fits in shared memory
+static bool try_launch_sgu(const SGArgs<float>& a, cudaStream_t st, cudaError_t* err) {
+  if (!a.u_mb || a.n1 < 24 || a.M + 1 > 17) return false;
+  const size_t smem = sgu_smem(a);
+  if (smem + 4096 > kMaxSmem) return false;
+  if (a.M + 1 <= 5) *err = launch_sgu_km<5>(a, smem, st);
+  else if (a.M + 1 <= 9) *err = launch_sgu_km<9>(a, smem, st);
+  else *err = launch_sgu_km<17>(a, smem, st);
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// SG kernel variants and the tuning cache.  All variants form the same products
+// and sums in the same order, so the choice changes timing only.
+//   0: one-phase kernel (tile by the heuristic), 1: quad kernel, 32-node tile,
+//   2: quad kernel, 16-node tile, 3: two-phase kernel (float32, slot table).
+// The cache maps a launch shape (grid, column ranges, KL terms, truncation,
+// slabs, element size, epilogue terms) to the variant measured fastest.
+// ---------------------------------------------------------------------------
+namespace {
+struct SGKey {
+  int n1, in0, in1, out0, out1, M, kmax, nslabs, esize, flags;
+  bool operator<(const SGKey& o) const {
+    const int a[10] = {n1, in0, in1, out0, out1, M, kmax, nslabs, esize, flags};
+    const int b[10] = {o.n1, o.in0, o.in1, o.out0, o.out1, o.M, o.kmax, o.nslabs, o.esize, o.flags};
+    for (int i = 0; i < 10; ++i)
+      if (a[i] != b[i]) return a[i] < b[i];
+    return false;
+  }
+};
+std::mutex g_tune_mu;
+std::map<SGKey, int> g_tune;
+
+template <typename T>
+SGKey sg_key(const SGArgs<T>& a) {
+  const int flags = (a.cm != T(0) ? 1 : 0) | (a.R ? 2 : 0) | (a.cy != T(0) ? 4 : 0);
+  return SGKey{a.n1, a.in0, a.in1, a.out0, a.out1, a.M, a.kmax, a.nslabs, int(sizeof(T)), flags};
+}
+}  // namespace
+
+template <typename T>
+int sg_tuned_variant(const SGArgs<T>& a) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  const auto it = g_tune.find(sg_key(a));
+  return it == g_tune.end() ? -1 : it->second;
+}
+
+template <typename T>
+void sg_set_variant(const SGArgs<T>& a, int v) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune[sg_key(a)] = v;
+}
+
+void sg_clear_tuning() {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune.clear();
+}
+
+template <typename T>
+bool sg_variant_feasible(const SGArgs<T>& a, int v) {
+  switch (v) {
+    case 0: return true;
+    case 1: return a.n1 >= 24 && a.M + 1 <= 17 && sg4_smem<T, 32>(a) <= kMaxSmem;
+    case 2: return a.n1 >= 15 && a.M + 1 <= 17 && sg4_smem<T, 16>(a) <= kMaxSmem;
+    case 3:
+      if constexpr (std::is_same<T, float>::value)
+        return a.u_mb && a.n1 >= 24 && a.M + 1 <= 17 && sgu_smem(a) + 4096 <= kMaxSmem;
+      return false;
+    default: return false;
+  }
+}
+
+template <typename T>
+static cudaError_t launch_sg_one_phase(const SGArgs<T>& a, cudaStream_t st) {
+  size_t s32 = sg_smem<T, 32>(a), s16 = sg_smem<T, 16>(a), s8 = sg_smem<T, 8>(a);
+  if (s32 <= kMaxSmem && a.n1 >= 24) return launch_sg_tx<T, 32>(a, s32, st);
+  if (s16 <= kMaxSmem && a.n1 >= 12) return launch_sg_tx<T, 16>(a, s16, st);
+  if (s8 <= kMaxSmem) return launch_sg_tx<T, 8>(a, s8, st);
+  return cudaErrorInvalidConfiguration;
+}
+
+template <typename T>
+cudaError_t launch_sg_variant(const SGArgs<T>& a, int v, cudaStream_t st) {
+  if (a.out1 <= a.out0 || a.nslabs <= 0) return cudaSuccess;
+  if (a.out0 < a.in0 || a.out1 > a.in1) return cudaErrorInvalidValue;
+  if (!sg_variant_feasible(a, v)) return cudaErrorInvalidConfiguration;
+  switch (v) {
+    case 1: return launch_sg4_tx<T, 32>(a, sg4_smem<T, 32>(a), st);
+    case 2: return launch_sg4_tx<T, 16>(a, sg4_smem<T, 16>(a), st);
+    case 3:
+      if constexpr (std::is_same<T, float>::value) {
+        cudaError_t e = cudaSuccess;
+        if (try_launch_sgu(a, st, &e)) return e;
+      }
+      return cudaErrorInvalidConfiguration;
+    default: return launch_sg_one_phase<T>(a, st);
+  }
+}
+
 template <typename T>
 cudaError_t launch_sg(const SGArgs<T>& a, cudaStream_t st) {
   if (a.out1 <= a.out0 || a.nslabs <= 0) return cudaSuccess;
   if (a.out0 < a.in0 || a.out1 > a.in1) return cudaErrorInvalidValue;
+  const int tuned = sg_tuned_variant(a);
+  if (tuned >= 0 && sg_variant_feasible(a, tuned)) return launch_sg_variant(a, tuned, st);
+  // untuned: the quad kernel (the 16-node tile when it keeps more CTAs resident), else one-phase
   if (a.n1 >= 15 && a.M + 1 <= 17) {
-    // quad kernel: the 16-node tile when it keeps more CTAs resident than the 32-node one
     const size_t q32 = sg4_smem<T, 32>(a), q16 = sg4_smem<T, 16>(a);
     auto resident = [](size_t b) { return int((228 * 1024) / (b + 1024)); };
     if (q32 <= kMaxSmem && a.n1 >= 24 && resident(q32) >= std::min(2, resident(q16)))
       return launch_sg4_tx<T, 32>(a, q32, st);
     if (q16 <= kMaxSmem) return launch_sg4_tx<T, 16>(a, q16, st);
   }
-  size_t s32 = sg_smem<T, 32>(a), s16 = sg_smem<T, 16>(a), s8 = sg_smem<T, 8>(a);
-  if (s32 <= kMaxSmem && a.n1 >= 24) return launch_sg_tx<T, 32>(a, s32, st);
-  if (s16 <= kMaxSmem && a.n1 >= 12) return launch_sg_tx<T, 16>(a, s16, st);
-  if (s8 <= kMaxSmem) return launch_sg_tx<T, 8>(a, s8, st);
-  return cudaErrorInvalidConfiguration;
+  return launch_sg_one_phase<T>(a, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -2266,6 +2553,10 @@ cudaError_t launch_fill(T* x, int64_t n, T v, cudaStream_t st) {
 // explicit instantiations
 #define SGOC_INST(T)                                                                                               \
   template cudaError_t launch_sg<T>(const SGArgs<T>&, cudaStream_t);                                               \
+  template cudaError_t launch_sg_variant<T>(const SGArgs<T>&, int, cudaStream_t);                              \
+  template int sg_tuned_variant<T>(const SGArgs<T>&);                                                              \
+  template void sg_set_variant<T>(const SGArgs<T>&, int);                                                          \
+  template bool sg_variant_feasible<T>(const SGArgs<T>&, int);                                                     \
   template cudaError_t launch_mass<T>(const MassArgs<T>&, cudaStream_t);                                           \
   template cudaError_t launch_cheb<T>(const ChebArgs<T>&, cudaStream_t);                                           \
   template cudaError_t launch_smooth<T>(const T*, const T*, T*, int64_t, int, Stencil, T, T*, int64_t, int, int,   \

@@ -49,9 +49,24 @@ struct SGArgs {
   const int* nbr_end;           // per output column: end of its entries with k < kmax
   double deg_sum;               // number of (beta, neighbour) pairs used (work accounting only)
   int nnz_out;                  // neighbour-table entries of the output columns (all k)
+  // slot table of this launch shape (two-phase kernel; null: the one-phase kernels)
+  const int* u_mb; const int* u_diag; const int* u_eptr; const int2* u_e32;
+  int u_nslots, u_nent;
 };
 template <typename T>
 cudaError_t launch_sg(const SGArgs<T>& a, cudaStream_t st);
+// SG kernel variants (0 one-phase, 1 quad 32-node tile, 2 quad 16-node tile,
+// 3 two-phase float32) and the process-wide tuning cache keyed by launch shape.
+constexpr int kSGVariants = 4;
+template <typename T>
+cudaError_t launch_sg_variant(const SGArgs<T>& a, int variant, cudaStream_t st);
+template <typename T>
+bool sg_variant_feasible(const SGArgs<T>& a, int variant);
+template <typename T>
+int sg_tuned_variant(const SGArgs<T>& a);          // -1: not tuned
+template <typename T>
+void sg_set_variant(const SGArgs<T>& a, int variant);
+void sg_clear_tuning();
 
 // out[t][c] = cy*out_old + sum_j a_j w_j(c,t) (M V_j[t + shift_j])[c] + ar*R[t][c]
 // for columns c in [0, ncols) of each slab (column c is global column col0 + c).

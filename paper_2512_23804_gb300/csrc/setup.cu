@@ -84,6 +84,57 @@ void sgoc_default_options(sgoc_options* o) {
   o->max_outer = 20;
 }
 
+namespace sgoc {
+// Slot table of one SG launch shape (see UTab): which (alpha, k) products
+// sum_e kappa_k(e) T_e(alpha) the outputs of the shape use, and where each
+// output finds them.  Entries keep the order of the neighbour table.
+static UTab build_utab(const sgoc_problem* pb, int in0, int in1, int out0, int out1, int kmax) {
+  UTab u;
+  u.in0 = in0; u.in1 = in1; u.out0 = out0; u.out1 = out1; u.kmax = kmax;
+  const int nin = in1 - in0, nout = out1 - out0;
+  std::vector<unsigned> mask(nin, 0u);
+  auto end_of = [&](int b) {
+    int e = pb->nbr_ptr[b];
+    while (e < pb->nbr_ptr[b + 1] && pb->nbr_k[e] < kmax) ++e;
+    return e;
+  };
+  for (int b = out0; b < out1; ++b) {
+    mask[b - in0] |= 1u;
+    for (int e = pb->nbr_ptr[b]; e < end_of(b); ++e) mask[pb->nbr_alpha[e] - in0] |= 1u << pb->nbr_k[e];
+  }
+  u.mb.resize(2 * size_t(nin));
+  int base = 0;
+  for (int c = 0; c < nin; ++c) {
+    u.mb[2 * c] = int(mask[c]);
+    u.mb[2 * c + 1] = base;
+    base += __builtin_popcount(mask[c]);
+  }
+  u.nslots = base;
+  auto slot = [&](int a, int k) {
+    const unsigned m = mask[a - in0];
+    return u.mb[2 * (a - in0) + 1] + __builtin_popcount(m & ((1u << k) - 1u));
+  };
+  u.diag.resize(nout);
+  u.eptr.assign(nout + 1, 0);
+  for (int b = out0; b < out1; ++b) {
+    u.diag[b - out0] = slot(b, 0);
+    for (int e = pb->nbr_ptr[b]; e < end_of(b); ++e) {
+      u.eslot.push_back(slot(pb->nbr_alpha[e], pb->nbr_k[e]));
+      u.ec.push_back(pb->nbr_c[e]);
+    }
+    u.eptr[b - out0 + 1] = int(u.eslot.size());
+  }
+  u.nent = int(u.eslot.size());
+  return u;
+}
+
+static size_t utab_bytes(const UTab& u) {
+  const size_t nin = u.in1 - u.in0, nout = u.out1 - u.out0;
+  return align256(nin * 8) + align256(nout * 4) + align256((nout + 1) * 4) + align256(size_t(u.nent) * 8) +
+         align256(size_t(u.nent) * 4) + align256(size_t(u.nent) * 8);
+}
+}  // namespace sgoc
+
 sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* opt,
                                 sgoc_problem** out) {
   if (!d || !out) { set_error("null desc/out"); return SGOC_ERR_INVALID_ARG; }
@@ -215,6 +266,12 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
   pb->dweights.assign(pb->slabs, 1.0);
   if (d->nt > 1) { pb->dweights[0] = 0.5; pb->dweights[d->nt - 1] = 0.5; }
 
+  // slot tables of the SG launch shapes: the full operator and the hGS visit of each level
+  pb->utabs.push_back(build_utab(pb, 0, pb->P, 0, pb->P, M + 1));
+  for (int d = 0; d <= p; ++d)
+    pb->utabs.push_back(build_utab(pb, pb->off[d > 0 ? d - 1 : 0], pb->off[d + 2 <= p + 1 ? d + 2 : p + 1],
+                                   pb->off[d], pb->off[d + 1], pb->r));
+
   // persistent layout
   const size_t nk = size_t(M + 1) * nel;
   const size_t nnz = pb->nbr_alpha.size();
@@ -224,6 +281,7 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
   off = align256(off + pb->P * 4);
   off = align256(off + nnz * 8); off = align256(off + nnz * 4);
   off = align256(off + size_t(pb->slabs) * pb->n * 8); off = align256(off + size_t(pb->n) * 8);
+  for (const UTab& u : pb->utabs) off += utab_bytes(u);
   pb->persistent_bytes = off;
   *out = pb;
   return SGOC_OK;
@@ -275,6 +333,24 @@ sgoc_status sgoc_problem_upload(sgoc_problem* pb, void* d_persistent, size_t byt
   pb->dev.nbr_c32 = reinterpret_cast<float*>(carve(nnz * 4));
   pb->dev.yhat = reinterpret_cast<double*>(carve(size_t(pb->slabs) * pb->n * 8));
   pb->dev.y0 = reinterpret_cast<double*>(carve(size_t(pb->n) * 8));
+  std::vector<std::vector<int2>> e32s;
+  for (UTab& u : pb->utabs) {
+    const size_t nin = u.in1 - u.in0, nout = u.out1 - u.out0;
+    u.d_mb = reinterpret_cast<int*>(carve(nin * 8));
+    u.d_diag = reinterpret_cast<int*>(carve(nout * 4));
+    u.d_eptr = reinterpret_cast<int*>(carve((nout + 1) * 4));
+    u.d_e32 = reinterpret_cast<int2*>(carve(size_t(u.nent) * 8));
+    u.d_eslot = reinterpret_cast<int*>(carve(size_t(u.nent) * 4));
+    u.d_ec64 = reinterpret_cast<double*>(carve(size_t(u.nent) * 8));
+    std::vector<int2> e32(u.nent);
+    for (int i = 0; i < u.nent; ++i) {
+      const float c = float(u.ec[i]);
+      int bits;
+      std::memcpy(&bits, &c, 4);
+      e32[i] = make_int2(u.eslot[i] * 32, bits);            // offset of the slot's row of 32 nodes
+    }
+    e32s.push_back(std::move(e32));
+  }
 
   std::vector<double> k64(nk);
   std::vector<float> k32(nk);
@@ -296,6 +372,18 @@ sgoc_status sgoc_problem_upload(sgoc_problem* pb, void* d_persistent, size_t byt
     SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.y0, pb->y0.data(), size_t(pb->n) * 8, cudaMemcpyHostToDevice, st));
   else
     SGOC_CUDA_TRY(cudaMemsetAsync(pb->dev.y0, 0, size_t(pb->n) * 8, st));
+  for (size_t i = 0; i < pb->utabs.size(); ++i) {
+    const UTab& u = pb->utabs[i];
+    const size_t nin = u.in1 - u.in0, nout = u.out1 - u.out0;
+    SGOC_CUDA_TRY(cudaMemcpyAsync(u.d_mb, u.mb.data(), nin * 8, cudaMemcpyHostToDevice, st));
+    SGOC_CUDA_TRY(cudaMemcpyAsync(u.d_diag, u.diag.data(), nout * 4, cudaMemcpyHostToDevice, st));
+    SGOC_CUDA_TRY(cudaMemcpyAsync(u.d_eptr, u.eptr.data(), (nout + 1) * 4, cudaMemcpyHostToDevice, st));
+    if (u.nent) {
+      SGOC_CUDA_TRY(cudaMemcpyAsync(u.d_e32, e32s[i].data(), size_t(u.nent) * 8, cudaMemcpyHostToDevice, st));
+      SGOC_CUDA_TRY(cudaMemcpyAsync(u.d_eslot, u.eslot.data(), size_t(u.nent) * 4, cudaMemcpyHostToDevice, st));
+      SGOC_CUDA_TRY(cudaMemcpyAsync(u.d_ec64, u.ec.data(), size_t(u.nent) * 8, cudaMemcpyHostToDevice, st));
+    }
+  }
   // the host vectors above go out of scope: finish the copies first
   SGOC_CUDA_TRY(cudaStreamSynchronize(st));
   pdl_fence(st);

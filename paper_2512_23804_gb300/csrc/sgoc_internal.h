@@ -38,6 +38,24 @@ struct Level {
   double diag, edge, corner;
 };
 
+// Slot table of one SG launch shape (output columns [out0, out1), input columns
+// [in0, in1), couplings k < kmax) for the two-phase SG kernel: every input
+// column alpha gets one slot per KL index k its outputs use (bit k of mask,
+// slots numbered from base in increasing k); every output column beta gets the
+// slot of (beta, 0) and a list of (slot, coefficient) pairs in table order.
+struct UTab {
+  int in0 = 0, in1 = 0, out0 = 0, out1 = 0, kmax = 0;
+  int nslots = 0, nent = 0;
+  std::vector<int> mb;        // 2 per input column: mask, base
+  std::vector<int> diag;      // per output column
+  std::vector<int> eptr;      // per output column + 1
+  std::vector<int> eslot;     // per entry
+  std::vector<double> ec;     // per entry
+  int* d_mb = nullptr; int* d_diag = nullptr; int* d_eptr = nullptr;
+  int2* d_e32 = nullptr;      // (32 * slot, float bits of c) per entry
+  int* d_eslot = nullptr; double* d_ec64 = nullptr;
+};
+
 // Device pointers into the caller's persistent buffer.
 struct DevData {
   double* kap64 = nullptr;     // (M+1) x nx x nx, kappa_k(e) / 6
@@ -73,6 +91,8 @@ struct sgoc_problem {
   std::vector<sgoc::Level> levels;
   double mass_h2_36 = 0;             // h^2 / 36 on the finest grid
   std::vector<double> dweights;      // time weights D_t (1 when steady)
+  // SG launch shapes: [0] the full operator (all columns, all k), [1 + d] the hGS visit of level d
+  std::vector<sgoc::UTab> utabs;
   // device
   sgoc::DevData dev;
   bool uploaded = false;

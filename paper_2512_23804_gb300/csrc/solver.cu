@@ -212,36 +212,53 @@ static double deg_sum(const sgoc_problem* pb, int out0, int out1, int kmax) {
 
 // -------------------------------------------------------------------- hGS --
 // V = Z_hGS^{-1} R over `slabs` panels (Alg. 1, correction form, palindromic level order).
+// The slot table of an SG launch shape (two-phase kernel).
+template <typename T>
+static void set_utab(SGArgs<T>& g, const UTab& u) {
+  g.u_mb = u.d_mb; g.u_diag = u.d_diag; g.u_eptr = u.d_eptr; g.u_e32 = u.d_e32;
+  g.u_nslots = u.nslots; g.u_nent = u.nent;
+}
+
+// SG launch of the hGS visit of level d: rhs of the level's columns (correction form)
+template <typename T>
+static SGArgs<T> hgs_args(const sgoc_problem* pb, PrecWS<T>& w, const T* R, T* V, int slabs, int d) {
+  const int P = pb->P, p = pb->p;
+  const int64_t n = pb->n, ps = int64_t(P) * n;
+  const bool time = pb->nt > 0;
+  const T cK = T(time ? pb->tau : 1.0);                 // multiplies K_0 .. K_M
+  const T cM = T(time ? 1.0 + pb->tau * pb->s : pb->s); // multiplies M in the mean operator
+  const int a0 = pb->off[d], a1 = pb->off[d + 1], L = a1 - a0;
+  SGArgs<T> g{};
+  g.X = V; g.xs = ps;
+  g.Y = w.RH; g.ys = int64_t(L) * n; g.ycol0 = a0;
+  g.R = R; g.rs = ps; g.rcol0 = 0;
+  g.n1 = pb->n1; g.n = n; g.nx = pb->nx; g.M = pb->M;
+  g.out0 = a0; g.out1 = a1;
+  g.in0 = pb->off[d > 0 ? d - 1 : 0];
+  g.in1 = pb->off[d + 2 <= p + 1 ? d + 2 : p + 1];
+  g.kmax = pb->r; g.nslabs = slabs;
+  g.c0 = -cK; g.c1 = -cK; g.cm = -cM; g.cr = T(1); g.cy = T(0);
+  g.mass = T(pb->mass_h2_36);
+  g.kap = kap_of<T>(pb);
+  g.nbr_ptr = pb->dev.nbr_ptr; g.nbr_alpha = pb->dev.nbr_alpha; g.nbr_k = pb->dev.nbr_k; g.nbr_c = nbrc_of<T>(pb);
+  g.nbr_end = pb->r == pb->M + 1 ? pb->dev.nbr_end_all : pb->dev.nbr_end_r;
+  g.deg_sum = deg_sum(pb, a0, a1, pb->r);
+  g.nnz_out = pb->nbr_ptr[a1] - pb->nbr_ptr[a0];
+  set_utab(g, pb->utabs[1 + d]);
+  return g;
+}
+
 template <typename T>
 static sgoc_status hgs(const sgoc_problem* pb, PrecWS<T>& w, const T* R, T* V, int slabs, cudaStream_t st) {
   const int P = pb->P, p = pb->p;
   const int64_t n = pb->n, ps = int64_t(P) * n;
   SGOC_LAUNCH(launch_fill<T>(V, slabs * ps, T(0), st));
-  const bool time = pb->nt > 0;
-  const T cK = T(time ? pb->tau : 1.0);                 // multiplies K_0 .. K_M
-  const T cM = T(time ? 1.0 + pb->tau * pb->s : pb->s); // multiplies M in the mean operator
   std::vector<int> order;
   for (int d = 0; d <= p; ++d) order.push_back(d);
   for (int d = p - 1; d >= 0; --d) order.push_back(d);
   for (int d : order) {
-    const int a0 = pb->off[d], a1 = pb->off[d + 1], L = a1 - a0;
-    SGArgs<T> g{};
-    g.X = V; g.xs = ps;
-    g.Y = w.RH; g.ys = int64_t(L) * n; g.ycol0 = a0;
-    g.R = R; g.rs = ps; g.rcol0 = 0;
-    g.n1 = pb->n1; g.n = n; g.nx = pb->nx; g.M = pb->M;
-    g.out0 = a0; g.out1 = a1;
-    g.in0 = pb->off[d > 0 ? d - 1 : 0];
-    g.in1 = pb->off[d + 2 <= p + 1 ? d + 2 : p + 1];
-    g.kmax = pb->r; g.nslabs = slabs;
-    g.c0 = -cK; g.c1 = -cK; g.cm = -cM; g.cr = T(1); g.cy = T(0);
-    g.mass = T(pb->mass_h2_36);
-    g.kap = kap_of<T>(pb);
-    g.nbr_ptr = pb->dev.nbr_ptr; g.nbr_alpha = pb->dev.nbr_alpha; g.nbr_k = pb->dev.nbr_k; g.nbr_c = nbrc_of<T>(pb);
-    g.nbr_end = pb->r == pb->M + 1 ? pb->dev.nbr_end_all : pb->dev.nbr_end_r;
-    g.deg_sum = deg_sum(pb, a0, a1, pb->r);
-    g.nnz_out = pb->nbr_ptr[a1] - pb->nbr_ptr[a0];
-    SGOC_LAUNCH(launch_sg<T>(g, st));
+    const int a0 = pb->off[d], L = pb->off[d + 1] - a0;
+    SGOC_LAUNCH(launch_sg<T>(hgs_args<T>(pb, w, R, V, slabs, d), st));
     SGOC_TRY(vcycle<T>(pb, w, w.RH, nullptr, int64_t(slabs) * L, V, ps, L, a0, st));
   }
   return SGOC_OK;
@@ -278,6 +295,7 @@ static SGArgs<T> sg_full(const sgoc_problem* pb, const T* X, T* Y, T coef) {
   g.nbr_end = pb->dev.nbr_end_all;
   g.deg_sum = double(pb->nbr_alpha.size());
   g.nnz_out = int(pb->nbr_alpha.size());
+  set_utab(g, pb->utabs[0]);
   return g;
 }
 
@@ -1072,6 +1090,55 @@ static sgoc_status prec_hook(sgoc_problem* pb, void* ws, size_t bytes, PrecWS<T>
 
 using namespace sgoc;
 
+// ------------------------------------------------------------------ tuning --
+// Times every feasible SG kernel variant on each SG launch shape of a solve of
+// this problem (the KKT product, the operator alone, each hGS level visit) on the
+// caller's workspace and records the fastest in the tuning cache.
+template <typename T>
+static sgoc_status tune_sg_shape(const SGArgs<T>& a, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int reps,
+                                 double* best_ms, int* best_v) {
+  *best_v = -1;
+  *best_ms = 1e30;
+  for (int v = 0; v < kSGVariants; ++v) {
+    if (!sg_variant_feasible(a, v)) continue;
+    for (int w = 0; w < 2; ++w) SGOC_LAUNCH(launch_sg_variant<T>(a, v, st));
+    SGOC_CUDA_TRY(cudaEventRecord(e0, st));
+    for (int r = 0; r < reps; ++r) SGOC_LAUNCH(launch_sg_variant<T>(a, v, st));
+    SGOC_CUDA_TRY(cudaEventRecord(e1, st));
+    SGOC_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0;
+    SGOC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms / reps < *best_ms) { *best_ms = ms / reps; *best_v = v; }
+  }
+  if (*best_v >= 0) sg_set_variant(a, *best_v);
+  return SGOC_OK;
+}
+
+template <typename T>
+static sgoc_status tune_problem(sgoc_problem* pb, Layout& L, PrecWS<T>& w, T* X, T* Y, cudaStream_t st,
+                                cudaEvent_t e0, cudaEvent_t e1, int32_t* chosen, int nchosen) {
+  const int64_t F = pb->F;
+  SGOC_LAUNCH(launch_fill<T>(X, F, T(0), st));
+  SGOC_LAUNCH(launch_fill<T>(Y, F, T(0), st));
+  SGOC_LAUNCH(launch_fill<T>(w.RH, int64_t(pb->slabs) * level_columns_max(pb) * pb->n, T(0), st));
+  std::vector<SGArgs<T>> shapes;
+  shapes.push_back(sg_full<T>(pb, X, Y, T(-1)));               // KKT product rows (accumulating)
+  SGArgs<T> op = sg_full<T>(pb, X, Y, T(1));
+  op.cy = T(0);
+  shapes.push_back(op);                                       // the operator alone
+  for (int d = 0; d <= pb->p; ++d) shapes.push_back(hgs_args<T>(pb, w, Y, X, pb->slabs, d));
+  int k = 0;
+  for (const SGArgs<T>& a : shapes) {
+    double ms = 0;
+    int v = -1;
+    SGOC_TRY(tune_sg_shape<T>(a, st, e0, e1, 5, &ms, &v));
+    if (chosen && k < nchosen) chosen[k] = v;
+    ++k;
+  }
+  (void)L;
+  return SGOC_OK;
+}
+
 extern "C" {
 
 int64_t sgoc_kernel_launches(void) { return kernel_launches(); }
@@ -1281,6 +1348,64 @@ sgoc_status sgoc_apply_chebyshev(sgoc_problem* pb, int32_t precision, const void
     c.ncols = ncols; c.n1 = pb->n1; c.n = pb->n; c.steps = pb->opt.cheb_steps; c.mass = float(pb->mass_h2_36);
     c.scale_mode = 0;
     return cuda_status(launch_cheb<float>(c, st), "chebyshev");
+  }
+  set_error("precision must be 0 or 1");
+  return SGOC_ERR_INVALID_ARG;
+}
+
+
+sgoc_status sgoc_autotune(sgoc_problem* pb, void* d_ws, size_t ws_bytes, int32_t* chosen, int32_t nchosen,
+                          void* stream) {
+  SGOC_TRY(check_ready(pb));
+  SGOC_TRY(check_ws(d_ws, ws_bytes, workspace_bytes(pb, pb->opt.precision)));
+  if (nchosen < 0 || (nchosen > 0 && !chosen)) { set_error("bad chosen array"); return SGOC_ERR_INVALID_ARG; }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  pdl_fence(st);                                   // the caller's prior work on st
+  Layout L;
+  carve_layout(pb, pb->opt.precision, d_ws, ws_bytes, L);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SGOC_CUDA_TRY(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) { cudaEventDestroy(e0); return cuda_status(ce, "cudaEventCreate"); }
+  sgoc_status s;
+  if (pb->opt.precision == SGOC_FP64) {
+    s = tune_problem<double>(pb, L, L.p64, L.k64.r, L.k64.t, st, e0, e1, chosen, nchosen);
+  } else {
+    // float32 shapes on the mixed workspace, then the float64 true-residual product
+    s = tune_problem<float>(pb, L, L.p32, L.rhs32, L.c32, st, e0, e1, chosen, nchosen);
+    if (s == SGOC_OK) {
+      double ms = 0;
+      int v = -1;
+      s = tune_sg_shape<double>(sg_full<double>(pb, L.k64.r, L.k64.t, -1.0), st, e0, e1, 3, &ms, &v);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  invalidate_graphs(pb);          // captured iterations carry the kernels chosen before
+  return s;
+}
+
+
+sgoc_status sgoc_apply_operator_variant(sgoc_problem* pb, int32_t precision, int32_t variant, const void* d_X,
+                                        void* d_Y, int32_t nslabs, void* stream) {
+  SGOC_TRY(check_ready(pb));
+  if (!d_X || !d_Y || nslabs < 1 || variant < 0 || variant >= kSGVariants) {
+    set_error("bad arguments");
+    return SGOC_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  pdl_fence(st);                                   // the caller's prior work on st
+  if (precision == 0) {
+    SGArgs<double> g = sg_full<double>(pb, static_cast<const double*>(d_X), static_cast<double*>(d_Y), 1.0);
+    g.cy = 0.0; g.nslabs = nslabs;
+    if (!sg_variant_feasible(g, variant)) { set_error("kernel variant not applicable"); return SGOC_ERR_UNSUPPORTED; }
+    return cuda_status(launch_sg_variant<double>(g, variant, st), "sg apply");
+  }
+  if (precision == 1) {
+    SGArgs<float> g = sg_full<float>(pb, static_cast<const float*>(d_X), static_cast<float*>(d_Y), 1.0f);
+    g.cy = 0.f; g.nslabs = nslabs;
+    if (!sg_variant_feasible(g, variant)) { set_error("kernel variant not applicable"); return SGOC_ERR_UNSUPPORTED; }
+    return cuda_status(launch_sg_variant<float>(g, variant, st), "sg apply");
   }
   set_error("precision must be 0 or 1");
   return SGOC_ERR_INVALID_ARG;

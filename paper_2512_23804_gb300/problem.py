@@ -120,6 +120,17 @@ class SGProblem:
             raise abi.SgocError(st, f"sgoc_solve {info}")
         return x, info
 
+    def autotune(self, stream=None):
+        """Time the SG kernel variants on this problem's launch shapes and keep the
+        fastest per shape (process-wide); returns the chosen kernel per shape."""
+        self.upload(stream)
+        ws = self.workspace()
+        n = self.p + 3
+        chosen = (ctypes.c_int32 * n)()
+        abi.check(abi.load().sgoc_autotune(self._handle, _dptr(ws), ws.numel(), ctypes.cast(chosen, ctypes.c_void_p),
+                                           n, _stream(stream)), "sgoc_autotune")
+        return list(chosen)
+
     def _prec_id(self, t):
         import torch
         return 0 if t.dtype == torch.float64 else 1
@@ -130,6 +141,15 @@ class SGProblem:
         Y = out if out is not None else torch.empty_like(X)
         abi.check(abi.load().sgoc_apply_operator(self._handle, self._prec_id(X), _dptr(X), _dptr(Y), nslabs,
                                                  _stream(stream)), "sgoc_apply_operator")
+        return Y
+
+    def apply_operator_variant(self, X, variant, nslabs=1, out=None, stream=None):
+        """The SG operator with a given kernel variant (0..3, see sgoc_autotune)."""
+        import torch
+        self.upload(stream)
+        Y = out if out is not None else torch.empty_like(X)
+        abi.check(abi.load().sgoc_apply_operator_variant(self._handle, self._prec_id(X), variant, _dptr(X), _dptr(Y),
+                                                         nslabs, _stream(stream)), "sgoc_apply_operator_variant")
         return Y
 
     def apply_kkt(self, v, out=None, stream=None):

@@ -1,0 +1,76 @@
+"""SG kernel variants and the autotuner.
+
+Every SG kernel variant forms the same products and sums in the same order, so
+the variants must agree bit for bit and each must match the oracle within the
+operator tolerances (1e-13 float64, 2e-6 float32).  Tuning may change only the
+kernel choice: a solve after sgoc_autotune returns the identical solution.
+"""
+import numpy as np
+import pytest
+
+import sg_inputs as si
+from oracle.operators import SGData
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_ready():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests selected but no CUDA device is visible")
+    from paper_2512_23804_gb300 import build
+    build.build()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+CASES = [dict(seed=61, nx=64, M=3, p=3), dict(seed=62, nx=32, M=2, p=2, nt=3), dict(seed=63, nx=128, M=6, p=3),
+         dict(seed=64, nx=16, M=2, p=2)]
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-13), (torch.float32, 2e-6)])
+def test_sg_variants_agree_bitwise(case, dtype, tol):
+    from paper_2512_23804_gb300 import SGProblem, abi
+    c = dict(case)
+    pr = si.random_small(c.pop("seed"), **c)
+    d = SGData(pr)
+    sp = SGProblem.from_problem(pr)
+    X = si.random_panel(70, d.n, d.P, d.slabs)
+    if dtype == torch.float32:
+        X = X.astype(np.float32).astype(np.float64)
+    ps = d.P * d.n
+    ref = np.concatenate([d.vec(d.sg_apply(d.mat(X[t * ps:(t + 1) * ps]))) for t in range(d.slabs)])
+    Xd = torch.from_numpy(X).to("cuda", dtype)
+    outs = []
+    for v in range(4):
+        try:
+            Y = sp.apply_operator_variant(Xd, v, nslabs=d.slabs)
+        except abi.SgocError as e:
+            assert e.status == abi.SGOC_ERR_UNSUPPORTED
+            continue
+        torch.cuda.synchronize()
+        outs.append((v, Y.double().cpu().numpy()))
+    assert len(outs) >= 1 and outs[0][0] == 0          # the one-phase kernel always applies
+    for v, Y in outs:
+        assert rel(Y, ref) <= tol, v
+    for v, Y in outs[1:]:
+        assert np.array_equal(Y, outs[0][1]), v
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotune_keeps_the_solution(precision):
+    from paper_2512_23804_gb300 import SGProblem
+    pr = si.random_small(65, nx=64, M=3, p=3, beta=1e-4)
+    sp = SGProblem.from_problem(pr, precision=precision)
+    x0, i0 = sp.solve()
+    x0 = x0.clone()
+    chosen = sp.autotune()
+    assert len(chosen) == pr.p + 3
+    assert all(0 <= v <= 3 for v in chosen)
+    x1, i1 = sp.solve()
+    assert i1["iterations"] == i0["iterations"]
+    assert torch.equal(x1, x0)
