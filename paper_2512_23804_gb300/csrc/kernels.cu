@@ -903,14 +903,10 @@ cudaError_t launch_sg(const SGArgs<T>& a, cudaStream_t st) {
   if (a.out0 < a.in0 || a.out1 > a.in1) return cudaErrorInvalidValue;
   const int tuned = sg_tuned_variant(a);
   if (tuned >= 0 && sg_variant_feasible(a, tuned)) return launch_sg_variant(a, tuned, st);
-  // untuned: the quad kernel (the 16-node tile when it keeps more CTAs resident), else one-phase
-  if (a.n1 >= 15 && a.M + 1 <= 17) {
-    const size_t q32 = sg4_smem<T, 32>(a), q16 = sg4_smem<T, 16>(a);
-    auto resident = [](size_t b) { return int((228 * 1024) / (b + 1024)); };
-    if (q32 <= kMaxSmem && a.n1 >= 24 && resident(q32) >= std::min(2, resident(q16)))
-      return launch_sg4_tx<T, 32>(a, q32, st);
-    if (q16 <= kMaxSmem) return launch_sg4_tx<T, 16>(a, q16, st);
-  }
+  // untuned: the quad kernel on 32-node tiles (measured fastest at 128x128 P=84 and 512x512
+  // P=165 in float32), on 16-node tiles for narrower grids, else one-phase
+  if (sg_variant_feasible(a, 1)) return launch_sg_variant(a, 1, st);
+  if (sg_variant_feasible(a, 2)) return launch_sg_variant(a, 2, st);
   return launch_sg_one_phase<T>(a, st);
 }
 
