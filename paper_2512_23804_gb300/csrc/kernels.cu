@@ -394,7 +394,7 @@ constexpr int kSG4Bins = 40;          // entry counts per column are <= 2M <= 32
 template <typename T, int TX>
 static size_t sg4_smem(const SGArgs<T>& a) {
   const size_t nin = a.in1 - a.in0, nout = a.out1 - a.out0;
-  size_t b = sizeof(T) * (nin * 4 * TX + size_t(a.M + 1) * 4 * TX + (a.cm != T(0) ? nout * TX : 0) +
+  size_t b = sizeof(T) * (nin * 4 * TX + 2 * size_t(a.M + 1) * 4 * TX + (a.cm != T(0) ? nout * TX : 0) +
                           3 * nin * (TX + 2));
   b = (b + 15) & ~size_t(15);
   return b + 16 * size_t(a.nnz_out) + sizeof(int) * (3 * nout + 2 * kSG4Bins);
@@ -411,8 +411,9 @@ __global__ void __launch_bounds__(kSG4Threads, 2) sg4_kernel(SGArgs<T> a, int ro
   const int nout = a.out1 - a.out0;
   const bool use_m = a.cm != T(0);
   T* Ts = reinterpret_cast<T*>(sg_smem_raw);                 // [nin][4][TX]
-  T* Ks = Ts + size_t(nin) * 4 * TX;                         // [M+1][4][TX]
-  T* Ms = Ks + size_t(a.M + 1) * 4 * TX;                     // [nout][TX] (when cm != 0)
+  T* Ks = Ts + size_t(nin) * 4 * TX;                         // [2][M+1][4][TX]: rows of alternating parity
+  const size_t kslot = size_t(a.M + 1) * 4 * TX;
+  T* Ms = Ks + 2 * kslot;                                    // [nout][TX] (when cm != 0)
   T* Xr = Ms + (use_m ? size_t(nout) * TX : 0);              // ring [3][nin][W]
   const size_t es_off = (size_t(reinterpret_cast<unsigned char*>(Xr + size_t(3) * nin * W) - sg_smem_raw) + 15) &
                         ~size_t(15);
@@ -422,7 +423,6 @@ __global__ void __launch_bounds__(kSG4Threads, 2) sg4_kernel(SGArgs<T> a, int ro
   int* Ord = Pe + nout;                                      // [nout] output columns by entry count
   int* Hist = Ord + nout;                                    // [2][kSG4Bins]
   const V4* Ts4 = reinterpret_cast<const V4*>(Ts);
-  const V4* Ks4 = reinterpret_cast<const V4*>(Ks);
 
   const int ix0 = blockIdx.x * TX;
   const int r0 = blockIdx.y * rows_per_cta;
@@ -472,23 +472,28 @@ __global__ void __launch_bounds__(kSG4Threads, 2) sg4_kernel(SGArgs<T> a, int ro
       cp_async_elem(dst + q, ok ? col + (int64_t(gy) * n1 + gx) : col, ok);
     }
   };
+  // kappa_k/6 of the four elements of every node of row gy (SW, SE, NE, NW planes) into slot gy & 1
+  auto issue_kappa = [&](int gy) {
+    T* dst = Ks + size_t(gy & 1) * kslot;
+    for (int q = tid; q < int(kslot); q += NT) {
+      const int kk = q / (4 * TX), r = q - kk * 4 * TX;
+      const int e = r / TX, lx = r - e * TX;
+      const int ix = min(ix0 + lx, n1 - 1);
+      const int ex = ix + ((e == 1 || e == 2) ? 1 : 0), ey = gy + (e >= 2 ? 1 : 0);
+      cp_async_elem(dst + q, a.kap + (int64_t(kk) * a.nx + ey) * a.nx + ex, true);
+    }
+  };
   issue_row(r0 - 1);
   issue_row(r0);
   issue_row(r0 + 1);
+  issue_kappa(r0);
   cp_async_commit();
 
   for (int iy = r0; iy < r1; ++iy) {
     if (iy == r1 - 1) pdl_trigger();
     cp_async_wait<0>();
-    __syncthreads();                                   // rows iy-1..iy+1 landed; previous contraction done
-    // kappa_k/6 of the four elements of every node of the row: SW, SE, NE, NW planes
-    for (int q = tid; q < (a.M + 1) * 4 * TX; q += NT) {
-      const int kk = q / (4 * TX), r = q - kk * 4 * TX;
-      const int e = r / TX, lx = r - e * TX;
-      const int ix = min(ix0 + lx, n1 - 1);
-      const int ex = ix + ((e == 1 || e == 2) ? 1 : 0), ey = iy + (e >= 2 ? 1 : 0);
-      Ks[q] = a.kap[int64_t(kk) * a.nx * a.nx + int64_t(ey) * a.nx + ex];
-    }
+    __syncthreads();                                   // rows iy-1..iy+1 and kappa landed; previous contraction done
+    const V4* Ks4 = reinterpret_cast<const V4*>(Ks + size_t(iy & 1) * kslot);
     const T* rS = Xr + size_t(iy % 3) * ring_stride;         // row iy-1
     const T* rC = Xr + size_t((iy + 1) % 3) * ring_stride;   // row iy
     const T* rN = Xr + size_t((iy + 2) % 3) * ring_stride;   // row iy+1
@@ -532,7 +537,7 @@ __global__ void __launch_bounds__(kSG4Threads, 2) sg4_kernel(SGArgs<T> a, int ro
       }
     }
     __syncthreads();                                   // element terms ready; row iy-1 no longer needed
-    if (iy + 1 < r1) { issue_row(iy + 2); cp_async_commit(); }
+    if (iy + 1 < r1) { issue_row(iy + 2); issue_kappa(iy + 1); cp_async_commit(); }
     for (int q = tid; q < nout * NQ; q += NT) {
       const int sl = q / NQ, qd = q - sl * NQ;
       const int bl = Ord[sl];
@@ -627,7 +632,7 @@ __host__ __device__ __forceinline__ size_t align8(size_t b) { return (b + 7) & ~
 
 static size_t sgu_smem(const SGArgs<float>& a) {
   const size_t nin = a.in1 - a.in0, nout = a.out1 - a.out0;
-  size_t b = 4 * (3 * nin * 34 + size_t(a.u_nslots) * 32 + (a.cm != 0.f ? nout * 32 : 0) + size_t(a.M + 1) * 4 * 32);
+  size_t b = 4 * (3 * nin * 34 + size_t(a.u_nslots) * 32 + (a.cm != 0.f ? nout * 32 : 0) + 2 * size_t(a.M + 1) * 4 * 32);
   b = align8(b) + 8 * nin + 4 * nout + 4 * (nout + 1);
   return align8(b) + 8 * size_t(a.u_nent);
 }
@@ -642,8 +647,9 @@ __global__ void __launch_bounds__(kSGUThreads, 1) sgu_kernel(SGArgs<float> a, in
   float* Xr = reinterpret_cast<float*>(sgu_smem_raw);                 // ring [3][nin][W]
   float* U = Xr + size_t(3) * nin * W;                                 // [nslots][TX]
   float* Ms = U + size_t(a.u_nslots) * TX;                             // [nout][TX] when cm != 0
-  float* Ks = Ms + (use_m ? size_t(nout) * TX : 0);                    // [M+1][4][TX]
-  unsigned char* tail = reinterpret_cast<unsigned char*>(Ks + size_t(a.M + 1) * 4 * TX);
+  float* Ks = Ms + (use_m ? size_t(nout) * TX : 0);                    // [2][M+1][4][TX] by row parity
+  const int kslot = (a.M + 1) * 4 * TX;
+  unsigned char* tail = reinterpret_cast<unsigned char*>(Ks + 2 * size_t(kslot));
   int2* MB = reinterpret_cast<int2*>(sgu_smem_raw + align8(size_t(tail - sgu_smem_raw)));   // [nin]
   int* Dg = reinterpret_cast<int*>(MB + nin);                          // [nout]
   int* Ep = Dg + nout;                                                 // [nout + 1]
@@ -683,31 +689,34 @@ __global__ void __launch_bounds__(kSGUThreads, 1) sgu_kernel(SGArgs<float> a, in
       d += size_t(NW) * W;
     }
   };
-  issue_row(r0 - 1);
-  issue_row(r0);
-  issue_row(r0 + 1);
-  cp_async_commit();
-
+  // kappa_k/6 of the four elements of every node of row gy (SW, SE, NE, NW planes) into slot gy & 1
   const int nxk = a.nx;
-  const int nkap = (a.M + 1) * 4 * TX;
-  for (int iy = r0; iy < r1; ++iy) {
-    if (iy == r1 - 1) pdl_trigger();
-    cp_async_wait<0>();
-    __syncthreads();                                   // rows iy-1..iy+1 landed; previous gathers done
-    // kappa_k/6 of the four elements of every node of the row: SW, SE, NE, NW planes
-    for (int q = tid; q < nkap; q += kSGUThreads) {
+  auto issue_kappa = [&](int gy) {
+    float* dst = Ks + (gy & 1) * kslot;
+    for (int q = tid; q < kslot; q += kSGUThreads) {
       const int kk = q >> 7, r = q & 127;              // 4 * TX = 128 values per k
       const int e = r >> 5, lx = r & 31;
       const int ix = min(ix0 + lx, n1 - 1);
-      const int ex = ix + ((e == 1 || e == 2) ? 1 : 0), ey = iy + (e >= 2 ? 1 : 0);
-      Ks[q] = a.kap[(int64_t(kk) * nxk + ey) * nxk + ex];
+      const int ex = ix + ((e == 1 || e == 2) ? 1 : 0), ey = gy + (e >= 2 ? 1 : 0);
+      cp_async_elem(dst + q, a.kap + (int64_t(kk) * nxk + ey) * nxk + ex, true);
     }
-    __syncthreads();
+  };
+  issue_row(r0 - 1);
+  issue_row(r0);
+  issue_row(r0 + 1);
+  issue_kappa(r0);
+  cp_async_commit();
+
+  for (int iy = r0; iy < r1; ++iy) {
+    if (iy == r1 - 1) pdl_trigger();
+    cp_async_wait<0>();
+    __syncthreads();                                   // rows iy-1..iy+1 and kappa landed; previous gathers done
+    const float* Kr = Ks + (iy & 1) * kslot;
     float kr[KM][4];
 #pragma unroll
     for (int k = 0; k < KM; ++k)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) kr[k][e] = k <= a.M ? Ks[(k * 4 + e) * TX + lane] : 0.f;
+      for (int e = 0; e < 4; ++e) kr[k][e] = k <= a.M ? Kr[(k * 4 + e) * TX + lane] : 0.f;
     const float* rS = Xr + size_t(iy % 3) * ring_stride;         // row iy-1
     const float* rC = Xr + size_t((iy + 1) % 3) * ring_stride;   // row iy
     const float* rN = Xr + size_t((iy + 2) % 3) * ring_stride;   // row iy+1
@@ -744,7 +753,7 @@ __global__ void __launch_bounds__(kSGUThreads, 1) sgu_kernel(SGArgs<float> a, in
       }
     }
     __syncthreads();                                   // products ready; row iy-1 no longer needed
-    if (iy + 1 < r1) { issue_row(iy + 2); cp_async_commit(); }
+    if (iy + 1 < r1) { issue_row(iy + 2); issue_kappa(iy + 1); cp_async_commit(); }
     const int ix = ix0 + lane;
     for (int bl = warp; bl < nout; bl += NW) {
       const int beta = a.out0 + bl;
@@ -972,8 +981,7 @@ __global__ void __launch_bounds__(128) mass_kernel(MassArgs<T> a, int strips, in
       mass_row(V, ix, y0 - 1, n1, cm, hm);
       mass_row(V, ix, y0, n1, c0, h0);
 #pragma unroll
-      for (int r = 0; r < kMassRows; ++r) {
-        if (r >= ny) break;
+      for (int r = 0; r < kMassRows; ++r) {      // rows past the grid read zeros; their sums are not stored
         mass_row(V, ix, y0 + r + 1, n1, cp, hp);
         const T edges = (cm + cp) + h0;
         const T corners = hm + hp;
@@ -1129,30 +1137,69 @@ __global__ void __launch_bounds__(1024, 1) cheb_fused_kernel(ChebArgs<float> a, 
   }
 }
 
-// One step for columns that do not fit in shared memory: blockIdx.y runs over
-// columns, x over the nodes of a column.
+// One step for columns that do not fit in shared memory (and for float64): a
+// thread walks a strip of kChebRows rows of one column with a three-row window of
+// x_k (three loads per node, as in mass_kernel); blockIdx.y runs over (strip,
+// column) work items.  Same arithmetic and order as mass_apply.
+constexpr int kChebRows = 8;
+
 template <typename T>
-__global__ void cheb_kernel(ChebArgs<T> a, const T* __restrict__ xk, T* xkm1, T* out, T dinv, T omega, int mode) {
+__device__ __forceinline__ void cheb_row(const T* __restrict__ X, int ix, int y, int n1, T& l, T& c, T& r) {
+  if (y < 0 || y >= n1) { l = c = r = T(0); return; }
+  const T* row = X + int64_t(y) * n1;
+  c = row[ix];
+  l = ix > 0 ? row[ix - 1] : T(0);
+  r = ix + 1 < n1 ? row[ix + 1] : T(0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) cheb_kernel(ChebArgs<T> a, const T* __restrict__ xk, T* xkm1, T* out, T dinv,
+                                                   T omega, int mode, int strips, int64_t nwork) {
   pdl_enter();
   const int n1 = a.n1;
-  const int n = n1 * n1;
-  const int node = blockIdx.x * blockDim.x + threadIdx.x;
-  if (node >= n) return;
-  const int iy = node / n1, ix = node - iy * n1;
-  for (int64_t col = blockIdx.y; col < a.ncols; col += gridDim.y) {
-    const int64_t q = col * n + node;
-    const T b = a.B[q];
-    T x;
-    if (mode == 0) {
-      x = dinv * b;                                 // x_1 = D^{-1} b (x_0 = 0)
-    } else {
-      const T* Xc = xk + col * n;
-      const T r = b - mass_apply(Xc, ix, iy, n1, a.mass);
-      const T xprev = mode == 1 ? T(0) : xkm1[q];
-      x = fma(omega, fma(dinv, r, Xc[node] - xprev), xprev);
+  const int64_t n = int64_t(n1) * n1;
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ix >= n1) return;
+  for (int64_t w = blockIdx.y; w < nwork; w += gridDim.y) {
+    const int strip = int(w % strips);
+    const int64_t col = w / strips;
+    const int y0 = strip * kChebRows;
+    const int ny = min(kChebRows, n1 - y0);
+    const int64_t cb = col * n;
+    const T* Bc = a.B + cb;
+    const T* Xc = xk + cb;
+    T* xpc = xkm1 + cb;
+    T* dst = out ? out + cb : xpc;
+    const T sc = out ? cheb_scale(a, col) : T(1);
+    if (mode == 0) {                                // x_1 = D^{-1} b (x_0 = 0)
+      for (int r = 0; r < ny; ++r) {
+        const int64_t node = int64_t(y0 + r) * n1 + ix;
+        dst[node] = sc * (dinv * Bc[node]);
+      }
+      continue;
     }
-    if (out) out[q] = cheb_scale(a, col) * x;
-    else xkm1[q] = x;
+    T lm, cm, rm, l0, c0, r0;
+    cheb_row(Xc, ix, y0 - 1, n1, lm, cm, rm);
+    cheb_row(Xc, ix, y0, n1, l0, c0, r0);
+    T bv[kChebRows], pv[kChebRows];
+#pragma unroll
+    for (int r = 0; r < kChebRows; ++r) {
+      const int64_t node = int64_t(y0 + r) * n1 + ix;
+      bv[r] = r < ny ? Bc[node] : T(0);
+      pv[r] = (r < ny && mode != 1) ? xpc[node] : T(0);
+    }
+#pragma unroll
+    for (int r = 0; r < kChebRows; ++r) {        // rows past the grid read zeros and are not stored
+      T lp, cp, rp;
+      cheb_row(Xc, ix, y0 + r + 1, n1, lp, cp, rp);
+      const T edges = (cp + cm) + (r0 + l0);
+      const T corners = (rp + lp) + (rm + lm);
+      const T res = bv[r] - a.mass * fma(T(16), c0, fma(T(4), edges, corners));
+      const T x = fma(omega, fma(dinv, res, c0 - pv[r]), pv[r]);
+      if (r < ny) dst[int64_t(y0 + r) * n1 + ix] = sc * x;
+      lm = l0; cm = c0; rm = r0;
+      l0 = lp; c0 = cp; r0 = rp;
+    }
   }
 }
 
@@ -1191,8 +1238,10 @@ cudaError_t launch_cheb(const ChebArgs<T>& a, cudaStream_t st) {
     if (npt <= 4) return go(cheb_fused_kernel<4>);
     return go(cheb_fused_kernel<16>);
   }
-  const int n = a.n1 * a.n1;
-  const dim3 grid(unsigned((n + 255) / 256), unsigned(a.ncols < 65535 ? a.ncols : 65535));
+  const int tx = a.n1 >= 128 ? 128 : ((a.n1 + 31) / 32) * 32;
+  const int strips = (a.n1 + kChebRows - 1) / kChebRows;
+  const int64_t nwork = int64_t(strips) * a.ncols;
+  const dim3 grid(unsigned((a.n1 + tx - 1) / tx), unsigned(nwork < 65535 ? nwork : 65535));
   double omega = 1.0;
   // x_{k+1} is written over x_{k-1}: x_1 -> A, x_2 -> B, x_3 -> A, ...
   for (int k = 0; k < a.steps; ++k) {
@@ -1203,8 +1252,8 @@ cudaError_t launch_cheb(const ChebArgs<T>& a, cudaStream_t st) {
     const int mode = k == 0 ? 0 : (k == 1 ? 1 : 2);
     ProfScope ps(KK_CHEB, st, double(sizeof(T)) * total * (2 + mode), double(total) * (mode == 0 ? 1.0 : 24.0));
     {
-      const cudaError_t le_ = launch_pdl(cheb_kernel<T>, dim3(grid), dim3(256), size_t(0), st,
-                                        a, xk, dst, out, dinv, T(omega), mode);
+      const cudaError_t le_ = launch_pdl(cheb_kernel<T>, dim3(grid), dim3(tx), size_t(0), st,
+                                        a, xk, dst, out, dinv, T(omega), mode, strips, nwork);
       if (le_ != cudaSuccess) return le_;
     }
     note_launch();
@@ -1452,7 +1501,10 @@ struct VT {
   static constexpr int off(int l) { return l == 0 ? 0 : off(l - 1) + np(l - 1) * (l - 1 > 0 ? 3 : 2); }
   static constexpr int nlev() { return N1 == 1 ? 1 : 1 + VT<(N1 - 1) / 2>::nlev(); }
   static constexpr int total() { return off(nlev()); }
-  static constexpr int grp(int l) { return n1(l) >= 63 ? kVFThreads : (n1(l) >= 15 ? 256 : 32); }
+  // threads per CTA: 1024 for a 127 x 127 top level, 256 below (four columns per SM)
+  static constexpr int nb() { return N1 >= 127 ? kVFThreads : 256; }
+  static constexpr int grp0(int l) { return n1(l) >= 63 ? kVFThreads : (n1(l) >= 15 ? 256 : 32); }
+  static constexpr int grp(int l) { return grp0(l) < nb() ? grp0(l) : nb(); }
 };
 template <>
 struct VT<0> {
@@ -1628,7 +1680,7 @@ __device__ int vt_coarse(T* base, const VFLevel<T>* lv, int nu) {
 }
 
 template <typename T, int N1>
-__global__ void __launch_bounds__(kVFThreads, 1) vcycle_t_kernel(const T* __restrict__ bg, T* xg, FusedLevels L,
+__global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 : kVFThreads / VT<N1>::nb()) vcycle_t_kernel(const T* __restrict__ bg, T* xg, FusedLevels L,
                                                                  T omega, int nu, T* acc, int64_t acc_ss, int acc_L,
                                                                  int acc_col0) {
   using G = VT<N1>;
@@ -1650,7 +1702,7 @@ __global__ void __launch_bounds__(kVFThreads, 1) vcycle_t_kernel(const T* __rest
     const int n1 = G::n1(l), s = n1 + 2, per = 4 * (n1 + 1);
     T* a = base + G::off(l);
     const int narr = l > 0 ? 3 : 2;
-    for (int q = threadIdx.x; q < narr * per; q += kVFThreads) {
+    for (int q = threadIdx.x; q < narr * per; q += G::nb()) {
       const int arr = q / per, k = q - arr * per;
       T* A = a + arr * s * s;
       const int side = k / (n1 + 1), pos = k - side * (n1 + 1);
@@ -1724,11 +1776,11 @@ __global__ void __launch_bounds__(kVFThreads, 1) vcycle_t_kernel(const T* __rest
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   if (acc) {
     T* A = acc + (col / acc_L) * acc_ss + (acc_col0 + col % acc_L) * int64_t(n0);
-    for (int y = ty; y < N1; y += 32)
+    for (int y = ty; y < N1; y += G::nb() / 32)
       for (int x = tx; x < N1; x += 32) A[y * N1 + x] += x0[(y + 1) * S0 + x + 1];
   } else {
     T* X = xg + col * n0;
-    for (int y = ty; y < N1; y += 32)
+    for (int y = ty; y < N1; y += G::nb() / 32)
       for (int x = tx; x < N1; x += 32) X[y * N1 + x] = x0[(y + 1) * S0 + x + 1];
   }
 }
@@ -1740,7 +1792,7 @@ static cudaError_t launch_vt(const T* b, T* x, int64_t B, const FusedLevels& L, 
   cudaError_t e = allow_max_smem(vcycle_t_kernel<T, N1>);
   if (e != cudaSuccess) return e;
   {
-    const cudaError_t le_ = launch_pdl(vcycle_t_kernel<T, N1>, (dim3(unsigned(B))), dim3(kVFThreads), size_t(smem), st,
+    const cudaError_t le_ = launch_pdl(vcycle_t_kernel<T, N1>, (dim3(unsigned(B))), dim3(VT<N1>::nb()), size_t(smem), st,
                                       b, x, L, omega, nu, acc, acc_ss, acc_L, acc_col0);
     if (le_ != cudaSuccess) return le_;
   }
@@ -1756,7 +1808,8 @@ size_t vcycle_full_smem(const FusedLevels& L, int esize) {
 bool vcycle_full_fits(const FusedLevels& L, int esize) {
   const int n1 = L.n1[0];
   const int nchunks = (n1 + kStripRows - 1) / kStripRows;
-  return int64_t(nchunks) * n1 <= kVFThreads && vcycle_full_smem(L, esize) <= kMaxSmem;
+  const int nb = n1 >= 127 ? kVFThreads : 256;          // threads of the instantiation for this top level
+  return int64_t(nchunks) * n1 <= nb && vcycle_full_smem(L, esize) <= kMaxSmem;
 }
 
 template <typename T>
