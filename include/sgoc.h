@@ -202,7 +202,8 @@ sgoc_status sgoc_server_stats(const sgoc_server* sv, int64_t* admitted, int64_t*
  * same grid, chaos levels, truncation, slabs and precision) uses.  Without
  * tuning a built-in rule chooses.  chosen (nullable, nchosen entries) receives
  * the kernel index per shape in the order above (0 one-phase, 1 and 2 four
- * nodes per thread on 32- and 16-node tiles, 3 two-phase float32).  Synchronizes
+ * nodes per thread on 32- and 16-node tiles, 3 two-phase float32, 4 and 5 the
+ * four-node kernels built for four instead of two CTAs per SM).  Synchronizes
  * the stream.  The paper has no counterpart: it concerns this GPU code only. */
 sgoc_status sgoc_autotune(sgoc_problem* pb, void* d_ws, size_t ws_bytes, int32_t* chosen,
                           int32_t nchosen, void* stream);
@@ -214,7 +215,7 @@ sgoc_status sgoc_autotune(sgoc_problem* pb, void* d_ws, size_t ws_bytes, int32_t
  * 1: float32.  X and Y must not overlap. */
 sgoc_status sgoc_apply_operator(sgoc_problem* pb, int32_t precision, const void* d_X,
                                 void* d_Y, int32_t nslabs, void* stream);
-/* The same product with one given kernel variant (0..3 as listed for
+/* The same product with one given kernel variant (0..5 as listed for
  * sgoc_autotune); SGOC_ERR_UNSUPPORTED when that kernel does not apply to this
  * shape or precision.  For tests of the variants against each other. */
 sgoc_status sgoc_apply_operator_variant(sgoc_problem* pb, int32_t precision, int32_t variant,

@@ -400,8 +400,8 @@ static size_t sg4_smem(const SGArgs<T>& a) {
   return b + 16 * size_t(a.nnz_out) + sizeof(int) * (3 * nout + 2 * kSG4Bins);
 }
 
-template <typename T, int TX>
-__global__ void __launch_bounds__(kSG4Threads, 2) sg4_kernel(SGArgs<T> a, int rows_per_cta) {
+template <typename T, int TX, int MINB>
+__global__ void __launch_bounds__(kSG4Threads, MINB) sg4_kernel(SGArgs<T> a, int rows_per_cta) {
   using V4 = typename Vec4<T>::type;
   constexpr int NQ = TX / 4;          // quads per row of the tile
   constexpr int W = TX + 2;
@@ -587,13 +587,13 @@ __global__ void __launch_bounds__(kSG4Threads, 2) sg4_kernel(SGArgs<T> a, int ro
   cp_async_wait<0>();
 }
 
-template <typename T, int TX>
+template <typename T, int TX, int MINB>
 static cudaError_t launch_sg4_tx(const SGArgs<T>& a, size_t smem, cudaStream_t st) {
-  cudaError_t e = allow_max_smem(sg4_kernel<T, TX>);
+  cudaError_t e = allow_max_smem(sg4_kernel<T, TX, MINB>);
   if (e != cudaSuccess) return e;
   const int xt = (a.n1 + TX - 1) / TX;
-  // resident CTAs per SM: shared memory, and registers (launch bounds: two of 256 threads)
-  const int per_sm = std::max(1, std::min(2, int((228 * 1024) / (smem + 1024))));
+  // resident CTAs per SM: shared memory, and registers (launch bounds: MINB of 256 threads)
+  const int per_sm = std::max(1, std::min(MINB, int((228 * 1024) / (smem + 1024))));
   const int64_t want = int64_t(152) * per_sm;
   const int64_t tiles = int64_t(xt) * a.nslabs;
   int rows = int(std::max<int64_t>(1, (tiles * a.n1 + want - 1) / want));
@@ -606,7 +606,7 @@ static cudaError_t launch_sg4_tx(const SGArgs<T>& a, size_t smem, cudaStream_t s
   const double flops = cells * (15.0 * nin + 9.0 * nout + 9.0 * (a.c1 != T(0) ? a.deg_sum : 0));
   ProfScope ps(KK_SG, st, bytes, flops);
   {
-    const cudaError_t le_ = launch_pdl(sg4_kernel<T, TX>, dim3(grid), dim3(kSG4Threads), size_t(smem), st,
+    const cudaError_t le_ = launch_pdl(sg4_kernel<T, TX, MINB>, dim3(grid), dim3(kSG4Threads), size_t(smem), st,
                                       a, rows);
     if (le_ != cudaSuccess) return le_;
   }
@@ -822,7 +822,9 @@ static bool try_launch_sgu(const SGArgs<float>& a, cudaStream_t st, cudaError_t*
 // SG kernel variants and the tuning cache.  All variants form the same products
 // and sums in the same order, so the choice changes timing only.
 //   0: one-phase kernel (tile by the heuristic), 1: quad kernel, 32-node tile,
-//   2: quad kernel, 16-node tile, 3: two-phase kernel (float32, slot table).
+//   2: quad kernel, 16-node tile, 3: two-phase kernel (float32, slot table),
+//   4, 5: quad kernel on 32- and 16-node tiles compiled for four CTAs per SM
+//   (64 registers) instead of two.
 // The cache maps a launch shape (grid, column ranges, KL terms, truncation,
 // slabs, element size, epilogue terms) to the variant measured fastest.
 // ---------------------------------------------------------------------------
@@ -869,8 +871,8 @@ template <typename T>
 bool sg_variant_feasible(const SGArgs<T>& a, int v) {
   switch (v) {
     case 0: return true;
-    case 1: return a.n1 >= 24 && a.M + 1 <= 17 && sg4_smem<T, 32>(a) <= kMaxSmem;
-    case 2: return a.n1 >= 15 && a.M + 1 <= 17 && sg4_smem<T, 16>(a) <= kMaxSmem;
+    case 1: case 4: return a.n1 >= 24 && a.M + 1 <= 17 && sg4_smem<T, 32>(a) <= kMaxSmem;
+    case 2: case 5: return a.n1 >= 15 && a.M + 1 <= 17 && sg4_smem<T, 16>(a) <= kMaxSmem;
     case 3:
       if constexpr (std::is_same<T, float>::value)
         return a.u_mb && a.n1 >= 24 && a.M + 1 <= 17 && sgu_smem(a) + 4096 <= kMaxSmem;
@@ -894,8 +896,10 @@ cudaError_t launch_sg_variant(const SGArgs<T>& a, int v, cudaStream_t st) {
   if (a.out0 < a.in0 || a.out1 > a.in1) return cudaErrorInvalidValue;
   if (!sg_variant_feasible(a, v)) return cudaErrorInvalidConfiguration;
   switch (v) {
-    case 1: return launch_sg4_tx<T, 32>(a, sg4_smem<T, 32>(a), st);
-    case 2: return launch_sg4_tx<T, 16>(a, sg4_smem<T, 16>(a), st);
+    case 1: return launch_sg4_tx<T, 32, 2>(a, sg4_smem<T, 32>(a), st);
+    case 2: return launch_sg4_tx<T, 16, 2>(a, sg4_smem<T, 16>(a), st);
+    case 4: return launch_sg4_tx<T, 32, 4>(a, sg4_smem<T, 32>(a), st);
+    case 5: return launch_sg4_tx<T, 16, 4>(a, sg4_smem<T, 16>(a), st);
     case 3:
       if constexpr (std::is_same<T, float>::value) {
         cudaError_t e = cudaSuccess;
@@ -981,7 +985,8 @@ __global__ void __launch_bounds__(128) mass_kernel(MassArgs<T> a, int strips, in
       mass_row(V, ix, y0 - 1, n1, cm, hm);
       mass_row(V, ix, y0, n1, c0, h0);
 #pragma unroll
-      for (int r = 0; r < kMassRows; ++r) {      // rows past the grid read zeros; their sums are not stored
+      for (int r = 0; r < kMassRows; ++r) {
+        if (r >= ny) break;
         mass_row(V, ix, y0 + r + 1, n1, cp, hp);
         const T edges = (cm + cp) + h0;
         const T corners = hm + hp;
@@ -1181,22 +1186,18 @@ __global__ void __launch_bounds__(128) cheb_kernel(ChebArgs<T> a, const T* __res
     T lm, cm, rm, l0, c0, r0;
     cheb_row(Xc, ix, y0 - 1, n1, lm, cm, rm);
     cheb_row(Xc, ix, y0, n1, l0, c0, r0);
-    T bv[kChebRows], pv[kChebRows];
 #pragma unroll
     for (int r = 0; r < kChebRows; ++r) {
-      const int64_t node = int64_t(y0 + r) * n1 + ix;
-      bv[r] = r < ny ? Bc[node] : T(0);
-      pv[r] = (r < ny && mode != 1) ? xpc[node] : T(0);
-    }
-#pragma unroll
-    for (int r = 0; r < kChebRows; ++r) {        // rows past the grid read zeros and are not stored
+      if (r >= ny) break;
       T lp, cp, rp;
       cheb_row(Xc, ix, y0 + r + 1, n1, lp, cp, rp);
+      const int64_t node = int64_t(y0 + r) * n1 + ix;
       const T edges = (cp + cm) + (r0 + l0);
       const T corners = (rp + lp) + (rm + lm);
-      const T res = bv[r] - a.mass * fma(T(16), c0, fma(T(4), edges, corners));
-      const T x = fma(omega, fma(dinv, res, c0 - pv[r]), pv[r]);
-      if (r < ny) dst[int64_t(y0 + r) * n1 + ix] = sc * x;
+      const T res = Bc[node] - a.mass * fma(T(16), c0, fma(T(4), edges, corners));
+      const T xprev = mode == 1 ? T(0) : xpc[node];
+      const T x = fma(omega, fma(dinv, res, c0 - xprev), xprev);
+      dst[node] = sc * x;
       lm = l0; cm = c0; rm = r0;
       l0 = lp; c0 = cp; r0 = rp;
     }

@@ -144,7 +144,7 @@ class SGProblem:
         return Y
 
     def apply_operator_variant(self, X, variant, nslabs=1, out=None, stream=None):
-        """The SG operator with a given kernel variant (0..3, see sgoc_autotune)."""
+        """The SG operator with a given kernel variant (0..5, see sgoc_autotune)."""
         import torch
         self.upload(stream)
         Y = out if out is not None else torch.empty_like(X)
