@@ -15,10 +15,14 @@ workload on the host cores.
 """
 from __future__ import annotations
 
+import os
+
+# independent streams (three per solve: the solve and its two parallel branches) map onto this many
+# hardware work queues; the runtime default of 8 serialises concurrent solves against each other
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 import argparse
 import json
 import math
-import os
 import statistics
 import subprocess
 import sys

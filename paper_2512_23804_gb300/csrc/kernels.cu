@@ -1680,6 +1680,94 @@ __device__ int vt_coarse(T* base, const VFLevel<T>* lv, int nu) {
   }
 }
 
+// Level-0 sweeps of the V-cycle kernel.  Scalar form: a thread owns a strip of
+// up to kStripRows rows of one grid column (vt_strip).  Float32 form for 63 x 63
+// and 127 x 127: a thread owns two adjacent columns over 8 rows and computes both
+// nodes with packed FP32x2 arithmetic (four loads per row for the pair instead of
+// six; the same operations in the same order as vt_strip, per lane).
+template <typename T, int N1, bool PAIR = (std::is_same<T, float>::value && N1 >= 63)>
+struct VtLevel0 {
+  Strip g;
+  T bv[kStripRows];
+  __device__ __forceinline__ void init(const T* __restrict__ b0) {
+    g = strip_of(N1);
+#pragma unroll
+    for (int j = 0; j < kStripRows; ++j) {
+      const int y = g.y0 + j;
+      bv[j] = (g.x >= 0 && y < g.y1) ? b0[y * N1 + g.x] : T(0);
+    }
+  }
+  template <int MODE>
+  __device__ __forceinline__ void pass(const T* __restrict__ xs, T* __restrict__ xd, T d, T e, T c, T wd) const {
+    vt_strip<T, N1 + 2, MODE>(xs, xd, bv, g, d, e, c, wd);
+  }
+  __device__ __forceinline__ T first_b() const { return bv[0]; }
+};
+
+template <int N1>
+struct VtLevel0<float, N1, true> {
+  static constexpr int NP = (N1 + 1) / 2;      // column pairs (the last one has a single node)
+  static constexpr int R = 8;                  // rows per thread
+  static constexpr int S = N1 + 2;
+  static_assert(VT<N1>::nb() / NP * R >= N1, "pair strips must cover the grid");
+  int x0, y0, ny;
+  bool v1;                                      // the pair's second node exists
+  float2 bv[R];
+  __device__ __forceinline__ void init(const float* __restrict__ b0) {
+    const int t = threadIdx.x;
+    const int px = t % NP, chunk = t / NP;
+    x0 = 2 * px;
+    y0 = chunk * R;
+    ny = max(0, min(R, N1 - y0));
+    v1 = x0 + 1 < N1;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int y = y0 + j;
+      bv[j] = j < ny ? make_float2(b0[y * N1 + x0], v1 ? b0[y * N1 + x0 + 1] : 0.f) : make_float2(0.f, 0.f);
+    }
+  }
+  template <int MODE>
+  __device__ __forceinline__ void pass(const float* __restrict__ xs, float* __restrict__ xd, float d, float e,
+                                       float c, float wd) const {
+    if (ny <= 0) return;
+    float* q = xd + (y0 + 1) * S + x0 + 1;
+    if (MODE == 1) {
+#pragma unroll
+      for (int j = 0; j < R; ++j)
+        if (j < ny) {
+          q[j * S] = wd * bv[j].x;
+          if (v1) q[j * S + 1] = wd * bv[j].y;
+        }
+      return;
+    }
+    const float* p = xs + y0 * S + x0;         // row y0 - 1, column x0 - 1 (zero-bordered)
+    float a0 = p[0], b0 = p[1], c0 = p[2], d0 = v1 ? p[3] : 0.f;
+    float a1 = p[S], b1 = p[S + 1], c1 = p[S + 2], d1 = v1 ? p[S + 3] : 0.f;
+    const float2 dd = make_float2(d, d), ee = make_float2(e, e), cc = make_float2(c, c);
+    const float2 ww = make_float2(wd, wd), m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      if (j < ny) {
+        const float* pr = p + (j + 2) * S;
+        const float a2 = pr[0], b2 = pr[1], c2 = pr[2], d2 = v1 ? pr[3] : 0.f;
+        const float2 C = make_float2(b1, c1);
+        const float2 edges = __fadd2_rn(__fadd2_rn(make_float2(b0, c0), make_float2(b2, c2)),
+                                        __fadd2_rn(make_float2(a1, b1), make_float2(c1, d1)));
+        const float2 corners = __fadd2_rn(__fadd2_rn(make_float2(a0, b0), make_float2(c0, d0)),
+                                          __fadd2_rn(make_float2(a2, b2), make_float2(c2, d2)));
+        const float2 av = __ffma2_rn(dd, C, __ffma2_rn(ee, edges, __fmul2_rn(cc, corners)));
+        const float2 r = __ffma2_rn(m1, av, bv[j]);                 // b - A x, rounded once
+        const float2 o = MODE == 2 ? r : __ffma2_rn(ww, r, C);
+        q[j * S] = o.x;
+        if (v1) q[j * S + 1] = o.y;
+        a0 = a1; b0 = b1; c0 = c1; d0 = d1;
+        a1 = a2; b1 = b2; c1 = c2; d1 = d2;
+      }
+    }
+  }
+  __device__ __forceinline__ float first_b() const { return bv[0].x; }
+};
+
 template <typename T, int N1>
 __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 : kVFThreads / VT<N1>::nb()) vcycle_t_kernel(const T* __restrict__ bg, T* xg, FusedLevels L,
                                                                  T omega, int nu, T* acc, int64_t acc_ss, int acc_L,
@@ -1712,22 +1800,14 @@ __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 :
     }
   }
   pdl_wait();                                        // b and the output are shared with earlier kernels
-  const Strip g = strip_of(N1);
-  T bv[kStripRows];
-  {
-    const T* b0 = bg + col * n0;
-#pragma unroll
-    for (int j = 0; j < kStripRows; ++j) {
-      const int y = g.y0 + j;
-      bv[j] = (g.x >= 0 && y < g.y1) ? b0[y * N1 + g.x] : T(0);
-    }
-  }
+  VtLevel0<T, N1> z;
+  z.init(bg + col * n0);
   __syncthreads();
   T* xa = base;
   T* xb = base + G::np(0);
   int cur = 0;
   if constexpr (N1 == 1) {
-    if (threadIdx.x == 0) xa[4] = bv[0] / lv[0].d;
+    if (threadIdx.x == 0) xa[4] = z.first_b() / lv[0].d;
     __syncthreads();
   } else {
     constexpr int NT0 = G::grp(0);
@@ -1738,15 +1818,15 @@ __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 :
         vt_sync<NT0>();
       }
       for (int sw = 0; sw < nu; ++sw) {
-        if (sw == 0) vt_strip<T, S0, 1>(xb, xa, bv, g, d, e, c, wd);
-        else if (cur == 0) vt_strip<T, S0, 0>(xa, xb, bv, g, d, e, c, wd);
-        else vt_strip<T, S0, 0>(xb, xa, bv, g, d, e, c, wd);
+        if (sw == 0) z.template pass<1>(xb, xa, d, e, c, wd);
+        else if (cur == 0) z.template pass<0>(xa, xb, d, e, c, wd);
+        else z.template pass<0>(xb, xa, d, e, c, wd);
         cur = sw == 0 ? 0 : cur ^ 1;
         vt_sync<NT0>();
       }
       T* xcur = cur == 0 ? xa : xb;
       T* rbuf = cur == 0 ? xb : xa;
-      vt_strip<T, S0, 2>(xcur, rbuf, bv, g, d, e, c, wd);
+      z.template pass<2>(xcur, rbuf, d, e, c, wd);
       vt_sync<NT0>();
       vt_restrict<T, N1, NT0>(rbuf, base + G::off(1) + 2 * G::np(1));
       vt_sync<NT0>();
@@ -1760,7 +1840,7 @@ __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 :
       vt_sync<NT0>();
       pdl_trigger();                                   // only the post-smoothing and the write remain
       for (int sw = 0; sw < nu; ++sw) {
-        if (cur == 0) vt_strip<T, S0, 0>(xa, xb, bv, g, d, e, c, wd); else vt_strip<T, S0, 0>(xb, xa, bv, g, d, e, c, wd);
+        if (cur == 0) z.template pass<0>(xa, xb, d, e, c, wd); else z.template pass<0>(xb, xa, d, e, c, wd);
         cur ^= 1;
         vt_sync<NT0>();
       }
