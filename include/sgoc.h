@@ -207,6 +207,12 @@ sgoc_status sgoc_server_stats(const sgoc_server* sv, int64_t* admitted, int64_t*
  * the stream.  The paper has no counterpart: it concerns this GPU code only. */
 sgoc_status sgoc_autotune(sgoc_problem* pb, void* d_ws, size_t ws_bytes, int32_t* chosen,
                           int32_t nchosen, void* stream);
+/* Pins kernel `variant` (0..5 as above; -1 clears the entry, restoring the
+ * built-in rule) for SG launch shape `shape` of a solve of pb (0 the KKT product,
+ * 1 the operator alone, 2 + d the hGS visit of level d) in precision 0
+ * (float64) or 1 (float32), in the same process-wide table.  The problem need
+ * not be uploaded.  SGOC_ERR_UNSUPPORTED when the variant does not apply. */
+sgoc_status sgoc_set_kernel(sgoc_problem* pb, int32_t precision, int32_t shape, int32_t variant);
 
 /* ---- building blocks (used by tests and benchmarks) ---- */
 

@@ -71,6 +71,7 @@ SIGNATURES = {
     "sgoc_server_poll": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Result), _I32, _PI32]),
     "sgoc_server_stats": (ctypes.c_int, [_P, _PI64, _PI64, _PI64, _PSZ]),
     "sgoc_autotune": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _I32, _P]),
+    "sgoc_set_kernel": (ctypes.c_int, [_P, _I32, _I32, _I32]),
     "sgoc_apply_operator": (ctypes.c_int, [_P, _I32, _P, _P, _I32, _P]),
     "sgoc_apply_operator_variant": (ctypes.c_int, [_P, _I32, _I32, _P, _P, _I32, _P]),
     "sgoc_apply_kkt": (ctypes.c_int, [_P, _I32, _P, _P, _P]),

@@ -862,6 +862,12 @@ void sg_set_variant(const SGArgs<T>& a, int v) {
   g_tune[sg_key(a)] = v;
 }
 
+template <typename T>
+void sg_clear_variant(const SGArgs<T>& a) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune.erase(sg_key(a));
+}
+
 void sg_clear_tuning() {
   std::lock_guard<std::mutex> g(g_tune_mu);
   g_tune.clear();
@@ -2686,6 +2692,7 @@ cudaError_t launch_fill(T* x, int64_t n, T v, cudaStream_t st) {
   template cudaError_t launch_sg_variant<T>(const SGArgs<T>&, int, cudaStream_t);                              \
   template int sg_tuned_variant<T>(const SGArgs<T>&);                                                              \
   template void sg_set_variant<T>(const SGArgs<T>&, int);                                                          \
+  template void sg_clear_variant<T>(const SGArgs<T>&);                                                             \
   template bool sg_variant_feasible<T>(const SGArgs<T>&, int);                                                     \
   template cudaError_t launch_mass<T>(const MassArgs<T>&, cudaStream_t);                                           \
   template cudaError_t launch_cheb<T>(const ChebArgs<T>&, cudaStream_t);                                           \

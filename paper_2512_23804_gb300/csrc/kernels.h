@@ -67,6 +67,8 @@ template <typename T>
 int sg_tuned_variant(const SGArgs<T>& a);          // -1: not tuned
 template <typename T>
 void sg_set_variant(const SGArgs<T>& a, int variant);
+template <typename T>
+void sg_clear_variant(const SGArgs<T>& a);
 void sg_clear_tuning();
 
 // out[t][c] = cy*out_old + sum_j a_j w_j(c,t) (M V_j[t + shift_j])[c] + ar*R[t][c]

@@ -1090,6 +1090,28 @@ static sgoc_status prec_hook(sgoc_problem* pb, void* ws, size_t bytes, PrecWS<T>
 
 using namespace sgoc;
 
+
+// SG launch shape `shape` of a solve (0 KKT product, 1 operator alone, 2 + d hGS visit of level d)
+// with placeholder pointers: the tuning table is keyed by the shape only.
+template <typename T>
+static bool shape_args(sgoc_problem* pb, int shape, SGArgs<T>* out) {
+  static T dummy[1];
+  if (shape == 0 || shape == 1) {
+    SGArgs<T> g = sg_full<T>(pb, dummy, dummy, T(shape == 0 ? -1 : 1));
+    if (shape == 1) g.cy = T(0);
+    if (!g.u_mb) g.u_mb = reinterpret_cast<const int*>(dummy);       // slot table exists once uploaded
+    *out = g;
+    return true;
+  }
+  const int d = shape - 2;
+  if (d < 0 || d > pb->p) return false;
+  PrecWS<T> w;
+  w.RH = dummy;
+  *out = hgs_args<T>(pb, w, dummy, dummy, pb->slabs, d);
+  if (!out->u_mb) out->u_mb = reinterpret_cast<const int*>(dummy);   // slot table exists once uploaded
+  return true;
+}
+
 // ------------------------------------------------------------------ tuning --
 // Times every feasible SG kernel variant on each SG launch shape of a solve of
 // this problem (the KKT product, the operator alone, each hGS level visit) on the
@@ -1409,6 +1431,30 @@ sgoc_status sgoc_apply_operator_variant(sgoc_problem* pb, int32_t precision, int
   }
   set_error("precision must be 0 or 1");
   return SGOC_ERR_INVALID_ARG;
+}
+
+
+sgoc_status sgoc_set_kernel(sgoc_problem* pb, int32_t precision, int32_t shape, int32_t variant) {
+  if (!pb) { set_error("null problem"); return SGOC_ERR_INVALID_ARG; }
+  if (variant < -1 || variant >= kSGVariants) { set_error("kernel variant out of range"); return SGOC_ERR_INVALID_ARG; }
+  if (precision == 0) {
+    SGArgs<double> g{};
+    if (!shape_args<double>(pb, shape, &g)) { set_error("shape out of range"); return SGOC_ERR_INVALID_ARG; }
+    if (variant < 0) { sg_clear_variant(g); return SGOC_OK; }
+    if (!sg_variant_feasible(g, variant)) { set_error("kernel variant not applicable"); return SGOC_ERR_UNSUPPORTED; }
+    sg_set_variant(g, variant);
+  } else if (precision == 1) {
+    SGArgs<float> g{};
+    if (!shape_args<float>(pb, shape, &g)) { set_error("shape out of range"); return SGOC_ERR_INVALID_ARG; }
+    if (variant < 0) { sg_clear_variant(g); return SGOC_OK; }
+    if (!sg_variant_feasible(g, variant)) { set_error("kernel variant not applicable"); return SGOC_ERR_UNSUPPORTED; }
+    sg_set_variant(g, variant);
+  } else {
+    set_error("precision must be 0 or 1");
+    return SGOC_ERR_INVALID_ARG;
+  }
+  invalidate_graphs(pb);
+  return SGOC_OK;
 }
 
 }  // extern "C"

@@ -143,6 +143,12 @@ class SGProblem:
                                                  _stream(stream)), "sgoc_apply_operator")
         return Y
 
+    def set_kernel(self, shape, variant, precision=None):
+        """Pin SG kernel `variant` (-1: built-in rule) for launch shape `shape` (0 KKT,
+        1 operator, 2 + d hGS level d) in this problem's precision (or the given one)."""
+        prec = precision if precision is not None else (0 if self.precision == "fp64" else 1)
+        abi.check(abi.load().sgoc_set_kernel(self._handle, prec, shape, variant), "sgoc_set_kernel")
+
     def apply_operator_variant(self, X, variant, nslabs=1, out=None, stream=None):
         """The SG operator with a given kernel variant (0..5, see sgoc_autotune)."""
         import torch

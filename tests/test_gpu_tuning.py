@@ -74,3 +74,51 @@ def test_autotune_keeps_the_solution(precision):
     x1, i1 = sp.solve()
     assert i1["iterations"] == i0["iterations"]
     assert torch.equal(x1, x0)
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-5)])
+def test_pinned_kernels_in_hgs_and_kkt(dtype, tol):
+    """Every applicable SG kernel pinned on every SG shape of a solve: the hGS sweep (mass
+    term and right-hand side in the epilogue) matches the oracle and all kernels agree bit
+    for bit; so does the KKT product."""
+    from paper_2512_23804_gb300 import SGProblem, abi
+    from oracle.precond import BlockPreconditioner
+    pr = si.random_small(66, nx=64, M=3, p=3, beta=1e-3)
+    d = SGData(pr)
+    prec = "fp64" if dtype == torch.float64 else "mixed"
+    sp = SGProblem.from_problem(pr, precision=prec).upload()
+    pc = BlockPreconditioner(d)
+    R = si.random_panel(71, d.n, d.P)
+    v = si.random_panel(72, 3 * d.n, d.P)
+    if dtype == torch.float32:
+        R = R.astype(np.float32).astype(np.float64)
+        v = v.astype(np.float32).astype(np.float64)
+    ref_h = d.vec(pc.hgs.apply(d.mat(R)))
+    ref_k = d.kkt_apply(v)
+    Rd = torch.from_numpy(R).to("cuda", dtype)
+    vd = torch.from_numpy(v).to("cuda", dtype)
+    pid = 0 if dtype == torch.float64 else 1
+    shapes = [0, 1] + [2 + lev for lev in range(pr.p + 1)]
+    outs = []
+    try:
+        for var in range(6):
+            for sh in shapes:
+                try:
+                    sp.set_kernel(sh, var, precision=pid)
+                except abi.SgocError as e:           # not applicable here: the built-in choice
+                    assert e.status == abi.SGOC_ERR_UNSUPPORTED
+                    sp.set_kernel(sh, -1, precision=pid)
+            h = sp.apply_hgs(Rd)
+            k = sp.apply_kkt(vd)
+            torch.cuda.synchronize()
+            h = h.double().cpu().numpy()
+            k = k.double().cpu().numpy()
+            assert rel(h, ref_h) <= tol, var
+            assert rel(k, ref_k) <= (1e-13 if dtype == torch.float64 else 2e-6), var
+            outs.append((var, h, k))
+    finally:
+        for sh in shapes:
+            sp.set_kernel(sh, -1, precision=pid)
+    for var, h, k in outs[1:]:
+        assert np.array_equal(h, outs[0][1]), var
+        assert np.array_equal(k, outs[0][2]), var
