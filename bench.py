@@ -294,7 +294,8 @@ def run_ours(args):
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}",
                    "batching": "sequential" if args.sequential else "3 concurrent solves (sgoc_solve_batch, 3 streams)",
                    "sg_kernels": "built-in choice" if sg_kernels is None else
-                   dict(zip(["kkt", "operator"] + [f"hgs_level{d}" for d in range(len(sg_kernels) - 2)],
+                   dict(zip(["kkt", "operator"] + [f"hgs_level{d}" for d in range((len(sg_kernels) - 2) // 2)] +
+                            [f"hgs_level{d}_first" for d in range((len(sg_kernels) - 2) // 2)],
                             [SG_KERNEL_NAMES[v] for v in sg_kernels]))},
         "latency_ms": {"p50": float(sorted(solve_ms)[len(solve_ms) // 2]),
                        "p99": float(sorted(solve_ms)[min(len(solve_ms) - 1, math.ceil(0.99 * len(solve_ms)) - 1)])},

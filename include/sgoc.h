@@ -194,14 +194,16 @@ sgoc_status sgoc_server_stats(const sgoc_server* sv, int64_t* admitted, int64_t*
  * form) that form the same products and sums in the same order, so they give
  * bitwise identical results and differ only in speed.  sgoc_autotune times each
  * applicable kernel on every SG launch shape a solve of `pb` uses (the KKT
- * product, the operator alone, the right-hand side of each hGS level visit of
- * Alg. 1; in mixed precision also the float64 true-residual product) on the
+ * product, the operator alone, the right-hand side of the return visit of each
+ * hGS level of Alg. 1 (d = 0..p), the right-hand side of the first visit of each
+ * level (couplings to the level below only); in mixed precision also the
+ * float64 true-residual product) on the
  * caller's workspace (d_ws, ws_bytes as for sgoc_solve; its contents are
  * overwritten) and stream, and records the fastest in a process-wide table keyed
  * by launch shape, which every later launch of that shape (any problem with the
  * same grid, chaos levels, truncation, slabs and precision) uses.  Without
- * tuning a built-in rule chooses.  chosen (nullable, nchosen entries) receives
- * the kernel index per shape in the order above (0 one-phase, 1 and 2 four
+ * tuning a built-in rule chooses.  chosen (nullable, nchosen entries, 2p + 4 used)
+ * receives the kernel index per shape in the order above (0 one-phase, 1 and 2 four
  * nodes per thread on 32- and 16-node tiles, 3 two-phase float32, 4 and 5 the
  * four-node kernels built for four instead of two CTAs per SM).  Synchronizes
  * the stream.  The paper has no counterpart: it concerns this GPU code only. */
@@ -209,7 +211,8 @@ sgoc_status sgoc_autotune(sgoc_problem* pb, void* d_ws, size_t ws_bytes, int32_t
                           int32_t nchosen, void* stream);
 /* Pins kernel `variant` (0..5 as above; -1 clears the entry, restoring the
  * built-in rule) for SG launch shape `shape` of a solve of pb (0 the KKT product,
- * 1 the operator alone, 2 + d the hGS visit of level d) in precision 0
+ * 1 the operator alone, 2 + d the return visit of hGS level d, 3 + p + d the
+ * first visit of level d) in precision 0
  * (float64) or 1 (float32), in the same process-wide table.  The problem need
  * not be uploaded.  SGOC_ERR_UNSUPPORTED when the variant does not apply. */
 sgoc_status sgoc_set_kernel(sgoc_problem* pb, int32_t precision, int32_t shape, int32_t variant);

@@ -320,8 +320,8 @@ __global__ void __launch_bounds__(kSGThreads, 2) sg_kernel(SGArgs<T> a, int rows
       const int lx = q % TX, bl = q / TX;
       const int ix = ix0 + lx;
       const int beta = a.out0 + bl;
-      const V4 tb = Ts[size_t(beta - a.in0) * TX + lx];
-      T diag = dot4<T>(Ks[lx], tb);
+      T diag = T(0);
+      if (!a.no_own) diag = dot4<T>(Ks[lx], Ts[size_t(beta - a.in0) * TX + lx]);
       T off = T(0);
       const int e1 = Pe[bl];
       for (int e = Ps[bl]; e < e1; ++e) {
@@ -542,8 +542,8 @@ __global__ void __launch_bounds__(kSG4Threads, MINB) sg4_kernel(SGArgs<T> a, int
       const int sl = q / NQ, qd = q - sl * NQ;
       const int bl = Ord[sl];
       const int beta = a.out0 + bl;
-      T diag[4], off[4];
-      {
+      T diag[4] = {T(0), T(0), T(0), T(0)}, off[4];
+      if (!a.no_own) {
         const V4* kb = Ks4 + qd;
         const V4* tb = Ts4 + size_t(beta - a.in0) * TX + qd;
         const V4 k0 = kb[0], k1 = kb[NQ], k2 = kb[2 * NQ], k3 = kb[3 * NQ];
@@ -758,7 +758,7 @@ __global__ void __launch_bounds__(kSGUThreads, 1) sgu_kernel(SGArgs<float> a, in
     for (int bl = warp; bl < nout; bl += NW) {
       const int beta = a.out0 + bl;
       const float* ul = U + lane;
-      const float diag = ul[Dg[bl] * TX];
+      const float diag = a.no_own ? 0.f : ul[Dg[bl] * TX];
       float off = 0.f;
       const int e1 = Ep[bl + 1];
       for (int e = Ep[bl]; e < e1; ++e) {
@@ -844,7 +844,7 @@ std::map<SGKey, int> g_tune;
 
 template <typename T>
 SGKey sg_key(const SGArgs<T>& a) {
-  const int flags = (a.cm != T(0) ? 1 : 0) | (a.R ? 2 : 0) | (a.cy != T(0) ? 4 : 0);
+  const int flags = (a.cm != T(0) ? 1 : 0) | (a.R ? 2 : 0) | (a.cy != T(0) ? 4 : 0) | (a.no_own ? 8 : 0);
   return SGKey{a.n1, a.in0, a.in1, a.out0, a.out1, a.M, a.kmax, a.nslabs, int(sizeof(T)), flags};
 }
 }  // namespace
@@ -899,7 +899,7 @@ static cudaError_t launch_sg_one_phase(const SGArgs<T>& a, cudaStream_t st) {
 template <typename T>
 cudaError_t launch_sg_variant(const SGArgs<T>& a, int v, cudaStream_t st) {
   if (a.out1 <= a.out0 || a.nslabs <= 0) return cudaSuccess;
-  if (a.out0 < a.in0 || a.out1 > a.in1) return cudaErrorInvalidValue;
+  if (!a.no_own && (a.out0 < a.in0 || a.out1 > a.in1)) return cudaErrorInvalidValue;
   if (!sg_variant_feasible(a, v)) return cudaErrorInvalidConfiguration;
   switch (v) {
     case 1: return launch_sg4_tx<T, 32, 2>(a, sg4_smem<T, 32>(a), st);
@@ -919,7 +919,7 @@ cudaError_t launch_sg_variant(const SGArgs<T>& a, int v, cudaStream_t st) {
 template <typename T>
 cudaError_t launch_sg(const SGArgs<T>& a, cudaStream_t st) {
   if (a.out1 <= a.out0 || a.nslabs <= 0) return cudaSuccess;
-  if (a.out0 < a.in0 || a.out1 > a.in1) return cudaErrorInvalidValue;
+  if (!a.no_own && (a.out0 < a.in0 || a.out1 > a.in1)) return cudaErrorInvalidValue;
   const int tuned = sg_tuned_variant(a);
   if (tuned >= 0 && sg_variant_feasible(a, tuned)) return launch_sg_variant(a, tuned, st);
   // untuned: the quad kernel on 32-node tiles (measured fastest at 128x128 P=84 and 512x512

@@ -52,6 +52,9 @@ struct SGArgs {
   // slot table of this launch shape (two-phase kernel; null: the one-phase kernels)
   const int* u_mb; const int* u_diag; const int* u_eptr; const int2* u_e32;
   int u_nslots, u_nent;
+  // 1: the outputs' own columns take no part (no kappa_0 or mass term, c0 and cm unused);
+  // the output range then need not lie inside the input range
+  int no_own;
 };
 template <typename T>
 cudaError_t launch_sg(const SGArgs<T>& a, cudaStream_t st);

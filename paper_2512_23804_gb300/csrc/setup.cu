@@ -88,19 +88,29 @@ namespace sgoc {
 // Slot table of one SG launch shape (see UTab): which (alpha, k) products
 // sum_e kappa_k(e) T_e(alpha) the outputs of the shape use, and where each
 // output finds them.  Entries keep the order of the neighbour table.
-static UTab build_utab(const sgoc_problem* pb, int in0, int in1, int out0, int out1, int kmax) {
+// Neighbour table of the output columns: the full one or its downward part (entries
+// whose input column lies one level below the output's).
+struct NbrView {
+  const std::vector<int>& ptr;
+  const std::vector<int>& alpha;
+  const std::vector<int>& k;
+  const std::vector<double>& c;
+};
+
+// own: the outputs also use their own columns (kappa_0 term); then (beta, 0) has a slot.
+static UTab build_utab(const NbrView& t, int in0, int in1, int out0, int out1, int kmax, bool own) {
   UTab u;
   u.in0 = in0; u.in1 = in1; u.out0 = out0; u.out1 = out1; u.kmax = kmax;
   const int nin = in1 - in0, nout = out1 - out0;
   std::vector<unsigned> mask(nin, 0u);
   auto end_of = [&](int b) {
-    int e = pb->nbr_ptr[b];
-    while (e < pb->nbr_ptr[b + 1] && pb->nbr_k[e] < kmax) ++e;
+    int e = t.ptr[b];
+    while (e < t.ptr[b + 1] && t.k[e] < kmax) ++e;
     return e;
   };
   for (int b = out0; b < out1; ++b) {
-    mask[b - in0] |= 1u;
-    for (int e = pb->nbr_ptr[b]; e < end_of(b); ++e) mask[pb->nbr_alpha[e] - in0] |= 1u << pb->nbr_k[e];
+    if (own) mask[b - in0] |= 1u;
+    for (int e = t.ptr[b]; e < end_of(b); ++e) mask[t.alpha[e] - in0] |= 1u << t.k[e];
   }
   u.mb.resize(2 * size_t(nin));
   int base = 0;
@@ -117,10 +127,10 @@ static UTab build_utab(const sgoc_problem* pb, int in0, int in1, int out0, int o
   u.diag.resize(nout);
   u.eptr.assign(nout + 1, 0);
   for (int b = out0; b < out1; ++b) {
-    u.diag[b - out0] = slot(b, 0);
-    for (int e = pb->nbr_ptr[b]; e < end_of(b); ++e) {
-      u.eslot.push_back(slot(pb->nbr_alpha[e], pb->nbr_k[e]));
-      u.ec.push_back(pb->nbr_c[e]);
+    u.diag[b - out0] = own ? slot(b, 0) : -1;
+    for (int e = t.ptr[b]; e < end_of(b); ++e) {
+      u.eslot.push_back(slot(t.alpha[e], t.k[e]));
+      u.ec.push_back(t.c[e]);
     }
     u.eptr[b - out0 + 1] = int(u.eslot.size());
   }
@@ -245,6 +255,25 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
     while (e < pb->nbr_ptr[b + 1] && pb->nbr_k[e] < pb->r) ++e;
     pb->nbr_end_r[b] = e;
   }
+  // downward part: entries alpha = beta - e_k one level below beta (the only nonzero couplings of a
+  // level's first hGS visit, when the levels at and above it are still zero)
+  std::vector<int> level_of(pb->P);
+  for (int d = 0; d <= p; ++d)
+    for (int b = pb->off[d]; b < pb->off[d + 1]; ++b) level_of[b] = d;
+  pb->dn_ptr.assign(pb->P + 1, 0);
+  pb->dn_end_r.resize(pb->P);
+  for (int b = 0; b < pb->P; ++b) {
+    for (int e = pb->nbr_ptr[b]; e < pb->nbr_ptr[b + 1]; ++e)
+      if (level_of[pb->nbr_alpha[e]] < level_of[b]) {
+        pb->dn_alpha.push_back(pb->nbr_alpha[e]);
+        pb->dn_k.push_back(pb->nbr_k[e]);
+        pb->dn_c.push_back(pb->nbr_c[e]);
+      }
+    pb->dn_ptr[b + 1] = int(pb->dn_alpha.size());
+    int e = pb->dn_ptr[b];
+    while (e < pb->dn_ptr[b + 1] && pb->dn_k[e] < pb->r) ++e;
+    pb->dn_end_r[b] = e;
+  }
 
   // multigrid hierarchy of the mean operator:
   // steady  A~_1 = kappa0 K + s M            (Eq. (mathcalZ))
@@ -267,10 +296,15 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
   if (d->nt > 1) { pb->dweights[0] = 0.5; pb->dweights[d->nt - 1] = 0.5; }
 
   // slot tables of the SG launch shapes: the full operator and the hGS visit of each level
-  pb->utabs.push_back(build_utab(pb, 0, pb->P, 0, pb->P, M + 1));
+  const NbrView full{pb->nbr_ptr, pb->nbr_alpha, pb->nbr_k, pb->nbr_c};
+  const NbrView down{pb->dn_ptr, pb->dn_alpha, pb->dn_k, pb->dn_c};
+  pb->utabs.push_back(build_utab(full, 0, pb->P, 0, pb->P, M + 1, true));
   for (int d = 0; d <= p; ++d)
-    pb->utabs.push_back(build_utab(pb, pb->off[d > 0 ? d - 1 : 0], pb->off[d + 2 <= p + 1 ? d + 2 : p + 1],
-                                   pb->off[d], pb->off[d + 1], pb->r));
+    pb->utabs.push_back(build_utab(full, pb->off[d > 0 ? d - 1 : 0], pb->off[d + 2 <= p + 1 ? d + 2 : p + 1],
+                                   pb->off[d], pb->off[d + 1], pb->r, true));
+  for (int d = 0; d <= p; ++d)
+    pb->utabs.push_back(build_utab(down, pb->off[d > 0 ? d - 1 : 0], pb->off[d], pb->off[d], pb->off[d + 1],
+                                   pb->r, false));
 
   // persistent layout
   const size_t nk = size_t(M + 1) * nel;
@@ -281,6 +315,9 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
   off = align256(off + pb->P * 4);
   off = align256(off + nnz * 8); off = align256(off + nnz * 4);
   off = align256(off + size_t(pb->slabs) * pb->n * 8); off = align256(off + size_t(pb->n) * 8);
+  const size_t nnz_dn = pb->dn_alpha.size();
+  off = align256(off + (pb->P + 1) * 4); off = align256(off + pb->P * 4); off = align256(off + nnz_dn * 4);
+  off = align256(off + nnz_dn * 4); off = align256(off + nnz_dn * 8); off = align256(off + nnz_dn * 4);
   for (const UTab& u : pb->utabs) off += utab_bytes(u);
   pb->persistent_bytes = off;
   *out = pb;
@@ -333,6 +370,14 @@ sgoc_status sgoc_problem_upload(sgoc_problem* pb, void* d_persistent, size_t byt
   pb->dev.nbr_c32 = reinterpret_cast<float*>(carve(nnz * 4));
   pb->dev.yhat = reinterpret_cast<double*>(carve(size_t(pb->slabs) * pb->n * 8));
   pb->dev.y0 = reinterpret_cast<double*>(carve(size_t(pb->n) * 8));
+  const size_t nnz_dn = pb->dn_alpha.size();
+  pb->dev.dn_ptr = reinterpret_cast<int*>(carve((pb->P + 1) * 4));
+  pb->dev.dn_end_r = reinterpret_cast<int*>(carve(pb->P * 4));
+  pb->dev.dn_alpha = reinterpret_cast<int*>(carve(nnz_dn * 4));
+  pb->dev.dn_k = reinterpret_cast<int*>(carve(nnz_dn * 4));
+  pb->dev.dn_c64 = reinterpret_cast<double*>(carve(nnz_dn * 8));
+  pb->dev.dn_c32 = reinterpret_cast<float*>(carve(nnz_dn * 4));
+  std::vector<float> dn32(pb->dn_c.begin(), pb->dn_c.end());
   std::vector<std::vector<int2>> e32s;
   for (UTab& u : pb->utabs) {
     const size_t nin = u.in1 - u.in0, nout = u.out1 - u.out0;
@@ -372,6 +417,14 @@ sgoc_status sgoc_problem_upload(sgoc_problem* pb, void* d_persistent, size_t byt
     SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.y0, pb->y0.data(), size_t(pb->n) * 8, cudaMemcpyHostToDevice, st));
   else
     SGOC_CUDA_TRY(cudaMemsetAsync(pb->dev.y0, 0, size_t(pb->n) * 8, st));
+  SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.dn_ptr, pb->dn_ptr.data(), (pb->P + 1) * 4, cudaMemcpyHostToDevice, st));
+  SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.dn_end_r, pb->dn_end_r.data(), pb->P * 4, cudaMemcpyHostToDevice, st));
+  if (nnz_dn) {
+    SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.dn_alpha, pb->dn_alpha.data(), nnz_dn * 4, cudaMemcpyHostToDevice, st));
+    SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.dn_k, pb->dn_k.data(), nnz_dn * 4, cudaMemcpyHostToDevice, st));
+    SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.dn_c64, pb->dn_c.data(), nnz_dn * 8, cudaMemcpyHostToDevice, st));
+    SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.dn_c32, dn32.data(), nnz_dn * 4, cudaMemcpyHostToDevice, st));
+  }
   for (size_t i = 0; i < pb->utabs.size(); ++i) {
     const UTab& u = pb->utabs[i];
     const size_t nin = u.in1 - u.in0, nout = u.out1 - u.out0;

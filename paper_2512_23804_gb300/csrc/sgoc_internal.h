@@ -67,6 +67,12 @@ struct DevData {
   int* nbr_k = nullptr;        // KL index k (1..M)
   double* nbr_c64 = nullptr;   // E[xi_k Psi_alpha Psi_beta]
   float* nbr_c32 = nullptr;
+  int* dn_ptr = nullptr;       // downward part of the neighbour table (alpha one level below beta)
+  int* dn_end_r = nullptr;
+  int* dn_alpha = nullptr;
+  int* dn_k = nullptr;
+  double* dn_c64 = nullptr;
+  float* dn_c32 = nullptr;
   double* yhat = nullptr;      // slabs x n target values
   double* y0 = nullptr;        // n initial state (zeros when absent)
 };
@@ -87,11 +93,14 @@ struct sgoc_problem {
   std::vector<int> off;              // p + 2 level offsets
   std::vector<int> nbr_ptr, nbr_alpha, nbr_k, nbr_end_r;
   std::vector<double> nbr_c;
+  std::vector<int> dn_ptr, dn_alpha, dn_k, dn_end_r;   // downward part (one level below)
+  std::vector<double> dn_c;
   // multigrid hierarchy of the mean operator (level 0 = finest)
   std::vector<sgoc::Level> levels;
   double mass_h2_36 = 0;             // h^2 / 36 on the finest grid
   std::vector<double> dweights;      // time weights D_t (1 when steady)
-  // SG launch shapes: [0] the full operator (all columns, all k), [1 + d] the hGS visit of level d
+  // SG launch shapes: [0] the full operator (all columns, all k), [1 + d] the hGS visit of level d,
+  // [2 + p + d] the first (ascending) hGS visit of level d: couplings to level d - 1 only
   std::vector<sgoc::UTab> utabs;
   // device
   sgoc::DevData dev;

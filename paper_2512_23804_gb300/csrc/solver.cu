@@ -248,17 +248,42 @@ static SGArgs<T> hgs_args(const sgoc_problem* pb, PrecWS<T>& w, const T* R, T* V
   return g;
 }
 
+// The first (ascending) visit of level d: levels d and above are still zero, so the right-hand
+// side is R_(d) minus the couplings to level d - 1 only (downward neighbour table), without the
+// level's own kappa_0 and mass terms.  The same values as hgs_args on the zero-padded levels.
+template <typename T>
+static SGArgs<T> hgs_args_first(const sgoc_problem* pb, PrecWS<T>& w, const T* R, T* V, int slabs, int d) {
+  SGArgs<T> g = hgs_args<T>(pb, w, R, V, slabs, d);
+  const int a0 = pb->off[d], a1 = pb->off[d + 1];
+  g.in0 = pb->off[d > 0 ? d - 1 : 0];
+  g.in1 = a0;
+  g.no_own = 1;
+  g.c0 = T(0); g.cm = T(0);
+  g.nbr_ptr = pb->dev.dn_ptr; g.nbr_alpha = pb->dev.dn_alpha; g.nbr_k = pb->dev.dn_k;
+  g.nbr_c = std::is_same<T, double>::value ? reinterpret_cast<const T*>(pb->dev.dn_c64)
+                                           : reinterpret_cast<const T*>(pb->dev.dn_c32);
+  g.nbr_end = pb->r == pb->M + 1 ? pb->dev.dn_ptr + 1 : pb->dev.dn_end_r;
+  g.nnz_out = pb->dn_ptr[a1] - pb->dn_ptr[a0];
+  double deg = 0;
+  for (int b = a0; b < a1; ++b)
+    for (int e = pb->dn_ptr[b]; e < pb->dn_ptr[b + 1]; ++e) deg += pb->dn_k[e] < pb->r ? 1 : 0;
+  g.deg_sum = deg;
+  set_utab(g, pb->utabs[2 + pb->p + d]);
+  return g;
+}
+
 template <typename T>
 static sgoc_status hgs(const sgoc_problem* pb, PrecWS<T>& w, const T* R, T* V, int slabs, cudaStream_t st) {
   const int P = pb->P, p = pb->p;
   const int64_t n = pb->n, ps = int64_t(P) * n;
   SGOC_LAUNCH(launch_fill<T>(V, slabs * ps, T(0), st));
-  std::vector<int> order;
-  for (int d = 0; d <= p; ++d) order.push_back(d);
-  for (int d = p - 1; d >= 0; --d) order.push_back(d);
-  for (int d : order) {
+  // palindromic sweep 0, 1, ..., p, ..., 1, 0: the first visit of each level, then the returns
+  for (int step = 0; step < 2 * p + 1; ++step) {
+    const bool first = step <= p;
+    const int d = first ? step : 2 * p - step;
     const int a0 = pb->off[d], L = pb->off[d + 1] - a0;
-    SGOC_LAUNCH(launch_sg<T>(hgs_args<T>(pb, w, R, V, slabs, d), st));
+    SGOC_LAUNCH(launch_sg<T>(first ? hgs_args_first<T>(pb, w, R, V, slabs, d) : hgs_args<T>(pb, w, R, V, slabs, d),
+                             st));
     SGOC_TRY(vcycle<T>(pb, w, w.RH, nullptr, int64_t(slabs) * L, V, ps, L, a0, st));
   }
   return SGOC_OK;
@@ -1091,7 +1116,8 @@ static sgoc_status prec_hook(sgoc_problem* pb, void* ws, size_t bytes, PrecWS<T>
 using namespace sgoc;
 
 
-// SG launch shape `shape` of a solve (0 KKT product, 1 operator alone, 2 + d hGS visit of level d)
+// SG launch shape `shape` of a solve (0 KKT product, 1 operator alone, 2 + d return visit of hGS
+// level d, 3 + p + d first visit of level d)
 // with placeholder pointers: the tuning table is keyed by the shape only.
 template <typename T>
 static bool shape_args(sgoc_problem* pb, int shape, SGArgs<T>* out) {
@@ -1103,11 +1129,12 @@ static bool shape_args(sgoc_problem* pb, int shape, SGArgs<T>* out) {
     *out = g;
     return true;
   }
-  const int d = shape - 2;
-  if (d < 0 || d > pb->p) return false;
+  const int d = shape - 2 <= pb->p ? shape - 2 : shape - 3 - pb->p;
+  if (shape < 2 || d < 0 || d > pb->p) return false;
   PrecWS<T> w;
   w.RH = dummy;
-  *out = hgs_args<T>(pb, w, dummy, dummy, pb->slabs, d);
+  *out = shape - 2 <= pb->p ? hgs_args<T>(pb, w, dummy, dummy, pb->slabs, d)
+                            : hgs_args_first<T>(pb, w, dummy, dummy, pb->slabs, d);
   if (!out->u_mb) out->u_mb = reinterpret_cast<const int*>(dummy);   // slot table exists once uploaded
   return true;
 }
@@ -1149,6 +1176,7 @@ static sgoc_status tune_problem(sgoc_problem* pb, Layout& L, PrecWS<T>& w, T* X,
   op.cy = T(0);
   shapes.push_back(op);                                       // the operator alone
   for (int d = 0; d <= pb->p; ++d) shapes.push_back(hgs_args<T>(pb, w, Y, X, pb->slabs, d));
+  for (int d = 0; d <= pb->p; ++d) shapes.push_back(hgs_args_first<T>(pb, w, Y, X, pb->slabs, d));
   int k = 0;
   for (const SGArgs<T>& a : shapes) {
     double ms = 0;

@@ -125,7 +125,7 @@ class SGProblem:
         fastest per shape (process-wide); returns the chosen kernel per shape."""
         self.upload(stream)
         ws = self.workspace()
-        n = self.p + 3
+        n = 2 * self.p + 4
         chosen = (ctypes.c_int32 * n)()
         abi.check(abi.load().sgoc_autotune(self._handle, _dptr(ws), ws.numel(), ctypes.cast(chosen, ctypes.c_void_p),
                                            n, _stream(stream)), "sgoc_autotune")
@@ -145,7 +145,8 @@ class SGProblem:
 
     def set_kernel(self, shape, variant, precision=None):
         """Pin SG kernel `variant` (-1: built-in rule) for launch shape `shape` (0 KKT,
-        1 operator, 2 + d hGS level d) in this problem's precision (or the given one)."""
+        1 operator, 2 + d return visit of hGS level d, 3 + p + d first visit of level d)
+        in this problem's precision (or the given one)."""
         prec = precision if precision is not None else (0 if self.precision == "fp64" else 1)
         abi.check(abi.load().sgoc_set_kernel(self._handle, prec, shape, variant), "sgoc_set_kernel")
 

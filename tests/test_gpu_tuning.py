@@ -69,7 +69,7 @@ def test_autotune_keeps_the_solution(precision):
     x0, i0 = sp.solve()
     x0 = x0.clone()
     chosen = sp.autotune()
-    assert len(chosen) == pr.p + 3
+    assert len(chosen) == 2 * pr.p + 4
     assert all(0 <= v <= 5 for v in chosen)
     x1, i1 = sp.solve()
     assert i1["iterations"] == i0["iterations"]
@@ -98,7 +98,7 @@ def test_pinned_kernels_in_hgs_and_kkt(dtype, tol):
     Rd = torch.from_numpy(R).to("cuda", dtype)
     vd = torch.from_numpy(v).to("cuda", dtype)
     pid = 0 if dtype == torch.float64 else 1
-    shapes = [0, 1] + [2 + lev for lev in range(pr.p + 1)]
+    shapes = [0, 1] + [2 + lev for lev in range(2 * pr.p + 2)]
     outs = []
     try:
         for var in range(6):
