@@ -962,9 +962,13 @@ __device__ __forceinline__ void mass_row(const T* __restrict__ V, int ix, int y,
 template <typename T>
 __global__ void __launch_bounds__(128) mass_kernel(MassArgs<T> a, int strips, int64_t nwork) {
   pdl_enter();
-  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ix >= a.n1) return;
+  // tile of the inputs: rows y0-1 .. y0+kMassRows, columns x0-1 .. x0+128 (zero outside the grid)
+  constexpr int TW = 128 + 2, TH = kMassRows + 2;
+  __shared__ T Vs[3][TH][TW];
   const int n1 = a.n1;
+  const int tid = threadIdx.x;
+  const int x0 = blockIdx.x * 128;
+  const int ix = x0 + tid;
   for (int64_t w = blockIdx.y; w < nwork; w += gridDim.y) {
     const int strip = int(w % strips);
     const int64_t cq = w / strips;
@@ -975,40 +979,54 @@ __global__ void __launch_bounds__(128) mass_kernel(MassArgs<T> a, int strips, in
     const int col = a.col0 + c;
     const T hg = col == 0 ? T(1) : T(1) + a.gamma;
     const T dt = (a.nt > 1 && (t == 0 || t == a.nt - 1)) ? T(0.5) : T(1);
-    T* op = a.out + int64_t(t) * a.os + int64_t(c) * a.n + int64_t(y0) * n1 + ix;
-    T acc[kMassRows];
-#pragma unroll
-    for (int r = 0; r < kMassRows; ++r) acc[r] = (r < ny && a.cy != T(0)) ? a.cy * op[int64_t(r) * n1] : T(0);
+    // stage every input's tile with independent loads
     for (int j = 0; j < a.nv; ++j) {
       const int ts = t + a.shift[j];
       if (ts < 0 || ts >= a.nslabs) continue;
-      T wj = a.a[j];
-      if (a.wflags[j] & 1) wj *= hg;
-      if (a.wflags[j] & 2) wj *= dt;
-      wj *= a.mass;
       const T* V = a.V[j] + int64_t(ts) * a.vs[j] + int64_t(c) * a.n;
-      T cm, hm, c0, h0, cp, hp;
-      mass_row(V, ix, y0 - 1, n1, cm, hm);
-      mass_row(V, ix, y0, n1, c0, h0);
-#pragma unroll
-      for (int r = 0; r < kMassRows; ++r) {
-        if (r >= ny) break;
-        mass_row(V, ix, y0 + r + 1, n1, cp, hp);
-        const T edges = (cm + cp) + h0;
-        const T corners = hm + hp;
-        acc[r] = fma(wj, fma(T(16), c0, fma(T(4), edges, corners)), acc[r]);
-        cm = c0; hm = h0; c0 = cp; h0 = hp;
+      for (int q = tid; q < TH * TW; q += 128) {
+        const int r = q / TW, xx = q - r * TW;
+        const int gy = y0 - 1 + r, gx = x0 - 1 + xx;
+        Vs[j][r][xx] = (gy >= 0 && gy < n1 && gx >= 0 && gx < n1) ? V[int64_t(gy) * n1 + gx] : T(0);
       }
     }
-    if (a.R) {
-      const T* Rp = a.R + int64_t(t) * a.rs + int64_t(c) * a.n + int64_t(y0) * n1 + ix;
+    __syncthreads();
+    if (ix < n1) {
+      T* op = a.out + int64_t(t) * a.os + int64_t(c) * a.n + int64_t(y0) * n1 + ix;
+      T acc[kMassRows];
+#pragma unroll
+      for (int r = 0; r < kMassRows; ++r) acc[r] = (r < ny && a.cy != T(0)) ? a.cy * op[int64_t(r) * n1] : T(0);
+      for (int j = 0; j < a.nv; ++j) {
+        const int ts = t + a.shift[j];
+        if (ts < 0 || ts >= a.nslabs) continue;
+        T wj = a.a[j];
+        if (a.wflags[j] & 1) wj *= hg;
+        if (a.wflags[j] & 2) wj *= dt;
+        wj *= a.mass;
+        const T(*tile)[TW] = Vs[j];
+        const int xx = tid + 1;
+        T cm = tile[0][xx], hm = tile[0][xx - 1] + tile[0][xx + 1];
+        T c0 = tile[1][xx], h0 = tile[1][xx - 1] + tile[1][xx + 1];
+#pragma unroll
+        for (int r = 0; r < kMassRows; ++r) {
+          const T cp = tile[r + 2][xx], hp = tile[r + 2][xx - 1] + tile[r + 2][xx + 1];
+          const T edges = (cm + cp) + h0;
+          const T corners = hm + hp;
+          acc[r] = fma(wj, fma(T(16), c0, fma(T(4), edges, corners)), acc[r]);
+          cm = c0; hm = h0; c0 = cp; h0 = hp;
+        }
+      }
+      if (a.R) {
+        const T* Rp = a.R + int64_t(t) * a.rs + int64_t(c) * a.n + int64_t(y0) * n1 + ix;
+#pragma unroll
+        for (int r = 0; r < kMassRows; ++r)
+          if (r < ny) acc[r] = fma(a.ar, Rp[int64_t(r) * n1], acc[r]);
+      }
 #pragma unroll
       for (int r = 0; r < kMassRows; ++r)
-        if (r < ny) acc[r] = fma(a.ar, Rp[int64_t(r) * n1], acc[r]);
+        if (r < ny) op[int64_t(r) * n1] = acc[r];
     }
-#pragma unroll
-    for (int r = 0; r < kMassRows; ++r)
-      if (r < ny) op[int64_t(r) * n1] = acc[r];
+    __syncthreads();                                  // the tile is rewritten by the next work item
   }
 }
 
@@ -1025,7 +1043,7 @@ cudaError_t launch_mass(const MassArgs<T>& a, cudaStream_t st) {
   const double w = sizeof(T);
   ProfScope ps(KK_MASS, st, w * total * (a.nv + 1 + (a.cy != T(0) ? 1 : 0) + (a.R ? 1 : 0)),
                double(total) * (20.0 * a.nv + 2.0));
-  const int tx = a.n1 >= 128 ? 128 : ((a.n1 + 31) / 32) * 32;
+  const int tx = 128;                                   // one 128-node tile per CTA and strip
   const int strips = (a.n1 + kMassRows - 1) / kMassRows;
   const int64_t nwork = int64_t(strips) * a.ncols * a.nslabs;
   const dim3 grid(unsigned((a.n1 + tx - 1) / tx), unsigned(nwork < 65535 ? nwork : 65535));
