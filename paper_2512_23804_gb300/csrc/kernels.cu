@@ -1300,41 +1300,78 @@ __device__ __forceinline__ T stencil_apply(const T* __restrict__ X, int ix, int 
   return fma(d, C, fma(e, edges, c * corners));
 }
 
+// Level-wise multigrid passes (levels above the fused V-cycle): a CTA stages the
+// tile of x its strip of kMassRows rows of one column needs (independent loads,
+// zero outside the grid) and each thread computes one grid column of the strip;
+// blockIdx.y runs over (strip, column) work items.  Stencil order as stencil_apply.
 template <typename T>
-__global__ void smooth_kernel(const T* __restrict__ b, const T* __restrict__ xin, T* xout, int64_t B, int n1, T d,
-                              T e, T c, T omega, T* acc, int64_t acc_ss, int acc_L, int acc_col0) {
-  pdl_enter();
-  const int64_t n = int64_t(n1) * n1;
-  const int64_t total = B * n;
-  const T wd = omega / d;
-  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total; q += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t col = q / n, node = q % n;
-    T x;
-    if (xin) {
-      const int ix = int(node % n1), iy = int(node / n1);
-      const T* X = xin + col * n;
-      x = fma(wd, b[q] - stencil_apply(X, ix, iy, n1, d, e, c), X[node]);
-    } else {
-      x = wd * b[q];
-    }
-    if (acc) {
-      const int64_t t = col / acc_L, cc = col % acc_L;
-      acc[t * acc_ss + (acc_col0 + cc) * n + node] += x;
-    } else {
-      xout[q] = x;
-    }
+__device__ __forceinline__ T tile_stencil(const T (*Xs)[130], int r, int xx, T d, T e, T c) {
+  const T C = Xs[r + 1][xx];
+  const T edges = (Xs[r + 2][xx] + Xs[r][xx]) + (Xs[r + 1][xx + 1] + Xs[r + 1][xx - 1]);
+  const T corners = (Xs[r + 2][xx + 1] + Xs[r + 2][xx - 1]) + (Xs[r][xx + 1] + Xs[r][xx - 1]);
+  return fma(d, C, fma(e, edges, c * corners));
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_tile(T (*Xs)[130], const T* __restrict__ X, int n1, int x0, int y0) {
+  constexpr int TW = 130, TH = kMassRows + 2;
+  for (int q = threadIdx.x; q < TH * TW; q += 128) {
+    const int r = q / TW, xx = q - r * TW;
+    const int gy = y0 - 1 + r, gx = x0 - 1 + xx;
+    Xs[r][xx] = (gy >= 0 && gy < n1 && gx >= 0 && gx < n1) ? X[int64_t(gy) * n1 + gx] : T(0);
   }
 }
 
 template <typename T>
-__global__ void residual_kernel(const T* __restrict__ b, const T* __restrict__ x, T* r, int64_t B, int n1, T d, T e, T c) {
+__global__ void __launch_bounds__(128) smooth_kernel(const T* __restrict__ b, const T* __restrict__ xin, T* xout,
+                                                     int n1, T d, T e, T c, T omega, T* acc, int64_t acc_ss,
+                                                     int acc_L, int acc_col0, int strips, int64_t nwork) {
   pdl_enter();
+  __shared__ T Xs[kMassRows + 2][130];
   const int64_t n = int64_t(n1) * n1;
-  const int64_t total = B * n;
-  for (int64_t q = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; q < total; q += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t col = q / n, node = q % n;
-    const int ix = int(node % n1), iy = int(node / n1);
-    r[q] = b[q] - stencil_apply(x + col * n, ix, iy, n1, d, e, c);
+  const T wd = omega / d;
+  const int tid = threadIdx.x, x0 = blockIdx.x * 128, ix = x0 + tid;
+  for (int64_t w = blockIdx.y; w < nwork; w += gridDim.y) {
+    const int strip = int(w % strips);
+    const int64_t col = w / strips;
+    const int y0 = strip * kMassRows, ny = min(kMassRows, n1 - y0);
+    if (xin) {
+      stage_tile(Xs, xin + col * n, n1, x0, y0);
+      __syncthreads();
+    }
+    if (ix < n1) {
+      const T* bc = b + col * n;
+      T* dst = acc ? acc + (col / acc_L) * acc_ss + (acc_col0 + col % acc_L) * n : xout + col * n;
+      for (int r = 0; r < ny; ++r) {
+        const int64_t node = int64_t(y0 + r) * n1 + ix;
+        const T x = xin ? fma(wd, bc[node] - tile_stencil(Xs, r, tid + 1, d, e, c), Xs[r + 1][tid + 1]) : wd * bc[node];
+        if (acc) dst[node] += x;
+        else dst[node] = x;
+      }
+    }
+    if (xin) __syncthreads();                        // the tile is rewritten by the next work item
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) residual_kernel(const T* __restrict__ b, const T* __restrict__ x, T* r, int n1,
+                                                       T d, T e, T c, int strips, int64_t nwork) {
+  pdl_enter();
+  __shared__ T Xs[kMassRows + 2][130];
+  const int64_t n = int64_t(n1) * n1;
+  const int tid = threadIdx.x, x0 = blockIdx.x * 128, ix = x0 + tid;
+  for (int64_t w = blockIdx.y; w < nwork; w += gridDim.y) {
+    const int strip = int(w % strips);
+    const int64_t col = w / strips;
+    const int y0 = strip * kMassRows, ny = min(kMassRows, n1 - y0);
+    stage_tile(Xs, x + col * n, n1, x0, y0);
+    __syncthreads();
+    if (ix < n1)
+      for (int rr = 0; rr < ny; ++rr) {
+        const int64_t node = col * n + int64_t(y0 + rr) * n1 + ix;
+        r[node] = b[node] - tile_stencil(Xs, rr, tid + 1, d, e, c);
+      }
+    __syncthreads();
   }
 }
 
@@ -1406,9 +1443,12 @@ cudaError_t launch_smooth(const T* b, const T* xin, T* xout, int64_t B, int n1, 
   if (total == 0) return cudaSuccess;
   ProfScope ps(KK_SMOOTH, st, double(sizeof(T)) * total * (xin ? 3 : 2) + (acc ? double(sizeof(T)) * total : 0.0),
                double(total) * (xin ? 21.0 : 1.0));
+  const int strips = (n1 + kMassRows - 1) / kMassRows;
+  const int64_t nwork = int64_t(strips) * B;
   {
-    const cudaError_t le_ = launch_pdl(smooth_kernel<T>, dim3(grid_for(total, 256)), dim3(256), size_t(0), st,
-                                      b, xin, xout, B, n1, T(s.diag), T(s.edge), T(s.corner), omega, acc, acc_ss, acc_L, acc_col0);
+    const cudaError_t le_ = launch_pdl(smooth_kernel<T>, dim3(unsigned((n1 + 127) / 128), unsigned(nwork < 65535 ? nwork : 65535)),
+                                      dim3(128), size_t(0), st, b, xin, xout, n1, T(s.diag), T(s.edge), T(s.corner),
+                                      omega, acc, acc_ss, acc_L, acc_col0, strips, nwork);
     if (le_ != cudaSuccess) return le_;
   }
   note_launch();
@@ -1420,9 +1460,12 @@ cudaError_t launch_residual(const T* b, const T* x, T* r, int64_t B, int n1, Ste
   const int64_t total = B * int64_t(n1) * n1;
   if (total == 0) return cudaSuccess;
   ProfScope ps(KK_RESIDUAL, st, double(sizeof(T)) * total * 3, double(total) * 18.0);
+  const int strips = (n1 + kMassRows - 1) / kMassRows;
+  const int64_t nwork = int64_t(strips) * B;
   {
-    const cudaError_t le_ = launch_pdl(residual_kernel<T>, dim3(grid_for(total, 256)), dim3(256), size_t(0), st,
-                                      b, x, r, B, n1, T(s.diag), T(s.edge), T(s.corner));
+    const cudaError_t le_ = launch_pdl(residual_kernel<T>, dim3(unsigned((n1 + 127) / 128), unsigned(nwork < 65535 ? nwork : 65535)),
+                                      dim3(128), size_t(0), st, b, x, r, n1, T(s.diag), T(s.edge), T(s.corner),
+                                      strips, nwork);
     if (le_ != cudaSuccess) return le_;
   }
   note_launch();

@@ -266,6 +266,27 @@ def test_solve_is_deterministic():
     assert torch.equal(xa, xb)
 
 
+@pytest.mark.parametrize("nx,dtype,tol", [(256, torch.float64, 1e-11), (512, torch.float32, 2e-5)])
+def test_vcycle_levelwise_fine_levels(nx, dtype, tol):
+    """Grids above the fused and cluster V-cycles: the fine levels run as grid-wide passes
+    (float64 255 x 255 over a cluster cycle from 127 x 127; float32 511 x 511 over 255 x 255).
+    float64 tolerance 1e-11: eight levels of summation-order differences, amplified by the mean
+    operator's condition number (about 4e4 at 255 x 255), against 1e-12 on the grids of at most
+    127 x 127 above."""
+    pr = si.random_small(83 + nx, nx=nx, M=2, p=1)
+    d = SGData(pr)
+    sp = SGProblem.from_problem(pr, precision="fp64" if dtype == torch.float64 else "mixed")
+    Pc = BlockPreconditioner(d)
+    ncols = 2
+    B = si.random_panel(84, d.n, ncols)
+    if dtype == torch.float32:
+        B = B.astype(np.float32).astype(np.float64)
+    X = host(sp.apply_vcycle(dev(B, dtype), ncols))
+    V = VCycle(Pc.A0, pr.nx, pr.nu_pre, pr.nu_post, pr.omega)
+    ref = V.apply(B.reshape(ncols, d.n).T).T.reshape(-1)
+    assert rel(X, ref) <= tol
+
+
 @pytest.mark.parametrize("nx,ncols", [(64, 3), (128, 3), (128, 56), (256, 3)])
 def test_vcycle_fp32_cluster_and_single(nx, ncols):
     """float32 V-cycle against the float64 oracle cycle (float32 rounding over ~50
