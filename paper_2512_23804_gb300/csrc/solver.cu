@@ -9,6 +9,7 @@
 #include <iterator>
 #include <map>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -1262,14 +1263,21 @@ sgoc_status sgoc_solve_batch(int32_t count, sgoc_problem* const* pbs, void* cons
                                    static_cast<cudaStream_t>(streams[i]));
     if (s != SGOC_OK) tasks[i].fail(s);
   }
-  // round robin: while one solve's unit runs, the others' units are already queued
+  // advance each solve as soon as its pending unit has completed (polling, so that no solve
+  // waits behind another); yield the host thread while none is ready
   for (bool busy = true; busy;) {
     busy = false;
+    bool progressed = false;
     for (auto& t : tasks) {
       if (t.phase == SolveTask::DONE) continue;
-      t.wait_and_step();
+      const cudaError_t q = cudaEventQuery(t.rt->ev);
+      if (q != cudaErrorNotReady) {               // completed, or an error wait_and_step reports
+        t.wait_and_step();
+        progressed = true;
+      }
       busy = busy || t.phase != SolveTask::DONE;
     }
+    if (busy && !progressed) std::this_thread::yield();
   }
   sgoc_status first = SGOC_OK;
   for (int i = 0; i < count; ++i) {
