@@ -1692,6 +1692,291 @@ __device__ __forceinline__ void vt_strip(const T* __restrict__ xs, T* __restrict
   }
 }
 
+// whether the V-cycle folds each level's prolongation into its first post-smoothing sweep
+template <typename T>
+constexpr bool kVtFuseProlong = std::is_same<T, float>::value;
+
+// Level-0 post-smoothing sweep with two passes folded in.  PRO: every value
+// read is first corrected by the prolonged coarse result xc (a quarter of the
+// sum of the four nearest coarse values, exactly as vt_prolong forms it), so the
+// prolongation needs no pass of its own: the corrected iterate is read only by
+// the first post-smoothing sweep.  OUT: the swept values go to the global column
+// gout (stored, or added when acc) instead of xd, replacing the final copy-out.
+// The window's fine rows are g.y0 + w (1-based, w = 0 .. rows + 1); g.y0 is even
+// (strips of kStripRows rows, or one strip from row 0), so row w reads coarse
+// rows g.y0/2 + floor(w/2) and g.y0/2 + ceil(w/2).
+template <typename T, int N1, bool PRO, bool OUT>
+__device__ __forceinline__ void vt_strip_post(const T* __restrict__ xs, T* __restrict__ xd, const T* __restrict__ xc,
+                                             T* __restrict__ gout, bool acc, const T (&bv)[kStripRows],
+                                             const Strip& g, T d, T e, T c, T wd) {
+  static_assert(kStripRows % 2 == 0, "strips must start on even rows");
+  constexpr int S = N1 + 2, SC = (N1 - 1) / 2 + 2;
+  if (g.x < 0) return;
+  const int cr = g.y1 - g.y0;
+  // window columns are the 1-based fine columns g.x, g.x+1, g.x+2; their coarse
+  // columns lie in lo .. lo+2 (lo+2 only for odd g.x, where it is at most SC-1)
+  const int lo = g.x >> 1;
+  const bool odd = g.x & 1;
+  const T* cp = xc + (g.y0 >> 1) * SC + lo;
+  T s0[3] = {T(0), T(0), T(0)};
+  // pair sums r[c0] + r[c1] of coarse row i (relative) for the three window columns
+  auto csum = [&](int i, T (&s)[3]) {
+    const T* q = cp + i * SC;
+    const T v0 = q[0], v1 = q[1], v2 = odd ? q[2] : T(0);
+    const T m0 = odd ? v1 : v0;
+    s[0] = v0 + m0;
+    s[1] = m0 + v1;
+    s[2] = v1 + (odd ? v2 : v1);
+  };
+  auto wrow = [&](int w, T& m, T& cc, T& pp) {
+    const T* pr = xs + (g.y0 + w) * S + g.x;
+    m = pr[0]; cc = pr[1]; pp = pr[2];
+    if (PRO) {
+      T k[3];
+      if (w & 1) {
+        T s1[3];
+        csum((w + 1) >> 1, s1);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) { k[q] = T(0.25) * (s0[q] + s1[q]); s0[q] = s1[q]; }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) k[q] = T(0.25) * (s0[q] + s0[q]);
+      }
+      m += k[0]; cc += k[1]; pp += k[2];
+    }
+  };
+  T* q = xd + (g.y0 + 1) * S + g.x + 1;
+  T* go = gout + g.y0 * N1 + g.x;
+  // the accumulator's values are all requested before the sweep, not one latency a row
+  T ga[kStripRows];
+#pragma unroll
+  for (int j = 0; j < kStripRows; ++j) ga[j] = (OUT && acc && j < cr) ? go[j * N1] : T(0);
+  if (PRO) csum(0, s0);
+  T wm0, wc0, wp0, wm1, wc1, wp1;
+  wrow(0, wm0, wc0, wp0);
+  wrow(1, wm1, wc1, wp1);
+#pragma unroll
+  for (int j = 0; j < kStripRows; ++j) {
+    if (j < cr) {
+      T wm2, wc2, wp2;
+      wrow(j + 2, wm2, wc2, wp2);
+      const T edges = (wc0 + wc2) + (wm1 + wp1);
+      const T corners = (wm0 + wp0) + (wm2 + wp2);
+      const T r = bv[j] - fma(d, wc1, fma(e, edges, c * corners));
+      const T o = fma(wd, r, wc1);
+      if (!OUT) q[j * S] = o;
+      else go[j * N1] = acc ? ga[j] + o : o;
+      wm0 = wm1; wc0 = wc1; wp0 = wp1;
+      wm1 = wm2; wc1 = wc2; wp1 = wp2;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The smallest levels (n1 <= 7) in one warp's registers: lane x holds grid
+// column x (rows 0 .. N-1 in an array), lanes >= N hold zeros; horizontal
+// neighbours come by shuffles, vertical ones from the lane's own array.  Every
+// value is formed by the same operations in the same order as vt_pass,
+// vt_restrict and vt_prolong (borders read as zero there and here).
+// ---------------------------------------------------------------------------
+constexpr unsigned kFullMask = 0xffffffffu;
+
+// left and right neighbours of a lane's value (zero beyond the grid: lane 0 has
+// no left neighbour, and lane N, the right neighbour of the last column, holds zero)
+template <typename T>
+__device__ __forceinline__ T wl_left(T u, int lane) {
+  const T s = __shfl_up_sync(kFullMask, u, 1);
+  return lane == 0 ? T(0) : s;
+}
+template <typename T>
+__device__ __forceinline__ T wl_right(T u) { return __shfl_down_sync(kFullMask, u, 1); }
+
+// 0 jacobi (x from xs), 1 double sweep from zero (on b), 2 residual; xd must not alias the
+// array read (xs, or b for MODE 1).  The side values of rows y-1, y, y+1 slide down the column.
+template <typename T, int N, int MODE>
+__device__ __forceinline__ void wl_pass(const T (&xs)[N], const T (&b)[N], T (&xd)[N], int lane, T d, T e, T c,
+                                        T wd) {
+  const T(&v)[N] = MODE == 1 ? b : xs;
+  T lm = T(0), rm = T(0);
+  T l0 = wl_left(v[0], lane), r0 = wl_right(v[0]);
+#pragma unroll
+  for (int y = 0; y < N; ++y) {
+    T l1 = T(0), r1 = T(0);
+    if (y + 1 < N) { l1 = wl_left(v[y + 1], lane); r1 = wl_right(v[y + 1]); }
+    const T up = y > 0 ? v[y - 1] : T(0), dn = y + 1 < N ? v[y + 1] : T(0);
+    const T edges = (up + dn) + (l0 + r0);
+    const T corners = (lm + rm) + (l1 + r1);
+    const T av = fma(d, v[y], fma(e, edges, c * corners));
+    T o;
+    if (MODE == 1) o = wd * fma(T(2), b[y], -wd * av);
+    else if (MODE == 2) o = b[y] - av;
+    else o = fma(wd, b[y] - av, xs[y]);
+    xd[y] = lane < N ? o : T(0);
+    lm = l0; rm = r0; l0 = l1; r0 = r1;
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void wl_restrict(const T (&rv)[N], T (&bc)[(N - 1) / 2], int lane) {
+  constexpr int NC = (N - 1) / 2;
+  T lm = wl_left(rv[0], lane), rm = wl_right(rv[0]);
+#pragma unroll
+  for (int J = 0; J < NC; ++J) {
+    const int y = 2 * J + 1;
+    const T l0 = wl_left(rv[y], lane), r0 = wl_right(rv[y]);
+    const T l1 = wl_left(rv[y + 1], lane), r1 = wl_right(rv[y + 1]);
+    const T cen = rv[y];
+    const T edg = (rv[y + 1] + rv[y - 1]) + (r0 + l0);
+    const T cor = (r1 + l1) + (rm + lm);
+    const T val = cen + T(0.5) * edg + T(0.25) * cor;
+    const T got = __shfl_sync(kFullMask, val, (2 * lane + 1) & 31);  // coarse column I = lane from fine 2I+1
+    bc[J] = lane < NC ? got : T(0);
+    lm = l1; rm = r1;
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void wl_prolong(const T (&xc)[(N - 1) / 2], T (&xf)[N], int lane) {
+  constexpr int NC = (N - 1) / 2;
+  // fine column lane (1-based lane+1) reads coarse padded columns (lane+1)>>1 and (lane+2)>>1,
+  // i.e. coarse lanes ((lane+1)>>1) - 1 and ((lane+2)>>1) - 1; padded column 0 is the zero border
+  const int c0 = (lane + 1) >> 1, c1 = (lane + 2) >> 1;
+  T A[NC], B[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    const T a = __shfl_sync(kFullMask, xc[q], (c0 + 31) & 31);
+    const T bq = __shfl_sync(kFullMask, xc[q], (c1 + 31) & 31);
+    A[q] = c0 == 0 ? T(0) : a;
+    B[q] = c1 == 0 ? T(0) : bq;                       // coarse lanes >= NC hold zeros
+  }
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const int q0 = (j + 1) >> 1, q1 = (j + 2) >> 1;   // padded coarse rows; 0 and NC+1 are borders
+    const T a0 = q0 >= 1 && q0 <= NC ? A[q0 - 1] : T(0), b0 = q0 >= 1 && q0 <= NC ? B[q0 - 1] : T(0);
+    const T a1 = q1 >= 1 && q1 <= NC ? A[q1 - 1] : T(0), b1 = q1 >= 1 && q1 <= NC ? B[q1 - 1] : T(0);
+    const T v = xf[j] + T(0.25) * ((a0 + b0) + (a1 + b1));
+    xf[j] = lane < N ? v : T(0);
+  }
+}
+
+// V(nu, nu) cycle on the warp-resident levels from an N x N level down to one node
+template <typename T, int N>
+__device__ __forceinline__ void wl_cycle(const T (&b)[N], T (&x)[N], const VFLevel<T>* lv, int L, int nu,
+                                         int lane) {
+  const T d = lv[L].d, e = lv[L].e, c = lv[L].c, wd = lv[L].wd;
+  if constexpr (N == 1) {
+    x[0] = lane == 0 ? b[0] / d : T(0);
+  } else {
+    constexpr int NC = (N - 1) / 2;
+    T t[N];
+    if (nu == 2) {
+      wl_pass<T, N, 1>(x, b, x, lane, d, e, c, wd);
+    } else {
+#pragma unroll
+      for (int y = 0; y < N; ++y) x[y] = T(0);
+      for (int sw = 0; sw < nu; ++sw) {
+        wl_pass<T, N, 0>(x, b, t, lane, d, e, c, wd);
+#pragma unroll
+        for (int y = 0; y < N; ++y) x[y] = t[y];
+      }
+    }
+    wl_pass<T, N, 2>(x, b, t, lane, d, e, c, wd);
+    T bc[NC], xc[NC];
+    wl_restrict<T, N>(t, bc, lane);
+    wl_cycle<T, NC>(bc, xc, lv, L + 1, nu, lane);
+    wl_prolong<T, N>(xc, x, lane);
+    for (int sw = 0; sw < nu; ++sw) {
+      wl_pass<T, N, 0>(x, b, t, lane, d, e, c, wd);
+#pragma unroll
+      for (int y = 0; y < N; ++y) x[y] = t[y];
+    }
+  }
+}
+
+// Coarse-level strip pass: thread t owns grid column t % N over R rows from row
+// (t / N) R and slides a 3 x 3 window down it (three loads a row instead of nine
+// a node).  MODE 0 jacobi, 1 double sweep from zero (window on b), 2 residual;
+// PRO (MODE 0) adds the prolonged coarse result xc to every value read, as
+// vt_strip_post.  The operations and their order are those of vt_pass.
+template <int N, int NT>
+struct CStrip {
+  static constexpr int chunks = NT / N;
+  static constexpr int R0 = chunks > 0 ? (N + chunks - 1) / chunks : N;
+  static constexpr int R = R0 + (R0 & 1);                  // even: strips start on even rows
+  static constexpr bool use = N >= 15 && chunks >= 2 && (N + R - 1) / R <= chunks;
+};
+
+template <typename T, int N, int NT, int MODE, bool PRO>
+__device__ __forceinline__ void vt_cstrip(const T* __restrict__ xs, T* __restrict__ xd, const T* __restrict__ b,
+                                          const T* __restrict__ xc, T d, T e, T c, T wd) {
+  constexpr int R = CStrip<N, NT>::R, S = N + 2, SC = (N - 1) / 2 + 2;
+  const int t = threadIdx.x;
+  const int x = t % N, y0 = (t / N) * R;
+  if (y0 >= N) return;
+  const int ny = min(R, N - y0);
+  const T* v = MODE == 1 ? b : xs;
+  const int lo = x >> 1;
+  const bool odd = x & 1;
+  const T* cp = xc + (y0 >> 1) * SC + lo;
+  T s0[3] = {T(0), T(0), T(0)};
+  auto csum = [&](int i, T (&sv)[3]) {
+    const T* q = cp + i * SC;
+    const T v0 = q[0], v1 = q[1], v2 = odd ? q[2] : T(0);
+    const T m0 = odd ? v1 : v0;
+    sv[0] = v0 + m0;
+    sv[1] = m0 + v1;
+    sv[2] = v1 + (odd ? v2 : v1);
+  };
+  auto wrow = [&](int w, T& m, T& cc, T& pp) {
+    const T* pr = v + (y0 + w) * S + x;
+    m = pr[0]; cc = pr[1]; pp = pr[2];
+    if (PRO) {
+      T k[3];
+      if (w & 1) {
+        T s1[3];
+        csum((w + 1) >> 1, s1);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) { k[q] = T(0.25) * (s0[q] + s1[q]); s0[q] = s1[q]; }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) k[q] = T(0.25) * (s0[q] + s0[q]);
+      }
+      m += k[0]; cc += k[1]; pp += k[2];
+    }
+  };
+  if (PRO) csum(0, s0);
+  T wm0, wc0, wp0, wm1, wc1, wp1;
+  wrow(0, wm0, wc0, wp0);
+  wrow(1, wm1, wc1, wp1);
+  T* q = xd + (y0 + 1) * S + x + 1;
+  const T* bq = b + (y0 + 1) * S + x + 1;
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    if (j < ny) {
+      T wm2, wc2, wp2;
+      wrow(j + 2, wm2, wc2, wp2);
+      const T edges = (wc0 + wc2) + (wm1 + wp1);
+      const T corners = (wm0 + wp0) + (wm2 + wp2);
+      const T av = fma(d, wc1, fma(e, edges, c * corners));
+      T o;
+      if (MODE == 1) o = wd * fma(T(2), wc1, -wd * av);
+      else if (MODE == 2) o = bq[j * S] - av;
+      else o = fma(wd, bq[j * S] - av, wc1);
+      q[j * S] = o;
+      wm0 = wm1; wc0 = wc1; wp0 = wp1;
+      wm1 = wm2; wc1 = wc2; wp1 = wp2;
+    }
+  }
+}
+
+// a pass of coarse level N on NT threads: the strip form where it applies
+template <typename T, int N, int NT, int MODE>
+__device__ __forceinline__ void vt_level_pass(const T* __restrict__ xs, T* __restrict__ xd, const T* __restrict__ b,
+                                              T d, T e, T c, T wd) {
+  if constexpr (CStrip<N, NT>::use) vt_cstrip<T, N, NT, MODE, false>(xs, xd, b, b, d, e, c, wd);
+  else vt_pass<T, N, NT, MODE>(xs, xd, b, d, e, c, wd);
+}
+
 // One level of the cycle (coarse levels L >= 1): pre-smoothing, residual, restriction,
 // the coarser levels, prolongation, post-smoothing.  Returns the buffer holding x.
 template <typename T, int N1, int L>
@@ -1703,27 +1988,41 @@ __device__ int vt_coarse(T* base, const VFLevel<T>* lv, int nu) {
   T* xb = xa + G::np(L);
   T* bl = xb + G::np(L);
   const T d = lv[L].d, e = lv[L].e, c = lv[L].c, wd = lv[L].wd;
-  if constexpr (N == 1) {
+  if constexpr (N <= 7 && NT == 32) {
+    // this level and all below it in the registers of the one warp that runs them
+    constexpr int S = N + 2;
+    const int lane = threadIdx.x & 31;
+    T b[N], x[N];
+#pragma unroll
+    for (int y = 0; y < N; ++y) b[y] = lane < N ? bl[(y + 1) * S + lane + 1] : T(0);
+    wl_cycle<T, N>(b, x, lv, L, nu, lane);
+#pragma unroll
+    for (int y = 0; y < N; ++y)
+      if (lane < N) xa[(y + 1) * S + lane + 1] = x[y];
+    __syncwarp();
+    return 0;
+  } else if constexpr (N == 1) {
     if (threadIdx.x == 0) xa[4] = bl[4] / d;
     vt_sync<NT>();
     return 0;
   } else {
     int cur = 0;
     if (nu == 2) {
-      vt_pass<T, N, NT, 1>(xa, xa, bl, d, e, c, wd);
+      vt_level_pass<T, N, NT, 1>(xb, xa, bl, d, e, c, wd);
       vt_sync<NT>();
     } else {
       for (int q = threadIdx.x; q < G::np(L); q += NT) xa[q] = T(0);
       vt_sync<NT>();
       for (int sw = 0; sw < nu; ++sw) {
-        if (cur == 0) vt_pass<T, N, NT, 0>(xa, xb, bl, d, e, c, wd); else vt_pass<T, N, NT, 0>(xb, xa, bl, d, e, c, wd);
+        if (cur == 0) vt_level_pass<T, N, NT, 0>(xa, xb, bl, d, e, c, wd);
+        else vt_level_pass<T, N, NT, 0>(xb, xa, bl, d, e, c, wd);
         cur ^= 1;
         vt_sync<NT>();
       }
     }
     T* xcur = cur == 0 ? xa : xb;
     T* rbuf = cur == 0 ? xb : xa;
-    vt_pass<T, N, NT, 2>(xcur, rbuf, bl, d, e, c, wd);
+    vt_level_pass<T, N, NT, 2>(xcur, rbuf, bl, d, e, c, wd);
     vt_sync<NT>();
     T* bc = base + G::off(L + 1) + 2 * G::np(L + 1);
     vt_restrict<T, N, NT>(rbuf, bc);
@@ -1736,10 +2035,23 @@ __device__ int vt_coarse(T* base, const VFLevel<T>* lv, int nu) {
     if (threadIdx.x == 0) cbuf = ccur;
     vt_sync<NT>();
     const T* xc = base + G::off(L + 1) + (cbuf == 0 ? 0 : G::np(L + 1));
-    vt_prolong<T, N, NT>(xc, xcur);
-    vt_sync<NT>();
-    for (int sw = 0; sw < nu; ++sw) {
-      if (cur == 0) vt_pass<T, N, NT, 0>(xa, xb, bl, d, e, c, wd); else vt_pass<T, N, NT, 0>(xb, xa, bl, d, e, c, wd);
+    int sw0 = 0;
+    if constexpr (CStrip<N, NT>::use && kVtFuseProlong<T>) {
+      if (nu >= 1) {                                 // prolongation folded into the first sweep
+        if (cur == 0) vt_cstrip<T, N, NT, 0, true>(xa, xb, bl, xc, d, e, c, wd);
+        else vt_cstrip<T, N, NT, 0, true>(xb, xa, bl, xc, d, e, c, wd);
+        cur ^= 1;
+        vt_sync<NT>();
+        sw0 = 1;
+      }
+    }
+    if (sw0 == 0) {
+      vt_prolong<T, N, NT>(xc, xcur);
+      vt_sync<NT>();
+    }
+    for (int sw = sw0; sw < nu; ++sw) {
+      if (cur == 0) vt_level_pass<T, N, NT, 0>(xa, xb, bl, d, e, c, wd);
+      else vt_level_pass<T, N, NT, 0>(xb, xa, bl, d, e, c, wd);
       cur ^= 1;
       vt_sync<NT>();
     }
@@ -1767,6 +2079,11 @@ struct VtLevel0 {
   template <int MODE>
   __device__ __forceinline__ void pass(const T* __restrict__ xs, T* __restrict__ xd, T d, T e, T c, T wd) const {
     vt_strip<T, N1 + 2, MODE>(xs, xd, bv, g, d, e, c, wd);
+  }
+  template <bool PRO, bool OUT>
+  __device__ __forceinline__ void post(const T* __restrict__ xs, T* __restrict__ xd, const T* __restrict__ xc,
+                                       T* __restrict__ gout, bool acc, T d, T e, T c, T wd) const {
+    vt_strip_post<T, N1, PRO, OUT>(xs, xd, xc, gout, acc, bv, g, d, e, c, wd);
   }
   __device__ __forceinline__ T first_b() const { return bv[0]; }
 };
@@ -1832,6 +2149,86 @@ struct VtLevel0<float, N1, true> {
       }
     }
   }
+  // post-smoothing sweep with the prolongation (PRO) or the copy-out (OUT) folded
+  // in, as vt_strip_post.  Window columns (a, b, c, d) are the 1-based fine columns
+  // x0 .. x0+3 (x0 even): their coarse column pairs are (A,A), (A,B), (B,B), (B,C)
+  // with A = x0/2; window row w is fine row y0 + w (y0 even).
+  template <bool PRO, bool OUT>
+  __device__ __forceinline__ void post(const float* __restrict__ xs, float* __restrict__ xd,
+                                       const float* __restrict__ xc, float* __restrict__ gout, bool acc, float d,
+                                       float e, float c, float wd) const {
+    if (ny <= 0) return;
+    constexpr int SC = (N1 - 1) / 2 + 2;
+    const float* p = xs + y0 * S + x0;
+    const float* cp = xc + (y0 / 2) * SC + x0 / 2;
+    const float2 q4 = make_float2(0.25f, 0.25f);
+    float2 s01 = make_float2(0.f, 0.f), s23 = s01;     // pair sums of the last coarse row read
+    auto csum = [&](int i, float2& u01, float2& u23) {
+      const float* r = cp + i * SC;
+      const float A = r[0], B = r[1], C = v1 ? r[2] : 0.f;
+      u01 = __fadd2_rn(make_float2(A, A), make_float2(A, B));
+      u23 = __fadd2_rn(make_float2(B, B), make_float2(B, C));
+    };
+    auto wrow = [&](int w, float& wa, float& wb, float& wc, float& wdn) {
+      const float* pr = p + w * S;
+      wa = pr[0]; wb = pr[1]; wc = pr[2]; wdn = v1 ? pr[3] : 0.f;
+      if (PRO) {
+        float2 k01, k23;
+        if (w & 1) {
+          float2 n01, n23;
+          csum((w + 1) >> 1, n01, n23);
+          k01 = __fmul2_rn(q4, __fadd2_rn(s01, n01));
+          k23 = __fmul2_rn(q4, __fadd2_rn(s23, n23));
+          s01 = n01; s23 = n23;
+        } else {
+          k01 = __fmul2_rn(q4, __fadd2_rn(s01, s01));
+          k23 = __fmul2_rn(q4, __fadd2_rn(s23, s23));
+        }
+        const float2 ab = __fadd2_rn(make_float2(wa, wb), k01);
+        const float2 cd = __fadd2_rn(make_float2(wc, wdn), k23);
+        wa = ab.x; wb = ab.y; wc = cd.x; wdn = v1 ? cd.y : 0.f;
+      }
+    };
+    float* q = xd + (y0 + 1) * S + x0 + 1;
+    float* go = gout + y0 * N1 + x0;
+    // the accumulator's values are all requested before the sweep, not one latency a row
+    float2 ga[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      ga[j] = (OUT && acc && j < ny) ? make_float2(go[j * N1], v1 ? go[j * N1 + 1] : 0.f) : make_float2(0.f, 0.f);
+    if (PRO) csum(0, s01, s23);
+    float a0, b0, c0, d0, a1, b1, c1, d1;
+    wrow(0, a0, b0, c0, d0);
+    wrow(1, a1, b1, c1, d1);
+    const float2 dd = make_float2(d, d), ee = make_float2(e, e), cc = make_float2(c, c);
+    const float2 ww = make_float2(wd, wd), m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      if (j < ny) {
+        float a2, b2, c2, d2;
+        wrow(j + 2, a2, b2, c2, d2);
+        const float2 C = make_float2(b1, c1);
+        const float2 edges = __fadd2_rn(__fadd2_rn(make_float2(b0, c0), make_float2(b2, c2)),
+                                        __fadd2_rn(make_float2(a1, b1), make_float2(c1, d1)));
+        const float2 corners = __fadd2_rn(__fadd2_rn(make_float2(a0, b0), make_float2(c0, d0)),
+                                          __fadd2_rn(make_float2(a2, b2), make_float2(c2, d2)));
+        const float2 av = __ffma2_rn(dd, C, __ffma2_rn(ee, edges, __fmul2_rn(cc, corners)));
+        const float2 o = __ffma2_rn(ww, __ffma2_rn(m1, av, bv[j]), C);
+        if (!OUT) {
+          q[j * S] = o.x;
+          if (v1) q[j * S + 1] = o.y;
+        } else if (acc) {
+          go[j * N1] = ga[j].x + o.x;
+          if (v1) go[j * N1 + 1] = ga[j].y + o.y;
+        } else {
+          go[j * N1] = o.x;
+          if (v1) go[j * N1 + 1] = o.y;
+        }
+        a0 = a1; b0 = b1; c0 = c1; d0 = d1;
+        a1 = a2; b1 = b2; c1 = c2; d1 = d2;
+      }
+    }
+  }
   __device__ __forceinline__ float first_b() const { return bv[0].x; }
 };
 
@@ -1847,6 +2244,9 @@ __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 :
   T* base = reinterpret_cast<T*>(vt_smem_raw);
   const int64_t col = blockIdx.x;
   constexpr int n0 = N1 * N1;
+  // the column's output: x itself, or the accumulator column x is added to
+  const bool acc_on = acc != nullptr;
+  T* gout = acc_on ? acc + (col / acc_L) * acc_ss + (acc_col0 + col % acc_L) * int64_t(n0) : xg + col * n0;
   if (threadIdx.x < NL) {
     const int l = threadIdx.x;
     lv[l].d = T(L.diag[l]); lv[l].e = T(L.edge[l]); lv[l].c = T(L.corner[l]);
@@ -1903,17 +2303,35 @@ __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 :
       __shared__ int cbuf0;
       if (threadIdx.x == 0) cbuf0 = ccur;
       vt_sync<NT0>();
-      vt_prolong<T, N1, NT0>(base + G::off(1) + (cbuf0 == 0 ? 0 : G::np(1)), xcur);
-      vt_sync<NT0>();
+      const T* xc = base + G::off(1) + (cbuf0 == 0 ? 0 : G::np(1));
       pdl_trigger();                                   // only the post-smoothing and the write remain
-      for (int sw = 0; sw < nu; ++sw) {
-        if (cur == 0) z.template pass<0>(xa, xb, d, e, c, wd); else z.template pass<0>(xb, xa, d, e, c, wd);
-        cur ^= 1;
+      // the copy-out is folded into the last sweep; in float32 the prolongation
+      // into the first (in float64 the extra window corrections cost more than the pass)
+      int sw0 = 0;
+      if constexpr (kVtFuseProlong<T>) {
+        if (nu >= 2) {
+          z.template post<true, false>(xa + cur * G::np(0), xa + (cur ^ 1) * G::np(0), xc, gout, acc_on, d, e, c, wd);
+          cur ^= 1;
+          vt_sync<NT0>();
+          sw0 = 1;
+        }
+      }
+      if (sw0 == 0) {
+        vt_prolong<T, N1, NT0>(xc, xcur);
         vt_sync<NT0>();
+      }
+      if (nu >= 1) {
+        for (int sw = sw0; sw + 1 < nu; ++sw) {
+          if (cur == 0) z.template pass<0>(xa, xb, d, e, c, wd); else z.template pass<0>(xb, xa, d, e, c, wd);
+          cur ^= 1;
+          vt_sync<NT0>();
+        }
+        z.template post<false, true>(xa + cur * G::np(0), xa + (cur ^ 1) * G::np(0), xc, gout, acc_on, d, e, c, wd);
       }
     } else {
       pdl_trigger();
     }
+    if (nu >= 1) return;                               // the last sweep wrote the column
     __syncthreads();
   }
   if constexpr (N1 == 1) pdl_trigger();
@@ -1922,14 +2340,12 @@ __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 :
   __syncthreads();
   const T* x0 = base + (cfin == 0 ? 0 : G::np(0));
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  if (acc) {
-    T* A = acc + (col / acc_L) * acc_ss + (acc_col0 + col % acc_L) * int64_t(n0);
+  if (acc_on) {
     for (int y = ty; y < N1; y += G::nb() / 32)
-      for (int x = tx; x < N1; x += 32) A[y * N1 + x] += x0[(y + 1) * S0 + x + 1];
+      for (int x = tx; x < N1; x += 32) gout[y * N1 + x] += x0[(y + 1) * S0 + x + 1];
   } else {
-    T* X = xg + col * n0;
     for (int y = ty; y < N1; y += G::nb() / 32)
-      for (int x = tx; x < N1; x += 32) X[y * N1 + x] = x0[(y + 1) * S0 + x + 1];
+      for (int x = tx; x < N1; x += 32) gout[y * N1 + x] = x0[(y + 1) * S0 + x + 1];
   }
 }
 
