@@ -1569,6 +1569,8 @@ struct VT {
   static constexpr int off(int l) { return l == 0 ? 0 : off(l - 1) + np(l - 1) * (l - 1 > 0 ? 3 : 2); }
   static constexpr int nlev() { return N1 == 1 ? 1 : 1 + VT<(N1 - 1) / 2>::nlev(); }
   static constexpr int total() { return off(nlev()); }
+  // threads of the border zeroing: one per position along a side, for every array
+  static constexpr int border_threads(int l = 0) { return l == nlev() ? 0 : s(l) * (l > 0 ? 3 : 2) + border_threads(l + 1); }
   // threads per CTA: 1024 for a 127 x 127 top level, 256 below (four columns per SM)
   static constexpr int nb() { return N1 >= 127 ? kVFThreads : 256; }
   static constexpr int grp0(int l) { return n1(l) >= 63 ? kVFThreads : (n1(l) >= 15 ? 256 : 32); }
@@ -2247,23 +2249,28 @@ __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 :
   // the column's output: x itself, or the accumulator column x is added to
   const bool acc_on = acc != nullptr;
   T* gout = acc_on ? acc + (col / acc_L) * acc_ss + (acc_col0 + col % acc_L) * int64_t(n0) : xg + col * n0;
-  if (threadIdx.x < NL) {
-    const int l = threadIdx.x;
+  // level constants, by the last warp (which has the least border work)
+  if (threadIdx.x >= G::nb() - 32 && threadIdx.x < G::nb() - 32 + NL) {
+    const int l = threadIdx.x - (G::nb() - 32);
     lv[l].d = T(L.diag[l]); lv[l].e = T(L.edge[l]); lv[l].c = T(L.corner[l]);
     lv[l].wd = omega / T(L.diag[l]);
   }
-  // zero borders of every array (interiors are always written before they are read)
+  // zero borders of every array (interiors are always written before they are read):
+  // border thread k of an s x s array zeroes position k of its four sides
+  for (int t0 = threadIdx.x; t0 < G::border_threads(); t0 += G::nb()) {
+    int t = t0;
 #pragma unroll
-  for (int l = 0; l < NL; ++l) {
-    const int n1 = G::n1(l), s = n1 + 2, per = 4 * (n1 + 1);
-    T* a = base + G::off(l);
-    const int narr = l > 0 ? 3 : 2;
-    for (int q = threadIdx.x; q < narr * per; q += G::nb()) {
-      const int arr = q / per, k = q - arr * per;
-      T* A = a + arr * s * s;
-      const int side = k / (n1 + 1), pos = k - side * (n1 + 1);
-      const int o = side == 0 ? pos : side == 1 ? (n1 + 1) * s + pos + 1 : side == 2 ? (pos + 1) * s : pos * s + n1 + 1;
-      A[o] = T(0);
+    for (int l = 0; l < NL; ++l) {
+      const int s = G::s(l), narr = l > 0 ? 3 : 2;
+      if (t >= 0 && t < narr * s) {
+        const int arr = t / s, k = t - arr * s;
+        T* A = base + G::off(l) + arr * s * s;
+        A[k] = T(0);
+        A[(s - 1) * s + k] = T(0);
+        A[k * s] = T(0);
+        A[k * s + s - 1] = T(0);
+      }
+      t -= narr * s;
     }
   }
   pdl_wait();                                        // b and the output are shared with earlier kernels
@@ -2766,8 +2773,18 @@ template <typename T>
 __global__ void __launch_bounds__(256) dot_kernel(const T* __restrict__ a, const T* __restrict__ b, int64_t n, double* partial) {
   pdl_enter();
   double s = 0.0;
-  for (int64_t i = blockIdx.x * int64_t(256) + threadIdx.x; i < n; i += int64_t(kDotBlocks) * 256)
-    s = fma(double(a[i]), double(b[i]), s);
+  const int64_t stride = int64_t(kDotBlocks) * 256;
+  int64_t i = blockIdx.x * int64_t(256) + threadIdx.x;
+  // four strides' loads in flight before their (in-order) accumulation
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    const T a0 = a[i], b0 = b[i], a1 = a[i + stride], b1 = b[i + stride];
+    const T a2 = a[i + 2 * stride], b2 = b[i + 2 * stride], a3 = a[i + 3 * stride], b3 = b[i + 3 * stride];
+    s = fma(double(a0), double(b0), s);
+    s = fma(double(a1), double(b1), s);
+    s = fma(double(a2), double(b2), s);
+    s = fma(double(a3), double(b3), s);
+  }
+  for (; i < n; i += stride) s = fma(double(a[i]), double(b[i]), s);
   s = block_sum<256>(s);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
@@ -2781,11 +2798,21 @@ __global__ void __launch_bounds__(256) dot4_kernel(const float4* __restrict__ a,
                                                    const float* __restrict__ bt, int tail, double* partial) {
   pdl_enter();
   double s = 0.0;
-  for (int64_t i = blockIdx.x * int64_t(256) + threadIdx.x; i < n4; i += int64_t(kDotBlocks) * 256) {
-    const float4 x = a[i], y = b[i];
-    const float p = fmaf(x.w, y.w, fmaf(x.z, y.z, fmaf(x.y, y.y, x.x * y.x)));
-    s += double(p);
+  const int64_t stride = int64_t(kDotBlocks) * 256;
+  auto prod = [](const float4& x, const float4& y) {
+    return fmaf(x.w, y.w, fmaf(x.z, y.z, fmaf(x.y, y.y, x.x * y.x)));
+  };
+  int64_t i = blockIdx.x * int64_t(256) + threadIdx.x;
+  // four strides' loads in flight before their (in-order) accumulation
+  for (; i + 3 * stride < n4; i += 4 * stride) {
+    const float4 x0 = a[i], y0 = b[i], x1 = a[i + stride], y1 = b[i + stride];
+    const float4 x2 = a[i + 2 * stride], y2 = b[i + 2 * stride], x3 = a[i + 3 * stride], y3 = b[i + 3 * stride];
+    s += double(prod(x0, y0));
+    s += double(prod(x1, y1));
+    s += double(prod(x2, y2));
+    s += double(prod(x3, y3));
   }
+  for (; i < n4; i += stride) s += double(prod(a[i], b[i]));
   if (blockIdx.x == 0 && threadIdx.x < tail) s = fma(double(at[threadIdx.x]), double(bt[threadIdx.x]), s);
   s = block_sum<256>(s);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;

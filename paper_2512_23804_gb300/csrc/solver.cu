@@ -283,9 +283,14 @@ static sgoc_status hgs(const sgoc_problem* pb, PrecWS<T>& w, const T* R, T* V, i
     const bool first = step <= p;
     const int d = first ? step : 2 * p - step;
     const int a0 = pb->off[d], L = pb->off[d + 1] - a0;
-    SGOC_LAUNCH(launch_sg<T>(first ? hgs_args_first<T>(pb, w, R, V, slabs, d) : hgs_args<T>(pb, w, R, V, slabs, d),
-                             st));
-    SGOC_TRY(vcycle<T>(pb, w, w.RH, nullptr, int64_t(slabs) * L, V, ps, L, a0, st));
+    // the first visit of level 0 has no couplings: its right-hand side is R_0 itself,
+    // which for one slab is a contiguous column the V-cycle reads in place
+    const T* rhs = w.RH;
+    if (first && d == 0 && slabs == 1) rhs = R;
+    else
+      SGOC_LAUNCH(launch_sg<T>(first ? hgs_args_first<T>(pb, w, R, V, slabs, d) : hgs_args<T>(pb, w, R, V, slabs, d),
+                               st));
+    SGOC_TRY(vcycle<T>(pb, w, rhs, nullptr, int64_t(slabs) * L, V, ps, L, a0, st));
   }
   return SGOC_OK;
 }
