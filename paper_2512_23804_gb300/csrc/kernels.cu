@@ -2872,6 +2872,8 @@ __global__ void minres_init_kernel(MinresState* s, const double* partial, double
   s->dot = vz;
   s->flag = 0;
   s->iter = 0;
+  s->wx_pending = 0;
+  s->w_q = s->w_m1 = s->w_m2 = s->x_w = 0.0;
   if (!(vz > 0.0)) { s->flag = (vz == vz) ? 3 : 4; s->beta = 1.0; s->beta1 = 1.0; s->est = 1.0; return; }
   s->beta = sqrt(vz);
   s->beta1 = s->beta;
@@ -2901,6 +2903,7 @@ __global__ void minres_rotate_kernel(MinresState* s, const double* partial) {
   const double vz = reduce_partials(partial);
   if (threadIdx.x != 0) return;
   s->dot = vz;
+  s->wx_pending = 0;
   if (!(vz == vz)) { s->flag = 4; return; }
   if (vz < 0.0) { s->flag = 3; return; }
   const double bn = sqrt(vz);
@@ -2924,6 +2927,7 @@ __global__ void minres_rotate_kernel(MinresState* s, const double* partial) {
   s->beta_prev = b;
   s->beta = bn;
   s->iter += 1;
+  s->wx_pending = 1;
   if (!(s->est == s->est)) s->flag = 4;
   else if (s->est <= s->target) s->flag = 1;
   else if (bn == 0.0) s->flag = 2;
@@ -2978,6 +2982,7 @@ __global__ void minres_wx_kernel(const T* __restrict__ z, const T* __restrict__ 
   pdl_enter();
   const T wq = T(s->w_q), w1 = T(s->w_m1), w2 = T(s->w_m2);
   const TX xw = TX(s->x_w);
+  if (!s->wx_pending) return;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     const T w = wq * z[i] - w1 * wm1[i] - w2 * wm2[i];
     wm2[i] = w;
@@ -3014,6 +3019,7 @@ __global__ void minres_wx4_kernel(const float4* __restrict__ z, const float4* __
                                   int tail, const MinresState* s) {
   pdl_enter();
   const float wq = float(s->w_q), w1 = float(s->w_m1), w2 = float(s->w_m2), xw = float(s->x_w);
+  if (!s->wx_pending) return;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n4; i += int64_t(gridDim.x) * blockDim.x) {
     const float4 a = z[i], b = wm1[i], c = wm2[i];
     float4 xv = x[i];

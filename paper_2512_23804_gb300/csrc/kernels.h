@@ -154,6 +154,7 @@ struct MinresState {
   double dot;                          // last reduced dot
   int flag;                            // 0 running, 1 est<=target, 2 breakdown(beta=0), 3 not SPD, 4 NaN
   int iter;
+  int wx_pending;                      // 1: the w/x update of the last rotation is still to be applied
 };
 cudaError_t launch_minres_init(MinresState* s, const double* partial, double target, cudaStream_t st);
 cudaError_t launch_minres_alpha(MinresState* s, const double* partial, cudaStream_t st);
@@ -162,6 +163,7 @@ cudaError_t launch_minres_rotate(MinresState* s, const double* partial, cudaStre
 template <typename T>
 cudaError_t launch_minres_v(const T* Kz, const T* v, T* vprev, int64_t n, const MinresState* s, cudaStream_t st);
 // w_new (over w_m2) = z*w_q - w_m1*w_m1c - w_m2*w_m2c ; x += x_w * w_new
+// (nothing when s->wx_pending is 0: no rotation since the start or since the last update)
 template <typename T, typename TX>
 cudaError_t launch_minres_wx(const T* z, const T* wm1, T* wm2, TX* x, int64_t n, const MinresState* s,
                              cudaStream_t st);

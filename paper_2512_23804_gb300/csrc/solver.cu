@@ -277,7 +277,11 @@ template <typename T>
 static sgoc_status hgs(const sgoc_problem* pb, PrecWS<T>& w, const T* R, T* V, int slabs, cudaStream_t st) {
   const int P = pb->P, p = pb->p;
   const int64_t n = pb->n, ps = int64_t(P) * n;
-  SGOC_LAUNCH(launch_fill<T>(V, slabs * ps, T(0), st));
+  // With one slab a level's columns of V are contiguous: the first visit of each level
+  // stores its correction there (levels are never read before their first visit), so V
+  // needs no zero fill.  With several slabs the corrections are added into a zeroed V.
+  const bool one = slabs == 1;
+  if (!one) SGOC_LAUNCH(launch_fill<T>(V, slabs * ps, T(0), st));
   // palindromic sweep 0, 1, ..., p, ..., 1, 0: the first visit of each level, then the returns
   for (int step = 0; step < 2 * p + 1; ++step) {
     const bool first = step <= p;
@@ -286,11 +290,12 @@ static sgoc_status hgs(const sgoc_problem* pb, PrecWS<T>& w, const T* R, T* V, i
     // the first visit of level 0 has no couplings: its right-hand side is R_0 itself,
     // which for one slab is a contiguous column the V-cycle reads in place
     const T* rhs = w.RH;
-    if (first && d == 0 && slabs == 1) rhs = R;
+    if (first && d == 0 && one) rhs = R;
     else
       SGOC_LAUNCH(launch_sg<T>(first ? hgs_args_first<T>(pb, w, R, V, slabs, d) : hgs_args<T>(pb, w, R, V, slabs, d),
                                st));
-    SGOC_TRY(vcycle<T>(pb, w, rhs, nullptr, int64_t(slabs) * L, V, ps, L, a0, st));
+    if (first && one) SGOC_TRY(vcycle<T>(pb, w, rhs, V + int64_t(a0) * n, L, nullptr, 0, 1, 0, st));
+    else SGOC_TRY(vcycle<T>(pb, w, rhs, nullptr, int64_t(slabs) * L, V, ps, L, a0, st));
   }
   return SGOC_OK;
 }
@@ -299,7 +304,8 @@ static sgoc_status hgs(const sgoc_problem* pb, PrecWS<T>& w, const T* R, T* V, i
 // auxiliary streams (parallel branches when captured into a graph).
 struct Fork {
   cudaStream_t s1 = nullptr, s2 = nullptr;
-  cudaEvent_t e[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t s3 = nullptr;            // the deferred MINRES w/x update beside the KKT product
+  cudaEvent_t e[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 static sgoc_status fork_to(cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
@@ -521,6 +527,7 @@ struct Runtime {
     if (ev) cudaEventDestroy(ev);
     if (fork.s1) cudaStreamDestroy(fork.s1);
     if (fork.s2) cudaStreamDestroy(fork.s2);
+    if (fork.s3) cudaStreamDestroy(fork.s3);
     for (auto& e : fork.e) if (e) cudaEventDestroy(e);
     if (hstate) cudaFreeHost(hstate);
     if (hscal) cudaFreeHost(hscal);
@@ -550,6 +557,7 @@ static sgoc_status runtime_of(sgoc_problem* pb, Runtime** out) {
     SGOC_CUDA_TRY(cudaEventCreateWithFlags(&rt->ev, cudaEventDisableTiming));
     SGOC_CUDA_TRY(cudaStreamCreateWithFlags(&rt->fork.s1, cudaStreamNonBlocking));
     SGOC_CUDA_TRY(cudaStreamCreateWithFlags(&rt->fork.s2, cudaStreamNonBlocking));
+    SGOC_CUDA_TRY(cudaStreamCreateWithFlags(&rt->fork.s3, cudaStreamNonBlocking));
     for (auto& e : rt->fork.e) SGOC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
   *out = static_cast<Runtime*>(pb->runtime);
@@ -587,19 +595,35 @@ static sgoc_status minres_start(const sgoc_problem* pb, Layout& L, const MinresV
   return SGOC_OK;
 }
 
+// The w/x update left pending by the last rotation, with the buffer roles `m` of the
+// iteration that follows it (a no-op when nothing is pending).
+template <typename T, typename TX>
+static sgoc_status prev_wx(const sgoc_problem* pb, Layout& L, const MinresVecs<T>& m, TX* x, cudaStream_t st) {
+  SGOC_LAUNCH((launch_minres_wx<T, TX>(m.zn, m.wm2, m.wm1, x, pb->N, L.k64.state, st)));
+  return SGOC_OK;
+}
+
 // One MINRES iteration with fixed buffer roles (see swapped()).
 template <typename T, typename TX>
 static sgoc_status minres_step(const sgoc_problem* pb, Layout& L, const MinresVecs<T>& m, TX* x, cudaStream_t st,
                                const Fork* f) {
   const int64_t N = pb->N;
+  // The w/x update of the previous iteration runs here, beside the KKT product: its
+  // coefficients stay in the state until this iteration's rotation, and its operands in
+  // this iteration's roles are z_prev = zn, w_prev = wm2 (read), w_prev-1 = wm1 (overwritten).
+  // It joins before the preconditioner, which overwrites zn.  (The update of the last
+  // iteration is applied by the caller, prev_wx, when the iteration loop ends.)
+  cudaStream_t sw = f ? f->s3 : st;
+  if (f) SGOC_TRY(fork_to(st, sw, f->e[6]));
+  SGOC_TRY((prev_wx<T, TX>(pb, L, m, x, sw)));
   SGOC_TRY(kkt_apply<T>(pb, m.z, m.Kz, st, f));
   SGOC_LAUNCH(launch_dot_partial<T>(m.z, m.Kz, N, L.k64.partial, st));
   SGOC_LAUNCH(launch_minres_alpha(L.k64.state, L.k64.partial, st));
   SGOC_LAUNCH(launch_minres_v<T>(m.Kz, m.v, m.vp, N, L.k64.state, st));
+  if (f) SGOC_TRY(fork_to(sw, st, f->e[7]));
   SGOC_TRY(precond_apply<T>(pb, prec_of<T>(L), m.vp, m.zn, st, f));
   SGOC_LAUNCH(launch_dot_partial<T>(m.vp, m.zn, N, L.k64.partial, st));
   SGOC_LAUNCH(launch_minres_rotate(L.k64.state, L.k64.partial, st));
-  SGOC_LAUNCH(launch_minres_wx<T, TX>(m.z, m.wm1, m.wm2, x, N, L.k64.state, st));
   return SGOC_OK;
 }
 
@@ -757,6 +781,15 @@ struct SolveTask {
     par ^= 1;
     return record();
   }
+  // apply the pending w/x update of the last iteration (roles of the next parity) and clear it
+  template <typename T, typename TX>
+  sgoc_status flush_wx(TX* x) {
+    const MinresVecs<T>& m = vecs_of<T>(L);
+    SGOC_TRY((prev_wx<T, TX>(pb, L, par == 0 ? m : swapped(m), x, st)));
+    SGOC_CUDA_TRY(cudaMemsetAsync(&L.k64.state->wx_pending, 0, sizeof(int), st));
+    pdl_fence(st);
+    return SGOC_OK;
+  }
   sgoc_status finish(sgoc_status s) {
     status = s;
     phase = DONE;
@@ -839,6 +872,7 @@ struct SolveTask {
         result.iterations = j; result.outer_iterations = 1; result.rel_estimate = hs.est;
         sgoc_status e = state_error(hs);
         if (e != SGOC_OK) return fail(e);
+        if (hs.flag == 1 || hs.flag == 2 || j >= pb->opt.max_iter) SGOC_TRY((flush_wx<double, double>(L.k64.x)));
         if (hs.flag == 1 || hs.flag == 2) { last_flag = hs.flag; phase = CHECK64; return launch_true_residual(); }
         if (j >= pb->opt.max_iter) { set_error("MINRES iteration limit reached"); return finish(SGOC_ERR_NO_CONVERGENCE); }
         return launch_iter<double, double>(L.k64.x);
@@ -878,6 +912,7 @@ struct SolveTask {
         sgoc_status e = state_error(hs);
         if (e != SGOC_OK) return fail(e);
         if (hs.flag == 1 || hs.flag == 2 || jin >= pb->opt.max_iter) {
+          SGOC_TRY((flush_wx<float, float>(L.c32)));
           SGOC_LAUNCH(launch_add_scaled(L.c32, L.k64.x, N, rn, st));
           ++outer;
           phase = OUTER;
