@@ -2062,10 +2062,11 @@ __device__ int vt_coarse(T* base, const VFLevel<T>* lv, int nu) {
 }
 
 // Level-0 sweeps of the V-cycle kernel.  Scalar form: a thread owns a strip of
-// up to kStripRows rows of one grid column (vt_strip).  Float32 form for 63 x 63
-// and 127 x 127: a thread owns two adjacent columns over 8 rows and computes both
-// nodes with packed FP32x2 arithmetic (four loads per row for the pair instead of
-// six; the same operations in the same order as vt_strip, per lane).
+// up to kStripRows rows of one grid column (vt_strip).  Float32 forms: a thread
+// owns two columns over 8 rows and computes both nodes with packed FP32x2
+// arithmetic (the same operations in the same order as vt_strip, per lane); the
+// two columns are adjacent (four loads per row for the pair) or half a grid apart
+// (six loads per row, but neighbouring lanes read neighbouring words).
 template <typename T, int N1, bool PAIR = (std::is_same<T, float>::value && N1 >= 63)>
 struct VtLevel0 {
   Strip g;
@@ -2234,6 +2235,164 @@ struct VtLevel0<float, N1, true> {
   __device__ __forceinline__ float first_b() const { return bv[0].x; }
 };
 
+template <int N1>
+struct VtLevel0Split {
+  // a thread owns grid columns xa and xa + NP over R rows: neighbouring lanes hold
+  // neighbouring columns, so every shared-memory access of a warp is conflict-free
+  static constexpr int NP = (N1 + 1) / 2;
+  static constexpr int R = 8;                  // rows per thread
+  static constexpr int S = N1 + 2;
+  static_assert(VT<N1>::nb() / NP * R >= N1, "strips must cover the grid");
+  static_assert(NP % 2 == 0, "the two columns of a thread must have the same parity");
+  int xa, y0, ny;
+  bool v1;                                      // the second column exists
+  float2 bv[R];
+  __device__ __forceinline__ void init(const float* __restrict__ b0) {
+    const int t = threadIdx.x;
+    xa = t % NP;
+    y0 = (t / NP) * R;
+    ny = max(0, min(R, N1 - y0));
+    v1 = xa + NP < N1;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int y = y0 + j;
+      bv[j] = j < ny ? make_float2(b0[y * N1 + xa], v1 ? b0[y * N1 + xa + NP] : 0.f) : make_float2(0.f, 0.f);
+    }
+  }
+  // window row of the two columns: left, centre, right neighbours as (column a, column b)
+  __device__ __forceinline__ void wload(const float* pr, float2& l, float2& m, float2& r) const {
+    l = make_float2(pr[0], v1 ? pr[NP] : 0.f);
+    m = make_float2(pr[1], v1 ? pr[NP + 1] : 0.f);
+    r = make_float2(pr[2], v1 ? pr[NP + 2] : 0.f);
+  }
+  template <int MODE>
+  __device__ __forceinline__ void pass(const float* __restrict__ xs, float* __restrict__ xd, float d, float e,
+                                       float c, float wd) const {
+    if (ny <= 0) return;
+    float* q = xd + (y0 + 1) * S + xa + 1;
+    if (MODE == 1) {
+#pragma unroll
+      for (int j = 0; j < R; ++j)
+        if (j < ny) {
+          q[j * S] = wd * bv[j].x;
+          if (v1) q[j * S + NP] = wd * bv[j].y;
+        }
+      return;
+    }
+    const float* p = xs + y0 * S + xa;         // row y0 - 1, column xa - 1 (zero-bordered)
+    float2 l0, m0, r0, l1, m1_, r1;
+    wload(p, l0, m0, r0);
+    wload(p + S, l1, m1_, r1);
+    const float2 dd = make_float2(d, d), ee = make_float2(e, e), cc = make_float2(c, c);
+    const float2 ww = make_float2(wd, wd), neg = make_float2(-1.f, -1.f);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      if (j < ny) {
+        float2 l2, m2, r2;
+        wload(p + (j + 2) * S, l2, m2, r2);
+        const float2 edges = __fadd2_rn(__fadd2_rn(m0, m2), __fadd2_rn(l1, r1));
+        const float2 corners = __fadd2_rn(__fadd2_rn(l0, r0), __fadd2_rn(l2, r2));
+        const float2 av = __ffma2_rn(dd, m1_, __ffma2_rn(ee, edges, __fmul2_rn(cc, corners)));
+        const float2 rr = __ffma2_rn(neg, av, bv[j]);                // b - A x, rounded once
+        const float2 o = MODE == 2 ? rr : __ffma2_rn(ww, rr, m1_);
+        q[j * S] = o.x;
+        if (v1) q[j * S + NP] = o.y;
+        l0 = l1; m0 = m1_; r0 = r1;
+        l1 = l2; m1_ = m2; r1 = r2;
+      }
+    }
+  }
+  // post-smoothing sweep with the prolongation (PRO) or the copy-out (OUT) folded
+  // in, as vt_strip_post; both columns have the parity of xa, so the coarse pair
+  // sums of a window row are formed by the same selects for both
+  template <bool PRO, bool OUT>
+  __device__ __forceinline__ void post(const float* __restrict__ xs, float* __restrict__ xd,
+                                       const float* __restrict__ xc, float* __restrict__ gout, bool acc, float d,
+                                       float e, float c, float wd) const {
+    if (ny <= 0) return;
+    constexpr int SC = (N1 - 1) / 2 + 2;
+    const float* p = xs + y0 * S + xa;
+    const int lo = xa >> 1;
+    const bool odd = xa & 1;
+    const float* cp = xc + (y0 / 2) * SC + lo;
+    const float2 q4 = make_float2(0.25f, 0.25f);
+    float2 s0[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    auto csum = [&](int i, float2 (&sv)[3]) {
+      const float* qa = cp + i * SC;
+      const float* qb = qa + NP / 2;
+      const float2 v0 = make_float2(qa[0], v1 ? qb[0] : 0.f);
+      const float2 w1 = make_float2(qa[1], v1 ? qb[1] : 0.f);
+      const float2 v2 = odd ? make_float2(qa[2], v1 ? qb[2] : 0.f) : make_float2(0.f, 0.f);
+      const float2 m0 = odd ? w1 : v0;
+      sv[0] = __fadd2_rn(v0, m0);
+      sv[1] = __fadd2_rn(m0, w1);
+      sv[2] = __fadd2_rn(w1, odd ? v2 : w1);
+    };
+    auto wrow = [&](int w, float2& l, float2& m, float2& r) {
+      wload(p + w * S, l, m, r);
+      if (PRO) {
+        float2 k[3];
+        if (w & 1) {
+          float2 s1[3];
+          csum((w + 1) >> 1, s1);
+#pragma unroll
+          for (int q = 0; q < 3; ++q) { k[q] = __fmul2_rn(q4, __fadd2_rn(s0[q], s1[q])); s0[q] = s1[q]; }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 3; ++q) k[q] = __fmul2_rn(q4, __fadd2_rn(s0[q], s0[q]));
+        }
+        l = __fadd2_rn(l, k[0]);
+        m = __fadd2_rn(m, k[1]);
+        r = __fadd2_rn(r, k[2]);
+      }
+    };
+    float* q = xd + (y0 + 1) * S + xa + 1;
+    float* go = gout + y0 * N1 + xa;
+    // the accumulator's values are all requested before the sweep, not one latency a row
+    float2 ga[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      ga[j] = (OUT && acc && j < ny) ? make_float2(go[j * N1], v1 ? go[j * N1 + NP] : 0.f) : make_float2(0.f, 0.f);
+    if (PRO) csum(0, s0);
+    float2 l0, m0, r0, l1, m1_, r1;
+    wrow(0, l0, m0, r0);
+    wrow(1, l1, m1_, r1);
+    const float2 dd = make_float2(d, d), ee = make_float2(e, e), cc = make_float2(c, c);
+    const float2 ww = make_float2(wd, wd), neg = make_float2(-1.f, -1.f);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      if (j < ny) {
+        float2 l2, m2, r2;
+        wrow(j + 2, l2, m2, r2);
+        const float2 edges = __fadd2_rn(__fadd2_rn(m0, m2), __fadd2_rn(l1, r1));
+        const float2 corners = __fadd2_rn(__fadd2_rn(l0, r0), __fadd2_rn(l2, r2));
+        const float2 av = __ffma2_rn(dd, m1_, __ffma2_rn(ee, edges, __fmul2_rn(cc, corners)));
+        const float2 o = __ffma2_rn(ww, __ffma2_rn(neg, av, bv[j]), m1_);
+        if (!OUT) {
+          q[j * S] = o.x;
+          if (v1) q[j * S + NP] = o.y;
+        } else if (acc) {
+          go[j * N1] = ga[j].x + o.x;
+          if (v1) go[j * N1 + NP] = ga[j].y + o.y;
+        } else {
+          go[j * N1] = o.x;
+          if (v1) go[j * N1 + NP] = o.y;
+        }
+        l0 = l1; m0 = m1_; r0 = r1;
+        l1 = l2; m1_ = m2; r1 = r2;
+      }
+    }
+  }
+  __device__ __forceinline__ float first_b() const { return bv[0].x; }
+};
+
+// the level-0 form a kernel uses: split column pairs at 127 x 127 (32 warps, where the
+// bank conflicts of adjacent pairs dominate), adjacent pairs at 63 x 63 (8 warps, where
+// the fewer loads of adjacent pairs win), scalar strips otherwise
+template <typename T, int N1>
+using VtLevel0Of = typename std::conditional<std::is_same<T, float>::value && N1 >= 127, VtLevel0Split<N1>,
+                                             VtLevel0<T, N1>>::type;
+
 template <typename T, int N1>
 __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 : kVFThreads / VT<N1>::nb()) vcycle_t_kernel(const T* __restrict__ bg, T* xg, FusedLevels L,
                                                                  T omega, int nu, T* acc, int64_t acc_ss, int acc_L,
@@ -2274,7 +2433,7 @@ __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 :
     }
   }
   pdl_wait();                                        // b and the output are shared with earlier kernels
-  VtLevel0<T, N1> z;
+  VtLevel0Of<T, N1> z;
   z.init(bg + col * n0);
   __syncthreads();
   T* xa = base;
