@@ -69,7 +69,7 @@ def load_peaks():
 # float64 ALU peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2070 MHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 SG_KERNEL_NAMES = {0: "one-phase", 1: "quad-32", 2: "quad-16", 3: "two-phase", 4: "quad-32x4", 5: "quad-16x4",
-                   -1: "none"}
+                   6: "direct", -1: "none"}
 # ncu: vcycle_t_kernel<float, 127>, 56 columns: 3,698,432 B read + 0 B written
 VCYCLE_DRAM_BYTES_PER_COLUMN = 3705088 / 56
 # float32 non-tensor peak: 152 SMs x 128 FMA/clk x 2 flop x 2070 MHz
@@ -401,7 +401,7 @@ def run_ours(args):
                 w = X.element_size()
                 byts = w * (2 * sp.n * sp.P) + w * (pr.M + 1) * pr.nx * pr.nx
                 per = {}
-                for v in range(6):
+                for v in range(7):
                     try:
                         sp.apply_operator_variant(X, v, out=Y)
                     except abi.SgocError:

@@ -205,11 +205,13 @@ sgoc_status sgoc_server_stats(const sgoc_server* sv, int64_t* admitted, int64_t*
  * tuning a built-in rule chooses.  chosen (nullable, nchosen entries, 2p + 4 used)
  * receives the kernel index per shape in the order above (0 one-phase, 1 and 2 four
  * nodes per thread on 32- and 16-node tiles, 3 two-phase float32, 4 and 5 the
- * four-node kernels built for four instead of two CTAs per SM).  Synchronizes
+ * four-node kernels built for four instead of two CTAs per SM, 6 the direct
+ * kernel: a thread per node and output column, for shapes with few outputs and
+ * couplings).  Synchronizes
  * the stream.  The paper has no counterpart: it concerns this GPU code only. */
 sgoc_status sgoc_autotune(sgoc_problem* pb, void* d_ws, size_t ws_bytes, int32_t* chosen,
                           int32_t nchosen, void* stream);
-/* Pins kernel `variant` (0..5 as above; -1 clears the entry, restoring the
+/* Pins kernel `variant` (0..6 as above; -1 clears the entry, restoring the
  * built-in rule) for SG launch shape `shape` of a solve of pb (0 the KKT product,
  * 1 the operator alone, 2 + d the return visit of hGS level d, 3 + p + d the
  * first visit of level d) in precision 0
@@ -224,7 +226,7 @@ sgoc_status sgoc_set_kernel(sgoc_problem* pb, int32_t precision, int32_t shape, 
  * 1: float32.  X and Y must not overlap. */
 sgoc_status sgoc_apply_operator(sgoc_problem* pb, int32_t precision, const void* d_X,
                                 void* d_Y, int32_t nslabs, void* stream);
-/* The same product with one given kernel variant (0..5 as listed for
+/* The same product with one given kernel variant (0..6 as listed for
  * sgoc_autotune); SGOC_ERR_UNSUPPORTED when that kernel does not apply to this
  * shape or precision.  For tests of the variants against each other. */
 sgoc_status sgoc_apply_operator_variant(sgoc_problem* pb, int32_t precision, int32_t variant,

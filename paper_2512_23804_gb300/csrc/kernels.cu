@@ -819,12 +819,107 @@ static bool try_launch_sgu(const SGArgs<float>& a, cudaStream_t st, cudaError_t*
 }
 
 // ---------------------------------------------------------------------------
+// SG apply, direct form: one thread per (node, output column), no shared memory
+// and no barriers; each element term is formed from its column's 3 x 3
+// neighbourhood read through the cache, once per table entry that needs it.  For
+// launch shapes with few output columns and few couplings (the hGS visits of the
+// low chaos levels), where the staged forms' fixed costs (table and kappa staging,
+// row pipelines) dominate.  The per-node arithmetic and its order are those of
+// sg_kernel.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) sgd_kernel(SGArgs<T> a) {
+  using V4 = typename Vec4<T>::type;
+  const int64_t node = int64_t(blockIdx.x) * 256 + threadIdx.x;
+  const int beta = a.out0 + int(blockIdx.y);
+  const int t = blockIdx.z;
+  const int n1 = a.n1;
+  const bool live = node < a.n;
+  const int iy = live ? int(node / n1) : 0, ix = live ? int(node - int64_t(iy) * n1) : 0;
+  const int64_t nx = a.nx;
+  const int e0 = a.nbr_ptr[beta], e1 = a.nbr_end[beta];
+  pdl_enter();                                       // X, R and Y are written by earlier kernels
+  if (!live) return;
+  const T* X = a.X + int64_t(t) * a.xs;
+  const bool use_m = a.cm != T(0);
+  const bool xl = ix > 0, xr = ix + 1 < n1, yd = iy > 0, yu = iy + 1 < n1;
+  // the 3 x 3 neighbourhood of column col (zero outside the grid) and its element terms
+  auto nb9 = [&](int col, T (&v)[9]) {
+    const T* c = X + int64_t(col) * a.n + node;
+    v[0] = (yd && xl) ? c[-n1 - 1] : T(0); v[1] = yd ? c[-n1] : T(0); v[2] = (yd && xr) ? c[-n1 + 1] : T(0);
+    v[3] = xl ? c[-1] : T(0);              v[4] = c[0];               v[5] = xr ? c[1] : T(0);
+    v[6] = (yu && xl) ? c[n1 - 1] : T(0);  v[7] = yu ? c[n1] : T(0);  v[8] = (yu && xr) ? c[n1 + 1] : T(0);
+  };
+  auto terms = [&](const T (&v)[9]) {
+    const T SW = v[0], S = v[1], SE = v[2], Wv = v[3], C = v[4], E = v[5], NW = v[6], N = v[7], NE = v[8];
+    const T c4 = T(4) * C;
+    const T aS = c4 - S, aN = c4 - N;
+    V4 r;
+    r.x = fma(T(-2), SW, aS - Wv);
+    r.y = fma(T(-2), SE, aS - E);
+    r.z = fma(T(-2), NE, aN - E);
+    r.w = fma(T(-2), NW, aN - Wv);
+    return r;
+  };
+  auto kap4 = [&](int k) {
+    const T* kp = a.kap + int64_t(k) * nx * nx;
+    V4 r;
+    r.x = kp[int64_t(iy) * nx + ix];             // SW element (ix, iy)
+    r.y = kp[int64_t(iy) * nx + ix + 1];         // SE element (ix+1, iy)
+    r.z = kp[int64_t(iy + 1) * nx + ix + 1];     // NE element (ix+1, iy+1)
+    r.w = kp[int64_t(iy + 1) * nx + ix];         // NW element (ix, iy+1)
+    return r;
+  };
+  T diag = T(0), mass = T(0);
+  if (!a.no_own || use_m) {
+    T v[9];
+    nb9(beta, v);
+    if (!a.no_own) diag = dot4<T>(kap4(0), terms(v));
+    if (use_m) {
+      const T edges = (v[7] + v[1]) + (v[5] + v[3]);
+      const T corners = (v[8] + v[6]) + (v[2] + v[0]);
+      mass = a.mass * fma(T(16), v[4], fma(T(4), edges, corners));
+    }
+  }
+  T off = T(0);
+  for (int e = e0; e < e1; ++e) {
+    T v[9];
+    nb9(a.nbr_alpha[e], v);
+    off = fma(a.nbr_c[e], dot4<T>(kap4(a.nbr_k[e]), terms(v)), off);
+  }
+  T out = fma(a.c0, diag, a.c1 * off);
+  if (use_m) out = fma(a.cm, mass, out);
+  if (a.R) out = fma(a.cr, a.R[int64_t(t) * a.rs + int64_t(beta - a.rcol0) * a.n + node], out);
+  T* yp = a.Y + int64_t(t) * a.ys + int64_t(beta - a.ycol0) * a.n + node;
+  if (a.cy != T(0)) out = fma(a.cy, *yp, out);
+  *yp = out;
+}
+
+template <typename T>
+static cudaError_t launch_sgd(const SGArgs<T>& a, cudaStream_t st) {
+  const int nout = a.out1 - a.out0;
+  dim3 grid(unsigned((a.n + 255) / 256), unsigned(nout), unsigned(a.nslabs));
+  const double w = sizeof(T), cells = double(a.n) * a.nslabs;
+  const double bytes = w * cells * (double(a.in1 - a.in0) + nout * (1.0 + (a.R ? 1 : 0) + (a.cy != T(0) ? 1 : 0))) +
+                       w * (a.M + 1.0) * a.nx * a.nx;
+  const double flops = cells * (15.0 * (nout + (a.c1 != T(0) ? a.deg_sum : 0)) + 9.0 * nout +
+                                9.0 * (a.c1 != T(0) ? a.deg_sum : 0));
+  ProfScope ps(KK_SG, st, bytes, flops);
+  {
+    const cudaError_t le_ = launch_pdl(sgd_kernel<T>, grid, dim3(256), size_t(0), st, a);
+    if (le_ != cudaSuccess) return le_;
+  }
+  note_launch();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // SG kernel variants and the tuning cache.  All variants form the same products
 // and sums in the same order, so the choice changes timing only.
 //   0: one-phase kernel (tile by the heuristic), 1: quad kernel, 32-node tile,
 //   2: quad kernel, 16-node tile, 3: two-phase kernel (float32, slot table),
 //   4, 5: quad kernel on 32- and 16-node tiles compiled for four CTAs per SM
-//   (64 registers) instead of two.
+//   (64 registers) instead of two, 6: direct kernel (few outputs and couplings).
 // The cache maps a launch shape (grid, column ranges, KL terms, truncation,
 // slabs, element size, epilogue terms) to the variant measured fastest.
 // ---------------------------------------------------------------------------
@@ -883,6 +978,8 @@ bool sg_variant_feasible(const SGArgs<T>& a, int v) {
       if constexpr (std::is_same<T, float>::value)
         return a.u_mb && a.n1 >= 24 && a.M + 1 <= 17 && sgu_smem(a) + 4096 <= kMaxSmem;
       return false;
+    case 6:                                   // its work grows with outputs x (1 + couplings)
+      return double(a.out1 - a.out0) + (a.c1 != T(0) ? a.deg_sum : 0.0) <= kSGDirectMaxTerms;
     default: return false;
   }
 }
@@ -906,6 +1003,7 @@ cudaError_t launch_sg_variant(const SGArgs<T>& a, int v, cudaStream_t st) {
     case 2: return launch_sg4_tx<T, 16, 2>(a, sg4_smem<T, 16>(a), st);
     case 4: return launch_sg4_tx<T, 32, 4>(a, sg4_smem<T, 32>(a), st);
     case 5: return launch_sg4_tx<T, 16, 4>(a, sg4_smem<T, 16>(a), st);
+    case 6: return launch_sgd<T>(a, st);
     case 3:
       if constexpr (std::is_same<T, float>::value) {
         cudaError_t e = cudaSuccess;

@@ -59,9 +59,11 @@ struct SGArgs {
 template <typename T>
 cudaError_t launch_sg(const SGArgs<T>& a, cudaStream_t st);
 // SG kernel variants (0 one-phase, 1 quad 32-node tile, 2 quad 16-node tile,
-// 3 two-phase float32, 4 and 5 the quad tiles at four CTAs per SM) and the
-// process-wide tuning cache keyed by launch shape.
-constexpr int kSGVariants = 6;
+// 3 two-phase float32, 4 and 5 the quad tiles at four CTAs per SM, 6 direct:
+// a thread per node and output, feasible while outputs + couplings <=
+// kSGDirectMaxTerms) and the process-wide tuning cache keyed by launch shape.
+constexpr int kSGVariants = 7;
+constexpr double kSGDirectMaxTerms = 256;
 template <typename T>
 cudaError_t launch_sg_variant(const SGArgs<T>& a, int variant, cudaStream_t st);
 template <typename T>

@@ -46,7 +46,7 @@ def test_sg_variants_agree_bitwise(case, dtype, tol):
     ref = np.concatenate([d.vec(d.sg_apply(d.mat(X[t * ps:(t + 1) * ps]))) for t in range(d.slabs)])
     Xd = torch.from_numpy(X).to("cuda", dtype)
     outs = []
-    for v in range(6):
+    for v in range(7):
         try:
             Y = sp.apply_operator_variant(Xd, v, nslabs=d.slabs)
         except abi.SgocError as e:
@@ -70,7 +70,7 @@ def test_autotune_keeps_the_solution(precision):
     x0 = x0.clone()
     chosen = sp.autotune()
     assert len(chosen) == 2 * pr.p + 4
-    assert all(0 <= v <= 5 for v in chosen)
+    assert all(0 <= v <= 6 for v in chosen)
     x1, i1 = sp.solve()
     assert i1["iterations"] == i0["iterations"]
     assert torch.equal(x1, x0)
@@ -101,7 +101,7 @@ def test_pinned_kernels_in_hgs_and_kkt(dtype, tol):
     shapes = [0, 1] + [2 + lev for lev in range(2 * pr.p + 2)]
     outs = []
     try:
-        for var in range(6):
+        for var in range(7):
             for sh in shapes:
                 try:
                     sp.set_kernel(sh, var, precision=pid)
