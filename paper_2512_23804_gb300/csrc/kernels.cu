@@ -461,26 +461,35 @@ __global__ void __launch_bounds__(kSG4Threads, MINB) sg4_kernel(SGArgs<T> a, int
   pdl_wait();                                        // X (and Y, R) are written by earlier kernels
   if (r0 >= r1) { pdl_trigger(); return; }
 
+  // row gy (-1 and n1 give zeros) into ring slot (gy + 1) % 3: a warp per input column,
+  // its lanes along the row segment (element lx is grid column ix0 + lx - 1)
+  static_assert(W <= 64, "a row segment is at most two lanes' worth per lane");
+  const int warp = tid >> 5, lane = tid & 31;
+  const int gxa = ix0 + lane - 1, gxb = ix0 + lane + 31;
+  const bool seg_a = lane < W, seg_b = lane + 32 < W;
   auto issue_row = [&](int gy) {
     T* dst = Xr + size_t((gy + 1) % 3) * ring_stride;
     const bool rok = gy >= 0 && gy < n1;
-    for (int q = tid; q < nin * W; q += NT) {
-      const int c = q / W, lx = q - c * W;
-      const int gx = ix0 + lx - 1;
-      const bool ok = rok && gx >= 0 && gx < n1;
-      const T* col = X + int64_t(a.in0 + c) * a.n;
-      cp_async_elem(dst + q, ok ? col + (int64_t(gy) * n1 + gx) : col, ok);
+    const bool oka = rok && gxa >= 0 && gxa < n1, okb = rok && seg_b && gxb < n1;
+    const T* col = X + int64_t(a.in0) * a.n + int64_t(rok ? gy : 0) * n1;
+    T* d = dst;
+    for (int c = warp; c < nin; c += NT / 32) {
+      const T* cc = col + int64_t(c) * a.n;
+      T* dc = d + c * W;
+      if (seg_a) cp_async_elem(dc + lane, oka ? cc + gxa : cc, oka);
+      if (seg_b) cp_async_elem(dc + lane + 32, okb ? cc + gxb : cc, okb);
     }
   };
-  // kappa_k/6 of the four elements of every node of row gy (SW, SE, NE, NW planes) into slot gy & 1
+  // kappa_k/6 of the four elements of every node of row gy (SW, SE, NE, NW planes) into slot
+  // gy & 1: a warp per (k, element) plane, its lanes along the tile
   auto issue_kappa = [&](int gy) {
     T* dst = Ks + size_t(gy & 1) * kslot;
-    for (int q = tid; q < int(kslot); q += NT) {
-      const int kk = q / (4 * TX), r = q - kk * 4 * TX;
-      const int e = r / TX, lx = r - e * TX;
-      const int ix = min(ix0 + lx, n1 - 1);
-      const int ex = ix + ((e == 1 || e == 2) ? 1 : 0), ey = gy + (e >= 2 ? 1 : 0);
-      cp_async_elem(dst + q, a.kap + (int64_t(kk) * a.nx + ey) * a.nx + ex, true);
+    for (int pl = warp; pl < (a.M + 1) * 4; pl += NT / 32) {
+      const int kk = pl >> 2, e = pl & 3;
+      const int ey = gy + (e >= 2 ? 1 : 0);
+      const T* kp = a.kap + (int64_t(kk) * a.nx + ey) * a.nx + ((e == 1 || e == 2) ? 1 : 0);
+      for (int lx = lane; lx < TX; lx += 32)
+        cp_async_elem(dst + size_t(pl) * TX + lx, kp + min(ix0 + lx, n1 - 1), true);
     }
   };
   issue_row(r0 - 1);
