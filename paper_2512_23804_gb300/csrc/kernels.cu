@@ -258,16 +258,22 @@ __global__ void __launch_bounds__(kSGThreads, 2) sg_kernel(SGArgs<T> a, int rows
   pdl_wait();                                        // X (and Y, R) are written by earlier kernels
   if (r0 >= r1) { pdl_trigger(); return; }
 
-  // row gy (-1 and n1 give zeros) into ring slot (gy + 1) % 3
+  // row gy (-1 and n1 give zeros) into ring slot (gy + 1) % 3: a warp per input column,
+  // its lanes along the row segment (element lx is grid column ix0 + lx - 1)
+  static_assert(W <= 64, "a row segment is at most two lanes' worth per lane");
+  const int warp = tid >> 5, lane = tid & 31;
+  const int gxa = ix0 + lane - 1, gxb = ix0 + lane + 31;
+  const bool seg_a = lane < W, seg_b = lane + 32 < W;
   auto issue_row = [&](int gy) {
     T* dst = Xr + size_t((gy + 1) % 3) * ring_stride;
     const bool rok = gy >= 0 && gy < n1;
-    for (int q = tid; q < nin * W; q += kSGThreads) {
-      const int c = q / W, lx = q - c * W;
-      const int gx = ix0 + lx - 1;
-      const bool ok = rok && gx >= 0 && gx < n1;
-      const T* col = X + int64_t(a.in0 + c) * a.n;
-      cp_async_elem(dst + q, ok ? col + (int64_t(gy) * n1 + gx) : col, ok);
+    const bool oka = rok && gxa >= 0 && gxa < n1, okb = rok && seg_b && gxb < n1;
+    const T* col = X + int64_t(a.in0) * a.n + int64_t(rok ? gy : 0) * n1;
+    for (int c = warp; c < nin; c += kSGThreads / 32) {
+      const T* cc = col + int64_t(c) * a.n;
+      T* dc = dst + c * W;
+      if (seg_a) cp_async_elem(dc + lane, oka ? cc + gxa : cc, oka);
+      if (seg_b) cp_async_elem(dc + lane + 32, okb ? cc + gxb : cc, okb);
     }
   };
   issue_row(r0 - 1);
