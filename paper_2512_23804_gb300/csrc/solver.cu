@@ -10,6 +10,7 @@
 #include <map>
 #include <string>
 #include <thread>
+#include <functional>
 #include <type_traits>
 #include <vector>
 
@@ -413,7 +414,8 @@ static sgoc_status kkt_apply(const sgoc_problem* pb, const T* v, T* w, cudaStrea
 // ------------------------------------------------------ block preconditioner --
 template <typename T>
 static sgoc_status precond_apply(const sgoc_problem* pb, PrecWS<T>& w, const T* r, T* z, cudaStream_t st,
-                                 const Fork* f = nullptr) {
+                                 const Fork* f = nullptr,
+                                 const std::function<sgoc_status(cudaStream_t)>& before_cheb = nullptr) {
   const int64_t F = pb->F, ps = int64_t(pb->P) * pb->n;
   // blocks 1, 2: Chebyshev on M, scaled by 1/(sc_t H^gamma) and 1/(sc_t beta)
   ChebArgs<T> c{};
@@ -424,6 +426,7 @@ static sgoc_status precond_apply(const sgoc_problem* pb, PrecWS<T>& w, const T* 
   // blocks 1, 2 (Chebyshev) are independent of block 3: run them on an auxiliary stream
   cudaStream_t sc = st;
   if (f) { SGOC_TRY(fork_to(st, f->s1, f->e[3])); sc = f->s1; }
+  if (before_cheb) SGOC_TRY(before_cheb(sc));       // work only the Chebyshev blocks wait for
   SGOC_LAUNCH(launch_cheb<T>(c, sc));
   // block 3: S^{-1} = Z^{-1} M_gamma Z^{-1} (steady), tau Z~^{-1} (D (x) M_gamma) Z~^{-1} (time)
   SGOC_TRY(hgs<T>(pb, w, r + 2 * F, w.W1, pb->slabs, st));
@@ -619,9 +622,15 @@ static sgoc_status minres_step(const sgoc_problem* pb, Layout& L, const MinresVe
   SGOC_TRY(kkt_apply<T>(pb, m.z, m.Kz, st, f));
   SGOC_LAUNCH(launch_dot_partial<T>(m.z, m.Kz, N, L.k64.partial, st));
   SGOC_LAUNCH(launch_minres_alpha(L.k64.state, L.k64.partial, st));
-  SGOC_LAUNCH(launch_minres_v<T>(m.Kz, m.v, m.vp, N, L.k64.state, st));
+  // v_{j+1}: its third block row (the multiplier block, all the hGS sweeps read) on the
+  // main stream, the first two ahead of the Chebyshev blocks on their branch
+  const int64_t F2 = 2 * pb->F;
+  SGOC_LAUNCH(launch_minres_v<T>(m.Kz + F2, m.v + F2, m.vp + F2, N - F2, L.k64.state, st));
   if (f) SGOC_TRY(fork_to(sw, st, f->e[7]));
-  SGOC_TRY(precond_apply<T>(pb, prec_of<T>(L), m.vp, m.zn, st, f));
+  SGOC_TRY(precond_apply<T>(pb, prec_of<T>(L), m.vp, m.zn, st, f, [&](cudaStream_t sc) -> sgoc_status {
+    SGOC_LAUNCH(launch_minres_v<T>(m.Kz, m.v, m.vp, F2, L.k64.state, sc));
+    return SGOC_OK;
+  }));
   SGOC_LAUNCH(launch_dot_partial<T>(m.vp, m.zn, N, L.k64.partial, st));
   SGOC_LAUNCH(launch_minres_rotate(L.k64.state, L.k64.partial, st));
   return SGOC_OK;
