@@ -556,11 +556,16 @@ static sgoc_status runtime_of(sgoc_problem* pb, Runtime** out) {
     pb->runtime = rt;
     SGOC_CUDA_TRY(cudaMallocHost(&rt->hstate, sizeof(MinresState)));
     SGOC_CUDA_TRY(cudaMallocHost(&rt->hscal, 16 * sizeof(double)));
-    SGOC_CUDA_TRY(cudaStreamCreateWithFlags(&rt->cap, cudaStreamNonBlocking));
+    // the iteration's critical chain is captured on a high-priority stream, its side branches
+    // (Chebyshev blocks, deferred w/x update, KKT block rows 2 and 3) on low-priority ones; the
+    // graphs keep these priorities, so concurrent solves schedule critical kernels first
+    int least = 0, greatest = 0;
+    SGOC_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    SGOC_CUDA_TRY(cudaStreamCreateWithPriority(&rt->cap, cudaStreamNonBlocking, greatest));
     SGOC_CUDA_TRY(cudaEventCreateWithFlags(&rt->ev, cudaEventDisableTiming));
-    SGOC_CUDA_TRY(cudaStreamCreateWithFlags(&rt->fork.s1, cudaStreamNonBlocking));
-    SGOC_CUDA_TRY(cudaStreamCreateWithFlags(&rt->fork.s2, cudaStreamNonBlocking));
-    SGOC_CUDA_TRY(cudaStreamCreateWithFlags(&rt->fork.s3, cudaStreamNonBlocking));
+    SGOC_CUDA_TRY(cudaStreamCreateWithPriority(&rt->fork.s1, cudaStreamNonBlocking, least));
+    SGOC_CUDA_TRY(cudaStreamCreateWithPriority(&rt->fork.s2, cudaStreamNonBlocking, least));
+    SGOC_CUDA_TRY(cudaStreamCreateWithPriority(&rt->fork.s3, cudaStreamNonBlocking, least));
     for (auto& e : rt->fork.e) SGOC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
   *out = static_cast<Runtime*>(pb->runtime);
@@ -659,7 +664,7 @@ static sgoc_status ensure_graphs(sgoc_problem* pb, Runtime& rt, Layout& L, const
       if (g) cudaGraphDestroy(g);
       return cuda_status(ce != cudaSuccess ? ce : ee, "iteration graph capture");
     }
-    cudaError_t ie = cudaGraphInstantiate(&rt.it[par], g, 0);
+    cudaError_t ie = cudaGraphInstantiateWithFlags(&rt.it[par], g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     SGOC_TRY(cuda_status(ie, "cudaGraphInstantiate"));
     rt.nk[par] = nk;
