@@ -2094,8 +2094,9 @@ __device__ __forceinline__ void vt_level_pass(const T* __restrict__ xs, T* __res
 
 // One level of the cycle (coarse levels L >= 1): pre-smoothing, residual, restriction,
 // the coarser levels, prolongation, post-smoothing.  Returns the buffer holding x.
-template <typename T, int N1, int L>
-__device__ int vt_coarse(T* base, const VFLevel<T>* lv, int nu) {
+template <typename T, int N1, int L, int NU>
+__device__ int vt_coarse(T* base, const VFLevel<T>* lv, int nu_arg) {
+  const int nu = NU > 0 ? NU : nu_arg;
   using G = VT<N1>;
   constexpr int N = G::n1(L);
   constexpr int NT = G::grp(L);
@@ -2143,7 +2144,7 @@ __device__ int vt_coarse(T* base, const VFLevel<T>* lv, int nu) {
     vt_restrict<T, N, NT>(rbuf, bc);
     vt_sync<NT>();
     int ccur = 0;
-    if (threadIdx.x < G::grp(L + 1)) ccur = vt_coarse<T, N1, L + 1>(base, lv, nu);
+    if (threadIdx.x < G::grp(L + 1)) ccur = vt_coarse<T, N1, L + 1, NU>(base, lv, nu);
     vt_sync<NT>();
     // the coarse result's buffer index is the same in every thread of the coarse group; share it
     __shared__ int cbuf;
@@ -2506,13 +2507,15 @@ template <typename T, int N1>
 using VtLevel0Of = typename std::conditional<std::is_same<T, float>::value && N1 >= 127, VtLevel0Split<N1>,
                                              VtLevel0<T, N1>>::type;
 
-template <typename T, int N1>
+template <typename T, int N1, int NU>
 __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 : kVFThreads / VT<N1>::nb()) vcycle_t_kernel(const T* __restrict__ bg, T* xg, FusedLevels L,
-                                                                 T omega, int nu, T* acc, int64_t acc_ss, int acc_L,
+                                                                 T omega, int nu_arg, T* acc, int64_t acc_ss, int acc_L,
                                                                  int acc_col0) {
   using G = VT<N1>;
   constexpr int NL = G::nlev();
   constexpr int S0 = N1 + 2;
+  // smoothing sweeps: fixed at compile time in the NU > 0 instantiation (no code for other counts)
+  const int nu = NU > 0 ? NU : nu_arg;
   extern __shared__ __align__(32) unsigned char vt_smem_raw[];
   __shared__ VFLevel<T> lv[13];
   T* base = reinterpret_cast<T*>(vt_smem_raw);
@@ -2577,7 +2580,7 @@ __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 :
       vt_restrict<T, N1, NT0>(rbuf, base + G::off(1) + 2 * G::np(1));
       vt_sync<NT0>();
       int ccur = 0;
-      if (threadIdx.x < G::grp(1)) ccur = vt_coarse<T, N1, 1>(base, lv, nu);
+      if (threadIdx.x < G::grp(1)) ccur = vt_coarse<T, N1, 1, NU>(base, lv, nu);
       vt_sync<NT0>();
       __shared__ int cbuf0;
       if (threadIdx.x == 0) cbuf0 = ccur;
@@ -2632,10 +2635,12 @@ template <typename T, int N1>
 static cudaError_t launch_vt(const T* b, T* x, int64_t B, const FusedLevels& L, T omega, int nu, T* acc,
                              int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st) {
   const size_t smem = size_t(VT<N1>::total()) * sizeof(T);
-  cudaError_t e = allow_max_smem(vcycle_t_kernel<T, N1>);
+  // V(2,2), the cycle of every solve, has an instantiation of its own; other sweep counts share one
+  auto k = nu == 2 ? vcycle_t_kernel<T, N1, 2> : vcycle_t_kernel<T, N1, 0>;
+  cudaError_t e = allow_max_smem(k);
   if (e != cudaSuccess) return e;
   {
-    const cudaError_t le_ = launch_pdl(vcycle_t_kernel<T, N1>, (dim3(unsigned(B))), dim3(VT<N1>::nb()), size_t(smem), st,
+    const cudaError_t le_ = launch_pdl(k, (dim3(unsigned(B))), dim3(VT<N1>::nb()), size_t(smem), st,
                                       b, x, L, omega, nu, acc, acc_ss, acc_L, acc_col0);
     if (le_ != cudaSuccess) return le_;
   }
