@@ -70,8 +70,8 @@ def load_peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 SG_KERNEL_NAMES = {0: "one-phase", 1: "quad-32", 2: "quad-16", 3: "two-phase", 4: "quad-32x4", 5: "quad-16x4",
                    6: "direct", -1: "none"}
-# ncu: vcycle_t_kernel<float, 127>, 56 columns: 3,698,432 B read + 0 B written
-VCYCLE_DRAM_BYTES_PER_COLUMN = 3705088 / 56
+# ncu: vcycle_t_kernel<float, 127, 2>, 56 columns: 3,681,536 B read + 0 B written
+VCYCLE_DRAM_BYTES_PER_COLUMN = 3681536 / 56
 # float32 non-tensor peak: 152 SMs x 128 FMA/clk x 2 flop x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
