@@ -2685,7 +2685,7 @@ cudaError_t launch_vcycle_full(const T* b, T* x, int64_t B, const FusedLevels& L
 
 // ---------------------------------------------------------------------------
 // Cluster V-cycle: one thread-block cluster of C CTAs per column.  The fine
-// levels ("distributed", band height B_l = (n1_l + 1) / C >= kMinBand rows)
+// levels ("distributed", band height B_l = (n1_l + 1) / C of at least 8 rows)
 // are split into horizontal bands, one per CTA; each band array carries one
 // halo row above and below, filled from the neighbouring CTAs' shared memory
 // (DSMEM) after a cluster barrier whenever a pass reads neighbours.  The first
@@ -2695,7 +2695,6 @@ cudaError_t launch_vcycle_full(const T* b, T* x, int64_t B, const FusedLevels& L
 // row B is the Dirichlet boundary and stays zero.
 // ---------------------------------------------------------------------------
 constexpr int kVCThreads = 512;
-constexpr int kMinBand = 8;
 constexpr int kCStrip = 16;
 
 template <typename T>

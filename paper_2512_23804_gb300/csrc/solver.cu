@@ -572,23 +572,6 @@ static sgoc_status runtime_of(sgoc_problem* pb, Runtime** out) {
   return SGOC_OK;
 }
 
-static sgoc_status sync_state(Runtime& rt, const Layout& L, cudaStream_t st) {
-  SGOC_CUDA_TRY(cudaMemcpyAsync(rt.hstate, L.k64.state, sizeof(MinresState), cudaMemcpyDeviceToHost, st));
-  pdl_fence(st);
-  SGOC_CUDA_TRY(cudaStreamSynchronize(st));
-  return SGOC_OK;
-}
-
-static sgoc_status norm2(Runtime& rt, const double* a, int64_t n, const Layout& L, double* out, cudaStream_t st) {
-  SGOC_LAUNCH(launch_dot_partial<double>(a, a, n, L.k64.partial, st));
-  SGOC_LAUNCH(launch_sum_partials(L.k64.partial, L.k64.scal, st));
-  SGOC_CUDA_TRY(cudaMemcpyAsync(rt.hscal, L.k64.scal, sizeof(double), cudaMemcpyDeviceToHost, st));
-  pdl_fence(st);
-  SGOC_CUDA_TRY(cudaStreamSynchronize(st));
-  *out = std::sqrt(rt.hscal[0]);
-  return SGOC_OK;
-}
-
 // MINRES start: v_1 = rhs, z_1 = P^{-1} v_1, beta_1 = sqrt(v_1 . z_1), w = 0.
 template <typename T>
 static sgoc_status minres_start(const sgoc_problem* pb, Layout& L, const MinresVecs<T>& m, const T* rhs,
@@ -674,21 +657,6 @@ static sgoc_status ensure_graphs(sgoc_problem* pb, Runtime& rt, Layout& L, const
   return SGOC_OK;
 }
 
-// Run one iteration of parity `par` on `st` and bring the scalar state to the host.
-template <typename T, typename TX>
-static sgoc_status run_step(sgoc_problem* pb, Runtime& rt, Layout& L, bool graphs, int par, TX* x, cudaStream_t st) {
-  if (graphs) {
-    SGOC_CUDA_TRY(cudaGraphLaunch(rt.it[par], st));
-    pdl_fence(st);
-    add_launches(rt.nk[par]);
-    SGOC_CUDA_TRY(cudaStreamSynchronize(st));
-    return SGOC_OK;
-  }
-  const MinresVecs<T>& m = vecs_of<T>(L);
-  SGOC_TRY((minres_step<T, TX>(pb, L, par == 0 ? m : swapped(m), x, st)));
-  return sync_state(rt, L, st);
-}
-
 static sgoc_status state_error(const MinresState& hs) {
   if (hs.flag == 4) { set_error("NaN in MINRES recurrences"); return SGOC_ERR_NAN; }
   if (hs.flag == 3) { set_error("preconditioner not positive definite"); return SGOC_ERR_NOT_SPD; }
@@ -722,16 +690,6 @@ static sgoc_status check_ws(void* ws, size_t bytes, size_t need) {
   if (bytes < need) { set_error("workspace too small: need " + std::to_string(need)); return SGOC_ERR_WORKSPACE_TOO_SMALL; }
   if (need && !ws) { set_error("null workspace"); return SGOC_ERR_INVALID_ARG; }
   if (reinterpret_cast<uintptr_t>(ws) % 256) { set_error("workspace must be 256-byte aligned"); return SGOC_ERR_INVALID_ARG; }
-  return SGOC_OK;
-}
-
-// true float64 residual r = b - K x and its relative norm
-static sgoc_status true_residual(sgoc_problem* pb, Runtime& rt, const Layout& L, double bnorm, double* rel,
-                                 double* rn, cudaStream_t st) {
-  SGOC_TRY(kkt_apply<double>(pb, L.k64.x, L.k64.t, st));
-  SGOC_LAUNCH(launch_sub(L.k64.b, L.k64.t, L.k64.r, pb->N, st));
-  SGOC_TRY(norm2(rt, L.k64.r, pb->N, L, rn, st));
-  *rel = *rn / bnorm;
   return SGOC_OK;
 }
 
