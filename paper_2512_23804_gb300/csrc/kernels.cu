@@ -1072,15 +1072,17 @@ __device__ __forceinline__ void mass_row(const T* __restrict__ V, int ix, int y,
   h = (ix > 0 ? row[ix - 1] : T(0)) + (ix + 1 < n1 ? row[ix + 1] : T(0));
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128) mass_kernel(MassArgs<T> a, int strips, int64_t nwork) {
+// TX: nodes per tile row (= threads per CTA): 128, or 64 / 32 on narrower grids so that
+// no thread and no staged column is idle
+template <typename T, int TX>
+__global__ void __launch_bounds__(TX) mass_kernel(MassArgs<T> a, int strips, int64_t nwork) {
   pdl_enter();
-  // tile of the inputs: rows y0-1 .. y0+kMassRows, columns x0-1 .. x0+128 (zero outside the grid)
-  constexpr int TW = 128 + 2, TH = kMassRows + 2;
+  // tile of the inputs: rows y0-1 .. y0+kMassRows, columns x0-1 .. x0+TX (zero outside the grid)
+  constexpr int TW = TX + 2, TH = kMassRows + 2;
   __shared__ T Vs[3][TH][TW];
   const int n1 = a.n1;
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * 128;
+  const int x0 = blockIdx.x * TX;
   const int ix = x0 + tid;
   for (int64_t w = blockIdx.y; w < nwork; w += gridDim.y) {
     const int strip = int(w % strips);
@@ -1097,7 +1099,7 @@ __global__ void __launch_bounds__(128) mass_kernel(MassArgs<T> a, int strips, in
       const int ts = t + a.shift[j];
       if (ts < 0 || ts >= a.nslabs) continue;
       const T* V = a.V[j] + int64_t(ts) * a.vs[j] + int64_t(c) * a.n;
-      for (int q = tid; q < TH * TW; q += 128) {
+      for (int q = tid; q < TH * TW; q += TX) {
         const int r = q / TW, xx = q - r * TW;
         const int gy = y0 - 1 + r, gx = x0 - 1 + xx;
         Vs[j][r][xx] = (gy >= 0 && gy < n1 && gx >= 0 && gx < n1) ? V[int64_t(gy) * n1 + gx] : T(0);
@@ -1156,13 +1158,17 @@ cudaError_t launch_mass(const MassArgs<T>& a, cudaStream_t st) {
   const double w = sizeof(T);
   ProfScope ps(KK_MASS, st, w * total * (a.nv + 1 + (a.cy != T(0) ? 1 : 0) + (a.R ? 1 : 0)),
                double(total) * (20.0 * a.nv + 2.0));
-  const int tx = 128;                                   // one 128-node tile per CTA and strip
+  // one tile of tx nodes per CTA and strip: the narrowest of 128 / 64 / 32 that spans a row
+  // (or 128 on wider grids)
+  const int tx = a.n1 <= 32 ? 32 : a.n1 <= 64 ? 64 : 128;
   const int strips = (a.n1 + kMassRows - 1) / kMassRows;
   const int64_t nwork = int64_t(strips) * a.ncols * a.nslabs;
   const dim3 grid(unsigned((a.n1 + tx - 1) / tx), unsigned(nwork < 65535 ? nwork : 65535));
   {
-    const cudaError_t le_ = launch_pdl(mass_kernel<T>, dim3(grid), dim3(tx), size_t(0), st,
-                                      a, strips, nwork);
+    const cudaError_t le_ =
+        tx == 32 ? launch_pdl(mass_kernel<T, 32>, dim3(grid), dim3(tx), size_t(0), st, a, strips, nwork)
+        : tx == 64 ? launch_pdl(mass_kernel<T, 64>, dim3(grid), dim3(tx), size_t(0), st, a, strips, nwork)
+                   : launch_pdl(mass_kernel<T, 128>, dim3(grid), dim3(tx), size_t(0), st, a, strips, nwork);
     if (le_ != cudaSuccess) return le_;
   }
   note_launch();
