@@ -21,6 +21,7 @@ import os
 # hardware work queues; the runtime default of 8 serialises concurrent solves against each other
 os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 import argparse
+import datetime
 import json
 import math
 import statistics
@@ -77,7 +78,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
+    """nvidia-smi clock/throttle sampling, started before the warm-up so that it is running when the
+    timed region starts; stop() keeps the samples whose timestamps fall inside [t0, t1]."""
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
@@ -88,16 +90,16 @@ class ClockSampler:
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
-            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+            q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -105,23 +107,28 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f")
+                rows.append((ts, float(f[2]), float(f[3]), f[6:10]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
         os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        inside = [r for r in rows if t0 is None or (t0 <= r[0] <= t1)]
+        window = "timed region"
+        if not inside:                         # region shorter than the sampling interval
+            inside = [min(rows, key=lambda r: abs((r[0] - t0).total_seconds()))] if rows and t0 else rows
+            window = "nearest sample"
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = {nm for r in inside for nm, v in zip(names, r[3]) if v.lower().startswith("active")}
+        sm = [r[1] for r in inside]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(r[2] for r in inside) if inside else None,
+                "reasons": sorted(reasons), "samples": len(sm), "window": window}
 
 
 def dist_info():
@@ -242,6 +249,8 @@ def run_ours(args):
         _, infos = solve_batch(sps, outs=xs, streams=streams)
         return infos
 
+    sampler = ClockSampler(local)
+    sampler.start()                            # running before the timed region starts
     for _ in range(args.warmup):
         flush.fill_(1.0)
         step()
@@ -249,8 +258,7 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
+    t_region0 = datetime.datetime.now()
     l0 = lib.sgoc_kernel_launches()
     step_ms, solve_ms, iters, outer, resid = [], [], [], [], []
     for _ in range(args.steps):
@@ -272,7 +280,7 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clocks = sampler.stop()
+    clocks = sampler.stop(t_region0, datetime.datetime.now())
     total_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
