@@ -599,11 +599,11 @@ template <typename T, typename TX>
 static sgoc_status minres_step(const sgoc_problem* pb, Layout& L, const MinresVecs<T>& m, TX* x, cudaStream_t st,
                                const Fork* f) {
   const int64_t N = pb->N;
-  // The w/x update of the previous iteration runs here, beside the KKT product: its
+  // The w/x update of the previous iteration j runs here, beside the KKT product: its
   // coefficients stay in the state until this iteration's rotation, and its operands in
-  // this iteration's roles are z_prev = zn, w_prev = wm2 (read), w_prev-1 = wm1 (overwritten).
-  // It joins before the preconditioner, which overwrites zn.  (The update of the last
-  // iteration is applied by the caller, prev_wx, when the iteration loop ends.)
+  // this iteration's roles are z_j = zn, w_{j-1} = wm2 (read) and w_{j-2} = wm1 (overwritten
+  // by w_j).  It joins before the preconditioner, which overwrites zn.  (The update of the
+  // last iteration is applied by the caller, prev_wx, when the iteration loop ends.)
   cudaStream_t sw = f ? f->s3 : st;
   if (f) SGOC_TRY(fork_to(st, sw, f->e[6]));
   SGOC_TRY((prev_wx<T, TX>(pb, L, m, x, sw)));
