@@ -107,28 +107,39 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 10:
-                continue
-            try:
-                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f")
-                rows.append((ts, float(f[2]), float(f[3]), f[6:10]))
-            except ValueError:
-                continue
+        lines = open(self.path).read().splitlines()
         os.unlink(self.path)
-        inside = [r for r in rows if t0 is None or (t0 <= r[0] <= t1)]
-        window = "timed region"
-        if not inside:                         # region shorter than the sampling interval
-            inside = [min(rows, key=lambda r: abs((r[0] - t0).total_seconds()))] if rows and t0 else rows
-            window = "nearest sample"
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = {nm for r in inside for nm, v in zip(names, r[3]) if v.lower().startswith("active")}
-        sm = [r[1] for r in inside]
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(r[2] for r in inside) if inside else None,
-                "reasons": sorted(reasons), "samples": len(sm), "window": window}
+        return parse_clock_samples(lines, t0, t1)
+
+
+THROTTLE_NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+
+def parse_clock_samples(lines, t0=None, t1=None):
+    """Summary of nvidia-smi CSV rows (timestamp, index, clocks.sm, clocks.max.sm, power.draw,
+    event-reason mask, the four reasons): the median SM clock, the maximum, and the throttle
+    reasons active in the samples taken inside [t0, t1] (all samples without a window; the
+    sample nearest t0 when none falls inside)."""
+    rows = []
+    for line in lines:
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 10:
+            continue
+        try:
+            ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f")
+            rows.append((ts, float(f[2]), float(f[3]), f[6:10]))
+        except ValueError:
+            continue
+    inside = [r for r in rows if t0 is None or (t0 <= r[0] <= t1)]
+    window = "timed region"
+    if not inside:                             # region shorter than the sampling interval
+        inside = [min(rows, key=lambda r: abs((r[0] - t0).total_seconds()))] if rows and t0 else rows
+        window = "nearest sample"
+    reasons = {nm for r in inside for nm, v in zip(THROTTLE_NAMES, r[3]) if v.lower().startswith("active")}
+    sm = [r[1] for r in inside]
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(r[2] for r in inside) if inside else None,
+            "reasons": sorted(reasons), "samples": len(sm), "window": window}
 
 
 def dist_info():
