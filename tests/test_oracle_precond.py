@@ -71,10 +71,11 @@ def test_galerkin_coarse_equals_coarse_discretisation(nx):
     assert np.max(np.abs(Ac - ref)) < 1e-13
 
 
+@pytest.mark.parametrize("nu", [1, 2, 3])
 @pytest.mark.parametrize("nx,s", [(16, 10.0), (32, 1000.0), (8, 0.0)])
-def test_vcycle_symmetric_and_converges_to_direct(nx, s):
+def test_vcycle_symmetric_and_converges_to_direct(nx, s, nu):
     A = fe.assemble(nx, np.ones((nx, nx))) + s * fe.mass(nx)
-    V = VCycle(A, nx)
+    V = VCycle(A, nx, nu, nu)
     rng = np.random.default_rng(1)
     v, w = rng.standard_normal((2, A.shape[0]))
     assert abs(v @ V.apply(w) - w @ V.apply(v)) <= 1e-13 * abs(v @ V.apply(w))
