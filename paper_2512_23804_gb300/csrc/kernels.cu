@@ -2516,7 +2516,7 @@ using VtLevel0Of = typename std::conditional<std::is_same<T, float>::value && N1
 template <typename T, int N1, int NU>
 __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 : kVFThreads / VT<N1>::nb()) vcycle_t_kernel(const T* __restrict__ bg, T* xg, FusedLevels L,
                                                                  T omega, int nu_arg, T* acc, int64_t acc_ss, int acc_L,
-                                                                 int acc_col0) {
+                                                                 int acc_col0, VColumns cols) {
   using G = VT<N1>;
   constexpr int NL = G::nlev();
   constexpr int S0 = N1 + 2;
@@ -2527,9 +2527,11 @@ __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 :
   T* base = reinterpret_cast<T*>(vt_smem_raw);
   const int64_t col = blockIdx.x;
   constexpr int n0 = N1 * N1;
-  // the column's output: x itself, or the accumulator column x is added to
-  const bool acc_on = acc != nullptr;
-  T* gout = acc_on ? acc + (col / acc_L) * acc_ss + (acc_col0 + col % acc_L) * int64_t(n0) : xg + col * n0;
+  // the column's right-hand side, and its output: x itself, or the strided column x is
+  // added to (or stored into)
+  const T* bcol = cols.b_L > 0 ? bg + (col / cols.b_L) * cols.b_ss + (col % cols.b_L) * int64_t(n0) : bg + col * n0;
+  const bool acc_on = acc != nullptr && cols.acc_add;
+  T* gout = acc != nullptr ? acc + (col / acc_L) * acc_ss + (acc_col0 + col % acc_L) * int64_t(n0) : xg + col * n0;
   // level constants, by the last warp (which has the least border work)
   if (threadIdx.x >= G::nb() - 32 && threadIdx.x < G::nb() - 32 + NL) {
     const int l = threadIdx.x - (G::nb() - 32);
@@ -2556,7 +2558,7 @@ __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 :
   }
   pdl_wait();                                        // b and the output are shared with earlier kernels
   VtLevel0Of<T, N1> z;
-  z.init(bg + col * n0);
+  z.init(bcol);
   __syncthreads();
   T* xa = base;
   T* xb = base + G::np(0);
@@ -2639,7 +2641,7 @@ __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 :
 
 template <typename T, int N1>
 static cudaError_t launch_vt(const T* b, T* x, int64_t B, const FusedLevels& L, T omega, int nu, T* acc,
-                             int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st) {
+                             int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st, VColumns cols) {
   const size_t smem = size_t(VT<N1>::total()) * sizeof(T);
   // V(2,2), the cycle of every solve, has an instantiation of its own; other sweep counts share one
   auto k = nu == 2 ? vcycle_t_kernel<T, N1, 2> : vcycle_t_kernel<T, N1, 0>;
@@ -2647,7 +2649,7 @@ static cudaError_t launch_vt(const T* b, T* x, int64_t B, const FusedLevels& L, 
   if (e != cudaSuccess) return e;
   {
     const cudaError_t le_ = launch_pdl(k, (dim3(unsigned(B))), dim3(VT<N1>::nb()), size_t(smem), st,
-                                      b, x, L, omega, nu, acc, acc_ss, acc_L, acc_col0);
+                                      b, x, L, omega, nu, acc, acc_ss, acc_L, acc_col0, cols);
     if (le_ != cudaSuccess) return le_;
   }
   return cudaGetLastError();
@@ -2668,7 +2670,7 @@ bool vcycle_full_fits(const FusedLevels& L, int esize) {
 
 template <typename T>
 cudaError_t launch_vcycle_full(const T* b, T* x, int64_t B, const FusedLevels& L, T omega, int nu, T* acc,
-                               int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st) {
+                               int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st, VColumns cols) {
   if (B == 0) return cudaSuccess;
   if (!vcycle_full_fits(L, sizeof(T))) return cudaErrorInvalidConfiguration;
   const double n0 = double(L.n1[0]) * L.n1[0];
@@ -2676,13 +2678,13 @@ cudaError_t launch_vcycle_full(const T* b, T* x, int64_t B, const FusedLevels& L
                double(B) * n0 * (4.0 / 3.0) * (21.0 * 2 * nu + 18.0 + 10.0));
   cudaError_t e;
   switch (L.n1[0]) {
-    case 1: e = launch_vt<T, 1>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st); break;
-    case 3: e = launch_vt<T, 3>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st); break;
-    case 7: e = launch_vt<T, 7>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st); break;
-    case 15: e = launch_vt<T, 15>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st); break;
-    case 31: e = launch_vt<T, 31>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st); break;
-    case 63: e = launch_vt<T, 63>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st); break;
-    case 127: e = launch_vt<T, 127>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st); break;
+    case 1: e = launch_vt<T, 1>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols); break;
+    case 3: e = launch_vt<T, 3>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols); break;
+    case 7: e = launch_vt<T, 7>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols); break;
+    case 15: e = launch_vt<T, 15>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols); break;
+    case 31: e = launch_vt<T, 31>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols); break;
+    case 63: e = launch_vt<T, 63>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols); break;
+    case 127: e = launch_vt<T, 127>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols); break;
     default: return cudaErrorInvalidConfiguration;
   }
   note_launch();
@@ -3495,7 +3497,7 @@ cudaError_t launch_fill(T* x, int64_t n, T v, cudaStream_t st) {
   template cudaError_t launch_prolong_add<T>(const T*, T*, int64_t, int, cudaStream_t);                            \
   template cudaError_t launch_scale<T>(const T*, T*, int64_t, T, cudaStream_t);                                    \
   template cudaError_t launch_vcycle_full<T>(const T*, T*, int64_t, const FusedLevels&, T, int, T*, int64_t, int,  \
-                                             int, cudaStream_t);                                                   \
+                                             int, cudaStream_t, VColumns);                                                   \
   template cudaError_t launch_vcycle_cluster<T>(const T*, T*, int64_t, const ClusterLevels&, int, T, int, T*,      \
                                                 int64_t, int, int, cudaStream_t);                                  \
   template cudaError_t launch_dot_partial<T>(const T*, const T*, int64_t, double*, cudaStream_t);                  \

@@ -134,10 +134,15 @@ cudaError_t launch_vcycle_cluster(const T* b, T* x, int64_t B, const ClusterLeve
 
 // Full-hierarchy V-cycle (top level read from global memory, register-blocked
 // sweeps, 1024 threads): usable when vcycle_full_fits(L, sizeof(T)).
+// Column layouts beyond the compact [column][node] one: with b_L > 0 right-hand-side
+// column c is read at b + (c / b_L) b_ss + (c % b_L) n; with acc the result of column c
+// goes to acc + (c / acc_L) acc_ss + (acc_col0 + c % acc_L) n, added (acc_add) or stored.
+struct VColumns { int64_t b_ss = 0; int b_L = 0; int acc_add = 1; };
 bool vcycle_full_fits(const FusedLevels& L, int esize);
 template <typename T>
 cudaError_t launch_vcycle_full(const T* b, T* x, int64_t B, const FusedLevels& L, T omega, int nu,
-                               T* acc, int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st);
+                               T* acc, int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st,
+                               VColumns cols = VColumns());
 
 // Krylov kernels.  Reductions are deterministic: fixed grid, fixed order.
 constexpr int kDotBlocks = 608;

@@ -125,9 +125,10 @@ size_t precond_workspace_bytes(const sgoc_problem* pb, int esize) {
 // One V(nu, nu) cycle for B columns of rhs `b` (compact [col][node] at level 0).
 // With acc != nullptr the correction is added to the chaos columns of V
 // (column col of the batch is slab col / acc_L, chaos column acc_col0 + col % acc_L).
+// cols: strided right-hand side / stored strided output (VColumns), on the single-CTA path only
 template <typename T>
 static sgoc_status vcycle(const sgoc_problem* pb, PrecWS<T>& w, const T* b, T* xout, int64_t B, T* acc,
-                          int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st) {
+                          int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st, VColumns cols = VColumns()) {
   const int nl = int(pb->levels.size());
   const T om = T(pb->opt.omega);
   const int nu = pb->opt.nu_pre;
@@ -144,9 +145,13 @@ static sgoc_status vcycle(const sgoc_problem* pb, PrecWS<T>& w, const T* b, T* x
     FL.corner[l - lf] = CL.corner[l - lf] = pb->levels[l].corner;
   }
   if (!vp.cluster && !vcycle_full_fits(FL, sizeof(T))) { set_error("internal: V-cycle level does not fit"); return SGOC_ERR_UNSUPPORTED; }
+  if ((cols.b_L > 0 || !cols.acc_add) && (lf != 0 || vp.cluster)) {
+    set_error("internal: strided V-cycle columns need the single-CTA cycle");
+    return SGOC_ERR_UNSUPPORTED;
+  }
   auto fused = [&](const T* bb, T* xx, T* ac, int64_t ss, int aL, int ac0) -> cudaError_t {
     if (vp.cluster) return launch_vcycle_cluster<T>(bb, xx, B, CL, vp.C, om, nu, ac, ss, aL, ac0, st);
-    return launch_vcycle_full<T>(bb, xx, B, FL, om, nu, ac, ss, aL, ac0, st);
+    return launch_vcycle_full<T>(bb, xx, B, FL, om, nu, ac, ss, aL, ac0, st, cols);
   };
   if (lf == 0) {
     SGOC_LAUNCH(fused(b, xout, acc, acc_ss, acc_L, acc_col0));
@@ -278,25 +283,36 @@ template <typename T>
 static sgoc_status hgs(const sgoc_problem* pb, PrecWS<T>& w, const T* R, T* V, int slabs, cudaStream_t st) {
   const int P = pb->P, p = pb->p;
   const int64_t n = pb->n, ps = int64_t(P) * n;
-  // With one slab a level's columns of V are contiguous: the first visit of each level
-  // stores its correction there (levels are never read before their first visit), so V
-  // needs no zero fill.  With several slabs the corrections are added into a zeroed V.
+  // The first visit of each level stores its correction (levels are never read before their
+  // first visit), so V needs no zero fill: with one slab a level's columns are contiguous;
+  // with several, the single-CTA V-cycle stores into the strided layout.  Otherwise (several
+  // slabs on the cluster or level-wise cycle) the corrections are added into a zeroed V.
   const bool one = slabs == 1;
-  if (!one) SGOC_LAUNCH(launch_fill<T>(V, slabs * ps, T(0), st));
+  const VPlan vp = plan_vcycle(pb, sizeof(T));
+  const bool strided = vp.lf == 0 && !vp.cluster;
+  if (!one && !strided) SGOC_LAUNCH(launch_fill<T>(V, slabs * ps, T(0), st));
   // palindromic sweep 0, 1, ..., p, ..., 1, 0: the first visit of each level, then the returns
   for (int step = 0; step < 2 * p + 1; ++step) {
     const bool first = step <= p;
     const int d = first ? step : 2 * p - step;
     const int a0 = pb->off[d], L = pb->off[d + 1] - a0;
-    // the first visit of level 0 has no couplings: its right-hand side is R_0 itself,
-    // which for one slab is a contiguous column the V-cycle reads in place
+    // the first visit of level 0 has no couplings: its right-hand side is R_0 itself, read in
+    // place by the V-cycle (a contiguous column with one slab, slab-strided columns otherwise)
     const T* rhs = w.RH;
-    if (first && d == 0 && one) rhs = R;
-    else
+    VColumns cols;
+    if (first && d == 0 && (one || strided)) {
+      rhs = R;
+      if (!one) { cols.b_L = 1; cols.b_ss = ps; }
+    } else {
       SGOC_LAUNCH(launch_sg<T>(first ? hgs_args_first<T>(pb, w, R, V, slabs, d) : hgs_args<T>(pb, w, R, V, slabs, d),
                                st));
-    if (first && one) SGOC_TRY(vcycle<T>(pb, w, rhs, V + int64_t(a0) * n, L, nullptr, 0, 1, 0, st));
-    else SGOC_TRY(vcycle<T>(pb, w, rhs, nullptr, int64_t(slabs) * L, V, ps, L, a0, st));
+    }
+    if (first && one) {
+      SGOC_TRY(vcycle<T>(pb, w, rhs, V + int64_t(a0) * n, L, nullptr, 0, 1, 0, st, cols));
+    } else {
+      if (first && strided) cols.acc_add = 0;       // store (V was not zero-filled)
+      SGOC_TRY(vcycle<T>(pb, w, rhs, nullptr, int64_t(slabs) * L, V, ps, L, a0, st, cols));
+    }
   }
   return SGOC_OK;
 }
