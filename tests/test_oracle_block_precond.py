@@ -1,0 +1,211 @@
+"""Pins of the oracle's block preconditioner against dense constructions.
+
+The block preconditioner of the paper is P = blkdiag(K11, K22, S) where K11 and
+K22 are the (1,1) and (2,2) blocks of the KKT matrix (Sec. 2, Eq. (stoch-prec);
+Sec. 3, Eq. (precon for time)) and S approximates the Schur complement
+S_exact = K31 K11^{-1} K31^T + K32 K22^{-1} K32^T.  Every matrix below is read off
+the explicitly assembled KKT matrix (itself pinned by the M = 0 reduction and the
+optimality residuals), not retyped from the oracle's preconditioner:
+
+* Z_bar = -K31 + s K32 with s = sqrt((1+gamma)/beta): the steady Z of
+  Eq. (mathcalZ) (K31 = -A, K32 = M_cal) and the time Z_bar of Eq. (S hat)
+  (K31 = -A_t, K32 = tau N).
+* Z_tilde = the part of Z_bar that is block-diagonal in time (dropping the
+  -C (x) M_cal coupling gives Eq. (Z hat approx)); steady, Z_tilde = Z.
+* S_tilde = (1/tau) Z_tilde (D (x) M_gamma)^{-1} Z_tilde (Eq. (S_tilde) with the 1/tau
+  of Eq. (S hat)) = Z_tilde K11^{-1} Z_tilde because K11 = tau D (x) M_gamma; steady
+  (tau = 1, D = I) this is S = Z M_gamma^{-1} Z of Eq. (stoch-prec).
+* One hGS sweep with exact mean solves applies Z_hGS^{-1} with
+  Z_hGS = (X1 + Xr) X1^{-1} (X1 + Xr^T) (Sec. 4), X1 the level-diagonal blocks of
+  Z_tilde and Xr its strictly level-lower part (truncated to the first r terms).
+
+The oracle's apply() must then equal blkdiag(K11, K22, Z_hGS K11^{-1} Z_hGS)^{-1} r
+when the Chebyshev mass solves are run to convergence (1/T_N(1/rho) < 1e-17 at
+N = 60).  Spectral pins tie the scalars to the paper's theorems: Thm. approx
+(lambda(S_bar^{-1} S_exact) in [1/(2(1+alpha)), 1)) and the theorem that bounds
+lambda(S_bar^{-1} S_tilde) by (1 -+ theta)^2 with theta its defined supremum.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import sg_inputs as si
+from oracle import basis
+from oracle.operators import SGData
+from oracle.precond import BlockPreconditioner
+
+
+def _problem(nt, gamma, sigma, r, seed=11, M=2, p=2, nx=4, beta=1e-2):
+    pr = si.random_small(seed, nx=nx, M=M, p=p, nt=nt, beta=beta, sigma=sigma, gamma=gamma)
+    pr.r = r
+    pr.cheb_steps = 60
+    if nt:
+        pr.T = 0.75            # tau = 0.25 for nt = 3: tau, 1/tau and tau^2 all differ from 1
+    return pr
+
+
+def _blocks(d):
+    K = d.kkt_matrix().toarray()
+    F = d.slabs * d.P * d.n
+    K11, K22 = K[:F, :F], K[F:2 * F, F:2 * F]
+    K31, K32 = K[2 * F:, :F], K[2 * F:, F:2 * F]
+    assert np.array_equal(K[:F, 2 * F:], K31.T) and np.array_equal(K[F:2 * F, 2 * F:], K32.T)
+    assert not K[2 * F:, 2 * F:].any() and not K[:F, F:2 * F].any()
+    return F, K11, K22, K31, K32
+
+
+def _time_block_diag(Z, d):
+    nP = d.P * d.n
+    out = np.zeros_like(Z)
+    for t in range(d.slabs):
+        s = slice(t * nP, (t + 1) * nP)
+        out[s, s] = Z[s, s]
+    return out
+
+
+def _z_hgs(Zt, d, r):
+    """Z_hGS of the symmetric hierarchical block Gauss-Seidel sweep (Sec. 4) for the
+    time-block-diagonal Z_tilde, with couplings kept for the first r terms only."""
+    n, P = d.n, d.P
+    off = basis.level_offsets(d.M, d.p)
+    lev = np.zeros(P, dtype=int)
+    for dd in range(d.p + 1):
+        lev[off[dd]:off[dd + 1]] = dd
+    # which chaos pairs a term k < r couples: alpha and beta differ by e_k with k < r
+    idx = basis.multi_indices(d.M, d.p)
+    keep = np.zeros((P, P), dtype=bool)
+    for a in range(P):
+        for b in range(P):
+            diff = idx[a].astype(int) - idx[b].astype(int)
+            nz = np.nonzero(diff)[0]
+            if len(nz) == 1 and abs(diff[nz[0]]) == 1 and nz[0] + 1 < r:
+                keep[a, b] = True
+    nP = n * P
+    Zh = np.zeros_like(Zt)
+    for t in range(d.slabs):
+        base = t * nP
+        blk = Zt[base:base + nP, base:base + nP]
+        X1 = np.zeros_like(blk)
+        Xr = np.zeros_like(blk)
+        for a in range(P):
+            for b in range(P):
+                B = blk[a * n:(a + 1) * n, b * n:(b + 1) * n]
+                if a == b:
+                    X1[a * n:(a + 1) * n, b * n:(b + 1) * n] = B
+                elif lev[a] > lev[b] and keep[a, b]:
+                    Xr[a * n:(a + 1) * n, b * n:(b + 1) * n] = B
+        Zh[base:base + nP, base:base + nP] = (X1 + Xr) @ np.linalg.solve(X1, X1 + Xr.T)
+    return Zh
+
+
+CASES = [
+    # nt, gamma, sigma, r
+    (0, 0.0, 0.0, 3),        # sigma = 0: Z_tilde = I (x) A~_1, the sweep is exact
+    (0, 0.5, 0.3, 1),        # mean-based truncation r = 1, gamma != 0
+    (0, 0.5, 0.3, 3),        # full hierarchical sweep r = M + 1
+    (3, 0.0, 0.0, 3),        # time: Z_tilde = I (x) I (x) A^_1
+    (3, 0.7, 0.3, 3),        # time, gamma != 0, full sweep
+    (3, 0.0, 0.3, 2),        # time, truncated
+]
+
+
+@pytest.mark.parametrize("nt,gamma,sigma,r", CASES)
+def test_block_preconditioner_equals_dense_definition(nt, gamma, sigma, r):
+    pr = _problem(nt, gamma, sigma, r)
+    d = SGData(pr)
+    F, K11, K22, K31, K32 = _blocks(d)
+    s = math.sqrt((1.0 + gamma) / pr.beta)
+    Zbar = -K31 + s * K32
+    Zt = _time_block_diag(Zbar, d)
+    Zh = _z_hgs(Zt, d, r)
+    if sigma == 0.0:                         # no couplings: the sweep is Z_tilde^{-1} itself
+        assert np.allclose(Zh, Zt, rtol=0, atol=1e-12 * np.abs(Zt).max())
+    S3 = Zh @ np.linalg.solve(K11, Zh)
+    Pc = BlockPreconditioner(d, mode="exact")
+    rng = np.random.default_rng(7)
+    for _ in range(2):
+        rv = rng.standard_normal(3 * F)
+        z = Pc.apply(rv)
+        ref = np.concatenate([np.linalg.solve(K11, rv[:F]), np.linalg.solve(K22, rv[F:2 * F]),
+                              np.linalg.solve(S3, rv[2 * F:])])
+        for blk in range(3):
+            sl = slice(blk * F, (blk + 1) * F)
+            err = np.linalg.norm(z[sl] - ref[sl]) / np.linalg.norm(ref[sl])
+            assert err <= 1e-11, (blk, err)
+
+
+def test_steady_schur_approximation_bounds_with_kkt_blocks():
+    """Steady, gamma = 0: lambda(S^{-1} S_exact) in [1/2, 1] for S = Z M^{-1} Z (the n_t = 1
+    case of Thm. approx), with Z and S_exact read off the assembled KKT matrix.  The oracle's
+    block 3 as an explicit matrix (exact mean solves, sigma != 0, r = M + 1) must be symmetric
+    positive definite."""
+    pr = _problem(0, 0.0, 0.3, 3)
+    d = SGData(pr)
+    F, K11, K22, K31, K32 = _blocks(d)
+    Sx = K31 @ np.linalg.solve(K11, K31.T) + K32 @ np.linalg.solve(K22, K32.T)
+    s = math.sqrt(1.0 / pr.beta)
+    Z = -K31 + s * K32
+    S = Z @ np.linalg.solve(K11, Z)
+    ev = np.sort(np.linalg.eigvals(np.linalg.solve(S, Sx)).real)
+    assert ev[0] >= 0.5 - 1e-10 and ev[-1] <= 1 + 1e-10
+    assert ev[-1] >= 0.9 and ev[0] <= 0.6          # the interval is (nearly) attained
+    # the oracle's block 3 (Z replaced by Z_hGS) as an explicit matrix
+    Pc = BlockPreconditioner(d, mode="exact")
+    S3inv = np.stack([Pc.apply(np.concatenate([np.zeros(2 * F), e]))[2 * F:]
+                      for e in np.eye(F)], axis=1)
+    assert np.allclose(S3inv, S3inv.T, rtol=0, atol=1e-12 * np.abs(S3inv).max())
+    assert np.linalg.eigvalsh(0.5 * (S3inv + S3inv.T)).min() > 0
+
+
+def _theta(Zt, Cm, W):
+    """theta = sup_v ||W^{1/2} Cm^T v|| / ||W^{1/2} Zt^T v|| (definition in the paper's
+    theorem relating S_bar and S_tilde), as a generalized eigenvalue problem."""
+    A = Cm @ W @ Cm.T
+    B = Zt @ W @ Zt.T
+    ev = np.linalg.eigvals(np.linalg.solve(B, A)).real
+    return math.sqrt(max(ev.max(), 0.0))
+
+
+@pytest.mark.parametrize("gamma", [0.0, 0.7])
+def test_time_schur_scalars_follow_the_paper_theorems(gamma):
+    """Time mode (Sec. 3-4): with W = (1/tau)(D (x) M_gamma)^{-1} = K11^{-1},
+    (i) Thm. approx: lambda(S_bar^{-1} S_exact) in [1/(2(1+alpha)), 1) with
+        S_bar = Z_bar W Z_bar^T and alpha below ((sqrt k + 1)/(sqrt k - 1))^2 - 1,
+        k = cond(A_t);
+    (ii) (1 - theta)^2 <= lambda(S_bar^{-1} S_tilde) <= (1 + theta)^2 with
+        S_tilde = Z_tilde W Z_tilde;
+    (iii) the oracle's block 3 with exact mean solves and sigma = 0 is S_tilde^{-1}.
+    A wrong power of tau in W, or a missing 1 + gamma, moves the spectrum in (i) by
+    a factor 1/tau = 4 or (1+gamma) and fails the bound."""
+    pr = _problem(3, gamma, 0.0, 3, beta=1e-1)
+    d = SGData(pr)
+    F, K11, K22, K31, K32 = _blocks(d)
+    tau = d.tau
+    assert tau == pytest.approx(0.25)
+    Sx = K31 @ np.linalg.solve(K11, K31.T) + K32 @ np.linalg.solve(K22, K32.T)
+    s = math.sqrt((1.0 + gamma) / pr.beta)
+    W = np.linalg.inv(K11)
+    Zbar = -K31 + s * K32
+    Sbar = Zbar @ W @ Zbar.T
+    At = -K31
+    sv = np.linalg.svd(At, compute_uv=False)
+    kap = sv[0] / sv[-1]
+    alpha_sup = ((math.sqrt(kap) + 1) / (math.sqrt(kap) - 1)) ** 2 - 1
+    ev = np.sort(np.linalg.eigvals(np.linalg.solve(Sbar, Sx)).real)
+    assert ev[-1] <= 1 + 1e-10
+    assert ev[0] >= 1 / (2 * (1 + alpha_sup)) - 1e-10
+    Zt = _time_block_diag(Zbar, d)
+    Cm = Zt - Zbar                          # C (x) M_cal, the dropped coupling
+    assert np.abs(Cm).max() > 0
+    theta = _theta(Zt, Cm, W)
+    St = Zt @ W @ Zt
+    ev2 = np.sort(np.linalg.eigvals(np.linalg.solve(Sbar, St)).real)
+    if theta < 1:
+        assert ev2[0] >= (1 - theta) ** 2 - 1e-10
+    assert ev2[-1] <= (1 + theta) ** 2 + 1e-10
+    Pc = BlockPreconditioner(d, mode="exact")
+    rv = np.random.default_rng(3).standard_normal(F)
+    z3 = Pc.apply(np.concatenate([np.zeros(2 * F), rv]))[2 * F:]
+    ref = np.linalg.solve(St, rv)
+    assert np.linalg.norm(z3 - ref) <= 1e-11 * np.linalg.norm(ref)
