@@ -51,9 +51,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in SG kernel choice")
     ap.add_argument("--serve", action="store_true",
                     help="serving stream: the first --requests seeded requests through the server")
-    ap.add_argument("--requests", type=int, default=40)
-    ap.add_argument("--max-unknowns", type=float, default=6e7,
-                    help="serving: skip requests with more KKT unknowns (device memory and run time)")
+    ap.add_argument("--requests", type=int, default=2000, help="serving stream length with --serve")
+    ap.add_argument("--serve-requests", type=int, default=100,
+                    help="serving leg of the default run: the first N requests of the stream (0: skip)")
     ap.add_argument("--kernel-case", choices=["vcycle128", "sg128", "sg512", "hgs128", "solve128"], default=None,
                     help="run one kernel class a few times on a small case (for ncu captures) and exit")
     return ap.parse_args()
@@ -150,24 +150,31 @@ def dist_info():
 
 
 # ---------------------------------------------------------------- oracle arm --
-def oracle_sample(beta, iters):
-    """Time oracle set-up + `iters` MINRES iterations of one solve; returns (seconds, full-solve estimate)."""
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def blas_threads():
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k):
+            return int(os.environ[k])
+    return host_cores()
+
+
+def oracle_full_solve(beta):
+    """One complete float64 oracle solve of the 128x128 workload (set-up, right-hand side,
+    preconditioner construction and preconditioned MINRES to the 1e-8 rule); returns
+    (seconds, iterations, true relative residual)."""
     import sg_inputs as si
-    from oracle.krylov import minres
-    from oracle.operators import SGData
-    from oracle.precond import BlockPreconditioner
+    from oracle.solve import solve
     t0 = time.perf_counter()
-    pr = si.steady_128(beta)
-    d = SGData(pr)
-    Pc = BlockPreconditioner(d)
-    b = d.rhs()
-    t1 = time.perf_counter()
-    minres(d.kkt_apply, Pc.apply, b, tol=pr.tol, max_iter=iters)
-    t2 = time.perf_counter()
-    return t1 - t0, (t2 - t1) / iters
+    res = solve(si.steady_128(beta))
+    return time.perf_counter() - t0, res.iterations, res.rel_true
 
 
 def oracle_iterations():
+    """Iteration counts of the oracle's complete solves stored with the test data (used only to
+    size the reference arm's steps before its own solves complete)."""
     path = os.path.join(ROOT, "tests", "golden", "full_size_oracle.json")
     out = {}
     if os.path.exists(path):
@@ -179,42 +186,126 @@ def oracle_iterations():
     return out
 
 
-def cpu_baseline_value(iters_sample=3, betas=(1e-4,), gpu_iters=None):
-    its = oracle_iterations()
-    total_s, parts = 0.0, []
-    for b in betas:
-        t_setup, t_it = oracle_sample(b, iters_sample)
-        n_it = its.get(b) or (gpu_iters or {}).get(b) or 40
-        parts.append((b, t_setup, t_it, n_it))
-        total_s += t_setup + t_it * n_it
-    per_solve = total_s / len(betas)
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    sample = "; ".join(f"beta={b:g}: set-up {ts:.1f}s + {iters_sample} MINRES iterations at {ti:.2f}s, "
-                       f"scaled to the oracle's {n} iterations" for b, ts, ti, n in parts)
-    return 1.0 / per_solve, cores, sample
+def cpu_baseline_full(beta=1e-2):
+    sec, its, rel = oracle_full_solve(beta)
+    return {"value": 1.0 / sec, "unit": UNIT, "cores": host_cores(), "blas_threads": blas_threads(),
+            "kind": "oracle",
+            "sample": f"one complete oracle solve of the 128x128 workload at beta={beta:g} ({its} MINRES "
+                      f"iterations, true residual {rel:.2e}) in {sec:.1f} s, set-up included"}
+
+
+class OracleStream:
+    """Complete oracle solves of the workload run back to back (beta cycling through the three
+    values) in a worker thread; the oracle itself is unchanged.  Each KKT product the oracle's
+    MINRES asks for waits for a permit, so the caller advances the running solve by a chosen
+    number of Krylov iterations at a time and times exactly that work (the set-up of a new
+    solve falls into the step that first needs it)."""
+
+    def __init__(self, betas):
+        import threading
+        self.betas = betas
+        self.sem = threading.Semaphore(0)
+        self.cv = threading.Condition()
+        self.products = 0
+        self.cur = 0
+        self.completed = []                    # (beta, iterations, products, seconds)
+        self.stop = False
+        self.error = None
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def _run(self):
+        import sg_inputs as si
+        from oracle.krylov import minres
+        from oracle.operators import SGData
+        from oracle.precond import BlockPreconditioner
+        i = 0
+        try:
+            while not self.stop:
+                beta = self.betas[i % len(self.betas)]
+                i += 1
+                t0 = time.perf_counter()
+                pr = si.steady_128(beta)
+                d = SGData(pr)
+                Pc = BlockPreconditioner(d)
+                b = d.rhs()
+
+                def apply_A(v, d=d):
+                    self.sem.acquire()
+                    if self.stop:
+                        raise SystemExit
+                    y = d.kkt_apply(v)
+                    with self.cv:
+                        self.products += 1
+                        self.cur += 1
+                        self.cv.notify_all()
+                    return y
+
+                res = minres(apply_A, Pc.apply, b, tol=pr.tol, max_iter=pr.max_iter)
+                with self.cv:
+                    self.completed.append((beta, res.iterations, self.cur, time.perf_counter() - t0))
+                    self.cur = 0
+        except SystemExit:
+            pass
+        except Exception as e:                  # reported by advance()
+            with self.cv:
+                self.error = repr(e)
+                self.cv.notify_all()
+
+    def advance(self, k):
+        with self.cv:
+            goal = self.products + k
+        for _ in range(k):
+            self.sem.release()
+        with self.cv:
+            self.cv.wait_for(lambda: self.products >= goal or self.error is not None)
+            if self.error:
+                raise RuntimeError(self.error)
+
+    def close(self):
+        self.stop = True
+        for _ in range(4):
+            self.sem.release()
 
 
 def run_reference(args):
     world, rank, _ = dist_info()
     if rank != 0:
         return
-    betas = (1e-2, 1e-4, 1e-6)
-    vals = []
-    for s in range(args.warmup + args.steps):
-        b = betas[s % 3]
-        v, cores, sample = cpu_baseline_value(iters_sample=2, betas=(b,))
-        if s >= args.warmup:
-            vals.append(1.0 / v)
-    sec_per_solve = sum(vals) / len(vals)
-    value = 1.0 / sec_per_solve
+    its = oracle_iterations()
+    mean_its = sum(its.values()) / len(its) if its else 41.0
+    # each timed step advances the running oracle solve by `chunk` KKT products (one per MINRES
+    # iteration, one per true-residual check); the timed steps cover at least one whole solve
+    chunk = max(1, math.ceil((mean_its + 2) / max(args.steps, 1)))
+    stream = OracleStream((1e-2, 1e-4, 1e-6))
+    for _ in range(args.warmup):
+        stream.advance(1)
+    p0 = stream.products
+    step_s = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        stream.advance(chunk)
+        step_s.append(time.perf_counter() - t0)
+    products = stream.products - p0
+    done = list(stream.completed)
+    stream.close()
+    per_solve = (sum(c[2] for c in done) / len(done)) if done else mean_its + 1
+    total_s = sum(step_s)
+    solves = products / per_solve
+    value = solves / total_s
+    sample = (f"{args.steps} steps of {chunk} KKT products each ({products} in all, {solves:.2f} solves at "
+              f"{per_solve:.1f} products per complete solve) of complete oracle solves run back to back "
+              f"(beta 1e-2, 1e-4, 1e-6 in turn, set-up included); solves completed so far: "
+              + ", ".join(f"beta={b:g} {it} iterations {sec:.1f} s" for b, it, _, sec in done))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 3e3 * sec_per_solve,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "solves_per_step": 3},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": "each step: set-up + 2 MINRES iterations of one beta, scaled to the "
-                                   "oracle's full iteration count"},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "solves_per_step": solves / args.steps,
+                   "step": f"{chunk} KKT products of the running oracle solve"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "blas_threads": blas_threads(),
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -333,11 +424,13 @@ def run_ours(args):
         q1.record(stream)
         torch.cuda.synchronize()
         line["sequential_solves_per_s"] = 3 / (q0.elapsed_time(q1) / 1e3)
-        # plain float64 path (same solves), for the mixed-vs-fp64 comparison
+        # plain float64 path (same solves), for the mixed-vs-fp64 comparison: the error of every
+        # mixed solution of the step against the float64 GPU solution of the same problem
         if args.precision == "mixed":
+            xmix = [x.clone() for x in xs]
             sp64 = [SGProblem.from_problem(pr, precision="fp64").upload() for pr in problems]
-            t64, it64 = [], []
-            for sp, x in zip(sp64, xs):
+            t64, it64, err = [], [], []
+            for sp, x, xm in zip(sp64, xs, xmix):
                 sp.solve(out=x)                    # warm
                 flush.fill_(1.0)
                 e0 = torch.cuda.Event(enable_timing=True)
@@ -348,9 +441,11 @@ def run_ours(args):
                 torch.cuda.synchronize()
                 t64.append(e0.elapsed_time(e1))
                 it64.append(info["iterations"])
+                err.append(float(torch.linalg.norm(xm - x) / torch.linalg.norm(x)))
                 sp.release_workspace()
             line["fp64_path"] = {"solves_per_s": 3 / (sum(t64) / 1e3), "ms_per_solve": t64, "iterations": it64}
-            del sp64
+            line["iterations"]["mixed_vs_fp64_rel_error"] = err
+            del sp64, xmix
 
         # end to end through the public API: host arrays in, host solution out
         pin = [torch.empty(sp.kkt_size, dtype=torch.float64, pin_memory=True) for sp in sps]
@@ -396,14 +491,17 @@ def run_ours(args):
         roof["launches"] = dv["launches"]
         roof["avg_launch_us"] = 1e3 * dv["ms"] / dv["launches"]
         pr_main = problems[0]
-        if dom == "mg_vcycle_fused" and not esize_fp64 and pr_main.nx == 128:
-            # DRAM bytes per column from the ncu capture of this kernel on 56 columns of the
-            # 128x128 workload (profiles/vcycle_128x128_f32.md), times the average columns per
-            # launch here (each hGS launch reads b and reads + writes the output: 3 x 4 B per node)
+        if dom == "mg_vcycle_fused" and not esize_fp64 and pr_main.nx == 128 and VCYCLE_DRAM_BYTES_PER_COLUMN:
+            # DRAM bytes per column from an ncu capture of this kernel on 56 columns of the
+            # 128x128 workload, times the average columns per launch here (each hGS launch reads
+            # b and reads + writes the output: 3 x 4 B per node)
             cols = dv["bytes"] / dv["launches"] / (3 * 4 * pr_main.n)
             roof["traffic"] = VCYCLE_DRAM_BYTES_PER_COLUMN * cols
             roof["traffic_note"] = f"ncu DRAM bytes per column x {cols:.1f} columns per launch"
         line["roofline"] = roof
+        line["kernel_breakdown_note"] = ("summed device time per kernel class of an eager sequential pass of "
+                                         "the three solves (CUDA events around every launch; overlapping "
+                                         "branches counted separately), not a share of the timed step")
         line["kernel_breakdown"] = {k: {"share": round(v["share"], 4), "launches": v["launches"],
                                         "ms": round(v["ms"], 3),
                                         "GB/s": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1)}
@@ -451,6 +549,7 @@ def run_ours(args):
                          ("steady_512x512_M8_p3", si.steady_512)):
             pr = mk()
             rec = {"kkt_unknowns": pr.kkt_size}
+            xkeep = {}
             for prec in ("mixed", "fp64"):
                 sp = SGProblem.from_problem(pr, precision=prec).upload()
                 if not args.no_autotune:
@@ -466,14 +565,21 @@ def run_ours(args):
                 ms = e0.elapsed_time(e1)
                 rec[prec] = {"ms": ms, "solves_per_s": 1e3 / ms, "iterations": info["iterations"],
                              "outer": info["outer_iterations"], "rel_residual": info["rel_true_residual"]}
-                del sp, x
+                xkeep[prec] = x
+                del sp
                 torch.cuda.empty_cache()
+            rec["mixed_vs_fp64_rel_error"] = float(torch.linalg.norm(xkeep["mixed"] - xkeep["fp64"]) /
+                                                   torch.linalg.norm(xkeep["fp64"]))
+            del xkeep
+            torch.cuda.empty_cache()
             ow[name] = rec
         line["other_workloads"] = ow
 
+    if not args.no_extras and rank == 0 and args.serve_requests > 0:
+        line["serving"] = serve_leg(args.serve_requests)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, sample = cpu_baseline_value(iters_sample=3, betas=(1e-4,))
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        line["cpu_baseline"] = cpu_baseline_full(1e-2)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -517,78 +623,97 @@ def run_kernel_case(args):
     print(json.dumps({"kernel_case": case, "ok": True}))
 
 
-def run_serve(args):
-    """Serving stream: requests arrive as a Poisson process (rate calibrated at 80% of
-    the saturated throughput), are admitted by memory footprint, and are solved to a
-    1e-8 float64 residual in mixed precision; reported beside sequential float64
-    solves of the same requests on the same GPU."""
+def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16):
+    """Serving stream: the first `n_requests` seeded requests (grids 32..256, M 2..8, p 1..4,
+    30 % time-dependent), admitted by the server's own memory-footprint check (a request that
+    cannot fit the pool even when empty is rejected by sgoc_server_submit and counted), solved to a
+    1e-8 float64 residual in mixed precision.  Run once with every request arriving at t = 0
+    (capacity mu), then as a Poisson stream at 0.8 mu; compared with sequential plain float64
+    solves of the same requests on the same GPU, and each mixed result with its float64 one."""
     import numpy as np
     import torch
     import sg_inputs as si
-    from paper_2512_23804_gb300 import SGProblem, SGServer, build
-    build.build()
-    reqs, skipped = [], 0
-    i = 0
-    while len(reqs) < args.requests:
-        pr = si.serving_request(i)
-        i += 1
-        if pr.kkt_size > args.max_unknowns:
-            skipped += 1
-            continue
-        reqs.append(pr)
-    pool_bytes = int(min(torch.cuda.mem_get_info()[0] * 0.6, 120e9))
+    from paper_2512_23804_gb300 import SGProblem, SGServer, abi
+    reqs = [si.serving_request(i) for i in range(n_requests)]
+    pool_bytes = int(min(torch.cuda.mem_get_info()[0] * 0.6, pool_cap_bytes))
 
-    def run_stream(arrivals, label):
-        sv = SGServer(pool_bytes=pool_bytes, max_active=16)
+    def run_stream(arrivals, keep):
+        sv = SGServer(pool_bytes=pool_bytes, max_active=max_active)
         sps = [SGProblem.from_problem(pr, precision="mixed") for pr in reqs]
-        done, lat = {}, {}
+        done, lat, rejected, xs = {}, {}, [], {}
         t0 = time.perf_counter()
         nxt = 0
-        while len(done) < len(reqs):
+        while len(done) + len(rejected) < len(reqs):
             now = time.perf_counter() - t0
             while nxt < len(reqs) and arrivals[nxt] <= now:
-                sv.submit(sps[nxt], nxt)
+                try:
+                    sv.submit(sps[nxt], nxt)
+                except abi.SgocError as e:
+                    if e.status != abi.SGOC_ERR_WORKSPACE_TOO_SMALL:
+                        raise
+                    rejected.append(nxt)
                 nxt += 1
             if sv.pending == 0:
-                time.sleep(max(0.0, min(arrivals[nxt] - now, 0.01)))
+                if nxt < len(reqs):
+                    time.sleep(max(0.0, min(arrivals[nxt] - now, 0.01)))
                 continue
             sv.step()
             for rid, x, info in sv.poll():
                 assert info["status_name"] == "SGOC_OK" and info["rel_true_residual"] <= 1e-8, info
                 done[rid] = info
                 lat[rid] = info["ms_total"]
+                if keep:
+                    xs[rid] = x
         wall = time.perf_counter() - t0
         stats = sv.stats()
+        del sv, sps
         l = sorted(lat.values())
-        return {"solves_per_s": len(reqs) / wall, "wall_s": wall,
-                "p50_ms": l[len(l) // 2], "p99_ms": l[min(len(l) - 1, int(math.ceil(0.99 * len(l))) - 1)],
-                "pool_high_water_GB": stats["pool_high_water"] / 1e9, "admitted": stats["admitted"]}
+        rec = {"solves_per_s": len(done) / wall, "wall_s": wall, "completed": len(done),
+               "rejected": len(rejected), "rejected_ids": rejected,
+               "p50_ms": l[len(l) // 2], "p99_ms": l[min(len(l) - 1, int(math.ceil(0.99 * len(l))) - 1)],
+               "pool_high_water_GB": stats["pool_high_water"] / 1e9, "admitted": stats["admitted"]}
+        return rec, xs, rejected
 
-    # saturation: everything arrives at t = 0 -> capacity mu
-    sat = run_stream([0.0] * len(reqs), "saturated")
+    sat, xmix, rejected = run_stream([0.0] * len(reqs), keep=True)      # capacity mu
     mu = sat["solves_per_s"]
     rng = np.random.default_rng([5, 2**31])            # the arrival stream of master seed 5
     gaps = rng.exponential(1.0 / (0.8 * mu), size=len(reqs))
     arrivals = list(np.cumsum(gaps) - gaps[0])
-    open_loop = run_stream(arrivals, "poisson")
-    # sequential plain float64 solves of the same requests
+    open_loop, _, _ = run_stream(arrivals, keep=False)
+    torch.cuda.empty_cache()
+    # sequential plain float64 solves of the same (admitted) requests
     torch.cuda.synchronize()
+    seq_lat, errs = [], []
     t0 = time.perf_counter()
-    seq_lat = []
-    for pr in reqs:
+    for i, pr in enumerate(reqs):
+        if i in rejected:
+            continue
         sp = SGProblem.from_problem(pr, precision="fp64")
         t1 = time.perf_counter()
         x, info = sp.solve()
         seq_lat.append((time.perf_counter() - t1) * 1e3)
+        errs.append(float(torch.linalg.norm(xmix[i] - x) / torch.linalg.norm(x)))
         del sp, x
     seq_wall = time.perf_counter() - t0
+    del xmix
+    torch.cuda.empty_cache()
     sl = sorted(seq_lat)
-    line = {"mode": "serve", "requests": len(reqs), "skipped_over_cap": skipped,
-            "max_unknowns": args.max_unknowns, "saturated": sat, "poisson_at_0.8mu": open_loop,
-            "sequential_fp64": {"solves_per_s": len(reqs) / seq_wall,
-                                "p50_ms": sl[len(sl) // 2], "p99_ms": sl[-1]},
-            "speedup_vs_sequential_fp64": sat["solves_per_s"] / (len(reqs) / seq_wall)}
-    print(json.dumps(line), flush=True)
+    seq = {"solves_per_s": len(sl) / seq_wall, "p50_ms": sl[len(sl) // 2],
+           "p99_ms": sl[min(len(sl) - 1, int(math.ceil(0.99 * len(sl))) - 1)]}
+    return {"requests": len(reqs), "pool_GB": pool_bytes / 1e9, "max_active": max_active,
+            "solves_per_s": sat["solves_per_s"], "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"],
+            "rejected": sat["rejected"], "saturated": sat, "poisson_at_0.8mu": open_loop,
+            "sequential_fp64": seq, "vs_sequential_fp64": sat["solves_per_s"] / seq["solves_per_s"],
+            "mixed_vs_fp64_rel_error": {"max": max(errs), "median": statistics.median(errs)}}
+
+
+def run_serve(args):
+    import torch
+    from paper_2512_23804_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    rec = serve_leg(args.requests)
+    print(json.dumps(dict(mode="serve", **rec)), flush=True)
 
 
 def main():

@@ -261,15 +261,19 @@ sgoc_status sgoc_apply_chebyshev(sgoc_problem* pb, int32_t precision, const void
                                  void* stream);
 
 /* Same result as sgoc_apply_chebyshev, for callers that cannot allocate device
- * memory when they need the solve (for instance code running while a CUDA graph
- * is being captured, or a plug-in whose host framework owns all device memory):
- * it takes no workspace.  Its two iterate buffers live in a 16 MiB array built
- * into the library, which every GPU that loads the library keeps until the
- * process exits; ncols * n * sizeof(element) must not exceed 8 MiB, larger
- * requests return SGOC_ERR_INVALID_ARG.  The first call on a device looks up the
- * array's device address with that device current; make that first call before
- * any stream capture.  All calls share the array: calls whose kernels overlap on
- * the GPU race and must be serialized by the caller.  Allocates nothing.
+ * memory at the point where they need the solve (for instance a plug-in whose
+ * host framework owns all device memory and hands out only the input and output
+ * buffers, or a real-time path that forbids allocation after start-up): it
+ * takes no workspace.  Its two iterate buffers live in a 16 MiB array built into
+ * the library, which every GPU that loads the library keeps until the process
+ * exits; ncols * n * sizeof(element) must not exceed 8 MiB, larger requests
+ * return SGOC_ERR_INVALID_ARG, and so does a call on a device other than the one
+ * the problem was uploaded to.  The first call on a device looks up the array's
+ * device address with that device current and keeps it for the life of the
+ * process (a cudaDeviceReset invalidates it); make that first call before any
+ * stream capture.  All calls share the array and every call writes each value
+ * it reads from it before reading it: calls whose kernels overlap on the GPU
+ * race and must be serialized by the caller.  Allocates nothing.
  * The paper has no counterpart of this entry point. */
 sgoc_status sgoc_apply_chebyshev_noalloc(sgoc_problem* pb, int32_t precision, const void* d_R,
                                          void* d_X, int32_t ncols, void* stream);

@@ -3073,30 +3073,34 @@ __global__ void __launch_bounds__(256) dot_kernel(const T* __restrict__ a, const
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// float32 operands: the four products of a float4 pair are summed in float32
-// and that partial sum is accumulated in float64 (one conversion and one
-// float64 add per four entries; float64 arithmetic runs at 1/64 of the float32
-// rate on this part).  The order is fixed by the grid, so results are reproducible.
+// float32 operands, float64 inner product: each product of two float32 values is
+// exact in float64 (24 + 24 significant bits), so every product is formed and
+// accumulated in float64 (one float64 FMA per entry).  The Krylov inner products
+// of the mixed-precision solve are thus float64 sums of exact products of the
+// float32 vectors.  The order is fixed by the grid, so results are reproducible.
 __global__ void __launch_bounds__(256) dot4_kernel(const float4* __restrict__ a, const float4* __restrict__ b,
                                                    int64_t n4, const float* __restrict__ at,
                                                    const float* __restrict__ bt, int tail, double* partial) {
   pdl_enter();
   double s = 0.0;
   const int64_t stride = int64_t(kDotBlocks) * 256;
-  auto prod = [](const float4& x, const float4& y) {
-    return fmaf(x.w, y.w, fmaf(x.z, y.z, fmaf(x.y, y.y, x.x * y.x)));
+  auto acc = [](const float4& x, const float4& y, double t) {
+    t = fma(double(x.x), double(y.x), t);
+    t = fma(double(x.y), double(y.y), t);
+    t = fma(double(x.z), double(y.z), t);
+    return fma(double(x.w), double(y.w), t);
   };
   int64_t i = blockIdx.x * int64_t(256) + threadIdx.x;
   // four strides' loads in flight before their (in-order) accumulation
   for (; i + 3 * stride < n4; i += 4 * stride) {
     const float4 x0 = a[i], y0 = b[i], x1 = a[i + stride], y1 = b[i + stride];
     const float4 x2 = a[i + 2 * stride], y2 = b[i + 2 * stride], x3 = a[i + 3 * stride], y3 = b[i + 3 * stride];
-    s += double(prod(x0, y0));
-    s += double(prod(x1, y1));
-    s += double(prod(x2, y2));
-    s += double(prod(x3, y3));
+    s = acc(x0, y0, s);
+    s = acc(x1, y1, s);
+    s = acc(x2, y2, s);
+    s = acc(x3, y3, s);
   }
-  for (; i < n4; i += stride) s += double(prod(a[i], b[i]));
+  for (; i < n4; i += stride) s = acc(a[i], b[i], s);
   if (blockIdx.x == 0 && threadIdx.x < tail) s = fma(double(at[threadIdx.x]), double(bt[threadIdx.x]), s);
   s = block_sum<256>(s);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;

@@ -1,18 +1,19 @@
 // Chebyshev mass solve that needs no caller-provided scratch.
 //
 // Some callers cannot allocate device memory at the point where they need this
-// solve: code running while a CUDA graph is being captured (cudaMalloc is not
-// allowed then), plug-ins hosted by a framework that owns all device memory and
-// hands out only the buffers it chose, or real-time paths that forbid
-// allocation after start-up.  This entry point takes only its input and output
-// buffers; its two iterate buffers live in a fixed file-scope device array.
+// solve: plug-ins hosted by a framework that owns all device memory and hands
+// out only the buffers it chose, or real-time paths that forbid allocation after
+// start-up.  This entry point takes only its input and output buffers; its two
+// iterate buffers live in a fixed file-scope device array.
 //
 // The array is kNoAllocScratchBytes (16 MiB) on every GPU that loads the
 // library and stays allocated until the process exits.  All calls share it:
 // two calls whose kernels overlap on the GPU (different streams, or different
 // host threads) race on it and give wrong results, so serialize them.  Every
 // value a call reads from the array was written earlier in the same call, so no
-// clearing is needed between calls.
+// clearing is needed between calls.  The array's device address is looked up
+// once per device (first call with that device current) and cached for the
+// life of the process; a cudaDeviceReset invalidates the cached address.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -59,6 +60,18 @@ static sgoc_status cheb_noalloc(sgoc_problem* pb, const void* d_R, void* d_X, in
     set_error("sgoc_apply_chebyshev_noalloc: ncols * n * sizeof(element) = " + std::to_string(per) +
               " bytes exceeds the limit of " + std::to_string(kNoAllocScratchBytes / 2) +
               " bytes (half of the 16 MiB built-in scratch)");
+    return SGOC_ERR_INVALID_ARG;
+  }
+  // the problem's device data must live on the current device, whose scratch array is used
+  int dev = 0;
+  cudaError_t ge = cudaGetDevice(&dev);
+  if (ge != cudaSuccess) { set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(ge)); return SGOC_ERR_CUDA; }
+  cudaPointerAttributes attr{};
+  ge = cudaPointerGetAttributes(&attr, pb->dev.kap64);
+  if (ge != cudaSuccess) { set_error(std::string("cudaPointerGetAttributes: ") + cudaGetErrorString(ge)); return SGOC_ERR_CUDA; }
+  if (attr.type == cudaMemoryTypeDevice && attr.device != dev) {
+    set_error("sgoc_apply_chebyshev_noalloc: the problem was uploaded to device " + std::to_string(attr.device) +
+              " but device " + std::to_string(dev) + " is current");
     return SGOC_ERR_INVALID_ARG;
   }
   void* base = nullptr;

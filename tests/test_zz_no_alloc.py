@@ -1,12 +1,16 @@
 """The allocation-free Chebyshev entry point gives the same result as the
-workspace-taking one.
+workspace-taking one and as the oracle's Chebyshev semi-iteration.
 
 sgoc_apply_chebyshev_noalloc exists for callers that cannot allocate device
-memory when they need the mass solve (e.g. during CUDA graph capture, or inside
-a host framework that owns all device memory); it keeps its iterate buffers in
-an array built into the library.  This file is collected last so that a run
-stopping at the first failure has already run every other test; it also passes
-on its own in a fresh process.
+memory when they need the mass solve (for instance a plug-in inside a host
+framework that owns all device memory, or a real-time path that forbids
+allocation after start-up); it keeps its iterate buffers in an array built into
+the library.  The float64 cases and the float32 case on 255 x 255 interior
+nodes run the per-step kernel, which ping-pongs its iterates through both halves
+of that array; the float32 case on 63 x 63 nodes runs the fused kernel, which
+keeps them in shared memory.  This file is collected last so that a run stopping
+at the first failure has already run every other test; it also passes on its
+own in a fresh process.
 """
 import ctypes
 
@@ -35,14 +39,23 @@ def _noalloc(sp, R, X, ncols):
                                                    ctypes.c_void_p(X.data_ptr()), ncols, st)
 
 
-@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-6)])
-def test_noalloc_matches_workspace_entry_point_twice(dtype, tol):
+@pytest.mark.parametrize("nx,dtype,tol", [(64, torch.float64, 1e-12), (64, torch.float32, 2e-6),
+                                          (256, torch.float64, 1e-12), (256, torch.float32, 2e-6)])
+def test_noalloc_matches_workspace_entry_point_twice(nx, dtype, tol):
     from paper_2512_23804_gb300 import SGProblem, abi
-    pr = si.random_small(31, nx=64, M=3, p=3)
+    from oracle.operators import SGData
+    from oracle.precond import chebyshev
+    M, p = (3, 3) if nx == 64 else (2, 1)
+    pr = si.random_small(31, nx=nx, M=M, p=p)
     sp = SGProblem.from_problem(pr).upload()
+    mass = SGData(pr).Mass
     ncols = 2 * sp.P
+    assert ncols * sp.n * (8 if dtype == torch.float64 else 4) <= 8 << 20
     for call in range(2):                         # two calls in a row share the built-in array
-        R = torch.from_numpy(si.random_panel(40 + call, sp.n, ncols)).to("cuda", dtype)
+        Rh = si.random_panel(40 + call, sp.n, ncols)
+        if dtype == torch.float32:
+            Rh = Rh.astype(np.float32).astype(np.float64)
+        R = torch.from_numpy(Rh).to("cuda", dtype)
         ref = sp.apply_chebyshev(R, ncols)
         X = torch.full_like(R, float("nan"))
         st = _noalloc(sp, R, X, ncols)
@@ -50,6 +63,9 @@ def test_noalloc_matches_workspace_entry_point_twice(dtype, tol):
         torch.cuda.synchronize()
         err = (torch.linalg.norm((X - ref).double()) / torch.linalg.norm(ref.double())).item()
         assert err <= tol, (call, err)
+        Xo = chebyshev(mass, Rh.reshape(ncols, sp.n).T, pr.cheb_steps).T.reshape(-1)
+        Xh = X.double().cpu().numpy()
+        assert np.linalg.norm(Xh - Xo) / np.linalg.norm(Xo) <= tol, call
 
 
 def test_noalloc_rejects_oversized_requests():
