@@ -640,7 +640,7 @@ def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16):
     def run_stream(arrivals, keep):
         sv = SGServer(pool_bytes=pool_bytes, max_active=max_active)
         sps = [SGProblem.from_problem(pr, precision="mixed") for pr in reqs]
-        done, lat, rejected, xs = {}, {}, [], {}
+        done, lat, rejected, xs, failed = {}, {}, [], {}, []
         t0 = time.perf_counter()
         nxt = 0
         while len(done) + len(rejected) < len(reqs):
@@ -659,8 +659,12 @@ def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16):
                 continue
             sv.step()
             for rid, x, info in sv.poll():
-                assert info["status_name"] == "SGOC_OK" and info["rel_true_residual"] <= 1e-8, info
                 done[rid] = info
+                if info["status_name"] != "SGOC_OK" or not info["rel_true_residual"] <= 1e-8:
+                    failed.append({"id": rid, "status": info["status_name"],
+                                   "rel_residual": info["rel_true_residual"],
+                                   "error": abi.load().sgoc_last_error().decode()[:200]})
+                    continue
                 lat[rid] = info["ms_total"]
                 if keep:
                     xs[rid] = x
@@ -668,8 +672,8 @@ def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16):
         stats = sv.stats()
         del sv, sps
         l = sorted(lat.values())
-        rec = {"solves_per_s": len(done) / wall, "wall_s": wall, "completed": len(done),
-               "rejected": len(rejected), "rejected_ids": rejected,
+        rec = {"solves_per_s": len(lat) / wall, "wall_s": wall, "completed": len(lat),
+               "failed": failed, "rejected": len(rejected), "rejected_ids": rejected,
                "p50_ms": l[len(l) // 2], "p99_ms": l[min(len(l) - 1, int(math.ceil(0.99 * len(l))) - 1)],
                "pool_high_water_GB": stats["pool_high_water"] / 1e9, "admitted": stats["admitted"]}
         return rec, xs, rejected
@@ -686,7 +690,7 @@ def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16):
     seq_lat, errs = [], []
     t0 = time.perf_counter()
     for i, pr in enumerate(reqs):
-        if i in rejected:
+        if i not in xmix:
             continue
         sp = SGProblem.from_problem(pr, precision="fp64")
         t1 = time.perf_counter()

@@ -207,7 +207,8 @@ sgoc_status sgoc_server_stats(const sgoc_server* sv, int64_t* admitted, int64_t*
  * nodes per thread on 32- and 16-node tiles, 3 two-phase float32, 4 and 5 the
  * four-node kernels built for four instead of two CTAs per SM, 6 the direct
  * kernel: a thread per node and output column, for shapes with few outputs and
- * couplings).  Synchronizes
+ * couplings, and the only kernel for shapes whose input columns do not fit any
+ * staged kernel's shared memory, e.g. float64 with P = 495).  Synchronizes
  * the stream.  The paper has no counterpart: it concerns this GPU code only. */
 sgoc_status sgoc_autotune(sgoc_problem* pb, void* d_ws, size_t ws_bytes, int32_t* chosen,
                           int32_t nchosen, void* stream);

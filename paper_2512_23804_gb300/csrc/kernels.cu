@@ -984,17 +984,25 @@ void sg_clear_tuning() {
 }
 
 template <typename T>
+static bool sg_one_phase_fits(const SGArgs<T>& a) {
+  return (sg_smem<T, 32>(a) <= kMaxSmem && a.n1 >= 24) || (sg_smem<T, 16>(a) <= kMaxSmem && a.n1 >= 12) ||
+         sg_smem<T, 8>(a) <= kMaxSmem;
+}
+
+template <typename T>
 bool sg_variant_feasible(const SGArgs<T>& a, int v) {
   switch (v) {
-    case 0: return true;
+    case 0: return sg_one_phase_fits(a);
     case 1: case 4: return a.n1 >= 24 && a.M + 1 <= 17 && sg4_smem<T, 32>(a) <= kMaxSmem;
     case 2: case 5: return a.n1 >= 15 && a.M + 1 <= 17 && sg4_smem<T, 16>(a) <= kMaxSmem;
     case 3:
       if constexpr (std::is_same<T, float>::value)
         return a.u_mb && a.n1 >= 24 && a.M + 1 <= 17 && sgu_smem(a) + 4096 <= kMaxSmem;
       return false;
-    case 6:                                   // its work grows with outputs x (1 + couplings)
-      return double(a.out1 - a.out0) + (a.c1 != T(0) ? a.deg_sum : 0.0) <= kSGDirectMaxTerms;
+    case 6:                                   // its work grows with outputs x (1 + couplings); it is
+                                              // also the only form when no staged form fits
+      return double(a.out1 - a.out0) + (a.c1 != T(0) ? a.deg_sum : 0.0) <= kSGDirectMaxTerms ||
+             !sg_one_phase_fits(a);
     default: return false;
   }
 }
@@ -1039,7 +1047,10 @@ cudaError_t launch_sg(const SGArgs<T>& a, cudaStream_t st) {
   // P=165 in float32), on 16-node tiles for narrower grids, else one-phase
   if (sg_variant_feasible(a, 1)) return launch_sg_variant(a, 1, st);
   if (sg_variant_feasible(a, 2)) return launch_sg_variant(a, 2, st);
-  return launch_sg_one_phase<T>(a, st);
+  if (sg_one_phase_fits(a)) return launch_sg_one_phase<T>(a, st);
+  // no staged form fits shared memory (hundreds of float64 input columns, e.g. P = 495):
+  // the direct form needs none and applies to every shape
+  return launch_sgd<T>(a, st);
 }
 
 // ---------------------------------------------------------------------------

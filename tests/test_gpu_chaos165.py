@@ -1,5 +1,5 @@
-"""Parity at the largest chaos shape of the workloads (M = 8, p = 3, P = 165) and
-for the multi-slab float32 hGS path.
+"""Parity at the large chaos shapes of the workloads (M = 8, p = 3, P = 165 and the
+serving stream's M = 8, p = 4, P = 495) and for the multi-slab hGS paths.
 
 P = 165 is the shape of the 512 x 512 steady workload.  Its table and staging
 offsets are the ones where a misaligned shared-memory access once occurred, so
@@ -137,3 +137,38 @@ def test_hgs_multi_slab_nan_filled_output(seed, precision, dtype, tol, shape):
     out = host(sp.apply_hgs(dev(R, dtype), out=V))
     assert np.isfinite(out).all()
     assert rel(out, slabwise(d, R, Pc.hgs.apply)) <= tol
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-13), (torch.float32, 2e-6)])
+def test_p495_operator_kkt_and_hgs(dtype, tol):
+    """M = 8, p = 4 (P = 495), the largest chaos shape of the serving stream: in float64 no
+    shared-memory-staged SG kernel holds the 495 input columns of the full operator, and the
+    direct kernel (no shared memory) applies; its results match the oracle and the float32
+    staged kernels."""
+    precision = "fp64" if dtype == torch.float64 else "mixed"
+    pr, d, sp = make(495, precision=precision, nx=16, M=8, p=4)
+    assert d.P == 495
+    X = si.random_panel(496, d.n, d.P)
+    v = si.random_panel(497, 3 * d.n, d.P)
+    if dtype == torch.float32:
+        X = X.astype(np.float32).astype(np.float64)
+        v = v.astype(np.float32).astype(np.float64)
+    Y = host(sp.apply_operator(dev(X, dtype)))
+    assert rel(Y, d.vec(d.sg_apply(d.mat(X)))) <= tol
+    assert np.array_equal(host(sp.apply_operator_variant(dev(X, dtype), 6)), Y)
+    assert rel(host(sp.apply_kkt(dev(v, dtype))), d.kkt_apply(v)) <= tol
+    R = si.random_panel(498, d.n, d.P)
+    if dtype == torch.float32:
+        R = R.astype(np.float32).astype(np.float64)
+    out = host(sp.apply_hgs(dev(R, dtype)))
+    assert rel(out, d.vec(BlockPreconditioner(d).hgs.apply(d.mat(R)))) <= (1e-12 if dtype == torch.float64 else 2e-5)
+
+
+def test_p495_mixed_solve_reaches_the_float64_residual():
+    from paper_2512_23804_gb300 import SGProblem
+    pr = si.random_small(499, nx=32, M=8, p=4, beta=1e-3)
+    d = SGData(pr)
+    x, info = SGProblem.from_problem(pr, precision="mixed").solve()
+    assert info["status_name"] == "SGOC_OK" and info["rel_true_residual"] <= 1e-8
+    xh = host(x)
+    assert rel(d.kkt_apply(xh), d.rhs()) <= 1.01e-8
