@@ -279,6 +279,20 @@ sgoc_status sgoc_apply_chebyshev(sgoc_problem* pb, int32_t precision, const void
 sgoc_status sgoc_apply_chebyshev_noalloc(sgoc_problem* pb, int32_t precision, const void* d_R,
                                          void* d_X, int32_t ncols, void* stream);
 
+/* d_out[0] = sum_i a[i] b[i] (float64) over n entries of two device vectors of the
+ * given precision (0 float64, 1 float32): the Krylov inner product of the MINRES
+ * recurrences (Sec. 5: the Krylov solver's scalars stay float64 in both
+ * precisions).  float64 vectors are summed in float64; float32 vectors with
+ * exact float32 products and sums split by error-free transformations, whose
+ * leading parts are summed in float64, which gives the float64 inner product to
+ * a relative error of order 2^-48.  The order of summation is fixed, so the
+ * result is reproducible bit for bit.  d_ws: device scratch of at least
+ * SGOC_INNER_PRODUCT_WS_BYTES bytes (8-byte aligned); d_out: one device double.
+ * Enqueued on `stream`, no synchronization. */
+#define SGOC_INNER_PRODUCT_WS_BYTES 8192
+sgoc_status sgoc_inner_product(int32_t precision, const void* d_a, const void* d_b, int64_t n, void* d_ws,
+                               size_t ws_bytes, double* d_out, void* stream);
+
 /* The multi-index set, P x M int32 (host), graded by total degree and
  * lexicographically descending within a degree. */
 sgoc_status sgoc_pc_indices(const sgoc_problem* pb, int32_t* host_out);

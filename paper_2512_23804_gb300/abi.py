@@ -22,6 +22,7 @@ STATUS_NAMES = {
 }
 SGOC_FP64, SGOC_MIXED_FP32 = 0, 1
 SGOC_KERNEL_KINDS = 11
+SGOC_INNER_PRODUCT_WS_BYTES = 8192
 
 
 class ProblemDesc(ctypes.Structure):
@@ -80,6 +81,7 @@ SIGNATURES = {
     "sgoc_apply_vcycle": (ctypes.c_int, [_P, _I32, _P, _P, _I32, _P, _SZ, _P]),
     "sgoc_apply_chebyshev": (ctypes.c_int, [_P, _I32, _P, _P, _I32, _P, _SZ, _P]),
     "sgoc_apply_chebyshev_noalloc": (ctypes.c_int, [_P, _I32, _P, _P, _I32, _P]),
+    "sgoc_inner_product": (ctypes.c_int, [_I32, _P, _P, _I64, _P, _SZ, _P, _P]),
     "sgoc_pc_indices": (ctypes.c_int, [_P, _PI32]),
     "sgoc_triple_products": (ctypes.c_int, [_P, _PI32, _PI32, _PI32, _PD, _PI64]),
     "sgoc_kernel_launches": (ctypes.c_int64, []),
@@ -149,4 +151,17 @@ def profile_report():
         if n.value:
             out[lib.sgoc_kernel_kind_name(k).decode()] = dict(launches=n.value, ms=ms.value, bytes=by.value,
                                                              flops=fl.value)
+    return out
+
+
+def inner_product(a, b, stream=None):
+    """sum(a * b) in float64 through sgoc_inner_product (a, b: CUDA tensors of one dtype)."""
+    import torch
+    ws = torch.empty(SGOC_INNER_PRODUCT_WS_BYTES // 8, dtype=torch.float64, device=a.device)
+    out = torch.empty(1, dtype=torch.float64, device=a.device)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    check(load().sgoc_inner_product(0 if a.dtype == torch.float64 else 1, ctypes.c_void_p(a.data_ptr()),
+                                    ctypes.c_void_p(b.data_ptr()), a.numel(), ctypes.c_void_p(ws.data_ptr()),
+                                    ws.numel() * 8, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream)),
+          "sgoc_inner_product")
     return out

