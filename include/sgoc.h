@@ -287,7 +287,8 @@ sgoc_status sgoc_apply_chebyshev_noalloc(sgoc_problem* pb, int32_t precision, co
  * leading parts are summed in float64, which gives the float64 inner product to
  * a relative error of order 2^-48.  The order of summation is fixed, so the
  * result is reproducible bit for bit.  d_ws: device scratch of at least
- * SGOC_INNER_PRODUCT_WS_BYTES bytes (8-byte aligned); d_out: one device double.
+ * SGOC_INNER_PRODUCT_WS_BYTES bytes (8-byte aligned); d_out: one device double;
+ * d_a and d_b may be NULL when n = 0 (the result is then 0).
  * Enqueued on `stream`, no synchronization. */
 #define SGOC_INNER_PRODUCT_WS_BYTES 8192
 sgoc_status sgoc_inner_product(int32_t precision, const void* d_a, const void* d_b, int64_t n, void* d_ws,

@@ -1244,7 +1244,7 @@ const char* sgoc_kernel_kind_name(int32_t kind) { return kernel_kind_name(kind);
 sgoc_status sgoc_inner_product(int32_t precision, const void* d_a, const void* d_b, int64_t n, void* d_ws,
                                size_t ws_bytes, double* d_out, void* stream) {
   static_assert(SGOC_INNER_PRODUCT_WS_BYTES >= kDotBlocks * sizeof(double), "inner-product scratch too small");
-  if (!d_a || !d_b || !d_out || !d_ws || n < 0 || (precision != 0 && precision != 1)) {
+  if ((n > 0 && (!d_a || !d_b)) || !d_out || !d_ws || n < 0 || (precision != 0 && precision != 1)) {
     set_error("inner product: null pointer, negative length or bad precision");
     return SGOC_ERR_INVALID_ARG;
   }
