@@ -424,6 +424,18 @@ def run_ours(args):
         q1.record(stream)
         torch.cuda.synchronize()
         line["sequential_solves_per_s"] = 3 / (q0.elapsed_time(q1) / 1e3)
+        # the merged schedule (sgoc_solve_batch_merged: the three solves in lockstep, each hGS
+        # level visit one SG and one V-cycle launch for all three), same solves
+        solve_batch(sps, outs=xs, streams=streams, merged=True)          # capture the group graphs
+        mt = []
+        for _ in range(2):
+            flush.fill_(1.0)
+            q0.record(stream)
+            solve_batch(sps, outs=xs, streams=streams, merged=True)
+            q1.record(stream)
+            torch.cuda.synchronize()
+            mt.append(q0.elapsed_time(q1))
+        line["merged_batch_solves_per_s"] = 3 / (min(mt) / 1e3)
         # plain float64 path (same solves), for the mixed-vs-fp64 comparison: the error of every
         # mixed solution of the step against the float64 GPU solution of the same problem
         if args.precision == "mixed":

@@ -158,6 +158,26 @@ sgoc_status sgoc_solve_batch(int32_t count, sgoc_problem* const* pbs, void* cons
                              const size_t* ws_bytes, const double* const* d_x0,
                              double* const* d_x, void* const* streams, sgoc_result* res);
 
+/* The same solves as sgoc_solve_batch with a merged schedule: problems of one
+ * shape (grid, M, p, time steps, truncation, precision and preconditioner
+ * options; beta, gamma, T, the coefficient fields and targets may differ) whose
+ * mean-operator V-cycles run one CTA per column (float32 up to 127 x 127 nodes,
+ * float64 up to 15 x 15) are grouped, at most 8 per group, and advanced in
+ * lockstep: one MINRES iteration of a group is one captured CUDA graph in which
+ * every level visit of the two hGS sweeps (Alg. 1) is a single SG launch and a
+ * single V-cycle launch covering the columns of all members, while each member's
+ * KKT product, inner products, recurrences and Chebyshev blocks run on its own
+ * graph branches.  Members that leave the lockstep for a residual check or a
+ * refinement step rejoin at the next group iteration.  Results are bitwise
+ * identical to sgoc_solve of each problem alone.  Problems that cannot be grouped
+ * are solved as by sgoc_solve_batch.  The paper has no counterpart: batching
+ * concerns this GPU code only.  Which schedule is faster depends on the shape: the
+ * merged one launches fewer kernels, the independent one lets different phases
+ * of different solves overlap. */
+sgoc_status sgoc_solve_batch_merged(int32_t count, sgoc_problem* const* pbs, void* const* d_ws,
+                                    const size_t* ws_bytes, const double* const* d_x0, double* const* d_x,
+                                    void* const* streams, sgoc_result* res);
+
 /* ---- serving: continuous batching of solves over a caller-owned device pool ----
  *
  * A server owns no device memory of its own: requests are sub-allocated (first

@@ -65,6 +65,9 @@ SIGNATURES = {
     "sgoc_solve": (ctypes.c_int, [_P, _P, _SZ, _P, _P, _P, ctypes.POINTER(Result)]),
     "sgoc_solve_batch": (ctypes.c_int, [_I32, ctypes.POINTER(_P), ctypes.POINTER(_P), _PSZ, ctypes.POINTER(_P),
                                         ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(Result)]),
+    "sgoc_solve_batch_merged": (ctypes.c_int, [_I32, ctypes.POINTER(_P), ctypes.POINTER(_P), _PSZ,
+                                               ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                               ctypes.POINTER(Result)]),
     "sgoc_server_create": (ctypes.c_int, [_P, _SZ, _I32, ctypes.POINTER(_P)]),
     "sgoc_server_destroy": (None, [_P]),
     "sgoc_server_submit": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint64]),

@@ -212,8 +212,28 @@ template <typename T> struct NbrEntry;
 template <> struct __align__(16) NbrEntry<float> { int ts, ks; float c; int pad; };
 template <> struct __align__(16) NbrEntry<double> { int ts, ks; double c; };
 
+// Member of a merged SG launch: CTAs of grid z in [g*nslabs, (g+1)*nslabs) work on
+// member g, whose operands, coefficient data and scalars replace those of the shared
+// arguments (constant indices only, so the member table stays in parameter space).
+// Returns the slab index within the member.
+template <typename T>
+__device__ __forceinline__ int sg_member(SGArgs<T>& a, const SGMulti<T>& m) {
+  const int g = int(blockIdx.z) / a.nslabs;
+  if (m.ng > 1) {
+#pragma unroll
+    for (int i = 1; i < kMaxGroup; ++i) {
+      if (i == g) {
+        a.X = m.X[i]; a.Y = m.Y[i]; a.R = m.R[i]; a.kap = m.kap[i];
+        a.c0 = m.c0[i]; a.c1 = m.c1[i]; a.cm = m.cm[i]; a.cr = m.cr[i];
+      }
+    }
+  }
+  return int(blockIdx.z) - g * a.nslabs;
+}
+
 template <typename T, int TX>
-__global__ void __launch_bounds__(kSGThreads, 2) sg_kernel(SGArgs<T> a, int rows_per_cta) {
+__global__ void __launch_bounds__(kSGThreads, 2) sg_kernel(SGArgs<T> a, const SGMulti<T> mg, int rows_per_cta) {
+  const int t = sg_member(a, mg);
   using V4 = typename Vec4<T>::type;
   extern __shared__ __align__(32) unsigned char sg_smem_raw[];
   constexpr int W = TX + 2;
@@ -234,7 +254,6 @@ __global__ void __launch_bounds__(kSGThreads, 2) sg_kernel(SGArgs<T> a, int rows
   const int ix0 = blockIdx.x * TX;
   const int r0 = blockIdx.y * rows_per_cta;
   const int r1 = min(a.n1, r0 + rows_per_cta);
-  const int t = blockIdx.z;
   const int tid = threadIdx.x;
   const int n1 = a.n1;
   const T* X = a.X + int64_t(t) * a.xs;
@@ -357,19 +376,25 @@ static size_t sg_smem(const SGArgs<T>& a) {
   return b + 16 * size_t(a.nnz_out) + sizeof(int) * 2 * nout;
 }
 
+template <typename T>
+static const SGMulti<T>& sg_solo() {
+  static const SGMulti<T> m{};
+  return m;
+}
+
 template <typename T, int TX>
-static cudaError_t launch_sg_tx(const SGArgs<T>& a, size_t smem, cudaStream_t st) {
+static cudaError_t launch_sg_tx(const SGArgs<T>& a, size_t smem, cudaStream_t st, const SGMulti<T>& mg) {
   cudaError_t e = allow_max_smem(sg_kernel<T, TX>);
   if (e != cudaSuccess) return e;
   const int xt = (a.n1 + TX - 1) / TX;
   const int per_sm = std::max(1, std::min(2, int((228 * 1024) / (smem + 1024))));
   // about one CTA per resident slot of the GPU: rows per CTA amortise the set-up
   const int64_t want = int64_t(152) * per_sm;
-  const int64_t tiles = int64_t(xt) * a.nslabs;
+  const int64_t tiles = int64_t(xt) * a.nslabs * mg.ng;
   int rows = int(std::max<int64_t>(1, (tiles * a.n1 + want - 1) / want));
   rows = std::min(rows, a.n1);
-  dim3 grid(xt, (a.n1 + rows - 1) / rows, a.nslabs);
-  const double w = sizeof(T), cells = double(a.n) * a.nslabs;
+  dim3 grid(xt, (a.n1 + rows - 1) / rows, a.nslabs * mg.ng);
+  const double w = sizeof(T), cells = double(a.n) * a.nslabs * mg.ng;
   const int nout = a.out1 - a.out0, nin = a.in1 - a.in0;
   const double bytes = w * cells * (nin + nout * (1.0 + (a.R ? 1 : 0) + (a.cy != T(0) ? 1 : 0))) +
                        w * (a.M + 1.0) * a.nx * a.nx;
@@ -377,7 +402,7 @@ static cudaError_t launch_sg_tx(const SGArgs<T>& a, size_t smem, cudaStream_t st
   ProfScope ps(KK_SG, st, bytes, flops);
   {
     const cudaError_t le_ = launch_pdl(sg_kernel<T, TX>, dim3(grid), dim3(kSGThreads), size_t(smem), st,
-                                      a, rows);
+                                      a, mg, rows);
     if (le_ != cudaSuccess) return le_;
   }
   note_launch();
@@ -407,7 +432,8 @@ static size_t sg4_smem(const SGArgs<T>& a) {
 }
 
 template <typename T, int TX, int MINB>
-__global__ void __launch_bounds__(kSG4Threads, MINB) sg4_kernel(SGArgs<T> a, int rows_per_cta) {
+__global__ void __launch_bounds__(kSG4Threads, MINB) sg4_kernel(SGArgs<T> a, const SGMulti<T> mg, int rows_per_cta) {
+  const int t = sg_member(a, mg);
   using V4 = typename Vec4<T>::type;
   constexpr int NQ = TX / 4;          // quads per row of the tile
   constexpr int W = TX + 2;
@@ -433,7 +459,6 @@ __global__ void __launch_bounds__(kSG4Threads, MINB) sg4_kernel(SGArgs<T> a, int
   const int ix0 = blockIdx.x * TX;
   const int r0 = blockIdx.y * rows_per_cta;
   const int r1 = min(a.n1, r0 + rows_per_cta);
-  const int t = blockIdx.z;
   const int tid = threadIdx.x;
   const int n1 = a.n1;
   const T* X = a.X + int64_t(t) * a.xs;
@@ -603,18 +628,18 @@ __global__ void __launch_bounds__(kSG4Threads, MINB) sg4_kernel(SGArgs<T> a, int
 }
 
 template <typename T, int TX, int MINB>
-static cudaError_t launch_sg4_tx(const SGArgs<T>& a, size_t smem, cudaStream_t st) {
+static cudaError_t launch_sg4_tx(const SGArgs<T>& a, size_t smem, cudaStream_t st, const SGMulti<T>& mg) {
   cudaError_t e = allow_max_smem(sg4_kernel<T, TX, MINB>);
   if (e != cudaSuccess) return e;
   const int xt = (a.n1 + TX - 1) / TX;
   // resident CTAs per SM: shared memory, and registers (launch bounds: MINB of 256 threads)
   const int per_sm = std::max(1, std::min(MINB, int((228 * 1024) / (smem + 1024))));
   const int64_t want = int64_t(152) * per_sm;
-  const int64_t tiles = int64_t(xt) * a.nslabs;
+  const int64_t tiles = int64_t(xt) * a.nslabs * mg.ng;
   int rows = int(std::max<int64_t>(1, (tiles * a.n1 + want - 1) / want));
   rows = std::min(rows, a.n1);
-  dim3 grid(xt, (a.n1 + rows - 1) / rows, a.nslabs);
-  const double w = sizeof(T), cells = double(a.n) * a.nslabs;
+  dim3 grid(xt, (a.n1 + rows - 1) / rows, a.nslabs * mg.ng);
+  const double w = sizeof(T), cells = double(a.n) * a.nslabs * mg.ng;
   const int nout = a.out1 - a.out0, nin = a.in1 - a.in0;
   const double bytes = w * cells * (nin + nout * (1.0 + (a.R ? 1 : 0) + (a.cy != T(0) ? 1 : 0))) +
                        w * (a.M + 1.0) * a.nx * a.nx;
@@ -622,7 +647,7 @@ static cudaError_t launch_sg4_tx(const SGArgs<T>& a, size_t smem, cudaStream_t s
   ProfScope ps(KK_SG, st, bytes, flops);
   {
     const cudaError_t le_ = launch_pdl(sg4_kernel<T, TX, MINB>, dim3(grid), dim3(kSG4Threads), size_t(smem), st,
-                                      a, rows);
+                                      a, mg, rows);
     if (le_ != cudaSuccess) return le_;
   }
   note_launch();
@@ -653,7 +678,8 @@ static size_t sgu_smem(const SGArgs<float>& a) {
 }
 
 template <int KM>
-__global__ void __launch_bounds__(kSGUThreads, 1) sgu_kernel(SGArgs<float> a, int rows_per_cta) {
+__global__ void __launch_bounds__(kSGUThreads, 1) sgu_kernel(SGArgs<float> a, const SGMulti<float> mg, int rows_per_cta) {
+  const int t = sg_member(a, mg);
   constexpr int TX = 32, W = TX + 2, NW = kSGUThreads / 32;
   extern __shared__ __align__(16) unsigned char sgu_smem_raw[];
   const int nin = a.in1 - a.in0;
@@ -674,7 +700,6 @@ __global__ void __launch_bounds__(kSGUThreads, 1) sgu_kernel(SGArgs<float> a, in
   const int ix0 = blockIdx.x * TX;
   const int r0 = blockIdx.y * rows_per_cta;
   const int r1 = min(a.n1, r0 + rows_per_cta);
-  const int t = blockIdx.z;
   const int n1 = a.n1;
   const float* X = a.X + int64_t(t) * a.xs;
   const size_t ring_stride = size_t(nin) * W;
@@ -794,7 +819,7 @@ __global__ void __launch_bounds__(kSGUThreads, 1) sgu_kernel(SGArgs<float> a, in
 }
 
 template <int KM>
-static cudaError_t launch_sgu_km(const SGArgs<float>& a, size_t smem, cudaStream_t st) {
+static cudaError_t launch_sgu_km(const SGArgs<float>& a, size_t smem, cudaStream_t st, const SGMulti<float>& mg) {
   cudaError_t e = allow_max_smem(sgu_kernel<KM>);
   if (e != cudaSuccess) return e;
   constexpr int TX = 32;
@@ -804,18 +829,18 @@ static cudaError_t launch_sgu_km(const SGArgs<float>& a, size_t smem, cudaStream
   if (e != cudaSuccess) return e;
   per_sm = std::max(1, per_sm);
   const int64_t want = int64_t(152) * per_sm;
-  const int64_t tiles = int64_t(xt) * a.nslabs;
+  const int64_t tiles = int64_t(xt) * a.nslabs * mg.ng;
   int rows = int(std::max<int64_t>(1, (tiles * a.n1 + want - 1) / want));
   rows = std::min(rows, a.n1);
-  dim3 grid(xt, (a.n1 + rows - 1) / rows, a.nslabs);
-  const double w = 4.0, cells = double(a.n) * a.nslabs;
+  dim3 grid(xt, (a.n1 + rows - 1) / rows, a.nslabs * mg.ng);
+  const double w = 4.0, cells = double(a.n) * a.nslabs * mg.ng;
   const int nout = a.out1 - a.out0, nin = a.in1 - a.in0;
   const double bytes = w * cells * (nin + nout * (1.0 + (a.R ? 1 : 0) + (a.cy != 0.f ? 1 : 0))) +
                        w * (a.M + 1.0) * a.nx * a.nx;
   const double flops = cells * (15.0 * nin + 9.0 * nout + 9.0 * (a.c1 != 0.f ? a.deg_sum : 0));
   ProfScope ps(KK_SG, st, bytes, flops);
   {
-    const cudaError_t le_ = launch_pdl(sgu_kernel<KM>, dim3(grid), dim3(kSGUThreads), size_t(smem), st, a, rows);
+    const cudaError_t le_ = launch_pdl(sgu_kernel<KM>, dim3(grid), dim3(kSGUThreads), size_t(smem), st, a, mg, rows);
     if (le_ != cudaSuccess) return le_;
   }
   note_launch();
@@ -823,13 +848,13 @@ static cudaError_t launch_sgu_km(const SGArgs<float>& a, size_t smem, cudaStream
 }
 
 // the two-phase kernel when the shape has a slot table that fits in shared memory
-static bool try_launch_sgu(const SGArgs<float>& a, cudaStream_t st, cudaError_t* err) {
+static bool try_launch_sgu(const SGArgs<float>& a, cudaStream_t st, cudaError_t* err, const SGMulti<float>& mg) {
   if (!a.u_mb || a.n1 < 24 || a.M + 1 > 17) return false;
   const size_t smem = sgu_smem(a);
   if (smem + 4096 > kMaxSmem) return false;
-  if (a.M + 1 <= 5) *err = launch_sgu_km<5>(a, smem, st);
-  else if (a.M + 1 <= 9) *err = launch_sgu_km<9>(a, smem, st);
-  else *err = launch_sgu_km<17>(a, smem, st);
+  if (a.M + 1 <= 5) *err = launch_sgu_km<5>(a, smem, st, mg);
+  else if (a.M + 1 <= 9) *err = launch_sgu_km<9>(a, smem, st, mg);
+  else *err = launch_sgu_km<17>(a, smem, st, mg);
   return true;
 }
 
@@ -843,11 +868,11 @@ static bool try_launch_sgu(const SGArgs<float>& a, cudaStream_t st, cudaError_t*
 // sg_kernel.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) sgd_kernel(SGArgs<T> a) {
+__global__ void __launch_bounds__(256) sgd_kernel(SGArgs<T> a, const SGMulti<T> mg) {
+  const int t = sg_member(a, mg);
   using V4 = typename Vec4<T>::type;
   const int64_t node = int64_t(blockIdx.x) * 256 + threadIdx.x;
   const int beta = a.out0 + int(blockIdx.y);
-  const int t = blockIdx.z;
   const int n1 = a.n1;
   const bool live = node < a.n;
   const int iy = live ? int(node / n1) : 0, ix = live ? int(node - int64_t(iy) * n1) : 0;
@@ -911,17 +936,17 @@ __global__ void __launch_bounds__(256) sgd_kernel(SGArgs<T> a) {
 }
 
 template <typename T>
-static cudaError_t launch_sgd(const SGArgs<T>& a, cudaStream_t st) {
+static cudaError_t launch_sgd(const SGArgs<T>& a, cudaStream_t st, const SGMulti<T>& mg) {
   const int nout = a.out1 - a.out0;
-  dim3 grid(unsigned((a.n + 255) / 256), unsigned(nout), unsigned(a.nslabs));
-  const double w = sizeof(T), cells = double(a.n) * a.nslabs;
+  dim3 grid(unsigned((a.n + 255) / 256), unsigned(nout), unsigned(a.nslabs * mg.ng));
+  const double w = sizeof(T), cells = double(a.n) * a.nslabs * mg.ng;
   const double bytes = w * cells * (double(a.in1 - a.in0) + nout * (1.0 + (a.R ? 1 : 0) + (a.cy != T(0) ? 1 : 0))) +
                        w * (a.M + 1.0) * a.nx * a.nx;
   const double flops = cells * (15.0 * (nout + (a.c1 != T(0) ? a.deg_sum : 0)) + 9.0 * nout +
                                 9.0 * (a.c1 != T(0) ? a.deg_sum : 0));
   ProfScope ps(KK_SG, st, bytes, flops);
   {
-    const cudaError_t le_ = launch_pdl(sgd_kernel<T>, grid, dim3(256), size_t(0), st, a);
+    const cudaError_t le_ = launch_pdl(sgd_kernel<T>, grid, dim3(256), size_t(0), st, a, mg);
     if (le_ != cudaSuccess) return le_;
   }
   note_launch();
@@ -1008,49 +1033,71 @@ bool sg_variant_feasible(const SGArgs<T>& a, int v) {
 }
 
 template <typename T>
-static cudaError_t launch_sg_one_phase(const SGArgs<T>& a, cudaStream_t st) {
+static cudaError_t launch_sg_one_phase(const SGArgs<T>& a, cudaStream_t st, const SGMulti<T>& mg) {
   size_t s32 = sg_smem<T, 32>(a), s16 = sg_smem<T, 16>(a), s8 = sg_smem<T, 8>(a);
-  if (s32 <= kMaxSmem && a.n1 >= 24) return launch_sg_tx<T, 32>(a, s32, st);
-  if (s16 <= kMaxSmem && a.n1 >= 12) return launch_sg_tx<T, 16>(a, s16, st);
-  if (s8 <= kMaxSmem) return launch_sg_tx<T, 8>(a, s8, st);
+  if (s32 <= kMaxSmem && a.n1 >= 24) return launch_sg_tx<T, 32>(a, s32, st, mg);
+  if (s16 <= kMaxSmem && a.n1 >= 12) return launch_sg_tx<T, 16>(a, s16, st, mg);
+  if (s8 <= kMaxSmem) return launch_sg_tx<T, 8>(a, s8, st, mg);
   return cudaErrorInvalidConfiguration;
 }
 
 template <typename T>
-cudaError_t launch_sg_variant(const SGArgs<T>& a, int v, cudaStream_t st) {
+cudaError_t launch_sg_variant(const SGArgs<T>& a, int v, cudaStream_t st, const SGMulti<T>* mgp) {
   if (a.out1 <= a.out0 || a.nslabs <= 0) return cudaSuccess;
   if (!a.no_own && (a.out0 < a.in0 || a.out1 > a.in1)) return cudaErrorInvalidValue;
   if (!sg_variant_feasible(a, v)) return cudaErrorInvalidConfiguration;
+  const SGMulti<T>& mg = mgp ? *mgp : sg_solo<T>();
   switch (v) {
-    case 1: return launch_sg4_tx<T, 32, 2>(a, sg4_smem<T, 32>(a), st);
-    case 2: return launch_sg4_tx<T, 16, 2>(a, sg4_smem<T, 16>(a), st);
-    case 4: return launch_sg4_tx<T, 32, 4>(a, sg4_smem<T, 32>(a), st);
-    case 5: return launch_sg4_tx<T, 16, 4>(a, sg4_smem<T, 16>(a), st);
-    case 6: return launch_sgd<T>(a, st);
+    case 1: return launch_sg4_tx<T, 32, 2>(a, sg4_smem<T, 32>(a), st, mg);
+    case 2: return launch_sg4_tx<T, 16, 2>(a, sg4_smem<T, 16>(a), st, mg);
+    case 4: return launch_sg4_tx<T, 32, 4>(a, sg4_smem<T, 32>(a), st, mg);
+    case 5: return launch_sg4_tx<T, 16, 4>(a, sg4_smem<T, 16>(a), st, mg);
+    case 6: return launch_sgd<T>(a, st, mg);
     case 3:
       if constexpr (std::is_same<T, float>::value) {
         cudaError_t e = cudaSuccess;
-        if (try_launch_sgu(a, st, &e)) return e;
+        if (try_launch_sgu(a, st, &e, mg)) return e;
       }
       return cudaErrorInvalidConfiguration;
-    default: return launch_sg_one_phase<T>(a, st);
+    default: return launch_sg_one_phase<T>(a, st, mg);
   }
+}
+
+// the kernel for a launch shape: the tuned variant, else the built-in rule
+template <typename T>
+static int sg_choose(const SGArgs<T>& a) {
+  const int tuned = sg_tuned_variant(a);
+  if (tuned >= 0 && sg_variant_feasible(a, tuned)) return tuned;
+  // untuned: the quad kernel on 32-node tiles (measured fastest at 128x128 P=84 and 512x512
+  // P=165 in float32), on 16-node tiles for narrower grids, else one-phase
+  if (sg_variant_feasible(a, 1)) return 1;
+  if (sg_variant_feasible(a, 2)) return 2;
+  if (sg_one_phase_fits(a)) return 0;
+  // no staged form fits shared memory (hundreds of float64 input columns, e.g. P = 495):
+  // the direct form needs none and applies to every shape
+  return 6;
 }
 
 template <typename T>
 cudaError_t launch_sg(const SGArgs<T>& a, cudaStream_t st) {
   if (a.out1 <= a.out0 || a.nslabs <= 0) return cudaSuccess;
   if (!a.no_own && (a.out0 < a.in0 || a.out1 > a.in1)) return cudaErrorInvalidValue;
-  const int tuned = sg_tuned_variant(a);
-  if (tuned >= 0 && sg_variant_feasible(a, tuned)) return launch_sg_variant(a, tuned, st);
-  // untuned: the quad kernel on 32-node tiles (measured fastest at 128x128 P=84 and 512x512
-  // P=165 in float32), on 16-node tiles for narrower grids, else one-phase
-  if (sg_variant_feasible(a, 1)) return launch_sg_variant(a, 1, st);
-  if (sg_variant_feasible(a, 2)) return launch_sg_variant(a, 2, st);
-  if (sg_one_phase_fits(a)) return launch_sg_one_phase<T>(a, st);
-  // no staged form fits shared memory (hundreds of float64 input columns, e.g. P = 495):
-  // the direct form needs none and applies to every shape
-  return launch_sgd<T>(a, st);
+  return launch_sg_variant(a, sg_choose(a), st);
+}
+
+template <typename T>
+cudaError_t launch_sg_group(const SGArgs<T>* a, int ng, cudaStream_t st) {
+  if (ng == 1) return launch_sg(a[0], st);
+  if (ng < 1 || ng > kMaxGroup) return cudaErrorInvalidValue;
+  if (a[0].out1 <= a[0].out0 || a[0].nslabs <= 0) return cudaSuccess;
+  if (!a[0].no_own && (a[0].out0 < a[0].in0 || a[0].out1 > a[0].in1)) return cudaErrorInvalidValue;
+  SGMulti<T> mg{};
+  mg.ng = ng;
+  for (int g = 0; g < ng; ++g) {
+    mg.X[g] = a[g].X; mg.Y[g] = a[g].Y; mg.R[g] = a[g].R; mg.kap[g] = a[g].kap;
+    mg.c0[g] = a[g].c0; mg.c1[g] = a[g].c1; mg.cm[g] = a[g].cm; mg.cr[g] = a[g].cr;
+  }
+  return launch_sg_variant(a[0], sg_choose(a[0]), st, &mg);
 }
 
 // ---------------------------------------------------------------------------
@@ -2527,7 +2574,7 @@ using VtLevel0Of = typename std::conditional<std::is_same<T, float>::value && N1
 template <typename T, int N1, int NU>
 __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 : kVFThreads / VT<N1>::nb()) vcycle_t_kernel(const T* __restrict__ bg, T* xg, FusedLevels L,
                                                                  T omega, int nu_arg, T* acc, int64_t acc_ss, int acc_L,
-                                                                 int acc_col0, VColumns cols) {
+                                                                 int acc_col0, VColumns cols, const VtMulti vm) {
   using G = VT<N1>;
   constexpr int NL = G::nlev();
   constexpr int S0 = N1 + 2;
@@ -2536,7 +2583,20 @@ __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 :
   extern __shared__ __align__(32) unsigned char vt_smem_raw[];
   __shared__ VFLevel<T> lv[13];
   T* base = reinterpret_cast<T*>(vt_smem_raw);
-  const int64_t col = blockIdx.x;
+  int64_t col = blockIdx.x;
+  // member of a merged launch: columns [g*per, (g+1)*per) belong to member g, whose
+  // right-hand sides, outputs and level stencils replace those of the shared arguments
+  int g = 0;
+  if (vm.ng > 1) {
+    g = int(col / vm.per);
+    col -= int64_t(g) * vm.per;
+#pragma unroll
+    for (int i = 1; i < kMaxGroup; ++i) {
+      if (i == g) {
+        bg = static_cast<const T*>(vm.b[i]); xg = static_cast<T*>(vm.x[i]); acc = static_cast<T*>(vm.acc[i]);
+      }
+    }
+  }
   constexpr int n0 = N1 * N1;
   // the column's right-hand side, and its output: x itself, or the strided column x is
   // added to (or stored into)
@@ -2546,8 +2606,11 @@ __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 :
   // level constants, by the last warp (which has the least border work)
   if (threadIdx.x >= G::nb() - 32 && threadIdx.x < G::nb() - 32 + NL) {
     const int l = threadIdx.x - (G::nb() - 32);
-    lv[l].d = T(L.diag[l]); lv[l].e = T(L.edge[l]); lv[l].c = T(L.corner[l]);
-    lv[l].wd = omega / T(L.diag[l]);
+    const double dd = g == 0 ? L.diag[l] : vm.diag[g][l];
+    const double de = g == 0 ? L.edge[l] : vm.edge[g][l];
+    const double dc = g == 0 ? L.corner[l] : vm.corner[g][l];
+    lv[l].d = T(dd); lv[l].e = T(de); lv[l].c = T(dc);
+    lv[l].wd = omega / T(dd);
   }
   // zero borders of every array (interiors are always written before they are read):
   // border thread k of an s x s array zeroes position k of its four sides
@@ -2652,15 +2715,16 @@ __global__ void __launch_bounds__(VT<N1>::nb(), sizeof(T) == 8 && N1 < 127 ? 2 :
 
 template <typename T, int N1>
 static cudaError_t launch_vt(const T* b, T* x, int64_t B, const FusedLevels& L, T omega, int nu, T* acc,
-                             int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st, VColumns cols) {
+                             int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st, VColumns cols,
+                             const VtMulti& vm) {
   const size_t smem = size_t(VT<N1>::total()) * sizeof(T);
   // V(2,2), the cycle of every solve, has an instantiation of its own; other sweep counts share one
   auto k = nu == 2 ? vcycle_t_kernel<T, N1, 2> : vcycle_t_kernel<T, N1, 0>;
   cudaError_t e = allow_max_smem(k);
   if (e != cudaSuccess) return e;
   {
-    const cudaError_t le_ = launch_pdl(k, (dim3(unsigned(B))), dim3(VT<N1>::nb()), size_t(smem), st,
-                                      b, x, L, omega, nu, acc, acc_ss, acc_L, acc_col0, cols);
+    const cudaError_t le_ = launch_pdl(k, (dim3(unsigned(B * vm.ng))), dim3(VT<N1>::nb()), size_t(smem), st,
+                                      b, x, L, omega, nu, acc, acc_ss, acc_L, acc_col0, cols, vm);
     if (le_ != cudaSuccess) return le_;
   }
   return cudaGetLastError();
@@ -2680,26 +2744,53 @@ bool vcycle_full_fits(const FusedLevels& L, int esize) {
 }
 
 template <typename T>
-cudaError_t launch_vcycle_full(const T* b, T* x, int64_t B, const FusedLevels& L, T omega, int nu, T* acc,
-                               int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st, VColumns cols) {
+static cudaError_t launch_vt_any(const T* b, T* x, int64_t B, const FusedLevels& L, T omega, int nu, T* acc,
+                                 int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st, VColumns cols,
+                                 const VtMulti& vm) {
   if (B == 0) return cudaSuccess;
   if (!vcycle_full_fits(L, sizeof(T))) return cudaErrorInvalidConfiguration;
   const double n0 = double(L.n1[0]) * L.n1[0];
-  ProfScope ps(KK_VCYCLE_FUSED, st, double(sizeof(T)) * B * n0 * (acc ? 3 : 2),
-               double(B) * n0 * (4.0 / 3.0) * (21.0 * 2 * nu + 18.0 + 10.0));
+  ProfScope ps(KK_VCYCLE_FUSED, st, double(sizeof(T)) * B * vm.ng * n0 * (acc ? 3 : 2),
+               double(B) * vm.ng * n0 * (4.0 / 3.0) * (21.0 * 2 * nu + 18.0 + 10.0));
   cudaError_t e;
   switch (L.n1[0]) {
-    case 1: e = launch_vt<T, 1>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols); break;
-    case 3: e = launch_vt<T, 3>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols); break;
-    case 7: e = launch_vt<T, 7>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols); break;
-    case 15: e = launch_vt<T, 15>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols); break;
-    case 31: e = launch_vt<T, 31>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols); break;
-    case 63: e = launch_vt<T, 63>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols); break;
-    case 127: e = launch_vt<T, 127>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols); break;
+    case 1: e = launch_vt<T, 1>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols, vm); break;
+    case 3: e = launch_vt<T, 3>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols, vm); break;
+    case 7: e = launch_vt<T, 7>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols, vm); break;
+    case 15: e = launch_vt<T, 15>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols, vm); break;
+    case 31: e = launch_vt<T, 31>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols, vm); break;
+    case 63: e = launch_vt<T, 63>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols, vm); break;
+    case 127: e = launch_vt<T, 127>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols, vm); break;
     default: return cudaErrorInvalidConfiguration;
   }
   note_launch();
   return e;
+}
+
+template <typename T>
+cudaError_t launch_vcycle_full(const T* b, T* x, int64_t B, const FusedLevels& L, T omega, int nu, T* acc,
+                               int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st, VColumns cols) {
+  static const VtMulti solo{};
+  return launch_vt_any<T>(b, x, B, L, omega, nu, acc, acc_ss, acc_L, acc_col0, st, cols, solo);
+}
+
+template <typename T>
+cudaError_t launch_vcycle_full_group(const T* const* b, T* const* x, T* const* acc, const FusedLevels* L, int ng,
+                                     int64_t B, T omega, int nu, int64_t acc_ss, int acc_L, int acc_col0,
+                                     cudaStream_t st, VColumns cols) {
+  if (ng < 1 || ng > kMaxGroup) return cudaErrorInvalidValue;
+  VtMulti vm{};
+  vm.ng = ng;
+  vm.per = B;
+  for (int g = 0; g < ng; ++g) {
+    if (L[g].nlev != L[0].nlev || L[g].n1[0] != L[0].n1[0]) return cudaErrorInvalidValue;
+    if ((acc[g] != nullptr) != (acc[0] != nullptr)) return cudaErrorInvalidValue;
+    vm.b[g] = b[g]; vm.x[g] = x[g]; vm.acc[g] = acc[g];
+    for (int l = 0; l < L[g].nlev; ++l) {
+      vm.diag[g][l] = L[g].diag[l]; vm.edge[g][l] = L[g].edge[l]; vm.corner[g][l] = L[g].corner[l];
+    }
+  }
+  return launch_vt_any<T>(b[0], x[0], B, L[0], omega, nu, acc[0], acc_ss, acc_L, acc_col0, st, cols, vm);
 }
 
 // ---------------------------------------------------------------------------
@@ -3521,7 +3612,8 @@ cudaError_t launch_fill(T* x, int64_t n, T v, cudaStream_t st) {
 // explicit instantiations
 #define SGOC_INST(T)                                                                                               \
   template cudaError_t launch_sg<T>(const SGArgs<T>&, cudaStream_t);                                               \
-  template cudaError_t launch_sg_variant<T>(const SGArgs<T>&, int, cudaStream_t);                              \
+  template cudaError_t launch_sg_variant<T>(const SGArgs<T>&, int, cudaStream_t, const SGMulti<T>*);            \
+  template cudaError_t launch_sg_group<T>(const SGArgs<T>*, int, cudaStream_t);                                    \
   template int sg_tuned_variant<T>(const SGArgs<T>&);                                                              \
   template void sg_set_variant<T>(const SGArgs<T>&, int);                                                          \
   template void sg_clear_variant<T>(const SGArgs<T>&);                                                             \
@@ -3536,6 +3628,8 @@ cudaError_t launch_fill(T* x, int64_t n, T v, cudaStream_t st) {
   template cudaError_t launch_scale<T>(const T*, T*, int64_t, T, cudaStream_t);                                    \
   template cudaError_t launch_vcycle_full<T>(const T*, T*, int64_t, const FusedLevels&, T, int, T*, int64_t, int,  \
                                              int, cudaStream_t, VColumns);                                                   \
+  template cudaError_t launch_vcycle_full_group<T>(const T* const*, T* const*, T* const*, const FusedLevels*, int,  \
+                                                   int64_t, T, int, int64_t, int, int, cudaStream_t, VColumns);    \
   template cudaError_t launch_vcycle_cluster<T>(const T*, T*, int64_t, const ClusterLevels&, int, T, int, T*,      \
                                                 int64_t, int, int, cudaStream_t);                                  \
   template cudaError_t launch_dot_partial<T>(const T*, const T*, int64_t, double*, cudaStream_t);                  \

@@ -58,6 +58,20 @@ struct SGArgs {
 };
 template <typename T>
 cudaError_t launch_sg(const SGArgs<T>& a, cudaStream_t st);
+// Merged launches over several problems of one launch shape (same grid, chaos levels,
+// truncation, slabs and epilogue terms): member g's operands, coefficient data and
+// scalars replace those of the shared SGArgs in the CTAs of slabs [g*nslabs, (g+1)*nslabs)
+// of grid dimension z.  Member 0 is the SGArgs itself.  Every member's outputs are
+// computed exactly as by a launch of its own.
+constexpr int kMaxGroup = 8;
+template <typename T>
+struct SGMulti {
+  int ng = 1;
+  const T* X[kMaxGroup]; T* Y[kMaxGroup]; const T* R[kMaxGroup]; const T* kap[kMaxGroup];
+  T c0[kMaxGroup], c1[kMaxGroup], cm[kMaxGroup], cr[kMaxGroup];
+};
+template <typename T>
+cudaError_t launch_sg_group(const SGArgs<T>* a, int ng, cudaStream_t st);
 // SG kernel variants (0 one-phase, 1 quad 32-node tile, 2 quad 16-node tile,
 // 3 two-phase float32, 4 and 5 the quad tiles at four CTAs per SM, 6 direct:
 // a thread per node and output, feasible while outputs + couplings <=
@@ -65,7 +79,8 @@ cudaError_t launch_sg(const SGArgs<T>& a, cudaStream_t st);
 constexpr int kSGVariants = 7;
 constexpr double kSGDirectMaxTerms = 256;
 template <typename T>
-cudaError_t launch_sg_variant(const SGArgs<T>& a, int variant, cudaStream_t st);
+cudaError_t launch_sg_variant(const SGArgs<T>& a, int variant, cudaStream_t st,
+                              const SGMulti<T>* mg = nullptr);
 template <typename T>
 bool sg_variant_feasible(const SGArgs<T>& a, int variant);
 template <typename T>
@@ -139,6 +154,18 @@ cudaError_t launch_vcycle_cluster(const T* b, T* x, int64_t B, const ClusterLeve
 // goes to acc + (c / acc_L) acc_ss + (acc_col0 + c % acc_L) n, added (acc_add) or stored.
 struct VColumns { int64_t b_ss = 0; int b_L = 0; int acc_add = 1; };
 bool vcycle_full_fits(const FusedLevels& L, int esize);
+// Merged launches of the fused V-cycle over members with the same grid: member g's
+// right-hand sides, outputs and level stencils in the CTAs of columns [g*per, (g+1)*per).
+struct VtMulti {
+  int ng = 1;
+  int64_t per = 0;
+  const void* b[kMaxGroup]; void* x[kMaxGroup]; void* acc[kMaxGroup];
+  double diag[kMaxGroup][13], edge[kMaxGroup][13], corner[kMaxGroup][13];
+};
+template <typename T>
+cudaError_t launch_vcycle_full_group(const T* const* b, T* const* x, T* const* acc, const FusedLevels* L, int ng,
+                                     int64_t B, T omega, int nu, int64_t acc_ss, int acc_L, int acc_col0,
+                                     cudaStream_t st, VColumns cols = VColumns());
 template <typename T>
 cudaError_t launch_vcycle_full(const T* b, T* x, int64_t B, const FusedLevels& L, T omega, int nu,
                                T* acc, int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st,

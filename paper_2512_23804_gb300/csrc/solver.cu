@@ -8,6 +8,9 @@
 #include <deque>
 #include <iterator>
 #include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
 #include <string>
 #include <thread>
 #include <functional>
@@ -317,6 +320,96 @@ static sgoc_status hgs(const sgoc_problem* pb, PrecWS<T>& w, const T* R, T* V, i
   return SGOC_OK;
 }
 
+// ------------------------------------------------------------- merged hGS --
+// One hGS sweep (as hgs above) for several problems of one shape at once: each level
+// visit is one SG launch and one V-cycle launch over all members' columns (merged
+// launches: member g's operands, coefficient data and mean-operator stencils in its
+// own CTAs), so a visit of a level with L columns fills g * L * slabs CTAs.  Every
+// member's arithmetic is that of hgs() on its own, so the results are bitwise equal.
+// Mergeable: same grid, chaos levels, truncation, slabs, sweep counts, damping and a
+// single-CTA fused V-cycle from the finest level (otherwise the members' sweeps run
+// one after the other).
+template <typename T>
+struct HgsMember { const sgoc_problem* pb; PrecWS<T>* w; const T* R; T* V; };
+
+static FusedLevels fused_levels_of(const sgoc_problem* pb, int lf) {
+  FusedLevels FL{};
+  const int nl = int(pb->levels.size());
+  FL.nlev = nl - lf;
+  for (int l = lf; l < nl; ++l) {
+    FL.n1[l - lf] = pb->levels[l].n1;
+    FL.diag[l - lf] = pb->levels[l].diag;
+    FL.edge[l - lf] = pb->levels[l].edge;
+    FL.corner[l - lf] = pb->levels[l].corner;
+  }
+  return FL;
+}
+
+static bool same_shape(const sgoc_problem* a, const sgoc_problem* b) {
+  return a->nx == b->nx && a->M == b->M && a->p == b->p && a->slabs == b->slabs && a->r == b->r &&
+         a->opt.precision == b->opt.precision && a->opt.nu_pre == b->opt.nu_pre &&
+         a->opt.nu_post == b->opt.nu_post && a->opt.omega == b->opt.omega &&
+         a->opt.cheb_steps == b->opt.cheb_steps && (a->nt > 0) == (b->nt > 0);
+}
+
+template <typename T>
+static bool hgs_mergeable(const std::vector<HgsMember<T>>& ms) {
+  if (ms.size() < 2 || ms.size() > size_t(kMaxGroup)) return false;
+  const VPlan vp = plan_vcycle(ms[0].pb, sizeof(T));
+  if (vp.lf != 0 || vp.cluster) return false;
+  for (const auto& m : ms)
+    if (!same_shape(m.pb, ms[0].pb)) return false;
+  return true;
+}
+
+template <typename T>
+static sgoc_status hgs_multi(const std::vector<HgsMember<T>>& ms, int slabs, cudaStream_t st) {
+  if (!hgs_mergeable(ms)) {
+    for (const auto& m : ms) SGOC_TRY(hgs<T>(m.pb, *m.w, m.R, m.V, slabs, st));
+    return SGOC_OK;
+  }
+  const int ng = int(ms.size());
+  const sgoc_problem* pb = ms[0].pb;
+  const int P = pb->P, p = pb->p;
+  const int64_t n = pb->n, ps = int64_t(P) * n;
+  const bool one = slabs == 1;            // the single-CTA cycle stores strided columns otherwise
+  FusedLevels FL[kMaxGroup];
+  for (int g = 0; g < ng; ++g) FL[g] = fused_levels_of(ms[g].pb, 0);
+  const T om = T(pb->opt.omega);
+  const int nu = pb->opt.nu_pre;
+  for (int step = 0; step < 2 * p + 1; ++step) {
+    const bool first = step <= p;
+    const int d = first ? step : 2 * p - step;
+    const int a0 = pb->off[d], L = pb->off[d + 1] - a0;
+    const T* rhs[kMaxGroup];
+    T* xo[kMaxGroup];
+    T* acc[kMaxGroup];
+    VColumns cols;
+    if (first && d == 0) {
+      for (int g = 0; g < ng; ++g) rhs[g] = ms[g].R;
+      if (!one) { cols.b_L = 1; cols.b_ss = ps; }
+    } else {
+      SGArgs<T> a[kMaxGroup];
+      for (int g = 0; g < ng; ++g) {
+        a[g] = first ? hgs_args_first<T>(ms[g].pb, *ms[g].w, ms[g].R, ms[g].V, slabs, d)
+                     : hgs_args<T>(ms[g].pb, *ms[g].w, ms[g].R, ms[g].V, slabs, d);
+        rhs[g] = ms[g].w->RH;
+      }
+      SGOC_LAUNCH(launch_sg_group<T>(a, ng, st));
+    }
+    if (first && one) {
+      for (int g = 0; g < ng; ++g) { xo[g] = ms[g].V + int64_t(a0) * n; acc[g] = nullptr; }
+      SGOC_LAUNCH(launch_vcycle_full_group<T>(rhs, xo, acc, FL, ng, L, om, nu, 0, 1, 0, st, cols));
+    } else {
+      if (first) cols.acc_add = 0;                  // store (V was not zero-filled)
+      for (int g = 0; g < ng; ++g) { xo[g] = nullptr; acc[g] = ms[g].V; }
+      SGOC_LAUNCH(launch_vcycle_full_group<T>(rhs, xo, acc, FL, ng, int64_t(slabs) * L, om, nu, ps, L, a0, st,
+                                              cols));
+    }
+  }
+  return SGOC_OK;
+}
+
 // Independent pieces of one KKT product or preconditioner application run on two
 // auxiliary streams (parallel branches when captured into a graph).
 struct Fork {
@@ -557,11 +650,15 @@ struct Runtime {
 // kernels would inflate each other's event-bracketed durations.
 static const Fork* fork_of(Runtime* rt) { return profile_enabled() ? nullptr : &rt->fork; }
 
+static void drop_group_graphs(const sgoc_problem* pb);
+
 void invalidate_graphs(sgoc_problem* pb) {
   if (pb->runtime) static_cast<Runtime*>(pb->runtime)->drop_graphs();
+  drop_group_graphs(pb);
 }
 
 void release_runtime(sgoc_problem* pb) {
+  drop_group_graphs(pb);
   delete static_cast<Runtime*>(pb->runtime);
   pb->runtime = nullptr;
 }
@@ -673,6 +770,189 @@ static sgoc_status ensure_graphs(sgoc_problem* pb, Runtime& rt, Layout& L, const
   return SGOC_OK;
 }
 
+// ------------------------------------------------------- group iterations --
+// One MINRES iteration of several problems of one shape (sgoc_solve_batch groups
+// them): each member's KKT product, inner products, recurrences and Chebyshev
+// blocks run on the member's own streams (parallel graph branches), while the two
+// hGS sweeps of the Schur blocks run merged over all members (hgs_multi: one SG and
+// one V-cycle launch per level visit for the whole group).  Member g uses its own
+// buffer roles (parity) and its own scalar state; its arithmetic is that of
+// minres_step, so the iterates are bitwise those of the member solved alone.
+struct GroupMember {
+  sgoc_problem* pb;
+  Runtime* rt;
+  Layout* L;
+  int par;          // buffer roles of this iteration
+  void* x;          // the member's iterate (double* or float*)
+};
+
+struct GroupRuntime {
+  cudaStream_t st = nullptr;                 // launch / capture stream of the group iterations
+  cudaEvent_t done = nullptr;                // completion of the group iteration in flight
+  std::vector<cudaEvent_t> ev;               // fork / join events (6 per member)
+  ~GroupRuntime() {
+    if (st) cudaStreamDestroy(st);
+    if (done) cudaEventDestroy(done);
+    for (auto e : ev) if (e) cudaEventDestroy(e);
+  }
+  sgoc_status init() {
+    int least = 0, greatest = 0;
+    SGOC_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    SGOC_CUDA_TRY(cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, greatest));
+    SGOC_CUDA_TRY(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    ev.assign(6 * kMaxGroup, nullptr);
+    for (auto& e : ev) SGOC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return SGOC_OK;
+  }
+};
+
+template <typename T, typename TX>
+static sgoc_status group_step(const std::vector<GroupMember>& gm, GroupRuntime& gr, bool copy_state) {
+  const int ng = int(gm.size());
+  cudaStream_t gs = gr.st;
+  std::vector<MinresVecs<T>> mv(ng);
+  std::vector<HgsMember<T>> h1(ng), h2(ng);
+  for (int g = 0; g < ng; ++g) {
+    const GroupMember& m = gm[g];
+    const MinresVecs<T>& base = vecs_of<T>(*m.L);
+    mv[g] = m.par == 0 ? base : swapped(base);
+    PrecWS<T>& w = prec_of<T>(*m.L);
+    h1[g] = HgsMember<T>{m.pb, &w, mv[g].vp + 2 * m.pb->F, w.W1};
+    h2[g] = HgsMember<T>{m.pb, &w, w.W2, mv[g].zn + 2 * m.pb->F};
+  }
+  // A: per member, everything the first hGS sweep waits for (and the Chebyshev branch)
+  for (int g = 0; g < ng; ++g) {
+    const GroupMember& m = gm[g];
+    const sgoc_problem* pb = m.pb;
+    Layout& L = *m.L;
+    const MinresVecs<T>& v = mv[g];
+    TX* x = static_cast<TX*>(m.x);
+    const Fork* f = fork_of(m.rt);
+    cudaStream_t cs = m.rt->cap;
+    SGOC_TRY(fork_to(gs, cs, gr.ev[6 * g + 0]));
+    const int64_t N = pb->N, F2 = 2 * pb->F;
+    cudaStream_t sw = f ? f->s3 : cs;
+    if (f) SGOC_TRY(fork_to(cs, sw, f->e[6]));
+    SGOC_TRY((prev_wx<T, TX>(pb, L, v, x, sw)));
+    SGOC_TRY(kkt_apply<T>(pb, v.z, v.Kz, cs, f));
+    SGOC_LAUNCH(launch_dot_partial<T>(v.z, v.Kz, N, L.k64.partial, cs));
+    SGOC_LAUNCH(launch_minres_alpha(L.k64.state, L.k64.partial, cs));
+    SGOC_LAUNCH(launch_minres_v<T>(v.Kz + F2, v.v + F2, v.vp + F2, N - F2, L.k64.state, cs));
+    if (f) SGOC_TRY(fork_to(sw, cs, f->e[7]));
+    // Chebyshev blocks 1, 2 of the preconditioner on their branch (as in precond_apply)
+    PrecWS<T>& w = prec_of<T>(L);
+    ChebArgs<T> c{};
+    c.B = v.vp; c.X = v.zn; c.tmpA = w.chebA; c.tmpB = w.chebB;
+    c.ncols = 2 * int64_t(pb->slabs) * pb->P; c.n1 = pb->n1; c.n = pb->n; c.steps = pb->opt.cheb_steps;
+    c.mass = T(pb->mass_h2_36); c.scale_mode = 1; c.P = pb->P; c.slabs = pb->slabs; c.nt = pb->nt;
+    c.tau = T(pb->tau); c.beta = T(pb->beta); c.gamma = T(pb->gamma);
+    cudaStream_t sc = cs;
+    if (f) { SGOC_TRY(fork_to(cs, f->s1, f->e[3])); sc = f->s1; }
+    SGOC_LAUNCH(launch_minres_v<T>(v.Kz, v.v, v.vp, F2, L.k64.state, sc));
+    SGOC_LAUNCH(launch_cheb<T>(c, sc));
+    SGOC_TRY(fork_to(cs, gs, gr.ev[6 * g + 1]));
+  }
+  // B: the first hGS sweep of every member, merged
+  SGOC_TRY(hgs_multi<T>(h1, gm[0].pb->slabs, gs));
+  // C: per member, W2 = M_gamma W1 (steady) or tau (D (x) M_gamma) W1 (time)
+  for (int g = 0; g < ng; ++g) {
+    const sgoc_problem* pb = gm[g].pb;
+    cudaStream_t cs = gm[g].rt->cap;
+    PrecWS<T>& w = prec_of<T>(*gm[g].L);
+    SGOC_TRY(fork_to(gs, cs, gr.ev[6 * g + 2]));
+    MassArgs<T> ma = mass_base<T>(pb, w.W2);
+    mass_add(ma, w.W1, 0, pb->nt > 0 ? pb->tau : 1.0, pb->nt > 0 ? 3 : 1, int64_t(pb->P) * pb->n);
+    SGOC_LAUNCH(launch_mass<T>(ma, cs));
+    SGOC_TRY(fork_to(cs, gs, gr.ev[6 * g + 3]));
+  }
+  // D: the second hGS sweep, merged
+  SGOC_TRY(hgs_multi<T>(h2, gm[0].pb->slabs, gs));
+  // E: per member, the Chebyshev branch joins, then v.z and the rotation
+  for (int g = 0; g < ng; ++g) {
+    const GroupMember& m = gm[g];
+    const sgoc_problem* pb = m.pb;
+    Layout& L = *m.L;
+    const Fork* f = fork_of(m.rt);
+    cudaStream_t cs = m.rt->cap;
+    SGOC_TRY(fork_to(gs, cs, gr.ev[6 * g + 4]));
+    if (f) SGOC_TRY(fork_to(f->s1, cs, f->e[4]));
+    SGOC_LAUNCH(launch_dot_partial<T>(mv[g].vp, mv[g].zn, pb->N, L.k64.partial, cs));
+    SGOC_LAUNCH(launch_minres_rotate(L.k64.state, L.k64.partial, cs));
+    if (copy_state) {
+      SGOC_CUDA_TRY(cudaMemcpyAsync(m.rt->hstate, L.k64.state, sizeof(MinresState), cudaMemcpyDeviceToHost, cs));
+      pdl_fence(cs);
+    }
+    SGOC_TRY(fork_to(cs, gs, gr.ev[6 * g + 5]));
+  }
+  return SGOC_OK;
+}
+
+// Captured group iterations, keyed by the members (problem, workspace, buffer roles) in
+// order; a graph refers to device addresses of its members' problem data and
+// workspaces, so it is dropped when any member is re-uploaded or destroyed.
+struct GroupGraph { cudaGraphExec_t exec = nullptr; int64_t nk = 0; };
+using GroupKey = std::vector<std::tuple<const void*, const void*, int>>;
+static std::mutex g_group_mu;
+static std::map<GroupKey, GroupGraph> g_group_graphs;
+
+static void drop_group_graphs(const sgoc_problem* pb) {
+  std::lock_guard<std::mutex> lk(g_group_mu);
+  for (auto it = g_group_graphs.begin(); it != g_group_graphs.end();) {
+    bool hit = false;
+    for (const auto& t : it->first) hit = hit || std::get<0>(t) == pb;
+    if (hit) {
+      if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+      it = g_group_graphs.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+// Enqueue one iteration of the group on gr.st (a captured graph, or eagerly while
+// per-kernel timing is on) and record gr.done.
+template <typename T, typename TX>
+static sgoc_status launch_group_iteration(const std::vector<GroupMember>& gm, const std::vector<const void*>& ws,
+                                          GroupRuntime& gr, bool graphs) {
+  for (const auto& m : gm) SGOC_CUDA_TRY(cudaStreamWaitEvent(gr.st, m.rt->ev, 0));   // each member's last unit
+  pdl_fence(gr.st);
+  if (!graphs) {
+    SGOC_TRY((group_step<T, TX>(gm, gr, true)));
+    pdl_fence(gr.st);
+    SGOC_CUDA_TRY(cudaEventRecord(gr.done, gr.st));
+    return SGOC_OK;
+  }
+  GroupKey key;
+  for (size_t g = 0; g < gm.size(); ++g) key.emplace_back(gm[g].pb, ws[g], gm[g].par);
+  GroupGraph gg;
+  {
+    std::lock_guard<std::mutex> lk(g_group_mu);
+    auto it = g_group_graphs.find(key);
+    if (it != g_group_graphs.end()) gg = it->second;
+  }
+  if (!gg.exec) {
+    const int64_t k0 = kernel_launches();
+    SGOC_CUDA_TRY(cudaStreamBeginCapture(gr.st, cudaStreamCaptureModeRelaxed));
+    sgoc_status s = group_step<T, TX>(gm, gr, true);
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(gr.st, &g);
+    gg.nk = kernel_launches() - k0;
+    add_launches(-gg.nk);                       // counted when the graph runs
+    if (s != SGOC_OK) { if (g) cudaGraphDestroy(g); return s; }
+    if (ee != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_status(ee, "group iteration capture"); }
+    cudaError_t ie = cudaGraphInstantiateWithFlags(&gg.exec, g, cudaGraphInstantiateFlagUseNodePriority);
+    cudaGraphDestroy(g);
+    SGOC_TRY(cuda_status(ie, "cudaGraphInstantiate (group)"));
+    std::lock_guard<std::mutex> lk(g_group_mu);
+    g_group_graphs[key] = gg;
+  }
+  SGOC_CUDA_TRY(cudaGraphLaunch(gg.exec, gr.st));
+  add_launches(gg.nk);
+  pdl_fence(gr.st);
+  SGOC_CUDA_TRY(cudaEventRecord(gr.done, gr.st));
+  return SGOC_OK;
+}
+
 static sgoc_status state_error(const MinresState& hs) {
   if (hs.flag == 4) { set_error("NaN in MINRES recurrences"); return SGOC_ERR_NAN; }
   if (hs.flag == 3) { set_error("preconditioner not positive definite"); return SGOC_ERR_NOT_SPD; }
@@ -725,6 +1005,9 @@ struct SolveTask {
   const double* x0 = nullptr;
   double* x_out = nullptr;
   bool graphs = true;
+  // grouped: the iterations of this solve run inside its group's merged iterations
+  // (sgoc_solve_batch): launch_iter only marks the solve as waiting for the next one
+  bool grouped = false, want_iter = false, in_group = false;
   Phase phase = DONE;
   double bnorm = 0, target = 0, rn = 0;
   int j = 0, jin = 0, par = 0, outer = 0, total = 0, last_flag = 0;
@@ -756,6 +1039,7 @@ struct SolveTask {
   }
   template <typename T, typename TX>
   sgoc_status launch_iter(TX* x) {
+    if (grouped) { want_iter = true; return SGOC_OK; }
     if (graphs) {
       SGOC_CUDA_TRY(cudaGraphLaunch(rt->it[par], st));
       pdl_fence(st);
@@ -1293,9 +1577,9 @@ sgoc_status sgoc_solve(sgoc_problem* pb, void* d_ws, size_t ws_bytes, const doub
   return s;
 }
 
-sgoc_status sgoc_solve_batch(int32_t count, sgoc_problem* const* pbs, void* const* d_ws, const size_t* ws_bytes,
-                             const double* const* d_x0, double* const* d_x, void* const* streams,
-                             sgoc_result* res) {
+static sgoc_status solve_batch_impl(int32_t count, sgoc_problem* const* pbs, void* const* d_ws,
+                                   const size_t* ws_bytes, const double* const* d_x0, double* const* d_x,
+                                   void* const* streams, sgoc_result* res, bool merge) {
   if (count < 0 || (count > 0 && (!pbs || !d_ws || !ws_bytes || !d_x || !streams))) {
     set_error("bad batch arguments");
     return SGOC_ERR_INVALID_ARG;
@@ -1313,6 +1597,47 @@ sgoc_status sgoc_solve_batch(int32_t count, sgoc_problem* const* pbs, void* cons
                                    static_cast<cudaStream_t>(streams[i]));
     if (s != SGOC_OK) tasks[i].fail(s);
   }
+  // merged schedule: problems of one shape whose V-cycles can run merged form groups;
+  // their MINRES iterations run together (group_step), each level visit of the hGS
+  // sweeps as one SG and one V-cycle launch for the whole group
+  struct Group { GroupRuntime gr; std::vector<int> members, active; bool inflight = false; };
+  std::vector<std::unique_ptr<Group>> groups;
+  if (merge) {
+    std::vector<std::vector<int>> cand;
+    for (int i = 0; i < count; ++i) {
+      if (tasks[i].phase == SolveTask::DONE) continue;
+      const int esize = pbs[i]->opt.precision == SGOC_FP64 ? 8 : 4;
+      const VPlan vp = plan_vcycle(pbs[i], esize);
+      if (vp.lf != 0 || vp.cluster) continue;
+      bool placed = false;
+      for (auto& c : cand)
+        if (int(c.size()) < kMaxGroup && same_shape(pbs[c[0]], pbs[i])) { c.push_back(i); placed = true; break; }
+      if (!placed) cand.push_back({i});
+    }
+    for (auto& c : cand) {
+      if (c.size() < 2) continue;
+      auto g = std::make_unique<Group>();
+      sgoc_status s = g->gr.init();
+      if (s != SGOC_OK) return s;
+      g->members = c;
+      for (int i : c) tasks[i].grouped = true;
+      groups.push_back(std::move(g));
+    }
+  }
+  auto group_launch = [&](Group& G) -> sgoc_status {
+    std::vector<GroupMember> gm;
+    std::vector<const void*> ws;
+    for (int i : G.active) {
+      SolveTask& t = tasks[i];
+      const bool f64 = t.pb->opt.precision == SGOC_FP64;
+      gm.push_back(GroupMember{t.pb, t.rt, &t.L, t.par, f64 ? static_cast<void*>(t.L.k64.x) : static_cast<void*>(t.L.c32)});
+      ws.push_back(t.ws);
+    }
+    const bool f64 = tasks[G.active[0]].pb->opt.precision == SGOC_FP64;
+    const bool graphs = tasks[G.active[0]].graphs;
+    if (f64) return launch_group_iteration<double, double>(gm, ws, G.gr, graphs);
+    return launch_group_iteration<float, float>(gm, ws, G.gr, graphs);
+  };
   // advance each solve as soon as its pending unit has completed (polling, so that no solve
   // waits behind another); yield the host thread while none is ready
   for (bool busy = true; busy;) {
@@ -1320,12 +1645,49 @@ sgoc_status sgoc_solve_batch(int32_t count, sgoc_problem* const* pbs, void* cons
     bool progressed = false;
     for (auto& t : tasks) {
       if (t.phase == SolveTask::DONE) continue;
+      busy = true;
+      if (t.want_iter || t.in_group) continue;
       const cudaError_t q = cudaEventQuery(t.rt->ev);
       if (q != cudaErrorNotReady) {               // completed, or an error wait_and_step reports
         t.wait_and_step();
         progressed = true;
       }
-      busy = busy || t.phase != SolveTask::DONE;
+    }
+    for (auto& gp : groups) {
+      Group& G = *gp;
+      if (G.inflight) {
+        const cudaError_t q = cudaEventQuery(G.gr.done);
+        if (q == cudaErrorNotReady) continue;
+        G.inflight = false;
+        progressed = true;
+        for (int i : G.active) {
+          SolveTask& t = tasks[i];
+          t.in_group = false;
+          if (q != cudaSuccess) { t.fail(cuda_status(q, "group iteration")); continue; }
+          // the solve's next units on its own stream follow the group iteration
+          cudaError_t we = cudaStreamWaitEvent(t.st, G.gr.done, 0);
+          if (we != cudaSuccess) { t.fail(cuda_status(we, "cudaStreamWaitEvent")); continue; }
+          pdl_fence(t.st);
+          sgoc_status s = t.step();
+          if (s != SGOC_OK && t.phase != SolveTask::DONE) t.fail(s);
+        }
+      }
+      if (!G.inflight) {
+        G.active.clear();
+        for (int i : G.members)
+          if (tasks[i].phase != SolveTask::DONE && tasks[i].want_iter) G.active.push_back(i);
+        if (G.active.empty()) continue;
+        sgoc_status s = group_launch(G);
+        for (int i : G.active) {
+          SolveTask& t = tasks[i];
+          t.want_iter = false;
+          if (s != SGOC_OK) { t.fail(s); continue; }
+          t.in_group = true;
+          t.par ^= 1;
+        }
+        G.inflight = s == SGOC_OK;
+        progressed = true;
+      }
     }
     if (busy && !progressed) std::this_thread::yield();
   }
@@ -1342,6 +1704,18 @@ sgoc_status sgoc_solve_batch(int32_t count, sgoc_problem* const* pbs, void* cons
     if (first == SGOC_OK) first = s;
   }
   return first;
+}
+
+sgoc_status sgoc_solve_batch(int32_t count, sgoc_problem* const* pbs, void* const* d_ws, const size_t* ws_bytes,
+                             const double* const* d_x0, double* const* d_x, void* const* streams,
+                             sgoc_result* res) {
+  return solve_batch_impl(count, pbs, d_ws, ws_bytes, d_x0, d_x, streams, res, false);
+}
+
+sgoc_status sgoc_solve_batch_merged(int32_t count, sgoc_problem* const* pbs, void* const* d_ws,
+                                    const size_t* ws_bytes, const double* const* d_x0, double* const* d_x,
+                                    void* const* streams, sgoc_result* res) {
+  return solve_batch_impl(count, pbs, d_ws, ws_bytes, d_x0, d_x, streams, res, true);
 }
 
 sgoc_status sgoc_apply_operator(sgoc_problem* pb, int32_t precision, const void* d_X, void* d_Y, int32_t nslabs,

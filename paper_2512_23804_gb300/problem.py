@@ -233,10 +233,11 @@ class SGProblem:
         return k, a, b, c
 
 
-def solve_batch(problems, x0s=None, outs=None, streams=None):
+def solve_batch(problems, x0s=None, outs=None, streams=None, merged=False):
     """Solve several SGProblem instances concurrently (sgoc_solve_batch): each on its
-    own CUDA stream, all advanced together by the calling thread.  Returns
-    ([x_i], [info_i])."""
+    own CUDA stream, all advanced together by the calling thread; with merged=True
+    (sgoc_solve_batch_merged) problems of one shape share merged SG and V-cycle
+    launches in lockstep iterations.  Returns ([x_i], [info_i])."""
     import torch
     lib = abi.load()
     n = len(problems)
@@ -254,7 +255,8 @@ def solve_batch(problems, x0s=None, outs=None, streams=None):
     P = ctypes.c_void_p
     arr = lambda vals: (P * n)(*vals)
     res = (abi.Result * n)()
-    st = lib.sgoc_solve_batch(
+    fn = lib.sgoc_solve_batch_merged if merged else lib.sgoc_solve_batch
+    st = fn(
         n, arr([sp._handle.value for sp in problems]), arr([w.data_ptr() for w in wss]),
         (ctypes.c_size_t * n)(*[w.numel() for w in wss]),
         arr([(x0.data_ptr() if x0 is not None else None) for x0 in x0s]) if x0s is not None else None,
