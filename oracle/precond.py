@@ -6,6 +6,10 @@ Block-diagonal preconditioner (Eq. (stoch-prec) steady, Eq. (precon for time)):
   block 3: S^{-1} = Z^{-1} M_gamma Z^{-1} with Z = A + sqrt((1+gamma)/beta) M_cal (Eq. (mathcalZ));
            time: S~^{-1} = tau Z~^{-1} (D (x) M_gamma) Z~^{-1} with Z~ block diagonal in time
            (Eqs. (Z hat approx), (S_tilde), (S hat)); time blocks 1, 2 carry the extra 1/(tau D_t).
+  time, schur="coupled": S_bar^{-1} = tau Z_bar^{-T} (D (x) M_gamma) Z_bar^{-1} with the coupled
+           Z_bar = I (x) Z~_t - C (x) M_cal of Eq. (S hat) / Eq. (Z hat), which keeps the -C (x) H_1 (x) M
+           term: Z_bar^{-1} by block forward substitution in time, Z_bar^{-T} by backward
+           substitution, each step one solve with the slab operator Z~_t.
   Solves with Z / Z~ use the hierarchical Gauss-Seidel sweep of Alg. 1 (one application,
   i.e. the Richardson iteration of Sec. 5 with N = 1 and zero initial guess), truncated to
   the first r terms of the expansion (Sec. 2, Eq. (matvec-block) and the index set I_tau).
@@ -153,8 +157,10 @@ class HGS:
 
 # ------------------------------------------------------- block preconditioner --
 class BlockPreconditioner:
-    def __init__(self, data, mode="vcycle"):
+    def __init__(self, data, mode="vcycle", schur="diagonal"):
+        assert schur in ("diagonal", "coupled")
         self.d = data
+        self.schur = schur
         pr = data.pr
         s = math.sqrt((1.0 + data.gamma) / data.beta)
         Mm = data.Mass
@@ -180,6 +186,8 @@ class BlockPreconditioner:
         z = np.zeros_like(r)
         Mm = d.Mass
         Dw = d.d_weights()
+        if d.nt > 0 and self.schur == "coupled":
+            return self._apply_coupled(r)
         for t in range(d.slabs):
             sl = slice(t * nP, (t + 1) * nP)
             R1 = d.mat(r[:F][sl])
@@ -196,4 +204,35 @@ class BlockPreconditioner:
             z[:F][sl] = d.vec(Z1)
             z[F:2 * F][sl] = d.vec(Z2)
             z[2 * F:][sl] = d.vec(Z3)
+        return z
+
+    def _apply_coupled(self, r):
+        """Time mode with the coupled Schur block: blocks 1 and 2 as in apply(); block 3
+        is tau Z_bar^{-T} (D (x) M_gamma) Z_bar^{-1} r_3 where Z_bar x = r reads
+        Z~ x_t = r_t + M_cal x_{t-1} (x_0 = 0, forward in t) and Z_bar^T x = r reads
+        Z~ x_t = r_t + M_cal x_{t+1} (x_{n_t+1} = 0, backward in t); every solve with the
+        slab operator Z~ is one hGS sweep."""
+        d = self.d
+        F = d.slabs * d.P * d.n
+        nP = d.P * d.n
+        Mm = d.Mass
+        Dw = d.d_weights()
+        z = np.zeros_like(r)
+        for t in range(d.nt):
+            sl = slice(t * nP, (t + 1) * nP)
+            sc = d.tau * Dw[t]
+            z[:F][sl] = d.vec(chebyshev(Mm, d.mat(r[:F][sl]), self.steps) / (sc * d.hgam[None, :]))
+            z[F:2 * F][sl] = d.vec(chebyshev(Mm, d.mat(r[F:2 * F][sl]), self.steps) / (sc * d.beta))
+        R3 = [d.mat(r[2 * F:][t * nP:(t + 1) * nP]) for t in range(d.nt)]
+        X = []
+        for t in range(d.nt):                       # Z_bar X = R3, forward in time
+            rhs = R3[t] + (Mm @ X[t - 1] if t > 0 else 0.0)
+            X.append(self.hgs.apply(rhs))
+        W = [d.tau * Dw[t] * (Mm @ X[t]) * d.hgam[None, :] for t in range(d.nt)]
+        Z = [None] * d.nt
+        for t in reversed(range(d.nt)):             # Z_bar^T Z = W, backward in time
+            rhs = W[t] + (Mm @ Z[t + 1] if t + 1 < d.nt else 0.0)
+            Z[t] = self.hgs.apply(rhs)
+        for t in range(d.nt):
+            z[2 * F:][t * nP:(t + 1) * nP] = d.vec(Z[t])
         return z

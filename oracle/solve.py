@@ -17,15 +17,16 @@ from .operators import SGData
 from .precond import BlockPreconditioner
 
 
-def solve(pr, mode="vcycle", assembled=False, data=None):
+def solve(pr, mode="vcycle", assembled=False, data=None, schur=None):
     d = data or SGData(pr)
+    schur = schur or getattr(pr, "schur", "diagonal")
     b = d.rhs()
     if assembled:
         K = d.kkt_matrix()
         apply_A = lambda v: K @ v
     else:
         apply_A = d.kkt_apply
-    Pc = BlockPreconditioner(d, mode)
+    Pc = BlockPreconditioner(d, mode, schur=schur)
     res = minres(apply_A, Pc.apply, b, tol=pr.tol, max_iter=pr.max_iter)
     res.data = d
     return res

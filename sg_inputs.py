@@ -59,6 +59,7 @@ class Problem:
     nu_pre: int = 2
     nu_post: int = 2
     omega: float = 0.8
+    schur: str = "diagonal"     # time mode: "diagonal" (Z~, block-diagonal in time) or "coupled" (Z_bar)
     name: str = ""
 
     @property

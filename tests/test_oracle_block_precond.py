@@ -209,3 +209,76 @@ def test_time_schur_scalars_follow_the_paper_theorems(gamma):
     z3 = Pc.apply(np.concatenate([np.zeros(2 * F), rv]))[2 * F:]
     ref = np.linalg.solve(St, rv)
     assert np.linalg.norm(z3 - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def _z_bar_hgs(Zbar, Zt, d, r):
+    """Z_bar with the slab operator Z~_t replaced by its hGS approximation Z_hGS: the
+    time coupling -C (x) M_cal of Z_bar is kept exactly (Eq. (Z hat))."""
+    return _z_hgs(Zt, d, r) + (Zbar - Zt)
+
+
+@pytest.mark.parametrize("gamma,sigma,r", [(0.0, 0.0, 3), (0.7, 0.3, 3), (0.0, 0.3, 2)])
+def test_coupled_schur_block_equals_dense_definition(gamma, sigma, r):
+    """Time mode, coupled Schur block: with exact mean solves the oracle's block 3 is
+    S_bar^{-1} r with S_bar = (1/tau) Z_bar_hGS (D (x) M_gamma)^{-1} Z_bar_hGS^T = Z K11^{-1} Z^T
+    (Z = Z_bar_hGS: the paper's Z_bar of Eq. (Z hat), read off the assembled KKT matrix, with
+    the slab operator replaced by its hGS approximation; exact for sigma = 0); blocks 1, 2
+    are those of the block-diagonal form."""
+    pr = _problem(3, gamma, sigma, r)
+    d = SGData(pr)
+    F, K11, K22, K31, K32 = _blocks(d)
+    s = math.sqrt((1.0 + gamma) / pr.beta)
+    Zbar = -K31 + s * K32
+    Zt = _time_block_diag(Zbar, d)
+    Zc = _z_bar_hgs(Zbar, Zt, d, r)
+    if sigma == 0.0:
+        assert np.allclose(Zc, Zbar, rtol=0, atol=1e-12 * np.abs(Zbar).max())
+    Sbar = Zc @ np.linalg.solve(K11, Zc.T)
+    Pc = BlockPreconditioner(d, mode="exact", schur="coupled")
+    Pd = BlockPreconditioner(d, mode="exact")
+    rv = np.random.default_rng(9).standard_normal(3 * F)
+    z = Pc.apply(rv)
+    zd = Pd.apply(rv)
+    assert np.linalg.norm(z[:2 * F] - zd[:2 * F]) <= 1e-14 * np.linalg.norm(zd[:2 * F])
+    ref = np.linalg.solve(Sbar, rv[2 * F:])
+    assert np.linalg.norm(z[2 * F:] - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_coupled_schur_block_symmetric_positive_and_within_the_theorem_bounds():
+    """The coupled block with V-cycle mean solves is a symmetric positive definite map (the
+    forward and backward substitutions are transposes of each other for a symmetric sweep),
+    and with exact mean solves and sigma = 0 its spectrum against the exact Schur complement
+    obeys Thm. approx: lambda(S_bar^{-1} S_exact) in [1/(2(1+alpha)), 1)."""
+    pr = _problem(3, 0.3, 0.3, 3)
+    d = SGData(pr)
+    F = d.slabs * d.P * d.n
+    Pc = BlockPreconditioner(d, schur="coupled")
+    B = np.stack([Pc.apply(np.concatenate([np.zeros(2 * F), e]))[2 * F:] for e in np.eye(F)], axis=1)
+    assert np.allclose(B, B.T, rtol=0, atol=1e-12 * np.abs(B).max())
+    assert np.linalg.eigvalsh(0.5 * (B + B.T)).min() > 0
+    pr = _problem(3, 0.0, 0.0, 3, beta=1e-1)
+    d = SGData(pr)
+    F, K11, K22, K31, K32 = _blocks(d)
+    Sx = K31 @ np.linalg.solve(K11, K31.T) + K32 @ np.linalg.solve(K22, K32.T)
+    Pc = BlockPreconditioner(d, mode="exact", schur="coupled")
+    Sinv = np.stack([Pc.apply(np.concatenate([np.zeros(2 * F), e]))[2 * F:] for e in np.eye(F)], axis=1)
+    ev = np.sort(np.linalg.eigvals(Sinv @ Sx).real)
+    sv = np.linalg.svd(-K31, compute_uv=False)
+    kap = sv[0] / sv[-1]
+    alpha_sup = ((math.sqrt(kap) + 1) / (math.sqrt(kap) - 1)) ** 2 - 1
+    assert ev[-1] <= 1 + 1e-10 and ev[0] >= 1 / (2 * (1 + alpha_sup)) - 1e-10
+
+
+def test_coupled_schur_minres_converges_to_the_direct_solution():
+    """MINRES with the coupled preconditioner reaches the direct solution; at a small time step
+    it needs no more iterations than the block-diagonal one (Sec. 4: S_tilde departs from S_bar
+    when tau is small against sqrt(beta))."""
+    from oracle.solve import solve, direct_solve
+    pr = si.random_small(17, nx=8, M=2, p=2, nt=6, beta=1e-1)
+    pr.T = 0.06
+    xd = direct_solve(pr)
+    rc = solve(pr, schur="coupled")
+    rd = solve(pr, schur="diagonal")
+    assert rc.status == "ok" and rc.rel_true <= pr.tol
+    assert np.linalg.norm(rc.x - xd) <= 1e-6 * np.linalg.norm(xd)
+    assert rc.iterations <= rd.iterations, (rc.iterations, rd.iterations)
