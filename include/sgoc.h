@@ -93,6 +93,12 @@ typedef struct {
   int32_t precision;     /* sgoc_precision (SGOC_FP64) */
   double inner_tol;      /* mixed: inner MINRES relative tolerance (1e-3) */
   int32_t max_outer;     /* mixed: refinement steps cap (20) */
+  int32_t schur;         /* time mode, Schur block of the preconditioner (0):
+                            0: S~ = (1/tau) Z~ (D (x) M_gamma)^{-1} Z~ with Z~ block-diagonal in
+                               time (Eq. (Z hat approx), Eq. (S_tilde)): all slabs at once;
+                            1: S_bar = (1/tau) Z_bar (D (x) M_gamma)^{-1} Z_bar^T with the coupled
+                               Z_bar = I (x) Z~_t - C (x) M_cal (Eq. (S hat), Eq. (Z hat)): block
+                               forward and backward substitution in time, one hGS sweep per step */
 } sgoc_options;
 
 typedef struct {

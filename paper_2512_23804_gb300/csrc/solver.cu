@@ -520,6 +520,46 @@ static sgoc_status kkt_apply(const sgoc_problem* pb, const T* v, T* w, cudaStrea
   return SGOC_OK;
 }
 
+// ------------------------------------------------ coupled time Schur block --
+// z = tau Z_bar^{-T} (D (x) M_gamma) Z_bar^{-1} r with Z_bar = I (x) Z~_t - C (x) M_cal (Eq. (S hat),
+// Eq. (Z hat)): Z_bar x = r by forward substitution, Z~ x_t = r_t + M_cal x_{t-1}, and
+// Z_bar^T z = w by backward substitution, Z~ z_t = w_t + M_cal z_{t+1}; each solve with the slab
+// operator Z~ is one hGS sweep of one slab (Alg. 1), so the slabs run one after the other.
+template <typename T>
+static sgoc_status coupled_schur(const sgoc_problem* pb, PrecWS<T>& w, const T* r, T* z, cudaStream_t st) {
+  const int nt = pb->nt;
+  const int64_t ps = int64_t(pb->P) * pb->n;
+  // one slab: out = R + M V  (every chaos column, no weights)
+  auto coupled_rhs = [&](T* out, const T* R, const T* V) -> sgoc_status {
+    MassArgs<T> m = mass_base<T>(pb, out);
+    m.nslabs = 1;
+    m.R = R; m.rs = ps; m.ar = T(1);
+    mass_add(m, V, 0, 1.0, 0, ps);
+    SGOC_LAUNCH(launch_mass<T>(m, st));
+    return SGOC_OK;
+  };
+  for (int t = 0; t < nt; ++t) {                       // W1 = Z_bar^{-1} r
+    const T* rhs = r;
+    if (t > 0) {
+      SGOC_TRY(coupled_rhs(w.W2 + t * ps, r + t * ps, w.W1 + (t - 1) * ps));
+      rhs = w.W2 + t * ps;
+    }
+    SGOC_TRY(hgs<T>(pb, w, rhs, w.W1 + t * ps, 1, st));
+  }
+  MassArgs<T> m = mass_base<T>(pb, w.W2);               // W2 = tau (D (x) M_gamma) W1
+  mass_add(m, w.W1, 0, pb->tau, 3, ps);
+  SGOC_LAUNCH(launch_mass<T>(m, st));
+  for (int t = nt - 1; t >= 0; --t) {                  // z = Z_bar^{-T} W2
+    const T* rhs = w.W2 + t * ps;
+    if (t + 1 < nt) {
+      SGOC_TRY(coupled_rhs(w.W1 + t * ps, w.W2 + t * ps, z + (t + 1) * ps));
+      rhs = w.W1 + t * ps;
+    }
+    SGOC_TRY(hgs<T>(pb, w, rhs, z + t * ps, 1, st));
+  }
+  return SGOC_OK;
+}
+
 // ------------------------------------------------------ block preconditioner --
 template <typename T>
 static sgoc_status precond_apply(const sgoc_problem* pb, PrecWS<T>& w, const T* r, T* z, cudaStream_t st,
@@ -538,11 +578,15 @@ static sgoc_status precond_apply(const sgoc_problem* pb, PrecWS<T>& w, const T* 
   if (before_cheb) SGOC_TRY(before_cheb(sc));       // work only the Chebyshev blocks wait for
   SGOC_LAUNCH(launch_cheb<T>(c, sc));
   // block 3: S^{-1} = Z^{-1} M_gamma Z^{-1} (steady), tau Z~^{-1} (D (x) M_gamma) Z~^{-1} (time)
-  SGOC_TRY(hgs<T>(pb, w, r + 2 * F, w.W1, pb->slabs, st));
-  MassArgs<T> m = mass_base<T>(pb, w.W2);
-  mass_add(m, w.W1, 0, pb->nt > 0 ? pb->tau : 1.0, pb->nt > 0 ? 3 : 1, ps);
-  SGOC_LAUNCH(launch_mass<T>(m, st));
-  SGOC_TRY(hgs<T>(pb, w, w.W2, z + 2 * F, pb->slabs, st));
+  if (pb->nt > 1 && pb->opt.schur == 1) {
+    SGOC_TRY(coupled_schur<T>(pb, w, r + 2 * F, z + 2 * F, st));
+  } else {
+    SGOC_TRY(hgs<T>(pb, w, r + 2 * F, w.W1, pb->slabs, st));
+    MassArgs<T> m = mass_base<T>(pb, w.W2);
+    mass_add(m, w.W1, 0, pb->nt > 0 ? pb->tau : 1.0, pb->nt > 0 ? 3 : 1, ps);
+    SGOC_LAUNCH(launch_mass<T>(m, st));
+    SGOC_TRY(hgs<T>(pb, w, w.W2, z + 2 * F, pb->slabs, st));
+  }
   if (f) SGOC_TRY(fork_to(f->s1, st, f->e[4]));
   return SGOC_OK;
 }
