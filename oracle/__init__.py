@@ -12,10 +12,11 @@ Modules
   fe        Q1 stiffness K_k and mass M on the unit square            (Sec. 2, Eq. (gPC-A))
   operators SG operator sum_k G_k (x) K_k, KKT systems, right-hand sides (Eqs. (stoch-system), (KKT:stoch-time-dependent))
   precond   Chebyshev mass solve, V-cycle, hGS sweep, block preconditioners (Eqs. (stoch-prec), (precon for time), Alg. 1)
-  krylov    preconditioned MINRES with the stopping rule used by the library
+  krylov    preconditioned MINRES and flexible GMRES with the stopping rule used by the library
   solve     end-to-end solves and dense direct reference solutions
 
 Parity status: every function is pinned by tests in tests/test_oracle_*.py
-except the MINRES iteration count itself, which is pinned only against
-scipy's MINRES and the 3-iteration ideal-preconditioner case.
+except the Krylov iteration counts themselves, which are pinned only against
+scipy's MINRES / GMRES, the minimal-residual property of GMRES and the
+3-iteration ideal-preconditioner case.
 """

@@ -92,3 +92,73 @@ def minres(apply_A, apply_Pinv, b, tol=1e-8, max_iter=500):
             target *= tol / rel_true
     rel_true = float(np.linalg.norm(b - apply_A(x))) / bnorm2
     return MinresResult(x, max_iter, rel_true, abs(eta) / beta1, "max_iter", history)
+
+
+def fgmres(apply_A, apply_Pinv, b, tol=1e-8, max_iter=500, restart=None):
+    """Flexible GMRES (Saad's right-preconditioned variant, the Krylov method of Sec. 5):
+    x0 = 0; Arnoldi with modified Gram-Schmidt on the vectors A z_j, z_j = P_j^{-1} v_j (the
+    preconditioner may change from one iteration to the next), Givens rotations of the
+    Hessenberg matrix, x = x0 + Z_m y_m.  The estimate |g_{j+1}| / ||b||_2 is the 2-norm of
+    the residual in exact arithmetic; the stopping rule is that of minres(): when the
+    estimate reaches the target the true residual decides, and the target is rescaled by
+    tol / rho if it is still above tol.  restart=None: unrestarted (one cycle up to max_iter)."""
+    n = b.shape[0]
+    x = np.zeros(n)
+    bnorm = float(np.linalg.norm(b))
+    if bnorm == 0.0:
+        return MinresResult(x, 0, 0.0, 0.0, "ok", [])
+    m_cap = max_iter if restart is None else restart
+    target = tol
+    history = []
+    total = 0
+    r = b.copy()
+    rel_true = 1.0
+    while True:
+        beta = float(np.linalg.norm(r))
+        V = [r / beta]
+        Z = []
+        H = np.zeros((m_cap + 1, m_cap))
+        cs, sn = np.zeros(m_cap), np.zeros(m_cap)
+        g = np.zeros(m_cap + 1)
+        g[0] = beta
+        fired = False
+        j = 0
+        for j in range(m_cap):
+            z = apply_Pinv(V[j])
+            w = apply_A(z)
+            Z.append(z)
+            for i in range(j + 1):                  # modified Gram-Schmidt
+                H[i, j] = float(w @ V[i])
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = float(np.linalg.norm(w))
+            for i in range(j):                      # previous rotations on the new column
+                hi, hi1 = H[i, j], H[i + 1, j]
+                H[i, j] = cs[i] * hi + sn[i] * hi1
+                H[i + 1, j] = -sn[i] * hi + cs[i] * hi1
+            rho = math.hypot(H[j, j], H[j + 1, j])
+            if rho == 0.0:
+                return MinresResult(x, total + j + 1, rel_true, abs(g[j]) / bnorm, "breakdown", history)
+            cs[j], sn[j] = H[j, j] / rho, H[j + 1, j] / rho
+            H[j, j] = rho
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            est = abs(g[j + 1]) / bnorm
+            history.append(est)
+            lucky = H[j + 1, j] == 0.0 and float(np.linalg.norm(w)) == 0.0
+            if est <= target or lucky:
+                fired = True
+                break
+            V.append(w / float(np.linalg.norm(w)))
+        k = j + 1
+        y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
+        x = x + np.column_stack(Z) @ y
+        total += k
+        r = b - apply_A(x)
+        rel_true = float(np.linalg.norm(r)) / bnorm
+        if fired:
+            if rel_true <= tol:
+                return MinresResult(x, total, rel_true, history[-1], "ok", history)
+            target *= tol / rel_true
+        if total >= max_iter:
+            return MinresResult(x, total, rel_true, history[-1], "max_iter", history)

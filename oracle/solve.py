@@ -12,14 +12,16 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse.linalg as spla
 
-from .krylov import minres
+from .krylov import fgmres, minres
 from .operators import SGData
 from .precond import BlockPreconditioner
 
 
-def solve(pr, mode="vcycle", assembled=False, data=None, schur=None):
+def solve(pr, mode="vcycle", assembled=False, data=None, schur=None, krylov=None):
+    """krylov: "minres" (default) or "fgmres" (Sec. 5), from the argument or pr.krylov."""
     d = data or SGData(pr)
     schur = schur or getattr(pr, "schur", "diagonal")
+    krylov = krylov or getattr(pr, "krylov", "minres")
     b = d.rhs()
     if assembled:
         K = d.kkt_matrix()
@@ -27,7 +29,10 @@ def solve(pr, mode="vcycle", assembled=False, data=None, schur=None):
     else:
         apply_A = d.kkt_apply
     Pc = BlockPreconditioner(d, mode, schur=schur)
-    res = minres(apply_A, Pc.apply, b, tol=pr.tol, max_iter=pr.max_iter)
+    if krylov == "fgmres":
+        res = fgmres(apply_A, Pc.apply, b, tol=pr.tol, max_iter=pr.max_iter)
+    else:
+        res = minres(apply_A, Pc.apply, b, tol=pr.tol, max_iter=pr.max_iter)
     res.data = d
     return res
 

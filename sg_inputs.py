@@ -60,6 +60,7 @@ class Problem:
     nu_post: int = 2
     omega: float = 0.8
     schur: str = "diagonal"     # time mode: "diagonal" (Z~, block-diagonal in time) or "coupled" (Z_bar)
+    krylov: str = "minres"      # "minres" or "fgmres" (the paper's Sec. 5 solver)
     name: str = ""
 
     @property
