@@ -99,6 +99,14 @@ typedef struct {
                             1: S_bar = (1/tau) Z_bar (D (x) M_gamma)^{-1} Z_bar^T with the coupled
                                Z_bar = I (x) Z~_t - C (x) M_cal (Eq. (S hat), Eq. (Z hat)): block
                                forward and backward substitution in time, one hGS sweep per step */
+  int32_t krylov;        /* 0: preconditioned MINRES (needs the symmetric positive definite
+                            preconditioner, the default); 1: flexible GMRES (Sec. 5), right
+                            preconditioned, Arnoldi by classical Gram-Schmidt with one
+                            reorthogonalisation, float64 Hessenberg and Givens scalars, restarted
+                            every `restart` iterations.  In mixed precision the inner solves use
+                            the same method in float32 vectors (one cycle each). */
+  int32_t restart;       /* FGMRES cycle length, 1..128 (64); memory grows with it: 2*restart + 1
+                            KKT vectors of the solve precision */
 } sgoc_options;
 
 typedef struct {

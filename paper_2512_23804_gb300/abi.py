@@ -36,7 +36,8 @@ class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("r", ctypes.c_int32),
                 ("cheb_steps", ctypes.c_int32), ("nu_pre", ctypes.c_int32), ("nu_post", ctypes.c_int32),
                 ("omega", ctypes.c_double), ("precision", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-                ("max_outer", ctypes.c_int32), ("schur", ctypes.c_int32)]
+                ("max_outer", ctypes.c_int32), ("schur", ctypes.c_int32), ("krylov", ctypes.c_int32),
+                ("restart", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):

@@ -3609,6 +3609,206 @@ cudaError_t launch_fill(T* x, int64_t n, T v, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// FGMRES kernels (Arnoldi with classical Gram-Schmidt and one reorthogonalisation:
+// each pass is one multi-dot and one multi-axpy over all basis vectors instead of
+// j + 1 dependent dot/axpy pairs).  Inner products in float64 (float32 operands by
+// the error-free float32 transformations of dot4_kernel); vector updates in the
+// vectors' type with the float64 coefficients rounded to it.
+// ---------------------------------------------------------------------------
+// one basis vector's partial inner product over a block's chunk: float64 operands in
+// float64; float32 operands four at a time by the error-free transformations of dot4_kernel
+// (V_i and w 16-byte aligned: ldv and the chunk are multiples of four entries)
+template <typename T>
+__device__ __forceinline__ double fg_partial(const T* __restrict__ v, const T* __restrict__ w, int64_t i0, int64_t i1);
+template <>
+__device__ __forceinline__ double fg_partial<double>(const double* __restrict__ v, const double* __restrict__ w,
+                                                    int64_t i0, int64_t i1) {
+  double S = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += 256) S = fma(v[i], w[i], S);
+  return S;
+}
+template <>
+__device__ __forceinline__ double fg_partial<float>(const float* __restrict__ v, const float* __restrict__ w,
+                                                   int64_t i0, int64_t i1) {
+  double S = 0.0;
+  float C = 0.0f;
+  const int64_t q0 = i0 >> 2, q1 = i1 >> 2;            // whole float4 groups of the chunk
+  const float4* v4 = reinterpret_cast<const float4*>(v);
+  const float4* w4 = reinterpret_cast<const float4*>(w);
+  for (int64_t q = q0 + threadIdx.x; q < q1; q += 256) dot4_exact(v4[q], w4[q], S, C);
+  double r = __dadd_rn(S, double(C));
+  for (int64_t i = (q1 << 2) + threadIdx.x; i < i1; i += 256) r = fma(double(v[i]), double(w[i]), r);
+  return r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) fgmres_multidot_kernel(const T* __restrict__ V, int64_t ldv,
+                                                              const T* __restrict__ w, int64_t n,
+                                                              const FgmresState* s, double* partial) {
+  pdl_enter();
+  const int count = s->j + 1;
+  const int64_t chunk = ((n + kDotBlocks - 1) / kDotBlocks + 3) & ~int64_t(3);
+  const int64_t i0 = min(n, int64_t(blockIdx.x) * chunk), i1 = min(n, i0 + chunk);
+  for (int c = 0; c < count; ++c) {
+    const double r = block_sum<256>(fg_partial<T>(V + int64_t(c) * ldv, w, i0, i1));
+    if (threadIdx.x == 0) partial[int64_t(c) * kDotBlocks + blockIdx.x] = r;
+  }
+}
+
+__global__ void fgmres_reduce_kernel(FgmresState* s, const double* partial, int second) {
+  pdl_enter();
+  const int c = blockIdx.x;
+  if (c > s->j) return;
+  const double r = reduce_partials(partial + int64_t(c) * kDotBlocks);
+  if (threadIdx.x == 0) (second ? s->h2 : s->h)[c] = r;
+}
+
+template <typename T>
+cudaError_t launch_fgmres_multidot(const T* V, int64_t ldv, const T* w, int64_t n, FgmresState* s, int second,
+                                   double* partial, cudaStream_t st) {
+  ProfScope ps(KK_DOT, st, double(sizeof(T)) * n * 2, double(n) * 2);
+  cudaError_t e = launch_pdl(fgmres_multidot_kernel<T>, dim3(kDotBlocks), dim3(256), size_t(0), st, V, ldv, w, n,
+                             static_cast<const FgmresState*>(s), partial);
+  if (e != cudaSuccess) return e;
+  note_launch();
+  e = launch_pdl(fgmres_reduce_kernel, dim3(kFgmresMax + 1), dim3(256), size_t(0), st, s,
+                 static_cast<const double*>(partial), second);
+  if (e != cudaSuccess) return e;
+  note_launch();
+  return cudaGetLastError();
+}
+
+// mode 0: w -= sum_{c <= j} h[c] V_c; mode 1: the same with h2; mode 2: w += sum_{c < j} y[c] V_c
+template <typename T, typename TX>
+__global__ void __launch_bounds__(256) fgmres_axpy_kernel(TX* w, const T* __restrict__ V, int64_t ldv, int64_t n,
+                                                          const FgmresState* s, int mode) {
+  pdl_enter();
+  const int count = mode == 2 ? s->j : s->j + 1;
+  const double* coef = mode == 0 ? s->h : mode == 1 ? s->h2 : s->y;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    TX acc = w[i];
+    for (int c = 0; c < count; ++c) {
+      const TX cf = TX(coef[c]);
+      acc = mode == 2 ? fma(cf, TX(V[int64_t(c) * ldv + i]), acc) : fma(-cf, TX(V[int64_t(c) * ldv + i]), acc);
+    }
+    w[i] = acc;
+  }
+}
+
+template <typename T, typename TX>
+cudaError_t launch_fgmres_axpy(TX* w, const T* V, int64_t ldv, int64_t n, const FgmresState* s, int mode,
+                               cudaStream_t st) {
+  ProfScope ps(KK_VECTOR, st, double(sizeof(T)) * n * 3, double(n) * 2);
+  const cudaError_t e = launch_pdl(fgmres_axpy_kernel<T, TX>, dim3(grid_for(n, 256)), dim3(256), size_t(0), st, w, V,
+                                   ldv, n, s, mode);
+  if (e != cudaSuccess) return e;
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void fgmres_start_kernel(FgmresState* s, const double* partial, double target, double bnorm) {
+  pdl_enter();
+  const double rr = reduce_partials(partial);
+  if (threadIdx.x != 0) return;
+  const double beta = sqrt(rr);
+  s->beta = beta;
+  s->target = target;
+  s->bnorm = bnorm;
+  s->est = beta / bnorm;
+  s->j = 0;
+  s->flag = (beta == beta) ? 0 : 4;
+  s->g[0] = beta;
+}
+
+cudaError_t launch_fgmres_start(FgmresState* s, const double* partial, double target, double bnorm,
+                                cudaStream_t st) {
+  ProfScope ps(KK_SCALAR, st, 8.0 * kDotBlocks, 2.0 * kDotBlocks);
+  const cudaError_t e = launch_pdl(fgmres_start_kernel, dim3(1), dim3(256), size_t(0), st, s, partial, target, bnorm);
+  if (e != cudaSuccess) return e;
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void fgmres_rotate_kernel(FgmresState* s, const double* partial) {
+  pdl_enter();
+  const double ww = reduce_partials(partial);
+  if (threadIdx.x != 0) return;
+  const int j = s->j;
+  constexpr int ld = kFgmresMax + 1;
+  double* col = s->H + int64_t(j) * ld;
+  for (int i = 0; i <= j; ++i) col[i] = s->h[i] + s->h2[i];
+  const double hn = sqrt(ww);
+  s->hnext = hn;
+  col[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {                        // previous rotations
+    const double a = col[i], b = col[i + 1];
+    col[i] = s->cs[i] * a + s->sn[i] * b;
+    col[i + 1] = -s->sn[i] * a + s->cs[i] * b;
+  }
+  const double rho = hypot(col[j], col[j + 1]);
+  s->j = j + 1;
+  if (!(rho == rho) || !(hn == hn)) { s->flag = 4; return; }
+  if (rho == 0.0) { s->flag = 2; return; }
+  const double c = col[j] / rho, sn = col[j + 1] / rho;
+  s->cs[j] = c; s->sn[j] = sn;
+  col[j] = rho;
+  col[j + 1] = 0.0;
+  const double gj = s->g[j];
+  s->g[j + 1] = -sn * gj;
+  s->g[j] = c * gj;
+  s->est = fabs(s->g[j + 1]) / s->bnorm;
+  if (s->est <= s->target) s->flag = 1;
+  else if (hn == 0.0) s->flag = 2;                    // lucky breakdown: the Krylov space is invariant
+}
+
+cudaError_t launch_fgmres_rotate(FgmresState* s, const double* partial, cudaStream_t st) {
+  ProfScope ps(KK_SCALAR, st, 8.0 * kDotBlocks, 2.0 * kDotBlocks);
+  const cudaError_t e = launch_pdl(fgmres_rotate_kernel, dim3(1), dim3(256), size_t(0), st, s, partial);
+  if (e != cudaSuccess) return e;
+  note_launch();
+  return cudaGetLastError();
+}
+
+__global__ void fgmres_solve_y_kernel(FgmresState* s) {
+  pdl_enter();
+  if (threadIdx.x != 0) return;
+  const int k = s->j;
+  constexpr int ld = kFgmresMax + 1;
+  for (int i = k - 1; i >= 0; --i) {                   // back substitution with the rotated H
+    double r = s->g[i];
+    for (int c = i + 1; c < k; ++c) r -= s->H[int64_t(c) * ld + i] * s->y[c];
+    s->y[i] = r / s->H[int64_t(i) * ld + i];
+  }
+}
+
+cudaError_t launch_fgmres_solve_y(FgmresState* s, cudaStream_t st) {
+  ProfScope ps(KK_SCALAR, st, 0.0, 0.0);
+  const cudaError_t e = launch_pdl(fgmres_solve_y_kernel, dim3(1), dim3(32), size_t(0), st, s);
+  if (e != cudaSuccess) return e;
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void fgmres_scale_kernel(const T* __restrict__ in, T* out, int64_t n, const FgmresState* s, int which) {
+  pdl_enter();
+  const double d = which == 0 ? s->beta : s->hnext;
+  const T a = T(d != 0.0 ? 1.0 / d : 0.0);
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = a * in[i];
+}
+
+template <typename T>
+cudaError_t launch_fgmres_scale(const T* in, T* out, int64_t n, const FgmresState* s, int which, cudaStream_t st) {
+  ProfScope ps(KK_VECTOR, st, double(sizeof(T)) * n * 2, double(n));
+  const cudaError_t e = launch_pdl(fgmres_scale_kernel<T>, dim3(grid_for(n, 256)), dim3(256), size_t(0), st, in, out,
+                                   n, s, which);
+  if (e != cudaSuccess) return e;
+  note_launch();
+  return cudaGetLastError();
+}
+
 // explicit instantiations
 #define SGOC_INST(T)                                                                                               \
   template cudaError_t launch_sg<T>(const SGArgs<T>&, cudaStream_t);                                               \
@@ -3639,6 +3839,17 @@ cudaError_t launch_fill(T* x, int64_t n, T v, cudaStream_t st) {
 
 SGOC_INST(float)
 SGOC_INST(double)
+template cudaError_t launch_fgmres_multidot<float>(const float*, int64_t, const float*, int64_t, FgmresState*, int,
+                                                   double*, cudaStream_t);
+template cudaError_t launch_fgmres_multidot<double>(const double*, int64_t, const double*, int64_t, FgmresState*,
+                                                    int, double*, cudaStream_t);
+template cudaError_t launch_fgmres_axpy<float, float>(float*, const float*, int64_t, int64_t, const FgmresState*,
+                                                      int, cudaStream_t);
+template cudaError_t launch_fgmres_axpy<double, double>(double*, const double*, int64_t, int64_t,
+                                                        const FgmresState*, int, cudaStream_t);
+template cudaError_t launch_fgmres_scale<float>(const float*, float*, int64_t, const FgmresState*, int, cudaStream_t);
+template cudaError_t launch_fgmres_scale<double>(const double*, double*, int64_t, const FgmresState*, int,
+                                                 cudaStream_t);
 template cudaError_t launch_minres_wx<double, double>(const double*, const double*, double*, double*, int64_t,
                                                       const MinresState*, cudaStream_t);
 template cudaError_t launch_minres_wx<float, float>(const float*, const float*, float*, float*, int64_t,

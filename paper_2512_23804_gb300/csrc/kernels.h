@@ -202,6 +202,43 @@ template <typename T, typename TX>
 cudaError_t launch_minres_wx(const T* z, const T* wm1, T* wm2, TX* x, int64_t n, const MinresState* s,
                              cudaStream_t st);
 
+// FGMRES scalar state (float64, device resident): the cycle's Hessenberg matrix after
+// its Givens rotations (column-major, leading dimension kFgmresMax + 1), the rotations,
+// the rotated right-hand side g, the Gram-Schmidt coefficients of the current column
+// and the least-squares solution y.
+constexpr int kFgmresMax = 128;
+struct FgmresState {
+  double beta;                         // ||r|| at the start of the cycle
+  double target, est;                  // stopping target and estimate |g_{j+1}| / ||b||
+  double bnorm;                        // ||b|| of the solve (estimates are relative to it)
+  double hnext;                        // ||w|| of the last column before its rotation
+  int j;                               // columns of the cycle so far
+  int flag;                            // 0 running, 1 est <= target, 2 breakdown, 4 NaN
+  double h[kFgmresMax + 1], h2[kFgmresMax + 1];
+  double cs[kFgmresMax], sn[kFgmresMax], g[kFgmresMax + 1], y[kFgmresMax];
+  double H[(kFgmresMax + 1) * kFgmresMax];
+};
+// h[0..count) (or h2 with second = 1) = V_i . w for the count = s->j + 1 basis vectors
+// V_i = V + i * ldv (n entries each); partial needs count * kDotBlocks doubles.
+template <typename T>
+cudaError_t launch_fgmres_multidot(const T* V, int64_t ldv, const T* w, int64_t n, FgmresState* s, int second,
+                                   double* partial, cudaStream_t st);
+// w -= sum_i c_i V_i over the s->j + 1 basis vectors, c = s->h (second = 0) or s->h2 (1);
+// with add = 1 instead x += sum_i y_i V_i over the s->j columns (the solution update).
+template <typename T, typename TX>
+cudaError_t launch_fgmres_axpy(TX* w, const T* V, int64_t ldv, int64_t n, const FgmresState* s, int mode,
+                               cudaStream_t st);
+// start of a cycle from the reduced partials of r . r: beta, g = (beta, 0, ...), j = 0
+cudaError_t launch_fgmres_start(FgmresState* s, const double* partial, double target, double bnorm,
+                                cudaStream_t st);
+// column j of H from h + h2 and the norm partials of w, rotations, estimate and flag; j += 1
+cudaError_t launch_fgmres_rotate(FgmresState* s, const double* partial, cudaStream_t st);
+// y from the triangular system of the cycle's s->j columns
+cudaError_t launch_fgmres_solve_y(FgmresState* s, cudaStream_t st);
+// out = in * (1 / s->beta) (which = 0) or in * (1 / s->hnext) (which = 1)
+template <typename T>
+cudaError_t launch_fgmres_scale(const T* in, T* out, int64_t n, const FgmresState* s, int which, cudaStream_t st);
+
 // elementwise helpers
 template <typename TA, typename TB>
 cudaError_t launch_convert(const TA* a, TB* b, int64_t n, cudaStream_t st);

@@ -83,6 +83,8 @@ void sgoc_default_options(sgoc_options* o) {
   o->inner_tol = 1e-3;
   o->max_outer = 20;
   o->schur = 0;
+  o->krylov = 0;
+  o->restart = 64;
 }
 
 namespace sgoc {
@@ -171,7 +173,8 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
   if (!(o.tol > 0) || o.max_iter < 1 || o.cheb_steps < 1 || o.cheb_steps > 64 || o.nu_pre < 0 || o.nu_post < 0 ||
       o.nu_pre > 16 || o.nu_post > 16 || o.nu_pre != o.nu_post || !(o.omega > 0 && o.omega < 2) ||
       (o.precision != SGOC_FP64 && o.precision != SGOC_MIXED_FP32) || !(o.inner_tol > 0 && o.inner_tol < 1) ||
-      o.max_outer < 1 || (o.schur != 0 && o.schur != 1)) {
+      o.max_outer < 1 || (o.schur != 0 && o.schur != 1) || (o.krylov != 0 && o.krylov != 1) ||
+      o.restart < 1 || o.restart > 128) {
     set_error("invalid options (nu_pre must equal nu_post for a symmetric V-cycle)");
     return SGOC_ERR_INVALID_ARG;
   }

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <deque>
 #include <iterator>
@@ -617,7 +618,17 @@ static void carve_minres(const sgoc_problem* pb, Carver& c, MinresVecs<T>& m) {
   m.wm2 = c.template take<T>(N);
 }
 
+// FGMRES workspace: basis V (restart + 1 vectors) and preconditioned vectors Z (restart), each
+// of ld entries (ld: N rounded up to 64 entries, so every vector starts 256-byte aligned),
+// the Arnoldi vector w, the scalar state and the multi-dot partials.
+struct FgWS {
+  void* V = nullptr; void* Z = nullptr; void* w = nullptr;
+  int64_t ld = 0; int m = 0;
+  FgmresState* st = nullptr; double* partial = nullptr;
+};
+
 struct Layout {
+  FgWS fg;
   KrylovWS64 k64{};
   MinresVecs<double> m64{};
   MinresVecs<float> m32{};
@@ -637,11 +648,23 @@ static size_t carve_layout(const sgoc_problem* pb, int precision, void* base, si
   L.k64.partial = c.take<double>(kDotBlocks);
   L.k64.scal = c.take<double>(16);
   L.k64.state = c.take<MinresState>(1);
+  const bool fg = pb->opt.krylov == 1;
+  if (fg) {
+    const int m = pb->opt.restart;
+    const size_t ld = (N + 63) & ~size_t(63);
+    const size_t es = precision == SGOC_FP64 ? 8 : 4;
+    L.fg.m = m; L.fg.ld = int64_t(ld);
+    L.fg.V = c.take<unsigned char>(es * ld * size_t(m + 1));
+    L.fg.Z = c.take<unsigned char>(es * ld * size_t(m));
+    L.fg.w = c.take<unsigned char>(es * ld);
+    L.fg.st = c.take<FgmresState>(1);
+    L.fg.partial = c.take<double>(size_t(kFgmresMax + 1) * kDotBlocks);
+  }
   if (precision == SGOC_FP64) {
-    carve_minres(pb, c, L.m64);
+    if (!fg) carve_minres(pb, c, L.m64);
     carve_prec(pb, c, L.p64);
   } else {
-    carve_minres(pb, c, L.m32);
+    if (!fg) carve_minres(pb, c, L.m32);
     L.rhs32 = c.take<float>(N);
     L.c32 = c.take<float>(N);
     carve_prec(pb, c, L.p32);
@@ -665,6 +688,7 @@ template <> MinresVecs<float>& vecs_of<float>(Layout& L) { return L.m32; }
 // scalars, a private capture stream and the captured MINRES iteration graphs.
 struct Runtime {
   MinresState* hstate = nullptr;
+  FgmresState* hfg = nullptr;          // pinned mirror of the FGMRES state header (allocated on first use)
   double* hscal = nullptr;
   cudaStream_t cap = nullptr;
   const void* ws = nullptr;
@@ -686,6 +710,7 @@ struct Runtime {
     if (fork.s3) cudaStreamDestroy(fork.s3);
     for (auto& e : fork.e) if (e) cudaEventDestroy(e);
     if (hstate) cudaFreeHost(hstate);
+    if (hfg) cudaFreeHost(hfg);
     if (hscal) cudaFreeHost(hscal);
   }
 };
@@ -1040,7 +1065,8 @@ static sgoc_status check_ws(void* ws, size_t bytes, size_t need) {
 // stopping rule and enqueues the next unit.  One host thread can thus keep many
 // solves in flight on their own streams (sgoc_solve_batch, the server).
 struct SolveTask {
-  enum Phase { BNORM, R0, START64, ITER64, CHECK64, OUTER, START32, ITER32, DONE };
+  enum Phase { BNORM, R0, START64, ITER64, CHECK64, OUTER, START32, ITER32, FSTART64, FITER64, FCHECK64,
+               FSTART32, FITER32, DONE };
   sgoc_problem* pb = nullptr;
   Runtime* rt = nullptr;
   Layout L;
@@ -1055,6 +1081,8 @@ struct SolveTask {
   Phase phase = DONE;
   double bnorm = 0, target = 0, rn = 0;
   int j = 0, jin = 0, par = 0, outer = 0, total = 0, last_flag = 0;
+  int fj = 0;                          // FGMRES: columns of the current cycle
+  bool fgmres() const { return pb->opt.krylov == 1; }
   sgoc_status status = SGOC_OK;
   sgoc_result result{};
   std::chrono::steady_clock::time_point t0;
@@ -1106,6 +1134,53 @@ struct SolveTask {
     pdl_fence(st);
     return SGOC_OK;
   }
+  // ---- FGMRES units (Sec. 5): one Arnoldi step per unit, the host reads the state header ----
+  sgoc_status fg_head() {
+    SGOC_CUDA_TRY(cudaMemcpyAsync(rt->hfg, L.fg.st, offsetof(FgmresState, h), cudaMemcpyDeviceToHost, st));
+    pdl_fence(st);
+    return record();
+  }
+  // a cycle from rhs (the residual of the current iterate): v_0 = rhs / ||rhs||
+  template <typename T>
+  sgoc_status fg_start(const T* rhs, double tgt, double bn) {
+    if (!rt->hfg) SGOC_CUDA_TRY(cudaMallocHost(&rt->hfg, sizeof(FgmresState)));
+    SGOC_LAUNCH(launch_dot_partial<T>(rhs, rhs, pb->N, L.k64.partial, st));
+    SGOC_LAUNCH(launch_fgmres_start(L.fg.st, L.k64.partial, tgt, bn, st));
+    SGOC_LAUNCH(launch_fgmres_scale<T>(rhs, static_cast<T*>(L.fg.V), pb->N, L.fg.st, 0, st));
+    fj = 0;
+    return fg_head();
+  }
+  // z_j = P^{-1} v_j, w = K z_j, two classical Gram-Schmidt passes, h_{j+1,j} = ||w||,
+  // rotations and estimate, v_{j+1} = w / h_{j+1,j}
+  template <typename T>
+  sgoc_status fg_iter() {
+    T* V = static_cast<T*>(L.fg.V);
+    T* Z = static_cast<T*>(L.fg.Z);
+    T* w = static_cast<T*>(L.fg.w);
+    const int64_t ld = L.fg.ld, N = pb->N;
+    SGOC_TRY(precond_apply<T>(pb, prec_of<T>(L), V + fj * ld, Z + fj * ld, st, fork_of(rt)));
+    SGOC_TRY(kkt_apply<T>(pb, Z + fj * ld, w, st, fork_of(rt)));
+    for (int pass = 0; pass < 2; ++pass) {
+      SGOC_LAUNCH(launch_fgmres_multidot<T>(V, ld, w, N, L.fg.st, pass, L.fg.partial, st));
+      SGOC_LAUNCH((launch_fgmres_axpy<T, T>(w, V, ld, N, L.fg.st, pass, st)));
+    }
+    SGOC_LAUNCH(launch_dot_partial<T>(w, w, N, L.k64.partial, st));
+    SGOC_LAUNCH(launch_fgmres_rotate(L.fg.st, L.k64.partial, st));
+    SGOC_LAUNCH(launch_fgmres_scale<T>(w, V + (fj + 1) * ld, N, L.fg.st, 1, st));
+    return fg_head();
+  }
+  // x += Z y for the cycle's columns (enqueued; the caller's next unit follows)
+  template <typename T, typename TX>
+  sgoc_status fg_end(TX* x) {
+    SGOC_LAUNCH(launch_fgmres_solve_y(L.fg.st, st));
+    SGOC_LAUNCH((launch_fgmres_axpy<T, TX>(x, static_cast<const T*>(L.fg.Z), L.fg.ld, pb->N, L.fg.st, 2, st)));
+    return SGOC_OK;
+  }
+  sgoc_status fg_state_error(const FgmresState& h) {
+    if (h.flag == 4) { set_error("NaN in FGMRES recurrences"); return SGOC_ERR_NAN; }
+    return SGOC_OK;
+  }
+
   sgoc_status finish(sgoc_status s) {
     status = s;
     phase = DONE;
@@ -1133,7 +1208,7 @@ struct SolveTask {
     carve_layout(pb, pb->opt.precision, d_ws, ws_bytes, L);
     SGOC_TRY(runtime_of(pb, &rt));
     graphs = !profile_enabled();
-    if (graphs) {
+    if (graphs && !fgmres()) {
       if (pb->opt.precision == SGOC_FP64) SGOC_TRY((ensure_graphs<double, double>(pb, *rt, L, ws, L.k64.x)));
       else SGOC_TRY((ensure_graphs<float, float>(pb, *rt, L, ws, L.c32)));
     }
@@ -1160,6 +1235,7 @@ struct SolveTask {
         if (pb->opt.precision != SGOC_FP64) { phase = OUTER; return launch_true_residual(); }
         if (x0) { phase = R0; return launch_true_residual(); }
         target = tol;
+        if (fgmres()) { phase = FSTART64; return fg_start<double>(L.k64.b, target, bnorm); }
         phase = START64;
         return launch_start<double, double>(L.k64.b, target);
       }
@@ -1169,6 +1245,11 @@ struct SolveTask {
         const double rn0 = std::sqrt(rt->hscal[0]);
         result.rel_true_residual = rn0 / bnorm;
         if (rn0 / bnorm <= tol) return finish(SGOC_OK);
+        if (fgmres()) {                              // estimates are relative to ||b||: target tol
+          target = tol;
+          phase = FSTART64;
+          return fg_start<double>(L.k64.r, target, bnorm);
+        }
         target = std::min(0.5, tol * bnorm / rn0);
         phase = START64;
         return launch_start<double, double>(L.k64.r, target);
@@ -1218,6 +1299,7 @@ struct SolveTask {
         // unit-norm residual in float32, inner solve K c = r / ||r||, then x += ||r|| c
         SGOC_LAUNCH(launch_scale_to32(L.k64.r, L.rhs32, N, 1.0 / rn, st));
         SGOC_LAUNCH(launch_fill<float>(L.c32, N, 0.0f, st));
+        if (fgmres()) { jin = 0; phase = FSTART32; return fg_start<float>(L.rhs32, pb->opt.inner_tol, 1.0); }
         phase = START32;
         return launch_start<float, float>(L.rhs32, pb->opt.inner_tol);
       }
@@ -1235,6 +1317,50 @@ struct SolveTask {
           return launch_true_residual();
         }
         return launch_iter<float, float>(L.c32);
+      }
+      case FSTART64:
+      case FSTART32: {
+        sgoc_status e = fg_state_error(*rt->hfg);
+        if (e != SGOC_OK) return fail(e);
+        phase = phase == FSTART64 ? FITER64 : FITER32;
+        if (phase == FITER64) return fg_iter<double>();
+        return fg_iter<float>();
+      }
+      case FITER64: {
+        const FgmresState hs = *rt->hfg;
+        ++j;
+        result.iterations = j; result.outer_iterations = 1; result.rel_estimate = hs.est;
+        sgoc_status e = fg_state_error(hs);
+        if (e != SGOC_OK) return fail(e);
+        fj = hs.j;
+        if (hs.flag == 0 && fj < L.fg.m && j < pb->opt.max_iter) return fg_iter<double>();
+        last_flag = hs.flag;
+        SGOC_TRY((fg_end<double, double>(L.k64.x)));
+        phase = FCHECK64;
+        return launch_true_residual();
+      }
+      case FCHECK64: {
+        const double rel = std::sqrt(rt->hscal[0]) / bnorm;
+        result.rel_true_residual = rel;
+        if (rel <= tol) return finish(SGOC_OK);
+        if (j >= pb->opt.max_iter) { set_error("FGMRES iteration limit reached"); return finish(SGOC_ERR_NO_CONVERGENCE); }
+        if (last_flag == 1) target *= tol / rel;       // the estimate fired early: tighten it
+        phase = FSTART64;                             // restart from the current iterate
+        return fg_start<double>(L.k64.r, target, bnorm);
+      }
+      case FITER32: {
+        const FgmresState hs = *rt->hfg;
+        ++jin; ++total;
+        result.rel_estimate = hs.est; result.iterations = total;
+        sgoc_status e = fg_state_error(hs);
+        if (e != SGOC_OK) return fail(e);
+        fj = hs.j;
+        if (hs.flag == 0 && fj < L.fg.m && jin < pb->opt.max_iter) return fg_iter<float>();
+        SGOC_TRY((fg_end<float, float>(L.c32)));
+        SGOC_LAUNCH(launch_add_scaled(L.c32, L.k64.x, N, rn, st));
+        ++outer;
+        phase = OUTER;
+        return launch_true_residual();
       }
       case DONE:
         return status;
@@ -1649,7 +1775,7 @@ static sgoc_status solve_batch_impl(int32_t count, sgoc_problem* const* pbs, voi
   if (merge) {
     std::vector<std::vector<int>> cand;
     for (int i = 0; i < count; ++i) {
-      if (tasks[i].phase == SolveTask::DONE) continue;
+      if (tasks[i].phase == SolveTask::DONE || pbs[i]->opt.krylov != 0) continue;   // MINRES iterations only
       const int esize = pbs[i]->opt.precision == SGOC_FP64 ? 8 : 4;
       const VPlan vp = plan_vcycle(pbs[i], esize);
       if (vp.lf != 0 || vp.cluster) continue;
