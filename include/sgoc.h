@@ -107,6 +107,9 @@ typedef struct {
                             the same method in float32 vectors (one cycle each). */
   int32_t restart;       /* FGMRES cycle length, 1..128 (64); memory grows with it: 2*restart + 1
                             KKT vectors of the solve precision */
+  int32_t mass_solve;    /* mass blocks 1 and 2 of the preconditioner (Sec. 5): 0 Chebyshev
+                            semi-iteration with cheb_steps steps (0); 1 exact solve with the
+                            (square-root-free) Cholesky factorisation of M = M1 (x) M1 */
 } sgoc_options;
 
 typedef struct {

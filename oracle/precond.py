@@ -157,10 +157,15 @@ class HGS:
 
 # ------------------------------------------------------- block preconditioner --
 class BlockPreconditioner:
-    def __init__(self, data, mode="vcycle", schur="diagonal"):
+    def __init__(self, data, mode="vcycle", schur="diagonal", mass_solve=None):
         assert schur in ("diagonal", "coupled")
         self.d = data
         self.schur = schur
+        # mass blocks 1, 2 (Sec. 5): Chebyshev semi-iteration, or the exact solve with M (the
+        # paper's Cholesky option), here a sparse LU factorisation of M
+        self.mass_solve = mass_solve or getattr(data.pr, "mass_solve", "chebyshev")
+        assert self.mass_solve in ("chebyshev", "exact")
+        self.mass_lu = spla.splu(sp.csc_matrix(data.Mass)) if self.mass_solve == "exact" else None
         pr = data.pr
         s = math.sqrt((1.0 + data.gamma) / data.beta)
         Mm = data.Mass
@@ -194,8 +199,8 @@ class BlockPreconditioner:
             R2 = d.mat(r[F:2 * F][sl])
             R3 = d.mat(r[2 * F:][sl])
             sc = 1.0 if d.nt == 0 else d.tau * Dw[t]
-            Z1 = chebyshev(Mm, R1, self.steps) / (sc * d.hgam[None, :])
-            Z2 = chebyshev(Mm, R2, self.steps) / (sc * d.beta)
+            Z1 = self.mass_inv(R1) / (sc * d.hgam[None, :])
+            Z2 = self.mass_inv(R2) / (sc * d.beta)
             W = self.hgs.apply(R3)
             if d.nt == 0:
                 Z3 = self.hgs.apply(Mm @ W * d.hgam[None, :])
@@ -205,6 +210,11 @@ class BlockPreconditioner:
             z[F:2 * F][sl] = d.vec(Z2)
             z[2 * F:][sl] = d.vec(Z3)
         return z
+
+    def mass_inv(self, B):
+        if self.mass_lu is not None:
+            return self.mass_lu.solve(B)
+        return chebyshev(self.d.Mass, B, self.steps)
 
     def _apply_coupled(self, r):
         """Time mode with the coupled Schur block: blocks 1 and 2 as in apply(); block 3
@@ -221,8 +231,8 @@ class BlockPreconditioner:
         for t in range(d.nt):
             sl = slice(t * nP, (t + 1) * nP)
             sc = d.tau * Dw[t]
-            z[:F][sl] = d.vec(chebyshev(Mm, d.mat(r[:F][sl]), self.steps) / (sc * d.hgam[None, :]))
-            z[F:2 * F][sl] = d.vec(chebyshev(Mm, d.mat(r[F:2 * F][sl]), self.steps) / (sc * d.beta))
+            z[:F][sl] = d.vec(self.mass_inv(d.mat(r[:F][sl])) / (sc * d.hgam[None, :]))
+            z[F:2 * F][sl] = d.vec(self.mass_inv(d.mat(r[F:2 * F][sl])) / (sc * d.beta))
         R3 = [d.mat(r[2 * F:][t * nP:(t + 1) * nP]) for t in range(d.nt)]
         X = []
         for t in range(d.nt):                       # Z_bar X = R3, forward in time

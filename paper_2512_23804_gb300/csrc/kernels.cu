@@ -1249,6 +1249,84 @@ __device__ __forceinline__ T cheb_scale(const ChebArgs<T>& a, int64_t col) {
   return T(1) / s;
 }
 
+// ---------------------------------------------------------------------------
+// Exact mass solve.  M = M1 (x) M1 (x fastest), M1 = L D L^T with L unit lower bidiagonal
+// (subdiagonal l_i) and D diagonal (reciprocals id_i): solve along y (a thread per grid
+// column x, coalesced across the warp), then along x (a CTA stages kMassRows rows of a
+// column in shared memory, a thread solves one row there), with the block scaling.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128) mass_exact_y_kernel(const T* __restrict__ B, T* X, int n1, int64_t n,
+                                                          const T* __restrict__ l, const T* __restrict__ id) {
+  pdl_enter();
+  const int ix = blockIdx.x * 128 + threadIdx.x;
+  if (ix >= n1) return;
+  const T* b = B + int64_t(blockIdx.y) * n + ix;
+  T* x = X + int64_t(blockIdx.y) * n + ix;
+  T z = b[0];
+  x[0] = z;
+  for (int iy = 1; iy < n1; ++iy) {                    // L z = b
+    z = fma(-l[iy], z, b[int64_t(iy) * n1]);
+    x[int64_t(iy) * n1] = z;
+  }
+  T v = z * id[n1 - 1];                                 // L^T x = D^{-1} z
+  x[int64_t(n1 - 1) * n1] = v;
+  for (int iy = n1 - 2; iy >= 0; --iy) {
+    v = fma(-l[iy + 1], v, x[int64_t(iy) * n1] * id[iy]);
+    x[int64_t(iy) * n1] = v;
+  }
+}
+
+template <typename T>
+__global__ void mass_exact_x_kernel(ChebArgs<T> a, const T* __restrict__ l, const T* __restrict__ id, int rows) {
+  extern __shared__ __align__(16) unsigned char mx_smem_raw[];
+  T* tile = reinterpret_cast<T*>(mx_smem_raw);        // [rows][s], s odd: the rows' threads hit distinct banks
+  pdl_enter();
+  const int n1 = a.n1, s = n1 | 1;
+  const int64_t c = blockIdx.y;
+  const int y0 = blockIdx.x * rows;
+  const int nr = min(rows, n1 - y0);
+  T* X = a.X + c * a.n + int64_t(y0) * n1;
+  for (int q = threadIdx.x; q < nr * n1; q += blockDim.x) {
+    const int r = q / n1, x = q - r * n1;
+    tile[r * s + x] = X[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < nr) {
+    T* row = tile + threadIdx.x * s;
+    T z = row[0];
+    for (int ix = 1; ix < n1; ++ix) { z = fma(-l[ix], z, row[ix]); row[ix] = z; }
+    T v = z * id[n1 - 1];
+    row[n1 - 1] = v;
+    for (int ix = n1 - 2; ix >= 0; --ix) { v = fma(-l[ix + 1], v, row[ix] * id[ix]); row[ix] = v; }
+  }
+  __syncthreads();
+  const T sc = cheb_scale(a, c);
+  for (int q = threadIdx.x; q < nr * n1; q += blockDim.x) {
+    const int r = q / n1, x = q - r * n1;
+    X[q] = sc * tile[r * s + x];
+  }
+}
+
+template <typename T>
+cudaError_t launch_mass_exact(const ChebArgs<T>& a, const T* l, const T* id, cudaStream_t st) {
+  if (a.ncols == 0) return cudaSuccess;
+  if (a.ncols > 65535) return cudaErrorInvalidValue;
+  ProfScope ps(KK_CHEB, st, double(sizeof(T)) * a.n * a.ncols * 4, double(a.n) * a.ncols * 8);
+  cudaError_t e = launch_pdl(mass_exact_y_kernel<T>, dim3(unsigned((a.n1 + 127) / 128), unsigned(a.ncols)), dim3(128),
+                             size_t(0), st, a.B, a.X, a.n1, a.n, l, id);
+  if (e != cudaSuccess) return e;
+  note_launch();
+  const int s = a.n1 | 1;
+  int rows = int(std::max<int64_t>(1, std::min<int64_t>(32, (48 * 1024) / (int64_t(s) * sizeof(T)))));
+  const int threads = std::max(32, ((rows + 31) / 32) * 32);
+  e = launch_pdl(mass_exact_x_kernel<T>, dim3(unsigned((a.n1 + rows - 1) / rows), unsigned(a.ncols)), dim3(threads),
+                 size_t(rows) * s * sizeof(T), st, a, l, id, rows);
+  if (e != cudaSuccess) return e;
+  note_launch();
+  return cudaGetLastError();
+}
+
 // omega_{k+1} of the Golub-Varga recurrence (omega_1 = 1), in float64 on host and device alike
 __host__ __device__ __forceinline__ double cheb_omega(int k, double rho, double prev) {
   if (k == 0) return 1.0;
@@ -3820,6 +3898,7 @@ cudaError_t launch_fgmres_scale(const T* in, T* out, int64_t n, const FgmresStat
   template bool sg_variant_feasible<T>(const SGArgs<T>&, int);                                                     \
   template cudaError_t launch_mass<T>(const MassArgs<T>&, cudaStream_t);                                           \
   template cudaError_t launch_cheb<T>(const ChebArgs<T>&, cudaStream_t);                                           \
+  template cudaError_t launch_mass_exact<T>(const ChebArgs<T>&, const T*, const T*, cudaStream_t);                 \
   template cudaError_t launch_smooth<T>(const T*, const T*, T*, int64_t, int, Stencil, T, T*, int64_t, int, int,   \
                                         cudaStream_t);                                                             \
   template cudaError_t launch_residual<T>(const T*, const T*, T*, int64_t, int, Stencil, cudaStream_t);            \

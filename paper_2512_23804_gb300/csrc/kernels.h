@@ -121,6 +121,13 @@ struct ChebArgs {
 template <typename T>
 cudaError_t launch_cheb(const ChebArgs<T>& a, cudaStream_t st);
 
+// Exact mass solve (the direct alternative to the Chebyshev semi-iteration): X = M^{-1} B on
+// a.ncols columns with M = M1 (x) M1 on the uniform grid, M1 = (h/6) tridiag(1, 4, 1), by
+// the square-root-free Cholesky factors of M1 (subdiagonal l, reciprocal pivots id; n1
+// entries) along y and then along x; the scaling of a.scale_mode as for launch_cheb.
+template <typename T>
+cudaError_t launch_mass_exact(const ChebArgs<T>& a, const T* l, const T* id, cudaStream_t st);
+
 // Multigrid level kernels on batches of columns stored contiguously [b][node].
 struct Stencil { double diag, edge, corner; };
 template <typename T>

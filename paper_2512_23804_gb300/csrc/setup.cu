@@ -85,6 +85,7 @@ void sgoc_default_options(sgoc_options* o) {
   o->schur = 0;
   o->krylov = 0;
   o->restart = 64;
+  o->mass_solve = 0;
 }
 
 namespace sgoc {
@@ -174,7 +175,7 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
       o.nu_pre > 16 || o.nu_post > 16 || o.nu_pre != o.nu_post || !(o.omega > 0 && o.omega < 2) ||
       (o.precision != SGOC_FP64 && o.precision != SGOC_MIXED_FP32) || !(o.inner_tol > 0 && o.inner_tol < 1) ||
       o.max_outer < 1 || (o.schur != 0 && o.schur != 1) || (o.krylov != 0 && o.krylov != 1) ||
-      o.restart < 1 || o.restart > 128) {
+      o.restart < 1 || o.restart > 128 || (o.mass_solve != 0 && o.mass_solve != 1)) {
     set_error("invalid options (nu_pre must equal nu_post for a symmetric V-cycle)");
     return SGOC_ERR_INVALID_ARG;
   }
@@ -323,6 +324,7 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
   off = align256(off + (pb->P + 1) * 4); off = align256(off + pb->P * 4); off = align256(off + nnz_dn * 4);
   off = align256(off + nnz_dn * 4); off = align256(off + nnz_dn * 8); off = align256(off + nnz_dn * 4);
   for (const UTab& u : pb->utabs) off += utab_bytes(u);
+  off += 2 * align256(size_t(pb->n1) * 8) + 2 * align256(size_t(pb->n1) * 4);   // mass factor tables
   pb->persistent_bytes = off;
   *out = pb;
   return SGOC_OK;
@@ -401,6 +403,29 @@ sgoc_status sgoc_problem_upload(sgoc_problem* pb, void* d_persistent, size_t byt
     e32s.push_back(std::move(e32));
   }
 
+  pb->dev.mass_l64 = reinterpret_cast<double*>(carve(size_t(pb->n1) * 8));
+  pb->dev.mass_id64 = reinterpret_cast<double*>(carve(size_t(pb->n1) * 8));
+  pb->dev.mass_l32 = reinterpret_cast<float*>(carve(size_t(pb->n1) * 4));
+  pb->dev.mass_id32 = reinterpret_cast<float*>(carve(size_t(pb->n1) * 4));
+  // M1 = a tridiag(1, 4, 1), a = h/6: D_0 = 4a, l_i = a / D_{i-1}, D_i = 4a - a l_i
+  std::vector<double> l(pb->n1, 0.0), id(pb->n1);
+  std::vector<float> l32, id32;
+  {
+    const double a = 1.0 / (6.0 * pb->nx);
+    double D = 4.0 * a;
+    id[0] = 1.0 / D;
+    for (int i = 1; i < pb->n1; ++i) {
+      l[i] = a / D;
+      D = 4.0 * a - a * l[i];
+      id[i] = 1.0 / D;
+    }
+    l32.assign(l.begin(), l.end());
+    id32.assign(id.begin(), id.end());
+    SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.mass_l64, l.data(), l.size() * 8, cudaMemcpyHostToDevice, st));
+    SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.mass_id64, id.data(), id.size() * 8, cudaMemcpyHostToDevice, st));
+    SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.mass_l32, l32.data(), l32.size() * 4, cudaMemcpyHostToDevice, st));
+    SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.mass_id32, id32.data(), id32.size() * 4, cudaMemcpyHostToDevice, st));
+  }
   std::vector<double> k64(nk);
   std::vector<float> k32(nk);
   for (size_t i = 0; i < nk; ++i) { k64[i] = pb->kappa[i] / 6.0; k32[i] = float(k64[i]); }

@@ -73,6 +73,10 @@ struct DevData {
   int* dn_k = nullptr;
   double* dn_c64 = nullptr;
   float* dn_c32 = nullptr;
+  // square-root-free Cholesky M1 = L D L^T of the 1-D mass matrix (h/6) tridiag(1, 4, 1):
+  // subdiagonal l_i of L (l_0 = 0) and 1 / D_i, n1 entries each (the exact mass solve)
+  double* mass_l64 = nullptr; double* mass_id64 = nullptr;
+  float* mass_l32 = nullptr; float* mass_id32 = nullptr;
   double* yhat = nullptr;      // slabs x n target values
   double* y0 = nullptr;        // n initial state (zeros when absent)
 };

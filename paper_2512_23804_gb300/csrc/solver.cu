@@ -521,6 +521,20 @@ static sgoc_status kkt_apply(const sgoc_problem* pb, const T* v, T* w, cudaStrea
   return SGOC_OK;
 }
 
+// The mass blocks 1 and 2: Chebyshev semi-iteration, or the exact solve (sgoc_options.mass_solve)
+template <typename T> static const T* mass_l_of(const sgoc_problem* pb);
+template <> const double* mass_l_of<double>(const sgoc_problem* pb) { return pb->dev.mass_l64; }
+template <> const float* mass_l_of<float>(const sgoc_problem* pb) { return pb->dev.mass_l32; }
+template <typename T> static const T* mass_id_of(const sgoc_problem* pb);
+template <> const double* mass_id_of<double>(const sgoc_problem* pb) { return pb->dev.mass_id64; }
+template <> const float* mass_id_of<float>(const sgoc_problem* pb) { return pb->dev.mass_id32; }
+
+template <typename T>
+static cudaError_t launch_mass_blocks(const sgoc_problem* pb, const ChebArgs<T>& c, cudaStream_t st) {
+  if (pb->opt.mass_solve == 1) return launch_mass_exact<T>(c, mass_l_of<T>(pb), mass_id_of<T>(pb), st);
+  return launch_cheb<T>(c, st);
+}
+
 // ------------------------------------------------ coupled time Schur block --
 // z = tau Z_bar^{-T} (D (x) M_gamma) Z_bar^{-1} r with Z_bar = I (x) Z~_t - C (x) M_cal (Eq. (S hat),
 // Eq. (Z hat)): Z_bar x = r by forward substitution, Z~ x_t = r_t + M_cal x_{t-1}, and
@@ -577,7 +591,7 @@ static sgoc_status precond_apply(const sgoc_problem* pb, PrecWS<T>& w, const T* 
   cudaStream_t sc = st;
   if (f) { SGOC_TRY(fork_to(st, f->s1, f->e[3])); sc = f->s1; }
   if (before_cheb) SGOC_TRY(before_cheb(sc));       // work only the Chebyshev blocks wait for
-  SGOC_LAUNCH(launch_cheb<T>(c, sc));
+  SGOC_LAUNCH(launch_mass_blocks<T>(pb, c, sc));
   // block 3: S^{-1} = Z^{-1} M_gamma Z^{-1} (steady), tau Z~^{-1} (D (x) M_gamma) Z~^{-1} (time)
   if (pb->nt > 1 && pb->opt.schur == 1) {
     SGOC_TRY(coupled_schur<T>(pb, w, r + 2 * F, z + 2 * F, st));
@@ -918,7 +932,7 @@ static sgoc_status group_step(const std::vector<GroupMember>& gm, GroupRuntime& 
     cudaStream_t sc = cs;
     if (f) { SGOC_TRY(fork_to(cs, f->s1, f->e[3])); sc = f->s1; }
     SGOC_LAUNCH(launch_minres_v<T>(v.Kz, v.v, v.vp, F2, L.k64.state, sc));
-    SGOC_LAUNCH(launch_cheb<T>(c, sc));
+    SGOC_LAUNCH(launch_mass_blocks<T>(pb, c, sc));
     SGOC_TRY(fork_to(cs, gs, gr.ev[6 * g + 1]));
   }
   // B: the first hGS sweep of every member, merged

@@ -31,7 +31,7 @@ class SGProblem:
 
     def __init__(self, nx, M, p, kappa, beta, yhat, gamma=0.0, nt=0, T=1.0, y0=None, *, tol=1e-8,
                  max_iter=1000, r=0, cheb_steps=5, nu=2, omega=0.8, precision="fp64", inner_tol=1e-3,
-                 max_outer=20, schur="diagonal", krylov="minres", restart=64):
+                 max_outer=20, schur="diagonal", krylov="minres", restart=64, mass_solve="chebyshev"):
         self._handle = None
         lib = abi.load()
         self._kappa = np.ascontiguousarray(kappa, dtype=np.float64)
@@ -48,6 +48,7 @@ class SGProblem:
         opts.schur = {"diagonal": 0, "coupled": 1}[schur]
         opts.krylov = {"minres": 0, "fgmres": 1}[krylov]
         opts.restart = restart
+        opts.mass_solve = {"chebyshev": 0, "exact": 1}[mass_solve]
         h = ctypes.c_void_p()
         abi.check(lib.sgoc_problem_create(ctypes.byref(desc), ctypes.byref(opts), ctypes.byref(h)),
                   "sgoc_problem_create")
@@ -72,7 +73,8 @@ class SGProblem:
         r = getattr(pr, "r", -1)
         args = dict(gamma=pr.gamma, nt=pr.nt, T=pr.T, y0=pr.y0, tol=pr.tol, max_iter=pr.max_iter,
                     r=0 if r is None or r < 0 else r, cheb_steps=pr.cheb_steps, nu=pr.nu_pre, omega=pr.omega,
-                    schur=getattr(pr, "schur", "diagonal"), krylov=getattr(pr, "krylov", "minres"))
+                    schur=getattr(pr, "schur", "diagonal"), krylov=getattr(pr, "krylov", "minres"),
+                    mass_solve=getattr(pr, "mass_solve", "chebyshev"))
         args.update(kw)
         return cls(pr.nx, pr.M, pr.p, pr.kappa, pr.beta, pr.yhat, **args)
 

@@ -61,6 +61,7 @@ class Problem:
     omega: float = 0.8
     schur: str = "diagonal"     # time mode: "diagonal" (Z~, block-diagonal in time) or "coupled" (Z_bar)
     krylov: str = "minres"      # "minres" or "fgmres" (the paper's Sec. 5 solver)
+    mass_solve: str = "chebyshev"   # mass blocks: "chebyshev" (cheb_steps) or "exact" (Cholesky)
     name: str = ""
 
     @property

@@ -282,3 +282,18 @@ def test_coupled_schur_minres_converges_to_the_direct_solution():
     assert rc.status == "ok" and rc.rel_true <= pr.tol
     assert np.linalg.norm(rc.x - xd) <= 1e-6 * np.linalg.norm(xd)
     assert rc.iterations <= rd.iterations, (rc.iterations, rd.iterations)
+
+
+def test_exact_mass_blocks_are_the_inverse_mass():
+    """mass_solve = "exact": blocks 1 and 2 are exactly K11^{-1} and K22^{-1} (no Chebyshev
+    error), steady and time."""
+    for nt in (0, 3):
+        pr = _problem(nt, 0.5 if nt == 0 else 0.0, 0.3, 3)
+        pr.cheb_steps = 2                     # a poor Chebyshev: the exact option must not use it
+        pr.mass_solve = "exact"
+        d = SGData(pr)
+        F, K11, K22, K31, K32 = _blocks(d)
+        rv = np.random.default_rng(nt).standard_normal(3 * F)
+        z = BlockPreconditioner(d).apply(rv)
+        assert np.linalg.norm(K11 @ z[:F] - rv[:F]) <= 1e-13 * np.linalg.norm(rv[:F])
+        assert np.linalg.norm(K22 @ z[F:2 * F] - rv[F:2 * F]) <= 1e-13 * np.linalg.norm(rv[F:2 * F])
