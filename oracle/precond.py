@@ -246,3 +246,88 @@ class BlockPreconditioner:
         for t in range(d.nt):
             z[2 * F:][t * nP:(t + 1) * nP] = d.vec(Z[t])
         return z
+
+
+# -------------------------------------------------------------------- hGSoc --
+class HGSoc:
+    """The hGS preconditioner for the optimal control problem (Alg. 2-3, steady) and its
+    parallel-in-time form (Alg. 4: Alg. 2-3 on every time slab, the slabs independent).
+
+    Levels are visited 0, 1, ..., p, ..., 1, 0.  At a visit of level l the three fields of
+    the level's columns are set (overwritten, as in the algorithm) by one solve with
+    P~ = blkdiag(M, beta M, A~_1) of the right-hand side R_(l) minus the couplings of the
+    (truncated) KKT matrix to the other levels, with their current values:
+      Y: R^Y_(l) + c sum_{k=1}^{r-1} (K_k V^Lambda G_k)_(l)      (the -A^T Lambda row, Eq. (stoch-system))
+      U: R^U_(l)                                                  (beta M and M do not couple levels)
+      L: R^L_(l) + c sum_{k=1}^{r-1} (K_k V^Y G_k)_(l)           (the -A Y row)
+    with c = 1 steady, tau in time mode (the slab operator L = I (x) M + tau A).  G_k couples
+    only neighbouring levels and the level's own block is replaced by P~, so the terms
+    C, E, F, H of Alg. 2-3 (couplings through H^gamma and H_1, both diagonal here) vanish.
+    Reading of P~'s third block (the paper writes A~_1 and calls P~ "derived from the blocks
+    of the deterministic KKT system"): third="schur" (default) takes the deterministic
+    Schur-complement approximation S~_1 = A~_1 M^{-1} A~_1 (the n_xi = 1 case of
+    Eq. (mathcalZ)), so the Lambda solve is A~_1^{-1} M A~_1^{-1}: two mean solves.
+    third="literal" takes A~_1 itself (one mean solve); with it FGMRES does not converge on
+    the test problems (the block has the scale of a stiffness matrix, not of the Schur
+    complement), so the hot path uses the first reading.
+    Time mode (reading of Alg. 4): P~_t = blkdiag(tau D_t M, beta tau D_t M, S~_t) on slab t with
+    S~_t = (1/tau) A^_1 (D_t M)^{-1} A^_1 (the one-slab case of Eq. (S hat) / Eq. (S_tilde)).
+    Mass solves as in BlockPreconditioner (Chebyshev or exact); mean solves by one V-cycle
+    (or exactly in 'exact' mode).
+    """
+
+    def __init__(self, data, mode="vcycle", mass_solve=None, third="schur"):
+        assert third in ("schur", "literal")
+        self.third = third
+        self.d = data
+        pr = data.pr
+        s = math.sqrt((1.0 + data.gamma) / data.beta)
+        Mm = data.Mass
+        if data.nt == 0:
+            A0 = data.K[0] + s * Mm
+            self.coef = 1.0
+        else:
+            A0 = (1.0 + data.tau * s) * Mm + data.tau * data.K[0]
+            self.coef = data.tau
+        self.A0 = A0
+        self.B = ExactSolve(A0) if mode == "exact" else VCycle(A0, data.nx, pr.nu_pre, pr.nu_post, pr.omega)
+        self.r = pr.trunc
+        self.off = basis.level_offsets(data.M, data.p)
+        self.mass = BlockPreconditioner.__new__(BlockPreconditioner)     # only its mass solver
+        self.mass.d = data
+        self.mass.steps = pr.cheb_steps
+        self.mass.mass_solve = mass_solve or getattr(pr, "mass_solve", "chebyshev")
+        self.mass.mass_lu = spla.splu(sp.csc_matrix(Mm)) if self.mass.mass_solve == "exact" else None
+
+    def coupling(self, V):
+        """c sum_{k=1}^{r-1} K_k V G_k (all columns)."""
+        d = self.d
+        out = np.zeros_like(V)
+        for k in range(1, self.r):
+            out += d.K[k] @ V @ d.G[k]
+        return self.coef * out
+
+    def apply(self, rvec):
+        d = self.d
+        F = d.slabs * d.P * d.n
+        nP = d.P * d.n
+        Dw = d.d_weights()
+        z = np.zeros_like(rvec)
+        for t in range(d.slabs):
+            sl = slice(t * nP, (t + 1) * nP)
+            RY, RU, RL = d.mat(rvec[:F][sl]), d.mat(rvec[F:2 * F][sl]), d.mat(rvec[2 * F:][sl])
+            sc = 1.0 if d.nt == 0 else d.tau * Dw[t]
+            VU = self.mass.mass_inv(RU) / (sc * d.beta)
+            VY = np.zeros_like(RY)
+            VL = np.zeros_like(RL)
+            for lev in visit_order(d.p):
+                a, b = self.off[lev], self.off[lev + 1]
+                cY = RY[:, a:b] + self.coupling(VL)[:, a:b]
+                cL = RL[:, a:b] + self.coupling(VY)[:, a:b]
+                VY[:, a:b] = self.mass.mass_inv(cY) / sc
+                if self.third == "literal":
+                    VL[:, a:b] = self.B.apply(cL)
+                else:
+                    VL[:, a:b] = sc * self.B.apply(d.Mass @ self.B.apply(cL))
+            z[:F][sl], z[F:2 * F][sl], z[2 * F:][sl] = d.vec(VY), d.vec(VU), d.vec(VL)
+        return z

@@ -14,7 +14,7 @@ import scipy.sparse.linalg as spla
 
 from .krylov import fgmres, minres
 from .operators import SGData
-from .precond import BlockPreconditioner
+from .precond import BlockPreconditioner, HGSoc
 
 
 def solve(pr, mode="vcycle", assembled=False, data=None, schur=None, krylov=None):
@@ -28,7 +28,11 @@ def solve(pr, mode="vcycle", assembled=False, data=None, schur=None, krylov=None
         apply_A = lambda v: K @ v
     else:
         apply_A = d.kkt_apply
-    Pc = BlockPreconditioner(d, mode, schur=schur)
+    if getattr(pr, "precond", "block") == "hgsoc":          # Alg. 2-3 / Alg. 4: not symmetric
+        Pc = HGSoc(d, mode)
+        krylov = "fgmres"
+    else:
+        Pc = BlockPreconditioner(d, mode, schur=schur)
     if krylov == "fgmres":
         res = fgmres(apply_A, Pc.apply, b, tol=pr.tol, max_iter=pr.max_iter)
     else:

@@ -62,6 +62,7 @@ class Problem:
     schur: str = "diagonal"     # time mode: "diagonal" (Z~, block-diagonal in time) or "coupled" (Z_bar)
     krylov: str = "minres"      # "minres" or "fgmres" (the paper's Sec. 5 solver)
     mass_solve: str = "chebyshev"   # mass blocks: "chebyshev" (cheb_steps) or "exact" (Cholesky)
+    precond: str = "block"          # "block" (Eq. (stoch-prec) with hGS) or "hgsoc" (Alg. 2-3 / Alg. 4)
     name: str = ""
 
     @property

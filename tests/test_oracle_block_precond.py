@@ -297,3 +297,90 @@ def test_exact_mass_blocks_are_the_inverse_mass():
         z = BlockPreconditioner(d).apply(rv)
         assert np.linalg.norm(K11 @ z[:F] - rv[:F]) <= 1e-13 * np.linalg.norm(rv[:F])
         assert np.linalg.norm(K22 @ z[F:2 * F] - rv[F:2 * F]) <= 1e-13 * np.linalg.norm(rv[F:2 * F])
+
+
+def _hgsoc_dense(d, r_trunc, third_block):
+    """Symmetric block Gauss-Seidel over the chaos levels of the (truncated) KKT matrix, with
+    each level's own block replaced by P~ (third_block: the (3,3) block per chaos column),
+    for the block-diagonal-in-time part of the KKT matrix: forward sweep (D + L)^{-1} R, then
+    the backward sweep (D + U)^{-1} (R - L x_f)."""
+    K = d.kkt_matrix().toarray()
+    n, P, S = d.n, d.P, d.slabs
+    F = S * P * n
+    off = basis.level_offsets(d.M, d.p)
+    lev = np.zeros(P, dtype=int)
+    for dd in range(d.p + 1):
+        lev[off[dd]:off[dd + 1]] = dd
+    idx = basis.multi_indices(d.M, d.p)
+    keep = np.ones((P, P), dtype=bool)
+    for a in range(P):
+        for b in range(P):
+            diff = idx[a].astype(int) - idx[b].astype(int)
+            nz = np.nonzero(diff)[0]
+            if len(nz) == 1 and abs(diff[nz[0]]) == 1 and nz[0] + 1 >= r_trunc:
+                keep[a, b] = False                      # a coupling dropped by the truncation
+    # unknown u = (field f, slab t, chaos alpha, node i) at f*F + t*P*n + alpha*n + i
+    N3 = 3 * F
+    field = np.repeat(np.arange(3), F)
+    slab = np.tile(np.repeat(np.arange(S), P * n), 3)
+    alpha = np.tile(np.repeat(np.arange(P), n), 3 * S)
+    L = np.zeros_like(K)
+    U = np.zeros_like(K)
+    same_slab = slab[:, None] == slab[None, :]
+    la, lb = lev[alpha][:, None], lev[alpha][None, :]
+    kp = keep[alpha[:, None], alpha[None, :]]
+    L[(la > lb) & same_slab & kp] = K[(la > lb) & same_slab & kp]
+    U[(la < lb) & same_slab & kp] = K[(la < lb) & same_slab & kp]
+    Dm = np.zeros_like(K)
+    Dw = d.d_weights()
+    Mm = d.Mass.toarray()
+    for t in range(S):
+        sc = 1.0 if d.nt == 0 else d.tau * Dw[t]
+        for a in range(P):
+            for f, blk in ((0, sc * Mm), (1, sc * d.beta * Mm), (2, third_block(sc))):
+                o = f * F + t * P * n + a * n
+                Dm[o:o + n, o:o + n] = blk
+    def apply(R):
+        xf = np.linalg.solve(Dm + L, R)
+        return np.linalg.solve(Dm + U, R - L @ xf)
+    return apply
+
+
+@pytest.mark.parametrize("nt,gamma,sigma,r", [(0, 0.0, 0.3, 3), (0, 0.5, 0.3, 2), (3, 0.0, 0.3, 3), (0, 0.0, 0.0, 3)])
+def test_hgsoc_equals_symmetric_block_gauss_seidel(nt, gamma, sigma, r):
+    """Alg. 2-3 (Alg. 4 per slab) with exact mass and mean solves is the symmetric block
+    Gauss-Seidel sweep over the chaos levels of the truncated KKT matrix (block-diagonal in
+    time) whose level blocks are P~ = blkdiag(M, beta M, A~_1 M^{-1} A~_1) (time:
+    blkdiag(tau D_t M, beta tau D_t M, (1/tau) A^_1 (D_t M)^{-1} A^_1)): the paper's sweep
+    order 0..p-1, p, p-1..0 solves level p once, as the symmetric sweep does."""
+    from oracle.precond import HGSoc
+    pr = _problem(nt, gamma, sigma, r)
+    pr.mass_solve = "exact"
+    d = SGData(pr)
+    H = HGSoc(d, mode="exact")
+    A0 = H.A0.toarray()
+    Mm = d.Mass.toarray()
+    Dw = d.d_weights()
+    third = lambda sc: A0 @ np.linalg.solve(sc * Mm, A0)
+    ref = _hgsoc_dense(d, r, third)
+    rv = np.random.default_rng(13).standard_normal(3 * d.slabs * d.P * d.n)
+    assert np.linalg.norm(H.apply(rv) - ref(rv)) <= 1e-10 * np.linalg.norm(ref(rv))
+    Hl = HGSoc(d, mode="exact", third="literal")
+    refl = _hgsoc_dense(d, r, lambda sc: A0)
+    assert np.linalg.norm(Hl.apply(rv) - refl(rv)) <= 1e-10 * np.linalg.norm(refl(rv))
+
+
+def test_hgsoc_fgmres_converges_and_the_literal_block_does_not():
+    """FGMRES with hGSoc reaches the direct solution; with P~'s third block read literally as
+    A~_1 it stalls (the reason the Schur reading is taken)."""
+    from oracle.krylov import fgmres
+    from oracle.precond import HGSoc
+    from oracle.solve import direct_solve
+    pr = si.random_small(3, nx=8, M=2, p=2, beta=1e-2)
+    d = SGData(pr)
+    b = d.rhs()
+    xd = direct_solve(pr)
+    res = fgmres(d.kkt_apply, HGSoc(d).apply, b, tol=1e-9)
+    assert res.status == "ok" and np.linalg.norm(res.x - xd) <= 1e-7 * np.linalg.norm(xd)
+    lit = fgmres(d.kkt_apply, HGSoc(d, third="literal").apply, b, tol=1e-9, max_iter=150)
+    assert lit.status != "ok" and lit.rel_true > 1e-4
