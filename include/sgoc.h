@@ -110,6 +110,13 @@ typedef struct {
   int32_t mass_solve;    /* mass blocks 1 and 2 of the preconditioner (Sec. 5): 0 Chebyshev
                             semi-iteration with cheb_steps steps (0); 1 exact solve with the
                             (square-root-free) Cholesky factorisation of M = M1 (x) M1 */
+  int32_t precond;       /* 0: block-diagonal preconditioner of Eq. (stoch-prec) / Eq. (precon
+                            for time) with the hGS Schur block (0); 1: hGSoc, the hierarchical
+                            Gauss-Seidel sweep over the coupled KKT system (Alg. 2-3; in time mode
+                            Alg. 4, every slab independently) with level blocks
+                            P~ = blkdiag(M, beta M, A~_1 M^{-1} A~_1), time
+                            blkdiag(tau D_t M, beta tau D_t M, (1/tau) A^_1 (D_t M)^{-1} A^_1).  Not
+                            symmetric: requires krylov = 1 (FGMRES) */
 } sgoc_options;
 
 typedef struct {

@@ -37,7 +37,7 @@ class Options(ctypes.Structure):
                 ("cheb_steps", ctypes.c_int32), ("nu_pre", ctypes.c_int32), ("nu_post", ctypes.c_int32),
                 ("omega", ctypes.c_double), ("precision", ctypes.c_int32), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int32), ("schur", ctypes.c_int32), ("krylov", ctypes.c_int32),
-                ("restart", ctypes.c_int32), ("mass_solve", ctypes.c_int32)]
+                ("restart", ctypes.c_int32), ("mass_solve", ctypes.c_int32), ("precond", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):

@@ -1240,6 +1240,7 @@ cudaError_t launch_mass(const MassArgs<T>& a, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ T cheb_scale(const ChebArgs<T>& a, int64_t col) {
+  if (a.scale_mode == 2) return a.scale;
   if (a.scale_mode != 1) return T(1);
   const int64_t sp = int64_t(a.slabs) * a.P;
   const int64_t blk = col / sp, cc = col % sp;

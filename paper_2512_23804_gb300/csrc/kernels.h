@@ -111,12 +111,14 @@ cudaError_t launch_mass(const MassArgs<T>& a, cudaStream_t st);
 // Chebyshev semi-iteration for M X = B on ncols columns of n entries
 // (textbook Golub-Varga weights, D = 5/4 diag(M), rho = 4/5).
 // scale_mode 0: X scaled by 1; 1: block-preconditioner scaling of the
-// (1,1)/(2,2) blocks (1/(sc_t H^gamma) for the first slabs*P columns, 1/(sc_t beta) after).
+// (1,1)/(2,2) blocks (1/(sc_t H^gamma) for the first slabs*P columns, 1/(sc_t beta) after);
+// 2: X scaled by `scale`.
 template <typename T>
 struct ChebArgs {
   const T* B; T* X; T* tmpA; T* tmpB;
   int64_t ncols; int n1; int64_t n; int steps; T mass;
   int scale_mode; int P; int slabs; int nt; T tau; T beta; T gamma;
+  T scale;
 };
 template <typename T>
 cudaError_t launch_cheb(const ChebArgs<T>& a, cudaStream_t st);

@@ -86,6 +86,7 @@ void sgoc_default_options(sgoc_options* o) {
   o->krylov = 0;
   o->restart = 64;
   o->mass_solve = 0;
+  o->precond = 0;
 }
 
 namespace sgoc {
@@ -175,7 +176,8 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
       o.nu_pre > 16 || o.nu_post > 16 || o.nu_pre != o.nu_post || !(o.omega > 0 && o.omega < 2) ||
       (o.precision != SGOC_FP64 && o.precision != SGOC_MIXED_FP32) || !(o.inner_tol > 0 && o.inner_tol < 1) ||
       o.max_outer < 1 || (o.schur != 0 && o.schur != 1) || (o.krylov != 0 && o.krylov != 1) ||
-      o.restart < 1 || o.restart > 128 || (o.mass_solve != 0 && o.mass_solve != 1)) {
+      o.restart < 1 || o.restart > 128 || (o.mass_solve != 0 && o.mass_solve != 1) ||
+      (o.precond != 0 && o.precond != 1) || (o.precond == 1 && o.krylov != 1)) {
     set_error("invalid options (nu_pre must equal nu_post for a symmetric V-cycle)");
     return SGOC_ERR_INVALID_ARG;
   }

@@ -575,12 +575,73 @@ static sgoc_status coupled_schur(const sgoc_problem* pb, PrecWS<T>& w, const T* 
   return SGOC_OK;
 }
 
+// -------------------------------------------------------------------- hGSoc --
+// The hGS preconditioner for the optimal control problem (Alg. 2-3) on slab t of r (every slab
+// independently: Alg. 4), into z.  Levels 0, 1, ..., p, ..., 1, 0; at a visit of level d the
+// level's three fields are overwritten by one solve with
+//   P~ = blkdiag(sc M, beta sc M, (1/sc) A~ M^{-1} A~)     (sc = 1 steady, tau D_t in time mode)
+// of R_(d) plus the truncated couplings to the other levels: Y from c K_k Lambda G_k, Lambda from
+// c K_k Y G_k (c = 1, or tau); the U block has no coupling and is solved once.  First visits need
+// the couplings to the level below only (the levels above are still zero): the downward table.
+template <typename T>
+static sgoc_status hgsoc_slab(const sgoc_problem* pb, PrecWS<T>& w, const T* r, T* z, int t, cudaStream_t st) {
+  const int64_t F = pb->F, n = pb->n, ps = int64_t(pb->P) * n;
+  const bool time = pb->nt > 0;
+  const double sc = time ? pb->tau * pb->dweights[t] : 1.0;
+  const T cK = T(time ? pb->tau : 1.0);
+  const T* rY = r + t * ps; const T* rU = r + F + t * ps; const T* rL = r + 2 * F + t * ps;
+  T* zY = z + t * ps; T* zU = z + F + t * ps; T* zL = z + 2 * F + t * ps;
+  T* T1 = w.chebA;                       // Lambda solve intermediates (compact level columns)
+  T* T2 = w.chebA + F;
+  auto mass_solve = [&](const T* b, T* x, int ncols, double scale) -> sgoc_status {
+    ChebArgs<T> c{};
+    c.B = b; c.X = x; c.tmpA = w.chebB; c.tmpB = w.chebB + F;
+    c.ncols = ncols; c.n1 = pb->n1; c.n = n; c.steps = pb->opt.cheb_steps;
+    c.mass = T(pb->mass_h2_36); c.scale_mode = 2; c.scale = T(scale);
+    c.P = ncols; c.slabs = 1; c.nt = 0;
+    SGOC_LAUNCH(launch_mass_blocks<T>(pb, c, st));
+    return SGOC_OK;
+  };
+  SGOC_TRY(mass_solve(rU, zU, pb->P, 1.0 / (pb->beta * sc)));
+  const int p = pb->p;
+  for (int step = 0; step < 2 * p + 1; ++step) {
+    const bool first = step <= p;
+    const int d = first ? step : 2 * p - step;
+    const int a0 = pb->off[d], L = pb->off[d + 1] - a0;
+    const T* bY = rY + int64_t(a0) * n;
+    const T* bL = rL + int64_t(a0) * n;
+    if (!(first && d == 0)) {
+      for (int fld = 0; fld < 2; ++fld) {
+        // fld 0: the Y right-hand side from Lambda; fld 1: the Lambda right-hand side from Y
+        SGArgs<T> g = first ? hgs_args_first<T>(pb, w, fld == 0 ? rY : rL, fld == 0 ? zL : zY, 1, d)
+                            : hgs_args<T>(pb, w, fld == 0 ? rY : rL, fld == 0 ? zL : zY, 1, d);
+        g.no_own = 1; g.c0 = T(0); g.cm = T(0); g.c1 = cK; g.cr = T(1); g.cy = T(0);
+        g.Y = fld == 0 ? w.W1 : w.W2; g.ycol0 = a0; g.ys = int64_t(L) * n;
+        SGOC_LAUNCH(launch_sg<T>(g, st));
+      }
+      bY = w.W1; bL = w.W2;
+    }
+    SGOC_TRY(mass_solve(bY, zY + int64_t(a0) * n, L, 1.0 / sc));
+    SGOC_TRY(vcycle<T>(pb, w, bL, T1, L, nullptr, 0, 1, 0, st));
+    MassArgs<T> m = mass_base<T>(pb, T2);
+    m.ncols = L; m.nslabs = 1; m.os = int64_t(L) * n;
+    mass_add(m, T1, 0, sc, 0, int64_t(L) * n);
+    SGOC_LAUNCH(launch_mass<T>(m, st));
+    SGOC_TRY(vcycle<T>(pb, w, T2, zL + int64_t(a0) * n, L, nullptr, 0, 1, 0, st));
+  }
+  return SGOC_OK;
+}
+
 // ------------------------------------------------------ block preconditioner --
 template <typename T>
 static sgoc_status precond_apply(const sgoc_problem* pb, PrecWS<T>& w, const T* r, T* z, cudaStream_t st,
                                  const Fork* f = nullptr,
                                  const std::function<sgoc_status(cudaStream_t)>& before_cheb = nullptr) {
   const int64_t F = pb->F, ps = int64_t(pb->P) * pb->n;
+  if (pb->opt.precond == 1) {                           // hGSoc (Alg. 2-3), slab by slab (Alg. 4)
+    for (int t = 0; t < pb->slabs; ++t) SGOC_TRY(hgsoc_slab<T>(pb, w, r, z, t, st));
+    return SGOC_OK;
+  }
   // blocks 1, 2: Chebyshev on M, scaled by 1/(sc_t H^gamma) and 1/(sc_t beta)
   ChebArgs<T> c{};
   c.B = r; c.X = z; c.tmpA = w.chebA; c.tmpB = w.chebB;

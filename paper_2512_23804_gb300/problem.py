@@ -31,7 +31,8 @@ class SGProblem:
 
     def __init__(self, nx, M, p, kappa, beta, yhat, gamma=0.0, nt=0, T=1.0, y0=None, *, tol=1e-8,
                  max_iter=1000, r=0, cheb_steps=5, nu=2, omega=0.8, precision="fp64", inner_tol=1e-3,
-                 max_outer=20, schur="diagonal", krylov="minres", restart=64, mass_solve="chebyshev"):
+                 max_outer=20, schur="diagonal", krylov="minres", restart=64, mass_solve="chebyshev",
+                 precond="block"):
         self._handle = None
         lib = abi.load()
         self._kappa = np.ascontiguousarray(kappa, dtype=np.float64)
@@ -49,6 +50,9 @@ class SGProblem:
         opts.krylov = {"minres": 0, "fgmres": 1}[krylov]
         opts.restart = restart
         opts.mass_solve = {"chebyshev": 0, "exact": 1}[mass_solve]
+        opts.precond = {"block": 0, "hgsoc": 1}[precond]
+        if precond == "hgsoc":
+            opts.krylov = 1                   # the hGSoc preconditioner is not symmetric
         h = ctypes.c_void_p()
         abi.check(lib.sgoc_problem_create(ctypes.byref(desc), ctypes.byref(opts), ctypes.byref(h)),
                   "sgoc_problem_create")
@@ -74,7 +78,7 @@ class SGProblem:
         args = dict(gamma=pr.gamma, nt=pr.nt, T=pr.T, y0=pr.y0, tol=pr.tol, max_iter=pr.max_iter,
                     r=0 if r is None or r < 0 else r, cheb_steps=pr.cheb_steps, nu=pr.nu_pre, omega=pr.omega,
                     schur=getattr(pr, "schur", "diagonal"), krylov=getattr(pr, "krylov", "minres"),
-                    mass_solve=getattr(pr, "mass_solve", "chebyshev"))
+                    mass_solve=getattr(pr, "mass_solve", "chebyshev"), precond=getattr(pr, "precond", "block"))
         args.update(kw)
         return cls(pr.nx, pr.M, pr.p, pr.kappa, pr.beta, pr.yhat, **args)
 
