@@ -88,3 +88,78 @@ def g_matrices_quadrature(M: int, p: int) -> list:
             Gk *= tab[e][np.ix_(idx[:, j], idx[:, j])]
         G.append(Gk)
     return G
+
+
+# ----------------------------------------------------------- Hermite chaos --
+# The paper's own setting (Sec. 2, Sec. 5): xi_j ~ N(0, 1) independent, normalised
+# probabilists' Hermite polynomials psi_n = He_n / sqrt(n!), the same graded index set for
+# the solution (total degree p) and a coefficient expansion of total degree 2p with
+# n_A = C(M + 2p, 2p) terms; H_l = E[psi_l Psi_alpha Psi_beta] (H_0 = I).
+
+def hermite_triple(a: int, b: int, c: int) -> float:
+    """E[psi_a psi_b psi_c] for normalised Hermite polynomials: the textbook closed form
+    sqrt(a! b! c!) / ((s-a)! (s-b)! (s-c)!) with s = (a+b+c)/2 when a+b+c is even and
+    s >= max(a, b, c), else 0."""
+    if (a + b + c) % 2:
+        return 0.0
+    s = (a + b + c) // 2
+    if s < max(a, b, c):
+        return 0.0
+    return math.sqrt(math.factorial(a) * math.factorial(b) * math.factorial(c)) / (
+        math.factorial(s - a) * math.factorial(s - b) * math.factorial(s - c))
+
+
+def term_indices(M: int, p: int) -> np.ndarray:
+    """Multi-indices of the coefficient expansion: total degree <= 2p, the graded order of
+    multi_indices (so terms 0, 1..M are the mean and the M linear terms)."""
+    return multi_indices(M, 2 * p)
+
+
+def h_matrices(M: int, p: int, nterms: int) -> list:
+    """Dense H_l (P x P) for the first nterms coefficient terms l (graded order)."""
+    idx = multi_indices(M, p)
+    tl = term_indices(M, p)[:nterms]
+    P = idx.shape[0]
+    H = []
+    for l in tl:
+        Hl = np.ones((P, P))
+        for j in range(M):
+            e = np.array([[hermite_triple(int(a), int(b), int(l[j])) for b in idx[:, j]] for a in idx[:, j]])
+            Hl *= e
+        H.append(Hl)
+    return H
+
+
+def hermite_normalised(n: int, x: np.ndarray) -> np.ndarray:
+    """psi_n(x) = He_n(x) / sqrt(n!) by the three-term recurrence He_{m+1} = x He_m - m He_{m-1}."""
+    h0 = np.ones_like(x)
+    if n == 0:
+        return h0
+    h1 = x.copy()
+    for m in range(1, n):
+        h0, h1 = h1, x * h1 - m * h0
+    return h1 / math.sqrt(math.factorial(n))
+
+
+def h_matrices_quadrature(M: int, p: int, nterms: int) -> list:
+    """H_l by tensor Gauss-Hermite quadrature (probabilists' weight), exact for the degree
+    3p... 4p products involved (pin for h_matrices)."""
+    idx = multi_indices(M, p)
+    tl = term_indices(M, p)[:nterms]
+    P = idx.shape[0]
+    x, w = np.polynomial.hermite_e.hermegauss(2 * p + 2)
+    w = w / math.sqrt(2 * math.pi)
+    deg = max(2 * p, 1)
+    tab = np.zeros((deg + 1, p + 1, p + 1))
+    for c in range(deg + 1):
+        for a in range(p + 1):
+            for b in range(p + 1):
+                tab[c, a, b] = np.sum(w * hermite_normalised(c, x) * hermite_normalised(a, x) *
+                                      hermite_normalised(b, x))
+    H = []
+    for l in tl:
+        Hl = np.ones((P, P))
+        for j in range(M):
+            Hl *= tab[int(l[j])][np.ix_(idx[:, j], idx[:, j])]
+        H.append(Hl)
+    return H

@@ -33,10 +33,17 @@ class SGData:
         self.pr = pr
         self.nx, self.M, self.p = pr.nx, pr.M, pr.p
         self.n = (pr.nx - 1) ** 2
-        self.G = basis.g_matrices(pr.M, pr.p)
+        self.chaos = getattr(pr, "chaos", "legendre")
+        self.K = fe.stiffness_terms(pr.nx, pr.kappa)       # one per coefficient term
+        self.nterms = len(self.K)
+        if self.chaos == "hermite":                       # lognormal coefficient, Hermite chaos
+            self.G = basis.h_matrices(pr.M, pr.p, self.nterms)
+        else:                                              # affine coefficient, Legendre chaos
+            self.G = basis.g_matrices(pr.M, pr.p)
         self.P = self.G[0].shape[0]
-        self.K = fe.stiffness_terms(pr.nx, pr.kappa)
-        self.Mass = fe.mass(pr.nx)
+        # the stiffness integrals are invariant under scaling of the domain, the mass scales
+        # with the element area (side length^2)
+        self.Mass = fe.mass(pr.nx) * getattr(pr, "length", 1.0) ** 2
         self.hgam = np.array([1.0] + [1.0 + pr.gamma] * (self.P - 1))
         self.beta, self.gamma = pr.beta, pr.gamma
         self.nt = pr.nt
@@ -54,7 +61,7 @@ class SGData:
 
     def sg_apply(self, X, terms=None):
         """sum_k K_k X G_k over the given k (default all)."""
-        ks = range(self.M + 1) if terms is None else terms
+        ks = range(self.nterms) if terms is None else terms
         Y = np.zeros_like(X)
         for k in ks:
             Y += self.K[k] @ X @ self.G[k]
@@ -95,7 +102,7 @@ class SGData:
 
     # ---- explicit assembly ---------------------------------------------------
     def sg_matrix(self):
-        return sum(sp.kron(self.Gs[k], self.K[k], format="csr") for k in range(self.M + 1))
+        return sum(sp.kron(self.Gs[k], self.K[k], format="csr") for k in range(self.nterms))
 
     def mass_cal(self):
         return sp.kron(sp.identity(self.P), self.Mass, format="csr")

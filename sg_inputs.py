@@ -63,6 +63,10 @@ class Problem:
     krylov: str = "minres"      # "minres" or "fgmres" (the paper's Sec. 5 solver)
     mass_solve: str = "chebyshev"   # mass blocks: "chebyshev" (cheb_steps) or "exact" (Cholesky)
     precond: str = "block"          # "block" (Eq. (stoch-prec) with hGS) or "hgsoc" (Alg. 2-3 / Alg. 4)
+    # chaos: "legendre" (xi ~ U[-1,1], affine coefficient, kappa has M+1 planes) or "hermite"
+    # (xi ~ N(0,1), lognormal coefficient, kappa has n_A = C(M+2p, 2p) planes in graded order)
+    chaos: str = "legendre"
+    length: float = 1.0         # side of the square domain (2 for the paper's [-1,1]^2)
     name: str = ""
 
     @property
@@ -204,6 +208,44 @@ def serving_request(i: int, master_seed: int = 5) -> Problem:
         pr.yhat = np.stack([math.sin(math.pi * (k + 1) * tau) * base for k in range(nt)])
         return pr
     return steady_problem(nx, M, p, 0.5, 0.3, beta, yhat_bumps(nx, bump_seed), name=f"req{i}")
+
+
+def graded_indices(M: int, q: int) -> np.ndarray:
+    """Multi-indices of total degree <= q, graded, lexicographically descending within a
+    degree (the layout convention of the coefficient planes, shape (count, M))."""
+    if M == 0:
+        return np.zeros((1, 0), dtype=np.int64)
+    import itertools
+    allidx = [a for a in itertools.product(range(q + 1), repeat=M) if sum(a) <= q]
+    allidx.sort(key=lambda a: (sum(a), tuple(-x for x in a)))
+    return np.array(allidx, dtype=np.int64).reshape(-1, M)
+
+
+def lognormal_terms(nx: int, M: int, p: int, L: float = 0.5, sigma: float = 1.0) -> np.ndarray:
+    """Element values of the chaos terms of the lognormal coefficient k = exp(f) (Sec. 2),
+    shape (n_A, nx, nx), n_A = C(M+2p, 2p): the Gaussian field f = f_0 + sum_j f_j xi_j has the
+    KL modes f_j = sigma sqrt(lambda_j) phi_j of kl_terms and f_0 = -1/2 sum_j f_j^2, so that the
+    mean term is kappa_0 = 1 (the paper's setting); in normalised Hermite chaos the terms are
+    kappa_l = exp(f_0 + 1/2 sum_j f_j^2) prod_j f_j^{l_j} / sqrt(l_j!) = prod_j f_j^{l_j} / sqrt(l_j!)."""
+    f = kl_terms(nx, M, L, sigma)[1:]
+    tl = graded_indices(M, 2 * p)
+    out = np.ones((tl.shape[0], nx, nx))
+    for i, l in enumerate(tl):
+        for j in range(M):
+            if l[j]:
+                out[i] *= f[j] ** int(l[j]) / math.sqrt(math.factorial(int(l[j])))
+    return out
+
+
+def paper_problem(nx: int, M: int, p: int, beta: float = 1e-4, gamma: float = 1.0, **opts) -> Problem:
+    """The paper's steady setting (Sec. 5): D = [-1,1]^2 (length 2, nx elements per side, so
+    h = 2/nx), lognormal coefficient with the exponential covariance of correlation length 1
+    and unit variance (0.5 and 1 on the unit square the grid is indexed on), Hermite chaos,
+    gamma = 1, and the discontinuous target y_d = 1 on [-1,0]^2, 0 elsewhere."""
+    x1, x2 = interior_coords(nx)
+    yd = ((x1 <= 0.5 + 1e-12) & (x2 <= 0.5 + 1e-12)).astype(np.float64)
+    return Problem(nx=nx, M=M, p=p, kappa=lognormal_terms(nx, M, p), beta=beta, gamma=gamma, nt=0,
+                   yhat=yd[None, :], chaos="hermite", length=2.0, name=f"paper_{nx}x{nx}_M{M}_p{p}", **opts)
 
 
 def random_small(seed, nx=8, M=2, p=2, nt=0, beta=1e-2, sigma=0.3, L=0.5, gamma=0.0, **opts) -> Problem:
