@@ -78,14 +78,23 @@ typedef struct {
   const double* yhat;    /* max(nt,1)*n target values at interior nodes; in time mode
                             slab t holds yhat(., t_{t+1}), t_k = k tau */
   const double* y0;      /* n initial-state values (time mode) or NULL for y(0) = 0 */
+  int32_t chaos;         /* 0: orthonormal Legendre chaos, xi_k ~ U[-1,1], affine coefficient with
+                            n_terms = M + 1 planes in kappa (kappa_k multiplies xi_k);
+                            1: normalised Hermite chaos, xi_k ~ N(0,1), a coefficient expanded in
+                            the chaos itself (the paper's lognormal setting, Sec. 2): n_terms =
+                            C(M + 2p, 2p) planes, plane l multiplying psi_l for the multi-indices of
+                            total degree <= 2p in the graded order of sgoc_pc_indices */
+  double length;         /* side of the square domain (0 selects 1: the unit square; 2 for the
+                            paper's [-1,1]^2): the mass matrix scales with length^2 */
 } sgoc_problem_desc;
 
 /* Solver options; sgoc_default_options fills the defaults given here. */
 typedef struct {
   double tol;            /* relative residual target ||b - K x||_2 / ||b||_2 (1e-8) */
   int32_t max_iter;      /* MINRES iteration cap (FP64) / inner cap (mixed) (1000) */
-  int32_t r;             /* truncation: hGS couplings use kappa_1..kappa_{r-1}; 1..M+1;
-                            0 selects M+1 (Sec. 2, index set I_tau; Sec. 5, r = m+1) */
+  int32_t r;             /* truncation: hGS couplings use the coefficient terms 1..r-1; 1..n_terms;
+                            0 selects M+1 (Sec. 2, index set I_tau; Sec. 5, r = m+1: the mean and
+                            the M linear terms) */
   int32_t cheb_steps;    /* Chebyshev steps for the mass blocks (5) */
   int32_t nu_pre;        /* V-cycle pre-smoothing sweeps (2) */
   int32_t nu_post;       /* V-cycle post-smoothing sweeps (2) */

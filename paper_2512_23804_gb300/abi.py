@@ -29,7 +29,8 @@ class ProblemDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("M", ctypes.c_int32), ("p", ctypes.c_int32),
                 ("kappa", ctypes.POINTER(ctypes.c_double)), ("beta", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("nt", ctypes.c_int32), ("T", ctypes.c_double),
-                ("yhat", ctypes.POINTER(ctypes.c_double)), ("y0", ctypes.POINTER(ctypes.c_double))]
+                ("yhat", ctypes.POINTER(ctypes.c_double)), ("y0", ctypes.POINTER(ctypes.c_double)),
+                ("chaos", ctypes.c_int32), ("length", ctypes.c_double)]
 
 
 class Options(ctypes.Structure):

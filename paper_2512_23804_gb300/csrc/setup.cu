@@ -44,6 +44,16 @@ static double legendre_coupling(int n) {
   return (n + 1) / std::sqrt((2.0 * n + 1.0) * (2.0 * n + 3.0));
 }
 
+// E[psi_a psi_b psi_c] for normalised Hermite polynomials psi_n = He_n / sqrt(n!), xi ~ N(0,1):
+// sqrt(a! b! c!) / ((s-a)! (s-b)! (s-c)!) for even a+b+c = 2s with s >= max(a, b, c), else 0.
+static double hermite_triple(int a, int b, int c) {
+  if ((a + b + c) % 2) return 0.0;
+  const int s = (a + b + c) / 2;
+  if (s < std::max(a, std::max(b, c))) return 0.0;
+  auto fact = [](int n) { double f = 1.0; for (int i = 2; i <= n; ++i) f *= i; return f; };
+  return std::sqrt(fact(a) * fact(b) * fact(c)) / (fact(s - a) * fact(s - b) * fact(s - c));
+}
+
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace sgoc
@@ -166,12 +176,18 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
   if (d->nt < 0 || d->nt > 100000 || (d->nt > 0 && !(d->T > 0.0))) { set_error("nt >= 0, T > 0"); return SGOC_ERR_INVALID_ARG; }
   if (!d->kappa || !d->yhat) { set_error("kappa and yhat are required"); return SGOC_ERR_INVALID_ARG; }
   const double Pd = binom(d->M + d->p, d->p);
+  if (d->chaos != 0 && d->chaos != 1) { set_error("chaos must be 0 (Legendre) or 1 (Hermite)"); return SGOC_ERR_INVALID_ARG; }
+  const double length = d->length == 0.0 ? 1.0 : d->length;
+  if (!(length > 0) || !std::isfinite(length)) { set_error("domain length must be positive"); return SGOC_ERR_INVALID_ARG; }
+  const double nterms_d = d->chaos == 1 ? binom(d->M + 2 * d->p, 2 * d->p) : double(d->M + 1);
+  if (nterms_d > 20000) { set_error("too many coefficient terms"); return SGOC_ERR_INVALID_ARG; }
+  const int nterms = int(nterms_d + 0.5);
   if (Pd > 20000) { set_error("chaos basis too large (P > 20000)"); return SGOC_ERR_UNSUPPORTED; }
   sgoc_options o;
   sgoc_default_options(&o);
   if (opt) o = *opt;
   if (o.r == 0) o.r = d->M + 1;
-  if (o.r < 1 || o.r > d->M + 1) { set_error("truncation r must be in [1, M+1]"); return SGOC_ERR_INVALID_ARG; }
+  if (o.r < 1 || o.r > nterms) { set_error("truncation r must be in [1, n_terms]"); return SGOC_ERR_INVALID_ARG; }
   if (!(o.tol > 0) || o.max_iter < 1 || o.cheb_steps < 1 || o.cheb_steps > 64 || o.nu_pre < 0 || o.nu_post < 0 ||
       o.nu_pre > 16 || o.nu_post > 16 || o.nu_pre != o.nu_post || !(o.omega > 0 && o.omega < 2) ||
       (o.precision != SGOC_FP64 && o.precision != SGOC_MIXED_FP32) || !(o.inner_tol > 0 && o.inner_tol < 1) ||
@@ -184,6 +200,7 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
 
   auto* pb = new sgoc_problem();
   pb->nx = nx; pb->M = d->M; pb->p = d->p; pb->nt = d->nt;
+  pb->chaos = d->chaos; pb->nterms = nterms; pb->length = length;
   pb->beta = d->beta; pb->gamma = d->gamma; pb->T = d->T;
   pb->tau = d->nt > 0 ? d->T / d->nt : 1.0;
   pb->n1 = nx - 1;
@@ -197,7 +214,7 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
   pb->s = std::sqrt((1.0 + d->gamma) / d->beta);
 
   const int64_t nel = int64_t(nx) * nx;
-  pb->kappa.assign(d->kappa, d->kappa + (d->M + 1) * nel);
+  pb->kappa.assign(d->kappa, d->kappa + int64_t(nterms) * nel);
   for (double v : pb->kappa)
     if (!std::isfinite(v)) { delete pb; set_error("non-finite kappa"); return SGOC_ERR_NAN; }
   pb->kappa0 = pb->kappa[0];
@@ -234,7 +251,25 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
   for (int a = 0; a < pb->P && M > 0; ++a)
     pos[std::vector<int32_t>(pb->idx.begin() + int64_t(a) * M, pb->idx.begin() + int64_t(a + 1) * M)] = a;
   pb->nbr_ptr.assign(pb->P + 1, 0);
-  for (int b = 0; b < pb->P; ++b) {
+  if (d->chaos == 1 && M > 0) {
+    // Hermite: beta couples to alpha through term l >= 1 with c = E[psi_l Psi_alpha Psi_beta]
+    // = prod_j e(alpha_j, beta_j, l_j) (the closed form of hermite_triple), entries by l, then alpha
+    std::vector<int32_t> cur(M, 0);
+    for (int deg = 0; deg <= 2 * p; ++deg) gen_degree(M, 0, deg, cur, pb->tidx);
+    if (int64_t(pb->tidx.size()) != int64_t(nterms) * M) { delete pb; set_error("internal: term count"); return SGOC_ERR_INVALID_ARG; }
+    for (int b = 0; b < pb->P; ++b) {
+      for (int l = 1; l < nterms; ++l) {
+        for (int a = 0; a < pb->P; ++a) {
+          double c = 1.0;
+          for (int j = 0; j < M && c != 0.0; ++j)
+            c *= hermite_triple(pb->idx[int64_t(a) * M + j], pb->idx[int64_t(b) * M + j], pb->tidx[int64_t(l) * M + j]);
+          if (c != 0.0) { pb->nbr_alpha.push_back(a); pb->nbr_k.push_back(l); pb->nbr_c.push_back(c); }
+        }
+      }
+      pb->nbr_ptr[b + 1] = int(pb->nbr_alpha.size());
+    }
+  }
+  for (int b = 0; b < pb->P && d->chaos == 0; ++b) {
     for (int k = 0; k < M; ++k) {
       std::vector<int32_t> v(pb->idx.begin() + int64_t(b) * M, pb->idx.begin() + int64_t(b + 1) * M);
       const int bk = v[k];
@@ -281,6 +316,12 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
     while (e < pb->dn_ptr[b + 1] && pb->dn_k[e] < pb->r) ++e;
     pb->dn_end_r[b] = e;
   }
+  // input levels an hGS visit reads: the largest level distance of a kept coupling (1 for
+  // Legendre: G_k couples neighbouring levels only)
+  pb->lev_dist = 1;
+  for (int b = 0; b < pb->P; ++b)
+    for (int e = pb->nbr_ptr[b]; e < pb->nbr_end_r[b]; ++e)
+      pb->lev_dist = std::max(pb->lev_dist, std::abs(level_of[pb->nbr_alpha[e]] - level_of[b]));
 
   // multigrid hierarchy of the mean operator:
   // steady  A~_1 = kappa0 K + s M            (Eq. (mathcalZ))
@@ -292,29 +333,32 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
   for (int g = nx; g >= 2; g /= 2) {
     Level L;
     L.nx = g; L.n1 = g - 1; L.n = int64_t(L.n1) * L.n1;
-    const double h = 1.0 / g, m = h * h / 36.0;
+    const double h = length / g, m = h * h / 36.0;
     L.diag = ck * (8.0 / 3.0) + cm * 16.0 * m;
     L.edge = -ck / 3.0 + cm * 4.0 * m;
     L.corner = -ck / 3.0 + cm * m;
     pb->levels.push_back(L);
   }
-  pb->mass_h2_36 = 1.0 / (36.0 * nx * double(nx));
+  pb->mass_h2_36 = length * length / (36.0 * nx * double(nx));
   pb->dweights.assign(pb->slabs, 1.0);
   if (d->nt > 1) { pb->dweights[0] = 0.5; pb->dweights[d->nt - 1] = 0.5; }
 
   // slot tables of the SG launch shapes: the full operator and the hGS visit of each level
   const NbrView full{pb->nbr_ptr, pb->nbr_alpha, pb->nbr_k, pb->nbr_c};
   const NbrView down{pb->dn_ptr, pb->dn_alpha, pb->dn_k, pb->dn_c};
-  pb->utabs.push_back(build_utab(full, 0, pb->P, 0, pb->P, M + 1, true));
+  // (the two-phase kernel keeps one mask bit per coefficient term: at most 17 terms)
+  const int D = pb->lev_dist;
+  auto lo = [&](int d) { return pb->off[std::max(0, d - D)]; };
+  auto hi = [&](int d) { return pb->off[std::min(p + 1, d + D + 1)]; };
+  const bool slots = nterms <= 17;
+  pb->utabs.push_back(slots ? build_utab(full, 0, pb->P, 0, pb->P, nterms, true) : UTab());
   for (int d = 0; d <= p; ++d)
-    pb->utabs.push_back(build_utab(full, pb->off[d > 0 ? d - 1 : 0], pb->off[d + 2 <= p + 1 ? d + 2 : p + 1],
-                                   pb->off[d], pb->off[d + 1], pb->r, true));
+    pb->utabs.push_back(slots ? build_utab(full, lo(d), hi(d), pb->off[d], pb->off[d + 1], pb->r, true) : UTab());
   for (int d = 0; d <= p; ++d)
-    pb->utabs.push_back(build_utab(down, pb->off[d > 0 ? d - 1 : 0], pb->off[d], pb->off[d], pb->off[d + 1],
-                                   pb->r, false));
+    pb->utabs.push_back(slots ? build_utab(down, lo(d), pb->off[d], pb->off[d], pb->off[d + 1], pb->r, false) : UTab());
 
   // persistent layout
-  const size_t nk = size_t(M + 1) * nel;
+  const size_t nk = size_t(nterms) * nel;
   const size_t nnz = pb->nbr_alpha.size();
   size_t off = 0;
   off = align256(off + nk * 8); off = align256(off + nk * 4);
@@ -361,8 +405,7 @@ sgoc_status sgoc_problem_upload(sgoc_problem* pb, void* d_persistent, size_t byt
   if (reinterpret_cast<uintptr_t>(d_persistent) % 256) { set_error("persistent buffer must be 256-byte aligned"); return SGOC_ERR_INVALID_ARG; }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   invalidate_graphs(pb);
-  const int M = pb->M;
-  const size_t nel = size_t(pb->nx) * pb->nx, nk = size_t(M + 1) * nel;
+  const size_t nel = size_t(pb->nx) * pb->nx, nk = size_t(pb->nterms) * nel;
   const size_t nnz = pb->nbr_alpha.size();
   char* base = static_cast<char*>(d_persistent);
   size_t off = 0;
@@ -413,7 +456,7 @@ sgoc_status sgoc_problem_upload(sgoc_problem* pb, void* d_persistent, size_t byt
   std::vector<double> l(pb->n1, 0.0), id(pb->n1);
   std::vector<float> l32, id32;
   {
-    const double a = 1.0 / (6.0 * pb->nx);
+    const double a = pb->length / (6.0 * pb->nx);
     double D = 4.0 * a;
     id[0] = 1.0 / D;
     for (int i = 1; i < pb->n1; ++i) {

@@ -86,6 +86,10 @@ struct DevData {
 struct sgoc_problem {
   // problem statement
   int nx = 0, M = 0, p = 0, nt = 0;
+  int chaos = 0;                     // 0 Legendre / affine, 1 Hermite / chaos-expanded coefficient
+  int nterms = 1;                    // coefficient planes: M + 1, or C(M + 2p, 2p)
+  int lev_dist = 1;                  // largest chaos-level distance of a kept coupling
+  double length = 1.0;               // side of the square domain
   double beta = 0, gamma = 0, T = 1, tau = 1, kappa0 = 1, s = 0;  // s = sqrt((1+gamma)/beta)
   int n1 = 0, P = 0, slabs = 1;
   int64_t n = 0, F = 0, N = 0;       // F = slabs * P * n, N = 3F
@@ -94,6 +98,7 @@ struct sgoc_problem {
   int r = 1;                         // truncation
   // chaos basis
   std::vector<int32_t> idx;          // P x M
+  std::vector<int32_t> tidx;         // n_terms x M coefficient-term multi-indices (Hermite)
   std::vector<int> off;              // p + 2 level offsets
   std::vector<int> nbr_ptr, nbr_alpha, nbr_k, nbr_end_r;
   std::vector<double> nbr_c;

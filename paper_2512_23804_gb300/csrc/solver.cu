@@ -243,16 +243,17 @@ static SGArgs<T> hgs_args(const sgoc_problem* pb, PrecWS<T>& w, const T* R, T* V
   g.X = V; g.xs = ps;
   g.Y = w.RH; g.ys = int64_t(L) * n; g.ycol0 = a0;
   g.R = R; g.rs = ps; g.rcol0 = 0;
-  g.n1 = pb->n1; g.n = n; g.nx = pb->nx; g.M = pb->M;
+  g.n1 = pb->n1; g.n = n; g.nx = pb->nx; g.M = pb->nterms - 1;
   g.out0 = a0; g.out1 = a1;
-  g.in0 = pb->off[d > 0 ? d - 1 : 0];
-  g.in1 = pb->off[d + 2 <= p + 1 ? d + 2 : p + 1];
+  // the levels coupled to level d by a kept term: within lev_dist of d (1 for Legendre)
+  g.in0 = pb->off[std::max(0, d - pb->lev_dist)];
+  g.in1 = pb->off[std::min(p + 1, d + pb->lev_dist + 1)];
   g.kmax = pb->r; g.nslabs = slabs;
   g.c0 = -cK; g.c1 = -cK; g.cm = -cM; g.cr = T(1); g.cy = T(0);
   g.mass = T(pb->mass_h2_36);
   g.kap = kap_of<T>(pb);
   g.nbr_ptr = pb->dev.nbr_ptr; g.nbr_alpha = pb->dev.nbr_alpha; g.nbr_k = pb->dev.nbr_k; g.nbr_c = nbrc_of<T>(pb);
-  g.nbr_end = pb->r == pb->M + 1 ? pb->dev.nbr_end_all : pb->dev.nbr_end_r;
+  g.nbr_end = pb->r == pb->nterms ? pb->dev.nbr_end_all : pb->dev.nbr_end_r;
   g.deg_sum = deg_sum(pb, a0, a1, pb->r);
   g.nnz_out = pb->nbr_ptr[a1] - pb->nbr_ptr[a0];
   set_utab(g, pb->utabs[1 + d]);
@@ -266,14 +267,14 @@ template <typename T>
 static SGArgs<T> hgs_args_first(const sgoc_problem* pb, PrecWS<T>& w, const T* R, T* V, int slabs, int d) {
   SGArgs<T> g = hgs_args<T>(pb, w, R, V, slabs, d);
   const int a0 = pb->off[d], a1 = pb->off[d + 1];
-  g.in0 = pb->off[d > 0 ? d - 1 : 0];
+  g.in0 = pb->off[std::max(0, d - pb->lev_dist)];
   g.in1 = a0;
   g.no_own = 1;
   g.c0 = T(0); g.cm = T(0);
   g.nbr_ptr = pb->dev.dn_ptr; g.nbr_alpha = pb->dev.dn_alpha; g.nbr_k = pb->dev.dn_k;
   g.nbr_c = std::is_same<T, double>::value ? reinterpret_cast<const T*>(pb->dev.dn_c64)
                                            : reinterpret_cast<const T*>(pb->dev.dn_c32);
-  g.nbr_end = pb->r == pb->M + 1 ? pb->dev.dn_ptr + 1 : pb->dev.dn_end_r;
+  g.nbr_end = pb->r == pb->nterms ? pb->dev.dn_ptr + 1 : pb->dev.dn_end_r;
   g.nnz_out = pb->dn_ptr[a1] - pb->dn_ptr[a0];
   double deg = 0;
   for (int b = a0; b < a1; ++b)
@@ -348,6 +349,7 @@ static FusedLevels fused_levels_of(const sgoc_problem* pb, int lf) {
 
 static bool same_shape(const sgoc_problem* a, const sgoc_problem* b) {
   return a->nx == b->nx && a->M == b->M && a->p == b->p && a->slabs == b->slabs && a->r == b->r &&
+         a->chaos == b->chaos && a->nterms == b->nterms &&
          a->opt.precision == b->opt.precision && a->opt.nu_pre == b->opt.nu_pre &&
          a->opt.nu_post == b->opt.nu_post && a->opt.omega == b->opt.omega &&
          a->opt.cheb_steps == b->opt.cheb_steps && (a->nt > 0) == (b->nt > 0);
@@ -433,9 +435,9 @@ static SGArgs<T> sg_full(const sgoc_problem* pb, const T* X, T* Y, T coef) {
   const int64_t ps = int64_t(pb->P) * pb->n;
   g.X = X; g.xs = ps; g.Y = Y; g.ys = ps; g.ycol0 = 0;
   g.R = nullptr; g.rs = 0; g.rcol0 = 0;
-  g.n1 = pb->n1; g.n = pb->n; g.nx = pb->nx; g.M = pb->M;
+  g.n1 = pb->n1; g.n = pb->n; g.nx = pb->nx; g.M = pb->nterms - 1;
   g.out0 = 0; g.out1 = pb->P; g.in0 = 0; g.in1 = pb->P;
-  g.kmax = pb->M + 1; g.nslabs = pb->slabs;
+  g.kmax = pb->nterms; g.nslabs = pb->slabs;
   g.c0 = coef; g.c1 = coef; g.cm = T(0); g.cr = T(0); g.cy = T(1);
   g.mass = T(pb->mass_h2_36);
   g.kap = kap_of<T>(pb);

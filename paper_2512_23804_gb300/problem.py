@@ -29,7 +29,8 @@ class SGProblem:
     nodes, y0 (n,) or None.
     """
 
-    def __init__(self, nx, M, p, kappa, beta, yhat, gamma=0.0, nt=0, T=1.0, y0=None, *, tol=1e-8,
+    def __init__(self, nx, M, p, kappa, beta, yhat, gamma=0.0, nt=0, T=1.0, y0=None, *, chaos="legendre",
+                 length=1.0, tol=1e-8,
                  max_iter=1000, r=0, cheb_steps=5, nu=2, omega=0.8, precision="fp64", inner_tol=1e-3,
                  max_outer=20, schur="diagonal", krylov="minres", restart=64, mass_solve="chebyshev",
                  precond="block"):
@@ -39,7 +40,8 @@ class SGProblem:
         self._yhat = np.ascontiguousarray(yhat, dtype=np.float64)
         self._y0 = None if y0 is None else np.ascontiguousarray(y0, dtype=np.float64)
         dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
-        desc = abi.ProblemDesc(nx, M, p, dp(self._kappa), beta, gamma, nt, T, dp(self._yhat), dp(self._y0))
+        desc = abi.ProblemDesc(nx, M, p, dp(self._kappa), beta, gamma, nt, T, dp(self._yhat), dp(self._y0),
+                               {"legendre": 0, "hermite": 1}[chaos], length)
         opts = abi.Options()
         lib.sgoc_default_options(ctypes.byref(opts))
         opts.tol, opts.max_iter, opts.r, opts.cheb_steps = tol, max_iter, r, cheb_steps
@@ -78,7 +80,8 @@ class SGProblem:
         args = dict(gamma=pr.gamma, nt=pr.nt, T=pr.T, y0=pr.y0, tol=pr.tol, max_iter=pr.max_iter,
                     r=0 if r is None or r < 0 else r, cheb_steps=pr.cheb_steps, nu=pr.nu_pre, omega=pr.omega,
                     schur=getattr(pr, "schur", "diagonal"), krylov=getattr(pr, "krylov", "minres"),
-                    mass_solve=getattr(pr, "mass_solve", "chebyshev"), precond=getattr(pr, "precond", "block"))
+                    mass_solve=getattr(pr, "mass_solve", "chebyshev"), precond=getattr(pr, "precond", "block"),
+                    chaos=getattr(pr, "chaos", "legendre"), length=getattr(pr, "length", 1.0))
         args.update(kw)
         return cls(pr.nx, pr.M, pr.p, pr.kappa, pr.beta, pr.yhat, **args)
 

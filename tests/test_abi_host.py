@@ -112,3 +112,23 @@ def test_device_calls_require_upload():
     st = lib.sgoc_apply_kkt(sp._handle, 0, ctypes.c_void_p(1), ctypes.c_void_p(1), None)
     assert abi.STATUS_NAMES[st] == "SGOC_ERR_NOT_UPLOADED"
     assert "upload" in lib.sgoc_last_error().decode()
+
+
+def test_hermite_triple_products_match_oracle():
+    """The library's Hermite coupling table (the paper's lognormal setting) equals the oracle's
+    H_l for every term l >= 1, and the multi-indices are the oracle's."""
+    import sg_inputs as si
+    from oracle import basis
+    from paper_2512_23804_gb300 import SGProblem
+    for M, p in [(2, 2), (3, 2), (2, 3)]:
+        pr = si.paper_problem(8, M, p)
+        sp = SGProblem.from_problem(pr)
+        assert np.array_equal(sp.pc_indices(), basis.multi_indices(M, p))
+        k, a, b, c = sp.triple_products()
+        nA = basis.term_indices(M, p).shape[0]
+        H = basis.h_matrices(M, p, nA)
+        dense = [np.zeros_like(H[0]) for _ in range(nA)]
+        for kk, aa, bb, cc in zip(k, a, b, c):
+            dense[kk][aa, bb] = cc
+        for l in range(1, nA):
+            assert np.max(np.abs(dense[l] - H[l])) <= 1e-15 * max(1.0, np.max(np.abs(H[l]))), l

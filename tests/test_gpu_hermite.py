@@ -1,0 +1,91 @@
+"""The paper's own setting on the GPU (Hermite chaos, lognormal coefficient with
+n_A = C(M+2p, 2p) terms, [-1,1]^2, gamma = 1, discontinuous target) against the oracle.
+Tolerances as in the Legendre parity tests: float64 operator 1e-13, float64 preconditioner
+1e-12, float32 operator 2e-6, solves within 1e-7 and +-1 iteration."""
+import numpy as np
+import pytest
+
+import sg_inputs as si
+from oracle import basis
+from oracle.operators import SGData
+from oracle.precond import BlockPreconditioner
+from oracle.solve import solve as oracle_solve
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_ready():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests selected but no CUDA device is visible")
+    from paper_2512_23804_gb300 import build
+    build.build()
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+def make(nx, M, p, r=None, precision="fp64", **kw):
+    from paper_2512_23804_gb300 import SGProblem
+    pr = si.paper_problem(nx, M, p, **kw)
+    if r is not None:
+        pr.r = r
+    return pr, SGData(pr), SGProblem.from_problem(pr, precision=precision)
+
+
+SHAPES = [(16, 2, 2), (8, 3, 2), (32, 2, 3)]
+
+
+@pytest.mark.parametrize("nx,M,p", SHAPES)
+def test_hermite_operator_and_kkt(nx, M, p):
+    pr, d, sp = make(nx, M, p)
+    assert d.nterms == basis.term_indices(M, p).shape[0]
+    X = si.random_panel(5, d.n, d.P)
+    Y = sp.apply_operator(torch.from_numpy(X).cuda())
+    torch.cuda.synchronize()
+    assert rel(Y.cpu().numpy(), d.vec(d.sg_apply(d.mat(X)))) <= 1e-13
+    Xf = X.astype(np.float32).astype(np.float64)
+    Yf = sp.apply_operator(torch.from_numpy(Xf).to("cuda", torch.float32))
+    torch.cuda.synchronize()
+    assert rel(Yf.double().cpu().numpy(), d.vec(d.sg_apply(d.mat(Xf)))) <= 2e-6
+    v = si.random_panel(6, 3 * d.n, d.P)
+    w = sp.apply_kkt(torch.from_numpy(v).cuda())
+    torch.cuda.synchronize()
+    assert rel(w.cpu().numpy(), d.kkt_apply(v)) <= 1e-13
+
+
+@pytest.mark.parametrize("r", [1, None, -2])
+def test_hermite_hgs_and_preconditioner(r):
+    nx, M, p = 16, 2, 2
+    nA = basis.term_indices(M, p).shape[0]
+    rr = nA if r == -2 else r                       # -2: all n_A terms (within-level couplings)
+    pr, d, sp = make(nx, M, p, r=rr)
+    Pc = BlockPreconditioner(d)
+    R = si.random_panel(7, d.n, d.P)
+    V = sp.apply_hgs(torch.from_numpy(R).cuda())
+    torch.cuda.synchronize()
+    assert rel(V.cpu().numpy(), d.vec(Pc.hgs.apply(d.mat(R)))) <= 1e-12
+    rv = si.random_panel(8, 3 * d.n, d.P)
+    z = sp.apply_precond(torch.from_numpy(rv).cuda())
+    torch.cuda.synchronize()
+    assert rel(z.cpu().numpy(), Pc.apply(rv)) <= 1e-12
+
+
+@pytest.mark.parametrize("krylov,r", [("minres", None), ("fgmres", None), ("fgmres", 1), ("minres", -2)])
+def test_hermite_solves_match_oracle(krylov, r):
+    nx, M, p = 16, 2, 2
+    nA = basis.term_indices(M, p).shape[0]
+    pr, d, sp0 = make(nx, M, p, r=nA if r == -2 else r)
+    pr.krylov = krylov
+    from paper_2512_23804_gb300 import SGProblem
+    sp = SGProblem.from_problem(pr)
+    ref = oracle_solve(pr, data=d)
+    assert ref.status == "ok"
+    x, info = sp.solve()
+    assert info["status_name"] == "SGOC_OK" and info["rel_true_residual"] <= pr.tol
+    assert abs(info["iterations"] - ref.iterations) <= 1, (info["iterations"], ref.iterations)
+    assert rel(x.cpu().numpy(), ref.x) <= 1e-7
+    xm, im = SGProblem.from_problem(pr, precision="mixed").solve()
+    assert im["status_name"] == "SGOC_OK" and im["rel_true_residual"] <= pr.tol
