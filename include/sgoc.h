@@ -114,8 +114,9 @@ typedef struct {
                             reorthogonalisation, float64 Hessenberg and Givens scalars, restarted
                             every `restart` iterations.  In mixed precision the inner solves use
                             the same method in float32 vectors (one cycle each). */
-  int32_t restart;       /* FGMRES cycle length, 1..128 (64); memory grows with it: 2*restart + 1
-                            KKT vectors of the solve precision */
+  int32_t restart;       /* FGMRES cycle length, 1..512 (64); memory grows with it: 2*restart + 1
+                            KKT vectors of the solve precision (the paper's FGMRES is unrestarted:
+                            a cycle longer than the iterations needed) */
   int32_t mass_solve;    /* mass blocks 1 and 2 of the preconditioner (Sec. 5): 0 Chebyshev
                             semi-iteration with cheb_steps steps (0); 1 exact solve with the
                             (square-root-free) Cholesky factorisation of M = M1 (x) M1 */

@@ -34,7 +34,7 @@ def solve(pr, mode="vcycle", assembled=False, data=None, schur=None, krylov=None
     else:
         Pc = BlockPreconditioner(d, mode, schur=schur)
     if krylov == "fgmres":
-        res = fgmres(apply_A, Pc.apply, b, tol=pr.tol, max_iter=pr.max_iter)
+        res = fgmres(apply_A, Pc.apply, b, tol=pr.tol, max_iter=pr.max_iter, restart=getattr(pr, "restart", None))
     else:
         res = minres(apply_A, Pc.apply, b, tol=pr.tol, max_iter=pr.max_iter)
     res.data = d

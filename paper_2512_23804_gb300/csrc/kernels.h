@@ -215,7 +215,7 @@ cudaError_t launch_minres_wx(const T* z, const T* wm1, T* wm2, TX* x, int64_t n,
 // its Givens rotations (column-major, leading dimension kFgmresMax + 1), the rotations,
 // the rotated right-hand side g, the Gram-Schmidt coefficients of the current column
 // and the least-squares solution y.
-constexpr int kFgmresMax = 128;
+constexpr int kFgmresMax = 512;
 struct FgmresState {
   double beta;                         // ||r|| at the start of the cycle
   double target, est;                  // stopping target and estimate |g_{j+1}| / ||b||

@@ -192,7 +192,7 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
       o.nu_pre > 16 || o.nu_post > 16 || o.nu_pre != o.nu_post || !(o.omega > 0 && o.omega < 2) ||
       (o.precision != SGOC_FP64 && o.precision != SGOC_MIXED_FP32) || !(o.inner_tol > 0 && o.inner_tol < 1) ||
       o.max_outer < 1 || (o.schur != 0 && o.schur != 1) || (o.krylov != 0 && o.krylov != 1) ||
-      o.restart < 1 || o.restart > 128 || (o.mass_solve != 0 && o.mass_solve != 1) ||
+      o.restart < 1 || o.restart > kFgmresMax || (o.mass_solve != 0 && o.mass_solve != 1) ||
       (o.precond != 0 && o.precond != 1) || (o.precond == 1 && o.krylov != 1)) {
     set_error("invalid options (nu_pre must equal nu_post for a symmetric V-cycle)");
     return SGOC_ERR_INVALID_ARG;
@@ -501,6 +501,7 @@ sgoc_status sgoc_problem_upload(sgoc_problem* pb, void* d_persistent, size_t byt
   }
   for (size_t i = 0; i < pb->utabs.size(); ++i) {
     const UTab& u = pb->utabs[i];
+    if (u.eptr.empty()) continue;                 // no slot table (more than 17 coefficient terms)
     const size_t nin = u.in1 - u.in0, nout = u.out1 - u.out0;
     SGOC_CUDA_TRY(cudaMemcpyAsync(u.d_mb, u.mb.data(), nin * 8, cudaMemcpyHostToDevice, st));
     SGOC_CUDA_TRY(cudaMemcpyAsync(u.d_diag, u.diag.data(), nout * 4, cudaMemcpyHostToDevice, st));

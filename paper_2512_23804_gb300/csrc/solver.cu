@@ -1220,7 +1220,7 @@ struct SolveTask {
   // a cycle from rhs (the residual of the current iterate): v_0 = rhs / ||rhs||
   template <typename T>
   sgoc_status fg_start(const T* rhs, double tgt, double bn) {
-    if (!rt->hfg) SGOC_CUDA_TRY(cudaMallocHost(&rt->hfg, sizeof(FgmresState)));
+    if (!rt->hfg) SGOC_CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&rt->hfg), offsetof(FgmresState, h)));
     SGOC_LAUNCH(launch_dot_partial<T>(rhs, rhs, pb->N, L.k64.partial, st));
     SGOC_LAUNCH(launch_fgmres_start(L.fg.st, L.k64.partial, tgt, bn, st));
     SGOC_LAUNCH(launch_fgmres_scale<T>(rhs, static_cast<T*>(L.fg.V), pb->N, L.fg.st, 0, st));

@@ -81,7 +81,8 @@ class SGProblem:
                     r=0 if r is None or r < 0 else r, cheb_steps=pr.cheb_steps, nu=pr.nu_pre, omega=pr.omega,
                     schur=getattr(pr, "schur", "diagonal"), krylov=getattr(pr, "krylov", "minres"),
                     mass_solve=getattr(pr, "mass_solve", "chebyshev"), precond=getattr(pr, "precond", "block"),
-                    chaos=getattr(pr, "chaos", "legendre"), length=getattr(pr, "length", 1.0))
+                    chaos=getattr(pr, "chaos", "legendre"), length=getattr(pr, "length", 1.0),
+                    restart=getattr(pr, "restart", 64))
         args.update(kw)
         return cls(pr.nx, pr.M, pr.p, pr.kappa, pr.beta, pr.yhat, **args)
 

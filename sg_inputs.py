@@ -61,6 +61,7 @@ class Problem:
     omega: float = 0.8
     schur: str = "diagonal"     # time mode: "diagonal" (Z~, block-diagonal in time) or "coupled" (Z_bar)
     krylov: str = "minres"      # "minres" or "fgmres" (the paper's Sec. 5 solver)
+    restart: int = 64           # FGMRES cycle length (the library's default)
     mass_solve: str = "chebyshev"   # mass blocks: "chebyshev" (cheb_steps) or "exact" (Cholesky)
     precond: str = "block"          # "block" (Eq. (stoch-prec) with hGS) or "hgsoc" (Alg. 2-3 / Alg. 4)
     # chaos: "legendre" (xi ~ U[-1,1], affine coefficient, kappa has M+1 planes) or "hermite"

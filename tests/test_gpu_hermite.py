@@ -79,6 +79,7 @@ def test_hermite_solves_match_oracle(krylov, r):
     nA = basis.term_indices(M, p).shape[0]
     pr, d, sp0 = make(nx, M, p, r=nA if r == -2 else r)
     pr.krylov = krylov
+    pr.restart = 400                                 # unrestarted, as the paper's FGMRES
     from paper_2512_23804_gb300 import SGProblem
     sp = SGProblem.from_problem(pr)
     ref = oracle_solve(pr, data=d)
