@@ -557,8 +557,17 @@ def run_ours(args):
     if not args.no_extras and rank == 0:
         # the other workload shapes: one timed solve each (after a warm-up solve), mixed and float64
         ow = {}
+        def paper_setting():
+            # the paper's own setting (Hermite chaos, lognormal field with sigma = 0.4, [-1,1]^2,
+            # gamma = 1, discontinuous target, n_A = C(9, 6) = 84 coefficient terms, r = m + 1),
+            # solved with the paper's Krylov method, unrestarted FGMRES
+            pr = si.paper_problem(32, 3, 3, beta=1e-4, sigma=0.4)
+            pr.krylov, pr.restart = "fgmres", 256
+            return pr
+
         for name, mk in (("steady_16x16_M2_p2", si.steady_16), ("time_64x64_M4_p3_nt32", si.time_64),
-                         ("steady_512x512_M8_p3", si.steady_512)):
+                         ("steady_512x512_M8_p3", si.steady_512),
+                         ("paper_hermite_32x32_M3_p3_sigma0.4_fgmres", paper_setting)):
             pr = mk()
             rec = {"kkt_unknowns": pr.kkt_size}
             xkeep = {}

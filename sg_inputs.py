@@ -238,14 +238,16 @@ def lognormal_terms(nx: int, M: int, p: int, L: float = 0.5, sigma: float = 1.0)
     return out
 
 
-def paper_problem(nx: int, M: int, p: int, beta: float = 1e-4, gamma: float = 1.0, **opts) -> Problem:
+def paper_problem(nx: int, M: int, p: int, beta: float = 1e-4, gamma: float = 1.0, sigma: float = 1.0,
+                  **opts) -> Problem:
     """The paper's steady setting (Sec. 5): D = [-1,1]^2 (length 2, nx elements per side, so
     h = 2/nx), lognormal coefficient with the exponential covariance of correlation length 1
-    and unit variance (0.5 and 1 on the unit square the grid is indexed on), Hermite chaos,
+    and standard deviation sigma (1 by default; the paper's tables take 0.01, 0.1 and 0.4) --
+    correlation length 0.5 on the unit square the grid is indexed on --, Hermite chaos,
     gamma = 1, and the discontinuous target y_d = 1 on [-1,0]^2, 0 elsewhere."""
     x1, x2 = interior_coords(nx)
     yd = ((x1 <= 0.5 + 1e-12) & (x2 <= 0.5 + 1e-12)).astype(np.float64)
-    return Problem(nx=nx, M=M, p=p, kappa=lognormal_terms(nx, M, p), beta=beta, gamma=gamma, nt=0,
+    return Problem(nx=nx, M=M, p=p, kappa=lognormal_terms(nx, M, p, sigma=sigma), beta=beta, gamma=gamma, nt=0,
                    yhat=yd[None, :], chaos="hermite", length=2.0, name=f"paper_{nx}x{nx}_M{M}_p{p}", **opts)
 
 

@@ -93,3 +93,20 @@ def test_hermite_solves_match_oracle(krylov, r):
         # for this unit-variance field) a float32 Arnoldi basis of that length stagnates
         xm, im = SGProblem.from_problem(pr, precision="mixed").solve()
         assert im["status_name"] == "SGOC_OK" and im["rel_true_residual"] <= pr.tol
+
+
+def test_paper_setting_32x32_fgmres_matches_oracle():
+    """The benchmark's instance of the paper's setting: h = 2^-4 on [-1,1]^2, m = 3, p = 3 (P = 20,
+    n_A = 84), sigma = 0.4, beta = 1e-4, gamma = 1, r = m + 1, unrestarted FGMRES."""
+    from paper_2512_23804_gb300 import SGProblem
+    pr = si.paper_problem(32, 3, 3, beta=1e-4, sigma=0.4)
+    pr.krylov, pr.restart = "fgmres", 256
+    d = SGData(pr)
+    ref = oracle_solve(pr, data=d)
+    x, info = SGProblem.from_problem(pr).solve()
+    assert info["status_name"] == "SGOC_OK" and info["rel_true_residual"] <= pr.tol
+    assert abs(info["iterations"] - ref.iterations) <= 1, (info["iterations"], ref.iterations)
+    assert rel(x.cpu().numpy(), ref.x) <= 1e-7
+    xm, im = SGProblem.from_problem(pr, precision="mixed").solve()
+    assert im["status_name"] == "SGOC_OK" and im["rel_true_residual"] <= pr.tol
+    assert rel(xm.cpu().numpy(), ref.x) <= 1e-6
