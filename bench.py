@@ -71,8 +71,9 @@ def load_peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 SG_KERNEL_NAMES = {0: "one-phase", 1: "quad-32", 2: "quad-16", 3: "two-phase", 4: "quad-32x4", 5: "quad-16x4",
                    6: "direct", -1: "none"}
-# ncu: vcycle_t_kernel<float, 127, 2>, 56 columns: 3,681,536 B read + 0 B written
-VCYCLE_DRAM_BYTES_PER_COLUMN = 3681536 / 56
+# DRAM bytes of vcycle_t_kernel<float, 127, 2> (the current kernel) on 56 columns of the 128x128
+# workload, from one ncu capture: 3,681,280 B read + 0 B written
+VCYCLE_DRAM_BYTES_PER_COLUMN = 3681280 / 56
 # float32 non-tensor peak: 152 SMs x 128 FMA/clk x 2 flop x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
