@@ -645,13 +645,14 @@ def run_kernel_case(args):
     print(json.dumps({"kernel_case": case, "ok": True}))
 
 
-def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16):
+def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16, keep_every=1):
     """Serving stream: the first `n_requests` seeded requests (grids 32..256, M 2..8, p 1..4,
     30 % time-dependent), admitted by the server's own memory-footprint check (a request that
     cannot fit the pool even when empty is rejected by sgoc_server_submit and counted), solved to a
     1e-8 float64 residual in mixed precision.  Run once with every request arriving at t = 0
     (capacity mu), then as a Poisson stream at 0.8 mu; compared with sequential plain float64
-    solves of the same requests on the same GPU, and each mixed result with its float64 one."""
+    solves of the same requests on the same GPU, and each mixed result (every keep_every-th request,
+    to bound the device memory the kept solutions take) with its float64 one."""
     import numpy as np
     import torch
     import sg_inputs as si
@@ -688,7 +689,7 @@ def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16):
                                    "error": abi.load().sgoc_last_error().decode()[:200]})
                     continue
                 lat[rid] = info["ms_total"]
-                if keep:
+                if keep and rid % keep_every == 0:
                     xs[rid] = x
         wall = time.perf_counter() - t0
         stats = sv.stats()
@@ -711,14 +712,16 @@ def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16):
     torch.cuda.synchronize()
     seq_lat, errs = [], []
     t0 = time.perf_counter()
+    served = set(i for i in range(len(reqs)) if i not in rejected)
     for i, pr in enumerate(reqs):
-        if i not in xmix:
+        if i not in served:
             continue
         sp = SGProblem.from_problem(pr, precision="fp64")
         t1 = time.perf_counter()
         x, info = sp.solve()
         seq_lat.append((time.perf_counter() - t1) * 1e3)
-        errs.append(float(torch.linalg.norm(xmix[i] - x) / torch.linalg.norm(x)))
+        if i in xmix:
+            errs.append(float(torch.linalg.norm(xmix[i] - x) / torch.linalg.norm(x)))
         del sp, x
     seq_wall = time.perf_counter() - t0
     del xmix
@@ -730,7 +733,7 @@ def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16):
             "solves_per_s": sat["solves_per_s"], "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"],
             "rejected": sat["rejected"], "saturated": sat, "poisson_at_0.8mu": open_loop,
             "sequential_fp64": seq, "vs_sequential_fp64": sat["solves_per_s"] / seq["solves_per_s"],
-            "mixed_vs_fp64_rel_error": {"max": max(errs), "median": statistics.median(errs)}}
+            "mixed_vs_fp64_rel_error": {"max": max(errs), "median": statistics.median(errs), "compared": len(errs)}}
 
 
 def run_serve(args):
@@ -738,7 +741,7 @@ def run_serve(args):
     from paper_2512_23804_gb300 import build
     build.build()
     torch.cuda.set_device(0)
-    rec = serve_leg(args.requests)
+    rec = serve_leg(args.requests, keep_every=1 if args.requests <= 200 else 10)
     print(json.dumps(dict(mode="serve", **rec)), flush=True)
 
 
