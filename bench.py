@@ -710,7 +710,7 @@ def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16, keep_every=1):
     torch.cuda.empty_cache()
     # sequential plain float64 solves of the same (admitted) requests
     torch.cuda.synchronize()
-    seq_lat, errs = [], []
+    seq_lat, errs, seq_failed = [], [], []
     t0 = time.perf_counter()
     served = set(i for i in range(len(reqs)) if i not in rejected)
     for i, pr in enumerate(reqs):
@@ -718,7 +718,11 @@ def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16, keep_every=1):
             continue
         sp = SGProblem.from_problem(pr, precision="fp64")
         t1 = time.perf_counter()
-        x, info = sp.solve()
+        try:
+            x, info = sp.solve()
+        except abi.SgocError as e:
+            seq_failed.append({"id": i, "error": str(e)[:200]})
+            continue
         seq_lat.append((time.perf_counter() - t1) * 1e3)
         if i in xmix:
             errs.append(float(torch.linalg.norm(xmix[i] - x) / torch.linalg.norm(x)))
@@ -727,7 +731,7 @@ def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16, keep_every=1):
     del xmix
     torch.cuda.empty_cache()
     sl = sorted(seq_lat)
-    seq = {"solves_per_s": len(sl) / seq_wall, "p50_ms": sl[len(sl) // 2],
+    seq = {"solves_per_s": len(sl) / seq_wall, "failed": seq_failed, "p50_ms": sl[len(sl) // 2],
            "p99_ms": sl[min(len(sl) - 1, int(math.ceil(0.99 * len(sl))) - 1)]}
     return {"requests": len(reqs), "pool_GB": pool_bytes / 1e9, "max_active": max_active,
             "solves_per_s": sat["solves_per_s"], "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"],
