@@ -14,7 +14,15 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsgoc.so")
 
 SGOC_OK = 0
+SGOC_ERR_INVALID_ARG = 1
 SGOC_ERR_UNSUPPORTED = 2
+SGOC_ERR_WORKSPACE_TOO_SMALL = 3
+SGOC_ERR_CUDA = 4
+SGOC_ERR_NO_CONVERGENCE = 5
+SGOC_ERR_BREAKDOWN = 6
+SGOC_ERR_NOT_SPD = 7
+SGOC_ERR_NAN = 8
+SGOC_ERR_NOT_UPLOADED = 9
 STATUS_NAMES = {
     0: "SGOC_OK", 1: "SGOC_ERR_INVALID_ARG", 2: "SGOC_ERR_UNSUPPORTED", 3: "SGOC_ERR_WORKSPACE_TOO_SMALL",
     4: "SGOC_ERR_CUDA", 5: "SGOC_ERR_NO_CONVERGENCE", 6: "SGOC_ERR_BREAKDOWN", 7: "SGOC_ERR_NOT_SPD",

@@ -27,6 +27,15 @@ def header_symbols():
     return sorted(set(re.findall(r"\b(sgoc_[a-z_0-9]+)\s*\(", txt)))
 
 
+def test_status_codes_match_header():
+    txt = open(os.path.join(ROOT, "include", "sgoc.h")).read()
+    codes = {name: int(v) for name, v in re.findall(r"\b(SGOC_(?:OK|ERR_[A-Z_]+))\s*=\s*(\d+)", txt)}
+    assert len(codes) == 10
+    for name, v in codes.items():
+        assert getattr(abi, name) == v, name
+        assert abi.STATUS_NAMES[v] == name
+
+
 def test_exports_every_declared_symbol():
     lib = abi.load()
     syms = header_symbols()
