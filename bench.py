@@ -645,14 +645,15 @@ def run_kernel_case(args):
     print(json.dumps({"kernel_case": case, "ok": True}))
 
 
-def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16, keep_every=1):
+def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16, keep_every=1, queue_depth=32,
+              out_cap=24e9, keep_cap=16e9):
     """Serving stream: the first `n_requests` seeded requests (grids 32..256, M 2..8, p 1..4,
     30 % time-dependent), admitted by the server's own memory-footprint check (a request that
     cannot fit the pool even when empty is rejected by sgoc_server_submit and counted), solved to a
     1e-8 float64 residual in mixed precision.  Run once with every request arriving at t = 0
     (capacity mu), then as a Poisson stream at 0.8 mu; compared with sequential plain float64
-    solves of the same requests on the same GPU, and each mixed result (every keep_every-th request,
-    to bound the device memory the kept solutions take) with its float64 one."""
+    solves of the same requests on the same GPU, and each mixed result (every keep_every-th request
+    while the kept solutions take at most keep_cap bytes of device memory) with its float64 one."""
     import numpy as np
     import torch
     import sg_inputs as si
@@ -661,36 +662,59 @@ def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16, keep_every=1):
     pool_bytes = int(min(torch.cuda.mem_get_info()[0] * 0.6, pool_cap_bytes))
 
     def run_stream(arrivals, keep):
+        # Arrived requests wait in a client-side queue and are submitted while fewer than
+        # queue_depth are outstanding and their float64 output buffers (the caller's memory,
+        # outside the pool) stay under out_cap; latency runs from arrival to retirement.
         sv = SGServer(pool_bytes=pool_bytes, max_active=max_active)
         sps = [SGProblem.from_problem(pr, precision="mixed") for pr in reqs]
         done, lat, rejected, xs, failed = {}, {}, [], {}, []
+        queue, out_live, kept_bytes = [], {}, 0
         t0 = time.perf_counter()
         nxt = 0
         while len(done) + len(rejected) < len(reqs):
             now = time.perf_counter() - t0
             while nxt < len(reqs) and arrivals[nxt] <= now:
+                queue.append(nxt)
+                nxt += 1
+            while queue and sv.pending < queue_depth and \
+                    sum(out_live.values()) + 8 * sps[queue[0]].kkt_size <= out_cap:
+                i = queue.pop(0)
                 try:
-                    sv.submit(sps[nxt], nxt)
+                    sv.submit(sps[i], i)
+                    out_live[i] = 8 * sps[i].kkt_size
                 except abi.SgocError as e:
                     if e.status != abi.SGOC_ERR_WORKSPACE_TOO_SMALL:
                         raise
-                    rejected.append(nxt)
-                nxt += 1
+                    rejected.append(i)
+            if queue and sv.pending == 0 and not out_live:
+                i = queue.pop(0)          # larger than out_cap alone: submit it by itself
+                try:
+                    sv.submit(sps[i], i)
+                    out_live[i] = 8 * sps[i].kkt_size
+                except abi.SgocError as e:
+                    if e.status != abi.SGOC_ERR_WORKSPACE_TOO_SMALL:
+                        raise
+                    rejected.append(i)
             if sv.pending == 0:
-                if nxt < len(reqs):
+                if nxt < len(reqs) and not queue:
                     time.sleep(max(0.0, min(arrivals[nxt] - now, 0.01)))
                 continue
             sv.step()
             for rid, x, info in sv.poll():
+                t_done = time.perf_counter() - t0
                 done[rid] = info
+                out_live.pop(rid, None)
+                sps[rid] = None
                 if info["status_name"] != "SGOC_OK" or not info["rel_true_residual"] <= 1e-8:
                     failed.append({"id": rid, "status": info["status_name"],
                                    "rel_residual": info["rel_true_residual"],
                                    "error": abi.load().sgoc_last_error().decode()[:200]})
                     continue
-                lat[rid] = info["ms_total"]
-                if keep and rid % keep_every == 0:
+                lat[rid] = (t_done - arrivals[rid]) * 1e3
+                nb = x.numel() * 8
+                if keep and rid % keep_every == 0 and kept_bytes + nb <= keep_cap:
                     xs[rid] = x
+                    kept_bytes += nb
         wall = time.perf_counter() - t0
         stats = sv.stats()
         del sv, sps
