@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=2000, help="serving stream length with --serve")
     ap.add_argument("--serve-requests", type=int, default=100,
                     help="serving leg of the default run: the first N requests of the stream (0: skip)")
-    ap.add_argument("--kernel-case", choices=["vcycle128", "sg128", "sg512", "hgs128", "solve128"], default=None,
+    ap.add_argument("--kernel-case", choices=["vcycle128", "mean128", "sg128", "sg512", "hgs128", "solve128"],
+                    default=None,
                     help="run one kernel class a few times on a small case (for ncu captures) and exit")
     return ap.parse_args()
 
@@ -616,7 +617,7 @@ def run_kernel_case(args):
     build.build()
     case = args.kernel_case
     pr = si.steady_512() if case == "sg512" else si.steady_128(1e-4)
-    sp = SGProblem.from_problem(pr, precision="mixed").upload()
+    sp = SGProblem.from_problem(pr, precision="mixed", mean_solve="exact" if case == "mean128" else "vcycle").upload()
     if case == "solve128":
         # a few MINRES iterations of the 128x128 workload (loose tolerance), launched eagerly
         # (per-kernel timing on) so that a profiler sees ordinary launches, not graph nodes
@@ -631,7 +632,7 @@ def run_kernel_case(args):
         Y = torch.empty_like(X)
         for _ in range(3):
             sp.apply_operator(X, out=Y)
-    elif case == "vcycle128":
+    elif case in ("vcycle128", "mean128"):
         ncols = 56                                  # the largest chaos level of M=6, p=3
         R = torch.randn(ncols * sp.n, dtype=torch.float32, device="cuda")
         X = torch.empty_like(R)

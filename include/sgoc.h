@@ -127,6 +127,13 @@ typedef struct {
                             P~ = blkdiag(M, beta M, A~_1 M^{-1} A~_1), time
                             blkdiag(tau D_t M, beta tau D_t M, (1/tau) A^_1 (D_t M)^{-1} A^_1).  Not
                             symmetric: requires krylov = 1 (FGMRES) */
+  int32_t mean_solve;    /* mean solves B ~ A~_1^{-1} of the hGS sweeps (Alg. 1) and of hGSoc:
+                            0 one V(nu_pre, nu_post) multigrid cycle (0); 1 the exact inverse by fast
+                            diagonalisation (the type-I sine transform diagonalises the constant-
+                            stencil mean operator): four dense products with the transform on the
+                            tensor cores, operands split into two bfloat16 terms (about 1e-5
+                            relative).  Float32 solves only (precision SGOC_MIXED_FP32) on grids
+                            of nx = 64 or 128 elements per side; otherwise SGOC_ERR_UNSUPPORTED */
 } sgoc_options;
 
 typedef struct {
@@ -368,7 +375,7 @@ int64_t sgoc_kernel_launches(void);
  * sgoc_profile_query(kind, ...) waits for the recorded events of one kernel
  * class (kind in [0, SGOC_KERNEL_KINDS)) and returns the launch count, summed
  * device milliseconds, bytes and flops.  No counterpart in the paper. */
-#define SGOC_KERNEL_KINDS 11
+#define SGOC_KERNEL_KINDS 12
 sgoc_status sgoc_profile_enable(int32_t on);
 sgoc_status sgoc_profile_query(int32_t kind, int64_t* launches, double* ms, double* bytes,
                                double* flops);

@@ -29,7 +29,7 @@ STATUS_NAMES = {
     8: "SGOC_ERR_NAN", 9: "SGOC_ERR_NOT_UPLOADED",
 }
 SGOC_FP64, SGOC_MIXED_FP32 = 0, 1
-SGOC_KERNEL_KINDS = 11
+SGOC_KERNEL_KINDS = 12
 SGOC_INNER_PRODUCT_WS_BYTES = 8192
 
 
@@ -46,7 +46,8 @@ class Options(ctypes.Structure):
                 ("cheb_steps", ctypes.c_int32), ("nu_pre", ctypes.c_int32), ("nu_post", ctypes.c_int32),
                 ("omega", ctypes.c_double), ("precision", ctypes.c_int32), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int32), ("schur", ctypes.c_int32), ("krylov", ctypes.c_int32),
-                ("restart", ctypes.c_int32), ("mass_solve", ctypes.c_int32), ("precond", ctypes.c_int32)]
+                ("restart", ctypes.c_int32), ("mass_solve", ctypes.c_int32), ("precond", ctypes.c_int32),
+                ("mean_solve", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):

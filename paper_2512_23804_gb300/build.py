@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsgoc.so")
-SOURCES = ["setup.cu", "kernels.cu", "solver.cu", "noalloc.cu"]
+SOURCES = ["setup.cu", "kernels.cu", "solver.cu", "noalloc.cu", "spectral.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

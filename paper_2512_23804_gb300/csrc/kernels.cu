@@ -45,7 +45,7 @@ struct Profiler {
 Profiler& prof() { static Profiler p; return p; }
 const char* kKindNames[KK_COUNT] = {"sg_operator", "mass", "chebyshev", "mg_smooth", "mg_residual",
                                     "mg_restrict", "mg_prolong", "mg_vcycle_fused", "dot", "minres_scalar",
-                                    "vector_update"};
+                                    "vector_update", "mean_exact"};
 }  // namespace
 
 const char* kernel_kind_name(int kind) { return (kind >= 0 && kind < KK_COUNT) ? kKindNames[kind] : "?"; }
@@ -141,6 +141,8 @@ static bool take_fence(cudaStream_t st) {
     if (g_fenced[i] == st) { g_fenced[i] = g_fenced.back(); g_fenced.pop_back(); return true; }
   return false;
 }
+
+bool pdl_take_fence(cudaStream_t st) { return take_fence(st); }
 
 template <typename... KArgs, typename... Args>
 static cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace sgoc {
 
 // Number of kernels this library has launched in the process (all streams).
@@ -12,6 +14,8 @@ int64_t kernel_launches();
 // (no programmatic overlap): call after a cross-stream event wait, a copy or a
 // graph launch on `st`.
 void pdl_fence(cudaStream_t st);
+// Whether the next launch on `st` must take the full dependency (and clear the mark).
+bool pdl_take_fence(cudaStream_t st);
 void add_launches(int64_t n);
 bool profile_enabled();
 
@@ -19,7 +23,7 @@ bool profile_enabled();
 // CUDA events on its stream and its algorithmic bytes/flops are recorded.
 enum KernelKind {
   KK_SG = 0, KK_MASS, KK_CHEB, KK_SMOOTH, KK_RESIDUAL, KK_RESTRICT, KK_PROLONG, KK_VCYCLE_FUSED,
-  KK_DOT, KK_SCALAR, KK_VECTOR, KK_COUNT
+  KK_DOT, KK_SCALAR, KK_VECTOR, KK_MEAN_EXACT, KK_COUNT
 };
 const char* kernel_kind_name(int kind);
 void profile_enable(bool on);
@@ -179,6 +183,19 @@ template <typename T>
 cudaError_t launch_vcycle_full(const T* b, T* x, int64_t B, const FusedLevels& L, T omega, int nu,
                                T* acc, int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st,
                                VColumns cols = VColumns());
+
+// Exact mean solves by fast diagonalisation on the tensor cores (spectral.cu), float32,
+// for grids of n1 = 63 and 127 interior nodes per side: the V-cycle's column conventions,
+// the stencil (d, e, c) of the mean operator, and the constant image spectral_image(n1)
+// (16-byte aligned device copy).  spectral_take_error reports (and clears) a bounded wait
+// that ran out in one of its launches.
+bool spectral_mean_supported(int n1);
+size_t spectral_image_bytes(int n1);
+std::vector<uint8_t> spectral_image(int n1);
+cudaError_t launch_spectral_mean(const float* b, float* x, int64_t B, int n1, const void* img, double d, double e,
+                                 double c, float* acc, int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st,
+                                 VColumns cols = VColumns());
+cudaError_t spectral_take_error(bool* failed, cudaStream_t st);
 
 // Krylov kernels.  Reductions are deterministic: fixed grid, fixed order.
 constexpr int kDotBlocks = 608;

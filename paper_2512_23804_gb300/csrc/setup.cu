@@ -97,6 +97,7 @@ void sgoc_default_options(sgoc_options* o) {
   o->restart = 64;
   o->mass_solve = 0;
   o->precond = 0;
+  o->mean_solve = 0;
 }
 
 namespace sgoc {
@@ -193,9 +194,15 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
       (o.precision != SGOC_FP64 && o.precision != SGOC_MIXED_FP32) || !(o.inner_tol > 0 && o.inner_tol < 1) ||
       o.max_outer < 1 || (o.schur != 0 && o.schur != 1) || (o.krylov != 0 && o.krylov != 1) ||
       o.restart < 1 || o.restart > kFgmresMax || (o.mass_solve != 0 && o.mass_solve != 1) ||
-      (o.precond != 0 && o.precond != 1) || (o.precond == 1 && o.krylov != 1)) {
+      (o.precond != 0 && o.precond != 1) || (o.precond == 1 && o.krylov != 1) ||
+      (o.mean_solve != 0 && o.mean_solve != 1)) {
     set_error("invalid options (nu_pre must equal nu_post for a symmetric V-cycle)");
     return SGOC_ERR_INVALID_ARG;
+  }
+
+  if (o.mean_solve == 1 && (o.precision != SGOC_MIXED_FP32 || !spectral_mean_supported(nx - 1))) {
+    set_error("exact mean solves (mean_solve = 1) need mixed precision and nx = 64 or 128");
+    return SGOC_ERR_UNSUPPORTED;
   }
 
   auto* pb = new sgoc_problem();
@@ -371,6 +378,7 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
   off = align256(off + nnz_dn * 4); off = align256(off + nnz_dn * 8); off = align256(off + nnz_dn * 4);
   for (const UTab& u : pb->utabs) off += utab_bytes(u);
   off += 2 * align256(size_t(pb->n1) * 8) + 2 * align256(size_t(pb->n1) * 4);   // mass factor tables
+  if (o.mean_solve == 1) off += align256(spectral_image_bytes(pb->n1));            // exact mean solves
   pb->persistent_bytes = off;
   *out = pb;
   return SGOC_OK;
@@ -470,6 +478,14 @@ sgoc_status sgoc_problem_upload(sgoc_problem* pb, void* d_persistent, size_t byt
     SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.mass_id64, id.data(), id.size() * 8, cudaMemcpyHostToDevice, st));
     SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.mass_l32, l32.data(), l32.size() * 4, cudaMemcpyHostToDevice, st));
     SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.mass_id32, id32.data(), id32.size() * 4, cudaMemcpyHostToDevice, st));
+  }
+  // constant image of the exact mean solves: split sine-transform operands and mode table
+  std::vector<uint8_t> spec;
+  pb->dev.spec_img = nullptr;
+  if (pb->opt.mean_solve == 1) {
+    spec = spectral_image(pb->n1);
+    pb->dev.spec_img = carve(spec.size());
+    SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.spec_img, spec.data(), spec.size(), cudaMemcpyHostToDevice, st));
   }
   std::vector<double> k64(nk);
   std::vector<float> k32(nk);

@@ -77,6 +77,7 @@ struct DevData {
   // subdiagonal l_i of L (l_0 = 0) and 1 / D_i, n1 entries each (the exact mass solve)
   double* mass_l64 = nullptr; double* mass_id64 = nullptr;
   float* mass_l32 = nullptr; float* mass_id32 = nullptr;
+  void* spec_img = nullptr;    // exact mean solves: constant image of spectral_image(n1)
   double* yhat = nullptr;      // slabs x n target values
   double* y0 = nullptr;        // n initial state (zeros when absent)
 };

@@ -130,9 +130,22 @@ size_t precond_workspace_bytes(const sgoc_problem* pb, int esize) {
 // With acc != nullptr the correction is added to the chaos columns of V
 // (column col of the batch is slab col / acc_L, chaos column acc_col0 + col % acc_L).
 // cols: strided right-hand side / stored strided output (VColumns), on the single-CTA path only
+// With the exact mean solves (opt.mean_solve = 1) the same call is the exact solve by fast
+// diagonalisation on the tensor cores (float32), with the same column conventions.
 template <typename T>
 static sgoc_status vcycle(const sgoc_problem* pb, PrecWS<T>& w, const T* b, T* xout, int64_t B, T* acc,
                           int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st, VColumns cols = VColumns()) {
+  if (pb->opt.mean_solve == 1) {
+    if constexpr (std::is_same<T, float>::value) {
+      const Level& L0 = pb->levels[0];
+      SGOC_LAUNCH(launch_spectral_mean(b, xout, B, pb->n1, pb->dev.spec_img, L0.diag, L0.edge, L0.corner, acc,
+                                       acc_ss, acc_L, acc_col0, st, cols));
+      return SGOC_OK;
+    } else {
+      set_error("exact mean solves are float32 only");
+      return SGOC_ERR_UNSUPPORTED;
+    }
+  }
   const int nl = int(pb->levels.size());
   const T om = T(pb->opt.omega);
   const int nu = pb->opt.nu_pre;
@@ -361,7 +374,7 @@ static bool hgs_mergeable(const std::vector<HgsMember<T>>& ms) {
   const VPlan vp = plan_vcycle(ms[0].pb, sizeof(T));
   if (vp.lf != 0 || vp.cluster) return false;
   for (const auto& m : ms)
-    if (!same_shape(m.pb, ms[0].pb)) return false;
+    if (!same_shape(m.pb, ms[0].pb) || m.pb->opt.mean_solve != 0) return false;
   return true;
 }
 
@@ -1264,6 +1277,12 @@ struct SolveTask {
     cudaError_t e = cudaMemcpyAsync(x_out, L.k64.x, pb->N * sizeof(double), cudaMemcpyDeviceToDevice, st);
     pdl_fence(st);
     if (status == SGOC_OK && e != cudaSuccess) status = cuda_status(e, "copy solution");
+    if (status == SGOC_OK && pb->opt.mean_solve == 1) {
+      bool failed = false;
+      e = spectral_take_error(&failed, st);
+      if (e != cudaSuccess) status = cuda_status(e, "exact mean solve status");
+      else if (failed) { set_error("exact mean solve: a bounded wait on the tensor cores ran out"); status = SGOC_ERR_CUDA; }
+    }
     result.status = status;
     return status;
   }

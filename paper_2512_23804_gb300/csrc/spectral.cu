@@ -1,0 +1,550 @@
+// Exact mean solves by fast diagonalisation, on the tensor cores (tcgen05).
+//
+// Every mean solve of the preconditioner is a solve with a constant 9-point stencil
+// (d, e, c) of Q1 elements on a uniform grid with homogeneous Dirichlet boundary: the
+// steady A~_1 = kappa0 K + s M (Eq. (mathcalZ)) and the time slab operator
+// A^_1 = (1 + tau s) M + tau kappa0 K (Eq. (A_hat)).  In tensor form both 1-D factors
+// are tridiagonal Toeplitz matrices, diagonalised by the orthonormal type-I sine
+// transform S, S_pi = sqrt(2/(n1+1)) sin(pi (p+1)(i+1)/(n1+1)) (symmetric, S S = I):
+//   A = (S (x) S) Lambda (S (x) S),
+//   lambda_ij = d + 2e (cos th_i + cos th_j) + 4c cos th_i cos th_j,  th_i = pi (i+1)/(n1+1).
+// With a column of the batch as the n1 x n1 matrix X (rows y, columns x),
+//   A^{-1} X = S (Lambda^{-1} o (S X S)) S,
+// four dense products with the constant S: the exact B = A~_1^{-1} of Alg. 1 (the
+// paper's hierarchical Gauss-Seidel) in place of one V-cycle.
+//
+// Layout on the tensor cores.  A tile holds 128 / NB columns of NB = n1 + 1 (padded) rows
+// stacked along M = 128; each product is D = A B with A (M x K) K-major and B (K x N) in
+// shared memory, D (128 lanes x NB columns, float32) in tensor memory:
+//   G1  D1 = X S          A = X (K-major),          B = S_NB (K-major)
+//   G2  D2 = S D1         A = S_128 (K-major),      B = D1   (MN-major)
+//   --  Yh = Lambda^{-1} o D2 (per element, in registers)
+//   G3  D3 = Yh S         A = Yh (K-major),         B = S_NB
+//   G4  D4 = S D3         A = S_128,                B = D3   (MN-major)
+// S_128 is block-diagonal with 128 / NB copies of S_NB.  Thread r of the 128 owns row r
+// (tensor-memory lane r) of every D and writes its row of the next operand, so no
+// transpose is needed: the MN-major operand of G2 / G4 takes the rows of D as its K rows.
+// Operands use the 128-byte swizzled canonical layouts.
+//
+// Precision.  Both factors of every product are split into two bfloat16 terms
+// (v = hi + lo, hi = bf16(v), lo = bf16(v - hi)); a product accumulates
+// A_hi B_hi + A_hi B_lo + A_lo B_hi in float32, so it carries about 16 bits of both
+// operands (relative error ~2^-16, against 2^-24 for float32 arithmetic and ~0.1 for the
+// V-cycle's contraction): the operator applied is the exact inverse to about 1e-5.
+#include "kernels.h"
+
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace sgoc {
+
+namespace {
+
+constexpr int kSpecThreads = 256;        // two warps per tensor-memory lane quarter
+constexpr uint32_t kSpecTmemCols = 128;  // one float32 accumulator of up to 128 columns
+constexpr int kSpecSpin = 1 << 20;       // bounded mbarrier polls before the kernel gives up
+
+template <int NB>
+struct SpecGeo {
+  static_assert(NB == 64 || NB == 128, "padded grid sizes 64 and 128");
+  static constexpr int CPT = 128 / NB;                 // grid columns per tile
+  static constexpr int N1 = NB - 1;                    // interior nodes per side
+  static constexpr int N0 = N1 * N1;
+  static constexpr int KSTEPS_NB = NB / 16;            // bf16 MMA steps (K = 16) over NB
+  static constexpr int SA = 128 * 128 * 2;             // one bf16 128 x 128 operand
+  static constexpr int SB = NB == 128 ? 0 : NB * NB * 2;
+  static constexpr int DAT = 128 * NB * 2;             // one bf16 data operand
+  static constexpr int oSAh = 0, oSAl = SA;
+  static constexpr int oSBh = NB == 128 ? oSAh : 2 * SA;
+  static constexpr int oSBl = NB == 128 ? oSAl : 2 * SA + SB;
+  static constexpr int oT = 2 * SA + 2 * SB;           // mode table t_i = 1 - cos th_i
+  static constexpr int IMG = oT + NB * 4;              // bytes of the constant image
+  static constexpr int oDh = (IMG + 1023) / 1024 * 1024;
+  static constexpr int oDl = oDh + DAT;
+  static constexpr int oBar = oDl + DAT;               // two mbarriers
+  static constexpr int oTm = oBar + 16;                // tensor-memory address
+  static constexpr int SMEM = oTm + 16 + 1024;         // + slack to align the base to 1024
+  static constexpr int SBO_MN = (NB / 64) * 1024;      // MN-major: stride of 8-row K groups
+};
+
+// byte offset of element (r, k) of an R-row, K-major operand, 128-byte swizzle:
+// 8-row x 128-byte atoms, 16-byte chunks XOR-ed with the row within the atom,
+// atoms along K (64 bf16) at R / 8 * 1024 bytes
+__host__ __device__ constexpr int off_kmajor(int R, int r, int k) {
+  return (k >> 6) * (R / 8 * 1024) + (r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 3) & 7) ^ (r & 7)) << 4) +
+         (k & 7) * 2;
+}
+// byte offset of element (k, n) of a K x N MN-major operand, 128-byte swizzle: rows are
+// K indices, 64 n per 128-byte atom row, atoms along N at 1024 bytes, 8-row K groups at sbo
+__host__ __device__ constexpr int off_mnmajor(int sbo, int k, int n) {
+  return (k >> 3) * sbo + (n >> 6) * 1024 + (k & 7) * 128 + ((((n >> 3) & 7) ^ (k & 7)) << 4) + (n & 7) * 2;
+}
+
+// ------------------------------------------------------------ PTX wrappers --
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void spec_pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void spec_pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy shared-memory writes made visible to the tensor cores (async proxy)
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase of the given parity; false when the polls ran out
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int i = 0; i < kSpecSpin; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// 1-D bulk copy global -> shared, completing `bytes` transactions on the mbarrier
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// shared-memory matrix descriptor, 128-byte swizzle (sm_100 format: version bit 46,
+// layout type 2 in bits 61-63), start address, leading and stride byte offsets >> 4
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return uint64_t((saddr & 0x3FFFFu) >> 4) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
+         (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+}
+// instruction descriptor of kind::f16: float32 accumulator (bits 4-5 = 1), bf16 A and B
+// (bits 7-9, 10-12 = 1), A K-major, B K-major or MN-major (bit 16), N >> 3 (bits 17-22),
+// M >> 4 (bits 24-28)
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(b_mn ? 1 : 0) << 16) | (uint32_t(N >> 3) << 17) |
+         (uint32_t(M >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+// 32 consecutive float32 columns of this thread's lane; the wait is part of the same
+// statement, so no use of the values can be scheduled before the load completes
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+__device__ __forceinline__ void sts32(uint32_t addr, uint32_t a) {
+  asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(a) : "memory");
+}
+
+// v = hi + lo with hi = bf16(v), lo = bf16(v - hi), for a pair; packed bf16x2 words
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// D = A B over K = 16 * ksteps with the split operands: A_hi B_hi + A_hi B_lo + A_lo B_hi.
+// a_step / b_step give the byte offset of k-step s within an operand region.
+template <typename FA, typename FB>
+__device__ __forceinline__ void gemm3(uint32_t tmem, uint32_t a_hi, uint32_t a_lo, uint32_t a_lbo, uint32_t a_sbo,
+                                      uint32_t b_hi, uint32_t b_lo, uint32_t b_lbo, uint32_t b_sbo, uint32_t idesc,
+                                      int ksteps, FA a_step, FB b_step) {
+  for (int s = 0; s < ksteps; ++s) {
+    const uint32_t ao = a_step(s), bo = b_step(s);
+    const uint64_t ah = sw128_desc(a_hi + ao, a_lbo, a_sbo), al = sw128_desc(a_lo + ao, a_lbo, a_sbo);
+    const uint64_t bh = sw128_desc(b_hi + bo, b_lbo, b_sbo), bl = sw128_desc(b_lo + bo, b_lbo, b_sbo);
+    tc_mma(tmem, ah, bh, idesc, s > 0 ? 1u : 0u);
+    tc_mma(tmem, ah, bl, idesc, 1u);
+    tc_mma(tmem, al, bh, idesc, 1u);
+  }
+}
+
+}  // namespace
+
+// set when a bounded wait of the kernel ran out (the tensor cores or the bulk copy never
+// signalled); read and cleared by spectral_take_error
+__device__ int g_spec_err = 0;
+
+// Exact mean solves of B columns.  Column col's right-hand side is read at
+// b + (col / b_L) b_ss + (col % b_L) n0 when cols.b_L > 0, else at b + col n0; its solution
+// goes to x + col n0, or with acc to acc + (col / acc_L) acc_ss + (acc_col0 + col % acc_L) n0,
+// added when cols.acc_add (the V-cycle's conventions).  img is the constant image of the
+// split S operands and the mode table; (l0, l1, l2) the eigenvalue coefficients,
+// lambda_ij = l0 + l1 (t_i + t_j) + l2 t_i t_j with t_i = 1 - cos th_i.
+// 256 threads: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its lane quarter) and
+// takes the column half w / 4 of every accumulator row; thread 0 issues the products.
+template <int NB>
+__global__ void __launch_bounds__(kSpecThreads, 1)
+    spectral_mean_kernel(const float* __restrict__ bg, float* xg, int64_t B, const uint8_t* __restrict__ img,
+                         float l0, float l1, float l2, float* acc, int64_t acc_ss, int acc_L, int acc_col0,
+                         VColumns cols) {
+  using G = SpecGeo<NB>;
+  constexpr int NW = kSpecThreads / 32;              // warps
+  constexpr int HALF = NB / 2;                       // accumulator columns per warp
+  extern __shared__ uint8_t spec_raw[];
+  const uint32_t raw = smem_u32(spec_raw);
+  const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
+  const uint8_t* sm = spec_raw + pad;
+  const uint32_t s0 = raw + pad;                     // 1024-aligned: the swizzle atoms' base
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = (warp & 3) * 32 + lane;            // accumulator row (tensor-memory lane)
+  const int jbase = (warp >> 2) * HALF;              // first accumulator column of this thread
+  const uint32_t bar_ld = s0 + G::oBar, bar_mma = s0 + G::oBar + 8;
+  if (tid == 0) {
+    mbar_init(bar_ld, 1);
+    mbar_init(bar_mma, 1);
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(s0 + G::oTm, kSpecTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *reinterpret_cast<const volatile uint32_t*>(sm + G::oTm);
+  if (tid == 0) {                                    // constant data: before the dependency wait
+    mbar_expect_tx(bar_ld, uint32_t(G::IMG));
+    bulk_g2s(s0, img, uint32_t(G::IMG), bar_ld);
+  }
+  const int64_t col0 = int64_t(blockIdx.x) * G::CPT;
+  const float* bcol[G::CPT];
+#pragma unroll
+  for (int c = 0; c < G::CPT; ++c) {
+    const int64_t col = col0 + c;
+    bcol[c] = col >= B ? nullptr
+                       : (cols.b_L > 0 ? bg + (col / cols.b_L) * cols.b_ss + (col % cols.b_L) * int64_t(G::N0)
+                                       : bg + col * int64_t(G::N0));
+  }
+  spec_pdl_wait();                                   // the right-hand sides and outputs are shared
+  // L: right-hand sides of the tile (row r = c NB + y, K index x), split, as the K-major A of G1;
+  // the padding row y = N1, column x = N1 and absent columns are zero.  A warp takes rows
+  // warp, warp + NW, ...; lane l the pairs x = 2 l (+ 64): four rows' loads are in flight at once.
+  {
+    constexpr int PPL = NB / 64;                     // pairs per lane and row
+    constexpr int RB = 4;                            // rows per batch
+#pragma unroll 1
+    for (int r0 = warp; r0 < 128; r0 += NW * RB) {
+      float va[RB][PPL], vb[RB][PPL];
+#pragma unroll
+      for (int u = 0; u < RB; ++u) {
+        const int r = r0 + u * NW;
+        const int c = r / NB, y = r - c * NB;
+        const float* bc = bcol[0];
+#pragma unroll
+        for (int i = 1; i < G::CPT; ++i)
+          if (c == i) bc = bcol[i];
+        const bool live = bc != nullptr && y < G::N1;
+#pragma unroll
+        for (int h = 0; h < PPL; ++h) {
+          const int k = 2 * (lane + 32 * h);
+          va[u][h] = live ? bc[y * G::N1 + k] : 0.f;
+          vb[u][h] = live && k + 1 < G::N1 ? bc[y * G::N1 + k + 1] : 0.f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < RB; ++u) {
+        const int r = r0 + u * NW;
+#pragma unroll
+        for (int h = 0; h < PPL; ++h) {
+          uint32_t hi, lo;
+          split2(va[u][h], vb[u][h], hi, lo);
+          const int o = off_kmajor(128, r, 2 * (lane + 32 * h));
+          sts32(s0 + G::oDh + o, hi);
+          sts32(s0 + G::oDl + o, lo);
+        }
+      }
+    }
+  }
+  fence_async_smem();
+  bool ok = mbar_wait(bar_ld, 0);
+  ok = __syncthreads_and(ok) != 0;
+
+  constexpr uint32_t idK = idesc_bf16(128, NB, false), idMN = idesc_bf16(128, NB, true);
+  const auto stepA = [](int s) { return uint32_t((s >> 2) * (16 * 1024) + (s & 3) * 32); };    // K-major, 128 rows
+  const auto stepB = [](int s) { return uint32_t((s >> 2) * (NB / 8 * 1024) + (s & 3) * 32); }; // K-major, NB rows
+  const auto stepMN = [](int s) { return uint32_t(s * 2 * G::SBO_MN); };                        // MN-major
+  const uint32_t trow = tmem + (uint32_t((warp & 3) * 32) << 16);   // this warp's lane quarter
+  uint32_t parity = 0;
+  // issue one product (thread 0) and wait for it (every thread)
+  auto product = [&](bool left) {
+    if (tid == 0) {
+      tc_fence_after();
+      if (!left)
+        gemm3(tmem, s0 + G::oDh, s0 + G::oDl, 16, 1024, s0 + G::oSBh, s0 + G::oSBl, 16, 1024, idK, G::KSTEPS_NB,
+              stepA, stepB);
+      else
+        gemm3(tmem, s0 + G::oSAh, s0 + G::oSAl, 16, 1024, s0 + G::oDh, s0 + G::oDl, 1024, G::SBO_MN, idMN, 8, stepA,
+              stepMN);
+      tc_commit(bar_mma);
+    }
+    bool w = mbar_wait(bar_mma, parity);
+    parity ^= 1u;
+    w = __syncthreads_and(w) != 0;
+    tc_fence_after();
+    return w;
+  };
+  // this thread's half of accumulator row `row` -> split operand: MN-major B (K row `row`)
+  // or K-major A (row `row`), scaled by Lambda^{-1} when `scale`
+  auto store_row = [&](bool mn, bool scale) {
+    const float* tt = reinterpret_cast<const float*>(sm + G::oT);
+    const float tm = tt[row % NB];
+    const float ar = fmaf(l1, tm, l0), br = fmaf(l2, tm, l1);
+#pragma unroll 1
+    for (int j0 = jbase; j0 < jbase + HALF; j0 += 32) {
+      float v[32];
+      tmem_ld32(trow + uint32_t(j0), v);
+      if (scale) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = __fdividef(v[i], fmaf(br, tt[j0 + i], ar));
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) split2(v[8 * q + 2 * i], v[8 * q + 2 * i + 1], h[i], l[i]);
+        const int o = mn ? off_mnmajor(G::SBO_MN, row, j0 + 8 * q) : off_kmajor(128, row, j0 + 8 * q);
+        sts128(s0 + G::oDh + o, h[0], h[1], h[2], h[3]);
+        sts128(s0 + G::oDl + o, l[0], l[1], l[2], l[3]);
+      }
+    }
+    tc_fence_before();
+    fence_async_smem();
+    __syncthreads();
+  };
+  __syncthreads();
+  if (ok) ok = product(false);                       // G1: D1 = X S
+  if (ok) store_row(true, false);
+  if (ok) ok = product(true);                        // G2: D2 = S D1 = S X S
+  if (ok) store_row(false, true);                    // Lambda^{-1} o D2
+  if (ok) ok = product(false);                       // G3: D3 = Yh S
+  if (ok) store_row(true, false);
+  if (ok) ok = product(true);                        // G4: D4 = S D3, the solution
+  spec_pdl_trigger();                                // only the write of the solution remains
+  if (ok) {
+    // stage accumulator row `row` in float32 (16-byte chunks XOR-ed with the row), then write
+    // each grid row coalesced: a warp per row, lanes along x
+#pragma unroll 1
+    for (int j0 = jbase; j0 < jbase + HALF; j0 += 32) {
+      float v[32];
+      tmem_ld32(trow + uint32_t(j0), v);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int o = row * NB * 4 + ((((j0 >> 2) + q) ^ (row & 7)) << 4);
+        sts128(s0 + G::oDh + o, __float_as_uint(v[4 * q]), __float_as_uint(v[4 * q + 1]),
+               __float_as_uint(v[4 * q + 2]), __float_as_uint(v[4 * q + 3]));
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    const bool acc_on = acc != nullptr && cols.acc_add;
+    constexpr int XPL = (G::N1 + 31) / 32;           // grid columns per lane
+    constexpr int RB = 4;
+#pragma unroll 1
+    for (int r0 = warp; r0 < 128; r0 += NW * RB) {
+      float* go[RB];
+      float val[RB][XPL], old[RB][XPL];
+#pragma unroll
+      for (int u = 0; u < RB; ++u) {
+        const int r = r0 + u * NW;
+        const int c = r / NB, y = r - c * NB;
+        const int64_t col = col0 + c;
+        go[u] = nullptr;
+        if (col < B && y < G::N1)
+          go[u] = (acc != nullptr ? acc + (col / acc_L) * acc_ss + (acc_col0 + col % acc_L) * int64_t(G::N0)
+                                  : xg + col * int64_t(G::N0)) + y * G::N1;
+#pragma unroll
+        for (int h = 0; h < XPL; ++h) {
+          const int x = lane + 32 * h;
+          val[u][h] = *reinterpret_cast<const float*>(sm + G::oDh + r * NB * 4 + (((x >> 2) ^ (r & 7)) << 4) +
+                                                      (x & 3) * 4);
+          old[u][h] = acc_on && go[u] != nullptr && x < G::N1 ? go[u][x] : 0.f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < RB; ++u) {
+        if (go[u] == nullptr) continue;
+#pragma unroll
+        for (int h = 0; h < XPL; ++h) {
+          const int x = lane + 32 * h;
+          if (x < G::N1) go[u][x] = acc_on ? old[u][h] + val[u][h] : val[u][h];
+        }
+      }
+    }
+  } else {
+    if (tid == 0) atomicExch(&g_spec_err, 1);
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kSpecTmemCols);
+  }
+}
+
+template <int NB>
+std::vector<uint8_t> build_image(int n1) {
+  using G = SpecGeo<NB>;
+  std::vector<uint8_t> img(G::IMG, 0);
+  // S_NB padded with a zero row and column, split into bf16 hi and lo (round to nearest even)
+  auto bf16 = [](float v) -> uint16_t {
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return uint16_t(u >> 16);
+  };
+  auto unbf = [](uint16_t h) -> float {
+    const uint32_t u = uint32_t(h) << 16;
+    float v;
+    std::memcpy(&v, &u, 4);
+    return v;
+  };
+  const double sc = std::sqrt(2.0 / (n1 + 1)), pi = 3.14159265358979323846;
+  std::vector<uint16_t> hi(NB * NB, 0), lo(NB * NB, 0);
+  for (int p = 0; p < n1; ++p)
+    for (int i = 0; i < n1; ++i) {
+      const float v = float(sc * std::sin(pi * double(p + 1) * double(i + 1) / double(n1 + 1)));
+      const uint16_t h = bf16(v);
+      hi[p * NB + i] = h;
+      lo[p * NB + i] = bf16(v - unbf(h));
+    }
+  auto put = [&](int base, int R, int r, int k, uint16_t v) { std::memcpy(&img[base + off_kmajor(R, r, k)], &v, 2); };
+  // S_128: block-diagonal copies of S_NB
+  for (int r = 0; r < 128; ++r)
+    for (int k = 0; k < 128; ++k) {
+      if (r / NB != k / NB) continue;
+      put(G::oSAh, 128, r, k, hi[(r % NB) * NB + k % NB]);
+      put(G::oSAl, 128, r, k, lo[(r % NB) * NB + k % NB]);
+    }
+  if (NB < 128)
+    for (int r = 0; r < NB; ++r)
+      for (int k = 0; k < NB; ++k) {
+        put(G::oSBh, NB, r, k, hi[r * NB + k]);
+        put(G::oSBl, NB, r, k, lo[r * NB + k]);
+      }
+  // t_i = 1 - cos th_i = 2 sin^2(th_i / 2); the padding mode takes 1 (cos = 0: a positive lambda)
+  for (int i = 0; i < NB; ++i) {
+    const double s = std::sin(pi * double(i + 1) / (2.0 * (n1 + 1)));
+    const float t = i < n1 ? float(2.0 * s * s) : 1.0f;
+    std::memcpy(&img[G::oT + 4 * i], &t, 4);
+  }
+  return img;
+}
+
+template <int NB>
+cudaError_t launch_nb(const float* b, float* x, int64_t B, const void* img, double d, double e, double c, float* acc,
+                      int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st, VColumns cols) {
+  using G = SpecGeo<NB>;
+  auto k = spectral_mean_kernel<NB>;
+  cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+  if (err != cudaSuccess) return err;
+  // eigenvalue coefficients in the cancellation-free form (t = 1 - cos th):
+  // lambda = (d + 4e + 4c) - (2e + 4c)(t_i + t_j) + 4c t_i t_j
+  const float l0 = float(d + 4.0 * e + 4.0 * c), l1 = float(-(2.0 * e + 4.0 * c)), l2 = float(4.0 * c);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned((B + G::CPT - 1) / G::CPT));
+  cfg.blockDim = dim3(kSpecThreads);
+  cfg.dynamicSmemBytes = G::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_take_fence(st) ? 0 : 1;
+  return cudaLaunchKernelEx(&cfg, k, b, x, B, static_cast<const uint8_t*>(img), l0, l1, l2, acc, acc_ss, acc_L,
+                            acc_col0, cols);
+}
+
+bool spectral_mean_supported(int n1) { return n1 == 63 || n1 == 127; }
+
+size_t spectral_image_bytes(int n1) {
+  if (n1 == 63) return size_t(SpecGeo<64>::IMG);
+  if (n1 == 127) return size_t(SpecGeo<128>::IMG);
+  return 0;
+}
+
+std::vector<uint8_t> spectral_image(int n1) {
+  if (n1 == 63) return build_image<64>(n1);
+  if (n1 == 127) return build_image<128>(n1);
+  return {};
+}
+
+cudaError_t launch_spectral_mean(const float* b, float* x, int64_t B, int n1, const void* img, double d, double e,
+                                 double c, float* acc, int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st,
+                                 VColumns cols) {
+  if (B == 0) return cudaSuccess;
+  if (!spectral_mean_supported(n1) || img == nullptr || (reinterpret_cast<uintptr_t>(img) & 15))
+    return cudaErrorInvalidValue;
+  const int NB = n1 + 1, CPT = 128 / NB;
+  const double tiles = double((B + CPT - 1) / CPT);
+  // tensor work: per tile 3 bf16 products for each of G1, G3 (128 x NB x NB) and G2, G4 (128 x 128 x NB)
+  const double n0 = double(n1) * n1;
+  ProfScope ps(KK_MEAN_EXACT, st, 4.0 * double(B) * n0 * (acc ? 3 : 2),
+               tiles * 3.0 * 2.0 * 2.0 * 128.0 * NB * (double(NB) + 128.0));
+  cudaError_t err = n1 == 63 ? launch_nb<64>(b, x, B, img, d, e, c, acc, acc_ss, acc_L, acc_col0, st, cols)
+                             : launch_nb<128>(b, x, B, img, d, e, c, acc, acc_ss, acc_L, acc_col0, st, cols);
+  add_launches(1);
+  return err != cudaSuccess ? err : cudaGetLastError();
+}
+
+cudaError_t spectral_take_error(bool* failed, cudaStream_t st) {
+  static int* host = nullptr;
+  if (host == nullptr) {
+    cudaError_t e = cudaMallocHost(&host, sizeof(int));
+    if (e != cudaSuccess) return e;
+  }
+  static const int zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbolAsync(host, g_spec_err, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  *failed = *host != 0;
+  if (*failed) {
+    e = cudaMemcpyToSymbolAsync(g_spec_err, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  return e;
+}
+
+}  // namespace sgoc

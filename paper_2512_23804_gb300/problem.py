@@ -33,7 +33,7 @@ class SGProblem:
                  length=1.0, tol=1e-8,
                  max_iter=1000, r=0, cheb_steps=5, nu=2, omega=0.8, precision="fp64", inner_tol=1e-3,
                  max_outer=20, schur="diagonal", krylov="minres", restart=64, mass_solve="chebyshev",
-                 precond="block"):
+                 precond="block", mean_solve="vcycle"):
         self._handle = None
         lib = abi.load()
         self._kappa = np.ascontiguousarray(kappa, dtype=np.float64)
@@ -53,6 +53,7 @@ class SGProblem:
         opts.restart = restart
         opts.mass_solve = {"chebyshev": 0, "exact": 1}[mass_solve]
         opts.precond = {"block": 0, "hgsoc": 1}[precond]
+        opts.mean_solve = {"vcycle": 0, "exact": 1}[mean_solve]
         if precond == "hgsoc":
             opts.krylov = 1                   # the hGSoc preconditioner is not symmetric
         h = ctypes.c_void_p()
@@ -82,7 +83,7 @@ class SGProblem:
                     schur=getattr(pr, "schur", "diagonal"), krylov=getattr(pr, "krylov", "minres"),
                     mass_solve=getattr(pr, "mass_solve", "chebyshev"), precond=getattr(pr, "precond", "block"),
                     chaos=getattr(pr, "chaos", "legendre"), length=getattr(pr, "length", 1.0),
-                    restart=getattr(pr, "restart", 64))
+                    restart=getattr(pr, "restart", 64), mean_solve=getattr(pr, "mean_solve", "vcycle"))
         args.update(kw)
         return cls(pr.nx, pr.M, pr.p, pr.kappa, pr.beta, pr.yhat, **args)
 

@@ -64,6 +64,7 @@ class Problem:
     restart: int = 64           # FGMRES cycle length (the library's default)
     mass_solve: str = "chebyshev"   # mass blocks: "chebyshev" (cheb_steps) or "exact" (Cholesky)
     precond: str = "block"          # "block" (Eq. (stoch-prec) with hGS) or "hgsoc" (Alg. 2-3 / Alg. 4)
+    mean_solve: str = "vcycle"      # mean solves: "vcycle" (one multigrid cycle) or "exact" (A~_1^{-1})
     # chaos: "legendre" (xi ~ U[-1,1], affine coefficient, kappa has M+1 planes) or "hermite"
     # (xi ~ N(0,1), lognormal coefficient, kappa has n_A = C(M+2p, 2p) planes in graded order)
     chaos: str = "legendre"

@@ -101,6 +101,21 @@ def test_invalid_problems_rejected(over, status):
     assert abi.STATUS_NAMES[ei.value.status] == status
 
 
+def test_exact_mean_solve_option_scope():
+    """mean_solve = "exact" (the tensor-core fast-diagonalisation solve) exists for mixed
+    precision on 64 x 64 and 128 x 128 grids; float64 and other grids are refused at set-up."""
+    for nx, precision, ok in [(64, "mixed", True), (128, "mixed", True), (32, "mixed", False),
+                              (256, "mixed", False), (64, "fp64", False)]:
+        pr = si.random_small(7, nx=nx, M=1, p=1)
+        if ok:
+            sp = SGProblem.from_problem(pr, precision=precision, mean_solve="exact")
+            assert sp.persistent_bytes > SGProblem.from_problem(pr, precision=precision).persistent_bytes
+        else:
+            with pytest.raises(abi.SgocError) as ei:
+                SGProblem.from_problem(pr, precision=precision, mean_solve="exact")
+            assert abi.STATUS_NAMES[ei.value.status] == "SGOC_ERR_UNSUPPORTED"
+
+
 def test_nonconstant_mean_and_nan_rejected():
     pr = si.random_small(0, nx=8, M=2, p=2)
     k = pr.kappa.copy()

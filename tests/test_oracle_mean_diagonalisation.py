@@ -1,0 +1,66 @@
+"""The fact the exact mean solves on the tensor cores rest on, checked on the oracle's own
+assembled operators with SciPy's type-I discrete sine transform (an independent library
+routine): every mean operator of the preconditioner -- the steady A~_1 = K_0 + s M of
+Eq. (mathcalZ) and the time slab operator A^_1 = (1 + tau s) M + tau K_0 of Eq. (A_hat) --
+is diagonalised by the orthonormal 2-D sine transform, with the eigenvalue of mode (i, j)
+lambda_ij = d + 2e (cos th_i + cos th_j) + 4c cos th_i cos th_j, th_i = pi i / nx, where
+(d, e, c) is the operator's 9-point stencil (centre, edge, corner).  No GPU is used."""
+
+import numpy as np
+import pytest
+import scipy.fft
+
+import sg_inputs as si
+from oracle.operators import SGData
+from oracle.precond import BlockPreconditioner, ExactSolve
+
+
+def dst2(X):
+    return scipy.fft.dstn(X, type=1, norm="ortho")
+
+
+@pytest.mark.parametrize("nx,nt,beta,gamma", [(8, 0, 1e-2, 0.0), (16, 0, 1e-4, 1.0), (16, 4, 1e-3, 0.0),
+                                              (32, 0, 1e-6, 0.0)])
+def test_mean_operator_is_diagonal_in_the_sine_basis(nx, nt, beta, gamma):
+    pr = si.random_small(11 + nx, nx=nx, M=2, p=1, nt=nt, beta=beta, gamma=gamma)
+    d = SGData(pr)
+    A0 = BlockPreconditioner(d, mode="exact").A0.toarray()
+    n1 = nx - 1
+    c0 = n1 + 1                                   # interior node (1, 1) in x-fastest order
+    dg, ed, co = A0[c0, c0], A0[c0, c0 + 1], A0[c0, c0 + n1 + 1]
+    # the operator is exactly that constant stencil (homogeneous Dirichlet boundary)
+    for q in range(n1 * n1):
+        y, x = divmod(q, n1)
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                yy, xx = y + dy, x + dx
+                if 0 <= yy < n1 and 0 <= xx < n1:
+                    want = dg if dy == dx == 0 else (ed if dy == 0 or dx == 0 else co)
+                    assert A0[q, yy * n1 + xx] == pytest.approx(want, rel=1e-12, abs=1e-15)
+    cth = np.cos(np.pi * np.arange(1, n1 + 1) / nx)
+    lam = dg + 2 * ed * (cth[:, None] + cth[None, :]) + 4 * co * np.outer(cth, cth)
+    assert lam.min() > 0
+    # S_2 A S_2 = diag(lambda), column by column through the transform of each basis image
+    rng = np.random.default_rng(nx + nt)
+    for _ in range(3):
+        Xh = rng.standard_normal((n1, n1))
+        X = dst2(Xh)                              # X = S_2 Xh (S_2 is its own inverse)
+        AX = (A0 @ X.reshape(-1)).reshape(n1, n1)
+        np.testing.assert_allclose(dst2(AX), lam * Xh, rtol=1e-10, atol=1e-12 * np.abs(lam * Xh).max())
+
+
+@pytest.mark.parametrize("nx,nt", [(16, 0), (16, 3)])
+def test_spectral_solve_equals_lu_solve(nx, nt):
+    """A^{-1} b = S_2 (Lambda^{-1} o S_2 b) agrees with the oracle's sparse LU mean solve."""
+    pr = si.random_small(21 + nx + nt, nx=nx, M=2, p=1, nt=nt, beta=1e-3)
+    d = SGData(pr)
+    A0 = BlockPreconditioner(d, mode="exact").A0
+    n1 = nx - 1
+    Ad = A0.toarray()
+    c0 = n1 + 1
+    dg, ed, co = Ad[c0, c0], Ad[c0, c0 + 1], Ad[c0, c0 + n1 + 1]
+    cth = np.cos(np.pi * np.arange(1, n1 + 1) / nx)
+    lam = dg + 2 * ed * (cth[:, None] + cth[None, :]) + 4 * co * np.outer(cth, cth)
+    b = np.random.default_rng(3).standard_normal(n1 * n1)
+    x = dst2(dst2(b.reshape(n1, n1)) / lam).reshape(-1)
+    np.testing.assert_allclose(x, ExactSolve(A0).apply(b), rtol=1e-10, atol=1e-12 * np.abs(x).max())
