@@ -43,8 +43,8 @@ namespace sgoc {
 
 namespace {
 
-constexpr int kSpecThreads = 256;        // two warps per tensor-memory lane quarter
-constexpr uint32_t kSpecTmemCols = 128;  // one float32 accumulator of up to 128 columns
+constexpr int kSpecThreads = 512;        // four warps per tensor-memory lane quarter
+constexpr uint32_t kSpecTmemCols = 256;  // the float32 accumulator and the table of 1 / lambda
 constexpr int kSpecSpin = 1 << 20;       // bounded mbarrier polls before the kernel gives up
 
 template <int NB>
@@ -64,8 +64,10 @@ struct SpecGeo {
   static constexpr int IMG = oT + NB * 4;              // bytes of the constant image
   static constexpr int oDh = (IMG + 1023) / 1024 * 1024;
   static constexpr int oDl = oDh + DAT;
-  static constexpr int oBar = oDl + DAT;               // two mbarriers
-  static constexpr int oTm = oBar + 16;                // tensor-memory address
+  static constexpr int STG = (N0 * 4 + 16 + 15) / 16 * 16;   // float32 column in its global layout
+  static constexpr int oStg = oDl + DAT;               // CPT staging columns (input, then output)
+  static constexpr int oBar = oStg + CPT * STG;        // three mbarriers
+  static constexpr int oTm = oBar + 24;                // tensor-memory address
   static constexpr int SMEM = oTm + 16 + 1024;         // + slack to align the base to 1024
   static constexpr int SBO_MN = (NB / 64) * 1024;      // MN-major: stride of 8-row K groups
 };
@@ -123,6 +125,36 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
+// 1-D bulk copy shared -> global, and its float32 add-reduction form (bulk group completion)
+__device__ __forceinline__ void bulk_s2g(void* dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_s2g_add(void* dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst), "r"(src),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// A float32 column of n0 values at global address g, staged in shared memory at stage + (g & 15)
+// + 4 i (stage 16-byte aligned): the 16-byte aligned middle [lo, hi) moves by bulk copy, the
+// at most three values before lo (head) and after hi (tail) by ordinary accesses.
+struct StageSpan {
+  uint32_t off;      // g & 15: byte offset of value 0 in the staging column
+  int i_lo, i_hi;    // values [i_lo, i_hi) form the aligned middle
+};
+__device__ __forceinline__ StageSpan stage_span(const void* g, int n0) {
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(g), a1 = a0 + uintptr_t(n0) * 4;
+  const uintptr_t lo = (a0 + 15) & ~uintptr_t(15), hi = a1 & ~uintptr_t(15);
+  StageSpan sp;
+  sp.off = uint32_t(a0 & 15);
+  sp.i_lo = int((lo - a0) / 4);
+  sp.i_hi = hi > lo ? int((hi - a0) / 4) : sp.i_lo;
+  return sp;
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
                : "memory");
@@ -172,6 +204,39 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[N]) {
+  static_assert(N == 16 || N == 32, "16 or 32 columns");
+  if constexpr (N == 32) tmem_ld32(taddr, v);
+  else tmem_ld16(taddr, v);
+}
+// store 16 float32 columns of this thread's lane, and wait for the store to complete
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};\n"
+      "tcgen05.wait::st.sync.aligned;\n" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+
 __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
@@ -225,7 +290,7 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
                          VColumns cols) {
   using G = SpecGeo<NB>;
   constexpr int NW = kSpecThreads / 32;              // warps
-  constexpr int HALF = NB / 2;                       // accumulator columns per warp
+  constexpr int CPW = NB / (NW / 4);                 // accumulator columns per warp (16 or 32)
   extern __shared__ uint8_t spec_raw[];
   const uint32_t raw = smem_u32(spec_raw);
   const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
@@ -233,11 +298,12 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
   const uint32_t s0 = raw + pad;                     // 1024-aligned: the swizzle atoms' base
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row = (warp & 3) * 32 + lane;            // accumulator row (tensor-memory lane)
-  const int jbase = (warp >> 2) * HALF;              // first accumulator column of this thread
-  const uint32_t bar_ld = s0 + G::oBar, bar_mma = s0 + G::oBar + 8;
+  const int jbase = (warp >> 2) * CPW;               // first accumulator column of this thread
+  const uint32_t bar_ld = s0 + G::oBar, bar_mma = s0 + G::oBar + 8, bar_in = s0 + G::oBar + 16;
   if (tid == 0) {
     mbar_init(bar_ld, 1);
     mbar_init(bar_mma, 1);
+    mbar_init(bar_in, 1);
     mbar_init_fence();
   }
   if (warp == 0) tmem_alloc(s0 + G::oTm, kSpecTmemCols);
@@ -259,48 +325,77 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
                                        : bg + col * int64_t(G::N0));
   }
   spec_pdl_wait();                                   // the right-hand sides and outputs are shared
-  // L: right-hand sides of the tile (row r = c NB + y, K index x), split, as the K-major A of G1;
+  // the tile's right-hand sides into the staging columns: aligned middles by bulk copy, the
+  // at most three values before and after them by threads 8c .. 8c + 7
+  StageSpan span[G::CPT];
+#pragma unroll
+  for (int c = 0; c < G::CPT; ++c)
+    span[c] = bcol[c] != nullptr ? stage_span(bcol[c], G::N0) : StageSpan{0u, 0, 0};
+  if (tid == 0) {
+    uint32_t tx = 0;
+#pragma unroll
+    for (int c = 0; c < G::CPT; ++c) tx += uint32_t(span[c].i_hi - span[c].i_lo) * 4u;
+    mbar_expect_tx(bar_in, tx);
+#pragma unroll
+    for (int c = 0; c < G::CPT; ++c)
+      if (span[c].i_hi > span[c].i_lo)
+        bulk_g2s(s0 + G::oStg + c * G::STG + span[c].off + 4u * span[c].i_lo, bcol[c] + span[c].i_lo,
+                 uint32_t(span[c].i_hi - span[c].i_lo) * 4u, bar_in);
+  }
+#pragma unroll
+  for (int c = 0; c < G::CPT; ++c) {
+    const int j = tid - 8 * c;
+    if (j >= 0 && j < 8 && bcol[c] != nullptr) {
+      const int i = j < 4 ? j : span[c].i_hi + (j - 4);
+      if (j < 4 ? i < span[c].i_lo : i < G::N0)
+        *reinterpret_cast<float*>(spec_raw + pad + G::oStg + c * G::STG + span[c].off + 4 * i) = bcol[c][i];
+    }
+  }
+  // while the right-hand sides arrive: this thread's part of the table 1 / lambda_(mu, nu) (row
+  // mu = row mod NB, columns jbase ..) into tensor-memory columns 128 + nu, for the scaling step
+  bool ok = mbar_wait(bar_ld, 0);
+  if (ok) {
+    const float* tt = reinterpret_cast<const float*>(sm + G::oT);
+    const float tm = tt[row % NB];
+    const float ar = fmaf(l1, tm, l0), br = fmaf(l2, tm, l1);
+#pragma unroll
+    for (int j0 = 0; j0 < CPW; j0 += 16) {
+      float w[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) w[i] = __fdividef(1.0f, fmaf(br, tt[jbase + j0 + i], ar));
+      tmem_st16(tmem + (uint32_t((warp & 3) * 32) << 16) + uint32_t(128 + jbase + j0), w);
+    }
+  }
+  ok = mbar_wait(bar_in, 0) && ok;
+  ok = __syncthreads_and(ok) != 0;
+  // L: the staged right-hand sides (row r = c NB + y, K index x), split, as the K-major A of G1;
   // the padding row y = N1, column x = N1 and absent columns are zero.  A warp takes rows
-  // warp, warp + NW, ...; lane l the pairs x = 2 l (+ 64): four rows' loads are in flight at once.
-  {
+  // warp, warp + NW, ...; lane l the pairs x = 2 l (+ 64).
+  if (ok) {
     constexpr int PPL = NB / 64;                     // pairs per lane and row
-    constexpr int RB = 4;                            // rows per batch
-#pragma unroll 1
-    for (int r0 = warp; r0 < 128; r0 += NW * RB) {
-      float va[RB][PPL], vb[RB][PPL];
+#pragma unroll 2
+    for (int r = warp; r < 128; r += NW) {
+      const int c = r / NB, y = r - c * NB;
+      bool live = y < G::N1;
+      uint32_t soff = 0;
 #pragma unroll
-      for (int u = 0; u < RB; ++u) {
-        const int r = r0 + u * NW;
-        const int c = r / NB, y = r - c * NB;
-        const float* bc = bcol[0];
+      for (int i = 0; i < G::CPT; ++i)
+        if (c == i) { live = live && bcol[i] != nullptr; soff = G::oStg + i * G::STG + span[i].off; }
+      const float* sc = reinterpret_cast<const float*>(sm + soff) + y * G::N1;
 #pragma unroll
-        for (int i = 1; i < G::CPT; ++i)
-          if (c == i) bc = bcol[i];
-        const bool live = bc != nullptr && y < G::N1;
-#pragma unroll
-        for (int h = 0; h < PPL; ++h) {
-          const int k = 2 * (lane + 32 * h);
-          va[u][h] = live ? bc[y * G::N1 + k] : 0.f;
-          vb[u][h] = live && k + 1 < G::N1 ? bc[y * G::N1 + k + 1] : 0.f;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < RB; ++u) {
-        const int r = r0 + u * NW;
-#pragma unroll
-        for (int h = 0; h < PPL; ++h) {
-          uint32_t hi, lo;
-          split2(va[u][h], vb[u][h], hi, lo);
-          const int o = off_kmajor(128, r, 2 * (lane + 32 * h));
-          sts32(s0 + G::oDh + o, hi);
-          sts32(s0 + G::oDl + o, lo);
-        }
+      for (int h = 0; h < PPL; ++h) {
+        const int k = 2 * (lane + 32 * h);
+        const float va = live ? sc[k] : 0.f;
+        const float vb = live && k + 1 < G::N1 ? sc[k + 1] : 0.f;
+        uint32_t hi, lo;
+        split2(va, vb, hi, lo);
+        const int o = off_kmajor(128, r, k);
+        sts32(s0 + G::oDh + o, hi);
+        sts32(s0 + G::oDl + o, lo);
       }
     }
   }
   fence_async_smem();
-  bool ok = mbar_wait(bar_ld, 0);
-  ok = __syncthreads_and(ok) != 0;
 
   constexpr uint32_t idK = idesc_bf16(128, NB, false), idMN = idesc_bf16(128, NB, true);
   const auto stepA = [](int s) { return uint32_t((s >> 2) * (16 * 1024) + (s & 3) * 32); };    // K-major, 128 rows
@@ -329,26 +424,22 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
   // this thread's half of accumulator row `row` -> split operand: MN-major B (K row `row`)
   // or K-major A (row `row`), scaled by Lambda^{-1} when `scale`
   auto store_row = [&](bool mn, bool scale) {
-    const float* tt = reinterpret_cast<const float*>(sm + G::oT);
-    const float tm = tt[row % NB];
-    const float ar = fmaf(l1, tm, l0), br = fmaf(l2, tm, l1);
-#pragma unroll 1
-    for (int j0 = jbase; j0 < jbase + HALF; j0 += 32) {
-      float v[32];
-      tmem_ld32(trow + uint32_t(j0), v);
-      if (scale) {
+    float v[CPW];
+    tmem_ld<CPW>(trow + uint32_t(jbase), v);
+    if (scale) {
+      float w[CPW];
+      tmem_ld<CPW>(trow + uint32_t(128 + jbase), w);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = __fdividef(v[i], fmaf(br, tt[j0 + i], ar));
-      }
+      for (int i = 0; i < CPW; ++i) v[i] *= w[i];
+    }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        uint32_t h[4], l[4];
+    for (int q = 0; q < CPW / 8; ++q) {
+      uint32_t h[4], l[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) split2(v[8 * q + 2 * i], v[8 * q + 2 * i + 1], h[i], l[i]);
-        const int o = mn ? off_mnmajor(G::SBO_MN, row, j0 + 8 * q) : off_kmajor(128, row, j0 + 8 * q);
-        sts128(s0 + G::oDh + o, h[0], h[1], h[2], h[3]);
-        sts128(s0 + G::oDl + o, l[0], l[1], l[2], l[3]);
-      }
+      for (int i = 0; i < 4; ++i) split2(v[8 * q + 2 * i], v[8 * q + 2 * i + 1], h[i], l[i]);
+      const int o = mn ? off_mnmajor(G::SBO_MN, row, jbase + 8 * q) : off_kmajor(128, row, jbase + 8 * q);
+      sts128(s0 + G::oDh + o, h[0], h[1], h[2], h[3]);
+      sts128(s0 + G::oDl + o, l[0], l[1], l[2], l[3]);
     }
     tc_fence_before();
     fence_async_smem();
@@ -364,55 +455,62 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
   if (ok) ok = product(true);                        // G4: D4 = S D3, the solution
   spec_pdl_trigger();                                // only the write of the solution remains
   if (ok) {
-    // stage accumulator row `row` in float32 (16-byte chunks XOR-ed with the row), then write
-    // each grid row coalesced: a warp per row, lanes along x
-#pragma unroll 1
-    for (int j0 = jbase; j0 < jbase + HALF; j0 += 32) {
-      float v[32];
-      tmem_ld32(trow + uint32_t(j0), v);
+    // the solution rows into the staging columns in the global layout of each output column
+    // (value i = y N1 + x at off + 4 i; rows of a warp are N1 words apart: no bank conflicts),
+    // then bulk stores (or bulk float32 adds) of the aligned middles, the rest by threads
+    const bool acc_on = acc != nullptr && cols.acc_add;
+    float* gcol[G::CPT];
+    StageSpan ospan[G::CPT];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int o = row * NB * 4 + ((((j0 >> 2) + q) ^ (row & 7)) << 4);
-        sts128(s0 + G::oDh + o, __float_as_uint(v[4 * q]), __float_as_uint(v[4 * q + 1]),
-               __float_as_uint(v[4 * q + 2]), __float_as_uint(v[4 * q + 3]));
+    for (int c = 0; c < G::CPT; ++c) {
+      const int64_t col = col0 + c;
+      gcol[c] = col >= B ? nullptr
+                         : (acc != nullptr ? acc + (col / acc_L) * acc_ss + (acc_col0 + col % acc_L) * int64_t(G::N0)
+                                           : xg + col * int64_t(G::N0));
+      ospan[c] = gcol[c] != nullptr ? stage_span(gcol[c], G::N0) : StageSpan{0u, 0, 0};
+    }
+    {
+      const int c = row / NB, y = row - c * NB;
+      bool live = y < G::N1;
+      uint32_t soff = 0;
+#pragma unroll
+      for (int i = 0; i < G::CPT; ++i)
+        if (c == i) { live = live && gcol[i] != nullptr; soff = G::oStg + i * G::STG + ospan[i].off; }
+      float* so = reinterpret_cast<float*>(spec_raw + pad + soff) + y * G::N1;
+      float v[CPW];
+      tmem_ld<CPW>(trow + uint32_t(jbase), v);
+      if (live) {
+#pragma unroll
+        for (int i = 0; i < CPW; ++i)
+          if (jbase + i < G::N1) so[jbase + i] = v[i];
       }
     }
     tc_fence_before();
+    fence_async_smem();
     __syncthreads();
-    const bool acc_on = acc != nullptr && cols.acc_add;
-    constexpr int XPL = (G::N1 + 31) / 32;           // grid columns per lane
-    constexpr int RB = 4;
-#pragma unroll 1
-    for (int r0 = warp; r0 < 128; r0 += NW * RB) {
-      float* go[RB];
-      float val[RB][XPL], old[RB][XPL];
+    if (tid == 0) {
 #pragma unroll
-      for (int u = 0; u < RB; ++u) {
-        const int r = r0 + u * NW;
-        const int c = r / NB, y = r - c * NB;
-        const int64_t col = col0 + c;
-        go[u] = nullptr;
-        if (col < B && y < G::N1)
-          go[u] = (acc != nullptr ? acc + (col / acc_L) * acc_ss + (acc_col0 + col % acc_L) * int64_t(G::N0)
-                                  : xg + col * int64_t(G::N0)) + y * G::N1;
-#pragma unroll
-        for (int h = 0; h < XPL; ++h) {
-          const int x = lane + 32 * h;
-          val[u][h] = *reinterpret_cast<const float*>(sm + G::oDh + r * NB * 4 + (((x >> 2) ^ (r & 7)) << 4) +
-                                                      (x & 3) * 4);
-          old[u][h] = acc_on && go[u] != nullptr && x < G::N1 ? go[u][x] : 0.f;
-        }
+      for (int c = 0; c < G::CPT; ++c) {
+        if (gcol[c] == nullptr || ospan[c].i_hi <= ospan[c].i_lo) continue;
+        const uint32_t src = s0 + G::oStg + c * G::STG + ospan[c].off + 4u * ospan[c].i_lo;
+        const uint32_t bytes = uint32_t(ospan[c].i_hi - ospan[c].i_lo) * 4u;
+        if (acc_on) bulk_s2g_add(gcol[c] + ospan[c].i_lo, src, bytes);
+        else bulk_s2g(gcol[c] + ospan[c].i_lo, src, bytes);
       }
+      bulk_commit();
+    }
 #pragma unroll
-      for (int u = 0; u < RB; ++u) {
-        if (go[u] == nullptr) continue;
-#pragma unroll
-        for (int h = 0; h < XPL; ++h) {
-          const int x = lane + 32 * h;
-          if (x < G::N1) go[u][x] = acc_on ? old[u][h] + val[u][h] : val[u][h];
+    for (int c = 0; c < G::CPT; ++c) {
+      const int j = tid - 8 * c;
+      if (j >= 0 && j < 8 && gcol[c] != nullptr) {
+        const int i = j < 4 ? j : ospan[c].i_hi + (j - 4);
+        if (j < 4 ? i < ospan[c].i_lo : i < G::N0) {
+          const float v = *reinterpret_cast<const float*>(sm + G::oStg + c * G::STG + ospan[c].off + 4 * i);
+          gcol[c][i] = acc_on ? gcol[c][i] + v : v;
         }
       }
     }
+    if (tid == 0) bulk_wait_all();                   // the bulk writes are complete
   } else {
     if (tid == 0) atomicExch(&g_spec_err, 1);
     tc_fence_before();
