@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip fp64/e2e/profile/matvec legs")
     ap.add_argument("--sequential", action="store_true", help="solve the batch one problem at a time")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in SG kernel choice")
+    ap.add_argument("--mean-solve", choices=["exact", "vcycle"], default="exact",
+                    help="mean solves of the mixed-precision preconditioner: exact (fast diagonalisation on "
+                         "the tensor cores) or one V-cycle; float64 solves always use the V-cycle")
     ap.add_argument("--serve", action="store_true",
                     help="serving stream: the first --requests seeded requests through the server")
     ap.add_argument("--requests", type=int, default=2000, help="serving stream length with --serve")
@@ -75,6 +78,12 @@ SG_KERNEL_NAMES = {0: "one-phase", 1: "quad-32", 2: "quad-16", 3: "two-phase", 4
 # DRAM bytes of vcycle_t_kernel<float, 127, 2> (the current kernel) on 56 columns of the 128x128
 # workload, from one ncu capture: 3,681,280 B read + 0 B written
 VCYCLE_DRAM_BYTES_PER_COLUMN = 3681280 / 56
+# DRAM bytes of spectral_mean_kernel<128> (the exact mean solve) on 56 columns of the 128x128
+# workload, from one ncu capture: 3,744,768 B read + 0 B written
+MEAN_EXACT_DRAM_BYTES_PER_COLUMN = 3744768 / 56
+# tensor work of one tile (one 128 x 128 column) of the exact mean solve: 3 bf16 products for each of
+# the four 128 x 128 x 128 products with the sine transform, 2 flop per MAC
+MEAN_EXACT_FLOP_PER_TILE = 3 * 2 * 2 * 128 * 128 * (128 + 128)
 # float32 non-tensor peak: 152 SMs x 128 FMA/clk x 2 flop x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -163,14 +172,15 @@ def blas_threads():
     return host_cores()
 
 
-def oracle_full_solve(beta):
+def oracle_full_solve(beta, mode="vcycle"):
     """One complete float64 oracle solve of the 128x128 workload (set-up, right-hand side,
-    preconditioner construction and preconditioned MINRES to the 1e-8 rule); returns
-    (seconds, iterations, true relative residual)."""
+    preconditioner construction and preconditioned MINRES to the 1e-8 rule) with the mean solves
+    of `mode` (one V-cycle, or exact: the oracle's sparse LU); returns (seconds, iterations,
+    true relative residual)."""
     import sg_inputs as si
     from oracle.solve import solve
     t0 = time.perf_counter()
-    res = solve(si.steady_128(beta))
+    res = solve(si.steady_128(beta), mode=mode)
     return time.perf_counter() - t0, res.iterations, res.rel_true
 
 
@@ -188,12 +198,19 @@ def oracle_iterations():
     return out
 
 
-def cpu_baseline_full(beta=1e-2):
-    sec, its, rel = oracle_full_solve(beta)
+def oracle_mode(args):
+    """The oracle's mean-solve mode matching the GPU arm: exact (sparse LU) when the mixed path
+    uses the exact mean solves, else one V-cycle."""
+    return "exact" if args.precision == "mixed" and args.mean_solve == "exact" else "vcycle"
+
+
+def cpu_baseline_full(beta=1e-2, mode="vcycle"):
+    sec, its, rel = oracle_full_solve(beta, mode)
     return {"value": 1.0 / sec, "unit": UNIT, "cores": host_cores(), "blas_threads": blas_threads(),
             "kind": "oracle",
             "sample": f"one complete oracle solve of the 128x128 workload at beta={beta:g} ({its} MINRES "
-                      f"iterations, true residual {rel:.2e}) in {sec:.1f} s, set-up included"}
+                      f"iterations, true residual {rel:.2e}, mean solves: {mode}) in {sec:.1f} s, "
+                      f"set-up included"}
 
 
 class OracleStream:
@@ -203,9 +220,10 @@ class OracleStream:
     number of Krylov iterations at a time and times exactly that work (the set-up of a new
     solve falls into the step that first needs it)."""
 
-    def __init__(self, betas):
+    def __init__(self, betas, mode="vcycle"):
         import threading
         self.betas = betas
+        self.mode = mode
         self.sem = threading.Semaphore(0)
         self.cv = threading.Condition()
         self.products = 0
@@ -229,7 +247,7 @@ class OracleStream:
                 t0 = time.perf_counter()
                 pr = si.steady_128(beta)
                 d = SGData(pr)
-                Pc = BlockPreconditioner(d)
+                Pc = BlockPreconditioner(d, mode=self.mode)
                 b = d.rhs()
 
                 def apply_A(v, d=d):
@@ -279,7 +297,7 @@ def run_reference(args):
     # each timed step advances the running oracle solve by `chunk` KKT products (one per MINRES
     # iteration, one per true-residual check); the timed steps cover at least one whole solve
     chunk = max(1, math.ceil((mean_its + 2) / max(args.steps, 1)))
-    stream = OracleStream((1e-2, 1e-4, 1e-6))
+    stream = OracleStream((1e-2, 1e-4, 1e-6), oracle_mode(args))
     for _ in range(args.warmup):
         stream.advance(1)
     p0 = stream.products
@@ -305,7 +323,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "solves_per_step": solves / args.steps,
-                   "step": f"{chunk} KKT products of the running oracle solve"},
+                   "step": f"{chunk} KKT products of the running oracle solve",
+                   "mean_solves": oracle_mode(args)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "blas_threads": blas_threads(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -329,7 +348,8 @@ def run_ours(args):
 
     betas = si.STEADY_128_BETAS
     problems = [si.steady_128(b) for b in betas]
-    sps = [SGProblem.from_problem(pr, precision=args.precision).upload() for pr in problems]
+    mean_solve = args.mean_solve if args.precision == "mixed" else "vcycle"
+    sps = [SGProblem.from_problem(pr, precision=args.precision, mean_solve=mean_solve).upload() for pr in problems]
     for sp in sps:
         sp.workspace()
     # SG kernel per launch shape (process-wide; the three problems share their shapes); untimed
@@ -405,6 +425,8 @@ def run_ours(args):
                                  if args.precision == "mixed" else "float64"),
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}",
                    "batching": "sequential" if args.sequential else "3 concurrent solves (sgoc_solve_batch, 3 streams)",
+                   "mean_solves": ("exact: fast diagonalisation, tcgen05 tensor cores" if mean_solve == "exact"
+                                   else "one V(2,2) multigrid cycle"),
                    "sg_kernels": "built-in choice" if sg_kernels is None else
                    dict(zip(["kkt", "operator"] + [f"hgs_level{d}" for d in range((len(sg_kernels) - 2) // 2)] +
                             [f"hgs_level{d}_first" for d in range((len(sg_kernels) - 2) // 2)],
@@ -469,7 +491,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for pr, hx in zip(problems, pin):
-                sp = SGProblem.from_problem(pr, precision=args.precision).upload()
+                sp = SGProblem.from_problem(pr, precision=args.precision, mean_solve=mean_solve).upload()
                 x, _ = sp.solve()
                 hx.copy_(x, non_blocking=True)
                 if rep == 0:
@@ -493,7 +515,17 @@ def run_ours(args):
         dom = max(kinds, key=lambda k: kinds[k]["ms"])
         dv = kinds[dom]
         esize_fp64 = args.precision == "fp64"
-        if esize_fp64 and dom in ("sg_operator", "mg_vcycle_fused", "mg_smooth"):
+        if dom == "mean_exact":
+            peaks = load_peaks()[2]
+            tpk = peaks.get("bf16_tflops_sustained", 1700.0)
+            ach = dv["flops"] / (dv["ms"] / 1e3) / 1e12
+            roof = {"bound": "tensor", "achieved": ach, "peak": tpk, "unit": "TFLOP/s", "frac": ach / tpk,
+                    "traffic": None, "kernel": dom,
+                    "peak_source": ("measured (MEASURED_PEAKS.json bf16_tflops_sustained: cuBLAS bf16, the "
+                                    "kernel is timed inside a long step)" if "bf16_tflops_sustained" in peaks
+                                    else "fallback 1.7 PFLOP/s sustained"),
+                    "flops_note": "bf16 tensor flops executed: three bf16 products per float32-accurate product"}
+        elif esize_fp64 and dom in ("sg_operator", "mg_vcycle_fused", "mg_smooth"):
             ach = dv["flops"] / (dv["ms"] / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "kernel": dom,
@@ -511,6 +543,10 @@ def run_ours(args):
             # b and reads + writes the output: 3 x 4 B per node)
             cols = dv["bytes"] / dv["launches"] / (3 * 4 * pr_main.n)
             roof["traffic"] = VCYCLE_DRAM_BYTES_PER_COLUMN * cols
+            roof["traffic_note"] = f"ncu DRAM bytes per column x {cols:.1f} columns per launch"
+        if dom == "mean_exact" and pr_main.nx == 128 and MEAN_EXACT_DRAM_BYTES_PER_COLUMN:
+            cols = dv["flops"] / dv["launches"] / MEAN_EXACT_FLOP_PER_TILE       # one column per tile
+            roof["traffic"] = MEAN_EXACT_DRAM_BYTES_PER_COLUMN * cols
             roof["traffic_note"] = f"ncu DRAM bytes per column x {cols:.1f} columns per launch"
         line["roofline"] = roof
         line["kernel_breakdown_note"] = ("summed device time per kernel class of an eager sequential pass of "
@@ -573,8 +609,10 @@ def run_ours(args):
             pr = mk()
             rec = {"kkt_unknowns": pr.kkt_size}
             xkeep = {}
-            for prec in ("mixed", "fp64"):
-                sp = SGProblem.from_problem(pr, precision=prec).upload()
+            variants = ["mixed", "fp64"] + (["mixed_exact_mean"] if pr.nx in (64, 128) else [])
+            for prec in variants:
+                sp = SGProblem.from_problem(pr, precision="mixed" if prec == "mixed_exact_mean" else prec,
+                                            mean_solve="exact" if prec == "mixed_exact_mean" else "vcycle").upload()
                 if not args.no_autotune:
                     sp.autotune()
                 x, _ = sp.solve()
@@ -602,7 +640,7 @@ def run_ours(args):
         line["serving"] = serve_leg(args.serve_requests)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_full(1e-2)
+        line["cpu_baseline"] = cpu_baseline_full(1e-2, oracle_mode(args))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -623,7 +661,7 @@ def run_kernel_case(args):
         # (per-kernel timing on) so that a profiler sees ordinary launches, not graph nodes
         from paper_2512_23804_gb300 import abi
         abi.profile_enable(True)
-        sq = SGProblem.from_problem(pr, precision="mixed", tol=1e-2).upload()
+        sq = SGProblem.from_problem(pr, precision="mixed", tol=1e-2, mean_solve=args.mean_solve).upload()
         for _ in range(2):
             sq.solve()
         abi.profile_enable(False)
