@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=2000, help="serving stream length with --serve")
     ap.add_argument("--serve-requests", type=int, default=100,
                     help="serving leg of the default run: the first N requests of the stream (0: skip)")
-    ap.add_argument("--kernel-case", choices=["vcycle128", "mean128", "sg128", "sg512", "hgs128", "solve128"],
+    ap.add_argument("--kernel-case", choices=["vcycle128", "mean128", "sg128", "sg512", "sgr128", "sgr64t", "hgs128",
+                                              "solve128"],
                     default=None,
                     help="run one kernel class a few times on a small case (for ncu captures) and exit")
     return ap.parse_args()
@@ -654,7 +655,7 @@ def run_kernel_case(args):
     from paper_2512_23804_gb300 import SGProblem, build
     build.build()
     case = args.kernel_case
-    pr = si.steady_512() if case == "sg512" else si.steady_128(1e-4)
+    pr = si.steady_512() if case == "sg512" else (si.time_64() if case == "sgr64t" else si.steady_128(1e-4))
     sp = SGProblem.from_problem(pr, precision="mixed", mean_solve="exact" if case == "mean128" else "vcycle").upload()
     if case == "solve128":
         # a few MINRES iterations of the 128x128 workload (loose tolerance), launched eagerly
@@ -670,6 +671,11 @@ def run_kernel_case(args):
         Y = torch.empty_like(X)
         for _ in range(3):
             sp.apply_operator(X, out=Y)
+    elif case in ("sgr128", "sgr64t"):                 # the register SG kernel (variant 7)
+        X = torch.randn(sp.n * sp.P * sp.slabs, dtype=torch.float32, device="cuda")
+        Y = torch.empty_like(X)
+        for _ in range(3):
+            sp.apply_operator_variant(X, 7, nslabs=sp.slabs, out=Y)
     elif case in ("vcycle128", "mean128"):
         ncols = 56                                  # the largest chaos level of M=6, p=3
         R = torch.randn(ncols * sp.n, dtype=torch.float32, device="cuda")

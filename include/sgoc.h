@@ -252,8 +252,9 @@ sgoc_status sgoc_server_stats(const sgoc_server* sv, int64_t* admitted, int64_t*
  *
  * Kernel choice for the SG operator products of a solve.  The library has
  * several kernels for Y = sum_k K_k X G_k (Sec. 2, Eq. (gPC-A) in Kronecker
- * form) that form the same products and sums in the same order, so they give
- * bitwise identical results and differ only in speed.  sgoc_autotune times each
+ * form); kernels 0-6 form the same products and sums in the same order, so they
+ * give bitwise identical results and differ only in speed (kernel 7 agrees with
+ * them to rounding; a given table of choices is deterministic).  sgoc_autotune times each
  * applicable kernel on every SG launch shape a solve of `pb` uses (the KKT
  * product, the operator alone, the right-hand side of the return visit of each
  * hGS level of Alg. 1 (d = 0..p), the right-hand side of the first visit of each
@@ -269,11 +270,15 @@ sgoc_status sgoc_server_stats(const sgoc_server* sv, int64_t* admitted, int64_t*
  * four-node kernels built for four instead of two CTAs per SM, 6 the direct
  * kernel: a thread per node and output column, for shapes with few outputs and
  * couplings, and the only kernel for shapes whose input columns do not fit any
- * staged kernel's shared memory, e.g. float64 with P = 495).  Synchronizes
- * the stream.  The paper has no counterpart: it concerns this GPU code only. */
+ * staged kernel's shared memory, e.g. float64 with P = 495; 7 the register kernel:
+ * float32, Legendre chaos of the (M, p) it is compiled for ((1,1), (2,2), (3,2),
+ * (3,3), (4,3)), a thread per node with every output column's sum in
+ * registers; it sums a column's coupling terms in another order than 0-6 and
+ * agrees with them to rounding).  Synchronizes the stream.  The paper has no
+ * counterpart: it concerns this GPU code only. */
 sgoc_status sgoc_autotune(sgoc_problem* pb, void* d_ws, size_t ws_bytes, int32_t* chosen,
                           int32_t nchosen, void* stream);
-/* Pins kernel `variant` (0..6 as above; -1 clears the entry, restoring the
+/* Pins kernel `variant` (0..7 as above; -1 clears the entry, restoring the
  * built-in rule) for SG launch shape `shape` of a solve of pb (0 the KKT product,
  * 1 the operator alone, 2 + d the return visit of hGS level d, 3 + p + d the
  * first visit of level d) in precision 0
@@ -288,7 +293,7 @@ sgoc_status sgoc_set_kernel(sgoc_problem* pb, int32_t precision, int32_t shape, 
  * 1: float32.  X and Y must not overlap. */
 sgoc_status sgoc_apply_operator(sgoc_problem* pb, int32_t precision, const void* d_X,
                                 void* d_Y, int32_t nslabs, void* stream);
-/* The same product with one given kernel variant (0..6 as listed for
+/* The same product with one given kernel variant (0..7 as listed for
  * sgoc_autotune); SGOC_ERR_UNSUPPORTED when that kernel does not apply to this
  * shape or precision.  For tests of the variants against each other. */
 sgoc_status sgoc_apply_operator_variant(sgoc_problem* pb, int32_t precision, int32_t variant,

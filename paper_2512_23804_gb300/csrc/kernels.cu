@@ -6,6 +6,7 @@
 // south-west corner of (ix+1, iy+1) and the south-east corner of (ix, iy+1).
 #include <cooperative_groups.h>
 #include <type_traits>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -956,6 +957,264 @@ static cudaError_t launch_sgd(const SGArgs<T>& a, cudaStream_t st, const SGMulti
 }
 
 // ---------------------------------------------------------------------------
+// SG apply, register form (variant 7; float32, Legendre chaos of a compiled (M, p)).
+// One thread per node keeps the coupling sum of every chaos column in registers and
+// reads each input column once: from the 3 x 3 neighbourhood of X(alpha) (a 32 x 4
+// node tile with its halo, staged in shared memory) it forms the element terms
+// T_e(alpha), the diagonal term sum_e kappa_0(e) T_e(alpha) and the mass stencil when
+// alpha is an output column (kept in shared memory for the epilogue), and for every
+// kept k the product U_k(alpha) = sum_e kappa_k(e) T_e(alpha), added with its
+// coefficient to the outputs alpha + e_k and alpha - e_k.  The multi-indices and
+// their neighbours are a compile-time table, so every register index is a constant.
+// The products and the epilogue are those of the other variants; a column's coupling
+// terms arrive in increasing alpha rather than increasing k (agreement to rounding).
+// ---------------------------------------------------------------------------
+constexpr int binom_c(int n, int k) {
+  if (k < 0 || k > n) return 0;
+  long long r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+  return int(r);
+}
+// compositions of s into `parts` nonnegative parts
+constexpr int ncomp_c(int s, int parts) { return parts == 0 ? (s == 0 ? 1 : 0) : binom_c(s + parts - 1, parts - 1); }
+
+// graded multi-indices of total degree <= PD, lexicographically descending within a degree
+// (the order of the problem set-up, checked against it at launch), and their neighbours
+template <int M, int PD>
+struct LegChaos {
+  static constexpr int P = binom_c(M + PD, PD);
+  int idx[P][M];
+  int up[P][M];    // index of alpha + e_k, -1 beyond degree PD
+  int dn[P][M];    // index of alpha - e_k, -1 when alpha_k = 0
+  static constexpr int index_of(const int (&b)[M]) {
+    int deg = 0;
+    for (int j = 0; j < M; ++j) deg += b[j];
+    int r = binom_c(M + deg - 1, M);          // multi-indices of lower degree
+    int rem = deg;
+    for (int i = 0; i + 1 < M; ++i) {         // lexicographically greater ones of this degree
+      for (int v = b[i] + 1; v <= rem; ++v) r += ncomp_c(rem - v, M - i - 1);
+      rem -= b[i];
+    }
+    return r;
+  }
+  constexpr LegChaos() : idx(), up(), dn() {
+    int a[M] = {};
+    int pos = 0;
+    for (int deg = 0; deg <= PD; ++deg) {
+      for (int j = 0; j < M; ++j) a[j] = 0;
+      a[0] = deg;
+      while (true) {
+        for (int j = 0; j < M; ++j) idx[pos][j] = a[j];
+        ++pos;
+        int i = M - 2;                        // next smaller composition of deg
+        while (i >= 0 && a[i] == 0) --i;
+        if (i < 0) break;
+        int tail = 0;
+        for (int j = i + 1; j < M; ++j) { tail += a[j]; a[j] = 0; }
+        a[i] -= 1;
+        a[i + 1] = tail + 1;
+      }
+    }
+    for (int q = 0; q < P; ++q) {
+      int deg = 0;
+      for (int j = 0; j < M; ++j) deg += idx[q][j];
+      for (int k = 0; k < M; ++k) {
+        int b[M] = {};
+        for (int j = 0; j < M; ++j) b[j] = idx[q][j];
+        b[k] += 1;
+        up[q][k] = deg < PD ? index_of(b) : -1;
+        b[k] -= 2;
+        dn[q][k] = idx[q][k] > 0 ? index_of(b) : -1;
+      }
+    }
+  }
+};
+template <int M, int PD>
+struct LegTab {
+  static constexpr LegChaos<M, PD> t{};
+};
+
+constexpr int kSGRTX = 32, kSGRTY = 4, kSGRThreads = kSGRTX * kSGRTY;
+
+template <int... Is, typename F>
+__device__ __forceinline__ void static_for(std::integer_sequence<int, Is...>, F&& f) {
+  (f(std::integral_constant<int, Is>{}), ...);
+}
+
+inline size_t sgr_smem(int nin, int nout, bool own, bool use_m) {
+  return sizeof(float) * (size_t(nin) * (kSGRTY + 2) * (kSGRTX + 2) +
+                          size_t(nout) * kSGRThreads * ((own ? 1 : 0) + (use_m ? 1 : 0)));
+}
+
+template <int M, int PD>
+__global__ void __launch_bounds__(kSGRThreads, 1) sgr_kernel(SGArgs<float> a, const SGMulti<float> mg) {
+  using Tab = LegTab<M, PD>;
+  constexpr int P = LegChaos<M, PD>::P;
+  constexpr int WX = kSGRTX + 2, WY = kSGRTY + 2, TS = WX * WY;
+  const int t = sg_member(a, mg);
+  extern __shared__ __align__(16) float sgr_smem_f[];
+  const int nin = a.in1 - a.in0, nout = a.out1 - a.out0;
+  const bool own = !a.no_own, use_m = a.cm != 0.0f;
+  float* Xs = sgr_smem_f;                                    // [nin][WY][WX]
+  float* Ds = Xs + size_t(nin) * TS;                         // [nout][threads] diagonal terms
+  float* Ms = Ds + (own ? size_t(nout) * kSGRThreads : 0);   // [nout][threads] mass terms
+  const int tx = threadIdx.x % kSGRTX, ty = threadIdx.x / kSGRTX;
+  const int ix0 = blockIdx.x * kSGRTX, iy0 = blockIdx.y * kSGRTY;
+  const int n1 = a.n1, ix = ix0 + tx, iy = iy0 + ty;
+  const bool live = ix < n1 && iy < n1;
+  // kappa_k(e)/6 of the node's four elements (SW, SE, NE, NW), clamped at the edge
+  float kk[M + 1][4];
+  {
+    const int cx = min(ix, n1 - 1), cy = min(iy, n1 - 1);
+#pragma unroll
+    for (int k = 0; k <= M; ++k)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int ex = cx + ((e == 1 || e == 2) ? 1 : 0), ey = cy + (e >= 2 ? 1 : 0);
+        kk[k][e] = a.kap[(int64_t(k) * a.nx + ey) * a.nx + ex];
+      }
+  }
+  pdl_wait();                                                // X (and Y, R) are written by earlier kernels
+  {
+    const float* X = a.X + int64_t(t) * a.xs + int64_t(a.in0) * a.n;
+    for (int q = threadIdx.x; q < nin * TS; q += kSGRThreads) {
+      const int c = q / TS, rr = q - c * TS, r = rr / WX, col = rr - r * WX;
+      const int gx = ix0 - 1 + col, gy = iy0 - 1 + r;
+      const bool ok = gx >= 0 && gx < n1 && gy >= 0 && gy < n1;
+      cp_async_elem(Xs + q, ok ? X + int64_t(c) * a.n + int64_t(gy) * n1 + gx : X, ok);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+  }
+  pdl_trigger();
+  float off[P];
+#pragma unroll
+  for (int b = 0; b < P; ++b) off[b] = 0.0f;
+  const float* win = Xs + ty * WX + tx;                      // this node's 3 x 3 window in column in0
+  const int o0 = a.out0, o1 = a.out1, kmax = a.kmax;
+  static_for(std::make_integer_sequence<int, P>{}, [&](auto ia) {
+    constexpr int A = decltype(ia)::value;
+    if (A < a.in0 || A >= a.in1) return;
+    const float* w = win + (A - a.in0) * TS;
+    const float SW = w[0], S = w[1], SE = w[2];
+    const float W = w[WX], C = w[WX + 1], E = w[WX + 2];
+    const float NW = w[2 * WX], N = w[2 * WX + 1], NE = w[2 * WX + 2];
+    const float c4 = 4.0f * C;
+    const float aS = c4 - S, aN = c4 - N;
+    const float t0 = fmaf(-2.0f, SW, aS - W), t1 = fmaf(-2.0f, SE, aS - E);
+    const float t2 = fmaf(-2.0f, NE, aN - E), t3 = fmaf(-2.0f, NW, aN - W);
+    if (own && A >= o0 && A < o1) {
+      Ds[(A - o0) * kSGRThreads + threadIdx.x] = fmaf(kk[0][3], t3, fmaf(kk[0][2], t2, fmaf(kk[0][1], t1, kk[0][0] * t0)));
+      if (use_m) {
+        const float edges = (N + S) + (E + W), corners = (NE + NW) + (SE + SW);
+        Ms[(A - o0) * kSGRThreads + threadIdx.x] = a.mass * fmaf(16.0f, C, fmaf(4.0f, edges, corners));
+      }
+    }
+    static_for(std::make_integer_sequence<int, M>{}, [&](auto ik) {
+      constexpr int K = decltype(ik)::value;               // KL index K + 1
+      constexpr int UP = Tab::t.up[A][K], DN = Tab::t.dn[A][K], AK = Tab::t.idx[A][K];
+      if (K + 1 >= kmax) return;
+      const bool up = UP >= 0 && UP >= o0 && UP < o1;
+      const bool dn = DN >= 0 && DN >= o0 && DN < o1;
+      if (!up && !dn) return;
+      const float u = fmaf(kk[K + 1][3], t3, fmaf(kk[K + 1][2], t2, fmaf(kk[K + 1][1], t1, kk[K + 1][0] * t0)));
+      if constexpr (UP >= 0) {
+        if (up) off[UP] = fmaf(a.cup[AK], u, off[UP]);
+      }
+      if constexpr (DN >= 0) {
+        if (dn) off[DN] = fmaf(a.cup[AK - 1], u, off[DN]);
+      }
+    });
+  });
+  if (!live) return;
+  const int64_t node = int64_t(iy) * n1 + ix;
+  static_for(std::make_integer_sequence<int, P>{}, [&](auto ib) {
+    constexpr int Bc = decltype(ib)::value;
+    if (Bc < o0 || Bc >= o1) return;
+    const float diag = own ? Ds[(Bc - o0) * kSGRThreads + threadIdx.x] : 0.0f;
+    float out = fmaf(a.c0, diag, a.c1 * off[Bc]);
+    if (use_m) out = fmaf(a.cm, Ms[(Bc - o0) * kSGRThreads + threadIdx.x], out);
+    if (a.R) out = fmaf(a.cr, a.R[int64_t(t) * a.rs + int64_t(Bc - a.rcol0) * a.n + node], out);
+    float* yp = a.Y + int64_t(t) * a.ys + int64_t(Bc - a.ycol0) * a.n + node;
+    if (a.cy != 0.0f) out = fmaf(a.cy, *yp, out);
+    *yp = out;
+  });
+}
+
+// the compiled (M, p) of the register kernel: the time-dependent workload's (4, 3), where it
+// is the fastest form of the full operator, and small shapes.  Not (6, 3): with one thread
+// per node a 128 x 128 grid gives about three warps per SM, which cannot hide the
+// instruction fetches of its fully unrolled code (ncu: 5.7 no_instruction stalls per
+// issue, 37.6 us against 19.1 us for the quad kernel)
+#define SGOC_SGR_SHAPES(X) X(1, 1) X(2, 2) X(3, 2) X(3, 3) X(4, 3)
+
+static bool sgr_compiled(int M, int p) {
+#define SGOC_SGR_CASE(m, q) if (M == m && p == q) return true;
+  SGOC_SGR_SHAPES(SGOC_SGR_CASE)
+#undef SGOC_SGR_CASE
+  return false;
+}
+
+// the multi-index order the register kernel was compiled with, for a check against the
+// problem's own (first `count` indices, row-major (count x M)); false when not compiled
+bool sgr_indices(int M, int p, std::vector<int>& out) {
+  out.clear();
+#define SGOC_SGR_IDX(m, q)                                                   \
+  if (M == m && p == q) {                                                    \
+    constexpr const LegChaos<m, q>& c = LegTab<m, q>::t;                     \
+    for (int i = 0; i < LegChaos<m, q>::P; ++i)                              \
+      for (int j = 0; j < m; ++j) out.push_back(c.idx[i][j]);                \
+    return true;                                                             \
+  }
+  SGOC_SGR_SHAPES(SGOC_SGR_IDX)
+#undef SGOC_SGR_IDX
+  return false;
+}
+
+template <typename T>
+static bool sgr_feasible(const SGArgs<T>& a) {
+  if constexpr (!std::is_same<T, float>::value) {
+    return false;
+  } else {
+    if (a.legendre_p < 0 || !sgr_compiled(a.M, a.legendre_p)) return false;
+    return sgr_smem(a.in1 - a.in0, a.out1 - a.out0, !a.no_own, a.cm != 0.0f) <= kMaxSmem;
+  }
+}
+
+template <int M, int PD>
+static cudaError_t launch_sgr_mp(const SGArgs<float>& a, cudaStream_t st, const SGMulti<float>& mg) {
+  const size_t smem = sgr_smem(a.in1 - a.in0, a.out1 - a.out0, !a.no_own, a.cm != 0.0f);
+  cudaError_t e = cudaFuncSetAttribute(sgr_kernel<M, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMaxSmem));
+  if (e != cudaSuccess) return e;
+  dim3 grid(unsigned((a.n1 + kSGRTX - 1) / kSGRTX), unsigned((a.n1 + kSGRTY - 1) / kSGRTY),
+            unsigned(a.nslabs * mg.ng));
+  return launch_pdl(sgr_kernel<M, PD>, grid, dim3(kSGRThreads), smem, st, a, mg);
+}
+
+template <typename T>
+static cudaError_t launch_sgr(const SGArgs<T>& a, cudaStream_t st, const SGMulti<T>& mg) {
+  if constexpr (!std::is_same<T, float>::value) {
+    return cudaErrorInvalidConfiguration;
+  } else {
+    const int nout = a.out1 - a.out0;
+    const double w = 4.0, cells = double(a.n) * a.nslabs * mg.ng;
+    const double bytes = w * cells * (double(a.in1 - a.in0) + nout * (1.0 + (a.R ? 1 : 0) + (a.cy != 0.0f ? 1 : 0))) +
+                         w * (a.M + 1.0) * a.nx * a.nx;
+    const double flops = cells * (15.0 * (a.in1 - a.in0) + 9.0 * nout + 9.0 * (a.c1 != 0.0f ? a.deg_sum : 0));
+    ProfScope ps(KK_SG, st, bytes, flops);
+    cudaError_t e = cudaErrorInvalidConfiguration;
+#define SGOC_SGR_LAUNCH(m, q) \
+    if (a.M == m && a.legendre_p == q) e = launch_sgr_mp<m, q>(a, st, mg);
+    SGOC_SGR_SHAPES(SGOC_SGR_LAUNCH)
+#undef SGOC_SGR_LAUNCH
+    if (e != cudaSuccess) return e;
+    note_launch();
+    return cudaGetLastError();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // SG kernel variants and the tuning cache.  All variants form the same products
 // and sums in the same order, so the choice changes timing only.
 //   0: one-phase kernel (tile by the heuristic), 1: quad kernel, 32-node tile,
@@ -1030,6 +1289,7 @@ bool sg_variant_feasible(const SGArgs<T>& a, int v) {
                                               // also the only form when no staged form fits
       return double(a.out1 - a.out0) + (a.c1 != T(0) ? a.deg_sum : 0.0) <= kSGDirectMaxTerms ||
              !sg_one_phase_fits(a);
+    case 7: return sgr_feasible(a);
     default: return false;
   }
 }
@@ -1055,6 +1315,7 @@ cudaError_t launch_sg_variant(const SGArgs<T>& a, int v, cudaStream_t st, const 
     case 4: return launch_sg4_tx<T, 32, 4>(a, sg4_smem<T, 32>(a), st, mg);
     case 5: return launch_sg4_tx<T, 16, 4>(a, sg4_smem<T, 16>(a), st, mg);
     case 6: return launch_sgd<T>(a, st, mg);
+    case 7: return launch_sgr<T>(a, st, mg);
     case 3:
       if constexpr (std::is_same<T, float>::value) {
         cudaError_t e = cudaSuccess;

@@ -59,6 +59,11 @@ struct SGArgs {
   // 1: the outputs' own columns take no part (no kappa_0 or mass term, c0 and cm unused);
   // the output range then need not lie inside the input range
   int no_own;
+  // Legendre chaos of total degree p (the register kernel, variant 7, is compiled for a few
+  // (M, p)); -1 otherwise.  cup[j] = E[xi psi_j psi_(j+1)], the couplings of G_k by the k-th
+  // component j of the lower multi-index (equal to the table's float values).
+  int legendre_p = -1;
+  T cup[11];
 };
 template <typename T>
 cudaError_t launch_sg(const SGArgs<T>& a, cudaStream_t st);
@@ -79,8 +84,14 @@ cudaError_t launch_sg_group(const SGArgs<T>* a, int ng, cudaStream_t st);
 // SG kernel variants (0 one-phase, 1 quad 32-node tile, 2 quad 16-node tile,
 // 3 two-phase float32, 4 and 5 the quad tiles at four CTAs per SM, 6 direct:
 // a thread per node and output, feasible while outputs + couplings <=
-// kSGDirectMaxTerms) and the process-wide tuning cache keyed by launch shape.
-constexpr int kSGVariants = 7;
+// kSGDirectMaxTerms; 7 register form: float32 Legendre chaos of a compiled (M, p),
+// a thread per node with every output column's sum in registers) and the
+// process-wide tuning cache keyed by launch shape.  Variants 0-6 agree bit for bit;
+// 7 sums a column's coupling terms in another order and agrees with them to rounding.
+constexpr int kSGVariants = 8;
+// The multi-indices (count x M, row-major) the register SG kernel was compiled with for
+// (M, p); false when it is not compiled for them.
+bool sgr_indices(int M, int p, std::vector<int>& out);
 constexpr double kSGDirectMaxTerms = 256;
 template <typename T>
 cudaError_t launch_sg_variant(const SGArgs<T>& a, int variant, cudaStream_t st,

@@ -38,12 +38,6 @@ static double binom(int a, int b) {
   return r;
 }
 
-// E[xi psi_n psi_{n+1}] for orthonormal Legendre polynomials psi_n = sqrt(2n+1) P_n,
-// xi ~ U[-1,1], from the three-term recurrence xi P_n = ((n+1) P_{n+1} + n P_{n-1})/(2n+1).
-static double legendre_coupling(int n) {
-  return (n + 1) / std::sqrt((2.0 * n + 1.0) * (2.0 * n + 3.0));
-}
-
 // E[psi_a psi_b psi_c] for normalised Hermite polynomials psi_n = He_n / sqrt(n!), xi ~ N(0,1):
 // sqrt(a! b! c!) / ((s-a)! (s-b)! (s-c)!) for even a+b+c = 2s with s >= max(a, b, c), else 0.
 static double hermite_triple(int a, int b, int c) {
@@ -252,6 +246,12 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
   for (int deg = 0; deg <= p; ++deg) pb->off[deg + 1] = int(binom(M + deg, deg) + 0.5);
   if (M > 0 && int64_t(pb->idx.size()) != int64_t(pb->P) * M) {
     delete pb; set_error("internal: multi-index count"); return SGOC_ERR_INVALID_ARG;
+  }
+  // the register SG kernel's compiled multi-index order must be this one
+  {
+    std::vector<int> tab;
+    pb->sgr_ok = d->chaos == 0 && M > 0 && sgr_indices(M, p, tab) &&
+                 tab == std::vector<int>(pb->idx.begin(), pb->idx.end());
   }
   // neighbour table of G_k: beta couples to beta + e_k and beta - e_k
   std::map<std::vector<int32_t>, int> pos;

@@ -1,6 +1,8 @@
 // Internal definitions of the SG optimal-control solver library.
 #pragma once
 
+#include <cmath>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,6 +30,12 @@ void set_error(const std::string& msg);
     sgoc_status s_ = (expr);                \
     if (s_ != SGOC_OK) return s_;           \
   } while (0)
+
+// E[xi psi_n psi_{n+1}] for orthonormal Legendre polynomials psi_n = sqrt(2n+1) P_n,
+// xi ~ U[-1,1], from the three-term recurrence xi P_n = ((n+1) P_{n+1} + n P_{n-1})/(2n+1).
+inline double legendre_coupling(int n) {
+  return (n + 1) / std::sqrt((2.0 * n + 1.0) * (2.0 * n + 3.0));
+}
 
 // One level of the geometric hierarchy for the mean operator: a constant
 // 9-point stencil (centre, edge, corner) on an nx-element grid.
@@ -90,6 +98,7 @@ struct sgoc_problem {
   int chaos = 0;                     // 0 Legendre / affine, 1 Hermite / chaos-expanded coefficient
   int nterms = 1;                    // coefficient planes: M + 1, or C(M + 2p, 2p)
   int lev_dist = 1;                  // largest chaos-level distance of a kept coupling
+  bool sgr_ok = false;               // the register SG kernel is compiled for this (M, p) in this index order
   double length = 1.0;               // side of the square domain
   double beta = 0, gamma = 0, T = 1, tau = 1, kappa0 = 1, s = 0;  // s = sqrt((1+gamma)/beta)
   int n1 = 0, P = 0, slabs = 1;

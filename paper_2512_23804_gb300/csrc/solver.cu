@@ -243,6 +243,13 @@ static void set_utab(SGArgs<T>& g, const UTab& u) {
   g.u_nslots = u.nslots; g.u_nent = u.nent;
 }
 
+// the chaos degree and coupling values the register SG kernel takes (Legendre chaos only)
+template <typename T>
+static void set_legendre(SGArgs<T>& g, const sgoc_problem* pb) {
+  g.legendre_p = pb->sgr_ok && pb->p <= 10 ? pb->p : -1;
+  for (int j = 0; j < 11; ++j) g.cup[j] = T(j < pb->p ? legendre_coupling(j) : 0.0);
+}
+
 // SG launch of the hGS visit of level d: rhs of the level's columns (correction form)
 template <typename T>
 static SGArgs<T> hgs_args(const sgoc_problem* pb, PrecWS<T>& w, const T* R, T* V, int slabs, int d) {
@@ -270,6 +277,7 @@ static SGArgs<T> hgs_args(const sgoc_problem* pb, PrecWS<T>& w, const T* R, T* V
   g.deg_sum = deg_sum(pb, a0, a1, pb->r);
   g.nnz_out = pb->nbr_ptr[a1] - pb->nbr_ptr[a0];
   set_utab(g, pb->utabs[1 + d]);
+  set_legendre(g, pb);
   return g;
 }
 
@@ -459,6 +467,7 @@ static SGArgs<T> sg_full(const sgoc_problem* pb, const T* X, T* Y, T coef) {
   g.deg_sum = double(pb->nbr_alpha.size());
   g.nnz_out = int(pb->nbr_alpha.size());
   set_utab(g, pb->utabs[0]);
+  set_legendre(g, pb);
   return g;
 }
 

@@ -166,7 +166,7 @@ class SGProblem:
         abi.check(abi.load().sgoc_set_kernel(self._handle, prec, shape, variant), "sgoc_set_kernel")
 
     def apply_operator_variant(self, X, variant, nslabs=1, out=None, stream=None):
-        """The SG operator with a given kernel variant (0..6, see sgoc_autotune)."""
+        """The SG operator with a given kernel variant (0..7, see sgoc_autotune)."""
         import torch
         self.upload(stream)
         Y = out if out is not None else torch.empty_like(X)

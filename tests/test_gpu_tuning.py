@@ -1,9 +1,12 @@
 """SG kernel variants and the autotuner.
 
-Every SG kernel variant forms the same products and sums in the same order, so
-the variants must agree bit for bit and each must match the oracle within the
-operator tolerances (1e-13 float64, 2e-6 float32).  Tuning may change only the
-kernel choice: a solve after sgoc_autotune returns the identical solution.
+SG kernel variants 0-6 form the same products and sums in the same order, so they
+must agree bit for bit and each must match the oracle within the operator
+tolerances (1e-13 float64, 2e-6 float32); the register kernel 7 (float32, some
+Legendre (M, p)) sums coupling terms in another order and is checked against them
+and the oracle to rounding in test_gpu_sg_register.py.  Tuning changes only the
+kernel choice: a solve after sgoc_autotune returns the identical solution, or, when
+the tuner picked kernel 7 somewhere, the same solution to rounding.
 """
 import numpy as np
 import pytest
@@ -70,10 +73,15 @@ def test_autotune_keeps_the_solution(precision):
     x0 = x0.clone()
     chosen = sp.autotune()
     assert len(chosen) == 2 * pr.p + 4
-    assert all(0 <= v <= 6 for v in chosen)
+    assert all(0 <= v <= 7 for v in chosen)
     x1, i1 = sp.solve()
-    assert i1["iterations"] == i0["iterations"]
-    assert torch.equal(x1, x0)
+    if 7 in chosen:
+        assert abs(i1["iterations"] - i0["iterations"]) <= 2
+        assert i1["rel_true_residual"] <= 1e-8
+        assert float(torch.linalg.norm(x1 - x0) / torch.linalg.norm(x0)) <= 1e-7
+    else:
+        assert i1["iterations"] == i0["iterations"]
+        assert torch.equal(x1, x0)
 
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-5)])
