@@ -203,9 +203,11 @@ cudaError_t launch_vcycle_full(const T* b, T* x, int64_t B, const FusedLevels& L
 bool spectral_mean_supported(int n1);
 size_t spectral_image_bytes(int n1);
 std::vector<uint8_t> spectral_image(int n1);
+// prec: 0, the exact form (both factors of every product split into two bfloat16 terms), is
+// the only one launched; other values return cudaErrorInvalidValue.
 cudaError_t launch_spectral_mean(const float* b, float* x, int64_t B, int n1, const void* img, double d, double e,
                                  double c, float* acc, int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st,
-                                 VColumns cols = VColumns());
+                                 VColumns cols = VColumns(), int prec = 0);
 cudaError_t spectral_take_error(bool* failed, cudaStream_t st);
 
 // Krylov kernels.  Reductions are deterministic: fixed grid, fixed order.

@@ -194,7 +194,7 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
     return SGOC_ERR_INVALID_ARG;
   }
 
-  if (o.mean_solve == 1 && (o.precision != SGOC_MIXED_FP32 || !spectral_mean_supported(nx - 1))) {
+  if (o.mean_solve != 0 && (o.precision != SGOC_MIXED_FP32 || !spectral_mean_supported(nx - 1))) {
     set_error("exact mean solves (mean_solve = 1) need mixed precision and nx = 64 or 128");
     return SGOC_ERR_UNSUPPORTED;
   }
@@ -378,7 +378,7 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
   off = align256(off + nnz_dn * 4); off = align256(off + nnz_dn * 8); off = align256(off + nnz_dn * 4);
   for (const UTab& u : pb->utabs) off += utab_bytes(u);
   off += 2 * align256(size_t(pb->n1) * 8) + 2 * align256(size_t(pb->n1) * 4);   // mass factor tables
-  if (o.mean_solve == 1) off += align256(spectral_image_bytes(pb->n1));            // exact mean solves
+  if (o.mean_solve != 0) off += align256(spectral_image_bytes(pb->n1));            // tensor-core mean solves
   pb->persistent_bytes = off;
   *out = pb;
   return SGOC_OK;
@@ -482,7 +482,7 @@ sgoc_status sgoc_problem_upload(sgoc_problem* pb, void* d_persistent, size_t byt
   // constant image of the exact mean solves: split sine-transform operands and mode table
   std::vector<uint8_t> spec;
   pb->dev.spec_img = nullptr;
-  if (pb->opt.mean_solve == 1) {
+  if (pb->opt.mean_solve != 0) {
     spec = spectral_image(pb->n1);
     pb->dev.spec_img = carve(spec.size());
     SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.spec_img, spec.data(), spec.size(), cudaMemcpyHostToDevice, st));

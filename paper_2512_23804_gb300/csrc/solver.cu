@@ -135,11 +135,11 @@ size_t precond_workspace_bytes(const sgoc_problem* pb, int esize) {
 template <typename T>
 static sgoc_status vcycle(const sgoc_problem* pb, PrecWS<T>& w, const T* b, T* xout, int64_t B, T* acc,
                           int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st, VColumns cols = VColumns()) {
-  if (pb->opt.mean_solve == 1) {
+  if (pb->opt.mean_solve != 0) {
     if constexpr (std::is_same<T, float>::value) {
       const Level& L0 = pb->levels[0];
       SGOC_LAUNCH(launch_spectral_mean(b, xout, B, pb->n1, pb->dev.spec_img, L0.diag, L0.edge, L0.corner, acc,
-                                       acc_ss, acc_L, acc_col0, st, cols));
+                                       acc_ss, acc_L, acc_col0, st, cols, pb->opt.mean_solve - 1));
       return SGOC_OK;
     } else {
       set_error("exact mean solves are float32 only");
@@ -1286,7 +1286,7 @@ struct SolveTask {
     cudaError_t e = cudaMemcpyAsync(x_out, L.k64.x, pb->N * sizeof(double), cudaMemcpyDeviceToDevice, st);
     pdl_fence(st);
     if (status == SGOC_OK && e != cudaSuccess) status = cuda_status(e, "copy solution");
-    if (status == SGOC_OK && pb->opt.mean_solve == 1) {
+    if (status == SGOC_OK && pb->opt.mean_solve != 0) {
       bool failed = false;
       e = spectral_take_error(&failed, st);
       if (e != cudaSuccess) status = cuda_status(e, "exact mean solve status");

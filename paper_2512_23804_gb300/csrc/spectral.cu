@@ -253,19 +253,18 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// D = A B over K = 16 * ksteps with the split operands: A_hi B_hi + A_hi B_lo + A_lo B_hi.
-// a_step / b_step give the byte offset of k-step s within an operand region.
-template <typename FA, typename FB>
-__device__ __forceinline__ void gemm3(uint32_t tmem, uint32_t a_hi, uint32_t a_lo, uint32_t a_lbo, uint32_t a_sbo,
-                                      uint32_t b_hi, uint32_t b_lo, uint32_t b_lbo, uint32_t b_sbo, uint32_t idesc,
-                                      int ksteps, FA a_step, FB b_step) {
+// D = A B over K = 16 * ksteps with the split operands: A_hi B_hi, plus A_hi B_lo when BLO and
+// A_lo B_hi when ALO.  a_step / b_step give the byte offset of k-step s within an operand region.
+template <bool ALO, bool BLO, typename FA, typename FB>
+__device__ __forceinline__ void gemm_split(uint32_t tmem, uint32_t a_hi, uint32_t a_lo, uint32_t a_lbo,
+                                           uint32_t a_sbo, uint32_t b_hi, uint32_t b_lo, uint32_t b_lbo,
+                                           uint32_t b_sbo, uint32_t idesc, int ksteps, FA a_step, FB b_step) {
   for (int s = 0; s < ksteps; ++s) {
     const uint32_t ao = a_step(s), bo = b_step(s);
-    const uint64_t ah = sw128_desc(a_hi + ao, a_lbo, a_sbo), al = sw128_desc(a_lo + ao, a_lbo, a_sbo);
-    const uint64_t bh = sw128_desc(b_hi + bo, b_lbo, b_sbo), bl = sw128_desc(b_lo + bo, b_lbo, b_sbo);
+    const uint64_t ah = sw128_desc(a_hi + ao, a_lbo, a_sbo), bh = sw128_desc(b_hi + bo, b_lbo, b_sbo);
     tc_mma(tmem, ah, bh, idesc, s > 0 ? 1u : 0u);
-    tc_mma(tmem, ah, bl, idesc, 1u);
-    tc_mma(tmem, al, bh, idesc, 1u);
+    if constexpr (BLO) tc_mma(tmem, ah, sw128_desc(b_lo + bo, b_lbo, b_sbo), idesc, 1u);
+    if constexpr (ALO) tc_mma(tmem, sw128_desc(a_lo + ao, a_lbo, a_sbo), bh, idesc, 1u);
   }
 }
 
@@ -281,9 +280,15 @@ __device__ int g_spec_err = 0;
 // added when cols.acc_add (the V-cycle's conventions).  img is the constant image of the
 // split S operands and the mode table; (l0, l1, l2) the eigenvalue coefficients,
 // lambda_ij = l0 + l1 (t_i + t_j) + l2 t_i t_j with t_i = 1 - cos th_i.
-// 256 threads: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its lane quarter) and
-// takes the column half w / 4 of every accumulator row; thread 0 issues the products.
-template <int NB>
+// 512 threads: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its lane quarter) and
+// takes the column quarter w / 4 of every accumulator row; thread 0 issues the products.
+// PREC 0: both factors of every product split (hi*hi + hi*lo + lo*hi, the exact solve), the
+// only form launched.  Measured and dropped: 1, the transform rounded to bfloat16 with the
+// data split (two products; 2.7e-3 from the exact inverse at 128 x 128), and 2, both rounded
+// (one product; also nonlinear at 5e-3).  The conditioning of the mean operator amplifies the
+// transform's rounding through the hGS sweep: at beta = 1e-2 the mixed 128 x 128 solve took
+// 351 (form 1) and 9000 (form 2) inner iterations instead of 43.
+template <int NB, int PREC>
 __global__ void __launch_bounds__(kSpecThreads, 1)
     spectral_mean_kernel(const float* __restrict__ bg, float* xg, int64_t B, const uint8_t* __restrict__ img,
                          float l0, float l1, float l2, float* acc, int64_t acc_ss, int acc_L, int acc_col0,
@@ -407,12 +412,13 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
   auto product = [&](bool left) {
     if (tid == 0) {
       tc_fence_after();
+      // right products: A the data, B the transform; left products: A the transform, B the data
       if (!left)
-        gemm3(tmem, s0 + G::oDh, s0 + G::oDl, 16, 1024, s0 + G::oSBh, s0 + G::oSBl, 16, 1024, idK, G::KSTEPS_NB,
-              stepA, stepB);
+        gemm_split<PREC <= 1, PREC == 0>(tmem, s0 + G::oDh, s0 + G::oDl, 16, 1024, s0 + G::oSBh, s0 + G::oSBl, 16,
+                                        1024, idK, G::KSTEPS_NB, stepA, stepB);
       else
-        gemm3(tmem, s0 + G::oSAh, s0 + G::oSAl, 16, 1024, s0 + G::oDh, s0 + G::oDl, 1024, G::SBO_MN, idMN, 8, stepA,
-              stepMN);
+        gemm_split<PREC == 0, PREC <= 1>(tmem, s0 + G::oSAh, s0 + G::oSAl, 16, 1024, s0 + G::oDh, s0 + G::oDl, 1024,
+                                        G::SBO_MN, idMN, 8, stepA, stepMN);
       tc_commit(bar_mma);
     }
     bool w = mbar_wait(bar_mma, parity);
@@ -571,11 +577,11 @@ std::vector<uint8_t> build_image(int n1) {
   return img;
 }
 
-template <int NB>
+template <int NB, int PREC>
 cudaError_t launch_nb(const float* b, float* x, int64_t B, const void* img, double d, double e, double c, float* acc,
                       int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st, VColumns cols) {
   using G = SpecGeo<NB>;
-  auto k = spectral_mean_kernel<NB>;
+  auto k = spectral_mean_kernel<NB, PREC>;
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
   if (err != cudaSuccess) return err;
   // eigenvalue coefficients in the cancellation-free form (t = 1 - cos th):
@@ -611,18 +617,22 @@ std::vector<uint8_t> spectral_image(int n1) {
 
 cudaError_t launch_spectral_mean(const float* b, float* x, int64_t B, int n1, const void* img, double d, double e,
                                  double c, float* acc, int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st,
-                                 VColumns cols) {
+                                 VColumns cols, int prec) {
   if (B == 0) return cudaSuccess;
-  if (!spectral_mean_supported(n1) || img == nullptr || (reinterpret_cast<uintptr_t>(img) & 15))
+  if (!spectral_mean_supported(n1) || img == nullptr || (reinterpret_cast<uintptr_t>(img) & 15) || prec < 0 ||
+      prec > 2)
     return cudaErrorInvalidValue;
   const int NB = n1 + 1, CPT = 128 / NB;
   const double tiles = double((B + CPT - 1) / CPT);
-  // tensor work: per tile 3 bf16 products for each of G1, G3 (128 x NB x NB) and G2, G4 (128 x 128 x NB)
+  // tensor work: per tile 3 - prec bf16 products for each of G1, G3 (128 x NB x NB) and G2, G4
+  // (128 x 128 x NB)
   const double n0 = double(n1) * n1;
   ProfScope ps(KK_MEAN_EXACT, st, 4.0 * double(B) * n0 * (acc ? 3 : 2),
-               tiles * 3.0 * 2.0 * 2.0 * 128.0 * NB * (double(NB) + 128.0));
-  cudaError_t err = n1 == 63 ? launch_nb<64>(b, x, B, img, d, e, c, acc, acc_ss, acc_L, acc_col0, st, cols)
-                             : launch_nb<128>(b, x, B, img, d, e, c, acc, acc_ss, acc_L, acc_col0, st, cols);
+               tiles * double(3 - prec) * 2.0 * 2.0 * 128.0 * NB * (double(NB) + 128.0));
+  cudaError_t err;
+  if (prec != 0) return cudaErrorInvalidValue;     // only the exact form is built (see the kernel)
+  err = n1 == 63 ? launch_nb<64, 0>(b, x, B, img, d, e, c, acc, acc_ss, acc_L, acc_col0, st, cols)
+                 : launch_nb<128, 0>(b, x, B, img, d, e, c, acc, acc_ss, acc_L, acc_col0, st, cols);
   add_launches(1);
   return err != cudaSuccess ? err : cudaGetLastError();
 }
