@@ -84,7 +84,7 @@ void sgoc_default_options(sgoc_options* o) {
   o->nu_post = 2;
   o->omega = 0.8;
   o->precision = SGOC_FP64;
-  o->inner_tol = 1e-3;
+  o->inner_tol = 5e-3;
   o->max_outer = 20;
   o->schur = 0;
   o->krylov = 0;
