@@ -82,6 +82,10 @@ VCYCLE_DRAM_BYTES_PER_COLUMN = 3681280 / 56
 # DRAM bytes of spectral_mean_kernel<128> (the exact mean solve) on 56 columns of the 128x128
 # workload, from one ncu capture: 3,744,768 B read + 0 B written
 MEAN_EXACT_DRAM_BYTES_PER_COLUMN = 3744768 / 56
+# DRAM bytes per float32 SG launch (all shapes) of the 128x128 mixed solve with the benchmark's
+# kernel choices, from one ncu capture of the solve kernel case: 4,276,229 B read + written (the
+# X panels, coefficient planes and outputs of the launch; about 2/3 of the algorithmic bytes)
+SG_DRAM_BYTES_PER_LAUNCH_128 = 4276229
 # tensor work of one tile (one 128 x 128 column) of the exact mean solve: 3 bf16 products for each of
 # the four 128 x 128 x 128 products with the sine transform, 2 flop per MAC
 MEAN_EXACT_FLOP_PER_TILE = 3 * 2 * 2 * 128 * 128 * (128 + 128)
@@ -545,6 +549,9 @@ def run_ours(args):
             cols = dv["bytes"] / dv["launches"] / (3 * 4 * pr_main.n)
             roof["traffic"] = VCYCLE_DRAM_BYTES_PER_COLUMN * cols
             roof["traffic_note"] = f"ncu DRAM bytes per column x {cols:.1f} columns per launch"
+        if dom == "sg_operator" and not esize_fp64 and pr_main.nx == 128 and SG_DRAM_BYTES_PER_LAUNCH_128:
+            roof["traffic"] = SG_DRAM_BYTES_PER_LAUNCH_128
+            roof["traffic_note"] = "ncu DRAM bytes per float32 SG launch of this solve (kernel case solve128)"
         if dom == "mean_exact" and pr_main.nx == 128 and MEAN_EXACT_DRAM_BYTES_PER_COLUMN:
             cols = dv["flops"] / dv["launches"] / MEAN_EXACT_FLOP_PER_TILE       # one column per tile
             roof["traffic"] = MEAN_EXACT_DRAM_BYTES_PER_COLUMN * cols
@@ -659,12 +666,23 @@ def run_kernel_case(args):
     sp = SGProblem.from_problem(pr, precision="mixed", mean_solve="exact" if case == "mean128" else "vcycle").upload()
     if case == "solve128":
         # a few MINRES iterations of the 128x128 workload (loose tolerance), launched eagerly
-        # (per-kernel timing on) so that a profiler sees ordinary launches, not graph nodes
+        # (per-kernel timing on) so that a profiler sees ordinary launches, not graph nodes, with
+        # the SG kernels the benchmark's tuning chooses on this workload in plain runs (quad on
+        # 32-node tiles for the KKT product, the operator and the visits of levels 2 and 3, the
+        # direct kernel for the others), pinned rather than tuned: tuning by timing inside a
+        # profiled process would time the variants under the profiler.  The profiler range
+        # (cudaProfilerStart / Stop, for `ncu --profile-from-start off`) holds the solves only.
         from paper_2512_23804_gb300 import abi
-        abi.profile_enable(True)
         sq = SGProblem.from_problem(pr, precision="mixed", tol=1e-2, mean_solve=args.mean_solve).upload()
+        for shape, var in enumerate([1, 1, 6, 6, 1, 1, 6, 6, 6, 1]):
+            sq.set_kernel(shape, var)
+        torch.cuda.synchronize()
+        abi.profile_enable(True)
+        torch.cuda.profiler.start()
         for _ in range(2):
             sq.solve()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
         abi.profile_enable(False)
     elif case in ("sg128", "sg512"):
         X = torch.randn(sp.n * sp.P, dtype=torch.float32, device="cuda")
