@@ -208,6 +208,17 @@ std::vector<uint8_t> spectral_image(int n1);
 cudaError_t launch_spectral_mean(const float* b, float* x, int64_t B, int n1, const void* img, double d, double e,
                                  double c, float* acc, int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st,
                                  VColumns cols = VColumns(), int prec = 0);
+// Merged launches over members with the same grid: member g's right-hand sides b[g], outputs
+// (x[g], or acc[g] with the shared strides) and mean-operator stencil (d, e, c) = stencil[g].
+struct SpecMulti {
+  int ng = 1;
+  const float* b[kMaxGroup]; float* x[kMaxGroup]; float* acc[kMaxGroup];
+  float l0[kMaxGroup], l1[kMaxGroup], l2[kMaxGroup];
+};
+cudaError_t launch_spectral_mean_group(const float* const* b, float* const* x, float* const* acc,
+                                       const double (*stencil)[3], int ng, int64_t B, int n1, const void* img,
+                                       int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st,
+                                       VColumns cols = VColumns());
 cudaError_t spectral_take_error(bool* failed, cudaStream_t st);
 
 // Krylov kernels.  Reductions are deterministic: fixed grid, fixed order.

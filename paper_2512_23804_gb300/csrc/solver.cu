@@ -373,17 +373,46 @@ static bool same_shape(const sgoc_problem* a, const sgoc_problem* b) {
          a->chaos == b->chaos && a->nterms == b->nterms &&
          a->opt.precision == b->opt.precision && a->opt.nu_pre == b->opt.nu_pre &&
          a->opt.nu_post == b->opt.nu_post && a->opt.omega == b->opt.omega &&
-         a->opt.cheb_steps == b->opt.cheb_steps && (a->nt > 0) == (b->nt > 0);
+         a->opt.cheb_steps == b->opt.cheb_steps && a->opt.mean_solve == b->opt.mean_solve &&
+         (a->nt > 0) == (b->nt > 0);
 }
 
 template <typename T>
 static bool hgs_mergeable(const std::vector<HgsMember<T>>& ms) {
   if (ms.size() < 2 || ms.size() > size_t(kMaxGroup)) return false;
-  const VPlan vp = plan_vcycle(ms[0].pb, sizeof(T));
-  if (vp.lf != 0 || vp.cluster) return false;
+  const int mean = ms[0].pb->opt.mean_solve;
   for (const auto& m : ms)
-    if (!same_shape(m.pb, ms[0].pb) || m.pb->opt.mean_solve != 0) return false;
-  return true;
+    if (!same_shape(m.pb, ms[0].pb) || m.pb->opt.mean_solve != mean) return false;
+  if (mean != 0) return std::is_same<T, float>::value;   // exact mean solves: one merged launch per visit
+  const VPlan vp = plan_vcycle(ms[0].pb, sizeof(T));
+  return vp.lf == 0 && !vp.cluster;
+}
+
+// the mean solves of one hGS level visit for every member (merged launches): the V-cycle, or
+// the exact solve by fast diagonalisation
+template <typename T>
+static sgoc_status mean_group(const std::vector<HgsMember<T>>& ms, const T* const* rhs, T* const* xo, T* const* acc,
+                              const FusedLevels* FL, int64_t B, int64_t acc_ss, int acc_L, int acc_col0,
+                              cudaStream_t st, VColumns cols) {
+  const sgoc_problem* pb = ms[0].pb;
+  const int ng = int(ms.size());
+  if (pb->opt.mean_solve != 0) {
+    if constexpr (std::is_same<T, float>::value) {
+      double sten[kMaxGroup][3];
+      for (int g = 0; g < ng; ++g) {
+        const Level& L0 = ms[g].pb->levels[0];
+        sten[g][0] = L0.diag; sten[g][1] = L0.edge; sten[g][2] = L0.corner;
+      }
+      SGOC_LAUNCH(launch_spectral_mean_group(rhs, xo, acc, sten, ng, B, pb->n1, pb->dev.spec_img, acc_ss, acc_L,
+                                             acc_col0, st, cols));
+      return SGOC_OK;
+    }
+    set_error("exact mean solves are float32 only");
+    return SGOC_ERR_UNSUPPORTED;
+  }
+  SGOC_LAUNCH(launch_vcycle_full_group<T>(rhs, xo, acc, FL, ng, B, T(pb->opt.omega), pb->opt.nu_pre, acc_ss, acc_L,
+                                          acc_col0, st, cols));
+  return SGOC_OK;
 }
 
 template <typename T>
@@ -398,9 +427,8 @@ static sgoc_status hgs_multi(const std::vector<HgsMember<T>>& ms, int slabs, cud
   const int64_t n = pb->n, ps = int64_t(P) * n;
   const bool one = slabs == 1;            // the single-CTA cycle stores strided columns otherwise
   FusedLevels FL[kMaxGroup];
-  for (int g = 0; g < ng; ++g) FL[g] = fused_levels_of(ms[g].pb, 0);
-  const T om = T(pb->opt.omega);
-  const int nu = pb->opt.nu_pre;
+  if (pb->opt.mean_solve == 0)
+    for (int g = 0; g < ng; ++g) FL[g] = fused_levels_of(ms[g].pb, 0);
   for (int step = 0; step < 2 * p + 1; ++step) {
     const bool first = step <= p;
     const int d = first ? step : 2 * p - step;
@@ -423,12 +451,11 @@ static sgoc_status hgs_multi(const std::vector<HgsMember<T>>& ms, int slabs, cud
     }
     if (first && one) {
       for (int g = 0; g < ng; ++g) { xo[g] = ms[g].V + int64_t(a0) * n; acc[g] = nullptr; }
-      SGOC_LAUNCH(launch_vcycle_full_group<T>(rhs, xo, acc, FL, ng, L, om, nu, 0, 1, 0, st, cols));
+      SGOC_TRY(mean_group<T>(ms, rhs, xo, acc, FL, L, 0, 1, 0, st, cols));
     } else {
       if (first) cols.acc_add = 0;                  // store (V was not zero-filled)
       for (int g = 0; g < ng; ++g) { xo[g] = nullptr; acc[g] = ms[g].V; }
-      SGOC_LAUNCH(launch_vcycle_full_group<T>(rhs, xo, acc, FL, ng, int64_t(slabs) * L, om, nu, ps, L, a0, st,
-                                              cols));
+      SGOC_TRY(mean_group<T>(ms, rhs, xo, acc, FL, int64_t(slabs) * L, ps, L, a0, st, cols));
     }
   }
   return SGOC_OK;
@@ -1736,16 +1763,22 @@ static sgoc_status tune_sg_shape(const SGArgs<T>& a, cudaStream_t st, cudaEvent_
                                  double* best_ms, int* best_v) {
   *best_v = -1;
   *best_ms = 1e30;
+  // each variant: two warm-up launches, then the best of three rounds of `reps` launches (one
+  // round alone was seen to pick a twice slower kernel now and then)
   for (int v = 0; v < kSGVariants; ++v) {
     if (!sg_variant_feasible(a, v)) continue;
     for (int w = 0; w < 2; ++w) SGOC_LAUNCH(launch_sg_variant<T>(a, v, st));
-    SGOC_CUDA_TRY(cudaEventRecord(e0, st));
-    for (int r = 0; r < reps; ++r) SGOC_LAUNCH(launch_sg_variant<T>(a, v, st));
-    SGOC_CUDA_TRY(cudaEventRecord(e1, st));
-    SGOC_CUDA_TRY(cudaEventSynchronize(e1));
-    float ms = 0;
-    SGOC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms / reps < *best_ms) { *best_ms = ms / reps; *best_v = v; }
+    double best_round = 1e30;
+    for (int round = 0; round < 3; ++round) {
+      SGOC_CUDA_TRY(cudaEventRecord(e0, st));
+      for (int r = 0; r < reps; ++r) SGOC_LAUNCH(launch_sg_variant<T>(a, v, st));
+      SGOC_CUDA_TRY(cudaEventRecord(e1, st));
+      SGOC_CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0;
+      SGOC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      best_round = std::min(best_round, double(ms) / reps);
+    }
+    if (best_round < *best_ms) { *best_ms = best_round; *best_v = v; }
   }
   if (*best_v >= 0) sg_set_variant(a, *best_v);
   return SGOC_OK;
@@ -1872,9 +1905,9 @@ static sgoc_status solve_batch_impl(int32_t count, sgoc_problem* const* pbs, voi
                                    static_cast<cudaStream_t>(streams[i]));
     if (s != SGOC_OK) tasks[i].fail(s);
   }
-  // merged schedule: problems of one shape whose V-cycles can run merged form groups;
+  // merged schedule: problems of one shape whose mean solves can run merged form groups;
   // their MINRES iterations run together (group_step), each level visit of the hGS
-  // sweeps as one SG and one V-cycle launch for the whole group
+  // sweeps as one SG and one mean-solve launch (V-cycle or exact) for the whole group
   struct Group { GroupRuntime gr; std::vector<int> members, active; bool inflight = false; };
   std::vector<std::unique_ptr<Group>> groups;
   if (merge) {

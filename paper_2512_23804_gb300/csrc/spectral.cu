@@ -288,12 +288,26 @@ __device__ int g_spec_err = 0;
 // (one product; also nonlinear at 5e-3).  The conditioning of the mean operator amplifies the
 // transform's rounding through the hGS sweep: at beta = 1e-2 the mixed 128 x 128 solve took
 // 351 (form 1) and 9000 (form 2) inner iterations instead of 43.
+// Merged launches (several problems of one grid): member g's tiles are blocks
+// [g * tiles, (g + 1) * tiles) of the grid, with its own right-hand sides, outputs and
+// eigenvalue coefficients selected by constant indices (they stay in parameter space).
 template <int NB, int PREC>
 __global__ void __launch_bounds__(kSpecThreads, 1)
     spectral_mean_kernel(const float* __restrict__ bg, float* xg, int64_t B, const uint8_t* __restrict__ img,
                          float l0, float l1, float l2, float* acc, int64_t acc_ss, int acc_L, int acc_col0,
-                         VColumns cols) {
+                         VColumns cols, const SpecMulti sm_) {
   using G = SpecGeo<NB>;
+  int64_t tile = blockIdx.x;
+  if (sm_.ng > 1) {
+    const int64_t tiles = (B + G::CPT - 1) / G::CPT;
+    const int g = int(tile / tiles);
+    tile -= int64_t(g) * tiles;
+#pragma unroll
+    for (int i = 1; i < kMaxGroup; ++i)
+      if (i == g) {
+        bg = sm_.b[i]; xg = sm_.x[i]; acc = sm_.acc[i]; l0 = sm_.l0[i]; l1 = sm_.l1[i]; l2 = sm_.l2[i];
+      }
+  }
   constexpr int NW = kSpecThreads / 32;              // warps
   constexpr int CPW = NB / (NW / 4);                 // accumulator columns per warp (16 or 32)
   extern __shared__ uint8_t spec_raw[];
@@ -320,7 +334,7 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
     mbar_expect_tx(bar_ld, uint32_t(G::IMG));
     bulk_g2s(s0, img, uint32_t(G::IMG), bar_ld);
   }
-  const int64_t col0 = int64_t(blockIdx.x) * G::CPT;
+  const int64_t col0 = tile * G::CPT;
   const float* bcol[G::CPT];
 #pragma unroll
   for (int c = 0; c < G::CPT; ++c) {
@@ -577,18 +591,25 @@ std::vector<uint8_t> build_image(int n1) {
   return img;
 }
 
+// eigenvalue coefficients in the cancellation-free form (t = 1 - cos th):
+// lambda = (d + 4e + 4c) - (2e + 4c)(t_i + t_j) + 4c t_i t_j
+static void lambda_coefs(double d, double e, double c, float* l0, float* l1, float* l2) {
+  *l0 = float(d + 4.0 * e + 4.0 * c);
+  *l1 = float(-(2.0 * e + 4.0 * c));
+  *l2 = float(4.0 * c);
+}
+
 template <int NB, int PREC>
 cudaError_t launch_nb(const float* b, float* x, int64_t B, const void* img, double d, double e, double c, float* acc,
-                      int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st, VColumns cols) {
+                      int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st, VColumns cols, const SpecMulti& sm) {
   using G = SpecGeo<NB>;
   auto k = spectral_mean_kernel<NB, PREC>;
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
   if (err != cudaSuccess) return err;
-  // eigenvalue coefficients in the cancellation-free form (t = 1 - cos th):
-  // lambda = (d + 4e + 4c) - (2e + 4c)(t_i + t_j) + 4c t_i t_j
-  const float l0 = float(d + 4.0 * e + 4.0 * c), l1 = float(-(2.0 * e + 4.0 * c)), l2 = float(4.0 * c);
+  float l0, l1, l2;
+  lambda_coefs(d, e, c, &l0, &l1, &l2);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned((B + G::CPT - 1) / G::CPT));
+  cfg.gridDim = dim3(unsigned((B + G::CPT - 1) / G::CPT * sm.ng));
   cfg.blockDim = dim3(kSpecThreads);
   cfg.dynamicSmemBytes = G::SMEM;
   cfg.stream = st;
@@ -598,7 +619,7 @@ cudaError_t launch_nb(const float* b, float* x, int64_t B, const void* img, doub
   cfg.attrs = at;
   cfg.numAttrs = pdl_take_fence(st) ? 0 : 1;
   return cudaLaunchKernelEx(&cfg, k, b, x, B, static_cast<const uint8_t*>(img), l0, l1, l2, acc, acc_ss, acc_L,
-                            acc_col0, cols);
+                            acc_col0, cols, sm);
 }
 
 bool spectral_mean_supported(int n1) { return n1 == 63 || n1 == 127; }
@@ -615,24 +636,50 @@ std::vector<uint8_t> spectral_image(int n1) {
   return {};
 }
 
+static cudaError_t launch_spectral_any(const float* b, float* x, int64_t B, int n1, const void* img, double d,
+                                       double e, double c, float* acc, int64_t acc_ss, int acc_L, int acc_col0,
+                                       cudaStream_t st, VColumns cols, int prec, const SpecMulti& sm);
+
 cudaError_t launch_spectral_mean(const float* b, float* x, int64_t B, int n1, const void* img, double d, double e,
                                  double c, float* acc, int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st,
                                  VColumns cols, int prec) {
+  static const SpecMulti solo{};
+  return launch_spectral_any(b, x, B, n1, img, d, e, c, acc, acc_ss, acc_L, acc_col0, st, cols, prec, solo);
+}
+
+cudaError_t launch_spectral_mean_group(const float* const* b, float* const* x, float* const* acc,
+                                       const double (*stencil)[3], int ng, int64_t B, int n1, const void* img,
+                                       int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st, VColumns cols) {
+  if (ng < 1 || ng > kMaxGroup) return cudaErrorInvalidValue;
+  SpecMulti sm{};
+  sm.ng = ng;
+  for (int g = 0; g < ng; ++g) {
+    if ((acc[g] != nullptr) != (acc[0] != nullptr)) return cudaErrorInvalidValue;
+    sm.b[g] = b[g]; sm.x[g] = x[g]; sm.acc[g] = acc[g];
+    lambda_coefs(stencil[g][0], stencil[g][1], stencil[g][2], &sm.l0[g], &sm.l1[g], &sm.l2[g]);
+  }
+  return launch_spectral_any(b[0], x[0], B, n1, img, stencil[0][0], stencil[0][1], stencil[0][2], acc[0], acc_ss,
+                             acc_L, acc_col0, st, cols, 0, sm);
+}
+
+static cudaError_t launch_spectral_any(const float* b, float* x, int64_t B, int n1, const void* img, double d,
+                                       double e, double c, float* acc, int64_t acc_ss, int acc_L, int acc_col0,
+                                       cudaStream_t st, VColumns cols, int prec, const SpecMulti& sm) {
   if (B == 0) return cudaSuccess;
   if (!spectral_mean_supported(n1) || img == nullptr || (reinterpret_cast<uintptr_t>(img) & 15) || prec < 0 ||
       prec > 2)
     return cudaErrorInvalidValue;
   const int NB = n1 + 1, CPT = 128 / NB;
-  const double tiles = double((B + CPT - 1) / CPT);
+  const double tiles = double((B + CPT - 1) / CPT) * sm.ng;
   // tensor work: per tile 3 - prec bf16 products for each of G1, G3 (128 x NB x NB) and G2, G4
   // (128 x 128 x NB)
   const double n0 = double(n1) * n1;
-  ProfScope ps(KK_MEAN_EXACT, st, 4.0 * double(B) * n0 * (acc ? 3 : 2),
+  ProfScope ps(KK_MEAN_EXACT, st, 4.0 * double(B) * sm.ng * n0 * (acc ? 3 : 2),
                tiles * double(3 - prec) * 2.0 * 2.0 * 128.0 * NB * (double(NB) + 128.0));
   cudaError_t err;
   if (prec != 0) return cudaErrorInvalidValue;     // only the exact form is built (see the kernel)
-  err = n1 == 63 ? launch_nb<64, 0>(b, x, B, img, d, e, c, acc, acc_ss, acc_L, acc_col0, st, cols)
-                 : launch_nb<128, 0>(b, x, B, img, d, e, c, acc, acc_ss, acc_L, acc_col0, st, cols);
+  err = n1 == 63 ? launch_nb<64, 0>(b, x, B, img, d, e, c, acc, acc_ss, acc_L, acc_col0, st, cols, sm)
+                 : launch_nb<128, 0>(b, x, B, img, d, e, c, acc, acc_ss, acc_L, acc_col0, st, cols, sm);
   add_launches(1);
   return err != cudaSuccess ? err : cudaGetLastError();
 }

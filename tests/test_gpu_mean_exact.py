@@ -152,14 +152,19 @@ def test_exact_mean_mixed_solve_reaches_float64_residual(nx, shape, beta):
     assert rel(xh, host(x64)) <= 1e-6
 
 
-def test_exact_mean_solve_batch_equals_alone():
-    """Concurrent solves with exact mean solves return the solutions of the solo runs."""
+@pytest.mark.parametrize("merged", [False, True], ids=["streams", "merged"])
+@pytest.mark.parametrize("nx,nt", [(64, 0), (128, 0), (64, 2)], ids=["64", "128", "64_nt2"])
+def test_exact_mean_solve_batch_equals_alone(merged, nx, nt):
+    """Concurrent solves with exact mean solves return the solutions of the solo runs: on
+    independent streams, and in the merged schedule, where each hGS level visit is one mean-solve
+    launch over all members (member tables; at 64 x 64 two columns share a tile, but never two
+    members)."""
     from paper_2512_23804_gb300 import SGProblem, solve_batch
-    prs = [dataclasses.replace(si.random_small(390 + i, nx=64, M=2, p=2, beta=b), mean_solve="exact")
+    prs = [dataclasses.replace(si.random_small(390 + i, nx=nx, M=3, p=2, nt=nt, beta=b), mean_solve="exact")
            for i, b in enumerate([1e-2, 1e-4, 1e-6])]
     alone = [host(SGProblem.from_problem(pr, precision="mixed").solve()[0]) for pr in prs]
     sps = [SGProblem.from_problem(pr, precision="mixed") for pr in prs]
-    xs, infos = solve_batch(sps)
+    xs, infos = solve_batch(sps, merged=merged)
     for x, a, info in zip(xs, alone, infos):
         assert info["status_name"] == "SGOC_OK"
         assert np.array_equal(host(x), a)
