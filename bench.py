@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--mean-solve", choices=["exact", "vcycle"], default="exact",
                     help="mean solves of the mixed-precision preconditioner: exact (fast diagonalisation on "
                          "the tensor cores) or one V-cycle; float64 solves always use the V-cycle")
+    ap.add_argument("--mass-solve", choices=["exact", "chebyshev"], default="exact",
+                    help="mass blocks of the preconditioner (Sec. 5): exact (the Cholesky option; in float32 "
+                         "on these grids by fast diagonalisation on the tensor cores) or Chebyshev-5")
     ap.add_argument("--serve", action="store_true",
                     help="serving stream: the first --requests seeded requests through the server")
     ap.add_argument("--requests", type=int, default=2000, help="serving stream length with --serve")
@@ -177,15 +180,15 @@ def blas_threads():
     return host_cores()
 
 
-def oracle_full_solve(beta, mode="vcycle"):
+def oracle_full_solve(beta, mode="vcycle", args=None):
     """One complete float64 oracle solve of the 128x128 workload (set-up, right-hand side,
     preconditioner construction and preconditioned MINRES to the 1e-8 rule) with the mean solves
-    of `mode` (one V-cycle, or exact: the oracle's sparse LU); returns (seconds, iterations,
-    true relative residual)."""
+    of `mode` (one V-cycle, or exact: the oracle's sparse LU) and the GPU arm's mass blocks;
+    returns (seconds, iterations, true relative residual)."""
     import sg_inputs as si
     from oracle.solve import solve
     t0 = time.perf_counter()
-    res = solve(si.steady_128(beta), mode=mode)
+    res = solve(oracle_problem(beta, args) if args is not None else si.steady_128(beta), mode=mode)
     return time.perf_counter() - t0, res.iterations, res.rel_true
 
 
@@ -209,13 +212,21 @@ def oracle_mode(args):
     return "exact" if args.precision == "mixed" and args.mean_solve == "exact" else "vcycle"
 
 
-def cpu_baseline_full(beta=1e-2, mode="vcycle"):
-    sec, its, rel = oracle_full_solve(beta, mode)
+def oracle_problem(beta, args):
+    """The 128x128 workload at beta with the GPU arm's mass-block option."""
+    import dataclasses
+    import sg_inputs as si
+    return dataclasses.replace(si.steady_128(beta), mass_solve=args.mass_solve)
+
+
+def cpu_baseline_full(beta=1e-2, mode="vcycle", args=None):
+    sec, its, rel = oracle_full_solve(beta, mode, args)
+    mass = args.mass_solve if args is not None else "chebyshev"
     return {"value": 1.0 / sec, "unit": UNIT, "cores": host_cores(), "blas_threads": blas_threads(),
             "kind": "oracle",
             "sample": f"one complete oracle solve of the 128x128 workload at beta={beta:g} ({its} MINRES "
-                      f"iterations, true residual {rel:.2e}, mean solves: {mode}) in {sec:.1f} s, "
-                      f"set-up included"}
+                      f"iterations, true residual {rel:.2e}, mean solves: {mode}, mass blocks: {mass}) in "
+                      f"{sec:.1f} s, set-up included"}
 
 
 class OracleStream:
@@ -225,10 +236,11 @@ class OracleStream:
     number of Krylov iterations at a time and times exactly that work (the set-up of a new
     solve falls into the step that first needs it)."""
 
-    def __init__(self, betas, mode="vcycle"):
+    def __init__(self, betas, mode="vcycle", args=None):
         import threading
         self.betas = betas
         self.mode = mode
+        self.args = args
         self.sem = threading.Semaphore(0)
         self.cv = threading.Condition()
         self.products = 0
@@ -250,7 +262,7 @@ class OracleStream:
                 beta = self.betas[i % len(self.betas)]
                 i += 1
                 t0 = time.perf_counter()
-                pr = si.steady_128(beta)
+                pr = oracle_problem(beta, self.args) if self.args is not None else si.steady_128(beta)
                 d = SGData(pr)
                 Pc = BlockPreconditioner(d, mode=self.mode)
                 b = d.rhs()
@@ -302,7 +314,7 @@ def run_reference(args):
     # each timed step advances the running oracle solve by `chunk` KKT products (one per MINRES
     # iteration, one per true-residual check); the timed steps cover at least one whole solve
     chunk = max(1, math.ceil((mean_its + 2) / max(args.steps, 1)))
-    stream = OracleStream((1e-2, 1e-4, 1e-6), oracle_mode(args))
+    stream = OracleStream((1e-2, 1e-4, 1e-6), oracle_mode(args), args)
     for _ in range(args.warmup):
         stream.advance(1)
     p0 = stream.products
@@ -329,7 +341,7 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "solves_per_step": solves / args.steps,
                    "step": f"{chunk} KKT products of the running oracle solve",
-                   "mean_solves": oracle_mode(args)},
+                   "mean_solves": oracle_mode(args), "mass_blocks": args.mass_solve},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": host_cores(), "blas_threads": blas_threads(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -354,7 +366,9 @@ def run_ours(args):
     betas = si.STEADY_128_BETAS
     problems = [si.steady_128(b) for b in betas]
     mean_solve = args.mean_solve if args.precision == "mixed" else "vcycle"
-    sps = [SGProblem.from_problem(pr, precision=args.precision, mean_solve=mean_solve).upload() for pr in problems]
+    mass_solve = args.mass_solve
+    sps = [SGProblem.from_problem(pr, precision=args.precision, mean_solve=mean_solve, mass_solve=mass_solve).upload()
+           for pr in problems]
     for sp in sps:
         sp.workspace()
     # SG kernel per launch shape (process-wide; the three problems share their shapes); untimed
@@ -432,6 +446,9 @@ def run_ours(args):
                    "batching": "sequential" if args.sequential else "3 concurrent solves (sgoc_solve_batch, 3 streams)",
                    "mean_solves": ("exact: fast diagonalisation, tcgen05 tensor cores" if mean_solve == "exact"
                                    else "one V(2,2) multigrid cycle"),
+                   "mass_blocks": ("exact (Sec. 5 Cholesky option)" + (": fast diagonalisation, tcgen05 tensor cores"
+                                   if args.precision == "mixed" else ": Cholesky factors of M1")
+                                   if mass_solve == "exact" else "Chebyshev-5"),
                    "sg_kernels": "built-in choice" if sg_kernels is None else
                    dict(zip(["kkt", "operator"] + [f"hgs_level{d}" for d in range((len(sg_kernels) - 2) // 2)] +
                             [f"hgs_level{d}_first" for d in range((len(sg_kernels) - 2) // 2)],
@@ -469,7 +486,7 @@ def run_ours(args):
         # mixed solution of the step against the float64 GPU solution of the same problem
         if args.precision == "mixed":
             xmix = [x.clone() for x in xs]
-            sp64 = [SGProblem.from_problem(pr, precision="fp64").upload() for pr in problems]
+            sp64 = [SGProblem.from_problem(pr, precision="fp64", mass_solve=mass_solve).upload() for pr in problems]
             t64, it64, err = [], [], []
             for sp, x, xm in zip(sp64, xs, xmix):
                 sp.solve(out=x)                    # warm
@@ -496,7 +513,8 @@ def run_ours(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for pr, hx in zip(problems, pin):
-                sp = SGProblem.from_problem(pr, precision=args.precision, mean_solve=mean_solve).upload()
+                sp = SGProblem.from_problem(pr, precision=args.precision, mean_solve=mean_solve,
+                                            mass_solve=mass_solve).upload()
                 x, _ = sp.solve()
                 hx.copy_(x, non_blocking=True)
                 if rep == 0:
@@ -648,7 +666,7 @@ def run_ours(args):
         line["serving"] = serve_leg(args.serve_requests)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_full(1e-2, oracle_mode(args))
+        line["cpu_baseline"] = cpu_baseline_full(1e-2, oracle_mode(args), args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -673,7 +691,8 @@ def run_kernel_case(args):
         # profiled process would time the variants under the profiler.  The profiler range
         # (cudaProfilerStart / Stop, for `ncu --profile-from-start off`) holds the solves only.
         from paper_2512_23804_gb300 import abi
-        sq = SGProblem.from_problem(pr, precision="mixed", tol=1e-2, mean_solve=args.mean_solve).upload()
+        sq = SGProblem.from_problem(pr, precision="mixed", tol=1e-2, mean_solve=args.mean_solve,
+                                    mass_solve=args.mass_solve).upload()
         for shape, var in enumerate([1, 1, 6, 6, 1, 1, 6, 6, 6, 1]):
             sq.set_kernel(shape, var)
         torch.cuda.synchronize()

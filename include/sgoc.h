@@ -100,7 +100,7 @@ typedef struct {
   int32_t nu_post;       /* V-cycle post-smoothing sweeps (2) */
   double omega;          /* damped-Jacobi weight (0.8) */
   int32_t precision;     /* sgoc_precision (SGOC_FP64) */
-  double inner_tol;      /* mixed: inner MINRES relative tolerance (5e-3) */
+  double inner_tol;      /* mixed: inner MINRES relative tolerance (1e-3) */
   int32_t max_outer;     /* mixed: refinement steps cap (20) */
   int32_t schur;         /* time mode, Schur block of the preconditioner (0):
                             0: S~ = (1/tau) Z~ (D (x) M_gamma)^{-1} Z~ with Z~ block-diagonal in

@@ -215,6 +215,18 @@ struct SpecMulti {
   const float* b[kMaxGroup]; float* x[kMaxGroup]; float* acc[kMaxGroup];
   float l0[kMaxGroup], l1[kMaxGroup], l2[kMaxGroup];
 };
+// Column scaling of the solution (the mass blocks of the preconditioner), as launch_cheb's
+// scale_mode: 1 scales column col by 1 / s with the block, time-weight and H^gamma factors of
+// the mass blocks, 2 by the uniform factor `scale`, 0 not at all.
+struct SpecScale {
+  int mode = 0;                  // 0 none, 1 the mass blocks' factors, 2 the uniform factor `scale`
+  int P = 1, slabs = 1, nt = 0;
+  float tau = 1.0f, beta = 1.0f, gamma = 0.0f, scale = 1.0f;
+};
+// X = s M^{-1} B for ncols contiguous columns: the exact mass solve by the same fast
+// diagonalisation (M = M1 (x) M1, stencil (16, 4, 1) h^2 / 36).
+cudaError_t launch_spectral_mass(const float* B, float* X, int64_t ncols, int n1, const void* img, double h2_36,
+                                 const SpecScale& sc, cudaStream_t st);
 cudaError_t launch_spectral_mean_group(const float* const* b, float* const* x, float* const* acc,
                                        const double (*stencil)[3], int ng, int64_t B, int n1, const void* img,
                                        int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st,

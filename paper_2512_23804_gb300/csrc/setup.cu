@@ -84,7 +84,7 @@ void sgoc_default_options(sgoc_options* o) {
   o->nu_post = 2;
   o->omega = 0.8;
   o->precision = SGOC_FP64;
-  o->inner_tol = 5e-3;
+  o->inner_tol = 1e-3;
   o->max_outer = 20;
   o->schur = 0;
   o->krylov = 0;
@@ -378,7 +378,10 @@ sgoc_status sgoc_problem_create(const sgoc_problem_desc* d, const sgoc_options* 
   off = align256(off + nnz_dn * 4); off = align256(off + nnz_dn * 8); off = align256(off + nnz_dn * 4);
   for (const UTab& u : pb->utabs) off += utab_bytes(u);
   off += 2 * align256(size_t(pb->n1) * 8) + 2 * align256(size_t(pb->n1) * 4);   // mass factor tables
-  if (o.mean_solve != 0) off += align256(spectral_image_bytes(pb->n1));            // tensor-core mean solves
+  // the fast-diagonalisation image: exact mean solves, and exact mass blocks in float32
+  pb->spec = o.precision == SGOC_MIXED_FP32 && spectral_mean_supported(pb->n1) &&
+             (o.mean_solve != 0 || o.mass_solve == 1);
+  if (pb->spec) off += align256(spectral_image_bytes(pb->n1));
   pb->persistent_bytes = off;
   *out = pb;
   return SGOC_OK;
@@ -482,7 +485,7 @@ sgoc_status sgoc_problem_upload(sgoc_problem* pb, void* d_persistent, size_t byt
   // constant image of the exact mean solves: split sine-transform operands and mode table
   std::vector<uint8_t> spec;
   pb->dev.spec_img = nullptr;
-  if (pb->opt.mean_solve != 0) {
+  if (pb->spec) {
     spec = spectral_image(pb->n1);
     pb->dev.spec_img = carve(spec.size());
     SGOC_CUDA_TRY(cudaMemcpyAsync(pb->dev.spec_img, spec.data(), spec.size(), cudaMemcpyHostToDevice, st));

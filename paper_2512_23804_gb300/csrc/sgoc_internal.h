@@ -99,6 +99,7 @@ struct sgoc_problem {
   int nterms = 1;                    // coefficient planes: M + 1, or C(M + 2p, 2p)
   int lev_dist = 1;                  // largest chaos-level distance of a kept coupling
   bool sgr_ok = false;               // the register SG kernel is compiled for this (M, p) in this index order
+  bool spec = false;                 // the fast-diagonalisation image is uploaded (exact mean or mass solves)
   double length = 1.0;               // side of the square domain
   double beta = 0, gamma = 0, T = 1, tau = 1, kappa0 = 1, s = 0;  // s = sqrt((1+gamma)/beta)
   int n1 = 0, P = 0, slabs = 1;

@@ -582,7 +582,18 @@ template <> const float* mass_id_of<float>(const sgoc_problem* pb) { return pb->
 
 template <typename T>
 static cudaError_t launch_mass_blocks(const sgoc_problem* pb, const ChebArgs<T>& c, cudaStream_t st) {
-  if (pb->opt.mass_solve == 1) return launch_mass_exact<T>(c, mass_l_of<T>(pb), mass_id_of<T>(pb), st);
+  if (pb->opt.mass_solve == 1) {
+    // float32 on the grids of the tensor-core transform: the exact solve by fast diagonalisation
+    if constexpr (std::is_same<T, float>::value) {
+      if (pb->dev.spec_img != nullptr && c.scale_mode >= 0 && c.scale_mode <= 2) {
+        SpecScale sc;
+        sc.mode = c.scale_mode; sc.P = c.P; sc.slabs = c.slabs; sc.nt = c.nt;
+        sc.tau = c.tau; sc.beta = c.beta; sc.gamma = c.gamma; sc.scale = c.scale;
+        return launch_spectral_mass(c.B, c.X, c.ncols, pb->n1, pb->dev.spec_img, pb->mass_h2_36, sc, st);
+      }
+    }
+    return launch_mass_exact<T>(c, mass_l_of<T>(pb), mass_id_of<T>(pb), st);
+  }
   return launch_cheb<T>(c, st);
 }
 

@@ -295,7 +295,7 @@ template <int NB, int PREC>
 __global__ void __launch_bounds__(kSpecThreads, 1)
     spectral_mean_kernel(const float* __restrict__ bg, float* xg, int64_t B, const uint8_t* __restrict__ img,
                          float l0, float l1, float l2, float* acc, int64_t acc_ss, int acc_L, int acc_col0,
-                         VColumns cols, const SpecMulti sm_) {
+                         VColumns cols, const SpecMulti sm_, const SpecScale sc) {
   using G = SpecGeo<NB>;
   int64_t tile = blockIdx.x;
   if (sm_.ng > 1) {
@@ -377,11 +377,22 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
     const float* tt = reinterpret_cast<const float*>(sm + G::oT);
     const float tm = tt[row % NB];
     const float ar = fmaf(l1, tm, l0), br = fmaf(l2, tm, l1);
+    // the column's scale factor (mass blocks), folded into the table
+    float num = sc.mode == 2 ? sc.scale : 1.0f;
+    if (sc.mode == 1) {
+      const int64_t col = col0 + row / NB;
+      const int64_t spc = int64_t(sc.slabs) * sc.P;
+      const int64_t blk = col / spc, cc = col % spc;
+      const int t = int(cc / sc.P), al = int(cc % sc.P);
+      float sv = sc.nt > 0 ? sc.tau * ((sc.nt > 1 && (t == 0 || t == sc.nt - 1)) ? 0.5f : 1.0f) : 1.0f;
+      sv *= blk == 0 ? (al == 0 ? 1.0f : 1.0f + sc.gamma) : sc.beta;
+      num = 1.0f / sv;
+    }
 #pragma unroll
     for (int j0 = 0; j0 < CPW; j0 += 16) {
       float w[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) w[i] = __fdividef(1.0f, fmaf(br, tt[jbase + j0 + i], ar));
+      for (int i = 0; i < 16; ++i) w[i] = __fdividef(num, fmaf(br, tt[jbase + j0 + i], ar));
       tmem_st16(tmem + (uint32_t((warp & 3) * 32) << 16) + uint32_t(128 + jbase + j0), w);
     }
   }
@@ -601,7 +612,8 @@ static void lambda_coefs(double d, double e, double c, float* l0, float* l1, flo
 
 template <int NB, int PREC>
 cudaError_t launch_nb(const float* b, float* x, int64_t B, const void* img, double d, double e, double c, float* acc,
-                      int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st, VColumns cols, const SpecMulti& sm) {
+                      int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st, VColumns cols, const SpecMulti& sm,
+                      const SpecScale& sc) {
   using G = SpecGeo<NB>;
   auto k = spectral_mean_kernel<NB, PREC>;
   cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
@@ -619,7 +631,7 @@ cudaError_t launch_nb(const float* b, float* x, int64_t B, const void* img, doub
   cfg.attrs = at;
   cfg.numAttrs = pdl_take_fence(st) ? 0 : 1;
   return cudaLaunchKernelEx(&cfg, k, b, x, B, static_cast<const uint8_t*>(img), l0, l1, l2, acc, acc_ss, acc_L,
-                            acc_col0, cols, sm);
+                            acc_col0, cols, sm, sc);
 }
 
 bool spectral_mean_supported(int n1) { return n1 == 63 || n1 == 127; }
@@ -638,7 +650,8 @@ std::vector<uint8_t> spectral_image(int n1) {
 
 static cudaError_t launch_spectral_any(const float* b, float* x, int64_t B, int n1, const void* img, double d,
                                        double e, double c, float* acc, int64_t acc_ss, int acc_L, int acc_col0,
-                                       cudaStream_t st, VColumns cols, int prec, const SpecMulti& sm);
+                                       cudaStream_t st, VColumns cols, int prec, const SpecMulti& sm,
+                                       const SpecScale& sc = SpecScale());
 
 cudaError_t launch_spectral_mean(const float* b, float* x, int64_t B, int n1, const void* img, double d, double e,
                                  double c, float* acc, int64_t acc_ss, int acc_L, int acc_col0, cudaStream_t st,
@@ -662,9 +675,17 @@ cudaError_t launch_spectral_mean_group(const float* const* b, float* const* x, f
                              acc_L, acc_col0, st, cols, 0, sm);
 }
 
+cudaError_t launch_spectral_mass(const float* B, float* X, int64_t ncols, int n1, const void* img, double h2_36,
+                                 const SpecScale& sc, cudaStream_t st) {
+  static const SpecMulti solo{};
+  return launch_spectral_any(B, X, ncols, n1, img, 16.0 * h2_36, 4.0 * h2_36, h2_36, nullptr, 0, 1, 0, st,
+                             VColumns(), 0, solo, sc);
+}
+
 static cudaError_t launch_spectral_any(const float* b, float* x, int64_t B, int n1, const void* img, double d,
                                        double e, double c, float* acc, int64_t acc_ss, int acc_L, int acc_col0,
-                                       cudaStream_t st, VColumns cols, int prec, const SpecMulti& sm) {
+                                       cudaStream_t st, VColumns cols, int prec, const SpecMulti& sm,
+                                       const SpecScale& sc) {
   if (B == 0) return cudaSuccess;
   if (!spectral_mean_supported(n1) || img == nullptr || (reinterpret_cast<uintptr_t>(img) & 15) || prec < 0 ||
       prec > 2)
@@ -678,8 +699,8 @@ static cudaError_t launch_spectral_any(const float* b, float* x, int64_t B, int 
                tiles * double(3 - prec) * 2.0 * 2.0 * 128.0 * NB * (double(NB) + 128.0));
   cudaError_t err;
   if (prec != 0) return cudaErrorInvalidValue;     // only the exact form is built (see the kernel)
-  err = n1 == 63 ? launch_nb<64, 0>(b, x, B, img, d, e, c, acc, acc_ss, acc_L, acc_col0, st, cols, sm)
-                 : launch_nb<128, 0>(b, x, B, img, d, e, c, acc, acc_ss, acc_L, acc_col0, st, cols, sm);
+  err = n1 == 63 ? launch_nb<64, 0>(b, x, B, img, d, e, c, acc, acc_ss, acc_L, acc_col0, st, cols, sm, sc)
+                 : launch_nb<128, 0>(b, x, B, img, d, e, c, acc, acc_ss, acc_L, acc_col0, st, cols, sm, sc);
   add_launches(1);
   return err != cudaSuccess ? err : cudaGetLastError();
 }

@@ -31,7 +31,7 @@ class SGProblem:
 
     def __init__(self, nx, M, p, kappa, beta, yhat, gamma=0.0, nt=0, T=1.0, y0=None, *, chaos="legendre",
                  length=1.0, tol=1e-8,
-                 max_iter=1000, r=0, cheb_steps=5, nu=2, omega=0.8, precision="fp64", inner_tol=5e-3,
+                 max_iter=1000, r=0, cheb_steps=5, nu=2, omega=0.8, precision="fp64", inner_tol=1e-3,
                  max_outer=20, schur="diagonal", krylov="minres", restart=64, mass_solve="chebyshev",
                  precond="block", mean_solve="vcycle"):
         self._handle = None
