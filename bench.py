@@ -635,10 +635,14 @@ def run_ours(args):
             pr = mk()
             rec = {"kkt_unknowns": pr.kkt_size}
             xkeep = {}
-            variants = ["mixed", "fp64"] + (["mixed_exact_mean"] if pr.nx in (64, 128) else [])
+            # library defaults (V-cycle mean solves, Chebyshev-5 mass blocks), and on the grids of the
+            # tensor-core transform also the benchmark's setting (exact mean and mass solves)
+            variants = ["mixed", "fp64"] + (["mixed_exact"] if pr.nx in (64, 128) else [])
             for prec in variants:
-                sp = SGProblem.from_problem(pr, precision="mixed" if prec == "mixed_exact_mean" else prec,
-                                            mean_solve="exact" if prec == "mixed_exact_mean" else "vcycle").upload()
+                ex = prec == "mixed_exact"
+                sp = SGProblem.from_problem(pr, precision="mixed" if ex else prec,
+                                            mean_solve="exact" if ex else "vcycle",
+                                            mass_solve="exact" if ex else "chebyshev").upload()
                 if not args.no_autotune:
                     sp.autotune()
                 x, _ = sp.solve()
@@ -732,7 +736,9 @@ def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16, keep_every=1, que
     """Serving stream: the first `n_requests` seeded requests (grids 32..256, M 2..8, p 1..4,
     30 % time-dependent), admitted by the server's own memory-footprint check (a request that
     cannot fit the pool even when empty is rejected by sgoc_server_submit and counted), solved to a
-    1e-8 float64 residual in mixed precision.  Run once with every request arriving at t = 0
+    1e-8 float64 residual in mixed precision (on 64 x 64 and 128 x 128 grids with exact mean solves
+    and mass blocks on the tensor cores, float64 with exact mass blocks; library defaults
+    elsewhere).  Run once with every request arriving at t = 0
     (capacity mu), then as a Poisson stream at 0.8 mu; compared with sequential plain float64
     solves of the same requests on the same GPU, and each mixed result (every keep_every-th request
     while the kept solutions take at most keep_cap bytes of device memory) with its float64 one."""
@@ -743,12 +749,20 @@ def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16, keep_every=1, que
     reqs = [si.serving_request(i) for i in range(n_requests)]
     pool_bytes = int(min(torch.cuda.mem_get_info()[0] * 0.6, pool_cap_bytes))
 
+    def options(pr, precision):
+        # the benchmark's preconditioner setting where the tensor-core transform applies (64 x 64
+        # and 128 x 128 grids: exact mean solves in mixed precision, exact mass blocks), else
+        # the library defaults
+        if pr.nx not in (64, 128):
+            return {}
+        return dict(mass_solve="exact", mean_solve="exact" if precision == "mixed" else "vcycle")
+
     def run_stream(arrivals, keep):
         # Arrived requests wait in a client-side queue and are submitted while fewer than
         # queue_depth are outstanding and their float64 output buffers (the caller's memory,
         # outside the pool) stay under out_cap; latency runs from arrival to retirement.
         sv = SGServer(pool_bytes=pool_bytes, max_active=max_active)
-        sps = [SGProblem.from_problem(pr, precision="mixed") for pr in reqs]
+        sps = [SGProblem.from_problem(pr, precision="mixed", **options(pr, "mixed")) for pr in reqs]
         done, lat, rejected, xs, failed = {}, {}, [], {}, []
         queue, out_live, kept_bytes = [], {}, 0
         t0 = time.perf_counter()
@@ -822,7 +836,7 @@ def serve_leg(n_requests, pool_cap_bytes=120e9, max_active=16, keep_every=1, que
     for i, pr in enumerate(reqs):
         if i not in served:
             continue
-        sp = SGProblem.from_problem(pr, precision="fp64")
+        sp = SGProblem.from_problem(pr, precision="fp64", **options(pr, "fp64"))
         t1 = time.perf_counter()
         try:
             x, info = sp.solve()
