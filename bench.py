@@ -83,12 +83,12 @@ SG_KERNEL_NAMES = {0: "one-phase", 1: "quad-32", 2: "quad-16", 3: "two-phase", 4
 # workload, from one ncu capture: 3,681,280 B read + 0 B written
 VCYCLE_DRAM_BYTES_PER_COLUMN = 3681280 / 56
 # DRAM bytes of spectral_mean_kernel<128> (the exact mean solve) on 56 columns of the 128x128
-# workload, from one ncu capture: 3,744,768 B read + 0 B written
-MEAN_EXACT_DRAM_BYTES_PER_COLUMN = 3744768 / 56
+# workload, from one ncu capture: 3,748,608 B read + 0 B written
+MEAN_EXACT_DRAM_BYTES_PER_COLUMN = 3748608 / 56
 # DRAM bytes per float32 SG launch (all shapes) of the 128x128 mixed solve with the benchmark's
-# kernel choices, from one ncu capture of the solve kernel case: 4,276,229 B read + written (the
+# kernel choices, from one ncu capture of the solve kernel case: 4,292,532 B read + written (the
 # X panels, coefficient planes and outputs of the launch; about 2/3 of the algorithmic bytes)
-SG_DRAM_BYTES_PER_LAUNCH_128 = 4276229
+SG_DRAM_BYTES_PER_LAUNCH_128 = 4292532
 # tensor work of one tile (one 128 x 128 column) of the exact mean solve: 3 bf16 products for each of
 # the four 128 x 128 x 128 products with the sine transform, 2 flop per MAC
 MEAN_EXACT_FLOP_PER_TILE = 3 * 2 * 2 * 128 * 128 * (128 + 128)
