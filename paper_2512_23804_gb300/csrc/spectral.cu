@@ -44,7 +44,11 @@ namespace sgoc {
 namespace {
 
 constexpr int kSpecThreads = 512;        // four warps per tensor-memory lane quarter
-constexpr uint32_t kSpecTmemCols = 256;  // the float32 accumulator and the table of 1 / lambda
+// tensor-memory columns: the float32 accumulator (0 ..), the table of 1 / lambda (128 ..), the
+// split transform S_128 as the A operand of the left products (hi 256 .., lo 320 ..) and the
+// split data as the A operand of the right products (hi 384 .., lo 448 ..)
+constexpr uint32_t kSpecTmemCols = 512;
+constexpr uint32_t kColTab = 128, kColSh = 256, kColSl = 320, kColXh = 384, kColXl = 448;
 constexpr int kSpecSpin = 1 << 20;       // bounded mbarrier polls before the kernel gives up
 
 template <int NB>
@@ -177,11 +181,15 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool b_mn) {
   return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(b_mn ? 1 : 0) << 16) | (uint32_t(N >> 3) << 17) |
          (uint32_t(M >> 4) << 24);
 }
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+// D (+)= A B, one M = 128, K = 16 step issued by this thread: A in tensor memory (row m on lane
+// m, two bf16 of consecutive K per 32-bit column, the lower K in the low half), B in shared
+// memory by descriptor, D in tensor memory; the previous D is kept when acc != 0
+__device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t acc) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
           d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
@@ -237,11 +245,29 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) 
       : "memory");
 }
 
+// store N (8 or 16) 32-bit columns of this thread's lane, and wait for the store to complete
+template <int N>
+__device__ __forceinline__ void tmem_st_u32(uint32_t taddr, const uint32_t (&v)[N]) {
+  static_assert(N == 8 || N == 16, "8 or 16 columns");
+  if constexpr (N == 16) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};\n"
+        "tcgen05.wait::st.sync.aligned;\n" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+        "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+  } else {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n"
+        "tcgen05.wait::st.sync.aligned;\n" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+        : "memory");
+  }
+}
+
 __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
-}
-__device__ __forceinline__ void sts32(uint32_t addr, uint32_t a) {
-  asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(a) : "memory");
 }
 
 // v = hi + lo with hi = bf16(v), lo = bf16(v - hi), for a pair; packed bf16x2 words
@@ -253,18 +279,19 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// D = A B over K = 16 * ksteps with the split operands: A_hi B_hi, plus A_hi B_lo when BLO and
-// A_lo B_hi when ALO.  a_step / b_step give the byte offset of k-step s within an operand region.
-template <bool ALO, bool BLO, typename FA, typename FB>
-__device__ __forceinline__ void gemm_split(uint32_t tmem, uint32_t a_hi, uint32_t a_lo, uint32_t a_lbo,
-                                           uint32_t a_sbo, uint32_t b_hi, uint32_t b_lo, uint32_t b_lbo,
-                                           uint32_t b_sbo, uint32_t idesc, int ksteps, FA a_step, FB b_step) {
+// D = A B over K = 16 * ksteps with the split operands, A_hi B_hi + A_hi B_lo + A_lo B_hi: A in
+// tensor memory (k-step s at columns a_hi / a_lo + 8 s), B in shared memory (k-step s at byte
+// offset b_step(s) of its region)
+template <typename FB>
+__device__ __forceinline__ void gemm_split_ts(uint32_t tmem_d, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
+                                              uint32_t b_lo, uint32_t b_lbo, uint32_t b_sbo, uint32_t idesc, int ksteps,
+                                              FB b_step) {
   for (int s = 0; s < ksteps; ++s) {
-    const uint32_t ao = a_step(s), bo = b_step(s);
-    const uint64_t ah = sw128_desc(a_hi + ao, a_lbo, a_sbo), bh = sw128_desc(b_hi + bo, b_lbo, b_sbo);
-    tc_mma(tmem, ah, bh, idesc, s > 0 ? 1u : 0u);
-    if constexpr (BLO) tc_mma(tmem, ah, sw128_desc(b_lo + bo, b_lbo, b_sbo), idesc, 1u);
-    if constexpr (ALO) tc_mma(tmem, sw128_desc(a_lo + ao, a_lbo, a_sbo), bh, idesc, 1u);
+    const uint32_t bo = b_step(s), ao = uint32_t(8 * s);
+    const uint64_t bh = sw128_desc(b_hi + bo, b_lbo, b_sbo);
+    tc_mma_ts(tmem_d, a_hi + ao, bh, idesc, s > 0 ? 1u : 0u);
+    tc_mma_ts(tmem_d, a_hi + ao, sw128_desc(b_lo + bo, b_lbo, b_sbo), idesc, 1u);
+    tc_mma_ts(tmem_d, a_lo + ao, bh, idesc, 1u);
   }
 }
 
@@ -373,6 +400,7 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
   // while the right-hand sides arrive: this thread's part of the table 1 / lambda_(mu, nu) (row
   // mu = row mod NB, columns jbase ..) into tensor-memory columns 128 + nu, for the scaling step
   bool ok = mbar_wait(bar_ld, 0);
+  ok = __all_sync(0xffffffffu, ok) != 0;             // the tensor-memory stores below are warp-wide
   if (ok) {
     const float* tt = reinterpret_cast<const float*>(sm + G::oT);
     const float tm = tt[row % NB];
@@ -393,57 +421,69 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
       float w[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) w[i] = __fdividef(num, fmaf(br, tt[jbase + j0 + i], ar));
-      tmem_st16(tmem + (uint32_t((warp & 3) * 32) << 16) + uint32_t(128 + jbase + j0), w);
+      tmem_st16(tmem + (uint32_t((warp & 3) * 32) << 16) + kColTab + uint32_t(jbase + j0), w);
     }
+    // row `row` of the split S_128, K range 32 (warp / 4) .., into the A columns of the left
+    // products (16-byte chunks of the K-major image: 8 consecutive K each)
+    const int kq = (warp >> 2) * 32;
+    uint32_t sh[16], sl[16];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int o = off_kmajor(128, row, kq + 8 * i);
+      const uint4 h = *reinterpret_cast<const uint4*>(sm + G::oSAh + o);
+      const uint4 l = *reinterpret_cast<const uint4*>(sm + G::oSAl + o);
+      sh[4 * i] = h.x; sh[4 * i + 1] = h.y; sh[4 * i + 2] = h.z; sh[4 * i + 3] = h.w;
+      sl[4 * i] = l.x; sl[4 * i + 1] = l.y; sl[4 * i + 2] = l.z; sl[4 * i + 3] = l.w;
+    }
+    const uint32_t tq = tmem + (uint32_t((warp & 3) * 32) << 16) + uint32_t(kq / 2);
+    tmem_st_u32<16>(tq + kColSh, sh);
+    tmem_st_u32<16>(tq + kColSl, sl);
   }
   ok = mbar_wait(bar_in, 0) && ok;
   ok = __syncthreads_and(ok) != 0;
-  // L: the staged right-hand sides (row r = c NB + y, K index x), split, as the K-major A of G1;
-  // the padding row y = N1, column x = N1 and absent columns are zero.  A warp takes rows
-  // warp, warp + NW, ...; lane l the pairs x = 2 l (+ 64).
+  const uint32_t trow = tmem + (uint32_t((warp & 3) * 32) << 16);   // this warp's lane quarter
+  // v (this thread's accumulator columns jbase ..) split into the A operand of a right product:
+  // row `row`, K = jbase .., two K per tensor-memory column
+  auto store_a = [&](const float (&v)[CPW]) {
+    uint32_t h[CPW / 2], l[CPW / 2];
+#pragma unroll
+    for (int i = 0; i < CPW / 2; ++i) split2(v[2 * i], v[2 * i + 1], h[i], l[i]);
+    tmem_st_u32<CPW / 2>(trow + kColXh + uint32_t(jbase / 2), h);
+    tmem_st_u32<CPW / 2>(trow + kColXl + uint32_t(jbase / 2), l);
+  };
+  // L: the staged right-hand sides as the A of G1: row r = c NB + y, K index x; the padding row
+  // y = N1, column x = N1 and absent columns are zero.  Thread (row, jbase) reads x = jbase ..
+  // of its row (the rows of a warp are N1 words apart: no bank conflicts).
   if (ok) {
-    constexpr int PPL = NB / 64;                     // pairs per lane and row
-#pragma unroll 2
-    for (int r = warp; r < 128; r += NW) {
-      const int c = r / NB, y = r - c * NB;
-      bool live = y < G::N1;
-      uint32_t soff = 0;
+    const int c = row / NB, y = row - c * NB;
+    bool live = y < G::N1;
+    uint32_t soff = 0;
 #pragma unroll
-      for (int i = 0; i < G::CPT; ++i)
-        if (c == i) { live = live && bcol[i] != nullptr; soff = G::oStg + i * G::STG + span[i].off; }
-      const float* sc = reinterpret_cast<const float*>(sm + soff) + y * G::N1;
+    for (int i = 0; i < G::CPT; ++i)
+      if (c == i) { live = live && bcol[i] != nullptr; soff = G::oStg + i * G::STG + span[i].off; }
+    const float* sc = reinterpret_cast<const float*>(sm + soff) + y * G::N1;
+    float v[CPW];
 #pragma unroll
-      for (int h = 0; h < PPL; ++h) {
-        const int k = 2 * (lane + 32 * h);
-        const float va = live ? sc[k] : 0.f;
-        const float vb = live && k + 1 < G::N1 ? sc[k + 1] : 0.f;
-        uint32_t hi, lo;
-        split2(va, vb, hi, lo);
-        const int o = off_kmajor(128, r, k);
-        sts32(s0 + G::oDh + o, hi);
-        sts32(s0 + G::oDl + o, lo);
-      }
-    }
+    for (int i = 0; i < CPW; ++i) v[i] = live && jbase + i < G::N1 ? sc[jbase + i] : 0.f;
+    store_a(v);
   }
-  fence_async_smem();
+  tc_fence_before();
 
   constexpr uint32_t idK = idesc_bf16(128, NB, false), idMN = idesc_bf16(128, NB, true);
-  const auto stepA = [](int s) { return uint32_t((s >> 2) * (16 * 1024) + (s & 3) * 32); };    // K-major, 128 rows
   const auto stepB = [](int s) { return uint32_t((s >> 2) * (NB / 8 * 1024) + (s & 3) * 32); }; // K-major, NB rows
   const auto stepMN = [](int s) { return uint32_t(s * 2 * G::SBO_MN); };                        // MN-major
-  const uint32_t trow = tmem + (uint32_t((warp & 3) * 32) << 16);   // this warp's lane quarter
   uint32_t parity = 0;
   // issue one product (thread 0) and wait for it (every thread)
   auto product = [&](bool left) {
     if (tid == 0) {
       tc_fence_after();
-      // right products: A the data, B the transform; left products: A the transform, B the data
+      // right products: A the data (tensor memory), B the transform S_NB (K-major); left
+      // products: A the transform S_128 (tensor memory), B the data (MN-major)
       if (!left)
-        gemm_split<PREC <= 1, PREC == 0>(tmem, s0 + G::oDh, s0 + G::oDl, 16, 1024, s0 + G::oSBh, s0 + G::oSBl, 16,
-                                        1024, idK, G::KSTEPS_NB, stepA, stepB);
+        gemm_split_ts(tmem, tmem + kColXh, tmem + kColXl, s0 + G::oSBh, s0 + G::oSBl, 16, 1024, idK, G::KSTEPS_NB,
+                      stepB);
       else
-        gemm_split<PREC == 0, PREC <= 1>(tmem, s0 + G::oSAh, s0 + G::oSAl, 16, 1024, s0 + G::oDh, s0 + G::oDl, 1024,
-                                        G::SBO_MN, idMN, 8, stepA, stepMN);
+        gemm_split_ts(tmem, tmem + kColSh, tmem + kColSl, s0 + G::oDh, s0 + G::oDl, 1024, G::SBO_MN, idMN, 8, stepMN);
       tc_commit(bar_mma);
     }
     bool w = mbar_wait(bar_mma, parity);
@@ -452,28 +492,33 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
     tc_fence_after();
     return w;
   };
-  // this thread's half of accumulator row `row` -> split operand: MN-major B (K row `row`)
-  // or K-major A (row `row`), scaled by Lambda^{-1} when `scale`
+  // this thread's part of accumulator row `row` -> split operand: the MN-major B of a left
+  // product (K row `row`, shared memory), or, scaled by Lambda^{-1}, the A of a right product
+  // (row `row`, tensor memory)
   auto store_row = [&](bool mn, bool scale) {
     float v[CPW];
     tmem_ld<CPW>(trow + uint32_t(jbase), v);
     if (scale) {
       float w[CPW];
-      tmem_ld<CPW>(trow + uint32_t(128 + jbase), w);
+      tmem_ld<CPW>(trow + kColTab + uint32_t(jbase), w);
 #pragma unroll
       for (int i = 0; i < CPW; ++i) v[i] *= w[i];
     }
+    if (mn) {
 #pragma unroll
-    for (int q = 0; q < CPW / 8; ++q) {
-      uint32_t h[4], l[4];
+      for (int q = 0; q < CPW / 8; ++q) {
+        uint32_t h[4], l[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) split2(v[8 * q + 2 * i], v[8 * q + 2 * i + 1], h[i], l[i]);
-      const int o = mn ? off_mnmajor(G::SBO_MN, row, jbase + 8 * q) : off_kmajor(128, row, jbase + 8 * q);
-      sts128(s0 + G::oDh + o, h[0], h[1], h[2], h[3]);
-      sts128(s0 + G::oDl + o, l[0], l[1], l[2], l[3]);
+        for (int i = 0; i < 4; ++i) split2(v[8 * q + 2 * i], v[8 * q + 2 * i + 1], h[i], l[i]);
+        const int o = off_mnmajor(G::SBO_MN, row, jbase + 8 * q);
+        sts128(s0 + G::oDh + o, h[0], h[1], h[2], h[3]);
+        sts128(s0 + G::oDl + o, l[0], l[1], l[2], l[3]);
+      }
+      fence_async_smem();
+    } else {
+      store_a(v);
     }
     tc_fence_before();
-    fence_async_smem();
     __syncthreads();
   };
   __syncthreads();
