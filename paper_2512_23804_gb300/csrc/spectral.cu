@@ -231,19 +231,6 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[N]) {
   if constexpr (N == 32) tmem_ld32(taddr, v);
   else tmem_ld16(taddr, v);
 }
-// store 16 float32 columns of this thread's lane, and wait for the store to complete
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16};\n"
-      "tcgen05.wait::st.sync.aligned;\n" ::"r"(taddr),
-      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
-      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
-      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
-      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
-      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
-      : "memory");
-}
 
 // store N (8 or 16) 32-bit columns of this thread's lane, and wait for the store to complete
 template <int N>
@@ -397,11 +384,14 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
         *reinterpret_cast<float*>(spec_raw + pad + G::oStg + c * G::STG + span[c].off + 4 * i) = bcol[c][i];
     }
   }
-  // while the right-hand sides arrive: this thread's part of the table 1 / lambda_(mu, nu) (row
-  // mu = row mod NB, columns jbase ..) into tensor-memory columns 128 + nu, for the scaling step
   bool ok = mbar_wait(bar_ld, 0);
-  ok = __all_sync(0xffffffffu, ok) != 0;             // the tensor-memory stores below are warp-wide
-  if (ok) {
+  // Constant data derived from the image, written into tensor memory while the tensor cores
+  // work (after the image has landed): this thread's part of S_128, the A of the left products,
+  // and the first half of its part of the table 1 / lambda_(mu, nu) (row mu = row mod NB,
+  // columns jbase ..; tensor-memory columns kColTab + nu) during G1, the second half of the table
+  // during G2 (the reciprocals are bound by the special-function units); the table is first read
+  // by the scaling after G2.
+  auto table = [&](int half) {
     const float* tt = reinterpret_cast<const float*>(sm + G::oT);
     const float tm = tt[row % NB];
     const float ar = fmaf(l1, tm, l0), br = fmaf(l2, tm, l1);
@@ -416,15 +406,16 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
       sv *= blk == 0 ? (al == 0 ? 1.0f : 1.0f + sc.gamma) : sc.beta;
       num = 1.0f / sv;
     }
+    constexpr int H = CPW / 2;
+    const int j0 = jbase + half * H;
+    uint32_t w[H];
 #pragma unroll
-    for (int j0 = 0; j0 < CPW; j0 += 16) {
-      float w[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) w[i] = __fdividef(num, fmaf(br, tt[jbase + j0 + i], ar));
-      tmem_st16(tmem + (uint32_t((warp & 3) * 32) << 16) + kColTab + uint32_t(jbase + j0), w);
-    }
-    // row `row` of the split S_128, K range 32 (warp / 4) .., into the A columns of the left
-    // products (16-byte chunks of the K-major image: 8 consecutive K each)
+    for (int i = 0; i < H; ++i) w[i] = __float_as_uint(__fdividef(num, fmaf(br, tt[j0 + i], ar)));
+    tmem_st_u32<H>(tmem + (uint32_t((warp & 3) * 32) << 16) + kColTab + uint32_t(j0), w);
+  };
+  auto load_s = [&]() {
+    // row `row` of the split S_128, K range 32 (warp / 4) .. (16-byte chunks of the K-major
+    // image: 8 consecutive K each)
     const int kq = (warp >> 2) * 32;
     uint32_t sh[16], sl[16];
 #pragma unroll
@@ -438,7 +429,8 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
     const uint32_t tq = tmem + (uint32_t((warp & 3) * 32) << 16) + uint32_t(kq / 2);
     tmem_st_u32<16>(tq + kColSh, sh);
     tmem_st_u32<16>(tq + kColSl, sl);
-  }
+
+  };
   ok = mbar_wait(bar_in, 0) && ok;
   ok = __syncthreads_and(ok) != 0;
   const uint32_t trow = tmem + (uint32_t((warp & 3) * 32) << 16);   // this warp's lane quarter
@@ -474,7 +466,7 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
   const auto stepMN = [](int s) { return uint32_t(s * 2 * G::SBO_MN); };                        // MN-major
   uint32_t parity = 0;
   // issue one product (thread 0) and wait for it (every thread)
-  auto product = [&](bool left) {
+  auto product = [&](bool left, auto&& during) {
     if (tid == 0) {
       tc_fence_after();
       // right products: A the data (tensor memory), B the transform S_NB (K-major); left
@@ -486,6 +478,8 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
         gemm_split_ts(tmem, tmem + kColSh, tmem + kColSl, s0 + G::oDh, s0 + G::oDl, 1024, G::SBO_MN, idMN, 8, stepMN);
       tc_commit(bar_mma);
     }
+    __syncwarp();
+    during();                                        // work that overlaps the product
     bool w = mbar_wait(bar_mma, parity);
     parity ^= 1u;
     w = __syncthreads_and(w) != 0;
@@ -522,13 +516,14 @@ __global__ void __launch_bounds__(kSpecThreads, 1)
     __syncthreads();
   };
   __syncthreads();
-  if (ok) ok = product(false);                       // G1: D1 = X S
+  const auto nothing = [] {};
+  if (ok) ok = product(false, [&] { load_s(); table(0); });  // G1: D1 = X S
   if (ok) store_row(true, false);
-  if (ok) ok = product(true);                        // G2: D2 = S D1 = S X S
+  if (ok) ok = product(true, [&] { table(1); });     // G2: D2 = S D1 = S X S
   if (ok) store_row(false, true);                    // Lambda^{-1} o D2
-  if (ok) ok = product(false);                       // G3: D3 = Yh S
+  if (ok) ok = product(false, nothing);              // G3: D3 = Yh S
   if (ok) store_row(true, false);
-  if (ok) ok = product(true);                        // G4: D4 = S D3, the solution
+  if (ok) ok = product(true, nothing);               // G4: D4 = S D3, the solution
   spec_pdl_trigger();                                // only the write of the solution remains
   if (ok) {
     // the solution rows into the staging columns in the global layout of each output column
