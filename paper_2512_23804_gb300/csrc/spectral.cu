@@ -14,17 +14,18 @@
 // paper's hierarchical Gauss-Seidel) in place of one V-cycle.
 //
 // Layout on the tensor cores.  A tile holds 128 / NB columns of NB = n1 + 1 (padded) rows
-// stacked along M = 128; each product is D = A B with A (M x K) K-major and B (K x N) in
-// shared memory, D (128 lanes x NB columns, float32) in tensor memory:
-//   G1  D1 = X S          A = X (K-major),          B = S_NB (K-major)
-//   G2  D2 = S D1         A = S_128 (K-major),      B = D1   (MN-major)
+// stacked along M = 128; each product is D = A B with A (M x K) in tensor memory (row m on
+// lane m), B (K x N) in shared memory and D (128 lanes x NB columns, float32) in tensor memory:
+//   G1  D1 = X S          A = X,                    B = S_NB (K-major)
+//   G2  D2 = S D1         A = S_128,                B = D1   (MN-major)
 //   --  Yh = Lambda^{-1} o D2 (per element, in registers)
-//   G3  D3 = Yh S         A = Yh (K-major),         B = S_NB
+//   G3  D3 = Yh S         A = Yh,                   B = S_NB (K-major)
 //   G4  D4 = S D3         A = S_128,                B = D3   (MN-major)
-// S_128 is block-diagonal with 128 / NB copies of S_NB.  Thread r of the 128 owns row r
-// (tensor-memory lane r) of every D and writes its row of the next operand, so no
-// transpose is needed: the MN-major operand of G2 / G4 takes the rows of D as its K rows.
-// Operands use the 128-byte swizzled canonical layouts.
+// S_128 is block-diagonal with 128 / NB copies of S_NB; it is put into tensor memory once per
+// CTA.  Thread r of the 128 owns row r (tensor-memory lane r) of every D and writes its row of
+// the next operand: into its own lane when that operand is an A, as K row r of the MN-major B
+// of G2 / G4 otherwise, so no transpose is needed.  The shared-memory operands use the
+// 128-byte swizzled canonical layouts.
 //
 // Precision.  Both factors of every product are split into two bfloat16 terms
 // (v = hi + lo, hi = bf16(v), lo = bf16(v - hi)); a product accumulates
