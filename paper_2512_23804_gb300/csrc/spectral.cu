@@ -50,6 +50,9 @@ constexpr int kSpecThreads = 512;        // four warps per tensor-memory lane qu
 // split data as the A operand of the right products (hi 384 .., lo 448 ..)
 constexpr uint32_t kSpecTmemCols = 512;
 constexpr uint32_t kColTab = 128, kColSh = 256, kColSl = 320, kColXh = 384, kColXl = 448;
+static_assert(kColTab >= 128 && kColSh >= kColTab + 128 && kColSl >= kColSh + 64 && kColXh >= kColSl + 64 &&
+                  kColXl >= kColXh + 64 && kColXl + 64 <= kSpecTmemCols,
+              "accumulator (NB columns), table (NB), S_128 hi / lo (64 each), data hi / lo (NB / 2 each)");
 constexpr int kSpecSpin = 1 << 20;       // bounded mbarrier polls before the kernel gives up
 
 template <int NB>
@@ -76,6 +79,9 @@ struct SpecGeo {
   static constexpr int SMEM = oTm + 16 + 1024;         // + slack to align the base to 1024
   static constexpr int SBO_MN = (NB / 64) * 1024;      // MN-major: stride of 8-row K groups
 };
+
+static_assert(SpecGeo<128>::SMEM <= 232448 && SpecGeo<64>::SMEM <= 232448, "shared memory of one CTA");
+static_assert(SpecGeo<128>::oBar % 8 == 0 && SpecGeo<64>::oBar % 8 == 0, "mbarriers are 8-byte aligned");
 
 // byte offset of element (r, k) of an R-row, K-major operand, 128-byte swizzle:
 // 8-row x 128-byte atoms, 16-byte chunks XOR-ed with the row within the atom,

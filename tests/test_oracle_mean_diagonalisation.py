@@ -4,7 +4,8 @@ routine): every mean operator of the preconditioner -- the steady A~_1 = K_0 + s
 Eq. (mathcalZ) and the time slab operator A^_1 = (1 + tau s) M + tau K_0 of Eq. (A_hat) --
 is diagonalised by the orthonormal 2-D sine transform, with the eigenvalue of mode (i, j)
 lambda_ij = d + 2e (cos th_i + cos th_j) + 4c cos th_i cos th_j, th_i = pi i / nx, where
-(d, e, c) is the operator's 9-point stencil (centre, edge, corner).  No GPU is used."""
+(d, e, c) is the operator's 9-point stencil (centre, edge, corner); likewise the mass matrix
+M = M_1 (x) M_1 of the exact mass-block solves.  No GPU is used."""
 
 import numpy as np
 import pytest
@@ -64,3 +65,37 @@ def test_spectral_solve_equals_lu_solve(nx, nt):
     b = np.random.default_rng(3).standard_normal(n1 * n1)
     x = dst2(dst2(b.reshape(n1, n1)) / lam).reshape(-1)
     np.testing.assert_allclose(x, ExactSolve(A0).apply(b), rtol=1e-10, atol=1e-12 * np.abs(x).max())
+
+
+@pytest.mark.parametrize("nx,length", [(8, 1.0), (16, 1.0), (16, 2.0), (32, 1.0)])
+def test_mass_matrix_is_diagonal_in_the_sine_basis(nx, length):
+    """The exact mass-block solves (Sec. 5's exact option) use the same transform: the oracle's
+    Q1 mass matrix M = M_1 (x) M_1 on the interior nodes is the constant 9-point stencil
+    (16, 4, 1) h^2 / 36 (centre, edge, corner) and so has the eigenvalues
+    lambda_ij = d + 2e (cos th_i + cos th_j) + 4c cos th_i cos th_j in the sine basis.  The
+    stencil is read off the assembled matrix, not assumed; the factors h^2 / 36 and 16 : 4 : 1
+    are the textbook bilinear-element mass stencil."""
+    pr = si.random_small(41 + nx, nx=nx, M=2, p=1)
+    if length != 1.0:
+        import dataclasses
+        pr = dataclasses.replace(pr, length=length)
+    d = SGData(pr)
+    Mm = d.Mass.toarray()
+    n1 = nx - 1
+    h = length / nx
+    c0 = n1 + 1
+    dg, ed, co = Mm[c0, c0], Mm[c0, c0 + 1], Mm[c0, c0 + n1 + 1]
+    np.testing.assert_allclose([dg, ed, co], np.array([16.0, 4.0, 1.0]) * h * h / 36.0, rtol=1e-12)
+    cth = np.cos(np.pi * np.arange(1, n1 + 1) / nx)
+    lam = dg + 2 * ed * (cth[:, None] + cth[None, :]) + 4 * co * np.outer(cth, cth)
+    assert lam.min() > 0
+    rng = np.random.default_rng(nx)
+    for _ in range(3):
+        Xh = rng.standard_normal((n1, n1))
+        X = dst2(Xh)
+        MX = (Mm @ X.reshape(-1)).reshape(n1, n1)
+        np.testing.assert_allclose(dst2(MX), lam * Xh, rtol=1e-10, atol=1e-12 * np.abs(lam * Xh).max())
+    # the solve S_2 (Lambda^{-1} o S_2 b) equals the direct solve
+    b = rng.standard_normal(n1 * n1)
+    x = dst2(dst2(b.reshape(n1, n1)) / lam).reshape(-1)
+    np.testing.assert_allclose(Mm @ x, b, rtol=1e-10, atol=1e-12 * np.abs(b).max())
