@@ -99,3 +99,58 @@ def test_mass_matrix_is_diagonal_in_the_sine_basis(nx, length):
     b = rng.standard_normal(n1 * n1)
     x = dst2(dst2(b.reshape(n1, n1)) / lam).reshape(-1)
     np.testing.assert_allclose(Mm @ x, b, rtol=1e-10, atol=1e-12 * np.abs(b).max())
+
+
+def _bf16(x):
+    """Round float32 values to bfloat16 (nearest, ties to even), returned as float32."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def _split_product(A, B, split_a=True, split_b=True):
+    """A B from bfloat16 terms as the tensor cores form it: v = hi + lo (hi = bf16(v),
+    lo = bf16(v - hi)); hi*hi + hi*lo + lo*hi with exact products and a float32 result."""
+    A = np.asarray(A, dtype=np.float32)
+    B = np.asarray(B, dtype=np.float32)
+    Ah = _bf16(A)
+    Al = _bf16(A - Ah) if split_a else np.zeros_like(A)
+    Bh = _bf16(B)
+    Bl = _bf16(B - Bh) if split_b else np.zeros_like(B)
+    f = lambda x: x.astype(np.float64)
+    return (f(Ah) @ f(Bh) + f(Ah) @ f(Bl) + f(Al) @ f(Bh)).astype(np.float32)
+
+
+@pytest.mark.parametrize("split_transform,bound", [(True, 1e-4), (False, None)], ids=["split", "bf16_transform"])
+def test_split_bf16_transform_chain_error(split_transform, bound):
+    """The precision of the exact mean solve's four tensor-core products, emulated on the CPU:
+    with both factors of every product split into two bfloat16 terms the chain
+    S (Lambda^{-1} o (S X S)) S stays within 1e-4 of the float64 solve (the GPU tests' tolerance,
+    whose derivation puts it near 5e-5; the emulation gives 9e-6 for this input, the GPU kernel
+    8e-6 against the LU solve); with the transform rounded to a single bfloat16 term the error is
+    about 3e-3 (the dropped form: 2.7e-3 measured on the GPU at 128 x 128)."""
+    nx = 128
+    pr = si.random_small(61, nx=nx, M=2, p=1, beta=1e-4)
+    d = SGData(pr)
+    A0 = BlockPreconditioner(d, mode="exact").A0.tocsr()
+    n1 = nx - 1
+    c0 = n1 + 1
+    dg, ed, co = A0[c0, c0], A0[c0, c0 + 1], A0[c0, c0 + n1 + 1]
+    th = np.pi * np.arange(1, n1 + 1) / nx
+    lam = dg + 2 * ed * (np.cos(th)[:, None] + np.cos(th)[None, :]) + 4 * co * np.outer(np.cos(th), np.cos(th))
+    S = np.sqrt(2.0 / nx) * np.sin(np.outer(np.arange(1, n1 + 1), np.arange(1, n1 + 1)) * np.pi / nx)
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((n1, n1)).astype(np.float32)
+    exact = S @ ((S @ X.astype(np.float64) @ S) / lam) @ S
+    D1 = _split_product(X, S, split_b=split_transform)                      # X S
+    D2 = _split_product(S, D1, split_a=split_transform)                     # S D1
+    Yh = (D2.astype(np.float64) / lam).astype(np.float32)
+    D3 = _split_product(Yh, S, split_b=split_transform)                     # Yh S
+    D4 = _split_product(S, D3, split_a=split_transform)                     # S D3
+    err = np.linalg.norm(D4 - exact) / np.linalg.norm(exact)
+    # the solution is that of the assembled operator: A0 x = b
+    np.testing.assert_allclose(A0 @ exact.reshape(-1), X.reshape(-1), rtol=1e-8, atol=1e-8 * np.abs(X).max())
+    if bound is not None:
+        assert err <= bound, err
+    else:
+        assert 1e-3 <= err <= 1e-2, err
